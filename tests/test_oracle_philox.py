@@ -1,0 +1,70 @@
+"""Pins of the oracle's Philox4x32-10 (Salmon et al., SC'11) that do not use
+the oracle itself: uniformity, avalanche, distinctness, and the exactness of
+the 24-bit uniform mapping in binary32.  The exact stream is additionally
+pinned by agreement with the independent CUDA implementation (GPU tests)."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+
+def _words(n, key=(0x12345678, 0x9ABCDEF0)):
+    out = np.zeros((n, 4), np.uint32)
+    for i in range(n):
+        out[i] = O.philox((i, 0, 7, 3), key)
+    return out
+
+
+def test_uniform_chi2_and_moments():
+    w = _words(20000).ravel()
+    hist = np.bincount(w >> 24, minlength=256)
+    exp = w.size / 256
+    chi2 = ((hist - exp) ** 2 / exp).sum()
+    # 255 dof: mean 255, sd ~22.6; accept within 5 sd
+    assert abs(chi2 - 255) < 5 * 22.6
+    u = ((w >> 9).astype(np.float64) + 0.5) / 2 ** 23
+    assert abs(u.mean() - 0.5) < 5 * np.sqrt(1 / 12 / u.size)
+    assert abs(u.var() - 1 / 12) < 0.002
+
+
+def test_avalanche_ten_rounds():
+    """Flipping any one counter or key bit changes about half of the 128 output
+    bits; a round count or permutation mistake (e.g. 1-3 rounds, a dropped xor)
+    fails this."""
+    rng = np.random.default_rng(5)
+    flips = []
+    for _ in range(30):
+        ctr = rng.integers(0, 2 ** 32, 4, dtype=np.uint64).astype(np.uint32)
+        key = rng.integers(0, 2 ** 32, 2, dtype=np.uint64).astype(np.uint32)
+        base = O.philox(ctr, key)
+        for bit in range(0, 128, 9):
+            c2 = ctr.copy()
+            c2[bit // 32] ^= np.uint32(1 << (bit % 32))
+            o = O.philox(c2, key)
+            flips.append(sum(bin(int(a ^ b)).count("1") for a, b in zip(base, o)))
+        for bit in range(0, 64, 7):
+            k2 = key.copy()
+            k2[bit // 32] ^= np.uint32(1 << (bit % 32))
+            o = O.philox(ctr, k2)
+            flips.append(sum(bin(int(a ^ b)).count("1") for a, b in zip(base, o)))
+    f = np.array(flips)
+    assert abs(f.mean() - 64) < 1.0
+    assert f.min() > 30
+
+
+def test_distinct_and_unit_interval():
+    w = _words(5000)
+    rows = {tuple(r) for r in w}
+    assert len(rows) == 5000
+    u = O.draw(2110144940, 17, 3, 1)
+    assert np.all((u > 0) & (u < 1))
+    assert np.all(u.astype(np.float32).astype(np.float64) == u)
+
+
+def test_draw_is_counter_based():
+    a = O.draw(99, 123456789012, 5, 2)
+    b = O.draw(99, 123456789012, 5, 2)
+    c = O.draw(99, 123456789012, 5, 3)
+    d = O.draw(100, 123456789012, 5, 2)
+    assert np.array_equal(a, b)
+    assert not np.array_equal(a, c) and not np.array_equal(a, d)
