@@ -1,0 +1,323 @@
+"""Benchmark: coupled 3D PIC-MCC streamer step on one GB300.
+
+Workload (the 128^3 streamer): 128^3 cells of 20 um, plates at 0 V and
+5.12 kV (20 kV/cm), a 0.5 mm needle of 0.1 mm radius held at the top-plate
+potential, a Gaussian neutral seed (peak 1e19 m^-3, radius 0.1 mm) at the
+needle tip sampled as 1e6 super-particles, synthetic 7-process N2/O2 cross
+sections, dt = 2 ps, float32 particles, weight update on 1.25x growth with
+a 2e7 particle cap, multigrid Poisson every step.
+
+A step is one pass of the whole hot path: gather, push, null-collision MCC,
+children, boundaries, deposit, (cell sort, weight update when due), space
+charge, Poisson and field.  Metric: particle-updates/s (parents plus
+children advanced) over the device time of the timed steps; L2 is flushed
+between timed steps (outside the timed events).
+
+`--impl reference` times the CPU oracle on a bounded sample of the same
+workload (there is no reference implementation to install).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "electron push+MCC+deposit particle-updates/s on 1 GB300; % of HBM roofline"
+UNIT = "particle-updates/s"
+BYTES_PER_UPDATE = 96          # float32 state x,v,a,w (40 B) + id (8 B), read and written
+WORKLOAD = "streamer-128^3-fp32"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", type=int, default=32)
+    ap.add_argument("--n-initial", type=int, default=1_000_000)
+    ap.add_argument("--grid", type=int, default=128)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    return ap.parse_args()
+
+
+def workload(n_cells=128, n_initial=1_000_000):
+    import workloads as W
+    wl = W.streamer_128()
+    if n_cells != 128:
+        s = n_cells / 128
+        g = W.grid_spec(n_cells, n_cells, n_cells, 20e-6)
+        L = n_cells * 20e-6
+        wl.update(grid=g, L=L, v_top=20e5 * L, seed_center=(0.5 * L, 0.5 * L, L - wl["needle_length"]))
+        del s
+    wl["n_initial"] = n_initial
+    return wl
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, idx=0):
+        self.f = os.path.join("/tmp", f"clocks_{os.getpid()}.csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={idx}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=open(self.f, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.f):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(wl, budget_s=12.0, sample=20000, seed=2110144940):
+    """The oracle, as it stands, on a random sample of the seeded particles in
+    the plates' background field (one thread)."""
+    import oracle as O
+    import workloads as W
+    g = wl["grid"]
+    gas = W.synthetic_air()
+    mask = W.needle_mask(g, wl["needle_length"], wl["needle_radius"])
+    w0 = wl["seed_n0"] * np.pi ** 1.5 * wl["seed_radius"] ** 3 / wl["n_initial"]
+    E0 = (0.0, 0.0, -(wl["v_top"] - wl["v_bottom"]) / wl["L"])
+    m = O.Model(gas, wl["dt"], seed, 64, g, None, E0=E0, mask=mask)
+    full = O.seed_gaussian(m, wl["seed_n0"], wl["seed_radius"], wl["seed_center"], w0, 2 * wl["n_initial"])
+    v = full.view()
+    pick = np.sort(np.random.default_rng(1).choice(full.n, size=min(sample, full.n), replace=False))
+    p = O.Particles(8 * sample, {k: v[k][pick] for k in v})
+    n_cell = g["nx"] * g["ny"] * g["nz"]
+    upd, t = 0, 0.0
+    step = 0
+    while t < budget_s and step < 1000:
+        step += 1
+        q = np.zeros(n_cell, np.int64)
+        t0 = time.perf_counter()
+        rc, st = O.step(m, p, step, step == 1, q, None, None)
+        t += time.perf_counter() - t0
+        upd += st.n_start + st.n_children
+    return {"value": upd / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{len(pick)} of the {full.n} seeded electrons, {step} steps of push+MCC+deposit in the "
+                      f"plates' background field (no Poisson), {t:.1f} s single-threaded"}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle on a bounded sample, per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    import workloads as W
+    wl = workload(args.grid, args.n_initial)
+    g = wl["grid"]
+    gas = W.synthetic_air()
+    mask = W.needle_mask(g, wl["needle_length"], wl["needle_radius"])
+    w0 = wl["seed_n0"] * np.pi ** 1.5 * wl["seed_radius"] ** 3 / wl["n_initial"]
+    E0 = (0.0, 0.0, -(wl["v_top"] - wl["v_bottom"]) / wl["L"])
+    m = O.Model(gas, wl["dt"], 2110144940, 64, g, None, E0=E0, mask=mask)
+    full = O.seed_gaussian(m, wl["seed_n0"], wl["seed_radius"], wl["seed_center"], w0, 2 * wl["n_initial"])
+    v = full.view()
+    sample = 2000
+    pick = np.sort(np.random.default_rng(1).choice(full.n, size=sample, replace=False))
+    p = O.Particles(40 * sample, {k: v[k][pick] for k in v})
+    n_cell = g["nx"] * g["ny"] * g["nz"]
+    init = {k: v[k][pick] for k in v}
+    for s in range(1, args.warmup + 1):
+        O.step(m, p, s, s == 1, np.zeros(n_cell, np.int64), None, None)
+    upd, t = 0, 0.0
+    for s in range(args.warmup + 1, args.warmup + args.steps + 1):
+        if p.n > 4 * sample:  # keep each step a bounded sample: restart from the seeded sample
+            p = O.Particles(40 * sample, init)
+        q = np.zeros(n_cell, np.int64)
+        t0 = time.perf_counter()
+        rc, st = O.step(m, p, s, False, q, None, None)
+        t += time.perf_counter() - t0
+        upd += st.n_start + st.n_children
+    val = upd / t
+    out = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD, "sample_electrons": sample},
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"{sample} seeded electrons per step, push+MCC+deposit in the plates' "
+                                      f"background field"},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__ as ge
+    ge.build()
+    import workloads as W
+    from paper_2110_14494_gb300 import PicContext
+
+    wl = workload(args.grid, args.n_initial)
+    g = wl["grid"]
+    gas = W.synthetic_air()
+    mask = W.needle_mask(g, wl["needle_length"], wl["needle_radius"])
+    cap = int(wl["particle_cap"] * 1.6) if args.grid == 128 else int(max(8 * args.n_initial, 1 << 20))
+    w0 = wl["seed_n0"] * np.pi ** 1.5 * wl["seed_radius"] ** 3 / wl["n_initial"]
+    ctx = PicContext(gas, g, precision=args.precision, capacity=cap, seed=2110144940 + rank, dt=wl["dt"],
+                     mask=mask, n_ppc=wl["n_ppc"], w_min=wl["w_min"], growth_trigger=wl["growth_trigger"],
+                     particle_cap=wl["particle_cap"], sort_interval=20, coupled=True, v_lo=wl["v_bottom"],
+                     v_hi=wl["v_top"], v_mask=wl["v_top"], poisson_rtol=1e-6, poisson_max_cycles=200)
+    n0 = ctx.seed_gaussian(wl["seed_n0"], wl["seed_radius"], wl["seed_center"], w0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        ctx.step(1)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    u0, p0, s0 = ctx.progress()
+    ctx.profile(True)
+    clocks = Clocks(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    n_trace = []
+    for i in range(args.steps):
+        flush.fill_(i & 0xff)
+        ev[i][0].record(stream)
+        ctx.step(1)
+        ev[i][1].record(stream)
+        if i % 25 == 0:
+            n_trace.append(ctx.count())
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    prof = ctx.profile(False)
+    u1, p1, s1 = ctx.progress()
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    upd_t = torch.tensor([float(u1 - u0)], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(upd_t, op=dist.ReduceOp.SUM)
+    ms_max = float(ms_t.item())
+    value = float(upd_t.item()) / (ms_max * 1e-3)
+
+    # dominant kernel: the parent push (gather + push + MCC + deposit)
+    parents_per_launch = (p1 - p0) / max(prof["n_push"], 1)
+    push_ms = prof["ms_push"] / max(prof["n_push"], 1)
+    hbm, peak_kind = peaks()
+    achieved = BYTES_PER_UPDATE * parents_per_launch / (push_ms * 1e-3) / 1e9
+    phases = {k: round(prof[k], 3) for k in ("ms_push", "ms_children", "ms_field", "ms_reorder")}
+    print(json.dumps({"diag": "device-timed", "value": value, "ms_per_step": ms_max / args.steps,
+                      "phases_ms": phases, "parents_per_launch": parents_per_launch, "push_ms": push_ms,
+                      "achieved_GBs": achieved, "n_trace": n_trace, "launches": prof["n_launches"]}),
+          file=sys.stderr, flush=True)
+
+    # end to end through the C ABI with host buffers: each step uploads the
+    # particle state from pinned host memory, steps, and downloads it again
+    e2e = None
+    if not args.no_e2e:
+        n = ctx.count()
+        capn = int(ctx.cfg.capacity)
+        dt_ = torch.float32 if args.precision == 32 else torch.float64
+        host = [torch.empty(capn, dtype=dt_, pin_memory=True) for _ in range(10)] + \
+            [torch.empty(capn, dtype=torch.int64, pin_memory=True)]
+        ctx.download(host, capn)
+        ee = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        ue0 = ctx.progress()[0]
+        h2d = d2h = 0
+        t0 = time.perf_counter()
+        ee[0].record(stream)
+        for _ in range(args.e2e_steps):
+            ctx.upload(host, n, True)
+            h2d += n * (10 * (4 if args.precision == 32 else 8) + 8)
+            ctx.step(1)
+            n = ctx.download(host, capn)
+            d2h += n * (10 * (4 if args.precision == 32 else 8) + 8)
+        ee[1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        ue1 = ctx.progress()[0]
+        e2e = {"value": (ue1 - ue0) / wall, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d / args.e2e_steps), "d2h_bytes_per_step": int(d2h / args.e2e_steps),
+               "steps": args.e2e_steps}
+
+    base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base = cpu_baseline(wl)
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == 32 else "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD if args.grid == 128 else f"streamer-{args.grid}^3",
+                       "grid": [g["nx"], g["ny"], g["nz"]], "dx_um": 20, "n_initial": n0,
+                       "particle_cap": wl["particle_cap"], "dt_ps": 2, "poisson": "multigrid rtol 1e-6 every step",
+                       "l2": "flushed between timed steps (256 MB write outside the timed events)",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "particles_trace": n_trace},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None, "kernel": "k_push<float,PIC>",
+                         "peak_source": peak_kind,
+                         "bytes_per_update": BYTES_PER_UPDATE, "parents_per_launch": parents_per_launch,
+                         "ms_per_launch": push_ms},
+            "phases_ms": phases,
+            "gpu_launches": int(prof["n_launches"]),
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": base,
+        }
+        print(json.dumps(out))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,271 @@
+/*
+ * picmcc.h -- C ABI of the GB300 PIC-MCC electron library.
+ *
+ * The library implements the particle model of Wang, Sun & Teunissen,
+ * "A comparison of particle and fluid models for positive streamer
+ * discharges in air" (arXiv 2110.14494), Sec. 2.1: electrons are
+ * super-particles advanced with the velocity-Verlet scheme (Eqs. 1-2) and
+ * collide with the neutral gas by the null-collision Monte Carlo method
+ * against rates tabulated from cross sections (Sec. 2.1.1, 2.1.5); they are
+ * mapped to the grid and the field is interpolated back with trilinear
+ * weights (Sec. 2.1.3); weights follow Eq. 3 with merge and split
+ * (Sec. 2.1.2); the field comes from Poisson's equation with the electrode
+ * held at its potential (Sec. 2.5); and a uniform-field swarm mode gives
+ * flux and bulk transport data (Sec. 2.2.2).
+ *
+ * Conventions for every call:
+ *  - Status codes: PIC_OK (0) or a negative PIC_ERR_*; no exception ever
+ *    crosses the ABI.  pic_last_error() gives a message for a context.
+ *  - Memory: the library never allocates device memory.  The caller passes
+ *    one device workspace of the size returned by the matching
+ *    *_workspace_bytes() call (alignment 256 bytes) and owns it; all
+ *    device-pointer arguments are caller-owned.  Host arrays are read during
+ *    the call only.
+ *  - Streams: work is enqueued on the stream given at init (or per call);
+ *    calls return without waiting unless they return data to the host
+ *    (statistics, particle read-back, swarm results), which synchronise that
+ *    stream.  One host thread per context.
+ *  - Grids are cell-centred, x fastest: index (k * ny + j) * nx + i, cell
+ *    (i, j, k) centred at origin + (i + 1/2, j + 1/2, k + 1/2) dx.
+ */
+#ifndef PICMCC_H
+#define PICMCC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *pic_stream_t; /* a cudaStream_t; NULL = legacy default stream */
+
+enum {
+    PIC_OK = 0,
+    PIC_ERR_ARG = -1,      /* invalid argument or configuration */
+    PIC_ERR_CUDA = -2,     /* a CUDA runtime call failed */
+    PIC_ERR_CAPACITY = -3, /* a particle buffer or queue ran full; the step's result is incomplete */
+    PIC_ERR_OVERFLOW = -4, /* a fixed-point value left its range */
+    PIC_ERR_TIMEOUT = -5,  /* an iteration limit was reached before convergence */
+    PIC_ERR_STATE = -6     /* call not valid in the context's current state */
+};
+
+enum { PIC_PROC_ELASTIC = 0, PIC_PROC_EXCITATION = 1, PIC_PROC_IONIZATION = 2, PIC_PROC_ATTACHMENT = 3 };
+
+#define PIC_MAX_PROC 16
+#define PIC_SWARM_NMOM 16
+#define PIC_SWARM_NRES 24
+
+/* Neutral gas as collision processes with tabulated cross sections
+ * (Sec. 2.1.5).  All pointers are host arrays read at init. */
+typedef struct pic_gas {
+    int n_proc;              /* 1..PIC_MAX_PROC (7 used at most by the fast table) */
+    int n_bins;              /* >= 2 nodes */
+    const double *eps;       /* [n_bins] node energies in eV, uniform in ln(eps) */
+    const double *sigma;     /* [n_proc][n_bins] cross sections, m^2 */
+    const int *kind;         /* [n_proc] PIC_PROC_* */
+    const double *threshold; /* [n_proc] energy loss / ionization energy, eV */
+    const double *density;   /* [n_proc] number density of the target species, m^-3 */
+    const double *mass;      /* [n_proc] target mass for elastic recoil, kg (0 = infinite) */
+} pic_gas;
+
+typedef struct pic_config {
+    int precision;            /* 32 or 64: arithmetic of the particle state and push */
+    int nx, ny, nz;           /* grid cells (each >= 2) */
+    double dx;                /* cell size, m */
+    double origin[3];         /* lower corner, m */
+    long long capacity;       /* particle slots per buffer (two buffers are kept) */
+    unsigned long long seed;  /* key of all random streams */
+    double dt;                /* time step, s */
+    pic_gas gas;
+    int n_ppc;                /* desired particles per cell, Eq. 3 (paper: 75) */
+    double w_min;             /* minimum desired weight (paper: 1) */
+    double growth_trigger;    /* weight update when N > trigger * N_last (paper: 1.25); <= 0 disables */
+    long long particle_cap;   /* predicted count above which all desired weights are raised (0 = none) */
+    int boundary;             /* 0: specular reflection at domain faces, 1: absorption */
+    int sort_interval;        /* sort particles by cell every this many steps (0 = never) */
+    /* coupled field solve inside pic_step (Sec. 2.5); coupled = 0 keeps the field set by pic_set_field */
+    int coupled;
+    double v_lo, v_hi;        /* plate potentials at z = origin and z = origin + nz dx, V */
+    double v_mask;            /* electrode potential, V */
+    double poisson_rtol;      /* relative residual target of the coupled solve (e.g. 1e-6) */
+    int poisson_max_cycles;   /* V-cycle limit per solve */
+} pic_config;
+
+/* Host-side particle arrays (float64, any n).  Positions m, velocities m/s,
+ * accelerations m/s^2 (the a(t) of Eq. 2 carried between steps), weights. */
+typedef struct pic_particles_host {
+    double *x, *y, *z, *vx, *vy, *vz, *ax, *ay, *az, *w;
+    uint64_t *id;
+} pic_particles_host;
+
+typedef struct pic_step_stats {
+    long long n_start, n_end;          /* live particles before the first / after the last step */
+    long long n_events;                /* candidate collisions that fell inside the step */
+    long long n_null;                  /* of which null */
+    long long n_coll[PIC_MAX_PROC];    /* real collisions per process */
+    long long n_children, n_attached, n_absorbed, n_clamped;
+    long long n_processed;             /* particle-updates (parents + children) */
+    long long n_weight_updates;        /* merge/split passes run */
+    long long n_sorts;
+    double w_ion, w_att, w_absorbed;   /* weights of ionization / attachment / absorption events */
+    int poisson_cycles;                /* V-cycles of the last coupled solve */
+    double poisson_rel_res;
+} pic_step_stats;
+
+typedef struct pic_ctx pic_ctx;
+
+/* Workspace size for pic_init. */
+size_t pic_workspace_bytes(const pic_config *cfg);
+
+/* Creates a context over caller memory.  d_mask: [nz][ny][nx] electrode
+ * cells (non-zero = conductor) in device memory, or NULL; it must outlive the
+ * context.  Builds the rate table (Sec. 2.1.1: nu_k = N_k sigma_k v) on the
+ * device; the particle set starts empty and ion grids at zero. */
+int pic_init(const pic_config *cfg, void *d_workspace, size_t workspace_bytes, const uint8_t *d_mask,
+             pic_stream_t stream, pic_ctx **out);
+
+void pic_destroy(pic_ctx *ctx);
+const char *pic_last_error(const pic_ctx *ctx);
+const char *pic_status_string(int status);
+
+/* Gaussian neutral seed (Sec. 2.3, Eq. 7 with a negative exponent):
+ * n(r) = n0 exp(-|r - center|^2 / radius^2).  Each cell outside the
+ * electrode gets floor(n dV / w0) particles plus one with probability equal
+ * to the remainder, uniform in the cell, at rest, weight w0; the positive-ion
+ * grid receives the same deposit.  Replaces the particle set. */
+int pic_seed_gaussian(pic_ctx *ctx, double n0, double radius, const double center[3], double w0,
+                      long long *n_out);
+
+/* Replaces the particle set with n host particles (ids must be unique). */
+int pic_set_particles(pic_ctx *ctx, long long n, const pic_particles_host *p, int accel_valid);
+
+/* Copies the particle set to host arrays of at least `cap` entries. */
+int pic_get_particles(pic_ctx *ctx, pic_particles_host *p, long long cap, long long *n_out);
+
+/* Sets the cell-centred field (V/m) from device arrays [nz][ny][nx] of
+ * float; with Ex == NULL the field is uniform and equal to E_uniform. */
+int pic_set_field(pic_ctx *ctx, const float *Ex, const float *Ey, const float *Ez, const double E_uniform[3]);
+
+/* Advances all electrons n_steps times (Sec. 2.1): trilinear gather, Verlet
+ * half-kick completing Eq. 2, collisional flight over dt with the
+ * null-collision method, children finishing the step, reflection at the
+ * domain faces, absorption by the electrode, fixed-point deposit of electrons
+ * and of ion-producing events; on schedule the cell sort and the weight
+ * update (Sec. 2.1.2); with cfg.coupled the space charge and Poisson solve
+ * that give the next step's field.  stats (host, optional) accumulates over
+ * the n_steps and synchronises the stream. */
+int pic_step(pic_ctx *ctx, int n_steps, pic_step_stats *stats);
+
+/* Deposits the current electrons and returns the fixed-point grids (units of
+ * 2^-32 physical particles per cell, int64) and the space charge
+ * rho = e (n_pos - n_neg - n_e) in C/m^3.  Any output may be NULL; all are
+ * device arrays [nz][ny][nx]. */
+int pic_deposit(pic_ctx *ctx, int64_t *q_e, int64_t *q_pos, int64_t *q_neg, double *rho);
+
+/* Runs the super-particle weight update now (Sec. 2.1.2, Eq. 3). */
+int pic_weight_update(pic_ctx *ctx);
+
+/* Number of live particles (synchronises). */
+int pic_count(pic_ctx *ctx, long long *n);
+
+/* Cumulative particle-updates (parents plus queued children advanced), of
+ * which parents, and steps since init (synchronises).  Any output may be NULL. */
+int pic_progress(pic_ctx *ctx, long long *particle_updates, long long *parent_updates, long long *steps);
+
+/* Per-phase device times, measured with CUDA events on the context stream. */
+typedef struct pic_profile_times {
+    double ms_push, ms_children, ms_field, ms_reorder; /* accumulated milliseconds */
+    long long n_push, n_children, n_field, n_reorder;  /* timed launches / phases */
+    long long n_launches;                              /* kernels pic_step launched since the last clear */
+} pic_profile_times;
+
+/* enable != 0 starts timing (cleared); out (optional) receives the
+ * accumulated times since the last clear, after which they are cleared. */
+int pic_profile(pic_ctx *ctx, int enable, pic_profile_times *out);
+
+/* Native-precision particle exchange with host memory (use pinned memory for
+ * asynchronous copies): arrays[0..9] = x, y, z, vx, vy, vz, ax, ay, az, w in
+ * the context precision (float or double), arrays[10] = uint64 ids.
+ * pic_upload replaces the particle set; pic_download writes the current set
+ * (including any not-yet-compacted zero-weight slots, which callers skip) and
+ * its size, and synchronises. */
+int pic_upload(pic_ctx *ctx, long long n, const void *const *arrays, int accel_valid);
+int pic_download(pic_ctx *ctx, void *const *arrays, long long cap, long long *n_out);
+
+/* Checkpoint: the particle set, ion grids, step counter and state flags
+ * into a host blob; *bytes in: blob capacity (or 0 to query), out: size. */
+int pic_save(pic_ctx *ctx, void *host_blob, size_t *bytes);
+int pic_load(pic_ctx *ctx, const void *host_blob, size_t bytes);
+
+/* ------------------------------------------------------------------ Poisson */
+/* -lap(phi) = rho / eps0 (Sec. 2.5; the sign printed there is read as a
+ * typo) on the cell-centred grid: Dirichlet phi = v_lo at the z = origin
+ * face and v_hi at the top face (ghost 2 phi_b - phi), homogeneous Neumann on
+ * the x and y faces, cells with mask != 0 held at v_mask.  Geometric
+ * multigrid V-cycles on the error equation in float32 inside a float64
+ * residual (defect correction) until ||b - A phi|| / ||b|| <= rtol.
+ * E = -grad(phi) by central differences at cell centres (float32). */
+typedef struct poisson_config {
+    int nx, ny, nz;
+    double dx;
+    double v_lo, v_hi, v_mask;
+} poisson_config;
+
+typedef struct poisson_stats {
+    int cycles;
+    double rel_res;
+} poisson_stats;
+
+size_t poisson_workspace_bytes(const poisson_config *pc);
+
+/* rho, mask, phi, Ex, Ey, Ez: device arrays [nz][ny][nx]; phi is the
+ * initial guess on entry and the solution on return; mask may be NULL;
+ * E outputs may be NULL.  Returns PIC_ERR_TIMEOUT if max_cycles ran out. */
+int poisson_solve(const poisson_config *pc, const double *rho, const uint8_t *mask, double *phi,
+                  float *Ex, float *Ey, float *Ez, double rtol, int max_cycles, void *d_workspace,
+                  size_t workspace_bytes, poisson_stats *stats, pic_stream_t stream);
+
+/* -------------------------------------------------------------------- swarm */
+/* Monte Carlo swarms in uniform fields (Sec. 2.2.2).  Each swarm starts
+ * n0 electrons at the origin with Maxwellian velocities at temperature kT,
+ * field E = -(E/N) N z-hat, and is advanced n_steps with the same collisions.
+ * Weighted moments are accumulated at the end of every step; adaptive
+ * resampling keeps counts in [n_lo, n_hi] (thinning with survival 1/2 and
+ * doubled weight above, duplication with halved weight below).
+ * Results per swarm (swarm_result.v):
+ *   0 W_flux  1 W_bulk  2 DL_flux  3 DT_flux  4 DL_bulk  5 DT_bulk
+ *   6 <eps> (eV)  7 k_ion  8 k_att (m^3/s)  9 alpha  10 eta (1/m)
+ *   11..21 one-sigma errors of 0..10 (10-block batch means)
+ *   22 final particle count  23 final total weight
+ * Moments per step (16): sw, swx, swy, swz, swx^2, swy^2, swz^2, swvx, swvy,
+ *   swvz, swxvx, swyvy, swzvz, sw eps, ionization weight, attachment weight. */
+typedef struct swarm_config {
+    int precision;           /* 32 or 64 */
+    pic_gas gas;
+    double n_gas;            /* total gas density N for E/N and the rate coefficients, m^-3 */
+    long long n0, n_lo, n_hi;
+    long long capacity;      /* particle slots per swarm and buffer (>= 2 n_hi) */
+    int n_steps;
+    double dt;
+    double kT_eV;
+    unsigned long long seed; /* swarm s uses seed + s */
+    double sample_from;      /* fraction of steps discarded before sampling (0.25) */
+} swarm_config;
+
+typedef struct swarm_result {
+    double v[PIC_SWARM_NRES];
+} swarm_result;
+
+size_t swarm_workspace_bytes(const swarm_config *sc, int n_swarms);
+
+/* EN_Td: host [n_swarms]; results: host [n_swarms]; moments (optional):
+ * host [n_swarms][n_steps][16]; counts (optional): host [n_swarms][n_steps]. */
+int swarm_run(const swarm_config *sc, int n_swarms, const double *EN_Td, void *d_workspace,
+              size_t workspace_bytes, swarm_result *results, double *moments, long long *counts,
+              pic_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PICMCC_H */

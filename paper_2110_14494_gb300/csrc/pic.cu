@@ -1,0 +1,1401 @@
+// PIC-MCC context, workspace layout, initialisation, cell sort, weight update,
+// step driver and the C ABI of include/picmcc.h.
+//
+// Compiled with --fmad=false: the seeding, sort keys and weight-update
+// arithmetic round every operation separately.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "poisson.cuh"
+#include "push.cuh"
+
+namespace pic {
+
+// ================================================================== scan
+// Exclusive prefix sum of n uint32 values into out[0..n]; out[n] = total.
+constexpr int kScanTile = 2048;
+
+__global__ void k_scan_tiles(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, long long n,
+                             uint32_t* __restrict__ sums) {
+    __shared__ uint32_t sh[kScanTile];
+    __shared__ uint32_t wsum[8];
+    const long long base = (long long)blockIdx.x * kScanTile;
+    for (int t = threadIdx.x; t < kScanTile; t += blockDim.x) {
+        const long long i = base + t;
+        sh[t] = i < n ? in[i] : 0u;
+    }
+    __syncthreads();
+    // each thread scans 8 consecutive values
+    const int t0 = threadIdx.x * 8;
+    uint32_t run = 0;
+    for (int q = 0; q < 8; ++q) { const uint32_t v = sh[t0 + q]; sh[t0 + q] = run; run += v; }
+    // warp-level exclusive scan of the per-thread totals
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t inc = run;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    uint32_t woff = 0;
+    for (int q = 0; q < w; ++q) woff += wsum[q];
+    const uint32_t off = woff + inc - run;
+    for (int q = 0; q < 8; ++q) sh[t0 + q] += off;
+    __syncthreads();
+    for (int t = threadIdx.x; t < kScanTile; t += blockDim.x) {
+        const long long i = base + t;
+        if (i < n) out[i] = sh[t];
+    }
+    if (threadIdx.x == blockDim.x - 1) sums[blockIdx.x] = off + run;
+}
+
+// Single block: exclusive scan of the tile sums in place; sums[nb] = total.
+__global__ void k_scan_sums(uint32_t* sums, int nb) {
+    __shared__ uint32_t carry;
+    __shared__ uint32_t wsum[8];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const uint32_t v = i < nb ? sums[i] : 0u;
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        uint32_t inc = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) wsum[w] = inc;
+        __syncthreads();
+        uint32_t woff = 0;
+        for (int q = 0; q < w; ++q) woff += wsum[q];
+        const uint32_t c = carry;
+        if (i < nb) sums[i] = c + woff + inc - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = c + woff + inc;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) sums[nb] = carry;
+}
+
+__global__ void k_scan_add(uint32_t* __restrict__ out, long long n, const uint32_t* __restrict__ sums, int nb) {
+    const uint32_t add = sums[blockIdx.x];
+    const long long base = (long long)blockIdx.x * kScanTile;
+    for (int t = threadIdx.x; t < kScanTile; t += blockDim.x) {
+        const long long i = base + t;
+        if (i < n) out[i] += add;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = sums[nb];
+}
+
+static int scan_blocks(long long n) { return (int)((n + kScanTile - 1) / kScanTile); }
+
+static cudaError_t scan_exclusive(const uint32_t* in, uint32_t* out, long long n, uint32_t* sums, cudaStream_t s) {
+    const int nb = scan_blocks(n > 0 ? n : 1);
+    k_scan_tiles<<<nb, 256, 0, s>>>(in, out, n, sums);
+    k_scan_sums<<<1, 256, 0, s>>>(sums, nb);
+    k_scan_add<<<nb, 256, 0, s>>>(out, n, sums, nb);
+    return cudaGetLastError();
+}
+
+static int grid_n(long long n, int cap_blocks = 152 * 16) {
+    long long b = (n + 255) / 256;
+    if (b > cap_blocks) b = cap_blocks;
+    return b < 1 ? 1 : (int)b;
+}
+
+// ================================================================== kernels
+// Rate table (Sec. 2.1.1 / 2.1.5): nu_k(eps_j) = N_k sigma_k(eps_j) v(eps_j) with
+// v = sqrt(2 e eps / m_e), evaluated in float64; row j holds the n_proc rates
+// and, in column 7, their sum; nu_max = max_j of the sum.
+template <class T>
+__global__ void k_rate_table(const double* __restrict__ eps, const double* __restrict__ sigma,
+                             const double* __restrict__ dens, int n_proc, int n_bins, T* __restrict__ tab,
+                             double* __restrict__ tab64, unsigned long long* numax_bits) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_bins) return;
+    const double v = sqrt(2.0 * kQ * eps[j] / kMe);
+    double tot = 0.0;
+    for (int k = 0; k < kTableStride; ++k) {
+        double r = 0.0;
+        if (k < n_proc) r = dens[k] * sigma[k * n_bins + j] * v;
+        if (k < 7) { tab[j * kTableStride + k] = (T)r; tab64[j * kTableStride + k] = r; }
+        tot += r;
+    }
+    tab[j * kTableStride + 7] = (T)tot;
+    tab64[j * kTableStride + 7] = tot;
+    atomicMax(numax_bits, (unsigned long long)__double_as_longlong(tot));
+}
+
+// Initial seeding (Sec. 2.3, Eq. 7 read with a negative exponent): per cell
+// floor(n dV / w0) particles plus one with probability equal to the remainder.
+__global__ void k_seed_count(Grid g, const uint8_t* __restrict__ mask, double n0, double R2, double cx, double cy,
+                             double cz, double w0, Keys K, uint32_t* __restrict__ cnt) {
+    const long long n = g.ncell();
+    const double dV = g.dx * g.dx * g.dx;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        if (mask && mask[c]) { cnt[c] = 0; continue; }
+        const int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / ((long long)g.nx * g.ny));
+        const double xc = g.ox + ((double)i + 0.5) * g.dx;
+        const double yc = g.oy + ((double)j + 0.5) * g.dx;
+        const double zc = g.oz + ((double)k + 0.5) * g.dx;
+        const double r2 = (xc - cx) * (xc - cx) + (yc - cy) * (yc - cy) + (zc - cz) * (zc - cz);
+        // same operation order as the definition: n0 exp(-r2 / R^2) dV / w0
+        const double expct = n0 * exp(-r2 / R2) * dV / w0;
+        const double fl = floor(expct);
+        long long m = (long long)fl;
+        const u32x4 o = philox(u32x4{(uint32_t)c, 0u, 0u, 0xB0000000u}, K.init0, K.init1);
+        if (unif<double>(o.x) < expct - fl) ++m;
+        if (m > 0x7fffffffLL) m = 0x7fffffffLL;
+        cnt[c] = (uint32_t)m;
+    }
+}
+
+template <class T>
+__global__ void k_seed_write(Grid g, const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ off, double w0,
+                             uint64_t id0, Keys K, Soa<T> p, long long cap, DevState* st) {
+    const long long n = g.ncell();
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const uint32_t m = cnt[c];
+        if (!m) continue;
+        const int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / ((long long)g.nx * g.ny));
+        for (uint32_t q = 0; q < m; ++q) {
+            const long long s = (long long)off[c] + q;
+            if (s >= cap) { atomicOr(&st->err, kErrOutCapacity); return; }
+            const u32x4 o = philox(u32x4{(uint32_t)c, q + 1u, 0u, 0xB0000000u}, K.init0, K.init1);
+            p.r[PX][s] = (T)(g.ox + ((double)i + unif<double>(o.x)) * g.dx);
+            p.r[PY][s] = (T)(g.oy + ((double)j + unif<double>(o.y)) * g.dx);
+            p.r[PZ][s] = (T)(g.oz + ((double)k + unif<double>(o.z)) * g.dx);
+            for (int d = VX; d <= AZ; ++d) p.r[d][s] = (T)0;
+            p.r[PW][s] = (T)w0;
+            p.id[s] = id0 + (uint64_t)s;
+        }
+    }
+}
+
+// Swarm start: Maxwellian components N(0, kT e / m_e) by Box-Muller on draw
+// (id, step 0, k 0); all at the origin, weight 1, ids 0..n-1.
+template <class T>
+__global__ void k_seed_maxwell(long long n, double sig, Keys K, Soa<T> p) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const u32x4 o = draw_words(K, (uint64_t)i, 0u, 0u);
+        const double u0 = unif<double>(o.x), u1 = unif<double>(o.y), u2 = unif<double>(o.z), u3 = unif<double>(o.w);
+        const double r1 = sqrt(-2.0 * log(u0)), r2 = sqrt(-2.0 * log(u2));
+        double s1, c1, s3, c3;
+        sincospi(2.0 * u1, &s1, &c1);
+        sincospi(2.0 * u3, &s3, &c3);
+        p.r[VX][i] = (T)(sig * r1 * c1);
+        p.r[VY][i] = (T)(sig * r1 * s1);
+        p.r[VZ][i] = (T)(sig * r2 * c3);
+        p.r[PX][i] = p.r[PY][i] = p.r[PZ][i] = (T)0;
+        p.r[AX][i] = p.r[AY][i] = p.r[AZ][i] = (T)0;
+        p.r[PW][i] = (T)1;
+        p.id[i] = (uint64_t)i;
+    }
+}
+
+template <class T>
+__global__ void k_pack_field(const float* __restrict__ Ex, const float* __restrict__ Ey, const float* __restrict__ Ez,
+                             long long n, T* __restrict__ E4) {
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        E4[4 * c] = (T)Ex[c];
+        E4[4 * c + 1] = (T)Ey[c];
+        E4[4 * c + 2] = (T)Ez[c];
+        E4[4 * c + 3] = (T)0;
+    }
+}
+
+// n = q / (2^32 dV); rho = e (n_pos - n_neg - n_e).
+__global__ void k_fixed_to_rho(const long long* __restrict__ qe, const long long* __restrict__ qp,
+                               const long long* __restrict__ qn, long long n, double inv, double* __restrict__ rho) {
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const double ne = (double)qe[c] * inv, np = (double)qp[c] * inv, nn = (double)qn[c] * inv;
+        rho[c] = kQ * (np - nn - ne);
+    }
+}
+
+// Next step's input count; cursors that ran past the capacity (an error
+// already flagged) are clamped so no kernel reads beyond the buffers.
+__global__ void k_end_step(DevState* st, long long* count_slot, long long cap) {
+    const unsigned long long nc = st->n_child < (unsigned long long)cap ? st->n_child : (unsigned long long)cap;
+    st->n_updates += st->n_in + nc;
+    st->n_parents += st->n_in;
+    st->n_in = st->n_out < (unsigned long long)cap ? st->n_out : (unsigned long long)cap;
+    st->n_out = 0;
+    st->n_child = 0;
+    if (count_slot) *count_slot = (long long)st->n_in;
+}
+
+__global__ void k_set_count(DevState* st, unsigned long long n) {
+    st->n_in = n;
+    st->n_out = 0;
+    st->n_child = 0;
+    st->n_extra = 0;
+}
+
+// Cell index in the particle precision (the same decision as the electrode test).
+template <class T>
+__device__ __forceinline__ uint32_t cell_index(T x, T y, T z, T ox, T oy, T oz, T dx, int nx, int ny, int nz) {
+    const int i = fold_idx((int)floor((x - ox) / dx), nx);
+    const int j = fold_idx((int)floor((y - oy) / dx), ny);
+    const int k = fold_idx((int)floor((z - oz) / dx), nz);
+    return (uint32_t)(((long long)k * ny + j) * nx + i);
+}
+
+struct GridT {
+    double ox, oy, oz, dx;
+    int nx, ny, nz;
+};
+
+// ---------------------------------------------------------------- cell sort
+template <class T>
+__global__ void k_cell_count(const Soa<T> p, const DevState* st, GridT g, uint32_t* __restrict__ cnt,
+                             uint32_t* __restrict__ key, uint32_t* __restrict__ rank) {
+    const long long n = (long long)st->n_in;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const uint32_t c = cell_index<T>(p.r[PX][i], p.r[PY][i], p.r[PZ][i], (T)g.ox, (T)g.oy, (T)g.oz, (T)g.dx, g.nx,
+                                         g.ny, g.nz);
+        key[i] = c;
+        rank[i] = atomicAdd(&cnt[c], 1u);
+    }
+}
+
+template <class T>
+__global__ void k_scatter(const Soa<T> a, Soa<T> b, const DevState* st, const uint32_t* __restrict__ start,
+                          const uint32_t* __restrict__ key, const uint32_t* __restrict__ rank) {
+    const long long n = (long long)st->n_in;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long d = (long long)start[key[i]] + rank[i];
+#pragma unroll
+        for (int f = 0; f < 10; ++f) b.r[f][d] = a.r[f][i];
+        b.id[d] = a.id[i];
+    }
+}
+
+// ---------------------------------------------------------------- weight update
+// Sec. 2.1.2, Eq. 3: desired weight omega = max(W_cell / N_ppc, w_min); the
+// per-cell weight W is summed as integers rint(w 2^24) so it does not depend
+// on the order of the particles.
+constexpr double kS24 = 16777216.0;
+
+__device__ __forceinline__ double omega_of(long long W, int n_ppc, double w_min) {
+    return fmax((double)W / kS24 / (double)n_ppc, w_min);
+}
+
+template <class T>
+__global__ void k_cell_weight(const Soa<T> p, const uint32_t* __restrict__ start, long long ncell, int n_ppc,
+                              double w_min, DevState* st) {
+    long long acc = 0;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x) {
+        const uint32_t s0 = start[c], s1 = start[c + 1];
+        if (s0 == s1) continue;
+        long long W = 0;
+        for (uint32_t t = s0; t < s1; ++t) W += __double2ll_rn((double)p.r[PW][t] * kS24);
+        const double om = omega_of(W, n_ppc, w_min);
+        acc += __double2ll_rn((double)W / om);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd((unsigned long long*)&st->pred_total, (unsigned long long)acc);
+}
+
+template <class T> __device__ __forceinline__ double speed2_key(const Soa<T>& p, long long i) {
+    const T a = p.r[VX][i], b = p.r[VY][i], c = p.r[VZ][i];
+    const T r = (a * a + b * b) + c * c;
+    return (double)r;
+}
+
+struct MergeScratch {
+    double* key;
+    uint64_t* id;
+    uint32_t* idx;
+    double* skey;
+    uint64_t* sid;
+    uint32_t* sidx;
+};
+
+// One block per occupied cell.  Merge: candidates w < (2/3) omega ordered by
+// (|v|^2, id) are paired (0,1), (2,3), ...; the pair's weights are summed and
+// one member's state is kept with probability proportional to its weight
+// (draw keyed by the smaller id, the step and the round); rounds repeat while
+// two or more candidates remain.  Split: w > (3/2) omega is halved m times
+// (m minimal with w / 2^m <= (3/2) omega) and 2^m - 1 identical copies are
+// appended after the n sorted particles.
+template <class T>
+__global__ void __launch_bounds__(256) k_merge_split(Soa<T> p, long long n, const uint32_t* __restrict__ start,
+                                                     long long ncell, int n_ppc, double w_min, double scale,
+                                                     MergeScratch sc, Keys K, uint32_t step, long long cap,
+                                                     DevState* st) {
+    __shared__ int m_sh, m2_sh;
+    __shared__ long long wsum_sh;
+    for (long long c = blockIdx.x; c < ncell; c += gridDim.x) {
+        const uint32_t s0 = start[c], s1 = start[c + 1];
+        if (s0 == s1) continue;
+        if (threadIdx.x == 0) { m_sh = 0; wsum_sh = 0; }
+        __syncthreads();
+        long long Wp = 0;
+        for (uint32_t t = s0 + threadIdx.x; t < s1; t += blockDim.x) Wp += __double2ll_rn((double)p.r[PW][t] * kS24);
+        for (int o = 16; o > 0; o >>= 1) Wp += __shfl_xor_sync(kFull, Wp, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd((unsigned long long*)&wsum_sh, (unsigned long long)Wp);
+        __syncthreads();
+        const double om = omega_of(wsum_sh, n_ppc, w_min) * scale;
+        const double lo = 2.0 * om / 3.0, hi = 1.5 * om;
+        // candidates
+        for (uint32_t t = s0 + threadIdx.x; t < s1; t += blockDim.x) {
+            if ((double)p.r[PW][t] < lo) {
+                const int q = atomicAdd(&m_sh, 1);
+                sc.key[s0 + q] = speed2_key(p, t);
+                sc.id[s0 + q] = p.id[t];
+                sc.idx[s0 + q] = t;
+            }
+        }
+        __syncthreads();
+        int m = m_sh;
+        for (uint32_t round = 0; m >= 2; ++round) {
+            // rank by counting: position of each candidate in (key, id) order
+            for (int a = threadIdx.x; a < m; a += blockDim.x) {
+                const double ka = sc.key[s0 + a];
+                const uint64_t ia = sc.id[s0 + a];
+                int r = 0;
+                for (int b = 0; b < m; ++b) {
+                    const double kb = sc.key[s0 + b];
+                    r += (kb < ka) || (kb == ka && sc.id[s0 + b] < ia);
+                }
+                sc.skey[s0 + r] = ka;
+                sc.sid[s0 + r] = ia;
+                sc.sidx[s0 + r] = sc.idx[s0 + a];
+            }
+            if (threadIdx.x == 0) m2_sh = 0;
+            __syncthreads();
+            for (int q = threadIdx.x; q < m / 2; q += blockDim.x) {
+                const uint32_t ia = sc.sidx[s0 + 2 * q], ib = sc.sidx[s0 + 2 * q + 1];
+                const uint64_t da = sc.sid[s0 + 2 * q], db = sc.sid[s0 + 2 * q + 1];
+                const T wa = p.r[PW][ia], wb = p.r[PW][ib];
+                const uint64_t mid = da < db ? da : db;
+                const u32x4 o = draw_words(K, mid, step, 0xC0000000u | round);
+                const double u = unif<double>(o.x);
+                const bool keep_a = u * ((double)wa + (double)wb) < (double)wa;
+                const uint32_t keep = keep_a ? ia : ib, drop = keep_a ? ib : ia;
+                const T ws = wa + wb;
+                p.r[PW][keep] = ws;
+                p.r[PW][drop] = (T)0;
+                if ((double)ws < lo) {
+                    const int s = atomicAdd(&m2_sh, 1);
+                    sc.key[s0 + s] = keep_a ? sc.skey[s0 + 2 * q] : sc.skey[s0 + 2 * q + 1];
+                    sc.id[s0 + s] = keep_a ? da : db;
+                    sc.idx[s0 + s] = keep;
+                }
+            }
+            if ((m & 1) && threadIdx.x == 0) {
+                const int s = atomicAdd(&m2_sh, 1);
+                sc.key[s0 + s] = sc.skey[s0 + m - 1];
+                sc.id[s0 + s] = sc.sid[s0 + m - 1];
+                sc.idx[s0 + s] = sc.sidx[s0 + m - 1];
+            }
+            __syncthreads();
+            const int m2 = m2_sh;
+            __syncthreads();
+            if (m2 == m) break;
+            m = m2;
+        }
+        // split
+        for (uint32_t t = s0 + threadIdx.x; t < s1; t += blockDim.x) {
+            const T w = p.r[PW][t];
+            if (!((double)w > hi)) continue;
+            int mm = 0;
+            double wc = (double)w;
+            while (wc > hi) { wc *= 0.5; ++mm; }
+            const T wn = (T)ldexp((double)w, -mm);
+            p.r[PW][t] = wn;
+            const unsigned long long copies = (1ull << mm) - 1ull;
+            const unsigned long long base = atomicAdd(&st->n_extra, copies);
+            for (unsigned long long q = 0; q < copies; ++q) {
+                const long long d = n + (long long)(base + q);
+                if (d >= cap) { atomicOr(&st->err, kErrSplitCapacity); break; }
+                for (int f = 0; f < 10; ++f) p.r[f][d] = p.r[f][t];
+                p.r[PW][d] = wn;
+                p.id[d] = derived_id(K, p.id[t], step, 0x40000000u | (uint32_t)(q + 1));
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Copies live particles (w > 0) of a into b with a warp-aggregated cursor.
+template <class T>
+__global__ void k_compact(const Soa<T> a, long long n, Soa<T> b, DevState* st) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long base = warp * 32; base < n; base += nwarp * 32) {
+        const long long i = base + lane;
+        const bool live = i < n && a.r[PW][i] > (T)0;
+        const unsigned m = __ballot_sync(kFull, live);
+        if (!m) continue;
+        unsigned long long s0 = 0;
+        const int leader = __ffs(m) - 1;
+        if (lane == leader) s0 = atomicAdd(&st->n_out, (unsigned long long)__popc(m));
+        s0 = __shfl_sync(kFull, s0, leader);
+        if (live) {
+            const long long d = (long long)(s0 + __popc(m & ((1u << lane) - 1u)));
+#pragma unroll
+            for (int f = 0; f < 10; ++f) b.r[f][d] = a.r[f][i];
+            b.id[d] = a.id[i];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- swarm moments
+// Accumulators are zeroed by the host; nothing else here.
+
+}  // namespace pic
+
+// ====================================================================== context
+using namespace pic;
+
+static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+    size_t total = 0;
+    size_t buf[2], cq, table, table64, E4, qe, qp, qn, st, cnt, start, sums, key, rank, msc, gas, rho, phi, mg, hostio;
+};
+
+static size_t real_size(int prec) { return prec == 64 ? 8 : 4; }
+
+static Layout make_layout(const pic_config* c) {
+    Layout L;
+    const size_t R = real_size(c->precision);
+    const size_t cap = (size_t)c->capacity;
+    const size_t ncell = (size_t)c->nx * c->ny * c->nz;
+    size_t o = 0;
+    auto take = [&](size_t b) { size_t r = o; o += al256(b); return r; };
+    for (int b = 0; b < 2; ++b) {
+        L.buf[b] = o;
+        for (int f = 0; f < 10; ++f) take(cap * R);
+        take(cap * 8);
+    }
+    L.cq = o;
+    for (int f = 0; f < 11; ++f) take(cap * R);  // 10 fields + t_left
+    take(cap * 8);
+    const int nb = c->gas.n_bins > 0 ? c->gas.n_bins : 2;
+    L.table = take((size_t)nb * kTableStride * R);
+    L.table64 = take((size_t)nb * kTableStride * 8);
+    L.E4 = take(ncell * 4 * R);
+    L.qe = take(ncell * 8);
+    L.qp = take(ncell * 8);
+    L.qn = take(ncell * 8);
+    L.st = take(sizeof(DevState) + 64);
+    L.cnt = take((ncell + 1) * 4);
+    L.start = take((ncell + 1) * 4);
+    L.sums = take(((ncell + 1) / kScanTile + 2) * 4);
+    L.key = take(cap * 4);
+    L.rank = take(cap * 4);
+    L.msc = o;
+    take(cap * 8); take(cap * 8); take(cap * 4); take(cap * 8); take(cap * 8); take(cap * 4);
+    L.gas = take(((size_t)(c->gas.n_proc > 0 ? c->gas.n_proc : 1) + 1) * nb * 8 + 64 * 8);
+    L.rho = take(ncell * 8);
+    L.phi = take(ncell * 8);
+    L.mg = take(MG::bytes(c->nx, c->ny, c->nz));
+    L.hostio = 0;
+    L.total = o;
+    return L;
+}
+
+struct pic_ctx {
+    pic_config cfg;
+    int prec;
+    cudaStream_t s;
+    char* ws;
+    Layout L;
+    Grid g;
+    Keys K;
+    const uint8_t* mask;
+    int cur = 0;
+    long long n_host = 0;       // live particles (valid after any synchronising call)
+    long long n_last_wu = 0;    // count after the last weight update
+    uint32_t step = 0;
+    int a_valid = 0;
+    int field_valid = 0;
+    int field_uniform = 0;
+    double E0[3] = {0, 0, 0};
+    double nu_max = 0, l0 = 0, inv_dl = 0;
+    int n_proc = 0, n_bins = 0;
+    int kind[8];
+    double thr[8], mratio[8];
+    int grid_push = 0;
+    MG mg;
+    std::string err;
+    long long n_wu = 0, n_sorts = 0;
+    int last_cycles = 0;
+    double last_rel = 0;
+    long long steps_done = 0;
+    long long launches = 0;   // kernels launched by pic_step (for the profile)
+    // per-phase timing
+    int prof = 0;
+    cudaEvent_t ev[8] = {};
+    pic_profile_times pt = {};
+    void mark(int i) {
+        if (prof) cudaEventRecord(ev[i], s);
+    }
+    void accumulate(int a, int b, double* ms, long long* n) {
+        if (!prof) return;
+        float t = 0.f;
+        if (cudaEventSynchronize(ev[b]) == cudaSuccess && cudaEventElapsedTime(&t, ev[a], ev[b]) == cudaSuccess) {
+            *ms += t;
+            ++*n;
+        }
+    }
+    ~pic_ctx() {
+        for (int i = 0; i < 8; ++i)
+            if (ev[i]) cudaEventDestroy(ev[i]);
+    }
+
+    template <class T> Soa<T> soa(int b) {
+        Soa<T> s;
+        char* p = ws + L.buf[b];
+        const size_t cap = (size_t)cfg.capacity;
+        for (int f = 0; f < 10; ++f) { s.r[f] = (T*)p; p += al256(cap * sizeof(T)); }
+        s.id = (uint64_t*)p;
+        return s;
+    }
+    template <class T> ChildQ<T> childq() {
+        ChildQ<T> q;
+        char* p = ws + L.cq;
+        const size_t cap = (size_t)cfg.capacity;
+        for (int f = 0; f < 10; ++f) { q.p.r[f] = (T*)p; p += al256(cap * sizeof(T)); }
+        q.t_left = (T*)p;
+        p += al256(cap * sizeof(T));
+        q.p.id = (uint64_t*)p;
+        return q;
+    }
+    DevState* st() { return (DevState*)(ws + L.st); }
+    unsigned long long* qe() { return (unsigned long long*)(ws + L.qe); }
+    unsigned long long* qp() { return (unsigned long long*)(ws + L.qp); }
+    unsigned long long* qn() { return (unsigned long long*)(ws + L.qn); }
+    double* rho() { return (double*)(ws + L.rho); }
+    double* phi() { return (double*)(ws + L.phi); }
+    MergeScratch msc() {
+        MergeScratch m;
+        const size_t cap = (size_t)cfg.capacity;
+        char* p = ws + L.msc;
+        m.key = (double*)p; p += al256(cap * 8);
+        m.id = (uint64_t*)p; p += al256(cap * 8);
+        m.idx = (uint32_t*)p; p += al256(cap * 4);
+        m.skey = (double*)p; p += al256(cap * 8);
+        m.sid = (uint64_t*)p; p += al256(cap * 8);
+        m.sidx = (uint32_t*)p;
+        return m;
+    }
+    int fail(int code, const std::string& msg) {
+        err = msg;
+        return code;
+    }
+    int cuda_fail(cudaError_t e, const char* where) {
+        err = std::string(where) + ": " + cudaGetErrorString(e);
+        return PIC_ERR_CUDA;
+    }
+};
+
+static const char* kStatusText[] = {"ok", "invalid argument", "CUDA error", "capacity exceeded",
+                                    "fixed-point overflow", "iteration limit reached", "invalid state"};
+
+extern "C" const char* pic_status_string(int status) {
+    if (status > 0 || status < -6) return "unknown status";
+    return kStatusText[-status];
+}
+
+extern "C" const char* pic_last_error(const pic_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+static int validate(const pic_config* c) {
+    if (!c) return PIC_ERR_ARG;
+    if (c->precision != 32 && c->precision != 64) return PIC_ERR_ARG;
+    if (c->nx < 2 || c->ny < 2 || c->nz < 2 || !(c->dx > 0) || c->capacity < 1) return PIC_ERR_ARG;
+    if (c->nx > 2046 || c->ny > 2046 || c->nz > 2046) return PIC_ERR_ARG;
+    if ((long long)c->nx * c->ny * c->nz > 0x7fffffffLL) return PIC_ERR_ARG;
+    if (c->capacity > 0x7fffffffLL) return PIC_ERR_ARG;
+    if (!(c->dt > 0)) return PIC_ERR_ARG;
+    const pic_gas& g = c->gas;
+    if (g.n_proc < 1 || g.n_proc > 7 || g.n_bins < 2 || g.n_bins > 4096) return PIC_ERR_ARG;
+    if (!g.eps || !g.sigma || !g.kind || !g.threshold || !g.density || !g.mass) return PIC_ERR_ARG;
+    if (!(g.eps[0] > 0) || !(g.eps[g.n_bins - 1] > g.eps[0])) return PIC_ERR_ARG;
+    for (int k = 0; k < g.n_proc; ++k)
+        if (g.kind[k] < 0 || g.kind[k] > 3) return PIC_ERR_ARG;
+    if (c->coupled && (!(c->poisson_rtol > 0) || c->poisson_max_cycles < 1)) return PIC_ERR_ARG;
+    return PIC_OK;
+}
+
+extern "C" size_t pic_workspace_bytes(const pic_config* cfg) {
+    if (validate(cfg) != PIC_OK) return 0;
+    return make_layout(cfg).total;
+}
+
+// Builds the rate table on the device and reads nu_max back.
+static int build_table(pic_ctx* c) {
+    const pic_gas& g = c->cfg.gas;
+    const int nb = g.n_bins, np = g.n_proc;
+    double* d = (double*)(c->ws + c->L.gas);
+    std::vector<double> host((size_t)nb * (np + 1) + np + 8);
+    memcpy(host.data(), g.eps, nb * 8);
+    memcpy(host.data() + nb, g.sigma, (size_t)np * nb * 8);
+    memcpy(host.data() + (size_t)nb * (np + 1), g.density, np * 8);
+    cudaError_t e = cudaMemcpyAsync(d, host.data(), host.size() * 8, cudaMemcpyHostToDevice, c->s);
+    if (e != cudaSuccess) return c->cuda_fail(e, "table upload");
+    unsigned long long* nmx = (unsigned long long*)(d + (size_t)nb * (np + 1) + np);
+    cudaMemsetAsync(nmx, 0, 8, c->s);
+    if (c->prec == 32)
+        k_rate_table<float><<<(nb + 127) / 128, 128, 0, c->s>>>(d, d + nb, d + (size_t)nb * (np + 1), np, nb,
+                                                                (float*)(c->ws + c->L.table),
+                                                                (double*)(c->ws + c->L.table64), nmx);
+    else
+        k_rate_table<double><<<(nb + 127) / 128, 128, 0, c->s>>>(d, d + nb, d + (size_t)nb * (np + 1), np, nb,
+                                                                 (double*)(c->ws + c->L.table),
+                                                                 (double*)(c->ws + c->L.table64), nmx);
+    unsigned long long bits = 0;
+    e = cudaMemcpyAsync(&bits, nmx, 8, cudaMemcpyDeviceToHost, c->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+    if (e != cudaSuccess) return c->cuda_fail(e, "rate table");
+    memcpy(&c->nu_max, &bits, 8);
+    if (!(c->nu_max > 0)) return c->fail(PIC_ERR_ARG, "all collision rates are zero");
+    c->n_proc = np;
+    c->n_bins = nb;
+    c->l0 = log(g.eps[0]);
+    c->inv_dl = (double)(nb - 1) / (log(g.eps[nb - 1]) - c->l0);
+    for (int k = 0; k < 8; ++k) {
+        c->kind[k] = k < np ? g.kind[k] : 0;
+        c->thr[k] = k < np ? g.threshold[k] : 0.0;
+        c->mratio[k] = (k < np && g.mass[k] > 0) ? kMe / g.mass[k] : 0.0;
+    }
+    return PIC_OK;
+}
+
+extern "C" int pic_init(const pic_config* cfg, void* d_ws, size_t ws_bytes, const uint8_t* d_mask,
+                        pic_stream_t stream, pic_ctx** out) {
+    if (!out) return PIC_ERR_ARG;
+    *out = nullptr;
+    int rc = validate(cfg);
+    if (rc) return rc;
+    Layout L = make_layout(cfg);
+    if (!d_ws || ws_bytes < L.total || ((uintptr_t)d_ws & 255)) return PIC_ERR_ARG;
+    pic_ctx* c = new pic_ctx();
+    c->cfg = *cfg;
+    c->prec = cfg->precision;
+    c->s = (cudaStream_t)stream;
+    c->ws = (char*)d_ws;
+    c->L = L;
+    c->g = Grid{cfg->nx, cfg->ny, cfg->nz, cfg->dx, cfg->origin[0], cfg->origin[1], cfg->origin[2]};
+    c->K = make_keys(cfg->seed);
+    c->mask = d_mask;
+    cudaError_t e = cudaMemsetAsync(c->ws + L.st, 0, sizeof(DevState), c->s);
+    const size_t ncell = (size_t)c->g.ncell();
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.qe, 0, ncell * 8, c->s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.qp, 0, ncell * 8, c->s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.qn, 0, ncell * 8, c->s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.phi, 0, ncell * 8, c->s);
+    if (e != cudaSuccess) { rc = c->cuda_fail(e, "pic_init"); delete c; return rc; }
+    rc = build_table(c);
+    if (rc) { delete c; return rc; }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int bps = c->prec == 32 ? PushLaunch<float>::blocks_per_sm(MODE_PIC, c->n_bins)
+                                  : PushLaunch<double>::blocks_per_sm(MODE_PIC, c->n_bins);
+    c->grid_push = sms * bps;
+    if (cfg->coupled) c->mg.carve(c->ws + L.mg, cfg->nx, cfg->ny, cfg->nz);
+    *out = c;
+    return PIC_OK;
+}
+
+extern "C" void pic_destroy(pic_ctx* ctx) { delete ctx; }
+
+template <class T> static PushArgs<T> make_args(pic_ctx* c, int mode) {
+    PushArgs<T> A;
+    memset(&A, 0, sizeof(A));
+    A.in = c->soa<T>(c->cur);
+    A.out = c->soa<T>(1 - c->cur);
+    A.cq = c->childq<T>();
+    A.st = c->st();
+    A.table = (const T*)(c->ws + c->L.table);
+    A.n_bins = c->n_bins;
+    A.n_proc = c->n_proc;
+    for (int k = 0; k < 8; ++k) { A.kind[k] = c->kind[k]; A.thr[k] = (T)c->thr[k]; A.mratio[k] = (T)c->mratio[k]; }
+    A.l0 = c->l0;
+    A.inv_dl = c->inv_dl;
+    A.eps_lo = (T)c->cfg.gas.eps[0];
+    A.eps_hi = (T)c->cfg.gas.eps[c->n_bins - 1];
+    A.nu_max = (T)c->nu_max;
+    A.dt = (T)c->cfg.dt;
+    A.K = c->K;
+    A.step = c->step;
+    A.first = c->a_valid ? 0 : 1;
+    A.cap_out = c->cfg.capacity;
+    A.cap_child = c->cfg.capacity;
+    A.nx = c->g.nx; A.ny = c->g.ny; A.nz = c->g.nz;
+    A.ox = (T)c->g.ox; A.oy = (T)c->g.oy; A.oz = (T)c->g.oz; A.dxr = (T)c->g.dx;
+    A.hx = (T)(c->g.ox + (double)c->g.nx * c->g.dx);
+    A.hy = (T)(c->g.oy + (double)c->g.ny * c->g.dx);
+    A.hz = (T)(c->g.oz + (double)c->g.nz * c->g.dx);
+    A.E4 = c->field_uniform ? nullptr : (const T*)(c->ws + c->L.E4);
+    for (int d = 0; d < 3; ++d) A.E0[d] = (T)c->E0[d];
+    A.mask = c->mask;
+    A.q_e = c->qe();
+    A.q_pos = c->qp();
+    A.q_neg = c->qn();
+    A.boundary = c->cfg.boundary;
+    (void)mode;
+    return A;
+}
+
+static int read_state(pic_ctx* c, DevState* h) {
+    cudaError_t e = cudaMemcpyAsync(h, c->st(), sizeof(DevState), cudaMemcpyDeviceToHost, c->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+    if (e != cudaSuccess) return c->cuda_fail(e, "state read-back");
+    c->n_host = (long long)h->n_in;
+    return PIC_OK;
+}
+
+static int check_err(pic_ctx* c, const DevState& h) {
+    if (!h.err) return PIC_OK;
+    cudaMemsetAsync(&c->st()->err, 0, sizeof(unsigned), c->s);
+    char msg[160];
+    snprintf(msg, sizeof msg, "device error flags 0x%x (1 output full, 2 child queue full, 4 fixed-point overflow, "
+             "8 descendant stack, 16 split output full)", h.err);
+    if (h.err & kErrOverflow) return c->fail(PIC_ERR_OVERFLOW, msg);
+    return c->fail(PIC_ERR_CAPACITY, msg);
+}
+
+template <class T> static void deposit_current(pic_ctx* c, unsigned long long* q) {
+    PushLaunch<T>::deposit(c->soa<T>(c->cur), c->st(), c->g, q, grid_n(c->cfg.capacity), c->s);
+}
+
+extern "C" int pic_seed_gaussian(pic_ctx* c, double n0, double radius, const double center[3], double w0,
+                                 long long* n_out) {
+    if (!c || !center || !(n0 >= 0) || !(radius > 0) || !(w0 > 0)) return PIC_ERR_ARG;
+    const long long ncell = c->g.ncell();
+    uint32_t* cnt = (uint32_t*)(c->ws + c->L.cnt);
+    uint32_t* off = (uint32_t*)(c->ws + c->L.start);
+    k_seed_count<<<grid_n(ncell), 256, 0, c->s>>>(c->g, c->mask, n0, radius * radius, center[0], center[1],
+                                                   center[2], w0, c->K, cnt);
+    scan_exclusive(cnt, off, ncell, (uint32_t*)(c->ws + c->L.sums), c->s);
+    uint32_t total = 0;
+    cudaError_t e = cudaMemcpyAsync(&total, off + ncell, 4, cudaMemcpyDeviceToHost, c->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+    if (e != cudaSuccess) return c->cuda_fail(e, "seed count");
+    if ((long long)total > c->cfg.capacity) return c->fail(PIC_ERR_CAPACITY, "seed exceeds capacity");
+    c->cur = 0;
+    if (c->prec == 32)
+        k_seed_write<float><<<grid_n(ncell), 256, 0, c->s>>>(c->g, cnt, off, w0, 0, c->K, c->soa<float>(0),
+                                                             c->cfg.capacity, c->st());
+    else
+        k_seed_write<double><<<grid_n(ncell), 256, 0, c->s>>>(c->g, cnt, off, w0, 0, c->K, c->soa<double>(0),
+                                                              c->cfg.capacity, c->st());
+    k_set_count<<<1, 1, 0, c->s>>>(c->st(), total);
+    cudaMemsetAsync(c->qp(), 0, ncell * 8, c->s);
+    cudaMemsetAsync(c->qn(), 0, ncell * 8, c->s);
+    if (c->prec == 32) deposit_current<float>(c, c->qp());
+    else deposit_current<double>(c, c->qp());
+    c->n_host = total;
+    c->n_last_wu = total;
+    c->a_valid = 0;
+    if (n_out) *n_out = total;
+    e = cudaGetLastError();
+    return e == cudaSuccess ? PIC_OK : c->cuda_fail(e, "seed");
+}
+
+template <class T> static int set_particles(pic_ctx* c, long long n, const pic_particles_host* p) {
+    std::vector<T> tmp((size_t)n);
+    Soa<T> d = c->soa<T>(0);
+    const double* src[10] = {p->x, p->y, p->z, p->vx, p->vy, p->vz, p->ax, p->ay, p->az, p->w};
+    for (int f = 0; f < 10; ++f) {
+        for (long long i = 0; i < n; ++i) tmp[i] = src[f] ? (T)src[f][i] : (T)0;
+        cudaError_t e = cudaMemcpyAsync(d.r[f], tmp.data(), n * sizeof(T), cudaMemcpyHostToDevice, c->s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+        if (e != cudaSuccess) return c->cuda_fail(e, "set particles");
+    }
+    cudaError_t e = cudaMemcpyAsync(d.id, p->id, n * 8, cudaMemcpyHostToDevice, c->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+    if (e != cudaSuccess) return c->cuda_fail(e, "set particles");
+    return PIC_OK;
+}
+
+extern "C" int pic_set_particles(pic_ctx* c, long long n, const pic_particles_host* p, int accel_valid) {
+    if (!c || n < 0 || (n > 0 && (!p || !p->x || !p->y || !p->z || !p->w || !p->id))) return PIC_ERR_ARG;
+    if (n > c->cfg.capacity) return c->fail(PIC_ERR_CAPACITY, "more particles than capacity");
+    c->cur = 0;
+    int rc = PIC_OK;
+    if (n > 0) rc = c->prec == 32 ? set_particles<float>(c, n, p) : set_particles<double>(c, n, p);
+    if (rc) return rc;
+    k_set_count<<<1, 1, 0, c->s>>>(c->st(), (unsigned long long)n);
+    c->n_host = n;
+    c->n_last_wu = n;
+    c->a_valid = accel_valid ? 1 : 0;
+    return PIC_OK;
+}
+
+template <class T> static int get_particles(pic_ctx* c, pic_particles_host* p, long long cap, long long* n_out) {
+    DevState h;
+    int rc = read_state(c, &h);
+    if (rc) return rc;
+    const long long n = (long long)h.n_in;
+    Soa<T> d = c->soa<T>(c->cur);
+    std::vector<T> w((size_t)n);
+    cudaError_t e = cudaMemcpy(w.data(), d.r[PW], n * sizeof(T), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return c->cuda_fail(e, "get particles");
+    long long live = 0;
+    for (long long i = 0; i < n; ++i) live += w[i] > (T)0;
+    if (n_out) *n_out = live;
+    if (!p) return PIC_OK;
+    if (live > cap) return c->fail(PIC_ERR_CAPACITY, "host arrays too small");
+    double* dst[10] = {p->x, p->y, p->z, p->vx, p->vy, p->vz, p->ax, p->ay, p->az, p->w};
+    std::vector<T> tmp((size_t)n);
+    for (int f = 0; f < 10; ++f) {
+        if (!dst[f]) continue;
+        e = cudaMemcpy(tmp.data(), d.r[f], n * sizeof(T), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return c->cuda_fail(e, "get particles");
+        long long j = 0;
+        for (long long i = 0; i < n; ++i)
+            if (w[i] > (T)0) dst[f][j++] = (double)tmp[i];
+    }
+    if (p->id) {
+        std::vector<uint64_t> ids((size_t)n);
+        e = cudaMemcpy(ids.data(), d.id, n * 8, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return c->cuda_fail(e, "get particles");
+        long long j = 0;
+        for (long long i = 0; i < n; ++i)
+            if (w[i] > (T)0) p->id[j++] = ids[i];
+    }
+    return PIC_OK;
+}
+
+extern "C" int pic_get_particles(pic_ctx* c, pic_particles_host* p, long long cap, long long* n_out) {
+    if (!c) return PIC_ERR_ARG;
+    return c->prec == 32 ? get_particles<float>(c, p, cap, n_out) : get_particles<double>(c, p, cap, n_out);
+}
+
+extern "C" int pic_count(pic_ctx* c, long long* n) {
+    if (!c || !n) return PIC_ERR_ARG;
+    DevState h;
+    int rc = read_state(c, &h);
+    *n = c->n_host;
+    return rc;
+}
+
+extern "C" int pic_set_field(pic_ctx* c, const float* Ex, const float* Ey, const float* Ez, const double E_uniform[3]) {
+    if (!c) return PIC_ERR_ARG;
+    if (Ex == nullptr) {
+        if (!E_uniform) return PIC_ERR_ARG;
+        c->field_uniform = 1;
+        for (int d = 0; d < 3; ++d) c->E0[d] = E_uniform[d];
+    } else {
+        if (!Ey || !Ez) return PIC_ERR_ARG;
+        c->field_uniform = 0;
+        const long long n = c->g.ncell();
+        if (c->prec == 32)
+            k_pack_field<float><<<grid_n(n), 256, 0, c->s>>>(Ex, Ey, Ez, n, (float*)(c->ws + c->L.E4));
+        else
+            k_pack_field<double><<<grid_n(n), 256, 0, c->s>>>(Ex, Ey, Ez, n, (double*)(c->ws + c->L.E4));
+    }
+    c->field_valid = 1;
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PIC_OK : c->cuda_fail(e, "set field");
+}
+
+static void fixed_to_rho(pic_ctx* c, double* rho) {
+    const long long n = c->g.ncell();
+    const double dV = c->g.dx * c->g.dx * c->g.dx;
+    k_fixed_to_rho<<<grid_n(n), 256, 0, c->s>>>((const long long*)c->qe(), (const long long*)c->qp(),
+                                                 (const long long*)c->qn(), n, 1.0 / (4294967296.0 * dV), rho);
+}
+
+// Coupled field: rho from the fixed-point grids, multigrid Poisson (warm
+// started from the previous potential), packed E for the next gather.
+static int solve_field(pic_ctx* c) {
+    fixed_to_rho(c, c->rho());
+    c->launches += 1;
+    const long long l0 = c->mg.launches;
+    double hn[2];
+    int rc = c->mg.solve(c->rho(), c->mask, c->phi(), c->g.dx, c->cfg.v_lo, c->cfg.v_hi, c->cfg.v_mask,
+                         c->cfg.poisson_rtol, c->cfg.poisson_max_cycles, c->prec, c->ws + c->L.E4, nullptr, nullptr,
+                         nullptr, c->s, &c->last_cycles, &c->last_rel, hn);
+    if (rc == PIC_ERR_CUDA) return c->fail(rc, "poisson solve: CUDA error");
+    if (rc == PIC_ERR_TIMEOUT) return c->fail(rc, "poisson solve: cycle limit reached");
+    c->launches += c->mg.launches - l0;
+    c->field_valid = 1;
+    c->field_uniform = 0;
+    return PIC_OK;
+}
+
+template <class T> static int sort_by_cell(pic_ctx* c) {
+    const long long ncell = c->g.ncell();
+    uint32_t* cnt = (uint32_t*)(c->ws + c->L.cnt);
+    uint32_t* start = (uint32_t*)(c->ws + c->L.start);
+    cudaMemsetAsync(cnt, 0, (ncell + 1) * 4, c->s);
+    GridT g{c->g.ox, c->g.oy, c->g.oz, c->g.dx, c->g.nx, c->g.ny, c->g.nz};
+    const int grid = grid_n(c->cfg.capacity);
+    k_cell_count<T><<<grid, 256, 0, c->s>>>(c->soa<T>(c->cur), c->st(), g, cnt, (uint32_t*)(c->ws + c->L.key),
+                                             (uint32_t*)(c->ws + c->L.rank));
+    scan_exclusive(cnt, start, ncell, (uint32_t*)(c->ws + c->L.sums), c->s);
+    k_scatter<T><<<grid, 256, 0, c->s>>>(c->soa<T>(c->cur), c->soa<T>(1 - c->cur), c->st(), start,
+                                          (const uint32_t*)(c->ws + c->L.key), (const uint32_t*)(c->ws + c->L.rank));
+    c->cur = 1 - c->cur;
+    c->n_sorts++;
+    c->launches += 5;
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PIC_OK : c->cuda_fail(e, "sort");
+}
+
+// Weight update (Sec. 2.1.2): sort by cell, per-cell merge and split, compaction.
+template <class T> static int weight_update(pic_ctx* c) {
+    int rc = sort_by_cell<T>(c);
+    if (rc) return rc;
+    const long long ncell = c->g.ncell();
+    const uint32_t* start = (const uint32_t*)(c->ws + c->L.start);
+    DevState h;
+    cudaMemsetAsync(&c->st()->pred_total, 0, 8, c->s);
+    cudaMemsetAsync(&c->st()->n_extra, 0, 8, c->s);
+    k_cell_weight<T><<<grid_n(ncell), 256, 0, c->s>>>(c->soa<T>(c->cur), start, ncell, c->cfg.n_ppc, c->cfg.w_min,
+                                                       c->st());
+    rc = read_state(c, &h);
+    if (rc) return rc;
+    const long long n = c->n_host;
+    double scale = 1.0;
+    const long long capp = c->cfg.particle_cap;
+    if (capp > 0 && h.pred_total > capp * 16777216LL) scale = (double)h.pred_total / ((double)capp * 16777216.0);
+    k_merge_split<T><<<152 * 8, 256, 0, c->s>>>(c->soa<T>(c->cur), n, start, ncell, c->cfg.n_ppc, c->cfg.w_min, scale,
+                                                 c->msc(), c->K, c->step, c->cfg.capacity, c->st());
+    rc = read_state(c, &h);
+    if (rc) return rc;
+    const long long ntot = n + (long long)h.n_extra;
+    cudaMemsetAsync(&c->st()->n_out, 0, 8, c->s);
+    k_compact<T><<<grid_n(ntot), 256, 0, c->s>>>(c->soa<T>(c->cur), ntot < c->cfg.capacity ? ntot : c->cfg.capacity,
+                                                  c->soa<T>(1 - c->cur), c->st());
+    k_end_step<<<1, 1, 0, c->s>>>(c->st(), nullptr, c->cfg.capacity);
+    c->cur = 1 - c->cur;
+    rc = read_state(c, &h);
+    if (rc) return rc;
+    c->n_last_wu = c->n_host;
+    c->n_wu++;
+    c->launches += 4;
+    return check_err(c, h);
+}
+
+extern "C" int pic_weight_update(pic_ctx* c) {
+    if (!c) return PIC_ERR_ARG;
+    return c->prec == 32 ? weight_update<float>(c) : weight_update<double>(c);
+}
+
+template <class T> static int one_step(pic_ctx* c, bool stats) {
+    c->step++;
+    PushArgs<T> A = make_args<T>(c, MODE_PIC);
+    cudaMemsetAsync(c->qe(), 0, (size_t)c->g.ncell() * 8, c->s);
+    c->mark(0);
+    c->launches += 3;
+    cudaError_t e = PushLaunch<T>::parents(A, MODE_PIC, stats, c->grid_push, c->s);
+    c->mark(1);
+    if (e == cudaSuccess) e = PushLaunch<T>::children(A, MODE_PIC, stats, c->grid_push, c->s);
+    c->mark(2);
+    if (e != cudaSuccess) return c->cuda_fail(e, "push");
+    k_end_step<<<1, 1, 0, c->s>>>(c->st(), nullptr, c->cfg.capacity);
+    c->cur = 1 - c->cur;
+    c->a_valid = 1;
+    c->steps_done++;
+    return PIC_OK;
+}
+
+extern "C" int pic_step(pic_ctx* c, int n_steps, pic_step_stats* stats) {
+    if (!c || n_steps < 0) return PIC_ERR_ARG;
+    if (!c->field_valid && !c->cfg.coupled) return c->fail(PIC_ERR_STATE, "no field: call pic_set_field first");
+    const bool want = stats != nullptr;
+    DevState h;
+    int rc;
+    if (want) {
+        cudaMemsetAsync(&c->st()->n_events, 0, offsetof(DevState, pred_total) - offsetof(DevState, n_events),
+                        c->s);
+        rc = read_state(c, &h);
+        if (rc) return rc;
+        memset(stats, 0, sizeof(*stats));
+        stats->n_start = c->n_host;
+    }
+    const long long wu0 = c->n_wu, so0 = c->n_sorts;
+    if (c->cfg.coupled && !c->field_valid) {
+        rc = solve_field(c);
+        if (rc) return rc;
+    }
+    for (int it = 0; it < n_steps; ++it) {
+        rc = c->prec == 32 ? one_step<float>(c, want) : one_step<double>(c, want);
+        if (rc) return rc;
+        c->accumulate(0, 1, &c->pt.ms_push, &c->pt.n_push);
+        c->accumulate(1, 2, &c->pt.ms_children, &c->pt.n_children);
+        bool sorted = false;
+        c->mark(3);
+        if (c->cfg.growth_trigger > 0) {
+            rc = read_state(c, &h);
+            if (rc) return rc;
+            if ((double)c->n_host > c->cfg.growth_trigger * (double)c->n_last_wu && c->n_host > 0) {
+                rc = pic_weight_update(c);
+                if (rc) return rc;
+                sorted = true;
+            }
+        }
+        if (!sorted && c->cfg.sort_interval > 0 && (c->step % (uint32_t)c->cfg.sort_interval) == 0) {
+            rc = c->prec == 32 ? sort_by_cell<float>(c) : sort_by_cell<double>(c);
+            if (rc) return rc;
+        }
+        if (sorted) {  // merged particles moved: redeposit the electrons
+            cudaMemsetAsync(c->qe(), 0, (size_t)c->g.ncell() * 8, c->s);
+            if (c->prec == 32) deposit_current<float>(c, c->qe());
+            else deposit_current<double>(c, c->qe());
+            c->launches += 1;
+        }
+        c->mark(4);
+        c->accumulate(3, 4, &c->pt.ms_reorder, &c->pt.n_reorder);
+        if (c->cfg.coupled) {
+            c->mark(5);
+            rc = solve_field(c);
+            if (rc) return rc;
+            c->mark(6);
+            c->accumulate(5, 6, &c->pt.ms_field, &c->pt.n_field);
+        }
+    }
+    rc = read_state(c, &h);
+    if (rc) return rc;
+    const int erc = check_err(c, h);
+    if (want) {
+        stats->n_end = c->n_host;
+        stats->n_events = (long long)h.n_events;
+        stats->n_null = (long long)h.n_null;
+        for (int k = 0; k < PIC_MAX_PROC; ++k) stats->n_coll[k] = (long long)h.n_coll[k];
+        stats->n_children = (long long)h.n_children;
+        stats->n_attached = (long long)h.n_attached;
+        stats->n_absorbed = (long long)h.n_absorbed;
+        stats->n_clamped = (long long)h.n_clamped;
+        stats->n_processed = (long long)h.n_processed;
+        stats->w_ion = h.w_ion;
+        stats->w_att = h.w_att;
+        stats->w_absorbed = h.w_absorbed;
+        stats->n_weight_updates = c->n_wu - wu0;
+        stats->n_sorts = c->n_sorts - so0;
+        stats->poisson_cycles = c->last_cycles;
+        stats->poisson_rel_res = c->last_rel;
+    }
+    return erc;
+}
+
+extern "C" int pic_deposit(pic_ctx* c, int64_t* q_e, int64_t* q_pos, int64_t* q_neg, double* rho) {
+    if (!c) return PIC_ERR_ARG;
+    const size_t n = (size_t)c->g.ncell();
+    cudaMemsetAsync(c->qe(), 0, n * 8, c->s);
+    if (c->prec == 32) deposit_current<float>(c, c->qe());
+    else deposit_current<double>(c, c->qe());
+    cudaError_t e = cudaSuccess;
+    if (q_e) e = cudaMemcpyAsync(q_e, c->qe(), n * 8, cudaMemcpyDeviceToDevice, c->s);
+    if (e == cudaSuccess && q_pos) e = cudaMemcpyAsync(q_pos, c->qp(), n * 8, cudaMemcpyDeviceToDevice, c->s);
+    if (e == cudaSuccess && q_neg) e = cudaMemcpyAsync(q_neg, c->qn(), n * 8, cudaMemcpyDeviceToDevice, c->s);
+    if (e != cudaSuccess) return c->cuda_fail(e, "deposit copy");
+    if (rho) fixed_to_rho(c, rho);
+    DevState h;
+    int rc = read_state(c, &h);
+    if (rc) return rc;
+    return check_err(c, h);
+}
+
+// ---------------------------------------------------------------- checkpoint
+struct BlobHead {
+    uint64_t magic;
+    int32_t prec, a_valid;
+    int64_t n, n_last_wu, ncell;
+    uint32_t step, pad;
+    int64_t n_wu, n_sorts;
+};
+static const uint64_t kMagic = 0x3130314D43435049ull;  // "IPCCM101"
+
+extern "C" int pic_save(pic_ctx* c, void* blob, size_t* bytes) {
+    if (!c || !bytes) return PIC_ERR_ARG;
+    DevState h;
+    int rc = read_state(c, &h);
+    if (rc) return rc;
+    const size_t R = real_size(c->prec), n = (size_t)c->n_host, ncell = (size_t)c->g.ncell();
+    const size_t need = sizeof(BlobHead) + n * (10 * R + 8) + 3 * ncell * 8;
+    if (!blob || *bytes < need) { *bytes = need; return blob ? PIC_ERR_CAPACITY : PIC_OK; }
+    BlobHead hd{kMagic, c->prec, c->a_valid, (int64_t)n, c->n_last_wu, (int64_t)ncell, c->step, 0, c->n_wu, c->n_sorts};
+    char* p = (char*)blob;
+    memcpy(p, &hd, sizeof hd);
+    p += sizeof hd;
+    char* base = c->ws + c->L.buf[c->cur];
+    const size_t cap = (size_t)c->cfg.capacity;
+    cudaError_t e = cudaSuccess;
+    for (int f = 0; f < 10 && e == cudaSuccess; ++f) {
+        e = cudaMemcpy(p, base + f * al256(cap * R), n * R, cudaMemcpyDeviceToHost);
+        p += n * R;
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(p, base + 10 * al256(cap * R), n * 8, cudaMemcpyDeviceToHost);
+    p += n * 8;
+    if (e == cudaSuccess) e = cudaMemcpy(p, c->qp(), ncell * 8, cudaMemcpyDeviceToHost);
+    p += ncell * 8;
+    if (e == cudaSuccess) e = cudaMemcpy(p, c->qn(), ncell * 8, cudaMemcpyDeviceToHost);
+    p += ncell * 8;
+    if (e == cudaSuccess) e = cudaMemcpy(p, c->phi(), ncell * 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return c->cuda_fail(e, "save");
+    *bytes = need;
+    return PIC_OK;
+}
+
+extern "C" int pic_load(pic_ctx* c, const void* blob, size_t bytes) {
+    if (!c || !blob || bytes < sizeof(BlobHead)) return PIC_ERR_ARG;
+    BlobHead hd;
+    memcpy(&hd, blob, sizeof hd);
+    const size_t R = real_size(c->prec), ncell = (size_t)c->g.ncell();
+    if (hd.magic != kMagic || hd.prec != c->prec || (size_t)hd.ncell != ncell || hd.n < 0 ||
+        hd.n > c->cfg.capacity)
+        return c->fail(PIC_ERR_ARG, "blob does not match this context");
+    const size_t n = (size_t)hd.n;
+    if (bytes < sizeof(BlobHead) + n * (10 * R + 8) + 3 * ncell * 8) return PIC_ERR_ARG;
+    const char* p = (const char*)blob + sizeof hd;
+    c->cur = 0;
+    char* base = c->ws + c->L.buf[0];
+    const size_t cap = (size_t)c->cfg.capacity;
+    cudaError_t e = cudaSuccess;
+    for (int f = 0; f < 10 && e == cudaSuccess; ++f) {
+        e = cudaMemcpy(base + f * al256(cap * R), p, n * R, cudaMemcpyHostToDevice);
+        p += n * R;
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(base + 10 * al256(cap * R), p, n * 8, cudaMemcpyHostToDevice);
+    p += n * 8;
+    if (e == cudaSuccess) e = cudaMemcpy(c->qp(), p, ncell * 8, cudaMemcpyHostToDevice);
+    p += ncell * 8;
+    if (e == cudaSuccess) e = cudaMemcpy(c->qn(), p, ncell * 8, cudaMemcpyHostToDevice);
+    p += ncell * 8;
+    if (e == cudaSuccess) e = cudaMemcpy(c->phi(), p, ncell * 8, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return c->cuda_fail(e, "load");
+    k_set_count<<<1, 1, 0, c->s>>>(c->st(), (unsigned long long)n);
+    c->n_host = (long long)n;
+    c->n_last_wu = hd.n_last_wu;
+    c->step = hd.step;
+    c->a_valid = hd.a_valid;
+    c->n_wu = hd.n_wu;
+    c->n_sorts = hd.n_sorts;
+    if (c->cfg.coupled) c->field_valid = 0;  // recomputed from the restored charge before the next step
+    return PIC_OK;
+}
+
+// ====================================================================== swarms
+// Sec. 2.2.2: electrons traced in a uniform field give flux coefficients
+// (averages over electrons) and bulk coefficients (motion and spread of the
+// centre of mass).  Each swarm runs in turn over one shared set of buffers.
+static pic_config swarm_pic_config(const swarm_config* sc) {
+    pic_config c;
+    memset(&c, 0, sizeof c);
+    c.precision = sc->precision;
+    c.nx = c.ny = c.nz = 2;
+    c.dx = 1.0;
+    c.capacity = sc->capacity;
+    c.seed = sc->seed;
+    c.dt = sc->dt;
+    c.gas = sc->gas;
+    return c;
+}
+
+static size_t swarm_extra(const swarm_config* sc) {
+    return al256((size_t)sc->n_steps * kNMom * 8) + al256((size_t)sc->n_steps * 8);
+}
+
+extern "C" size_t swarm_workspace_bytes(const swarm_config* sc, int n_swarms) {
+    if (!sc || n_swarms < 1 || sc->n_steps < 1) return 0;
+    pic_config c = swarm_pic_config(sc);
+    if (validate(&c) != PIC_OK) return 0;
+    return make_layout(&c).total + swarm_extra(sc);
+}
+
+// Flux = time average of per-step electron averages; bulk = least-squares
+// slopes of the centre of mass and of the spread; rate coefficients =
+// event weight / (N * integral of the swarm weight); errors from 10 blocks.
+static void swarm_coeffs(const double* mom, int r0, int r1, double dt, double n_gas, double* o) {
+    const int n = r1 - r0;
+    double wf = 0, dlf = 0, dtf = 0, me = 0, sion = 0, satt = 0, sw = 0;
+    double st = 0, stt = 0, sz = 0, stz = 0, sl = 0, stl = 0, sr = 0, str = 0;
+    for (int r = r0; r < r1; ++r) {
+        const double* m = mom + (size_t)r * kNMom;
+        const double W = m[0];
+        const double mx = m[1] / W, my = m[2] / W, mz = m[3] / W;
+        const double vx = m[7] / W, vy = m[8] / W, vz = m[9] / W;
+        wf += vz;
+        dlf += m[12] / W - mz * vz;
+        dtf += 0.5 * ((m[10] / W - mx * vx) + (m[11] / W - my * vy));
+        me += m[13] / W;
+        sion += m[14];
+        satt += m[15];
+        sw += W;
+        const double t = (double)(r + 1) * dt;
+        const double varz = m[6] / W - mz * mz;
+        const double vart = (m[4] / W - mx * mx) + (m[5] / W - my * my);
+        st += t; stt += t * t; sz += mz; stz += t * mz; sl += varz; stl += t * varz; sr += vart; str += t * vart;
+    }
+    const double den = n * stt - st * st;
+    o[0] = wf / n;
+    o[1] = (n * stz - st * sz) / den;
+    o[2] = dlf / n;
+    o[3] = dtf / n;
+    o[4] = 0.5 * (n * stl - st * sl) / den;
+    o[5] = 0.25 * (n * str - st * sr) / den;
+    o[6] = me / n;
+    o[7] = sion / (n_gas * dt * sw);
+    o[8] = satt / (n_gas * dt * sw);
+    o[9] = o[7] * n_gas / o[0];
+    o[10] = o[8] * n_gas / o[0];
+}
+
+static void swarm_result_from(const double* mom, int n_steps, double sample_from, double dt, double n_gas,
+                              swarm_result* res) {
+    for (int q = 0; q < PIC_SWARM_NRES; ++q) res->v[q] = NAN;
+    int i0 = (int)(sample_from * n_steps);
+    if (i0 < 0) i0 = 0;
+    const int nb = 10;
+    if (n_steps - i0 < 2 * nb) return;
+    swarm_coeffs(mom, i0, n_steps, dt, n_gas, res->v);
+    const int len = (n_steps - i0) / nb;
+    double blk[10][11];
+    for (int b = 0; b < nb; ++b) swarm_coeffs(mom, i0 + b * len, i0 + (b + 1) * len, dt, n_gas, blk[b]);
+    for (int q = 0; q < 11; ++q) {
+        double mean = 0, var = 0;
+        for (int b = 0; b < nb; ++b) mean += blk[b][q];
+        mean /= nb;
+        for (int b = 0; b < nb; ++b) var += (blk[b][q] - mean) * (blk[b][q] - mean);
+        res->v[11 + q] = sqrt(var / (nb - 1)) / sqrt((double)nb);
+    }
+}
+
+template <class T> static int swarm_one(pic_ctx* c, const swarm_config* sc, double EN, double* d_mom, long long* d_cnt,
+                                        double* h_mom, long long* h_cnt, swarm_result* res) {
+    const int ns = sc->n_steps;
+    cudaMemsetAsync(d_mom, 0, (size_t)ns * kNMom * 8, c->s);
+    cudaMemsetAsync(c->st(), 0, sizeof(DevState), c->s);
+    c->cur = 0;
+    const double sig = sqrt(sc->kT_eV * kQ / kMe);
+    k_seed_maxwell<T><<<grid_n(sc->n0), 256, 0, c->s>>>(sc->n0, sig, c->K, c->soa<T>(0));
+    k_set_count<<<1, 1, 0, c->s>>>(c->st(), (unsigned long long)sc->n0);
+    const double E = EN * 1e-21 * sc->n_gas;
+    c->field_uniform = 1;
+    c->E0[0] = 0.0; c->E0[1] = 0.0; c->E0[2] = -E;
+    c->step = 0;
+    for (int s = 1; s <= ns; ++s) {
+        c->step = (uint32_t)s;
+        c->a_valid = 0;  // uniform field: no half-kick
+        PushArgs<T> A = make_args<T>(c, MODE_SWARM);
+        A.mom = d_mom + (size_t)(s - 1) * kNMom;
+        A.n_lo = sc->n_lo;
+        A.n_hi = sc->n_hi;
+        A.mask = nullptr;
+        A.q_e = A.q_pos = A.q_neg = nullptr;
+        cudaError_t e = PushLaunch<T>::parents(A, MODE_SWARM, false, c->grid_push, c->s);
+        if (e == cudaSuccess) e = PushLaunch<T>::children(A, MODE_SWARM, false, c->grid_push, c->s);
+        if (e != cudaSuccess) return c->cuda_fail(e, "swarm push");
+        k_end_step<<<1, 1, 0, c->s>>>(c->st(), d_cnt + (s - 1), c->cfg.capacity);
+        c->cur = 1 - c->cur;
+    }
+    cudaError_t e = cudaMemcpyAsync(h_mom, d_mom, (size_t)ns * kNMom * 8, cudaMemcpyDeviceToHost, c->s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_cnt, d_cnt, (size_t)ns * 8, cudaMemcpyDeviceToHost, c->s);
+    DevState h;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, c->st(), sizeof h, cudaMemcpyDeviceToHost, c->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+    if (e != cudaSuccess) return c->cuda_fail(e, "swarm read-back");
+    if (h.err) return check_err(c, h);
+    swarm_result_from(h_mom, ns, sc->sample_from, sc->dt, sc->n_gas, res);
+    res->v[22] = (double)h_cnt[ns - 1];
+    res->v[23] = h_mom[(size_t)(ns - 1) * kNMom];
+    return PIC_OK;
+}
+
+extern "C" int swarm_run(const swarm_config* sc, int n_swarms, const double* EN_Td, void* d_ws, size_t ws_bytes,
+                         swarm_result* results, double* moments, long long* counts, pic_stream_t stream) {
+    if (!sc || n_swarms < 1 || !EN_Td || !results || !d_ws) return PIC_ERR_ARG;
+    if (sc->n0 < 1 || sc->n0 > sc->capacity || sc->n_steps < 1 || !(sc->n_gas > 0) || !(sc->kT_eV >= 0) ||
+        sc->n_lo < 0 || sc->n_hi < sc->n_lo || sc->capacity < 2 * sc->n_hi)
+        return PIC_ERR_ARG;
+    const size_t need = swarm_workspace_bytes(sc, n_swarms);
+    if (need == 0 || ws_bytes < need) return PIC_ERR_ARG;
+    pic_config pc = swarm_pic_config(sc);
+    Layout L = make_layout(&pc);
+    double* d_mom = (double*)((char*)d_ws + L.total);
+    long long* d_cnt = (long long*)((char*)d_ws + L.total + al256((size_t)sc->n_steps * kNMom * 8));
+    std::vector<double> hm((size_t)sc->n_steps * kNMom);
+    std::vector<long long> hc((size_t)sc->n_steps);
+    for (int s = 0; s < n_swarms; ++s) {
+        pc.seed = sc->seed + (unsigned long long)s;
+        pic_ctx* c = nullptr;
+        int rc = pic_init(&pc, d_ws, L.total, nullptr, stream, &c);
+        if (rc) return rc;
+        rc = sc->precision == 32 ? swarm_one<float>(c, sc, EN_Td[s], d_mom, d_cnt, hm.data(), hc.data(), &results[s])
+                                 : swarm_one<double>(c, sc, EN_Td[s], d_mom, d_cnt, hm.data(), hc.data(), &results[s]);
+        pic_destroy(c);
+        if (rc) return rc;
+        if (moments) memcpy(moments + (size_t)s * sc->n_steps * kNMom, hm.data(), hm.size() * 8);
+        if (counts) memcpy(counts + (size_t)s * sc->n_steps, hc.data(), hc.size() * 8);
+    }
+    return PIC_OK;
+}
+
+extern "C" int pic_progress(pic_ctx* c, long long* updates, long long* parents, long long* steps) {
+    if (!c) return PIC_ERR_ARG;
+    DevState h;
+    int rc = read_state(c, &h);
+    if (rc) return rc;
+    if (updates) *updates = (long long)h.n_updates;
+    if (parents) *parents = (long long)h.n_parents;
+    if (steps) *steps = c->steps_done;
+    return PIC_OK;
+}
+
+extern "C" int pic_profile(pic_ctx* c, int enable, pic_profile_times* out) {
+    if (!c) return PIC_ERR_ARG;
+    c->pt.n_launches = c->launches;
+    if (out) *out = c->pt;
+    memset(&c->pt, 0, sizeof c->pt);
+    c->launches = 0;
+    if (enable && !c->ev[0])
+        for (int i = 0; i < 8; ++i)
+            if (cudaEventCreate(&c->ev[i]) != cudaSuccess) return c->fail(PIC_ERR_CUDA, "event create");
+    c->prof = enable ? 1 : 0;
+    return PIC_OK;
+}
+
+extern "C" int pic_upload(pic_ctx* c, long long n, const void* const* arrays, int accel_valid) {
+    if (!c || n < 0 || (n > 0 && !arrays)) return PIC_ERR_ARG;
+    if (n > c->cfg.capacity) return c->fail(PIC_ERR_CAPACITY, "more particles than capacity");
+    c->cur = 0;
+    const size_t R = real_size(c->prec), cap = (size_t)c->cfg.capacity;
+    char* base = c->ws + c->L.buf[0];
+    for (int f = 0; f < 11 && n > 0; ++f) {
+        if (!arrays[f]) return PIC_ERR_ARG;
+        cudaError_t e = cudaMemcpyAsync(base + f * al256(cap * R), arrays[f], n * (f < 10 ? R : 8),
+                                        cudaMemcpyHostToDevice, c->s);
+        if (e != cudaSuccess) return c->cuda_fail(e, "upload");
+    }
+    k_set_count<<<1, 1, 0, c->s>>>(c->st(), (unsigned long long)n);
+    c->n_host = n;
+    c->n_last_wu = n;
+    c->a_valid = accel_valid ? 1 : 0;
+    return PIC_OK;
+}
+
+extern "C" int pic_download(pic_ctx* c, void* const* arrays, long long cap, long long* n_out) {
+    if (!c || !arrays) return PIC_ERR_ARG;
+    DevState h;
+    int rc = read_state(c, &h);
+    if (rc) return rc;
+    const long long n = c->n_host;
+    if (n_out) *n_out = n;
+    if (n > cap) return c->fail(PIC_ERR_CAPACITY, "host arrays too small");
+    const size_t R = real_size(c->prec), capd = (size_t)c->cfg.capacity;
+    char* base = c->ws + c->L.buf[c->cur];
+    for (int f = 0; f < 11 && n > 0; ++f) {
+        if (!arrays[f]) continue;
+        cudaError_t e = cudaMemcpyAsync(arrays[f], base + f * al256(capd * R), n * (f < 10 ? R : 8),
+                                        cudaMemcpyDeviceToHost, c->s);
+        if (e != cudaSuccess) return c->cuda_fail(e, "download");
+    }
+    cudaError_t e = cudaStreamSynchronize(c->s);
+    return e == cudaSuccess ? PIC_OK : c->cuda_fail(e, "download");
+}

@@ -1,0 +1,31 @@
+// Multigrid hierarchy carved from a caller workspace (see poisson.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pic {
+
+struct MG {
+    static constexpr int kMaxLevels = 12;
+    int levels = 0;
+    int lx[kMaxLevels], ly[kMaxLevels], lz[kMaxLevels];
+    float* e[kMaxLevels];
+    float* g[kMaxLevels];
+    uint8_t* m[kMaxLevels];
+    double* norms = nullptr;  // [0] ||b||^2, [1] ||r||^2
+    int pre = 2, post = 2, coarse_sweeps = 50;
+    long long launches = 0;  // kernels launched so far
+
+    void plan(int nx, int ny, int nz);
+    static size_t bytes(int nx, int ny, int nz);
+    void carve(void* base, int nx, int ny, int nz);
+    cudaError_t build_masks(const uint8_t* mask, cudaStream_t s);
+    void vcycle(cudaStream_t s);
+    // Returns PIC_OK, PIC_ERR_TIMEOUT or PIC_ERR_CUDA.  packed_prec selects the
+    // element type (32: float, 64: double) of the optional packed field E4.
+    int solve(const double* rho, const uint8_t* mask, double* phi, double h, double v_lo, double v_hi, double v_mask,
+              double rtol, int max_cycles, int packed_prec, void* E4, float* Ex, float* Ey, float* Ez,
+              cudaStream_t s, int* cycles_out, double* rel_out, double* host_norms);
+};
+
+}  // namespace pic

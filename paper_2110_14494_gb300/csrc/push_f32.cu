@@ -1,0 +1,3 @@
+// Single-precision electron push (FMA contraction allowed).
+#include "push_impl.cuh"
+template struct pic::PushLaunch<float>;

@@ -1,0 +1,344 @@
+"""Python binding of libpicmcc.so (include/picmcc.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  PyTorch provides device memory (workspaces, grids) and the
+stream.  The functions keep the C names; thin classes below own the
+workspace and the host arrays a context must keep alive.
+
+The library must have been built (``paper_2110_14494_gb300.build.build()``);
+importing this module without it raises, there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpicmcc.so")
+
+PIC_OK, PIC_ERR_ARG, PIC_ERR_CUDA, PIC_ERR_CAPACITY, PIC_ERR_OVERFLOW, PIC_ERR_TIMEOUT, PIC_ERR_STATE = \
+    0, -1, -2, -3, -4, -5, -6
+PIC_MAX_PROC, PIC_SWARM_NMOM, PIC_SWARM_NRES = 16, 16, 24
+RES_NAMES = ("W_flux", "W_bulk", "DL_flux", "DT_flux", "DL_bulk", "DT_bulk", "mean_eps", "k_ion", "k_att",
+             "alpha", "eta")
+
+PD = C.POINTER(C.c_double)
+PI = C.POINTER(C.c_int)
+PU64 = C.POINTER(C.c_uint64)
+VP = C.c_void_p
+
+
+class pic_gas(C.Structure):
+    _fields_ = [("n_proc", C.c_int), ("n_bins", C.c_int), ("eps", PD), ("sigma", PD), ("kind", PI),
+                ("threshold", PD), ("density", PD), ("mass", PD)]
+
+
+class pic_config(C.Structure):
+    _fields_ = [("precision", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dx", C.c_double),
+                ("origin", C.c_double * 3), ("capacity", C.c_longlong), ("seed", C.c_ulonglong),
+                ("dt", C.c_double), ("gas", pic_gas), ("n_ppc", C.c_int), ("w_min", C.c_double),
+                ("growth_trigger", C.c_double), ("particle_cap", C.c_longlong), ("boundary", C.c_int),
+                ("sort_interval", C.c_int), ("coupled", C.c_int), ("v_lo", C.c_double), ("v_hi", C.c_double),
+                ("v_mask", C.c_double), ("poisson_rtol", C.c_double), ("poisson_max_cycles", C.c_int)]
+
+
+class pic_particles_host(C.Structure):
+    _fields_ = [(k, PD) for k in ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az", "w")] + [("id", PU64)]
+
+
+class pic_step_stats(C.Structure):
+    _fields_ = [(k, C.c_longlong) for k in ("n_start", "n_end", "n_events", "n_null")] + \
+               [("n_coll", C.c_longlong * PIC_MAX_PROC)] + \
+               [(k, C.c_longlong) for k in ("n_children", "n_attached", "n_absorbed", "n_clamped",
+                                            "n_processed", "n_weight_updates", "n_sorts")] + \
+               [("w_ion", C.c_double), ("w_att", C.c_double), ("w_absorbed", C.c_double),
+                ("poisson_cycles", C.c_int), ("poisson_rel_res", C.c_double)]
+
+
+class pic_profile_times(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("ms_push", "ms_children", "ms_field", "ms_reorder")] + \
+               [(k, C.c_longlong) for k in ("n_push", "n_children", "n_field", "n_reorder", "n_launches")]
+
+
+class poisson_config(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dx", C.c_double), ("v_lo", C.c_double),
+                ("v_hi", C.c_double), ("v_mask", C.c_double)]
+
+
+class poisson_stats(C.Structure):
+    _fields_ = [("cycles", C.c_int), ("rel_res", C.c_double)]
+
+
+class swarm_config(C.Structure):
+    _fields_ = [("precision", C.c_int), ("gas", pic_gas), ("n_gas", C.c_double), ("n0", C.c_longlong),
+                ("n_lo", C.c_longlong), ("n_hi", C.c_longlong), ("capacity", C.c_longlong),
+                ("n_steps", C.c_int), ("dt", C.c_double), ("kT_eV", C.c_double), ("seed", C.c_ulonglong),
+                ("sample_from", C.c_double)]
+
+
+class swarm_result(C.Structure):
+    _fields_ = [("v", C.c_double * PIC_SWARM_NRES)]
+
+
+EXPORTS = ("pic_workspace_bytes", "pic_init", "pic_destroy", "pic_last_error", "pic_status_string",
+           "pic_seed_gaussian", "pic_set_particles", "pic_get_particles", "pic_set_field", "pic_step",
+           "pic_deposit", "pic_weight_update", "pic_count", "pic_save", "pic_load", "pic_progress",
+           "pic_profile", "pic_upload", "pic_download",
+           "poisson_workspace_bytes", "poisson_solve", "swarm_workspace_bytes", "swarm_run")
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2110_14494_gb300.build.build() "
+                           "(nvcc, sm_103a); there is no fallback")
+    L = C.CDLL(LIB_PATH)
+    P = C.POINTER
+    L.pic_workspace_bytes.argtypes = [P(pic_config)]
+    L.pic_workspace_bytes.restype = C.c_size_t
+    L.pic_init.argtypes = [P(pic_config), VP, C.c_size_t, VP, VP, P(VP)]
+    L.pic_destroy.argtypes = [VP]
+    L.pic_destroy.restype = None
+    L.pic_last_error.argtypes = [VP]
+    L.pic_last_error.restype = C.c_char_p
+    L.pic_status_string.argtypes = [C.c_int]
+    L.pic_status_string.restype = C.c_char_p
+    L.pic_seed_gaussian.argtypes = [VP, C.c_double, C.c_double, PD, C.c_double, P(C.c_longlong)]
+    L.pic_set_particles.argtypes = [VP, C.c_longlong, P(pic_particles_host), C.c_int]
+    L.pic_get_particles.argtypes = [VP, P(pic_particles_host), C.c_longlong, P(C.c_longlong)]
+    L.pic_set_field.argtypes = [VP, VP, VP, VP, PD]
+    L.pic_step.argtypes = [VP, C.c_int, P(pic_step_stats)]
+    L.pic_deposit.argtypes = [VP, VP, VP, VP, VP]
+    L.pic_weight_update.argtypes = [VP]
+    L.pic_count.argtypes = [VP, P(C.c_longlong)]
+    L.pic_save.argtypes = [VP, VP, P(C.c_size_t)]
+    L.pic_load.argtypes = [VP, VP, C.c_size_t]
+    L.pic_progress.argtypes = [VP, P(C.c_longlong), P(C.c_longlong), P(C.c_longlong)]
+    L.pic_profile.argtypes = [VP, C.c_int, P(pic_profile_times)]
+    L.pic_upload.argtypes = [VP, C.c_longlong, P(VP), C.c_int]
+    L.pic_download.argtypes = [VP, P(VP), C.c_longlong, P(C.c_longlong)]
+    L.poisson_workspace_bytes.argtypes = [P(poisson_config)]
+    L.poisson_workspace_bytes.restype = C.c_size_t
+    L.poisson_solve.argtypes = [P(poisson_config), VP, VP, VP, VP, VP, VP, C.c_double, C.c_int, VP, C.c_size_t,
+                                P(poisson_stats), VP]
+    L.swarm_workspace_bytes.argtypes = [P(swarm_config), C.c_int]
+    L.swarm_workspace_bytes.restype = C.c_size_t
+    L.swarm_run.argtypes = [P(swarm_config), C.c_int, PD, VP, C.c_size_t, P(swarm_result), PD,
+                            P(C.c_longlong), VP]
+    _lib = L
+    return L
+
+
+class PicError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+def _check(rc, ctx=None, what=""):
+    if rc != PIC_OK:
+        msg = lib().pic_last_error(ctx).decode() if ctx else lib().pic_status_string(rc).decode()
+        raise PicError(rc, f"{what}: {msg}")
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _workspace(nbytes: int):
+    import torch
+    t = torch.empty(max(int(nbytes), 256) + 256, dtype=torch.uint8, device="cuda")
+    off = (-t.data_ptr()) % 256
+    return t, t.data_ptr() + off
+
+
+class Gas:
+    """Keeps the host arrays of a pic_gas alive."""
+
+    def __init__(self, gas: dict):
+        self.arrays = dict(
+            eps=np.ascontiguousarray(gas["eps"], np.float64),
+            sigma=np.ascontiguousarray(gas["sigma"], np.float64),
+            kind=np.ascontiguousarray(gas["kind"], np.int32),
+            threshold=np.ascontiguousarray(gas["threshold"], np.float64),
+            density=np.ascontiguousarray(gas["density"], np.float64),
+            mass=np.ascontiguousarray(gas["mass"], np.float64))
+        a = self.arrays
+        self.c = pic_gas(a["sigma"].shape[0], a["sigma"].shape[1], a["eps"].ctypes.data_as(PD),
+                         a["sigma"].ctypes.data_as(PD), a["kind"].ctypes.data_as(PI),
+                         a["threshold"].ctypes.data_as(PD), a["density"].ctypes.data_as(PD),
+                         a["mass"].ctypes.data_as(PD))
+        self.n_gas = float(gas.get("n_gas", 0.0))
+
+
+class PicContext:
+    """A pic_ctx over a torch-allocated workspace."""
+
+    FIELDS = ("x", "y", "z", "vx", "vy", "vz", "ax", "ay", "az", "w")
+
+    def __init__(self, gas: dict, grid: dict, *, precision=32, capacity=1 << 20, seed=1, dt=1e-12, mask=None,
+                 n_ppc=75, w_min=1.0, growth_trigger=0.0, particle_cap=0, boundary=0, sort_interval=0,
+                 coupled=False, v_lo=0.0, v_hi=0.0, v_mask=0.0, poisson_rtol=1e-6, poisson_max_cycles=100,
+                 stream=None):
+        import torch
+        self.gas = Gas(gas)
+        c = pic_config()
+        c.precision, c.nx, c.ny, c.nz, c.dx = precision, grid["nx"], grid["ny"], grid["nz"], grid["dx"]
+        for d in range(3):
+            c.origin[d] = grid["origin"][d]
+        c.capacity, c.seed, c.dt, c.gas = capacity, seed, dt, self.gas.c
+        c.n_ppc, c.w_min, c.growth_trigger, c.particle_cap = n_ppc, w_min, growth_trigger, particle_cap
+        c.boundary, c.sort_interval, c.coupled = boundary, sort_interval, int(coupled)
+        c.v_lo, c.v_hi, c.v_mask, c.poisson_rtol, c.poisson_max_cycles = v_lo, v_hi, v_mask, poisson_rtol, \
+            poisson_max_cycles
+        self.cfg = c
+        self.grid = grid
+        self.ncell = grid["nx"] * grid["ny"] * grid["nz"]
+        nbytes = lib().pic_workspace_bytes(C.byref(c))
+        if nbytes == 0:
+            raise PicError(PIC_ERR_ARG, "invalid pic_config")
+        self.ws_bytes = nbytes
+        self._ws, self._ws_ptr = _workspace(nbytes)
+        self.mask = None
+        if mask is not None:
+            self.mask = torch.as_tensor(np.ascontiguousarray(mask, np.uint8)).cuda()
+        self.stream = stream
+        h = C.c_void_p()
+        _check(lib().pic_init(C.byref(c), C.c_void_p(self._ws_ptr), nbytes, _ptr(self.mask), _stream(stream),
+                              C.byref(h)), None, "pic_init")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def seed_gaussian(self, n0, radius, center, w0) -> int:
+        cen = (C.c_double * 3)(*center)
+        n = C.c_longlong()
+        _check(lib().pic_seed_gaussian(self.h, n0, radius, cen, w0, C.byref(n)), self.h, "pic_seed_gaussian")
+        return n.value
+
+    def set_particles(self, p: dict, accel_valid=False):
+        n = len(p["x"])
+        keep = {k: np.ascontiguousarray(p[k], np.float64) for k in self.FIELDS if k in p}
+        ids = np.ascontiguousarray(p["id"], np.uint64)
+        hp = pic_particles_host(*[keep[k].ctypes.data_as(PD) if k in keep else None for k in self.FIELDS],
+                                ids.ctypes.data_as(PU64))
+        _check(lib().pic_set_particles(self.h, n, C.byref(hp), int(accel_valid)), self.h, "pic_set_particles")
+
+    def get_particles(self) -> dict:
+        n = C.c_longlong()
+        _check(lib().pic_get_particles(self.h, None, 0, C.byref(n)), self.h, "pic_get_particles")
+        out = {k: np.zeros(n.value) for k in self.FIELDS}
+        out["id"] = np.zeros(n.value, np.uint64)
+        hp = pic_particles_host(*[out[k].ctypes.data_as(PD) for k in self.FIELDS], out["id"].ctypes.data_as(PU64))
+        _check(lib().pic_get_particles(self.h, C.byref(hp), n.value, C.byref(n)), self.h, "pic_get_particles")
+        return out
+
+    def set_field(self, Ex=None, Ey=None, Ez=None, uniform=None):
+        u = (C.c_double * 3)(*(uniform if uniform is not None else (0.0, 0.0, 0.0)))
+        _check(lib().pic_set_field(self.h, _ptr(Ex), _ptr(Ey), _ptr(Ez), u), self.h, "pic_set_field")
+
+    def step(self, n_steps=1, stats=False):
+        st = pic_step_stats() if stats else None
+        _check(lib().pic_step(self.h, n_steps, C.byref(st) if st is not None else None), self.h, "pic_step")
+        return st
+
+    def deposit(self, q_e=None, q_pos=None, q_neg=None, rho=None):
+        _check(lib().pic_deposit(self.h, _ptr(q_e), _ptr(q_pos), _ptr(q_neg), _ptr(rho)), self.h, "pic_deposit")
+
+    def weight_update(self):
+        _check(lib().pic_weight_update(self.h), self.h, "pic_weight_update")
+
+    def count(self) -> int:
+        n = C.c_longlong()
+        _check(lib().pic_count(self.h, C.byref(n)), self.h, "pic_count")
+        return n.value
+
+    def progress(self):
+        u, p, s = C.c_longlong(), C.c_longlong(), C.c_longlong()
+        _check(lib().pic_progress(self.h, C.byref(u), C.byref(p), C.byref(s)), self.h, "pic_progress")
+        return u.value, p.value, s.value
+
+    def profile(self, enable=True):
+        t = pic_profile_times()
+        _check(lib().pic_profile(self.h, int(enable), C.byref(t)), self.h, "pic_profile")
+        return {f[0]: getattr(t, f[0]) for f in pic_profile_times._fields_}
+
+    def upload(self, arrays, n, accel_valid=True):
+        """arrays: 11 host tensors/arrays (pinned for asynchronous copies) in native precision."""
+        ptrs = (VP * 11)(*[a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data for a in arrays])
+        _check(lib().pic_upload(self.h, n, ptrs, int(accel_valid)), self.h, "pic_upload")
+
+    def download(self, arrays, cap) -> int:
+        ptrs = (VP * 11)(*[a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data for a in arrays])
+        n = C.c_longlong()
+        _check(lib().pic_download(self.h, ptrs, cap, C.byref(n)), self.h, "pic_download")
+        return n.value
+
+    def save(self) -> bytes:
+        sz = C.c_size_t(0)
+        _check(lib().pic_save(self.h, None, C.byref(sz)), self.h, "pic_save")
+        buf = (C.c_char * sz.value)()
+        _check(lib().pic_save(self.h, buf, C.byref(sz)), self.h, "pic_save")
+        return bytes(buf)
+
+    def load(self, blob: bytes):
+        buf = (C.c_char * len(blob)).from_buffer_copy(blob)
+        _check(lib().pic_load(self.h, buf, len(blob)), self.h, "pic_load")
+
+
+def poisson_solve(grid: dict, rho, phi, mask=None, E=None, v_lo=0.0, v_hi=0.0, v_mask=0.0, rtol=1e-6,
+                  max_cycles=100, stream=None):
+    """rho, phi: float64 CUDA tensors [nz][ny][nx]; E: optional tuple of three float32 tensors."""
+    pc = poisson_config(grid["nx"], grid["ny"], grid["nz"], grid["dx"], v_lo, v_hi, v_mask)
+    nb = lib().poisson_workspace_bytes(C.byref(pc))
+    ws, ptr = _workspace(nb)
+    st = poisson_stats()
+    Ex, Ey, Ez = E if E is not None else (None, None, None)
+    rc = lib().poisson_solve(C.byref(pc), _ptr(rho), _ptr(mask), _ptr(phi), _ptr(Ex), _ptr(Ey), _ptr(Ez), rtol,
+                             max_cycles, C.c_void_p(ptr), nb, C.byref(st), _stream(stream))
+    _check(rc, None, "poisson_solve")
+    return st.cycles, st.rel_res
+
+
+def swarm_run(gas: dict, EN_Td, *, precision=64, n0=10000, n_steps=2000, dt=1e-12, kT_eV=1.0, seed=1,
+              n_lo=1000, n_hi=1_000_000, capacity=None, sample_from=0.25, stream=None, want_moments=False):
+    """Runs len(EN_Td) swarms; returns (results [n][24], moments or None, counts or None)."""
+    g = Gas(gas)
+    EN = np.ascontiguousarray(np.atleast_1d(EN_Td), np.float64)
+    if capacity is None:
+        capacity = max(2 * n_hi, 4 * n0)
+    sc = swarm_config(precision, g.c, g.n_gas, n0, n_lo, n_hi, capacity, n_steps, dt, kT_eV, seed, sample_from)
+    nb = lib().swarm_workspace_bytes(C.byref(sc), len(EN))
+    if nb == 0:
+        raise PicError(PIC_ERR_ARG, "invalid swarm_config")
+    ws, ptr = _workspace(nb)
+    res = (swarm_result * len(EN))()
+    mom = np.zeros((len(EN), n_steps, PIC_SWARM_NMOM)) if want_moments else None
+    cnt = np.zeros((len(EN), n_steps), np.int64) if want_moments else None
+    rc = lib().swarm_run(C.byref(sc), len(EN), EN.ctypes.data_as(PD), C.c_void_p(ptr), nb, res,
+                         mom.ctypes.data_as(PD) if mom is not None else None,
+                         cnt.ctypes.data_as(C.POINTER(C.c_longlong)) if cnt is not None else None, _stream(stream))
+    _check(rc, None, "swarm_run")
+    out = np.array([[r.v[i] for i in range(PIC_SWARM_NRES)] for r in res])
+    return out, mom, cnt

@@ -1,0 +1,66 @@
+"""The C-ABI library loads and exports every function include/picmcc.h
+declares; argument validation runs on the host (no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "picmcc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = set(re.findall(r"^\s*(?:const\s+)?[\w ]+?\**\s*\b(\w+)\s*\(", src, flags=re.M))
+    return {n for n in names if n.startswith(("pic_", "poisson_", "swarm_"))}
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2110_14494_gb300 import build
+    build.build()
+    from paper_2110_14494_gb300 import picmcc
+    return picmcc.lib()
+
+
+def test_every_declared_symbol_is_exported(L):
+    decl = _declared()
+    assert len(decl) >= 19, decl
+    for name in decl:
+        assert hasattr(L, name), name
+    from paper_2110_14494_gb300 import picmcc
+    assert set(picmcc.EXPORTS) == decl
+
+
+def test_status_strings(L):
+    assert L.pic_status_string(0) == b"ok"
+    assert L.pic_status_string(-3) == b"capacity exceeded"
+    assert L.pic_status_string(7) == b"unknown status"
+
+
+def test_host_argument_validation(L):
+    import workloads as W
+    from paper_2110_14494_gb300 import picmcc as P
+    gas = P.Gas(W.synthetic_air())
+    c = P.pic_config()
+    c.precision, c.nx, c.ny, c.nz, c.dx, c.capacity, c.dt, c.gas = 32, 8, 8, 8, 1e-5, 1000, 1e-12, gas.c
+    assert L.pic_workspace_bytes(C.byref(c)) > 0
+    for field, bad in (("precision", 16), ("nx", 1), ("dx", 0.0), ("capacity", 0), ("dt", -1.0)):
+        old = getattr(c, field)
+        setattr(c, field, bad)
+        assert L.pic_workspace_bytes(C.byref(c)) == 0, field
+        setattr(c, field, old)
+    h = C.c_void_p()
+    assert L.pic_init(C.byref(c), None, 0, None, None, C.byref(h)) == P.PIC_ERR_ARG
+    pc = P.poisson_config(1, 8, 8, 1e-5, 0, 0, 0)
+    assert L.poisson_workspace_bytes(C.byref(pc)) == 0
+    pc.nx = 8
+    assert L.poisson_workspace_bytes(C.byref(pc)) > 0
+    assert L.poisson_solve(C.byref(pc), None, None, None, None, None, None, 1e-6, 10, None, 0, None, None) == \
+        P.PIC_ERR_ARG
+    sc = P.swarm_config(64, gas.c, 2.45e25, 100, 10, 1000, 2000, 10, 1e-12, 1.0, 1, 0.25)
+    assert L.swarm_workspace_bytes(C.byref(sc), 1) > 0
+    sc.n_steps = 0
+    assert L.swarm_workspace_bytes(C.byref(sc), 1) == 0

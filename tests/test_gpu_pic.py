@@ -1,0 +1,193 @@
+"""GPU parity of the PIC electron step against the FP64 CPU oracle, through
+the C ABI, on identical seeded inputs (same Philox streams).
+
+Tolerances: double precision 1e-12 relative per particle (only libm versus
+CUDA ulps of log/sqrt/sincos differ); single precision 1e-5 relative (position
+per cell size, velocity per |v| + 1e5 m/s, the speed of a 0.03 eV electron,
+i.e. room-temperature thermal energy).  In single precision two kinds of
+particle miss that bound and are counted separately: decision flips (a branch
+taken differently at rounding distance, visible as a gross difference
+> 1e-3 or a particle present on one side only), bounded by 1e-5 of the
+particles plus two; and rounding amplification in eps - eps_threshold after an
+inelastic collision that leaves the electron just above zero energy (the
+float32 energy carries ~1e-7 relative error, amplified by eps/(eps - eps_th)),
+bounded by 1e-3 of the particles, each within 1e-3.  The deposit is bit-exact
+when both sides deposit identical particles."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from tests.gpu_common import by_id, compare_sets
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2110_14494_gb300 import build
+    build.build()
+
+
+def _ctx(gas, grid, prec, **kw):
+    from paper_2110_14494_gb300 import PicContext
+    return PicContext(gas, grid, precision=prec, **kw)
+
+
+def _field_dev(F):
+    return tuple(torch.as_tensor(f).cuda() for f in F)
+
+
+GRID = W.grid_spec(24, 20, 28, 2e-5, origin=(1e-5, -2e-5, 0.0))
+SEED = 2110144940
+
+
+def _setup(n, prec, seed_off, vmax=3e6, mask=True):
+    gas = W.synthetic_air()
+    F = W.smooth_field(GRID, 100 + seed_off, e0=3e6)
+    mk = W.needle_mask(GRID, 0.2e-3, 0.06e-3) if mask else None
+    p0 = W.random_particles(n, GRID, 200 + seed_off, vmax=vmax, w_range=(1.0, 500.0))
+    return gas, F, mk, p0
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_deposit_bit_exact(prec):
+    gas, F, mk, p0 = _setup(20000, prec, 1)
+    ctx = _ctx(gas, GRID, prec, capacity=40000, seed=SEED)
+    ctx.set_particles(p0)
+    n = GRID["nx"] * GRID["ny"] * GRID["nz"]
+    q = torch.zeros(n, dtype=torch.int64, device="cuda")
+    ctx.deposit(q_e=q)
+    m = O.Model(gas, 1e-12, SEED, prec, GRID)
+    ref = O.deposit(m, O.Particles(20000, p0))
+    assert np.array_equal(q.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("steps", [1, 10])
+def test_step_fp64_matches_oracle(steps):
+    gas, F, mk, p0 = _setup(6000, 64, 2)
+    dt = 2e-12
+    ctx = _ctx(gas, GRID, 64, capacity=40000, seed=SEED, dt=dt, mask=mk)
+    Fd = _field_dev(F)
+    ctx.set_field(*Fd)
+    ctx.set_particles(p0)
+    st = ctx.step(steps, stats=True)
+    n = GRID["nx"] * GRID["ny"] * GRID["nz"]
+    qe, qp, qn = (torch.zeros(n, dtype=torch.int64, device="cuda") for _ in range(3))
+    ctx.deposit(q_e=qe, q_pos=qp, q_neg=qn)
+    gpu = ctx.get_particles()
+
+    m = O.Model(gas, dt, SEED, 64, GRID, F, mask=mk)
+    P = O.Particles(40000, p0)
+    rq_pos, rq_neg = np.zeros(n, np.int64), np.zeros(n, np.int64)
+    for s in range(1, steps + 1):
+        rq_e = np.zeros(n, np.int64)
+        rc, ost = O.step(m, P, s, s == 1, rq_e, rq_pos, rq_neg)
+        assert rc == 0
+    ref = P.view()
+    nc, og, orf, bad, worst = compare_sets(gpu, ref, GRID["dx"], 1e-12, v_floor=1.0)
+    assert og == 0 and orf == 0, (og, orf)
+    assert bad == 0, worst
+    assert st.n_children > 0 and st.n_attached >= 0 and st.n_null > 0
+    # deposits agree to a few fixed-point units per cell (ulp-level position differences)
+    for a, b in ((qe, rq_e), (qp, rq_pos), (qn, rq_neg)):
+        d = np.abs(a.cpu().numpy() - b)
+        assert d.max() <= 64, d.max()
+    assert int(qe.sum()) == int(rq_e.sum()) or abs(int(qe.sum()) - int(rq_e.sum())) < 64
+
+
+def test_step_fp32_matches_oracle_single_step():
+    gas, F, mk, p0 = _setup(100000, 32, 3)
+    dt = 2e-12
+    ctx = _ctx(gas, GRID, 32, capacity=200000, seed=SEED, dt=dt, mask=mk)
+    ctx.set_field(*_field_dev(F))
+    ctx.set_particles(p0)
+    st = ctx.step(1, stats=True)
+    gpu = ctx.get_particles()
+    m = O.Model(gas, dt, SEED, 64, GRID, F, mask=mk)
+    P = O.Particles(200000, p0)
+    rc, ost = O.step(m, P, 1, True)
+    ref = P.view()
+    nc, og, orf, bad, worst = compare_sets(gpu, ref, GRID["dx"], 1e-5, v_floor=1e5)
+    flips = worst["gross"] + og + orf
+    print("fp32 single step: common", nc, "only gpu", og, "only ref", orf, "outside 1e-5", bad, worst)
+    assert flips <= 1e-5 * len(p0["x"]) + 2, (flips, worst)
+    assert bad - worst["gross"] <= 1e-3 * len(p0["x"]), (bad, worst)
+    assert st.n_events > 0 and abs(st.n_events - ost.n_events) <= 1e-4 * ost.n_events + 5
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_gaussian_seed_matches_oracle(prec):
+    grid = W.grid_spec(32, 32, 32, 2e-5)
+    L = 32 * 2e-5
+    mk = W.needle_mask(grid, 0.2e-3, 0.05e-3)
+    gas = W.synthetic_air()
+    ctx = _ctx(gas, grid, prec, capacity=600000, seed=SEED, mask=mk)
+    c = (0.5 * L, 0.5 * L, L - 0.2e-3)
+    n = ctx.seed_gaussian(1e19, 1e-4, c, 200.0)
+    gpu = by_id(ctx.get_particles())
+    m = O.Model(gas, 1e-12, SEED, prec, grid, mask=mk)
+    P = O.seed_gaussian(m, 1e19, 1e-4, c, 200.0, 600000)
+    ref = by_id(P.view())
+    assert n == P.n and np.array_equal(gpu["id"], ref["id"])
+    for k in ("x", "y", "z"):
+        r = ref[k].astype(np.float32).astype(np.float64) if prec == 32 else ref[k]
+        assert np.array_equal(gpu[k], r), k
+    qp = torch.zeros(32 ** 3, dtype=torch.int64, device="cuda")
+    ctx.deposit(q_pos=qp)
+    m2 = O.Model(gas, 1e-12, SEED, prec, grid)
+    assert np.array_equal(qp.cpu().numpy(), O.deposit(m2, P))
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_weight_update_matches_oracle(prec):
+    grid = W.grid_spec(6, 6, 6, 1e-4)
+    rng = np.random.default_rng(9)
+    p0 = W.random_particles(8000, grid, 41, w_range=(1.0, 3.0))
+    p0["w"][:60] = rng.uniform(100, 900, 60).astype(np.float32).astype(np.float64)
+    gas = W.synthetic_air()
+    ctx = _ctx(gas, grid, prec, capacity=40000, seed=SEED, n_ppc=10, w_min=1.0, particle_cap=0)
+    ctx.set_particles(p0)
+    ctx.weight_update()
+    gpu = by_id(ctx.get_particles())
+    m = O.Model(gas, 1e-12, SEED, prec, grid)
+    P = O.Particles(40000, p0)
+    rc, ms = O.merge_split(m, P, 0, n_ppc=10, w_min=1.0, cap=0)
+    ref = by_id(P.view())
+    assert np.array_equal(gpu["id"], ref["id"])
+    for k in ("x", "y", "z", "vx", "vy", "vz", "w"):
+        assert np.array_equal(gpu[k], ref[k]), k
+
+
+def test_checkpoint_resume_is_bit_identical():
+    gas, F, mk, p0 = _setup(5000, 32, 4)
+    Fd = _field_dev(F)
+    a = _ctx(gas, GRID, 32, capacity=20000, seed=SEED, dt=2e-12, mask=mk)
+    a.set_field(*Fd)
+    a.set_particles(p0)
+    a.step(3)
+    blob = a.save()
+    a.step(4)
+    ra = by_id(a.get_particles())
+    b = _ctx(gas, GRID, 32, capacity=20000, seed=SEED, dt=2e-12, mask=mk)
+    b.set_field(*Fd)
+    b.load(blob)
+    b.step(4)
+    rb = by_id(b.get_particles())
+    for k in ra:
+        assert np.array_equal(ra[k], rb[k]), k
+
+
+def test_capacity_error_is_reported_not_faulted():
+    from paper_2110_14494_gb300 import PicError
+    gas, F, mk, p0 = _setup(3000, 32, 5, vmax=6e6)
+    ctx = _ctx(gas, GRID, 32, capacity=3010, seed=SEED, dt=2e-12)
+    ctx.set_field(*_field_dev(F))
+    ctx.set_particles(p0)
+    with pytest.raises(PicError) as e:
+        ctx.step(5)
+    assert e.value.code == -3
