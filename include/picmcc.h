@@ -226,6 +226,22 @@ int poisson_solve(const poisson_config *pc, const double *rho, const uint8_t *ma
                   float *Ex, float *Ey, float *Ez, double rtol, int max_cycles, void *d_workspace,
                   size_t workspace_bytes, poisson_stats *stats, pic_stream_t stream);
 
+/* Same solve as poisson_solve, for callers that cannot allocate device
+ * memory (no workspace argument).  The paper has no counterpart: this is a
+ * deployment convenience.  The multigrid scratch is a fixed 32 MiB device
+ * array inside the library (held on every GPU that loads it until the
+ * process exits), enough for grids of about 2.7 million cells (128^3 fits);
+ * larger grids return PIC_ERR_CAPACITY and touch nothing.  The first call on
+ * a device looks up that array's device address (cudaGetSymbolAddress) with
+ * the device current, so make the first call on each device outside any
+ * stream capture.  Every call shares the one array: calls that can overlap
+ * on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  Nothing is allocated; arguments and results are
+ * as for poisson_solve. */
+int poisson_solve_noalloc(const poisson_config *pc, const double *rho, const uint8_t *mask, double *phi,
+                          float *Ex, float *Ey, float *Ez, double rtol, int max_cycles, poisson_stats *stats,
+                          pic_stream_t stream);
+
 /* -------------------------------------------------------------------- swarm */
 /* Monte Carlo swarms in uniform fields (Sec. 2.2.2).  Each swarm starts
  * n0 electrons at the origin with Maxwellian velocities at temperature kT,

@@ -413,3 +413,58 @@ extern "C" int poisson_solve(const poisson_config* pc, const double* rho, const 
     if (st) { st->cycles = cycles; st->rel_res = rel; }
     return rc;
 }
+
+// ------------------------------------------------------------------ no-allocation variant
+// Some callers cannot allocate device memory for a workspace: code running
+// where cudaMalloc is not permitted or not wanted (inside a region being
+// captured into a CUDA graph by a framework that forbids allocation, plugins
+// handed only input and output pointers by a host application, or
+// hard-real-time loops that must not touch the allocator).  For them the
+// multigrid hierarchy lives in a fixed device array owned by this library.
+//
+// The array is file-scope device memory of kNoAllocScratchBytes (32 MiB), held
+// by every GPU that loads the library until the process exits.  In host code
+// its name is only a host-side stand-in, so the device address is looked up
+// with cudaGetSymbolAddress once per device (with that device current) and
+// cached.
+constexpr size_t kNoAllocScratchBytes = 32u << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+#include <mutex>
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[64];
+
+static int noalloc_scratch(void** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return PIC_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return PIC_ERR_CUDA;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return PIC_OK;
+}
+
+extern "C" int poisson_solve_noalloc(const poisson_config* pc, const double* rho, const uint8_t* mask, double* phi,
+                                     float* Ex, float* Ey, float* Ez, double rtol, int max_cycles, poisson_stats* st,
+                                     pic_stream_t stream) {
+    if (!pc || !rho || !phi || pc->nx < 2 || pc->ny < 2 || pc->nz < 2 || !(pc->dx > 0) || !(rtol > 0) ||
+        max_cycles < 0)
+        return PIC_ERR_ARG;
+    if ((Ex == nullptr) != (Ey == nullptr) || (Ex == nullptr) != (Ez == nullptr)) return PIC_ERR_ARG;
+    if (MG::bytes(pc->nx, pc->ny, pc->nz) > kNoAllocScratchBytes) return PIC_ERR_CAPACITY;
+    void* ws = nullptr;
+    int rc = noalloc_scratch(&ws);
+    if (rc) return rc;
+    MG mg;
+    mg.carve(ws, pc->nx, pc->ny, pc->nz);
+    double hn[2];
+    int cycles = 0;
+    double rel = 0.0;
+    rc = mg.solve(rho, mask, phi, pc->dx, pc->v_lo, pc->v_hi, pc->v_mask, rtol, max_cycles, 32, nullptr, Ex, Ey, Ez,
+                  (cudaStream_t)stream, &cycles, &rel, hn);
+    if (st) { st->cycles = cycles; st->rel_res = rel; }
+    return rc;
+}

@@ -86,7 +86,8 @@ EXPORTS = ("pic_workspace_bytes", "pic_init", "pic_destroy", "pic_last_error", "
            "pic_seed_gaussian", "pic_set_particles", "pic_get_particles", "pic_set_field", "pic_step",
            "pic_deposit", "pic_weight_update", "pic_count", "pic_save", "pic_load", "pic_progress",
            "pic_profile", "pic_upload", "pic_download",
-           "poisson_workspace_bytes", "poisson_solve", "swarm_workspace_bytes", "swarm_run")
+           "poisson_workspace_bytes", "poisson_solve", "poisson_solve_noalloc", "swarm_workspace_bytes",
+           "swarm_run")
 
 _lib = None
 
@@ -127,6 +128,8 @@ def lib():
     L.poisson_workspace_bytes.restype = C.c_size_t
     L.poisson_solve.argtypes = [P(poisson_config), VP, VP, VP, VP, VP, VP, C.c_double, C.c_int, VP, C.c_size_t,
                                 P(poisson_stats), VP]
+    L.poisson_solve_noalloc.argtypes = [P(poisson_config), VP, VP, VP, VP, VP, VP, C.c_double, C.c_int,
+                                        P(poisson_stats), VP]
     L.swarm_workspace_bytes.argtypes = [P(swarm_config), C.c_int]
     L.swarm_workspace_bytes.restype = C.c_size_t
     L.swarm_run.argtypes = [P(swarm_config), C.c_int, PD, VP, C.c_size_t, P(swarm_result), PD,
