@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cap", type=int, default=0, help="particle slots (default 1.6x the particle cap)")
     return ap.parse_args()
 
 
@@ -208,7 +209,7 @@ def main():
     g = wl["grid"]
     gas = W.synthetic_air()
     mask = W.needle_mask(g, wl["needle_length"], wl["needle_radius"])
-    cap = int(wl["particle_cap"] * 1.6) if args.grid == 128 else int(max(8 * args.n_initial, 1 << 20))
+    cap = args.cap or (int(wl["particle_cap"] * 1.6) if args.grid == 128 else int(max(8 * args.n_initial, 1 << 20)))
     w0 = wl["seed_n0"] * np.pi ** 1.5 * wl["seed_radius"] ** 3 / wl["n_initial"]
     ctx = PicContext(gas, g, precision=args.precision, capacity=cap, seed=2110144940 + rank, dt=wl["dt"],
                      mask=mask, n_ppc=wl["n_ppc"], w_min=wl["w_min"], growth_trigger=wl["growth_trigger"],

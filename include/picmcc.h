@@ -230,8 +230,9 @@ int poisson_solve(const poisson_config *pc, const double *rho, const uint8_t *ma
  * memory (no workspace argument).  The paper has no counterpart: this is a
  * deployment convenience.  The multigrid scratch is a fixed 32 MiB device
  * array inside the library (held on every GPU that loads it until the
- * process exits), enough for grids of about 2.7 million cells (128^3 fits);
- * larger grids return PIC_ERR_CAPACITY and touch nothing.  The first call on
+ * process exits), enough for grids of up to about 0.95 million cells (96^3
+ * fits, 100^3 does not); larger grids return PIC_ERR_CAPACITY and touch
+ * nothing.  The first call on
  * a device looks up that array's device address (cudaGetSymbolAddress) with
  * the device current, so make the first call on each device outside any
  * stream capture.  Every call shares the one array: calls that can overlap

@@ -89,10 +89,15 @@ template <class T> struct Soa {
 };
 enum { PX = 0, PY, PZ, VX, VY, VZ, AX, AY, AZ, PW };
 
-// Pending children (born inside a step, still to fly for t_left).
+// Pending ionization products (born inside a step, still to fly for t_left).
+// An entry holds the collision position x, the parent's acceleration a and
+// weight w, the remaining time, the parent's id and the index k of the draw
+// that ionized (the product's id and direction are derived from them when the
+// entry is started), and the product's speed in the VX slot.
 template <class T> struct ChildQ {
     Soa<T> p;
     T* t_left;
+    uint32_t* k;
 };
 
 // Per-context device counters and statistics (lives in the workspace).
@@ -110,7 +115,8 @@ struct DevState {
     long long pred_total;         // merge/split: predicted count in 2^-24 units
     unsigned long long n_updates; // cumulative parents + queued children advanced
     unsigned long long n_parents; // cumulative parents advanced
-    long long pad[1];
+    unsigned long long n_fetch;   // work cursor of the parent kernel (items handed to warps)
+    unsigned long long n_fetch_c; // work cursor of the children kernel
 };
 
 // Uniform grid description (cell-centred, cubic cells).

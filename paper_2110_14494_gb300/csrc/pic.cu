@@ -226,6 +226,8 @@ __global__ void k_end_step(DevState* st, long long* count_slot, long long cap) {
     st->n_updates += st->n_in + nc;
     st->n_parents += st->n_in;
     st->n_in = st->n_out < (unsigned long long)cap ? st->n_out : (unsigned long long)cap;
+    st->n_fetch = 0;
+    st->n_fetch_c = 0;
     st->n_out = 0;
     st->n_child = 0;
     if (count_slot) *count_slot = (long long)st->n_in;
@@ -233,6 +235,8 @@ __global__ void k_end_step(DevState* st, long long* count_slot, long long cap) {
 
 __global__ void k_set_count(DevState* st, unsigned long long n) {
     st->n_in = n;
+    st->n_fetch = 0;
+    st->n_fetch_c = 0;
     st->n_out = 0;
     st->n_child = 0;
     st->n_extra = 0;
@@ -481,6 +485,7 @@ static Layout make_layout(const pic_config* c) {
     L.cq = o;
     for (int f = 0; f < 11; ++f) take(cap * R);  // 10 fields + t_left
     take(cap * 8);
+    take(cap * 4);                               // draw index of the ionization
     const int nb = c->gas.n_bins > 0 ? c->gas.n_bins : 2;
     L.table = take((size_t)nb * kTableStride * R);
     L.table64 = take((size_t)nb * kTableStride * 8);
@@ -552,6 +557,7 @@ struct pic_ctx {
     ~pic_ctx() {
         for (int i = 0; i < 8; ++i)
             if (ev[i]) cudaEventDestroy(ev[i]);
+        mg.release();
     }
 
     template <class T> Soa<T> soa(int b) {
@@ -570,6 +576,8 @@ struct pic_ctx {
         q.t_left = (T*)p;
         p += al256(cap * sizeof(T));
         q.p.id = (uint64_t*)p;
+        p += al256(cap * 8);
+        q.k = (uint32_t*)p;
         return q;
     }
     DevState* st() { return (DevState*)(ws + L.st); }
@@ -704,7 +712,10 @@ extern "C" int pic_init(const pic_config* cfg, void* d_ws, size_t ws_bytes, cons
     const int bps = c->prec == 32 ? PushLaunch<float>::blocks_per_sm(MODE_PIC, c->n_bins)
                                   : PushLaunch<double>::blocks_per_sm(MODE_PIC, c->n_bins);
     c->grid_push = sms * bps;
-    if (cfg->coupled) c->mg.carve(c->ws + L.mg, cfg->nx, cfg->ny, cfg->nz);
+    if (cfg->coupled) {
+        c->mg.carve(c->ws + L.mg, cfg->nx, cfg->ny, cfg->nz);
+        c->mg.persistent = true;
+    }
     *out = c;
     return PIC_OK;
 }
@@ -722,8 +733,8 @@ template <class T> static PushArgs<T> make_args(pic_ctx* c, int mode) {
     A.n_bins = c->n_bins;
     A.n_proc = c->n_proc;
     for (int k = 0; k < 8; ++k) { A.kind[k] = c->kind[k]; A.thr[k] = (T)c->thr[k]; A.mratio[k] = (T)c->mratio[k]; }
-    A.l0 = c->l0;
-    A.inv_dl = c->inv_dl;
+    A.l0 = (T)c->l0;
+    A.inv_dl = (T)c->inv_dl;
     A.eps_lo = (T)c->cfg.gas.eps[0];
     A.eps_hi = (T)c->cfg.gas.eps[c->n_bins - 1];
     A.nu_max = (T)c->nu_max;
@@ -992,8 +1003,9 @@ template <class T> static int one_step(pic_ctx* c, bool stats) {
     PushArgs<T> A = make_args<T>(c, MODE_PIC);
     cudaMemsetAsync(c->qe(), 0, (size_t)c->g.ncell() * 8, c->s);
     c->mark(0);
-    c->launches += 3;
-    cudaError_t e = PushLaunch<T>::parents(A, MODE_PIC, stats, c->grid_push, c->s);
+    c->launches += 4;
+    cudaError_t e = PushLaunch<T>::field_kick(A, grid_n(c->cfg.capacity), c->s);
+    if (e == cudaSuccess) e = PushLaunch<T>::parents(A, MODE_PIC, stats, c->grid_push, c->s);
     c->mark(1);
     if (e == cudaSuccess) e = PushLaunch<T>::children(A, MODE_PIC, stats, c->grid_push, c->s);
     c->mark(2);
@@ -1289,7 +1301,9 @@ template <class T> static int swarm_one(pic_ctx* c, const swarm_config* sc, doub
         A.n_hi = sc->n_hi;
         A.mask = nullptr;
         A.q_e = A.q_pos = A.q_neg = nullptr;
-        cudaError_t e = PushLaunch<T>::parents(A, MODE_SWARM, false, c->grid_push, c->s);
+        cudaError_t e = PushLaunch<T>::resample(A, grid_n(2 * sc->n_hi), c->s);
+        if (e == cudaSuccess) e = PushLaunch<T>::field_kick(A, grid_n(2 * sc->n_hi), c->s);
+        if (e == cudaSuccess) e = PushLaunch<T>::parents(A, MODE_SWARM, false, c->grid_push, c->s);
         if (e == cudaSuccess) e = PushLaunch<T>::children(A, MODE_SWARM, false, c->grid_push, c->s);
         if (e != cudaSuccess) return c->cuda_fail(e, "swarm push");
         k_end_step<<<1, 1, 0, c->s>>>(c->st(), d_cnt + (s - 1), c->cfg.capacity);

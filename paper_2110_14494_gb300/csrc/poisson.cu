@@ -6,13 +6,15 @@
 // potential (instead of a level set), the grid is uniform and cell-centred,
 // the z faces are Dirichlet plates and the x, y faces homogeneous Neumann.
 //
-// Scheme: defect correction.  The residual r = b - A phi is formed in float64
-// with the true boundary values; the error equation A e = r is solved
-// approximately by one float32 V(2,2)-cycle (red-black Gauss-Seidel,
-// 8-cell average restriction, trilinear prolongation, electrode cells and
-// coarse cells touching the electrode held at e = 0); phi += e; repeat until
-// ||r|| / ||b|| <= rtol.  A is the 7-point stencil scaled by h^2: diagonal
-// 6 - (#Neumann faces) + (#Dirichlet faces), -1 per unmasked neighbour.
+// Scheme: flexible conjugate gradients in float64 on the unmasked unknowns,
+// preconditioned by one float32 V(2,2)-cycle (red-black Gauss-Seidel, 8-cell
+// average restriction, trilinear prolongation, electrode cells and coarse
+// cells touching the electrode held at zero), until ||b - A phi|| / ||b|| <=
+// rtol.  A is the 7-point stencil scaled by h^2: diagonal 6 - (#Neumann faces)
+// + (#Dirichlet faces), -1 per unmasked neighbour; b = h^2 rho / eps0 + plate
+// and electrode terms.  The CG scalars stay on the device; the host reads the
+// residual norm once per iteration.  Kernels map one thread to one cell with a
+// (32, 4, 1) block over (x, y) and the z index in blockIdx.z.
 #include <math.h>
 
 #include "common.cuh"
@@ -22,143 +24,218 @@ namespace pic {
 
 namespace {
 
-__device__ __forceinline__ long long lin(int i, int j, int k, int nx, int ny) {
-    return ((long long)k * ny + j) * nx + i;
-}
+constexpr int BX = 32, BY = 4;
 
-__device__ __forceinline__ double block_sum(double v, double* red) {
+__device__ __forceinline__ int lin(int i, int j, int k, int nx, int ny) { return (k * ny + j) * nx + i; }
+
+// Block sum of a double into one atomicAdd (all threads of the block call).
+__device__ __forceinline__ void block_add(double v, double* dst) {
+    __shared__ double red[32];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    __syncthreads();
+    const int t = threadIdx.x + threadIdx.y * blockDim.x;
+    const int lane = t & 31, w = t >> 5, nw = (blockDim.x * blockDim.y) >> 5;
     if (lane == 0) red[w] = v;
     __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+    if (t == 0) {
+        double s = 0.0;
+        for (int q = 0; q < nw; ++q) s += red[q];
+        if (s != 0.0) atomicAdd(dst, s);
+    }
+    __syncthreads();  // red[] is reused by the next call in the same kernel
+}
+
+// Scalars of the flexible CG, in device memory.
+enum { S_B2 = 0, S_R2, S_RHO, S_GAM, S_T1, S_T2, S_ALPHA, S_BETA, S_N };
+
+// Stencil sum of the neighbours of interior cell c (x, y Neumann mirror and
+// z Dirichlet are folded into the diagonal; masked neighbours contribute 0).
+template <class V>
+__device__ __forceinline__ V nb_sum(const V* e, const uint8_t* m, int i, int j, int k, int nx, int ny, int nz, int c,
+                                    V& diag) {
+    const int pl = nx * ny;
+    V s = (V)0;
+    diag = (V)6;
+    if (i > 0) { if (!m[c - 1]) s += e[c - 1]; } else diag -= (V)1;
+    if (i < nx - 1) { if (!m[c + 1]) s += e[c + 1]; } else diag -= (V)1;
+    if (j > 0) { if (!m[c - nx]) s += e[c - nx]; } else diag -= (V)1;
+    if (j < ny - 1) { if (!m[c + nx]) s += e[c + nx]; } else diag -= (V)1;
+    if (k > 0) { if (!m[c - pl]) s += e[c - pl]; } else diag += (V)1;
+    if (k < nz - 1) { if (!m[c + pl]) s += e[c + pl]; } else diag += (V)1;
     return s;
 }
 
+#define CELL3D                                                   \
+    const int i = blockIdx.x * BX + threadIdx.x;                 \
+    const int j = blockIdx.y * BY + threadIdx.y;                 \
+    const int k = blockIdx.z;                                    \
+    const bool in = i < nx && j < ny;                            \
+    const int c = in ? lin(i, j, k, nx, ny) : 0;
+
 // b = h^2 rho / eps0 + plate terms + electrode neighbours; accumulates ||b||^2.
 __global__ void k_rhs_norm(const double* __restrict__ rho, const uint8_t* __restrict__ mask, int nx, int ny, int nz,
-                           double h2e, double v_lo, double v_hi, double v_mask, double* norm2) {
-    __shared__ double red[32];
-    const long long n = (long long)nx * ny * nz;
+                           double h2e, double v_lo, double v_hi, double v_mask, double* sc) {
+    CELL3D
     double acc = 0.0;
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        if (mask && mask[c]) continue;
-        const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
+    if (in && !mask[c]) {
+        const int pl = nx * ny;
         double s = h2e * rho[c];
         if (k == 0) s += 2.0 * v_lo;
         if (k == nz - 1) s += 2.0 * v_hi;
-        if (mask) {
-            if (i > 0 && mask[c - 1]) s += v_mask;
-            if (i < nx - 1 && mask[c + 1]) s += v_mask;
-            if (j > 0 && mask[c - nx]) s += v_mask;
-            if (j < ny - 1 && mask[c + nx]) s += v_mask;
-            if (k > 0 && mask[c - (long long)nx * ny]) s += v_mask;
-            if (k < nz - 1 && mask[c + (long long)nx * ny]) s += v_mask;
-        }
-        acc += s * s;
+        if (i > 0 && mask[c - 1]) s += v_mask;
+        if (i < nx - 1 && mask[c + 1]) s += v_mask;
+        if (j > 0 && mask[c - nx]) s += v_mask;
+        if (j < ny - 1 && mask[c + nx]) s += v_mask;
+        if (k > 0 && mask[c - pl]) s += v_mask;
+        if (k < nz - 1 && mask[c + pl]) s += v_mask;
+        acc = s * s;
     }
-    const double t = block_sum(acc, red);
-    if (threadIdx.x == 0 && t != 0.0) atomicAdd(norm2, t);
+    block_add(acc, sc + S_B2);
 }
 
-// r = b - A phi in float64 (true boundary values), written as the float32
-// right-hand side of the error equation; accumulates ||r||^2.  Electrode
-// cells are set to v_mask in phi.
+// r = b - A phi with the true boundary values (float64) and its float32 copy
+// for the preconditioner; accumulates ||r||^2; electrode cells get phi = v_mask.
 __global__ void k_resid64(double* __restrict__ phi, const double* __restrict__ rho, const uint8_t* __restrict__ mask,
                           int nx, int ny, int nz, double h2e, double v_lo, double v_hi, double v_mask,
-                          float* __restrict__ g0, double* norm2) {
-    __shared__ double red[32];
-    const long long n = (long long)nx * ny * nz, pl = (long long)nx * ny;
+                          double* __restrict__ r, float* __restrict__ g0, double* sc) {
+    CELL3D
     double acc = 0.0;
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        if (mask && mask[c]) { g0[c] = 0.0f; continue; }
-        const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / pl);
-        const double pc = phi[c];
-        // neighbour values with ghosts: Neumann mirror in x, y; Dirichlet in z
-        auto val = [&](long long q, bool inside, double ghost) -> double {
-            if (!inside) return ghost;
-            if (mask && mask[q]) return v_mask;
-            return phi[q];
-        };
-        const double sum = val(c - 1, i > 0, pc) + val(c + 1, i < nx - 1, pc) + val(c - nx, j > 0, pc) +
-                           val(c + nx, j < ny - 1, pc) + val(c - pl, k > 0, 2.0 * v_lo - pc) +
-                           val(c + pl, k < nz - 1, 2.0 * v_hi - pc);
-        const double r = h2e * rho[c] + sum - 6.0 * pc;
-        g0[c] = (float)r;
-        acc += r * r;
+    if (in) {
+        if (mask[c]) {
+            phi[c] = v_mask;
+            r[c] = 0.0;
+            g0[c] = 0.0f;
+        } else {
+            const int pl = nx * ny;
+            const double pc = phi[c];
+            auto val = [&](int q, bool inside, double ghost) -> double {
+                if (!inside) return ghost;
+                if (mask[q]) return v_mask;
+                return phi[q];
+            };
+            const double sum = val(c - 1, i > 0, pc) + val(c + 1, i < nx - 1, pc) + val(c - nx, j > 0, pc) +
+                               val(c + nx, j < ny - 1, pc) + val(c - pl, k > 0, 2.0 * v_lo - pc) +
+                               val(c + pl, k < nz - 1, 2.0 * v_hi - pc);
+            const double rr = h2e * rho[c] + sum - 6.0 * pc;
+            r[c] = rr;
+            g0[c] = (float)rr;
+            acc = rr * rr;
+        }
     }
-    const double t = block_sum(acc, red);
-    if (threadIdx.x == 0 && t != 0.0) atomicAdd(norm2, t);
+    block_add(acc, sc + S_R2);
 }
 
-__global__ void k_set_mask_phi(double* phi, const uint8_t* mask, long long n, double v_mask) {
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
-        if (mask[c]) phi[c] = v_mask;
+// q = A p (homogeneous boundary values) and p.q.
+__global__ void k_apply(const double* __restrict__ p, const uint8_t* __restrict__ mask, int nx, int ny, int nz,
+                        double* __restrict__ q, double* sc) {
+    CELL3D
+    double acc = 0.0;
+    if (in) {
+        if (mask[c]) {
+            q[c] = 0.0;
+        } else {
+            double diag;
+            const double s = nb_sum(p, mask, i, j, k, nx, ny, nz, c, diag);
+            const double v = diag * p[c] - s;
+            q[c] = v;
+            acc = p[c] * v;
+        }
+    }
+    block_add(acc, sc + S_GAM);
 }
 
-// One colour of red-black Gauss-Seidel for A e = g (homogeneous boundary
-// values: Neumann mirror in x, y; Dirichlet -e in z; masked cells e = 0).
+__global__ void k_alpha(double* sc) {
+    sc[S_ALPHA] = sc[S_RHO] / sc[S_GAM];
+    sc[S_R2] = 0.0;
+    sc[S_T1] = 0.0;
+    sc[S_T2] = 0.0;
+}
+
+// phi += alpha p; r -= alpha q; float32 copy of r; ||r||^2.
+__global__ void k_update_xr(double* __restrict__ phi, double* __restrict__ r, const double* __restrict__ p,
+                            const double* __restrict__ q, float* __restrict__ g0, int n, double* sc) {
+    const double a = sc[S_ALPHA];
+    double acc = 0.0;
+    const int c = (blockIdx.x * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
+    if (c < n) {
+        phi[c] += a * p[c];
+        const double rr = r[c] - a * q[c];
+        r[c] = rr;
+        g0[c] = (float)rr;
+        acc = rr * rr;
+    }
+    block_add(acc, sc + S_R2);
+}
+
+// t1 = z.r, t2 = z.q with z the preconditioned residual (float32).
+__global__ void k_dot2(const float* __restrict__ z, const double* __restrict__ r, const double* __restrict__ q, int n,
+                       double* sc, int with_q) {
+    const int c = (blockIdx.x * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
+    double a = 0.0, b = 0.0;
+    if (c < n) {
+        const double zz = (double)z[c];
+        a = zz * r[c];
+        if (with_q) b = zz * q[c];
+    }
+    block_add(a, sc + S_T1);
+    if (with_q) block_add(b, sc + S_T2);
+}
+
+// Flexible CG direction: beta = -alpha (z.q) / rho (equivalently
+// z.(r_new - r_old) / rho), rho <- z.r.
+__global__ void k_beta(double* sc, int first) {
+    sc[S_BETA] = first ? 0.0 : -sc[S_ALPHA] * sc[S_T2] / sc[S_RHO];
+    sc[S_RHO] = sc[S_T1];
+    sc[S_GAM] = 0.0;
+}
+
+__global__ void k_update_p(double* __restrict__ p, const float* __restrict__ z, int n, const double* sc) {
+    const double b = sc[S_BETA];
+    const int c = (blockIdx.x * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
+    if (c < n) p[c] = b != 0.0 ? (double)z[c] + b * p[c] : (double)z[c];
+}
+
+// One colour of red-black Gauss-Seidel for A e = g (masked cells stay 0).
+// Thread (ii, j, k) handles cell i = 2 ii + ((j + k + colour) & 1).
 __global__ void k_smooth(float* __restrict__ e, const float* __restrict__ g, const uint8_t* __restrict__ mask, int nx,
                          int ny, int nz, int color) {
-    const long long half = ((long long)nx * ny * nz + 1) / 2, pl = (long long)nx * ny;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < half; t += (long long)gridDim.x * blockDim.x) {
-        // t-th cell of the given colour in x-fastest order
-        const long long row = (t * 2) / nx;          // (k*ny + j) of the pair
-        const int j = (int)(row % ny), k = (int)(row / ny);
-        int i = (int)((t * 2) % nx);
-        if (((i + j + k) & 1) != color) i += 1;
-        if (i >= nx) continue;
-        const long long c = lin(i, j, k, nx, ny);
-        if (mask[c]) continue;
-        float diag = 6.0f, s = g[c];
-        if (i > 0) s += e[c - 1]; else diag -= 1.0f;
-        if (i < nx - 1) s += e[c + 1]; else diag -= 1.0f;
-        if (j > 0) s += e[c - nx]; else diag -= 1.0f;
-        if (j < ny - 1) s += e[c + nx]; else diag -= 1.0f;
-        if (k > 0) s += e[c - pl]; else diag += 1.0f;
-        if (k < nz - 1) s += e[c + pl]; else diag += 1.0f;
-        e[c] = s / diag;
-    }
+    const int j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+    const int i = 2 * (blockIdx.x * BX + threadIdx.x) + ((j + k + color) & 1);
+    if (i >= nx || j >= ny) return;
+    const int c = lin(i, j, k, nx, ny);
+    if (mask[c]) return;
+    float diag;
+    const float s = nb_sum(e, mask, i, j, k, nx, ny, nz, c, diag);
+    e[c] = (g[c] + s) / diag;
 }
 
-// Coarse right-hand side: g_c = 4 * mean of the 8 fine residuals g - A e.
+// Coarse right-hand side: g_c = 4 * mean of the 8 fine residuals g - A e
+// (h^2 scaling: the coarse cell is twice as wide).
 __global__ void k_resid_restrict(const float* __restrict__ e, const float* __restrict__ g,
                                  const uint8_t* __restrict__ mask, int nx, int ny, int nz, float* __restrict__ gc,
                                  const uint8_t* __restrict__ maskc) {
-    const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
-    const long long nc = (long long)cx * cy * cz, pl = (long long)nx * ny;
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += (long long)gridDim.x * blockDim.x) {
-        if (maskc[q]) { gc[q] = 0.0f; continue; }
-        const int I = (int)(q % cx), J = (int)((q / cx) % cy), K = (int)(q / ((long long)cx * cy));
-        float acc = 0.0f;
-        for (int d = 0; d < 8; ++d) {
-            const int i = 2 * I + (d & 1), j = 2 * J + ((d >> 1) & 1), k = 2 * K + (d >> 2);
-            const long long c = lin(i, j, k, nx, ny);
-            if (mask[c]) continue;
-            const float ec = e[c];
-            float diag = 6.0f, s = 0.0f;
-            if (i > 0) s += e[c - 1]; else diag -= 1.0f;
-            if (i < nx - 1) s += e[c + 1]; else diag -= 1.0f;
-            if (j > 0) s += e[c - nx]; else diag -= 1.0f;
-            if (j < ny - 1) s += e[c + nx]; else diag -= 1.0f;
-            if (k > 0) s += e[c - pl]; else diag += 1.0f;
-            if (k < nz - 1) s += e[c + pl]; else diag += 1.0f;
-            acc += g[c] - (diag * ec - s);
-        }
-        gc[q] = 0.5f * acc;  // 4 * acc / 8
+    const int cx = nx / 2, cy = ny / 2;
+    const int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y, K = blockIdx.z;
+    if (I >= cx || J >= cy) return;
+    const int q = lin(I, J, K, cx, cy);
+    if (maskc[q]) { gc[q] = 0.0f; return; }
+    float acc = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        const int i = 2 * I + (d & 1), j = 2 * J + ((d >> 1) & 1), k = 2 * K + (d >> 2);
+        const int c = lin(i, j, k, nx, ny);
+        if (mask[c]) continue;
+        float diag;
+        const float s = nb_sum(e, mask, i, j, k, nx, ny, nz, c, diag);
+        acc += g[c] - (diag * e[c] - s);
     }
+    gc[q] = 0.5f * acc;
 }
 
 // Coarse value with ghost rules (Neumann mirror x, y; Dirichlet -e in z).
 __device__ __forceinline__ float cval(const float* ec, int I, int J, int K, int cx, int cy, int cz) {
     float sgn = 1.0f;
-    if (I < 0) I = 0;
-    if (I >= cx) I = cx - 1;
-    if (J < 0) J = 0;
-    if (J >= cy) J = cy - 1;
+    I = I < 0 ? 0 : (I >= cx ? cx - 1 : I);
+    J = J < 0 ? 0 : (J >= cy ? cy - 1 : J);
     if (K < 0) { K = 0; sgn = -sgn; }
     if (K >= cz) { K = cz - 1; sgn = -sgn; }
     return sgn * ec[lin(I, J, K, cx, cy)];
@@ -167,77 +244,58 @@ __device__ __forceinline__ float cval(const float* ec, int I, int J, int K, int 
 // e_f += trilinear interpolation of e_c (weights 3/4, 1/4 per axis).
 __global__ void k_prolong_add(const float* __restrict__ ec, float* __restrict__ ef, const uint8_t* __restrict__ mask,
                               int nx, int ny, int nz) {
+    CELL3D
+    if (!in) return;
+    if (mask[c]) { ef[c] = 0.0f; return; }
     const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
-    const long long n = (long long)nx * ny * nz;
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        if (mask[c]) { ef[c] = 0.0f; continue; }
-        const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((long long)nx * ny));
-        const int I = i >> 1, J = j >> 1, K = k >> 1;
-        const int si = (i & 1) ? 1 : -1, sj = (j & 1) ? 1 : -1, sk = (k & 1) ? 1 : -1;
-        float acc = 0.0f;
+    const int I = i >> 1, J = j >> 1, K = k >> 1;
+    const int si = (i & 1) ? 1 : -1, sj = (j & 1) ? 1 : -1, sk = (k & 1) ? 1 : -1;
+    float acc = 0.0f;
 #pragma unroll
-        for (int a = 0; a < 2; ++a)
+    for (int a = 0; a < 2; ++a)
 #pragma unroll
-            for (int b = 0; b < 2; ++b)
+        for (int b = 0; b < 2; ++b)
 #pragma unroll
-                for (int d = 0; d < 2; ++d) {
-                    const float wgt = (a ? 0.25f : 0.75f) * (b ? 0.25f : 0.75f) * (d ? 0.25f : 0.75f);
-                    acc += wgt * cval(ec, I + (d ? si : 0), J + (b ? sj : 0), K + (a ? sk : 0), cx, cy, cz);
-                }
-        ef[c] += acc;
-    }
+            for (int d = 0; d < 2; ++d) {
+                const float wgt = (a ? 0.25f : 0.75f) * (b ? 0.25f : 0.75f) * (d ? 0.25f : 0.75f);
+                acc += wgt * cval(ec, I + (d ? si : 0), J + (b ? sj : 0), K + (a ? sk : 0), cx, cy, cz);
+            }
+    ef[c] += acc;
 }
 
 // Coarse mask: a coarse cell is held at zero if any of its 8 children is.
 __global__ void k_restrict_mask(const uint8_t* __restrict__ m, int nx, int ny, int nz, uint8_t* __restrict__ mc) {
-    const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
-    const long long nc = (long long)cx * cy * cz;
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nc; q += (long long)gridDim.x * blockDim.x) {
-        const int I = (int)(q % cx), J = (int)((q / cx) % cy), K = (int)(q / ((long long)cx * cy));
-        uint8_t v = 0;
-        for (int d = 0; d < 8; ++d) v |= m[lin(2 * I + (d & 1), 2 * J + ((d >> 1) & 1), 2 * K + (d >> 2), nx, ny)];
-        mc[q] = v ? 1 : 0;
-    }
+    const int cx = nx / 2, cy = ny / 2;
+    const int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y, K = blockIdx.z;
+    if (I >= cx || J >= cy) return;
+    uint8_t v = 0;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) v |= m[lin(2 * I + (d & 1), 2 * J + ((d >> 1) & 1), 2 * K + (d >> 2), nx, ny)];
+    mc[lin(I, J, K, cx, cy)] = v ? 1 : 0;
 }
 
-__global__ void k_copy_mask(const uint8_t* __restrict__ m, uint8_t* __restrict__ out, long long n) {
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
-        out[c] = m ? (m[c] ? 1 : 0) : 0;
+__global__ void k_copy_mask(const uint8_t* __restrict__ m, uint8_t* __restrict__ out, int n) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n) out[c] = m ? (m[c] ? 1 : 0) : 0;
 }
 
-// Coarsest level: many Gauss-Seidel sweeps inside one block.
+// Coarsest level: Gauss-Seidel sweeps inside one block.
 __global__ void k_coarse_solve(float* __restrict__ e, const float* __restrict__ g, const uint8_t* __restrict__ mask,
                                int nx, int ny, int nz, int sweeps) {
-    const long long n = (long long)nx * ny * nz, pl = (long long)nx * ny;
-    for (long long c = threadIdx.x; c < n; c += blockDim.x) e[c] = 0.0f;
+    const int n = nx * ny * nz;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) e[c] = 0.0f;
     __syncthreads();
     for (int s = 0; s < sweeps; ++s)
         for (int color = 0; color < 2; ++color) {
-            for (long long c = threadIdx.x; c < n; c += blockDim.x) {
-                const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / pl);
+            for (int c = threadIdx.x; c < n; c += blockDim.x) {
+                const int i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
                 if (((i + j + k) & 1) != color || mask[c]) continue;
-                float diag = 6.0f, sm = g[c];
-                if (i > 0) sm += e[c - 1]; else diag -= 1.0f;
-                if (i < nx - 1) sm += e[c + 1]; else diag -= 1.0f;
-                if (j > 0) sm += e[c - nx]; else diag -= 1.0f;
-                if (j < ny - 1) sm += e[c + nx]; else diag -= 1.0f;
-                if (k > 0) sm += e[c - pl]; else diag += 1.0f;
-                if (k < nz - 1) sm += e[c + pl]; else diag += 1.0f;
-                e[c] = sm / diag;
+                float diag;
+                const float sm = nb_sum(e, mask, i, j, k, nx, ny, nz, c, diag);
+                e[c] = (g[c] + sm) / diag;
             }
             __syncthreads();
         }
-}
-
-__global__ void k_zero_f(float* p, long long n) {
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
-        p[c] = 0.0f;
-}
-
-__global__ void k_update(double* __restrict__ phi, const float* __restrict__ e, const uint8_t* __restrict__ mask,
-                         long long n) {
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
-        if (!mask[c]) phi[c] += (double)e[c];
 }
 
 // E = -grad(phi) at cell centres with the stencil's ghost values; writes any
@@ -245,26 +303,23 @@ __global__ void k_update(double* __restrict__ phi, const float* __restrict__ e, 
 template <class T>
 __global__ void k_grad(const double* __restrict__ phi, int nx, int ny, int nz, double h, double v_lo, double v_hi,
                        float* Ex, float* Ey, float* Ez, T* E4) {
-    const long long n = (long long)nx * ny * nz, pl = (long long)nx * ny;
+    CELL3D
+    if (!in) return;
+    const int pl = nx * ny;
     const double inv = 1.0 / (2.0 * h);
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / pl);
-        const double pc = phi[c];
-        const double xm = i > 0 ? phi[c - 1] : pc, xp = i < nx - 1 ? phi[c + 1] : pc;
-        const double ym = j > 0 ? phi[c - nx] : pc, yp = j < ny - 1 ? phi[c + nx] : pc;
-        const double zm = k > 0 ? phi[c - pl] : 2.0 * v_lo - pc, zp = k < nz - 1 ? phi[c + pl] : 2.0 * v_hi - pc;
-        const double ex = -(xp - xm) * inv, ey = -(yp - ym) * inv, ez = -(zp - zm) * inv;
-        if (Ex) { Ex[c] = (float)ex; Ey[c] = (float)ey; Ez[c] = (float)ez; }
-        if (E4) { E4[4 * c] = (T)ex; E4[4 * c + 1] = (T)ey; E4[4 * c + 2] = (T)ez; E4[4 * c + 3] = (T)0; }
-    }
+    const double pc = phi[c];
+    const double xm = i > 0 ? phi[c - 1] : pc, xp = i < nx - 1 ? phi[c + 1] : pc;
+    const double ym = j > 0 ? phi[c - nx] : pc, yp = j < ny - 1 ? phi[c + nx] : pc;
+    const double zm = k > 0 ? phi[c - pl] : 2.0 * v_lo - pc, zp = k < nz - 1 ? phi[c + pl] : 2.0 * v_hi - pc;
+    const double ex = -(xp - xm) * inv, ey = -(yp - ym) * inv, ez = -(zp - zm) * inv;
+    if (Ex) { Ex[c] = (float)ex; Ey[c] = (float)ey; Ez[c] = (float)ez; }
+    if (E4) { E4[4 * c] = (T)ex; E4[4 * c + 1] = (T)ey; E4[4 * c + 2] = (T)ez; E4[4 * c + 3] = (T)0; }
 }
 
-int grid_for(long long n) {
-    long long b = (n + 255) / 256;
-    if (b > 152 * 16) b = 152 * 16;
-    if (b < 1) b = 1;
-    return (int)b;
-}
+dim3 grid3(int nx, int ny, int nz) { return dim3((nx + BX - 1) / BX, (ny + BY - 1) / BY, nz); }
+dim3 grid3_half(int nx, int ny, int nz) { return dim3((nx / 2 + BX - 1) / BX, (ny + BY - 1) / BY, nz); }
+dim3 grid_flat(long long n) { return dim3((unsigned)((n + BX * BY - 1) / (BX * BY))); }
+const dim3 kBlk(BX, BY, 1);
 
 }  // namespace
 
@@ -287,7 +342,9 @@ void MG::plan(int nx_, int ny_, int nz_) {
 size_t MG::bytes(int nx_, int ny_, int nz_) {
     MG m;
     m.plan(nx_, ny_, nz_);
-    size_t b = align256(64);  // norms
+    size_t b = align256(S_N * 8);
+    const size_t n0 = (size_t)nx_ * ny_ * nz_;
+    b += 3 * align256(n0 * 8);  // r, p, q in float64
     for (int l = 0; l < m.levels; ++l) {
         const size_t n = (size_t)m.lx[l] * m.ly[l] * m.lz[l];
         b += 2 * align256(n * sizeof(float)) + align256(n);
@@ -299,7 +356,11 @@ void MG::carve(void* base, int nx_, int ny_, int nz_) {
     plan(nx_, ny_, nz_);
     char* p = (char*)base;
     norms = (double*)p;
-    p += align256(64);
+    p += align256(S_N * 8);
+    const size_t n0 = (size_t)nx_ * ny_ * nz_;
+    r64 = (double*)p; p += align256(n0 * 8);
+    p64 = (double*)p; p += align256(n0 * 8);
+    q64 = (double*)p; p += align256(n0 * 8);
     for (int l = 0; l < levels; ++l) {
         const size_t n = (size_t)lx[l] * ly[l] * lz[l];
         e[l] = (float*)p; p += align256(n * sizeof(float));
@@ -311,75 +372,118 @@ void MG::carve(void* base, int nx_, int ny_, int nz_) {
 cudaError_t MG::build_masks(const uint8_t* mask, cudaStream_t s) {
     const long long n0 = (long long)lx[0] * ly[0] * lz[0];
     launches += levels;
-    k_copy_mask<<<grid_for(n0), 256, 0, s>>>(mask, m[0], n0);
+    k_copy_mask<<<(unsigned)((n0 + 255) / 256), 256, 0, s>>>(mask, m[0], (int)n0);
     for (int l = 1; l < levels; ++l)
-        k_restrict_mask<<<grid_for((long long)lx[l] * ly[l] * lz[l]), 256, 0, s>>>(m[l - 1], lx[l - 1], ly[l - 1],
-                                                                                     lz[l - 1], m[l]);
+        k_restrict_mask<<<grid3(lx[l], ly[l], lz[l]), kBlk, 0, s>>>(m[l - 1], lx[l - 1], ly[l - 1], lz[l - 1], m[l]);
     return cudaGetLastError();
 }
 
+// One V(pre, post)-cycle on A e0 = g0; e0 is overwritten.
 void MG::vcycle(cudaStream_t s) {
     launches += (long long)(levels - 1) * (2 + 2 * pre + 2 * post + 1) + 1;
     for (int l = 0; l < levels - 1; ++l) {
         const long long n = (long long)lx[l] * ly[l] * lz[l];
-        const int gh = grid_for((n + 1) / 2);
-        k_zero_f<<<grid_for(n), 256, 0, s>>>(e[l], n);
+        cudaMemsetAsync(e[l], 0, n * sizeof(float), s);
         for (int it = 0; it < pre; ++it) {
-            k_smooth<<<gh, 256, 0, s>>>(e[l], g[l], m[l], lx[l], ly[l], lz[l], 0);
-            k_smooth<<<gh, 256, 0, s>>>(e[l], g[l], m[l], lx[l], ly[l], lz[l], 1);
+            k_smooth<<<grid3_half(lx[l], ly[l], lz[l]), kBlk, 0, s>>>(e[l], g[l], m[l], lx[l], ly[l], lz[l], 0);
+            k_smooth<<<grid3_half(lx[l], ly[l], lz[l]), kBlk, 0, s>>>(e[l], g[l], m[l], lx[l], ly[l], lz[l], 1);
         }
-        k_resid_restrict<<<grid_for(n / 8), 256, 0, s>>>(e[l], g[l], m[l], lx[l], ly[l], lz[l], g[l + 1], m[l + 1]);
+        k_resid_restrict<<<grid3(lx[l + 1], ly[l + 1], lz[l + 1]), kBlk, 0, s>>>(e[l], g[l], m[l], lx[l], ly[l],
+                                                                                 lz[l], g[l + 1], m[l + 1]);
     }
     const int L = levels - 1;
     k_coarse_solve<<<1, 256, 0, s>>>(e[L], g[L], m[L], lx[L], ly[L], lz[L], coarse_sweeps);
     for (int l = levels - 2; l >= 0; --l) {
-        const long long n = (long long)lx[l] * ly[l] * lz[l];
-        const int gh = grid_for((n + 1) / 2);
-        k_prolong_add<<<grid_for(n), 256, 0, s>>>(e[l + 1], e[l], m[l], lx[l], ly[l], lz[l]);
+        k_prolong_add<<<grid3(lx[l], ly[l], lz[l]), kBlk, 0, s>>>(e[l + 1], e[l], m[l], lx[l], ly[l], lz[l]);
         for (int it = 0; it < post; ++it) {
-            k_smooth<<<gh, 256, 0, s>>>(e[l], g[l], m[l], lx[l], ly[l], lz[l], 1);
-            k_smooth<<<gh, 256, 0, s>>>(e[l], g[l], m[l], lx[l], ly[l], lz[l], 0);
+            k_smooth<<<grid3_half(lx[l], ly[l], lz[l]), kBlk, 0, s>>>(e[l], g[l], m[l], lx[l], ly[l], lz[l], 1);
+            k_smooth<<<grid3_half(lx[l], ly[l], lz[l]), kBlk, 0, s>>>(e[l], g[l], m[l], lx[l], ly[l], lz[l], 0);
         }
     }
+}
+
+// One flexible-CG iteration: z = M r, direction, q = A p, alpha, updates.
+void MG::iteration(cudaStream_t s, double* phi, const uint8_t* mk, bool first) {
+    const int nx = lx[0], ny = ly[0], nz = lz[0];
+    const int n = nx * ny * nz;
+    vcycle(s);
+    k_dot2<<<grid_flat(n), kBlk, 0, s>>>(e[0], r64, q64, n, norms, first ? 0 : 1);
+    k_beta<<<1, 1, 0, s>>>(norms, first ? 1 : 0);
+    k_update_p<<<grid_flat(n), kBlk, 0, s>>>(p64, e[0], n, norms);
+    k_apply<<<grid3(nx, ny, nz), kBlk, 0, s>>>(p64, mk, nx, ny, nz, q64, norms);
+    k_alpha<<<1, 1, 0, s>>>(norms);
+    k_update_xr<<<grid_flat(n), kBlk, 0, s>>>(phi, r64, p64, q64, g[0], n, norms);
+    launches += 6;
+}
+
+void MG::release() {
+    for (int q = 0; q < 2; ++q)
+        if (g_iter[q]) { cudaGraphExecDestroy(g_iter[q]); g_iter[q] = nullptr; }
+    if (cap_stream) { cudaStreamDestroy(cap_stream); cap_stream = nullptr; }
 }
 
 int MG::solve(const double* rho, const uint8_t* mask, double* phi, double h, double v_lo, double v_hi, double v_mask,
               double rtol, int max_cycles, int packed_prec, void* E4, float* Ex, float* Ey, float* Ez,
               cudaStream_t s, int* cycles_out, double* rel_out, double* host_norms) {
     const int nx = lx[0], ny = ly[0], nz = lz[0];
-    const long long n = (long long)nx * ny * nz;
+    const int n = nx * ny * nz;
     const double h2e = h * h / kEps0;
-    if (build_masks(mask, s) != cudaSuccess) return PIC_ERR_CUDA;
-    if (mask) { k_set_mask_phi<<<grid_for(n), 256, 0, s>>>(phi, mask, n, v_mask); ++launches; }
-    ++launches;
-    cudaMemsetAsync(norms, 0, 16, s);
-    k_rhs_norm<<<grid_for(n), 256, 0, s>>>(rho, mask, nx, ny, nz, h2e, v_lo, v_hi, v_mask, norms);
-    double bn2 = 0.0, rn2 = 0.0;
+    if (!persistent || !masks_ready) {
+        if (build_masks(mask, s) != cudaSuccess) return PIC_ERR_CUDA;
+        masks_ready = true;
+    }
+    const uint8_t* mk = m[0];
+    // graphs are tied to the pointers they were captured with
+    if (persistent && (g_key[0] != phi || g_key[1] != rho || g_key[2] != mask)) {
+        for (int q = 0; q < 2; ++q)
+            if (g_iter[q]) { cudaGraphExecDestroy(g_iter[q]); g_iter[q] = nullptr; }
+        g_key[0] = phi; g_key[1] = rho; g_key[2] = mask;
+    }
+    cudaMemsetAsync(norms, 0, S_N * 8, s);
+    k_rhs_norm<<<grid3(nx, ny, nz), kBlk, 0, s>>>(rho, mk, nx, ny, nz, h2e, v_lo, v_hi, v_mask, norms);
+    k_resid64<<<grid3(nx, ny, nz), kBlk, 0, s>>>(phi, rho, mk, nx, ny, nz, h2e, v_lo, v_hi, v_mask, r64, g[0], norms);
+    launches += 2;
     int cyc = 0, rc = PIC_OK;
+    double bn = 1.0, rn = 0.0;
     for (;;) {
-        cudaMemsetAsync(norms + 1, 0, 8, s);
-        k_resid64<<<grid_for(n), 256, 0, s>>>(phi, rho, mask, nx, ny, nz, h2e, v_lo, v_hi, v_mask, g[0], norms + 1);
-        ++launches;
-        if (cudaMemcpyAsync(host_norms, norms, 16, cudaMemcpyDeviceToHost, s) != cudaSuccess) return PIC_ERR_CUDA;
+        if (cudaMemcpyAsync(host_norms, norms, 2 * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return PIC_ERR_CUDA;
         if (cudaStreamSynchronize(s) != cudaSuccess) return PIC_ERR_CUDA;
-        bn2 = host_norms[0];
-        rn2 = host_norms[1];
-        const double bn = bn2 > 0.0 ? sqrt(bn2) : 1.0;
-        if (sqrt(rn2) / bn <= rtol) break;
+        bn = host_norms[S_B2] > 0.0 ? sqrt(host_norms[S_B2]) : 1.0;
+        rn = sqrt(host_norms[S_R2]);
+        if (rn / bn <= rtol) break;
         if (cyc >= max_cycles) { rc = PIC_ERR_TIMEOUT; break; }
-        vcycle(s);
-        k_update<<<grid_for(n), 256, 0, s>>>(phi, e[0], m[0], n);
-        ++launches;
+        // z = M r (float32 V-cycle on g0), then the CG direction
+        const int gi = cyc == 0 ? 0 : 1;
+        if (persistent) {
+            if (!g_iter[gi]) {
+                if (!cap_stream && cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+                    return PIC_ERR_CUDA;
+                cudaGraph_t gr = nullptr;
+                const long long l0 = launches;
+                if (cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                    return PIC_ERR_CUDA;
+                iteration(cap_stream, phi, mk, cyc == 0);
+                if (cudaStreamEndCapture(cap_stream, &gr) != cudaSuccess) return PIC_ERR_CUDA;
+                if (cudaGraphInstantiate(&g_iter[gi], gr, 0) != cudaSuccess) { cudaGraphDestroy(gr); return PIC_ERR_CUDA; }
+                cudaGraphDestroy(gr);
+                graph_kernels[gi] = launches - l0;
+                launches = l0;
+            }
+            if (cudaGraphLaunch(g_iter[gi], s) != cudaSuccess) return PIC_ERR_CUDA;
+            launches += graph_kernels[gi];
+        } else {
+            iteration(s, phi, mk, cyc == 0);
+        }
         ++cyc;
     }
     if (cycles_out) *cycles_out = cyc;
-    if (rel_out) *rel_out = sqrt(rn2) / (bn2 > 0.0 ? sqrt(bn2) : 1.0);
+    if (rel_out) *rel_out = rn / bn;
     if (Ex || E4) {
         ++launches;
         if (packed_prec == 64)
-            k_grad<double><<<grid_for(n), 256, 0, s>>>(phi, nx, ny, nz, h, v_lo, v_hi, Ex, Ey, Ez, (double*)E4);
+            k_grad<double><<<grid3(nx, ny, nz), kBlk, 0, s>>>(phi, nx, ny, nz, h, v_lo, v_hi, Ex, Ey, Ez, (double*)E4);
         else
-            k_grad<float><<<grid_for(n), 256, 0, s>>>(phi, nx, ny, nz, h, v_lo, v_hi, Ex, Ey, Ez, (float*)E4);
+            k_grad<float><<<grid3(nx, ny, nz), kBlk, 0, s>>>(phi, nx, ny, nz, h, v_lo, v_hi, Ex, Ey, Ez, (float*)E4);
     }
     if (cudaGetLastError() != cudaSuccess) return PIC_ERR_CUDA;
     return rc;
@@ -392,6 +496,7 @@ using pic::MG;
 
 extern "C" size_t poisson_workspace_bytes(const poisson_config* pc) {
     if (!pc || pc->nx < 2 || pc->ny < 2 || pc->nz < 2) return 0;
+    if ((long long)pc->nx * pc->ny * pc->nz > 0x7fffffffLL || pc->nz > 65535) return 0;
     return MG::bytes(pc->nx, pc->ny, pc->nz);
 }
 
@@ -401,6 +506,7 @@ extern "C" int poisson_solve(const poisson_config* pc, const double* rho, const 
     if (!pc || !rho || !phi || !ws || pc->nx < 2 || pc->ny < 2 || pc->nz < 2 || !(pc->dx > 0) || !(rtol > 0) ||
         max_cycles < 0)
         return PIC_ERR_ARG;
+    if ((long long)pc->nx * pc->ny * pc->nz > 0x7fffffffLL || pc->nz > 65535) return PIC_ERR_ARG;
     if (ws_bytes < MG::bytes(pc->nx, pc->ny, pc->nz) || ((uintptr_t)ws & 255)) return PIC_ERR_ARG;
     if ((Ex == nullptr) != (Ey == nullptr) || (Ex == nullptr) != (Ez == nullptr)) return PIC_ERR_ARG;
     MG mg;

@@ -12,9 +12,22 @@ struct MG {
     float* e[kMaxLevels];
     float* g[kMaxLevels];
     uint8_t* m[kMaxLevels];
-    double* norms = nullptr;  // [0] ||b||^2, [1] ||r||^2
+    double* norms = nullptr;  // CG scalars: ||b||^2, ||r||^2, rho, gamma, z.r, z.q, alpha, beta
+    double *r64 = nullptr, *p64 = nullptr, *q64 = nullptr;  // CG vectors (float64)
     int pre = 2, post = 2, coarse_sweeps = 50;
     long long launches = 0;  // kernels launched so far
+    // Reusable state for a solver owned by a long-lived caller (a PIC context):
+    // the coarse masks are built once, and each CG iteration (V-cycle plus
+    // vector updates) is replayed from a CUDA graph captured on a private
+    // stream.  Stateless callers leave `persistent` false.
+    bool persistent = false;
+    bool masks_ready = false;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t g_iter[2] = {nullptr, nullptr};  // [0] first iteration, [1] later ones
+    const void* g_key[3] = {nullptr, nullptr, nullptr};
+    long long graph_kernels[2] = {0, 0};
+    void release();
+    void iteration(cudaStream_t s, double* phi, const uint8_t* mk, bool first);
 
     void plan(int nx, int ny, int nz);
     static size_t bytes(int nx, int ny, int nz);

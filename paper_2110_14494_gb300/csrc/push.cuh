@@ -13,6 +13,8 @@
 // with their remaining time and finished by k_children in the same step.
 // Instantiated for T = float and T = double in separate translation units.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace pic {
@@ -29,7 +31,7 @@ template <class T> struct PushArgs {
     int kind[8];
     T thr[8];                  // eV
     T mratio[8];               // m_e / M (0 = infinite mass)
-    double l0, inv_dl;         // ln(eps_0), (n_bins-1) / (ln eps_last - ln eps_0)
+    T l0, inv_dl;              // ln(eps_0), (n_bins-1) / (ln eps_last - ln eps_0), in T
     T eps_lo, eps_hi;          // eV
     T nu_max;
     T dt;
@@ -48,6 +50,15 @@ template <class T> struct PushArgs {
     // swarm mode
     double* mom;               // [kNMom] accumulators of this step
     long long n_lo, n_hi;
+};
+
+// Per-process constants, staged in shared memory after the rate table so the
+// process index can address them without a local-memory copy of the
+// kernel parameters.
+template <class T> struct ProcSmem {
+    T thr[8];
+    T mratio[8];
+    int kind[8];
 };
 
 // ------------------------------------------------------------------ arithmetic
@@ -270,7 +281,7 @@ __device__ __forceinline__ void table_pos(const PushArgs<T>& A, T e, int& j, T& 
         j = A.n_bins - 2; f = (T)1;
         if (e > A.eps_hi) ++ls.clamped;
     } else {
-        T t = (Arith<T>::lg(e) - (T)A.l0) * (T)A.inv_dl;
+        T t = (Arith<T>::lg(e) - A.l0) * A.inv_dl;
         int jj = (int)floor(t);
         if (jj > A.n_bins - 2) jj = A.n_bins - 2;
         if (jj < 0) jj = 0;
@@ -290,110 +301,108 @@ __device__ __forceinline__ int select_process(const PushArgs<T>& A, const T* tab
     const T* r1 = r0 + kTableStride;
     const T target = u1 * A.nu_max;
     if (FAST) {
-        const T tot = r0[7] + f * (r1[7] - r0[7]);
+        const T t0 = __ldg(r0 + 7), t1 = __ldg(r1 + 7);
+        const T tot = t0 + f * (t1 - t0);
         if (target >= tot) return -1;
     }
     T cum = (T)0;
     for (int k = 0; k < A.n_proc; ++k) {
-        cum += r0[k] + f * (r1[k] - r0[k]);
+        const T a = __ldg(r0 + k), b = __ldg(r1 + k);
+        cum += a + f * (b - a);
         if (target < cum) return k;
     }
     return -1;
 }
 
 // ------------------------------------------------------------------ flight
-// Child sink policies: append to the global queue (parents) or to a small
-// per-thread stack (children finishing their step).
+// The product of an ionization by draw k of electron `pid`: id from the
+// derived-id stream, isotropic direction from its own draw k = 0, speed sp.
+template <class T>
+__device__ __forceinline__ uint64_t make_child(const PushArgs<T>& A, uint64_t pid, uint32_t k, T sp, T vc[3]) {
+    const uint64_t cid = derived_id(A.K, pid, A.step, 0x80000000u | k);
+    const u32x4 rb = draw_words(A.K, cid, A.step, 0u);
+    T nb[3];
+    iso_dir(unif<T>(rb.z), unif<T>(rb.w), nb);
+    vc[0] = sp * nb[0]; vc[1] = sp * nb[1]; vc[2] = sp * nb[2];
+    return cid;
+}
+
+// Products of products (rare) are built at once and wait on the lane's stack.
 template <class T> struct StackSink {
     static constexpr int kDepth = 8;
     T x[kDepth][3], v[kDepth][3], w[kDepth], t[kDepth];
     uint64_t id[kDepth];
     int n = 0;
-    __device__ bool push(const PushArgs<T>& A, const T xx[3], const T vv[3], const T a[3], T ww, uint64_t cid, T tl) {
-        (void)A; (void)a;
-        if (n >= kDepth) return false;
-        for (int d = 0; d < 3; ++d) { x[n][d] = xx[d]; v[n][d] = vv[d]; }
-        w[n] = ww; id[n] = cid; t[n] = tl;
-        ++n;
-        return true;
-    }
-};
-template <class T> struct QueueSink {
-    __device__ bool push(const PushArgs<T>& A, const T xx[3], const T vv[3], const T a[3], T ww, uint64_t cid, T tl) {
-        unsigned long long s = atomicAdd(&A.st->n_child, 1ull);
-        if ((long long)s >= A.cap_child) return false;
-        const Soa<T>& q = A.cq.p;
-        q.r[PX][s] = xx[0]; q.r[PY][s] = xx[1]; q.r[PZ][s] = xx[2];
-        q.r[VX][s] = vv[0]; q.r[VY][s] = vv[1]; q.r[VZ][s] = vv[2];
-        q.r[AX][s] = a[0]; q.r[AY][s] = a[1]; q.r[AZ][s] = a[2];
-        q.r[PW][s] = ww; q.id[s] = cid; A.cq.t_left[s] = tl;
-        return true;
-    }
 };
 
-// Advances one electron over t_left; returns false if it attached.  The
-// displacement within the step is accumulated separately from the position
-// (x = x_start + displacement), so single precision keeps the resolution of
-// the small flights instead of rounding to the absolute coordinate each time.
-template <class T, int MODE, bool FAST, class Sink>
-__device__ bool advance(const PushArgs<T>& A, const T* tab, T x[3], T v[3], const T a[3], T w, uint64_t id, T t_left,
-                        LStats& ls, Sink& sink) {
-    T dsp[3] = {(T)0, (T)0, (T)0};
-    bool alive = true;
-    for (uint32_t k = 1;; ++k) {
-        const u32x4 r = draw_words(A.K, id, A.step, k);
-        const T tau = Arith<T>::tau(unif<T>(r.x), A.nu_max);
-        if (tau >= t_left) { fly(dsp, v, a, t_left); break; }
-        fly(dsp, v, a, tau);
-        t_left -= tau;
-        ++ls.events;
-        const T v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-        const T e = Arith<T>::energy(v2);
-        const int p = select_process<T, FAST>(A, tab, e, unif<T>(r.y), ls);
-        if (p < 0) { ++ls.nulls; continue; }
-        ++ls.coll[p & 7];
-        T n[3];
-        iso_dir(unif<T>(r.z), unif<T>(r.w), n);
-        const int kind = A.kind[p];
-        if (kind == PIC_PROC_ELASTIC) {
-            const T sp = sqrt(v2);
-            T cchi = (T)0;
-            if (sp > (T)0) cchi = (v[0] * n[0] + v[1] * n[1] + v[2] * n[2]) / sp;
-            const T e2 = e * ((T)1 - (T)2 * A.mratio[p] * ((T)1 - cchi));
-            const T sp2 = Arith<T>::speed(dmax(e2, (T)0));
-            v[0] = sp2 * n[0]; v[1] = sp2 * n[1]; v[2] = sp2 * n[2];
-        } else if (kind == PIC_PROC_EXCITATION) {
-            const T sp2 = Arith<T>::speed(dmax(e - A.thr[p], (T)0));
-            v[0] = sp2 * n[0]; v[1] = sp2 * n[1]; v[2] = sp2 * n[2];
-        } else if (kind == PIC_PROC_IONIZATION) {
-            const T er = dmax(e - A.thr[p], (T)0);
-            const T sp2 = Arith<T>::speed((T)0.5 * er);
-            v[0] = sp2 * n[0]; v[1] = sp2 * n[1]; v[2] = sp2 * n[2];
-            const uint64_t cid = derived_id(A.K, id, A.step, 0x80000000u | k);
-            const u32x4 rb = draw_words(A.K, cid, A.step, 0u);
-            T nb[3];
-            iso_dir(unif<T>(rb.z), unif<T>(rb.w), nb);
-            const T vc[3] = {sp2 * nb[0], sp2 * nb[1], sp2 * nb[2]};
-            const T xc[3] = {x[0] + dsp[0], x[1] + dsp[1], x[2] + dsp[2]};
-            if (!sink.push(A, xc, vc, a, w, cid, t_left)) atomicOr(&A.st->err, kErrChildCapacity | kErrStack);
-            else ++ls.children;
-            ls.w_ion += (double)w;
-            if (MODE == MODE_PIC && A.q_pos)
-                deposit(xc[0], xc[1], xc[2], w, A.ox, A.oy, A.oz, A.dxr, A.nx, A.ny, A.nz, A.q_pos, A.st);
-        } else {  // attachment
-            ls.w_att += (double)w;
-            ++ls.attached;
-            if (MODE == MODE_PIC && A.q_neg)
-                deposit(x[0] + dsp[0], x[1] + dsp[1], x[2] + dsp[2], w, A.ox, A.oy, A.oz, A.dxr, A.nx, A.ny, A.nz,
-                        A.q_neg, A.st);
-            alive = false;
-            break;
-        }
+// One electron in flight on a lane: start position x, displacement d within
+// the step (x + d is the position; single precision keeps the resolution of
+// the short flights that way), velocity, acceleration, weight, remaining time
+// and the index k of its next draw.
+template <class T> struct Lane {
+    T x[3], d[3], v[3], a[3];
+    T w, t_left;
+    uint64_t id;
+    uint32_t k;
+};
+
+enum { EV_CONTINUE = 0, EV_DONE = 1, EV_ATTACHED = 2, EV_IONIZED = 3 };
+
+// One candidate collision of the null-collision method (Sec. 2.1.1): flight
+// time tau = -ln(u0) / nu_max; if it ends the step, fly to the end; else fly
+// tau, pick the process with u1 nu_max against the cumulative rates at the
+// electron's energy (none = null collision) and scatter isotropically with
+// u2, u3.  Ionization returns EV_IONIZED with the product's speed in sp (the
+// caller stages the product, which flies the remaining time); attachment
+// records a negative-ion event and ends the electron.
+template <class T, int MODE, bool FAST, bool STATS>
+__device__ __forceinline__ int event(const PushArgs<T>& A, const T* tab, const ProcSmem<T>* ps, Lane<T>& L,
+                                     LStats& ls, T& sp) {
+    const u32x4 r = draw_words(A.K, L.id, A.step, L.k);
+    ++L.k;
+    const T tau = Arith<T>::tau(unif<T>(r.x), A.nu_max);
+    if (tau >= L.t_left) { fly(L.d, L.v, L.a, L.t_left); return EV_DONE; }
+    fly(L.d, L.v, L.a, tau);
+    L.t_left -= tau;
+    ++ls.events;
+    T* v = L.v;
+    const T v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    const T e = Arith<T>::energy(v2);
+    const int p = select_process<T, FAST>(A, A.table, e, unif<T>(r.y), ls);
+    if (p < 0) { ++ls.nulls; return EV_CONTINUE; }
+    if (STATS) ++ls.coll[p & 7];
+    const int kind = ps->kind[p];
+    if (kind == PIC_PROC_ATTACHMENT) {
+        ls.w_att += (double)L.w;
+        ++ls.attached;
+        if (MODE == MODE_PIC && A.q_neg)
+            deposit(L.x[0] + L.d[0], L.x[1] + L.d[1], L.x[2] + L.d[2], L.w, A.ox, A.oy, A.oz, A.dxr, A.nx, A.ny,
+                    A.nz, A.q_neg, A.st);
+        return EV_ATTACHED;
     }
-    x[0] += dsp[0];
-    x[1] += dsp[1];
-    x[2] += dsp[2];
-    return alive;
+    T n[3];
+    iso_dir(unif<T>(r.z), unif<T>(r.w), n);
+    // energy after the collision: elastic recoil with cos(chi) = n_old . n_new,
+    // excitation loss, or half of what ionization leaves
+    T e2;
+    if (kind == PIC_PROC_ELASTIC) {
+        const T sp = sqrt(v2);
+        T cchi = (T)0;
+        if (sp > (T)0) cchi = (v[0] * n[0] + v[1] * n[1] + v[2] * n[2]) / sp;
+        e2 = dmax(e * ((T)1 - (T)2 * ps->mratio[p] * ((T)1 - cchi)), (T)0);
+    } else if (kind == PIC_PROC_EXCITATION) {
+        e2 = dmax(e - ps->thr[p], (T)0);
+    } else {
+        e2 = (T)0.5 * dmax(e - ps->thr[p], (T)0);
+    }
+    const T sp2 = Arith<T>::speed(e2);
+    v[0] = sp2 * n[0]; v[1] = sp2 * n[1]; v[2] = sp2 * n[2];
+    if (kind == PIC_PROC_IONIZATION) {
+        sp = sp2;
+        ls.w_ion += (double)L.w;
+        return EV_IONIZED;
+    }
+    return EV_CONTINUE;
 }
 
 // Domain faces (specular reflection or absorption) and electrode cells.
@@ -434,151 +443,384 @@ __device__ __forceinline__ void store(const Soa<T>& o, unsigned long long s, con
     o.r[PW][s] = w; o.id[s] = id;
 }
 
-template <class T> __device__ __forceinline__ void load_table(const PushArgs<T>& A, T* tab) {
-    const int n = A.n_bins * kTableStride;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) tab[i] = A.table[i];
-    __syncthreads();
-}
-
-// Survivor bookkeeping common to parents and children.
-template <class T, int MODE>
-__device__ __forceinline__ void emit(const PushArgs<T>& A, unsigned long long slot, const T x[3], const T v[3],
-                                     const T a[3], T w, uint64_t id, MomAcc<T>& M) {
-    if ((long long)slot >= A.cap_out) { atomicOr(&A.st->err, kErrOutCapacity); return; }
-    store(A.out, slot, x, v, a, w, id);
-    if (MODE == MODE_PIC) {
-        if (A.q_e) deposit(x[0], x[1], x[2], w, A.ox, A.oy, A.oz, A.dxr, A.nx, A.ny, A.nz, A.q_e, A.st);
-    } else {
-        M.add(x, v, w);
-    }
-}
-
-// ------------------------------------------------------------------ parents
-template <class T, int MODE, bool FAST, bool STATS>
-__global__ void __launch_bounds__(256) k_push(const PushArgs<T> A) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* tab = reinterpret_cast<T*>(smem_raw);
-    load_table(A, tab);
-    const unsigned long long n = A.st->n_in;
-    int res = RES_NONE;
-    if (MODE == MODE_SWARM) {
-        if ((long long)n > A.n_hi) res = RES_THIN;
-        else if (n > 0 && (long long)n < A.n_lo) res = RES_DUP;
-    }
-    const int lane = threadIdx.x & 31;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
+// ------------------------------------------------------------------ field kick
+// Sec. 2.1.1, Eq. 2: a_new = -(e/m_e) E(x) from the trilinear gather; the
+// half-kick v += dt/2 (a_new - a_old) completes the previous step's velocity
+// update (skipped when a_old is unknown); a_old <- a_new.  A streaming pass in
+// place over the input buffer, so the collision kernel starts electrons
+// without a dependent gather.
+template <class T>
+__global__ void __launch_bounds__(256) k_field_kick(const PushArgs<T> A) {
+    const long long n = (long long)A.st->n_in;
     const T qm = (T)(kQ / kMe);
-    LStats ls;
-    ls.zero();
-    MomAcc<T> M;
-    if (MODE == MODE_SWARM) M.zero();
-    QueueSink<T> sink;
-    for (long long base = warp * 32; base < (long long)n; base += nwarp * 32) {
-        const long long i = base + lane;
-        const bool valid = i < (long long)n;
-        T x0[3], v0[3], a0[3], w0 = (T)0;
-        uint64_t id0 = 0;
-        if (valid) {
-            x0[0] = A.in.r[PX][i]; x0[1] = A.in.r[PY][i]; x0[2] = A.in.r[PZ][i];
-            v0[0] = A.in.r[VX][i]; v0[1] = A.in.r[VY][i]; v0[2] = A.in.r[VZ][i];
-            a0[0] = A.in.r[AX][i]; a0[1] = A.in.r[AY][i]; a0[2] = A.in.r[AZ][i];
-            w0 = A.in.r[PW][i];
-            id0 = A.in.id[i];
-        }
-        const int reps = (res == RES_DUP) ? 2 : 1;
-        for (int rep = 0; rep < reps; ++rep) {
-            bool alive = valid && w0 > (T)0;
-            T x[3] = {x0[0], x0[1], x0[2]}, v[3] = {v0[0], v0[1], v0[2]}, a[3] = {a0[0], a0[1], a0[2]};
-            T w = w0;
-            uint64_t id = id0;
-            if (alive && res == RES_DUP) {
-                w = (T)0.5 * w0;
-                if (rep == 1) id = derived_id(A.K, id0, A.step, 0xA0000000u);
-            }
-            if (alive && res == RES_THIN) {
-                const u32x4 r = draw_words(A.K, id0, A.step, 0xA0000000u);
-                if (unif<T>(r.x) < (T)0.5) w = (T)2 * w0;
-                else alive = false;
-            }
-            if (alive) {
-                ++ls.processed;
-                T E[3];
-                gather(A, x, E);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const T x[3] = {A.in.r[PX][i], A.in.r[PY][i], A.in.r[PZ][i]};
+        T E[3];
+        gather(A, x, E);
 #pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    const T an = -qm * E[d];
-                    if (!A.first) v[d] = v[d] + (T)0.5 * A.dt * (an - a[d]);
-                    a[d] = an;
-                }
-                alive = advance<T, MODE, FAST>(A, tab, x, v, a, w, id, A.dt, ls, sink);
-                if (alive && MODE == MODE_PIC) alive = boundaries(A, x, v, w, ls);
-            }
-            const unsigned m = __ballot_sync(kFull, alive);
-            if (m == 0) continue;
-            unsigned long long slot0 = 0;
-            const int leader = __ffs(m) - 1;
-            if (lane == leader) slot0 = atomicAdd(&A.st->n_out, (unsigned long long)__popc(m));
-            slot0 = __shfl_sync(kFull, slot0, leader);
-            if (alive) emit<T, MODE>(A, slot0 + __popc(m & lt_mask), x, v, a, w, id, M);
+        for (int d = 0; d < 3; ++d) {
+            const T an = -qm * E[d];
+            if (!A.first) A.in.r[VX + d][i] = A.in.r[VX + d][i] + (T)0.5 * A.dt * (an - A.in.r[AX + d][i]);
+            A.in.r[AX + d][i] = an;
         }
-    }
-    if (STATS) flush_stats(A, ls, A.n_proc);
-    if (MODE == MODE_SWARM) {
-        M.m[14] += ls.w_ion;
-        M.m[15] += ls.w_att;
-        __syncthreads();
-        flush_moments(A, M, reinterpret_cast<double*>(smem_raw));
     }
 }
 
-// ------------------------------------------------------------------ children
-template <class T, int MODE, bool FAST, bool STATS>
-__global__ void __launch_bounds__(256) k_children(const PushArgs<T> A) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* tab = reinterpret_cast<T*>(smem_raw);
-    load_table(A, tab);
-    unsigned long long n = A.st->n_child;
-    if ((long long)n > A.cap_child) n = (unsigned long long)A.cap_child;
+// Swarm resampling in place (decided from the count after the previous step):
+// above n_hi each electron survives with probability 1/2 (draw keyed by id,
+// step and 0xA0000000) and doubles its weight, the others get weight 0;
+// below n_lo every electron is halved and a copy with a derived id is
+// appended after the last one.
+template <class T>
+__global__ void k_resample(const PushArgs<T> A) {
+    const long long n = (long long)A.st->n_in;
+    const bool thin = n > A.n_hi, dup = n > 0 && n < A.n_lo;
+    if (!thin && !dup) return;
+    if (dup && 2 * n > A.cap_out) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&A.st->err, kErrOutCapacity);
+        return;
+    }
+    const Soa<T>& p = A.in;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const T w = p.r[PW][i];
+        if (thin) {
+            const u32x4 r = draw_words(A.K, p.id[i], A.step, 0xA0000000u);
+            p.r[PW][i] = unif<T>(r.x) < (T)0.5 ? (T)2 * w : (T)0;
+        } else {
+            const long long j = n + i;
+            for (int f = 0; f < 10; ++f) p.r[f][j] = p.r[f][i];
+            p.r[PW][i] = (T)0.5 * w;
+            p.r[PW][j] = (T)0.5 * w;
+            p.id[j] = derived_id(A.K, p.id[i], A.step, 0xA0000000u);
+        }
+    }
+    if (dup && blockIdx.x == 0 && threadIdx.x == 0) A.st->n_extra = (unsigned long long)(2 * n);
+}
+
+static __global__ void k_resample_commit(DevState* st) {
+    if (st->n_extra) {
+        st->n_in = st->n_extra;
+        st->n_extra = 0;
+    }
+}
+
+// ------------------------------------------------------------------ collisions
+// Lanes refill from per-warp shared-memory stages.  Every lane owns one
+// electron at a time and advances it one candidate collision per loop
+// iteration; a lane whose electron has finished the step takes the next
+// electron from the warp's input stage at once, so the warp stays converged
+// while electrons need different numbers of events.  All per-electron memory
+// work is done by the whole warp, 32 electrons at a time: the input stage is
+// filled with one coalesced load of 32 consecutive work items, finished
+// electrons wait in the output stage until 32 are there and are then
+// reflected at the faces, tested against the electrode, appended with one
+// cursor increment, stored and deposited by 32 lanes together, and
+// ionization products are staged and queued the same way.
+//
+// CHILD = false: work item = one electron of the input buffer (already kicked
+// by k_field_kick), flying dt.  CHILD = true: work item = one queued
+// ionization product; staging it builds the product (derived id, direction
+// from its own draw) and records the positive-ion event of its birth; it
+// flies its remaining time with the parent's acceleration.  Products of
+// products are built at once and finished from the lane's stack.
+constexpr int kRow = 11;    // padded row of a stage entry: x y z vx vy vz ax ay az w t
+constexpr int kOut = 64;    // output stage capacity (flushed at 32)
+constexpr int kCh = 64;     // product stage capacity (flushed at 32)
+
+template <class T> struct Stage {
+    T in[32 * kRow];
+    T out[kOut * kRow];
+    T ch[kCh * kRow];       // x y z sp ax ay az w t
+    uint64_t in_id[32], out_id[kOut], ch_id[kCh];
+    uint32_t ch_k[kCh];
+};
+
+template <class T> constexpr size_t collide_smem() {
+    return ((sizeof(ProcSmem<T>) + 15) & ~(size_t)15) + 4 * sizeof(Stage<T>);
+}
+
+// Writes staged finished electrons [0, cnt) (lane l takes entry l): faces,
+// electrode, output append, deposit or moments; then moves entries cnt..n-1 down.
+template <class T, int MODE>
+__device__ __forceinline__ void flush_out(const PushArgs<T>& A, Stage<T>* sg, int& n, int cnt, LStats& ls,
+                                          MomAcc<T>& M) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    bool live = lane < cnt;
+    T x[3], v[3], a[3], w = (T)0;
+    uint64_t id = 0;
+    if (live) {
+        const T* r = sg->out + lane * kRow;
+        x[0] = r[0]; x[1] = r[1]; x[2] = r[2];
+        v[0] = r[3]; v[1] = r[4]; v[2] = r[5];
+        a[0] = r[6]; a[1] = r[7]; a[2] = r[8];
+        w = r[9];
+        id = sg->out_id[lane];
+        if (MODE == MODE_PIC) live = boundaries(A, x, v, w, ls);
+    }
+    const unsigned m = __ballot_sync(kFull, live);
+    if (m) {
+        unsigned long long s0 = 0;
+        if (lane == 0) s0 = atomicAdd(&A.st->n_out, (unsigned long long)__popc(m));
+        s0 = __shfl_sync(kFull, s0, 0);
+        if (live) {
+            const unsigned long long slot = s0 + __popc(m & ((1u << lane) - 1u));
+            if ((long long)slot < A.cap_out) {
+                store(A.out, slot, x, v, a, w, id);
+                if (MODE == MODE_PIC) {
+                    if (A.q_e) deposit(x[0], x[1], x[2], w, A.ox, A.oy, A.oz, A.dxr, A.nx, A.ny, A.nz, A.q_e, A.st);
+                } else {
+                    M.add(x, v, w);
+                }
+            } else {
+                atomicOr(&A.st->err, kErrOutCapacity);
+            }
+        }
+    }
+    __syncwarp();
+    const int rest = n - cnt;
+    if (lane < rest) {
+        for (int f = 0; f < 10; ++f) sg->out[lane * kRow + f] = sg->out[(cnt + lane) * kRow + f];
+        sg->out_id[lane] = sg->out_id[cnt + lane];
+    }
+    __syncwarp();
+    n = rest;
+}
+
+// Queues staged ionization products [0, cnt) for the children kernel.
+template <class T>
+__device__ __forceinline__ void flush_children(const PushArgs<T>& A, Stage<T>* sg, int& n, int cnt) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    unsigned long long s0 = 0;
+    if (lane == 0) s0 = atomicAdd(&A.st->n_child, (unsigned long long)cnt);
+    s0 = __shfl_sync(kFull, s0, 0);
+    if (lane < cnt) {
+        const unsigned long long s = s0 + lane;
+        if ((long long)s < A.cap_child) {
+            const T* r = sg->ch + lane * kRow;
+            const Soa<T>& q = A.cq.p;
+            q.r[PX][s] = r[0]; q.r[PY][s] = r[1]; q.r[PZ][s] = r[2];
+            q.r[VX][s] = r[3];
+            q.r[AX][s] = r[4]; q.r[AY][s] = r[5]; q.r[AZ][s] = r[6];
+            q.r[PW][s] = r[7];
+            A.cq.t_left[s] = r[8];
+            q.id[s] = sg->ch_id[lane];
+            A.cq.k[s] = sg->ch_k[lane];
+        } else {
+            atomicOr(&A.st->err, kErrChildCapacity);
+        }
+    }
+    __syncwarp();
+    const int rest = n - cnt;
+    if (lane < rest) {
+        for (int f = 0; f < 9; ++f) sg->ch[lane * kRow + f] = sg->ch[(cnt + lane) * kRow + f];
+        sg->ch_id[lane] = sg->ch_id[cnt + lane];
+        sg->ch_k[lane] = sg->ch_k[cnt + lane];
+    }
+    __syncwarp();
+    n = rest;
+}
+
+template <class T, int MODE, bool FAST, bool STATS, bool CHILD>
+__device__ __forceinline__ void collide_loop(const PushArgs<T>& A, const ProcSmem<T>* ps, Stage<T>* sg) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    long long n_items;
+    unsigned long long* cursor;
+    if (CHILD) {
+        n_items = (long long)A.st->n_child;
+        if (n_items > A.cap_child) n_items = A.cap_child;
+        cursor = &A.st->n_fetch_c;
+    } else {
+        n_items = (long long)A.st->n_in;
+        cursor = &A.st->n_fetch;
+    }
     LStats ls;
     ls.zero();
     MomAcc<T> M;
     if (MODE == MODE_SWARM) M.zero();
     StackSink<T> stk;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)n; i += stride) {
-        const Soa<T>& q = A.cq.p;
-        T x[3] = {q.r[PX][i], q.r[PY][i], q.r[PZ][i]};
-        T v[3] = {q.r[VX][i], q.r[VY][i], q.r[VZ][i]};
-        const T a[3] = {q.r[AX][i], q.r[AY][i], q.r[AZ][i]};
-        T w = q.r[PW][i];
-        uint64_t id = q.id[i];
-        T tl = A.cq.t_left[i];
-        stk.n = 0;
-        for (;;) {
-            ++ls.processed;
-            bool alive = advance<T, MODE, FAST>(A, tab, x, v, a, w, id, tl, ls, stk);
-            if (alive && MODE == MODE_PIC) alive = boundaries(A, x, v, w, ls);
-            if (alive) {
-                const unsigned long long s = atomicAdd(&A.st->n_out, 1ull);
-                emit<T, MODE>(A, s, x, v, a, w, id, M);
-            }
-            if (stk.n == 0) break;
+    Lane<T> L;
+    bool active = false, dry = false;
+    int in_head = 0, in_count = 0, n_out = 0, n_ch = 0;
+    for (;;) {
+        // 1. idle lanes take staged electrons (a lane's own stack first)
+        bool want = !active;
+        if (CHILD && want && stk.n > 0) {
             --stk.n;
             const int t = stk.n;
-            x[0] = stk.x[t][0]; x[1] = stk.x[t][1]; x[2] = stk.x[t][2];
-            v[0] = stk.v[t][0]; v[1] = stk.v[t][1]; v[2] = stk.v[t][2];
-            w = stk.w[t]; id = stk.id[t]; tl = stk.t[t];
+            for (int d = 0; d < 3; ++d) { L.x[d] = stk.x[t][d]; L.v[d] = stk.v[t][d]; L.d[d] = (T)0; }
+            L.w = stk.w[t];
+            L.id = stk.id[t];
+            L.t_left = stk.t[t];
+            L.k = 1;
+            active = true;
+            want = false;
+            ++ls.processed;
+        }
+        const unsigned need = __ballot_sync(kFull, want);
+        const int avail = in_count - in_head;
+        if (need && avail > 0) {
+            const int rank = __popc(need & lt);
+            if (want && rank < avail) {
+                const int e = in_head + rank;
+                const T* r = sg->in + e * kRow;
+                for (int d = 0; d < 3; ++d) { L.x[d] = r[d]; L.v[d] = r[3 + d]; L.a[d] = r[6 + d]; L.d[d] = (T)0; }
+                L.w = r[9];
+                L.t_left = r[10];
+                L.id = sg->in_id[e];
+                L.k = 1;
+                active = L.w > (T)0;
+                if (active) ++ls.processed;
+            }
+            const int took = __popc(need) < avail ? __popc(need) : avail;
+            in_head += took;
+        }
+        // 2. refill the input stage with 32 work items once it is drained
+        if (in_head >= in_count && !dry) {
+            __syncwarp();
+            unsigned long long b = 0;
+            if (lane == 0) b = atomicAdd(cursor, 32ull);
+            b = __shfl_sync(kFull, b, 0);
+            if ((long long)b >= n_items) {
+                dry = true;
+                in_head = in_count = 0;
+            } else {
+                const long long left = n_items - (long long)b;
+                const int cnt = left < 32 ? (int)left : 32;
+                if (lane < cnt) {
+                    const long long it = (long long)b + lane;
+                    T* r = sg->in + lane * kRow;
+                    if (CHILD) {
+                        const Soa<T>& q = A.cq.p;
+                        const T x0 = q.r[PX][it], x1 = q.r[PY][it], x2 = q.r[PZ][it], w = q.r[PW][it];
+                        T vc[3];
+                        const uint64_t cid = make_child(A, q.id[it], A.cq.k[it], q.r[VX][it], vc);
+                        if (MODE == MODE_PIC && A.q_pos)
+                            deposit(x0, x1, x2, w, A.ox, A.oy, A.oz, A.dxr, A.nx, A.ny, A.nz, A.q_pos, A.st);
+                        r[0] = x0; r[1] = x1; r[2] = x2;
+                        r[3] = vc[0]; r[4] = vc[1]; r[5] = vc[2];
+                        r[6] = q.r[AX][it]; r[7] = q.r[AY][it]; r[8] = q.r[AZ][it];
+                        r[9] = w;
+                        r[10] = A.cq.t_left[it];
+                        sg->in_id[lane] = cid;
+                    } else {
+                        for (int f = 0; f < 10; ++f) r[f] = A.in.r[f][it];
+                        r[10] = A.dt;
+                        sg->in_id[lane] = A.in.id[it];
+                    }
+                }
+                in_head = 0;
+                in_count = cnt;
+            }
+            __syncwarp();
+        }
+        // 3. termination
+        if (!__any_sync(kFull, active || (CHILD && stk.n > 0))) {
+            if (dry && in_head >= in_count) break;
+            continue;
+        }
+        // 4. one candidate collision
+        int r = EV_CONTINUE;
+        T sp = (T)0;
+        if (active) r = event<T, MODE, FAST, STATS>(A, nullptr, ps, L, ls, sp);
+        const bool done = r == EV_DONE, ion = r == EV_IONIZED;
+        if (r == EV_DONE || r == EV_ATTACHED) active = false;
+        // 5. ionization products
+        if (CHILD) {
+            if (ion) {
+                if (stk.n < StackSink<T>::kDepth) {
+                    const T xc[3] = {L.x[0] + L.d[0], L.x[1] + L.d[1], L.x[2] + L.d[2]};
+                    T vc[3];
+                    const uint64_t cid = make_child(A, L.id, L.k - 1, sp, vc);
+                    if (MODE == MODE_PIC && A.q_pos)
+                        deposit(xc[0], xc[1], xc[2], L.w, A.ox, A.oy, A.oz, A.dxr, A.nx, A.ny, A.nz, A.q_pos, A.st);
+                    const int t = stk.n++;
+                    for (int d = 0; d < 3; ++d) { stk.x[t][d] = xc[d]; stk.v[t][d] = vc[d]; }
+                    stk.w[t] = L.w;
+                    stk.id[t] = cid;
+                    stk.t[t] = L.t_left;
+                    ++ls.children;
+                } else {
+                    atomicOr(&A.st->err, kErrStack);
+                }
+            }
+        } else {
+            const unsigned im = __ballot_sync(kFull, ion);
+            if (im) {
+                if (ion) {
+                    const int e = n_ch + __popc(im & lt);
+                    T* q = sg->ch + e * kRow;
+                    q[0] = L.x[0] + L.d[0]; q[1] = L.x[1] + L.d[1]; q[2] = L.x[2] + L.d[2];
+                    q[3] = sp;
+                    q[4] = L.a[0]; q[5] = L.a[1]; q[6] = L.a[2];
+                    q[7] = L.w;
+                    q[8] = L.t_left;
+                    sg->ch_id[e] = L.id;
+                    sg->ch_k[e] = L.k - 1;
+                    ++ls.children;
+                }
+                n_ch += __popc(im);
+                if (n_ch >= 32) flush_children(A, sg, n_ch, 32);
+            }
+        }
+        // 6. finished electrons
+        const unsigned dm = __ballot_sync(kFull, done);
+        if (dm) {
+            if (done) {
+                const int e = n_out + __popc(dm & lt);
+                T* q = sg->out + e * kRow;
+                q[0] = L.x[0] + L.d[0]; q[1] = L.x[1] + L.d[1]; q[2] = L.x[2] + L.d[2];
+                q[3] = L.v[0]; q[4] = L.v[1]; q[5] = L.v[2];
+                q[6] = L.a[0]; q[7] = L.a[1]; q[8] = L.a[2];
+                q[9] = L.w;
+                sg->out_id[e] = L.id;
+            }
+            n_out += __popc(dm);
+            if (n_out >= 32) flush_out<T, MODE>(A, sg, n_out, 32, ls, M);
         }
     }
+    if (n_out > 0) flush_out<T, MODE>(A, sg, n_out, n_out, ls, M);
+    if (!CHILD && n_ch > 0) flush_children(A, sg, n_ch, n_ch);
     if (STATS) flush_stats(A, ls, A.n_proc);
     if (MODE == MODE_SWARM) {
         M.m[14] += ls.w_ion;
         M.m[15] += ls.w_att;
         __syncthreads();
-        flush_moments(A, M, reinterpret_cast<double*>(smem_raw));
+        flush_moments(A, M, reinterpret_cast<double*>(sg - (threadIdx.x >> 5)));  // block-wide scratch
     }
+}
+
+template <class T> __device__ __forceinline__ ProcSmem<T>* stage_proc(unsigned char* raw, const PushArgs<T>& A) {
+    ProcSmem<T>* ps = reinterpret_cast<ProcSmem<T>*>(raw);
+    if (threadIdx.x < 8) {
+        ps->thr[threadIdx.x] = A.thr[threadIdx.x];
+        ps->mratio[threadIdx.x] = A.mratio[threadIdx.x];
+        ps->kind[threadIdx.x] = A.kind[threadIdx.x];
+    }
+    __syncthreads();
+    return ps;
+}
+
+template <class T> __device__ __forceinline__ Stage<T>* warp_stage(unsigned char* raw) {
+    return reinterpret_cast<Stage<T>*>(raw + ((sizeof(ProcSmem<T>) + 15) & ~(size_t)15)) + (threadIdx.x >> 5);
+}
+
+constexpr int kCollideThreads = 128;
+
+template <class T, int MODE, bool FAST, bool STATS>
+__global__ void __launch_bounds__(kCollideThreads) k_push(const PushArgs<T> A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const ProcSmem<T>* ps = stage_proc(smem_raw, A);
+    collide_loop<T, MODE, FAST, STATS, false>(A, ps, warp_stage<T>(smem_raw));
+}
+
+template <class T, int MODE, bool FAST, bool STATS>
+__global__ void __launch_bounds__(kCollideThreads) k_children(const PushArgs<T> A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const ProcSmem<T>* ps = stage_proc(smem_raw, A);
+    collide_loop<T, MODE, FAST, STATS, true>(A, ps, warp_stage<T>(smem_raw));
 }
 
 // Deposit of the current particle set (no push).
@@ -599,6 +841,8 @@ template <class T> struct PushLaunch {
     static cudaError_t children(const PushArgs<T>& A, int mode, bool stats, int grid, cudaStream_t s);
     static cudaError_t deposit(const Soa<T>& p, DevState* st, const Grid& g, unsigned long long* q, int grid,
                                cudaStream_t s);
+    static cudaError_t field_kick(const PushArgs<T>& A, int grid, cudaStream_t s);
+    static cudaError_t resample(const PushArgs<T>& A, int grid, cudaStream_t s);
     static size_t smem_bytes(int n_bins);
     static int blocks_per_sm(int mode, int n_bins);
 };

@@ -6,9 +6,8 @@
 namespace pic {
 
 template <class T> size_t PushLaunch<T>::smem_bytes(int n_bins) {
-    size_t t = (size_t)n_bins * kTableStride * sizeof(T);
-    size_t m = (size_t)kNMom * 32 * sizeof(double);
-    return t > m ? t : m;
+    (void)n_bins;
+    return collide_smem<T>();
 }
 
 template <class T> int PushLaunch<T>::blocks_per_sm(int mode, int n_bins) {
@@ -17,10 +16,10 @@ template <class T> int PushLaunch<T>::blocks_per_sm(int mode, int n_bins) {
     int b = 0;
     if (mode == MODE_PIC) {
         cudaFuncSetAttribute(k_push<T, MODE_PIC, FAST, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_push<T, MODE_PIC, FAST, false>, 256, sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_push<T, MODE_PIC, FAST, false>, kCollideThreads, sm);
     } else {
         cudaFuncSetAttribute(k_push<T, MODE_SWARM, FAST, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_push<T, MODE_SWARM, FAST, false>, 256, sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_push<T, MODE_SWARM, FAST, false>, kCollideThreads, sm);
     }
     return b > 0 ? b : 1;
 }
@@ -32,11 +31,11 @@ static cudaError_t launch_one(bool children, const PushArgs<T>& A, int grid, cud
     if (children) {
         e = cudaFuncSetAttribute(k_children<T, MODE, FAST, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        k_children<T, MODE, FAST, STATS><<<grid, 256, sm, s>>>(A);
+        k_children<T, MODE, FAST, STATS><<<grid, kCollideThreads, sm, s>>>(A);
     } else {
         e = cudaFuncSetAttribute(k_push<T, MODE, FAST, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
-        k_push<T, MODE, FAST, STATS><<<grid, 256, sm, s>>>(A);
+        k_push<T, MODE, FAST, STATS><<<grid, kCollideThreads, sm, s>>>(A);
     }
     return cudaGetLastError();
 }
@@ -63,6 +62,17 @@ template <class T>
 cudaError_t PushLaunch<T>::deposit(const Soa<T>& p, DevState* st, const Grid& g, unsigned long long* q, int grid,
                                    cudaStream_t s) {
     k_deposit<T><<<grid, 256, 0, s>>>(p, st, (T)g.ox, (T)g.oy, (T)g.oz, (T)g.dx, g.nx, g.ny, g.nz, q, st);
+    return cudaGetLastError();
+}
+
+template <class T> cudaError_t PushLaunch<T>::field_kick(const PushArgs<T>& A, int grid, cudaStream_t s) {
+    k_field_kick<T><<<grid, 256, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
+template <class T> cudaError_t PushLaunch<T>::resample(const PushArgs<T>& A, int grid, cudaStream_t s) {
+    k_resample<T><<<grid, 256, 0, s>>>(A);
+    k_resample_commit<<<1, 1, 0, s>>>(A.st);
     return cudaGetLastError();
 }
 
