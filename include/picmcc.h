@@ -71,7 +71,9 @@ typedef struct pic_gas {
 
 typedef struct pic_config {
     int precision;            /* 32 or 64: arithmetic of the particle state and push */
-    int nx, ny, nz;           /* grid cells (each >= 2) */
+    int nx, ny, nz;           /* grid cells (each >= 2, at most 2046; with coupled != 0 the grid must halve
+                                 down to a coarsest multigrid level of at most ~22,000 cells, e.g. every
+                                 dimension a multiple of 16 for grids up to 512) */
     double dx;                /* cell size, m */
     double origin[3];         /* lower corner, m */
     long long capacity;       /* particle slots per buffer (two buffers are kept) */
@@ -207,7 +209,7 @@ int pic_load(pic_ctx *ctx, const void *host_blob, size_t bytes);
  * residual (defect correction) until ||b - A phi|| / ||b|| <= rtol.
  * E = -grad(phi) by central differences at cell centres (float32). */
 typedef struct poisson_config {
-    int nx, ny, nz;
+    int nx, ny, nz;           /* as for pic_config with coupled != 0; unsupported sizes give PIC_ERR_ARG */
     double dx;
     double v_lo, v_hi, v_mask;
 } poisson_config;

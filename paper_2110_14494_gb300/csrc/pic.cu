@@ -221,6 +221,16 @@ __global__ void k_fixed_to_rho(const long long* __restrict__ qe, const long long
 
 // Next step's input count; cursors that ran past the capacity (an error
 // already flagged) are clamped so no kernel reads beyond the buffers.
+// Warm start of the coupled solve: phi <- 2 phi_n - phi_{n-1} (linear
+// extrapolation in time), phi_prev <- phi_n.  With no history, only the copy.
+__global__ void k_extrapolate(double* __restrict__ phi, double* __restrict__ prev, long long n, int have_prev) {
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const double p = phi[c];
+        if (have_prev) phi[c] = 2.0 * p - prev[c];
+        prev[c] = p;
+    }
+}
+
 __global__ void k_end_step(DevState* st, long long* count_slot, long long cap) {
     const unsigned long long nc = st->n_child < (unsigned long long)cap ? st->n_child : (unsigned long long)cap;
     st->n_updates += st->n_in + nc;
@@ -322,6 +332,9 @@ struct MergeScratch {
     uint32_t* sidx;
 };
 
+constexpr int kSortMax = 2048;                  // candidates sorted in shared memory (else in global)
+constexpr int kPairsPerThread = kSortMax / 2 / 256;
+
 // One block per occupied cell.  Merge: candidates w < (2/3) omega ordered by
 // (|v|^2, id) are paired (0,1), (2,3), ...; the pair's weights are summed and
 // one member's state is kept with probability proportional to its weight
@@ -336,6 +349,8 @@ __global__ void __launch_bounds__(256) k_merge_split(Soa<T> p, long long n, cons
                                                      DevState* st) {
     __shared__ int m_sh, m2_sh;
     __shared__ long long wsum_sh;
+    __shared__ unsigned long long sk[kSortMax], sid[kSortMax];
+    __shared__ uint32_t six[kSortMax];
     for (long long c = blockIdx.x; c < ncell; c += gridDim.x) {
         const uint32_t s0 = start[c], s1 = start[c + 1];
         if (s0 == s1) continue;
@@ -359,6 +374,80 @@ __global__ void __launch_bounds__(256) k_merge_split(Soa<T> p, long long n, cons
         }
         __syncthreads();
         int m = m_sh;
+        if (m <= kSortMax) {
+            // shared-memory bitonic sort of (|v|^2 bits, id), padded to a power of two
+            for (int t = threadIdx.x; t < m; t += blockDim.x) {
+                sk[t] = (unsigned long long)__double_as_longlong(sc.key[s0 + t]);
+                sid[t] = sc.id[s0 + t];
+                six[t] = sc.idx[s0 + t];
+            }
+            __syncthreads();
+            for (uint32_t round = 0; m >= 2; ++round) {
+                int P = 1;
+                while (P < m) P <<= 1;
+                for (int t = m + threadIdx.x; t < P; t += blockDim.x) { sk[t] = ~0ull; sid[t] = ~0ull; six[t] = 0; }
+                __syncthreads();
+                for (int kk = 2; kk <= P; kk <<= 1)
+                    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+                        for (int t = threadIdx.x; t < P; t += blockDim.x) {
+                            const int u = t ^ jj;
+                            if (u > t) {
+                                const bool up = (t & kk) == 0;
+                                const bool gt = sk[t] > sk[u] || (sk[t] == sk[u] && sid[t] > sid[u]);
+                                if (gt == up) {
+                                    const unsigned long long a1 = sk[t], a2 = sid[t];
+                                    const uint32_t a3 = six[t];
+                                    sk[t] = sk[u]; sid[t] = sid[u]; six[t] = six[u];
+                                    sk[u] = a1; sid[u] = a2; six[u] = a3;
+                                }
+                            }
+                        }
+                        __syncthreads();
+                    }
+                // pair (0,1), (2,3), ...; results held in registers until all pairs are read
+                unsigned long long rk[kPairsPerThread], rid[kPairsPerThread];
+                uint32_t rix[kPairsPerThread];
+                int nres = 0;
+                for (int q = threadIdx.x; q < m / 2; q += blockDim.x) {
+                    const uint32_t ia = six[2 * q], ib = six[2 * q + 1];
+                    const uint64_t da = sid[2 * q], db = sid[2 * q + 1];
+                    const T wa = p.r[PW][ia], wb = p.r[PW][ib];
+                    const uint64_t mid = da < db ? da : db;
+                    const u32x4 o = draw_words(K, mid, step, 0xC0000000u | round);
+                    const double u = unif<double>(o.x);
+                    const bool keep_a = u * ((double)wa + (double)wb) < (double)wa;
+                    const uint32_t keep = keep_a ? ia : ib, drop = keep_a ? ib : ia;
+                    const T ws = wa + wb;
+                    p.r[PW][keep] = ws;
+                    p.r[PW][drop] = (T)0;
+                    if ((double)ws < lo) {
+                        rk[nres] = keep_a ? sk[2 * q] : sk[2 * q + 1];
+                        rid[nres] = keep_a ? da : db;
+                        rix[nres] = keep;
+                        ++nres;
+                    }
+                }
+                unsigned long long lk = 0, lid = 0;
+                uint32_t lix = 0;
+                const bool odd = (m & 1) != 0;
+                if (odd && threadIdx.x == 0) { lk = sk[m - 1]; lid = sid[m - 1]; lix = six[m - 1]; }
+                if (threadIdx.x == 0) m2_sh = 0;
+                __syncthreads();
+                for (int r = 0; r < nres; ++r) {
+                    const int t = atomicAdd(&m2_sh, 1);
+                    sk[t] = rk[r]; sid[t] = rid[r]; six[t] = rix[r];
+                }
+                if (odd && threadIdx.x == 0) {
+                    const int t = atomicAdd(&m2_sh, 1);
+                    sk[t] = lk; sid[t] = lid; six[t] = lix;
+                }
+                __syncthreads();
+                const int m2 = m2_sh;
+                __syncthreads();
+                if (m2 == m) break;
+                m = m2;
+            }
+        } else {
         for (uint32_t round = 0; m >= 2; ++round) {
             // rank by counting: position of each candidate in (key, id) order
             for (int a = threadIdx.x; a < m; a += blockDim.x) {
@@ -405,6 +494,7 @@ __global__ void __launch_bounds__(256) k_merge_split(Soa<T> p, long long n, cons
             __syncthreads();
             if (m2 == m) break;
             m = m2;
+        }
         }
         // split
         for (uint32_t t = s0 + threadIdx.x; t < s1; t += blockDim.x) {
@@ -465,7 +555,8 @@ static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
     size_t total = 0;
-    size_t buf[2], cq, table, table64, E4, qe, qp, qn, st, cnt, start, sums, key, rank, msc, gas, rho, phi, mg, hostio;
+    size_t buf[2], cq, table, table64, E4, qe, qp, qn, st, cnt, start, sums, key, rank, msc, gas, rho, phi, phi_prev, mg,
+        hostio;
 };
 
 static size_t real_size(int prec) { return prec == 64 ? 8 : 4; }
@@ -504,6 +595,7 @@ static Layout make_layout(const pic_config* c) {
     L.gas = take(((size_t)(c->gas.n_proc > 0 ? c->gas.n_proc : 1) + 1) * nb * 8 + 64 * 8);
     L.rho = take(ncell * 8);
     L.phi = take(ncell * 8);
+    L.phi_prev = take(ncell * 8);
     L.mg = take(MG::bytes(c->nx, c->ny, c->nz));
     L.hostio = 0;
     L.total = o;
@@ -538,6 +630,7 @@ struct pic_ctx {
     int last_cycles = 0;
     double last_rel = 0;
     long long steps_done = 0;
+    long long n_solves = 0;   // coupled solves so far (the warm start extrapolates after two)
     long long launches = 0;   // kernels launched by pic_step (for the profile)
     // per-phase timing
     int prof = 0;
@@ -633,6 +726,7 @@ static int validate(const pic_config* c) {
     for (int k = 0; k < g.n_proc; ++k)
         if (g.kind[k] < 0 || g.kind[k] > 3) return PIC_ERR_ARG;
     if (c->coupled && (!(c->poisson_rtol > 0) || c->poisson_max_cycles < 1)) return PIC_ERR_ARG;
+    if (c->coupled && !MG::supported(c->nx, c->ny, c->nz)) return PIC_ERR_ARG;
     return PIC_OK;
 }
 
@@ -925,7 +1019,10 @@ static void fixed_to_rho(pic_ctx* c, double* rho) {
 // started from the previous potential), packed E for the next gather.
 static int solve_field(pic_ctx* c) {
     fixed_to_rho(c, c->rho());
-    c->launches += 1;
+    k_extrapolate<<<grid_n(c->g.ncell()), 256, 0, c->s>>>(c->phi(), (double*)(c->ws + c->L.phi_prev), c->g.ncell(),
+                                                           c->n_solves >= 2 ? 1 : 0);
+    c->n_solves++;
+    c->launches += 2;
     const long long l0 = c->mg.launches;
     double hn[2];
     int rc = c->mg.solve(c->rho(), c->mask, c->phi(), c->g.dx, c->cfg.v_lo, c->cfg.v_hi, c->cfg.v_mask,
@@ -1189,7 +1286,10 @@ extern "C" int pic_load(pic_ctx* c, const void* blob, size_t bytes) {
     c->a_valid = hd.a_valid;
     c->n_wu = hd.n_wu;
     c->n_sorts = hd.n_sorts;
-    if (c->cfg.coupled) c->field_valid = 0;  // recomputed from the restored charge before the next step
+    if (c->cfg.coupled) {
+        c->field_valid = 0;  // recomputed from the restored charge before the next step
+        c->n_solves = 0;
+    }
     return PIC_OK;
 }
 

@@ -71,11 +71,21 @@ __device__ __forceinline__ V nb_sum(const V* e, const uint8_t* m, int i, int j, 
     const bool in = i < nx && j < ny;                            \
     const int c = in ? lin(i, j, k, nx, ny) : 0;
 
+// Reducing kernels run a bounded grid (z extent kZRed) and loop over z.
+constexpr int kZRed = 8;
+#define CELL3D_LOOP_BEGIN                                        \
+    const int i = blockIdx.x * BX + threadIdx.x;                 \
+    const int j = blockIdx.y * BY + threadIdx.y;                 \
+    const bool in = i < nx && j < ny;                            \
+    double acc = 0.0;                                            \
+    for (int k = blockIdx.z; k < nz; k += gridDim.z) {           \
+        const int c = in ? lin(i, j, k, nx, ny) : 0;
+#define CELL3D_LOOP_END }
+
 // b = h^2 rho / eps0 + plate terms + electrode neighbours; accumulates ||b||^2.
 __global__ void k_rhs_norm(const double* __restrict__ rho, const uint8_t* __restrict__ mask, int nx, int ny, int nz,
                            double h2e, double v_lo, double v_hi, double v_mask, double* sc) {
-    CELL3D
-    double acc = 0.0;
+    CELL3D_LOOP_BEGIN
     if (in && !mask[c]) {
         const int pl = nx * ny;
         double s = h2e * rho[c];
@@ -87,8 +97,9 @@ __global__ void k_rhs_norm(const double* __restrict__ rho, const uint8_t* __rest
         if (j < ny - 1 && mask[c + nx]) s += v_mask;
         if (k > 0 && mask[c - pl]) s += v_mask;
         if (k < nz - 1 && mask[c + pl]) s += v_mask;
-        acc = s * s;
+        acc += s * s;
     }
+    CELL3D_LOOP_END
     block_add(acc, sc + S_B2);
 }
 
@@ -97,8 +108,7 @@ __global__ void k_rhs_norm(const double* __restrict__ rho, const uint8_t* __rest
 __global__ void k_resid64(double* __restrict__ phi, const double* __restrict__ rho, const uint8_t* __restrict__ mask,
                           int nx, int ny, int nz, double h2e, double v_lo, double v_hi, double v_mask,
                           double* __restrict__ r, float* __restrict__ g0, double* sc) {
-    CELL3D
-    double acc = 0.0;
+    CELL3D_LOOP_BEGIN
     if (in) {
         if (mask[c]) {
             phi[c] = v_mask;
@@ -118,17 +128,17 @@ __global__ void k_resid64(double* __restrict__ phi, const double* __restrict__ r
             const double rr = h2e * rho[c] + sum - 6.0 * pc;
             r[c] = rr;
             g0[c] = (float)rr;
-            acc = rr * rr;
+            acc += rr * rr;
         }
     }
+    CELL3D_LOOP_END
     block_add(acc, sc + S_R2);
 }
 
 // q = A p (homogeneous boundary values) and p.q.
 __global__ void k_apply(const double* __restrict__ p, const uint8_t* __restrict__ mask, int nx, int ny, int nz,
                         double* __restrict__ q, double* sc) {
-    CELL3D
-    double acc = 0.0;
+    CELL3D_LOOP_BEGIN
     if (in) {
         if (mask[c]) {
             q[c] = 0.0;
@@ -137,9 +147,10 @@ __global__ void k_apply(const double* __restrict__ p, const uint8_t* __restrict_
             const double s = nb_sum(p, mask, i, j, k, nx, ny, nz, c, diag);
             const double v = diag * p[c] - s;
             q[c] = v;
-            acc = p[c] * v;
+            acc += p[c] * v;
         }
     }
+    CELL3D_LOOP_END
     block_add(acc, sc + S_GAM);
 }
 
@@ -155,13 +166,13 @@ __global__ void k_update_xr(double* __restrict__ phi, double* __restrict__ r, co
                             const double* __restrict__ q, float* __restrict__ g0, int n, double* sc) {
     const double a = sc[S_ALPHA];
     double acc = 0.0;
-    const int c = (blockIdx.x * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
-    if (c < n) {
+    const int stride = gridDim.x * blockDim.x * blockDim.y;
+    for (int c = (blockIdx.x * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x; c < n; c += stride) {
         phi[c] += a * p[c];
         const double rr = r[c] - a * q[c];
         r[c] = rr;
         g0[c] = (float)rr;
-        acc = rr * rr;
+        acc += rr * rr;
     }
     block_add(acc, sc + S_R2);
 }
@@ -169,12 +180,12 @@ __global__ void k_update_xr(double* __restrict__ phi, double* __restrict__ r, co
 // t1 = z.r, t2 = z.q with z the preconditioned residual (float32).
 __global__ void k_dot2(const float* __restrict__ z, const double* __restrict__ r, const double* __restrict__ q, int n,
                        double* sc, int with_q) {
-    const int c = (blockIdx.x * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
+    const int stride = gridDim.x * blockDim.x * blockDim.y;
     double a = 0.0, b = 0.0;
-    if (c < n) {
+    for (int c = (blockIdx.x * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x; c < n; c += stride) {
         const double zz = (double)z[c];
-        a = zz * r[c];
-        if (with_q) b = zz * q[c];
+        a += zz * r[c];
+        if (with_q) b += zz * q[c];
     }
     block_add(a, sc + S_T1);
     if (with_q) block_add(b, sc + S_T2);
@@ -279,23 +290,116 @@ __global__ void k_copy_mask(const uint8_t* __restrict__ m, uint8_t* __restrict__
     if (c < n) out[c] = m ? (m[c] ? 1 : 0) : 0;
 }
 
-// Coarsest level: Gauss-Seidel sweeps inside one block.
-__global__ void k_coarse_solve(float* __restrict__ e, const float* __restrict__ g, const uint8_t* __restrict__ mask,
-                               int nx, int ny, int nz, int sweeps) {
-    const int n = nx * ny * nz;
-    for (int c = threadIdx.x; c < n; c += blockDim.x) e[c] = 0.0f;
+
+// The small levels of the hierarchy (from level t down to the coarsest; the
+// first of them has at most kTailCells cells) run as one block in shared
+// memory: zero, pre-smooth, restrict, ... coarse sweeps ... prolong,
+// post-smooth, with block barriers between the phases instead of kernel
+// launches.  The block reads g and the masks of level t from global memory
+// and writes back e of level t.
+constexpr int kTailCells = 8192;
+
+struct TailLevels {
+    float* e_first;          // global e of level `first`
+    const float* g_first;    // global g of level `first`
+    const uint8_t* m[12];    // global masks
+    int nx[12], ny[12], nz[12], off[12];  // shared-memory offsets (cells)
+    int first, last, pre, post, coarse, total;
+};
+
+struct TailSmem {
+    float* e;
+    float* g;
+    uint8_t* m;
+};
+
+__device__ void tail_smooth(const TailLevels& T, const TailSmem& S, int l, int color) {
+    const int nx = T.nx[l], ny = T.ny[l], nz = T.nz[l], n = nx * ny * nz, o = T.off[l];
+    float* e = S.e + o;
+    const float* g = S.g + o;
+    const uint8_t* m = S.m + o;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        const int i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
+        if (((i + j + k) & 1) != color || m[c]) continue;
+        float diag;
+        const float s = nb_sum(e, m, i, j, k, nx, ny, nz, c, diag);
+        e[c] = (g[c] + s) / diag;
+    }
     __syncthreads();
-    for (int s = 0; s < sweeps; ++s)
-        for (int color = 0; color < 2; ++color) {
-            for (int c = threadIdx.x; c < n; c += blockDim.x) {
-                const int i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
-                if (((i + j + k) & 1) != color || mask[c]) continue;
-                float diag;
-                const float sm = nb_sum(e, mask, i, j, k, nx, ny, nz, c, diag);
-                e[c] = (g[c] + sm) / diag;
-            }
-            __syncthreads();
+}
+
+__global__ void __launch_bounds__(1024) k_tail_vcycle(const TailLevels T) {
+    extern __shared__ __align__(16) unsigned char tail_raw[];
+    TailSmem S;
+    S.e = reinterpret_cast<float*>(tail_raw);
+    S.g = S.e + T.total;
+    S.m = reinterpret_cast<uint8_t*>(S.g + T.total);
+    {
+        const int n0 = T.nx[T.first] * T.ny[T.first] * T.nz[T.first];
+        for (int c = threadIdx.x; c < n0; c += blockDim.x) S.g[T.off[T.first] + c] = T.g_first[c];
+        for (int l = T.first; l <= T.last; ++l) {
+            const int n = T.nx[l] * T.ny[l] * T.nz[l];
+            for (int c = threadIdx.x; c < n; c += blockDim.x) S.m[T.off[l] + c] = T.m[l][c];
         }
+    }
+    __syncthreads();
+    for (int l = T.first; l <= T.last; ++l) {
+        const int n = T.nx[l] * T.ny[l] * T.nz[l];
+        for (int c = threadIdx.x; c < n; c += blockDim.x) S.e[T.off[l] + c] = 0.0f;
+        __syncthreads();
+        if (l == T.last) {
+            for (int s = 0; s < T.coarse; ++s) { tail_smooth(T, S, l, 0); tail_smooth(T, S, l, 1); }
+            break;
+        }
+        for (int s = 0; s < T.pre; ++s) { tail_smooth(T, S, l, 0); tail_smooth(T, S, l, 1); }
+        // residual restricted to level l + 1 (h^2 scaling: 4 x mean of 8)
+        const int nx = T.nx[l], ny = T.ny[l], nz = T.nz[l];
+        const int cx = nx / 2, cy = ny / 2, cz = nz / 2, ncz = cx * cy * cz;
+        const float* e = S.e + T.off[l];
+        const float* g = S.g + T.off[l];
+        const uint8_t* m = S.m + T.off[l];
+        for (int q = threadIdx.x; q < ncz; q += blockDim.x) {
+            float* gc = S.g + T.off[l + 1];
+            if (S.m[T.off[l + 1] + q]) { gc[q] = 0.0f; continue; }
+            const int I = q % cx, J = (q / cx) % cy, K = q / (cx * cy);
+            float acc = 0.0f;
+            for (int d = 0; d < 8; ++d) {
+                const int i = 2 * I + (d & 1), j = 2 * J + ((d >> 1) & 1), k = 2 * K + (d >> 2);
+                const int c = lin(i, j, k, nx, ny);
+                if (m[c]) continue;
+                float diag;
+                const float s = nb_sum(e, m, i, j, k, nx, ny, nz, c, diag);
+                acc += g[c] - (diag * e[c] - s);
+            }
+            gc[q] = 0.5f * acc;
+        }
+        __syncthreads();
+    }
+    for (int l = T.last - 1; l >= T.first; --l) {
+        const int nx = T.nx[l], ny = T.ny[l], nz = T.nz[l], n = nx * ny * nz;
+        const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
+        float* e = S.e + T.off[l];
+        const float* ec = S.e + T.off[l + 1];
+        const uint8_t* m = S.m + T.off[l];
+        for (int c = threadIdx.x; c < n; c += blockDim.x) {
+            if (m[c]) { e[c] = 0.0f; continue; }
+            const int i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
+            const int I = i >> 1, J = j >> 1, K = k >> 1;
+            const int si = (i & 1) ? 1 : -1, sj = (j & 1) ? 1 : -1, sk = (k & 1) ? 1 : -1;
+            float acc = 0.0f;
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 2; ++b)
+                    for (int d = 0; d < 2; ++d) {
+                        const float wgt = (a ? 0.25f : 0.75f) * (b ? 0.25f : 0.75f) * (d ? 0.25f : 0.75f);
+                        acc += wgt * cval(ec, I + (d ? si : 0), J + (b ? sj : 0), K + (a ? sk : 0), cx, cy, cz);
+                    }
+            e[c] += acc;
+        }
+        __syncthreads();
+        for (int s = 0; s < T.post; ++s) { tail_smooth(T, S, l, 1); tail_smooth(T, S, l, 0); }
+    }
+    const int n0 = T.nx[T.first] * T.ny[T.first] * T.nz[T.first];
+    for (int c = threadIdx.x; c < n0; c += blockDim.x) T.e_first[c] = S.e[T.off[T.first] + c];
 }
 
 // E = -grad(phi) at cell centres with the stencil's ghost values; writes any
@@ -319,6 +423,11 @@ __global__ void k_grad(const double* __restrict__ phi, int nx, int ny, int nz, d
 dim3 grid3(int nx, int ny, int nz) { return dim3((nx + BX - 1) / BX, (ny + BY - 1) / BY, nz); }
 dim3 grid3_half(int nx, int ny, int nz) { return dim3((nx / 2 + BX - 1) / BX, (ny + BY - 1) / BY, nz); }
 dim3 grid_flat(long long n) { return dim3((unsigned)((n + BX * BY - 1) / (BX * BY))); }
+dim3 grid_red(long long n) {
+    long long b = (n + BX * BY - 1) / (BX * BY);
+    return dim3((unsigned)(b < 1216 ? b : 1216));
+}
+dim3 grid3_red(int nx, int ny, int nz) { return dim3((nx + BX - 1) / BX, (ny + BY - 1) / BY, nz < kZRed ? nz : kZRed); }
 const dim3 kBlk(BX, BY, 1);
 
 }  // namespace
@@ -337,6 +446,15 @@ void MG::plan(int nx_, int ny_, int nz_) {
         if (x < 4 || y < 4 || z < 4) break;
         x /= 2; y /= 2; z /= 2;
     }
+}
+
+bool MG::supported(int nx_, int ny_, int nz_) {
+    if (nx_ < 2 || ny_ < 2 || nz_ < 2 || nz_ > 65535) return false;
+    if ((long long)nx_ * ny_ * nz_ > 0x7fffffffLL) return false;
+    MG m;
+    m.plan(nx_, ny_, nz_);
+    const int L = m.levels - 1;
+    return (long long)m.lx[L] * m.ly[L] * m.lz[L] * 9 <= 200 * 1024;
 }
 
 size_t MG::bytes(int nx_, int ny_, int nz_) {
@@ -378,10 +496,20 @@ cudaError_t MG::build_masks(const uint8_t* mask, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// One V(pre, post)-cycle on A e0 = g0; e0 is overwritten.
+// One V(pre, post)-cycle on A e0 = g0; e0 is overwritten.  Levels above the
+// tail run as separate kernels; the tail runs as one block.
 void MG::vcycle(cudaStream_t s) {
-    launches += (long long)(levels - 1) * (2 + 2 * pre + 2 * post + 1) + 1;
-    for (int l = 0; l < levels - 1; ++l) {
+    int t = 0;
+    while (t < levels - 1 && (long long)lx[t] * ly[t] * lz[t] > kTailCells) ++t;
+    // the tail's shared memory must fit: keep full levels above it otherwise
+    while (t < levels - 1) {
+        long long cells = 0;
+        for (int l = t; l < levels; ++l) cells += (long long)lx[l] * ly[l] * lz[l];
+        if (cells * 9 <= 200 * 1024) break;
+        ++t;
+    }
+    launches += (long long)t * (1 + 2 * pre + 2 * post + 1) + 1;
+    for (int l = 0; l < t; ++l) {
         const long long n = (long long)lx[l] * ly[l] * lz[l];
         cudaMemsetAsync(e[l], 0, n * sizeof(float), s);
         for (int it = 0; it < pre; ++it) {
@@ -391,9 +519,26 @@ void MG::vcycle(cudaStream_t s) {
         k_resid_restrict<<<grid3(lx[l + 1], ly[l + 1], lz[l + 1]), kBlk, 0, s>>>(e[l], g[l], m[l], lx[l], ly[l],
                                                                                  lz[l], g[l + 1], m[l + 1]);
     }
-    const int L = levels - 1;
-    k_coarse_solve<<<1, 256, 0, s>>>(e[L], g[L], m[L], lx[L], ly[L], lz[L], coarse_sweeps);
-    for (int l = levels - 2; l >= 0; --l) {
+    TailLevels T;
+    int off = 0;
+    for (int l = 0; l < levels; ++l) {
+        T.m[l] = m[l];
+        T.nx[l] = lx[l]; T.ny[l] = ly[l]; T.nz[l] = lz[l];
+        T.off[l] = off;
+        if (l >= t) off += lx[l] * ly[l] * lz[l];
+    }
+    T.e_first = e[t];
+    T.g_first = g[t];
+    T.first = t;
+    T.last = levels - 1;
+    T.pre = pre;
+    T.post = post;
+    T.coarse = coarse_sweeps;
+    T.total = off;
+    const size_t smem = (size_t)off * (2 * sizeof(float) + 1);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_tail_vcycle, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_tail_vcycle<<<1, 1024, smem, s>>>(T);
+    for (int l = t - 1; l >= 0; --l) {
         k_prolong_add<<<grid3(lx[l], ly[l], lz[l]), kBlk, 0, s>>>(e[l + 1], e[l], m[l], lx[l], ly[l], lz[l]);
         for (int it = 0; it < post; ++it) {
             k_smooth<<<grid3_half(lx[l], ly[l], lz[l]), kBlk, 0, s>>>(e[l], g[l], m[l], lx[l], ly[l], lz[l], 1);
@@ -407,12 +552,12 @@ void MG::iteration(cudaStream_t s, double* phi, const uint8_t* mk, bool first) {
     const int nx = lx[0], ny = ly[0], nz = lz[0];
     const int n = nx * ny * nz;
     vcycle(s);
-    k_dot2<<<grid_flat(n), kBlk, 0, s>>>(e[0], r64, q64, n, norms, first ? 0 : 1);
+    k_dot2<<<grid_red(n), kBlk, 0, s>>>(e[0], r64, q64, n, norms, first ? 0 : 1);
     k_beta<<<1, 1, 0, s>>>(norms, first ? 1 : 0);
     k_update_p<<<grid_flat(n), kBlk, 0, s>>>(p64, e[0], n, norms);
-    k_apply<<<grid3(nx, ny, nz), kBlk, 0, s>>>(p64, mk, nx, ny, nz, q64, norms);
+    k_apply<<<grid3_red(nx, ny, nz), kBlk, 0, s>>>(p64, mk, nx, ny, nz, q64, norms);
     k_alpha<<<1, 1, 0, s>>>(norms);
-    k_update_xr<<<grid_flat(n), kBlk, 0, s>>>(phi, r64, p64, q64, g[0], n, norms);
+    k_update_xr<<<grid_red(n), kBlk, 0, s>>>(phi, r64, p64, q64, g[0], n, norms);
     launches += 6;
 }
 
@@ -426,7 +571,6 @@ int MG::solve(const double* rho, const uint8_t* mask, double* phi, double h, dou
               double rtol, int max_cycles, int packed_prec, void* E4, float* Ex, float* Ey, float* Ez,
               cudaStream_t s, int* cycles_out, double* rel_out, double* host_norms) {
     const int nx = lx[0], ny = ly[0], nz = lz[0];
-    const int n = nx * ny * nz;
     const double h2e = h * h / kEps0;
     if (!persistent || !masks_ready) {
         if (build_masks(mask, s) != cudaSuccess) return PIC_ERR_CUDA;
@@ -440,8 +584,8 @@ int MG::solve(const double* rho, const uint8_t* mask, double* phi, double h, dou
         g_key[0] = phi; g_key[1] = rho; g_key[2] = mask;
     }
     cudaMemsetAsync(norms, 0, S_N * 8, s);
-    k_rhs_norm<<<grid3(nx, ny, nz), kBlk, 0, s>>>(rho, mk, nx, ny, nz, h2e, v_lo, v_hi, v_mask, norms);
-    k_resid64<<<grid3(nx, ny, nz), kBlk, 0, s>>>(phi, rho, mk, nx, ny, nz, h2e, v_lo, v_hi, v_mask, r64, g[0], norms);
+    k_rhs_norm<<<grid3_red(nx, ny, nz), kBlk, 0, s>>>(rho, mk, nx, ny, nz, h2e, v_lo, v_hi, v_mask, norms);
+    k_resid64<<<grid3_red(nx, ny, nz), kBlk, 0, s>>>(phi, rho, mk, nx, ny, nz, h2e, v_lo, v_hi, v_mask, r64, g[0], norms);
     launches += 2;
     int cyc = 0, rc = PIC_OK;
     double bn = 1.0, rn = 0.0;
@@ -495,8 +639,7 @@ int MG::solve(const double* rho, const uint8_t* mask, double* phi, double h, dou
 using pic::MG;
 
 extern "C" size_t poisson_workspace_bytes(const poisson_config* pc) {
-    if (!pc || pc->nx < 2 || pc->ny < 2 || pc->nz < 2) return 0;
-    if ((long long)pc->nx * pc->ny * pc->nz > 0x7fffffffLL || pc->nz > 65535) return 0;
+    if (!pc || !MG::supported(pc->nx, pc->ny, pc->nz)) return 0;
     return MG::bytes(pc->nx, pc->ny, pc->nz);
 }
 
@@ -506,7 +649,7 @@ extern "C" int poisson_solve(const poisson_config* pc, const double* rho, const 
     if (!pc || !rho || !phi || !ws || pc->nx < 2 || pc->ny < 2 || pc->nz < 2 || !(pc->dx > 0) || !(rtol > 0) ||
         max_cycles < 0)
         return PIC_ERR_ARG;
-    if ((long long)pc->nx * pc->ny * pc->nz > 0x7fffffffLL || pc->nz > 65535) return PIC_ERR_ARG;
+    if (!MG::supported(pc->nx, pc->ny, pc->nz)) return PIC_ERR_ARG;
     if (ws_bytes < MG::bytes(pc->nx, pc->ny, pc->nz) || ((uintptr_t)ws & 255)) return PIC_ERR_ARG;
     if ((Ex == nullptr) != (Ey == nullptr) || (Ex == nullptr) != (Ez == nullptr)) return PIC_ERR_ARG;
     MG mg;
@@ -560,6 +703,7 @@ extern "C" int poisson_solve_noalloc(const poisson_config* pc, const double* rho
         max_cycles < 0)
         return PIC_ERR_ARG;
     if ((Ex == nullptr) != (Ey == nullptr) || (Ex == nullptr) != (Ez == nullptr)) return PIC_ERR_ARG;
+    if (!MG::supported(pc->nx, pc->ny, pc->nz)) return PIC_ERR_ARG;
     if (MG::bytes(pc->nx, pc->ny, pc->nz) > kNoAllocScratchBytes) return PIC_ERR_CAPACITY;
     void* ws = nullptr;
     int rc = noalloc_scratch(&ws);

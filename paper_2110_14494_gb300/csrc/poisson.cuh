@@ -14,7 +14,7 @@ struct MG {
     uint8_t* m[kMaxLevels];
     double* norms = nullptr;  // CG scalars: ||b||^2, ||r||^2, rho, gamma, z.r, z.q, alpha, beta
     double *r64 = nullptr, *p64 = nullptr, *q64 = nullptr;  // CG vectors (float64)
-    int pre = 2, post = 2, coarse_sweeps = 50;
+    int pre = 2, post = 2, coarse_sweeps = 8;
     long long launches = 0;  // kernels launched so far
     // Reusable state for a solver owned by a long-lived caller (a PIC context):
     // the coarse masks are built once, and each CG iteration (V-cycle plus
@@ -30,6 +30,9 @@ struct MG {
     void iteration(cudaStream_t s, double* phi, const uint8_t* mk, bool first);
 
     void plan(int nx, int ny, int nz);
+    // The coarsest level must be small enough for the single-block tail
+    // (its cells and those of nothing else fit in shared memory).
+    static bool supported(int nx, int ny, int nz);
     static size_t bytes(int nx, int ny, int nz);
     void carve(void* base, int nx, int ny, int nz);
     cudaError_t build_masks(const uint8_t* mask, cudaStream_t s);
