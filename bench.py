@@ -39,8 +39,8 @@ WORKLOAD = "streamer-128^3-fp32"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=1990)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", type=int, default=32)
     ap.add_argument("--n-initial", type=int, default=1_000_000)
@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cap", type=int, default=0, help="particle slots (default 1.6x the particle cap)")
+    ap.add_argument("--trace", action="store_true", help="per-step statistics (diagnostics, slower kernels)")
+    ap.add_argument("--boundary", type=int, default=1, help="0: reflect at the domain faces, 1: absorb (outflow)")
+    ap.add_argument("--fixed-dt", action="store_true", help="keep dt = 2 ps (no time-step control)")
     return ap.parse_args()
 
 
@@ -214,6 +217,8 @@ def main():
     ctx = PicContext(gas, g, precision=args.precision, capacity=cap, seed=2110144940 + rank, dt=wl["dt"],
                      mask=mask, n_ppc=wl["n_ppc"], w_min=wl["w_min"], growth_trigger=wl["growth_trigger"],
                      particle_cap=wl["particle_cap"], sort_interval=20, coupled=True, v_lo=wl["v_bottom"],
+                     boundary=args.boundary, adaptive_dt=not args.fixed_dt, cfl=0.5, mobility=0.06,
+                     max_growth=1.2,
                      v_hi=wl["v_top"], v_mask=wl["v_top"], poisson_rtol=1e-6, poisson_max_cycles=200)
     n0 = ctx.seed_gaussian(wl["seed_n0"], wl["seed_radius"], wl["seed_center"], w0)
     stream = torch.cuda.current_stream()
@@ -228,13 +233,27 @@ def main():
     clocks = Clocks(local)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     n_trace = []
+    t_wall = time.perf_counter()
+    recent_n = []
     for i in range(args.steps):
         flush.fill_(i & 0xff)
         ev[i][0].record(stream)
-        ctx.step(1)
+        try:
+            st = ctx.step(1, stats=args.trace)
+        except Exception:
+            print(json.dumps({"failed_at_step": i, "recent": recent_n[-40:]}), file=sys.stderr, flush=True)
+            raise
         ev[i][1].record(stream)
+        if args.trace:
+            recent_n.append((i, st.n_start, st.n_end, st.n_children, st.n_weight_updates, st.n_absorbed,
+                             st.poisson_cycles, round(st.dt_last * 1e12, 4), "%.3g" % st.ne_max))
         if i % 25 == 0:
             n_trace.append(ctx.count())
+        if (i + 1) % 200 == 0 and rank == 0:
+            torch.cuda.synchronize()
+            recent = sum(a.elapsed_time(b) for a, b in ev[i - 199:i + 1])
+            print(json.dumps({"progress": i + 1, "n": n_trace[-1], "ms_last_200": round(recent, 2),
+                              "wall_s": round(time.perf_counter() - t_wall, 2)}), file=sys.stderr, flush=True)
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = sum(a.elapsed_time(b) for a, b in ev)
@@ -246,6 +265,7 @@ def main():
         dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
         dist.all_reduce(upd_t, op=dist.ReduceOp.SUM)
     ms_max = float(ms_t.item())
+    fin = ctx.step(0, stats=True)
     value = float(upd_t.item()) / (ms_max * 1e-3)
 
     # dominant kernel: the parent push (gather + push + MCC + deposit)
@@ -299,7 +319,12 @@ def main():
             "data": "synthetic",
             "config": {"workload": WORKLOAD if args.grid == 128 else f"streamer-{args.grid}^3",
                        "grid": [g["nx"], g["ny"], g["nz"]], "dx_um": 20, "n_initial": n0,
-                       "particle_cap": wl["particle_cap"], "dt_ps": 2, "poisson": "multigrid rtol 1e-6 every step",
+                       "particle_cap": wl["particle_cap"],
+                       "dt": "fixed 2 ps" if args.fixed_dt else "adaptive <= 2 ps (CFL 0.5 on the 90% speed, "
+                             "dielectric relaxation with mu_e = 0.06 m^2/Vs, electron growth <= 20%/step)",
+                       "simulated_ns": round(fin.t_total * 1e9, 4), "last_dt_ps": round(fin.dt_last * 1e12, 4),
+                       "ne_max": fin.ne_max, "boundary": "absorbing faces" if args.boundary == 1 else "reflecting",
+                       "poisson": "multigrid-preconditioned CG, rtol 1e-6, every step",
                        "l2": "flushed between timed steps (256 MB write outside the timed events)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "particles_trace": n_trace},

@@ -92,6 +92,11 @@ typedef struct pic_config {
     double v_mask;            /* electrode potential, V */
     double poisson_rtol;      /* relative residual target of the coupled solve (e.g. 1e-6) */
     int poisson_max_cycles;   /* V-cycle limit per solve */
+    /* time-step control (Sec. 2.1.4); adaptive_dt = 0 keeps dt fixed */
+    int adaptive_dt;          /* 1: dt_next = min(dt, CFL, dielectric relaxation, growth limit) */
+    double cfl;               /* dt v_90 <= cfl dx, v_90 the 90 % quantile of the speeds (paper: 0.5) */
+    double mobility;          /* electron mobility for dt_drt = eps0 / (e n_e,max mu_e), m^2/(V s) */
+    double max_growth;        /* electrons may grow by at most this factor per step (paper: 1.2) */
 } pic_config;
 
 /* Host-side particle arrays (float64, any n).  Positions m, velocities m/s,
@@ -113,6 +118,9 @@ typedef struct pic_step_stats {
     double w_ion, w_att, w_absorbed;   /* weights of ionization / attachment / absorption events */
     int poisson_cycles;                /* V-cycles of the last coupled solve */
     double poisson_rel_res;
+    double dt_last;                    /* time step of the last step, s */
+    double t_total;                    /* simulated time since init, s */
+    double ne_max;                     /* largest cell electron density after the last step, m^-3 */
 } pic_step_stats;
 
 typedef struct pic_ctx pic_ctx;

@@ -17,6 +17,8 @@ constexpr int kMaxProc = PIC_MAX_PROC;
 constexpr int kTableStride = 8;            // processes per table row (7 used + total)
 constexpr int kNMom = PIC_SWARM_NMOM;
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kVBinsPerOctave = 6;
+constexpr int kVBins = 20 * kVBinsPerOctave;  // 2^10 .. 2^30 m/s
 
 // Error bits raised by kernels in DevState::err.
 enum : unsigned {
@@ -117,6 +119,11 @@ struct DevState {
     unsigned long long n_parents; // cumulative parents advanced
     unsigned long long n_fetch;   // work cursor of the parent kernel (items handed to warps)
     unsigned long long n_fetch_c; // work cursor of the children kernel
+    unsigned long long n_spill;   // products spilled to the second queue (a descendant stack ran full)
+    // end-of-step statistics for the time-step control
+    long long qe_max;             // largest fixed-point electron deposit of a cell
+    unsigned long long qe_sum;    // sum of the deposit (two's complement)
+    unsigned int vhist[kVBins];   // speeds, kVBinsPerOctave bins per octave from 2^10 m/s
 };
 
 // Uniform grid description (cell-centred, cubic cells).

@@ -3,6 +3,7 @@
 //
 // Compiled with --fmad=false: the seeding, sort keys and weight-update
 // arithmetic round every operation separately.
+#include <limits.h>
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -232,15 +233,62 @@ __global__ void k_extrapolate(double* __restrict__ phi, double* __restrict__ pre
 }
 
 __global__ void k_end_step(DevState* st, long long* count_slot, long long cap) {
-    const unsigned long long nc = st->n_child < (unsigned long long)cap ? st->n_child : (unsigned long long)cap;
-    st->n_updates += st->n_in + nc;
+    st->n_updates += st->n_in;
     st->n_parents += st->n_in;
+    st->n_spill = 0;
     st->n_in = st->n_out < (unsigned long long)cap ? st->n_out : (unsigned long long)cap;
     st->n_fetch = 0;
     st->n_fetch_c = 0;
     st->n_out = 0;
     st->n_child = 0;
     if (count_slot) *count_slot = (long long)st->n_in;
+}
+
+// End-of-step statistics for the time-step control (Sec. 2.1.4): a histogram
+// of the electron speeds (for the 90 % quantile of the CFL condition) and the
+// largest and total fixed-point electron deposit (for the dielectric
+// relaxation time and the growth limit).
+template <class T>
+__global__ void k_step_stats(const Soa<T> p, const DevState* stc, const unsigned long long* __restrict__ qe,
+                             long long ncell, DevState* st) {
+    __shared__ unsigned int h[kVBins];
+    for (int b = threadIdx.x; b < kVBins; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    const long long n = (long long)stc->n_out;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        if (!(p.r[PW][i] > (T)0)) continue;
+        const float vx = (float)p.r[VX][i], vy = (float)p.r[VY][i], vz = (float)p.r[VZ][i];
+        const float v2 = vx * vx + vy * vy + vz * vz;
+        int b = v2 > 0.0f ? (int)floorf((0.5f * log2f(v2) - 10.0f) * kVBinsPerOctave) : 0;
+        b = b < 0 ? 0 : (b >= kVBins ? kVBins - 1 : b);
+        atomicAdd(&h[b], 1u);
+    }
+    long long mx = LLONG_MIN, sm = 0;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += stride) {
+        const long long q = (long long)qe[c];
+        mx = q > mx ? q : mx;
+        sm += q;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long om = __shfl_xor_sync(kFull, mx, o);
+        mx = om > mx ? om : mx;
+        sm += __shfl_xor_sync(kFull, sm, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&st->qe_max, mx);
+        atomicAdd(&st->qe_sum, (unsigned long long)sm);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kVBins; b += blockDim.x)
+        if (h[b]) atomicAdd(&st->vhist[b], h[b]);
+}
+
+// Before children generation g >= 1: the queue it will spill into starts empty.
+__global__ void k_next_generation(DevState* st, int gen) {
+    st->n_fetch_c = 0;
+    if (gen & 1) st->n_child = 0;
+    else st->n_spill = 0;
 }
 
 __global__ void k_set_count(DevState* st, unsigned long long n) {
@@ -555,7 +603,7 @@ static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
     size_t total = 0;
-    size_t buf[2], cq, table, table64, E4, qe, qp, qn, st, cnt, start, sums, key, rank, msc, gas, rho, phi, phi_prev, mg,
+    size_t buf[2], cq[2], table, table64, E4, qe, qp, qn, st, cnt, start, sums, key, rank, msc, gas, rho, phi, phi_prev, mg,
         hostio;
 };
 
@@ -573,10 +621,12 @@ static Layout make_layout(const pic_config* c) {
         for (int f = 0; f < 10; ++f) take(cap * R);
         take(cap * 8);
     }
-    L.cq = o;
-    for (int f = 0; f < 11; ++f) take(cap * R);  // 10 fields + t_left
-    take(cap * 8);
-    take(cap * 4);                               // draw index of the ionization
+    for (int qq = 0; qq < 2; ++qq) {
+        L.cq[qq] = o;
+        for (int f = 0; f < 11; ++f) take(cap * R);  // 10 fields + t_left
+        take(cap * 8);
+        take(cap * 4);                               // draw index of the ionization
+    }
     const int nb = c->gas.n_bins > 0 ? c->gas.n_bins : 2;
     L.table = take((size_t)nb * kTableStride * R);
     L.table64 = take((size_t)nb * kTableStride * 8);
@@ -630,6 +680,9 @@ struct pic_ctx {
     int last_cycles = 0;
     double last_rel = 0;
     long long steps_done = 0;
+    long long n_next = 0;     // particle count after the step being run (known once its children finished)
+    double dt_cur = 0, dt_prev = 0, dt_next = 0;  // time steps (fixed unless adaptive_dt)
+    double w_prev = 0, ne_max = 0, t_total = 0;
     long long n_solves = 0;   // coupled solves so far (the warm start extrapolates after two)
     long long launches = 0;   // kernels launched by pic_step (for the profile)
     // per-phase timing
@@ -661,9 +714,9 @@ struct pic_ctx {
         s.id = (uint64_t*)p;
         return s;
     }
-    template <class T> ChildQ<T> childq() {
+    template <class T> ChildQ<T> childq(int which) {
         ChildQ<T> q;
-        char* p = ws + L.cq;
+        char* p = ws + L.cq[which];
         const size_t cap = (size_t)cfg.capacity;
         for (int f = 0; f < 10; ++f) { q.p.r[f] = (T*)p; p += al256(cap * sizeof(T)); }
         q.t_left = (T*)p;
@@ -727,6 +780,7 @@ static int validate(const pic_config* c) {
         if (g.kind[k] < 0 || g.kind[k] > 3) return PIC_ERR_ARG;
     if (c->coupled && (!(c->poisson_rtol > 0) || c->poisson_max_cycles < 1)) return PIC_ERR_ARG;
     if (c->coupled && !MG::supported(c->nx, c->ny, c->nz)) return PIC_ERR_ARG;
+    if (c->adaptive_dt && (!(c->cfl > 0) || c->mobility < 0 || !(c->max_growth > 1.0))) return PIC_ERR_ARG;
     return PIC_OK;
 }
 
@@ -791,6 +845,7 @@ extern "C" int pic_init(const pic_config* cfg, void* d_ws, size_t ws_bytes, cons
     c->g = Grid{cfg->nx, cfg->ny, cfg->nz, cfg->dx, cfg->origin[0], cfg->origin[1], cfg->origin[2]};
     c->K = make_keys(cfg->seed);
     c->mask = d_mask;
+    c->dt_cur = c->dt_prev = c->dt_next = cfg->dt;
     cudaError_t e = cudaMemsetAsync(c->ws + L.st, 0, sizeof(DevState), c->s);
     const size_t ncell = (size_t)c->g.ncell();
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.qe, 0, ncell * 8, c->s);
@@ -821,7 +876,9 @@ template <class T> static PushArgs<T> make_args(pic_ctx* c, int mode) {
     memset(&A, 0, sizeof(A));
     A.in = c->soa<T>(c->cur);
     A.out = c->soa<T>(1 - c->cur);
-    A.cq = c->childq<T>();
+    A.cq = c->childq<T>(0);
+    A.cq2 = c->childq<T>(1);
+    A.gen = 0;
     A.st = c->st();
     A.table = (const T*)(c->ws + c->L.table);
     A.n_bins = c->n_bins;
@@ -832,7 +889,8 @@ template <class T> static PushArgs<T> make_args(pic_ctx* c, int mode) {
     A.eps_lo = (T)c->cfg.gas.eps[0];
     A.eps_hi = (T)c->cfg.gas.eps[c->n_bins - 1];
     A.nu_max = (T)c->nu_max;
-    A.dt = (T)c->cfg.dt;
+    A.dt = (T)c->dt_cur;
+    A.dt_kick = (T)c->dt_prev;
     A.K = c->K;
     A.step = c->step;
     A.first = c->a_valid ? 0 : 1;
@@ -1095,6 +1153,69 @@ extern "C" int pic_weight_update(pic_ctx* c) {
     return c->prec == 32 ? weight_update<float>(c) : weight_update<double>(c);
 }
 
+// Time-step control (Sec. 2.1.4): dt_next = min(dt_max, CFL, dielectric
+// relaxation, growth limit).  CFL: dt v_90 <= cfl dx with v_90 the upper edge
+// of the speed-histogram bin holding the 90 % quantile; dielectric relaxation:
+// eps0 / (e n_e,max mu_e); growth: if the electrons (total deposited weight)
+// grew by g > max_growth in the last step, dt is scaled by ln(max_growth)/ln g.
+// dt may at most double from one step to the next.
+static void next_dt(pic_ctx* c, const DevState& h) {
+    const double dV = c->g.dx * c->g.dx * c->g.dx;
+    long long tot = 0;
+    for (int b = 0; b < kVBins; ++b) tot += h.vhist[b];
+    double v90 = 0.0;
+    long long acc = 0;
+    for (int b = 0; b < kVBins; ++b) {
+        acc += h.vhist[b];
+        if (tot > 0 && acc >= (long long)ceil(0.9 * (double)tot)) {
+            v90 = exp2(10.0 + (double)(b + 1) / kVBinsPerOctave);
+            break;
+        }
+    }
+    const double ne_max = (double)h.qe_max / (4294967296.0 * dV);
+    const double w_now = (double)(long long)h.qe_sum / 4294967296.0;
+    double dt = c->cfg.dt;
+    if (v90 > 0.0) dt = fmin(dt, c->cfg.cfl * c->g.dx / v90);
+    if (ne_max > 0.0 && c->cfg.mobility > 0.0) dt = fmin(dt, kEps0 / (kQ * ne_max * c->cfg.mobility));
+    if (c->w_prev > 0.0 && w_now > c->cfg.max_growth * c->w_prev && c->cfg.max_growth > 1.0)
+        dt = fmin(dt, c->dt_cur * log(c->cfg.max_growth) / log(w_now / c->w_prev));
+    dt = fmin(dt, 2.0 * c->dt_cur);
+    c->ne_max = ne_max;
+    c->w_prev = w_now;
+    c->dt_next = dt;
+}
+
+// Further children generations while descendants spilled out of the lane
+// stacks (deep ionization cascades within one step).  Reads the device state
+// once (synchronising); afterwards c->n_next holds the particle count the
+// step will leave.
+template <class T> static int extra_generations(pic_ctx* c, PushArgs<T>& A, int mode, bool stats) {
+    for (int gen = 1;; ++gen) {
+        if (c->cfg.adaptive_dt && mode == MODE_PIC) {
+            DevState* st = c->st();
+            cudaMemsetAsync(&st->qe_max, 0, sizeof(long long) + sizeof(unsigned long long) + sizeof(st->vhist), c->s);
+            k_step_stats<T><<<152 * 4, 256, 0, c->s>>>(A.out, st, c->qe(), c->g.ncell(), st);
+            c->launches += 1;
+        }
+        DevState h;
+        int rc = read_state(c, &h);
+        if (rc) return rc;
+        const unsigned long long pending = (gen & 1) ? h.n_spill : h.n_child;
+        c->n_next = (long long)(h.n_out < (unsigned long long)c->cfg.capacity ? h.n_out : c->cfg.capacity);
+        if (!pending) {
+            if (c->cfg.adaptive_dt && mode == MODE_PIC) next_dt(c, h);
+            break;
+        }
+        if (gen > 256) return c->fail(PIC_ERR_CAPACITY, "ionization cascade deeper than 256 generations");
+        k_next_generation<<<1, 1, 0, c->s>>>(c->st(), gen);
+        A.gen = gen;
+        cudaError_t e = PushLaunch<T>::children(A, mode, stats, c->grid_push, c->s);
+        if (e != cudaSuccess) return c->cuda_fail(e, "children");
+        c->launches += 2;
+    }
+    return PIC_OK;
+}
+
 template <class T> static int one_step(pic_ctx* c, bool stats) {
     c->step++;
     PushArgs<T> A = make_args<T>(c, MODE_PIC);
@@ -1107,6 +1228,8 @@ template <class T> static int one_step(pic_ctx* c, bool stats) {
     if (e == cudaSuccess) e = PushLaunch<T>::children(A, MODE_PIC, stats, c->grid_push, c->s);
     c->mark(2);
     if (e != cudaSuccess) return c->cuda_fail(e, "push");
+    int rc = extra_generations<T>(c, A, MODE_PIC, stats);
+    if (rc) return rc;
     k_end_step<<<1, 1, 0, c->s>>>(c->st(), nullptr, c->cfg.capacity);
     c->cur = 1 - c->cur;
     c->a_valid = 1;
@@ -1136,13 +1259,15 @@ extern "C" int pic_step(pic_ctx* c, int n_steps, pic_step_stats* stats) {
     for (int it = 0; it < n_steps; ++it) {
         rc = c->prec == 32 ? one_step<float>(c, want) : one_step<double>(c, want);
         if (rc) return rc;
+        c->t_total += c->dt_cur;
+        c->dt_prev = c->dt_cur;
+        if (c->cfg.adaptive_dt) c->dt_cur = c->dt_next;
         c->accumulate(0, 1, &c->pt.ms_push, &c->pt.n_push);
         c->accumulate(1, 2, &c->pt.ms_children, &c->pt.n_children);
         bool sorted = false;
         c->mark(3);
         if (c->cfg.growth_trigger > 0) {
-            rc = read_state(c, &h);
-            if (rc) return rc;
+            c->n_host = c->n_next;
             if ((double)c->n_host > c->cfg.growth_trigger * (double)c->n_last_wu && c->n_host > 0) {
                 rc = pic_weight_update(c);
                 if (rc) return rc;
@@ -1189,6 +1314,9 @@ extern "C" int pic_step(pic_ctx* c, int n_steps, pic_step_stats* stats) {
         stats->n_sorts = c->n_sorts - so0;
         stats->poisson_cycles = c->last_cycles;
         stats->poisson_rel_res = c->last_rel;
+        stats->dt_last = c->dt_prev;
+        stats->t_total = c->t_total;
+        stats->ne_max = c->ne_max;
     }
     return erc;
 }
@@ -1218,8 +1346,9 @@ struct BlobHead {
     int64_t n, n_last_wu, ncell;
     uint32_t step, pad;
     int64_t n_wu, n_sorts;
+    double dt_cur, dt_prev, w_prev, t_total;
 };
-static const uint64_t kMagic = 0x3130314D43435049ull;  // "IPCCM101"
+static const uint64_t kMagic = 0x3230314D43435049ull;  // "IPCCM102"
 
 extern "C" int pic_save(pic_ctx* c, void* blob, size_t* bytes) {
     if (!c || !bytes) return PIC_ERR_ARG;
@@ -1229,7 +1358,8 @@ extern "C" int pic_save(pic_ctx* c, void* blob, size_t* bytes) {
     const size_t R = real_size(c->prec), n = (size_t)c->n_host, ncell = (size_t)c->g.ncell();
     const size_t need = sizeof(BlobHead) + n * (10 * R + 8) + 3 * ncell * 8;
     if (!blob || *bytes < need) { *bytes = need; return blob ? PIC_ERR_CAPACITY : PIC_OK; }
-    BlobHead hd{kMagic, c->prec, c->a_valid, (int64_t)n, c->n_last_wu, (int64_t)ncell, c->step, 0, c->n_wu, c->n_sorts};
+    BlobHead hd{kMagic, c->prec, c->a_valid, (int64_t)n, c->n_last_wu, (int64_t)ncell, c->step, 0, c->n_wu, c->n_sorts,
+                c->dt_cur, c->dt_prev, c->w_prev, c->t_total};
     char* p = (char*)blob;
     memcpy(p, &hd, sizeof hd);
     p += sizeof hd;
@@ -1286,6 +1416,10 @@ extern "C" int pic_load(pic_ctx* c, const void* blob, size_t bytes) {
     c->a_valid = hd.a_valid;
     c->n_wu = hd.n_wu;
     c->n_sorts = hd.n_sorts;
+    c->dt_cur = hd.dt_cur;
+    c->dt_prev = hd.dt_prev;
+    c->w_prev = hd.w_prev;
+    c->t_total = hd.t_total;
     if (c->cfg.coupled) {
         c->field_valid = 0;  // recomputed from the restored charge before the next step
         c->n_solves = 0;
@@ -1406,6 +1540,8 @@ template <class T> static int swarm_one(pic_ctx* c, const swarm_config* sc, doub
         if (e == cudaSuccess) e = PushLaunch<T>::parents(A, MODE_SWARM, false, c->grid_push, c->s);
         if (e == cudaSuccess) e = PushLaunch<T>::children(A, MODE_SWARM, false, c->grid_push, c->s);
         if (e != cudaSuccess) return c->cuda_fail(e, "swarm push");
+        int rc = extra_generations<T>(c, A, MODE_SWARM, false);
+        if (rc) return rc;
         k_end_step<<<1, 1, 0, c->s>>>(c->st(), d_cnt + (s - 1), c->cfg.capacity);
         c->cur = 1 - c->cur;
     }

@@ -24,7 +24,9 @@ enum { RES_NONE = 0, RES_THIN = 1, RES_DUP = 2 };
 
 template <class T> struct PushArgs {
     Soa<T> in, out;
-    ChildQ<T> cq;
+    ChildQ<T> cq, cq2;         // product queues: parents fill cq; children generation g reads
+                               // (g even ? cq : cq2) and spills into the other one
+    int gen;
     DevState* st;
     const T* table;            // [n_bins][8]: nu_0..nu_{n_proc-1}, zeros, total
     int n_bins, n_proc;
@@ -34,7 +36,8 @@ template <class T> struct PushArgs {
     T l0, inv_dl;              // ln(eps_0), (n_bins-1) / (ln eps_last - ln eps_0), in T
     T eps_lo, eps_hi;          // eV
     T nu_max;
-    T dt;
+    T dt;                      // duration of this step
+    T dt_kick;                 // duration of the previous step (the half-kick completes its Eq. 2)
     Keys K;
     uint32_t step;
     int first;                 // previous acceleration unknown: no half-kick
@@ -460,7 +463,7 @@ __global__ void __launch_bounds__(256) k_field_kick(const PushArgs<T> A) {
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const T an = -qm * E[d];
-            if (!A.first) A.in.r[VX + d][i] = A.in.r[VX + d][i] + (T)0.5 * A.dt * (an - A.in.r[AX + d][i]);
+            if (!A.first) A.in.r[VX + d][i] = A.in.r[VX + d][i] + (T)0.5 * A.dt_kick * (an - A.in.r[AX + d][i]);
             A.in.r[AX + d][i] = an;
         }
     }
@@ -628,10 +631,14 @@ __device__ __forceinline__ void collide_loop(const PushArgs<T>& A, const ProcSme
     const unsigned lt = (1u << lane) - 1u;
     long long n_items;
     unsigned long long* cursor;
+    const ChildQ<T>& src = (A.gen & 1) ? A.cq2 : A.cq;
+    const ChildQ<T>& dst = (A.gen & 1) ? A.cq : A.cq2;
+    unsigned long long* dst_cnt = (A.gen & 1) ? &A.st->n_child : &A.st->n_spill;
     if (CHILD) {
-        n_items = (long long)A.st->n_child;
+        n_items = (long long)((A.gen & 1) ? A.st->n_spill : A.st->n_child);
         if (n_items > A.cap_child) n_items = A.cap_child;
         cursor = &A.st->n_fetch_c;
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&A.st->n_updates, (unsigned long long)n_items);
     } else {
         n_items = (long long)A.st->n_in;
         cursor = &A.st->n_fetch;
@@ -693,17 +700,17 @@ __device__ __forceinline__ void collide_loop(const PushArgs<T>& A, const ProcSme
                     const long long it = (long long)b + lane;
                     T* r = sg->in + lane * kRow;
                     if (CHILD) {
-                        const Soa<T>& q = A.cq.p;
+                        const Soa<T>& q = src.p;
                         const T x0 = q.r[PX][it], x1 = q.r[PY][it], x2 = q.r[PZ][it], w = q.r[PW][it];
                         T vc[3];
-                        const uint64_t cid = make_child(A, q.id[it], A.cq.k[it], q.r[VX][it], vc);
+                        const uint64_t cid = make_child(A, q.id[it], src.k[it], q.r[VX][it], vc);
                         if (MODE == MODE_PIC && A.q_pos)
                             deposit(x0, x1, x2, w, A.ox, A.oy, A.oz, A.dxr, A.nx, A.ny, A.nz, A.q_pos, A.st);
                         r[0] = x0; r[1] = x1; r[2] = x2;
                         r[3] = vc[0]; r[4] = vc[1]; r[5] = vc[2];
                         r[6] = q.r[AX][it]; r[7] = q.r[AY][it]; r[8] = q.r[AZ][it];
                         r[9] = w;
-                        r[10] = A.cq.t_left[it];
+                        r[10] = src.t_left[it];
                         sg->in_id[lane] = cid;
                     } else {
                         for (int f = 0; f < 10; ++f) r[f] = A.in.r[f][it];
@@ -742,8 +749,21 @@ __device__ __forceinline__ void collide_loop(const PushArgs<T>& A, const ProcSme
                     stk.id[t] = cid;
                     stk.t[t] = L.t_left;
                     ++ls.children;
-                } else {
-                    atomicOr(&A.st->err, kErrStack);
+                } else {  // stack full: the compact entry waits for the next generation
+                    const unsigned long long q = atomicAdd(dst_cnt, 1ull);
+                    if ((long long)q < A.cap_child) {
+                        const Soa<T>& d = dst.p;
+                        d.r[PX][q] = L.x[0] + L.d[0]; d.r[PY][q] = L.x[1] + L.d[1]; d.r[PZ][q] = L.x[2] + L.d[2];
+                        d.r[VX][q] = sp;
+                        d.r[AX][q] = L.a[0]; d.r[AY][q] = L.a[1]; d.r[AZ][q] = L.a[2];
+                        d.r[PW][q] = L.w;
+                        d.id[q] = L.id;
+                        dst.t_left[q] = L.t_left;
+                        dst.k[q] = L.k - 1;
+                        ++ls.children;
+                    } else {
+                        atomicOr(&A.st->err, kErrChildCapacity);
+                    }
                 }
             }
         } else {

@@ -41,7 +41,9 @@ class pic_config(C.Structure):
                 ("dt", C.c_double), ("gas", pic_gas), ("n_ppc", C.c_int), ("w_min", C.c_double),
                 ("growth_trigger", C.c_double), ("particle_cap", C.c_longlong), ("boundary", C.c_int),
                 ("sort_interval", C.c_int), ("coupled", C.c_int), ("v_lo", C.c_double), ("v_hi", C.c_double),
-                ("v_mask", C.c_double), ("poisson_rtol", C.c_double), ("poisson_max_cycles", C.c_int)]
+                ("v_mask", C.c_double), ("poisson_rtol", C.c_double), ("poisson_max_cycles", C.c_int),
+                ("adaptive_dt", C.c_int), ("cfl", C.c_double), ("mobility", C.c_double),
+                ("max_growth", C.c_double)]
 
 
 class pic_particles_host(C.Structure):
@@ -54,7 +56,8 @@ class pic_step_stats(C.Structure):
                [(k, C.c_longlong) for k in ("n_children", "n_attached", "n_absorbed", "n_clamped",
                                             "n_processed", "n_weight_updates", "n_sorts")] + \
                [("w_ion", C.c_double), ("w_att", C.c_double), ("w_absorbed", C.c_double),
-                ("poisson_cycles", C.c_int), ("poisson_rel_res", C.c_double)]
+                ("poisson_cycles", C.c_int), ("poisson_rel_res", C.c_double), ("dt_last", C.c_double),
+                ("t_total", C.c_double), ("ne_max", C.c_double)]
 
 
 class pic_profile_times(C.Structure):
@@ -194,7 +197,7 @@ class PicContext:
     def __init__(self, gas: dict, grid: dict, *, precision=32, capacity=1 << 20, seed=1, dt=1e-12, mask=None,
                  n_ppc=75, w_min=1.0, growth_trigger=0.0, particle_cap=0, boundary=0, sort_interval=0,
                  coupled=False, v_lo=0.0, v_hi=0.0, v_mask=0.0, poisson_rtol=1e-6, poisson_max_cycles=100,
-                 stream=None):
+                 adaptive_dt=False, cfl=0.5, mobility=0.06, max_growth=1.2, stream=None):
         import torch
         self.gas = Gas(gas)
         c = pic_config()
@@ -206,6 +209,7 @@ class PicContext:
         c.boundary, c.sort_interval, c.coupled = boundary, sort_interval, int(coupled)
         c.v_lo, c.v_hi, c.v_mask, c.poisson_rtol, c.poisson_max_cycles = v_lo, v_hi, v_mask, poisson_rtol, \
             poisson_max_cycles
+        c.adaptive_dt, c.cfl, c.mobility, c.max_growth = int(adaptive_dt), cfl, mobility, max_growth
         self.cfg = c
         self.grid = grid
         self.ncell = grid["nx"] * grid["ny"] * grid["nz"]

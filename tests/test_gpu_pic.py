@@ -67,11 +67,11 @@ def test_deposit_bit_exact(prec):
     assert np.array_equal(q.cpu().numpy(), ref)
 
 
-@pytest.mark.parametrize("steps", [1, 10])
-def test_step_fp64_matches_oracle(steps):
+@pytest.mark.parametrize("steps,boundary", [(1, 0), (10, 0), (10, 1)])
+def test_step_fp64_matches_oracle(steps, boundary):
     gas, F, mk, p0 = _setup(6000, 64, 2)
     dt = 2e-12
-    ctx = _ctx(gas, GRID, 64, capacity=40000, seed=SEED, dt=dt, mask=mk)
+    ctx = _ctx(gas, GRID, 64, capacity=40000, seed=SEED, dt=dt, mask=mk, boundary=boundary)
     Fd = _field_dev(F)
     ctx.set_field(*Fd)
     ctx.set_particles(p0)
@@ -81,7 +81,7 @@ def test_step_fp64_matches_oracle(steps):
     ctx.deposit(q_e=qe, q_pos=qp, q_neg=qn)
     gpu = ctx.get_particles()
 
-    m = O.Model(gas, dt, SEED, 64, GRID, F, mask=mk)
+    m = O.Model(gas, dt, SEED, 64, GRID, F, mask=mk, boundary=boundary)
     P = O.Particles(40000, p0)
     rq_pos, rq_neg = np.zeros(n, np.int64), np.zeros(n, np.int64)
     for s in range(1, steps + 1):
@@ -191,3 +191,56 @@ def test_capacity_error_is_reported_not_faulted():
     with pytest.raises(PicError) as e:
         ctx.step(5)
     assert e.value.code == -3
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_deep_ionization_cascades_match_oracle(prec):
+    """A constant ionization frequency of 4e12/s over 2 ps gives cascades much
+    deeper than a lane's product stack; the spilled generations must give the
+    oracle's particle set exactly (float64) or within float32 tolerance."""
+    nu_i = 4e12
+    gas = W.multi_gas([W.single_process_gas(W.ELASTIC, 1e12 / W.N_GAS, mass=0.0),
+                       W.single_process_gas(W.IONIZATION, nu_i / W.N_GAS, threshold=0.0)])
+    grid = W.grid_spec(16, 16, 16, 2e-5)
+    p0 = W.random_particles(400, grid, 301, vmax=1e6, box=([1e-4] * 3, [2.2e-4] * 3))
+    zero = tuple(np.zeros((16, 16, 16), np.float32) for _ in range(3))
+    ctx = _ctx(gas, grid, prec, capacity=400000, seed=SEED, dt=2e-12)
+    ctx.set_field(*_field_dev(zero))
+    ctx.set_particles(p0)
+    st = ctx.step(1, stats=True)
+    gpu = ctx.get_particles()
+    m = O.Model(gas, 2e-12, SEED, 64, grid, zero)
+    P = O.Particles(400000, p0)
+    rc, ost = O.step(m, P, 1, True)
+    ref = P.view()
+    assert rc == 0 and ost.n_children > 20 * 400
+    nc, og, orf, bad, worst = compare_sets(gpu, ref, grid["dx"], 1e-12 if prec == 64 else 1e-5, v_floor=1e5)
+    if prec == 64:
+        assert og == 0 and orf == 0 and bad == 0, (og, orf, bad, worst)
+    else:
+        assert worst["gross"] + og + orf <= 1e-5 * len(ref["id"]) + 2, (og, orf, worst)
+    assert st.n_children == ost.n_children
+
+
+def test_adaptive_time_step_bounds():
+    """Sec. 2.1.4: dt <= min(dt_max, CFL on the 90 % speed, dielectric relaxation)."""
+    from paper_2110_14494_gb300 import PicContext
+    grid = W.grid_spec(32, 32, 32, 2e-5)
+    gas = W.synthetic_air()
+    mu = 0.06
+    ctx = PicContext(gas, grid, precision=32, capacity=2_000_000, seed=SEED, dt=2e-12, coupled=True, v_lo=0.0,
+                     v_hi=1000.0, v_mask=1000.0, adaptive_dt=True, cfl=0.5, mobility=mu, max_growth=1.2,
+                     boundary=1)
+    L = 32 * 2e-5
+    ctx.seed_gaussian(2e21, 8e-5, (0.5 * L, 0.5 * L, 0.5 * L), 200.0)
+    dts = []
+    for _ in range(12):
+        st = ctx.step(1, stats=True)
+        dts.append((st.dt_last, st.ne_max))
+    for (dt_a, _), (dt_b, ne) in zip(dts[:-1], dts[1:]):
+        assert dt_b <= 2e-12 * (1 + 1e-12)
+        assert dt_b <= 2.0 * dt_a * (1 + 1e-12)
+    # a dense plasma (ne ~ 1e21) has a dielectric relaxation time below 2 ps
+    ne_max = max(ne for _, ne in dts[:-1])
+    assert ne_max > 1e20
+    assert min(dt for dt, _ in dts[1:]) <= 8.8541878128e-12 / (1.602176634e-19 * ne_max * mu) * 1.5
