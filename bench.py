@@ -68,6 +68,19 @@ def workload(n_cells=128, n_initial=1_000_000):
     return wl
 
 
+def aggregate(ms: float, updates: float, dist=None, device="cpu"):
+    """Whole-job figures of N replicas: the slowest rank's time and the sum of
+    all ranks' particle-updates (weak scaling: every rank runs its own
+    streamer with its own seed)."""
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([float(updates)], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -259,14 +272,9 @@ def main():
     ms = sum(a.elapsed_time(b) for a, b in ev)
     prof = ctx.profile(False)
     u1, p1, s1 = ctx.progress()
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    upd_t = torch.tensor([float(u1 - u0)], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(upd_t, op=dist.ReduceOp.SUM)
-    ms_max = float(ms_t.item())
+    ms_max, upd_all = aggregate(ms, u1 - u0, dist, device="cuda")
     fin = ctx.step(0, stats=True)
-    value = float(upd_t.item()) / (ms_max * 1e-3)
+    value = upd_all / (ms_max * 1e-3)
 
     # dominant kernel: the parent push (gather + push + MCC + deposit)
     parents_per_launch = (p1 - p0) / max(prof["n_push"], 1)
