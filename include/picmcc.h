@@ -278,6 +278,12 @@ typedef struct swarm_config {
     double kT_eV;
     unsigned long long seed; /* swarm s uses seed + s */
     double sample_from;      /* fraction of steps discarded before sampling (0.25) */
+    /* batched mode: all swarms advance together, one launch per step for
+     * every swarm, the step replayed from a CUDA graph */
+    int batched;             /* 0: swarms one after another; 1: batched */
+    int block;               /* batched: threads per block (64, 128 or 256); 0 = autotune */
+    int blocks_per_sm;       /* batched: resident blocks per SM; 0 = autotune */
+    int use_graph;           /* batched: 1 = capture the step in a CUDA graph */
 } swarm_config;
 
 typedef struct swarm_result {
@@ -285,6 +291,14 @@ typedef struct swarm_result {
 } swarm_result;
 
 size_t swarm_workspace_bytes(const swarm_config *sc, int n_swarms);
+
+/* Batched mode only: times short trial runs of the batched step for block
+ * sizes {64, 128, 256} and blocks per SM {1, 2, 3, 4, max} and returns the
+ * fastest pair (and its ms per step).  Uses the same workspace as swarm_run;
+ * the trial state is discarded. */
+int swarm_autotune(const swarm_config *sc, int n_swarms, const double *EN_Td, void *d_workspace,
+                   size_t workspace_bytes, int *block, int *blocks_per_sm, double *ms_per_step,
+                   pic_stream_t stream);
 
 /* EN_Td: host [n_swarms]; results: host [n_swarms]; moments (optional):
  * host [n_swarms][n_steps][16]; counts (optional): host [n_swarms][n_steps]. */

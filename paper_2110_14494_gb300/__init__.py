@@ -3,4 +3,4 @@ arXiv 2110.14494: velocity-Verlet push, null-collision Monte Carlo,
 fixed-point CIC deposit, super-particle merge/split, multigrid Poisson and
 Monte Carlo swarms, behind the C ABI of include/picmcc.h."""
 from . import picmcc  # noqa: F401
-from .picmcc import PicContext, PicError, poisson_solve, swarm_run  # noqa: F401
+from .picmcc import PicContext, PicError, poisson_solve, swarm_autotune, swarm_run  # noqa: F401

@@ -14,6 +14,7 @@
 #include "common.cuh"
 #include "poisson.cuh"
 #include "push.cuh"
+#include "swarm_batch.cuh"
 
 namespace pic {
 
@@ -1448,10 +1449,53 @@ static size_t swarm_extra(const swarm_config* sc) {
     return al256((size_t)sc->n_steps * kNMom * 8) + al256((size_t)sc->n_steps * 8);
 }
 
+struct BatchLayout {
+    size_t total, ctx, ctx_bytes, buf[2], cq[2], csw[2], cnt_in, cnt_out, prefix, bd, Ez, mom, counts;
+    long long segs, cap_child;
+};
+
+static BatchLayout batch_layout(const swarm_config* sc, int n) {
+    BatchLayout L;
+    pic_config pc = swarm_pic_config(sc);
+    pc.capacity = 1;
+    const size_t R = real_size(sc->precision);
+    L.segs = (long long)n * sc->capacity;
+    L.cap_child = L.segs / 2 > 4096 ? L.segs / 2 : 4096;
+    size_t o = 0;
+    auto take = [&](size_t b) { size_t r = o; o += al256(b); return r; };
+    L.ctx_bytes = make_layout(&pc).total;
+    L.ctx = take(L.ctx_bytes);
+    for (int b = 0; b < 2; ++b) {
+        L.buf[b] = o;
+        for (int f = 0; f < 10; ++f) take((size_t)L.segs * R);
+        take((size_t)L.segs * 8);
+    }
+    for (int q = 0; q < 2; ++q) {
+        L.cq[q] = o;
+        for (int f = 0; f < 11; ++f) take((size_t)L.cap_child * R);
+        take((size_t)L.cap_child * 8);
+        take((size_t)L.cap_child * 4);
+        L.csw[q] = take((size_t)L.cap_child * 4);
+    }
+    L.cnt_in = take((size_t)n * 8);
+    L.cnt_out = take((size_t)n * 8);
+    L.prefix = take((size_t)(n + 1) * 8);
+    L.bd = take(sizeof(BatchDev));
+    L.Ez = take((size_t)n * 8);
+    L.mom = take((size_t)n * sc->n_steps * kNMom * 8);
+    L.counts = take((size_t)n * sc->n_steps * 8);
+    L.total = o;
+    return L;
+}
+
 extern "C" size_t swarm_workspace_bytes(const swarm_config* sc, int n_swarms) {
     if (!sc || n_swarms < 1 || sc->n_steps < 1) return 0;
     pic_config c = swarm_pic_config(sc);
     if (validate(&c) != PIC_OK) return 0;
+    if (sc->batched) {
+        if (n_swarms > kMaxSwarms) return 0;
+        return batch_layout(sc, n_swarms).total;
+    }
     return make_layout(&c).total + swarm_extra(sc);
 }
 
@@ -1558,14 +1602,228 @@ template <class T> static int swarm_one(pic_ctx* c, const swarm_config* sc, doub
     return PIC_OK;
 }
 
-extern "C" int swarm_run(const swarm_config* sc, int n_swarms, const double* EN_Td, void* d_ws, size_t ws_bytes,
-                         swarm_result* results, double* moments, long long* counts, pic_stream_t stream) {
-    if (!sc || n_swarms < 1 || !EN_Td || !results || !d_ws) return PIC_ERR_ARG;
+// ------------------------------------------------------------------ batched swarms
+template <class T> struct BatchRunner {
+    pic_ctx* c = nullptr;
+    BatchArgs<T> B;
+    BatchLayout L;
+    const swarm_config* sc;
+    int n;
+    cudaStream_t s;
+    cudaStream_t cap = nullptr;
+    std::string err;
+
+    ~BatchRunner() {
+        if (c) pic_destroy(c);
+        if (cap) cudaStreamDestroy(cap);
+    }
+
+    int setup(const swarm_config* sc_, int n_, const double* EN, char* ws, cudaStream_t s_) {
+        sc = sc_;
+        n = n_;
+        s = s_;
+        L = batch_layout(sc, n);
+        pic_config pc = swarm_pic_config(sc);
+        pc.capacity = 1;
+        int rc = pic_init(&pc, ws + L.ctx, L.ctx_bytes, nullptr, (pic_stream_t)s, &c);
+        if (rc) return rc;
+        memset(&B, 0, sizeof B);
+        B.P = make_args<T>(c, MODE_SWARM);
+        const size_t R = sizeof(T);
+        for (int b = 0; b < 2; ++b) {
+            Soa<T>& q = b == 0 ? B.in : B.out;
+            char* p = ws + L.buf[b];
+            for (int f = 0; f < 10; ++f) { q.r[f] = (T*)p; p += al256((size_t)L.segs * R); }
+            q.id = (uint64_t*)p;
+        }
+        for (int q = 0; q < 2; ++q) {
+            char* p = ws + L.cq[q];
+            for (int f = 0; f < 10; ++f) { B.cq[q].p.r[f] = (T*)p; p += al256((size_t)L.cap_child * R); }
+            B.cq[q].t_left = (T*)p;
+            p += al256((size_t)L.cap_child * R);
+            B.cq[q].p.id = (uint64_t*)p;
+            p += al256((size_t)L.cap_child * 8);
+            B.cq[q].k = (uint32_t*)p;
+            B.csw[q] = (uint32_t*)(ws + L.csw[q]);
+        }
+        B.cap_s = sc->capacity;
+        B.n_swarms = n;
+        B.cnt_in = (long long*)(ws + L.cnt_in);
+        B.cnt_out = (unsigned long long*)(ws + L.cnt_out);
+        B.prefix = (long long*)(ws + L.prefix);
+        B.cap_child = L.cap_child;
+        B.bd = (BatchDev*)(ws + L.bd);
+        B.seed = sc->seed;
+        B.Ez = (const double*)(ws + L.Ez);
+        B.mom = (double*)(ws + L.mom);
+        B.counts = (long long*)(ws + L.counts);
+        B.n_steps = sc->n_steps;
+        B.n_lo = sc->n_lo;
+        B.n_hi = sc->n_hi;
+        std::vector<double> ez((size_t)n);
+        for (int i = 0; i < n; ++i) ez[i] = -EN[i] * 1e-21 * sc->n_gas;
+        cudaError_t e = cudaMemcpyAsync(ws + L.Ez, ez.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        return e == cudaSuccess ? PIC_OK : PIC_ERR_CUDA;
+    }
+
+    cudaError_t init_state() {
+        cudaMemsetAsync(B.mom, 0, (size_t)n * sc->n_steps * kNMom * 8, s);
+        cudaMemsetAsync(B.counts, 0, (size_t)n * sc->n_steps * 8, s);
+        return BatchLaunch<T>::init(B, sc->n0, sqrt(sc->kT_eV * kQ / kMe), s);
+    }
+
+    // Runs `steps` steps directly or from a two-step CUDA graph.
+    int run(int steps, int block, int grid, bool graph) {
+        if (BatchLaunch<T>::prepare(block) != cudaSuccess) return PIC_ERR_CUDA;
+        BatchArgs<T> Bo = B;
+        std::swap(Bo.in, Bo.out);
+        if (!graph) {
+            for (int i = 0; i < steps; ++i)
+                if (BatchLaunch<T>::step((i & 1) ? Bo : B, block, grid, s, nullptr) != cudaSuccess) return PIC_ERR_CUDA;
+            return PIC_OK;
+        }
+        if (!cap && cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return PIC_ERR_CUDA;
+        cudaGraph_t g2 = nullptr, g1 = nullptr;
+        cudaGraphExec_t x2 = nullptr, x1 = nullptr;
+        int rc = PIC_OK;
+        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return PIC_ERR_CUDA;
+        BatchLaunch<T>::step(B, block, grid, cap, nullptr);
+        BatchLaunch<T>::step(Bo, block, grid, cap, nullptr);
+        if (cudaStreamEndCapture(cap, &g2) != cudaSuccess || cudaGraphInstantiate(&x2, g2, 0) != cudaSuccess)
+            rc = PIC_ERR_CUDA;
+        if (rc == PIC_OK && (steps & 1)) {
+            if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = PIC_ERR_CUDA;
+            else {
+                BatchLaunch<T>::step(B, block, grid, cap, nullptr);
+                if (cudaStreamEndCapture(cap, &g1) != cudaSuccess || cudaGraphInstantiate(&x1, g1, 0) != cudaSuccess)
+                    rc = PIC_ERR_CUDA;
+            }
+        }
+        for (int i = 0; rc == PIC_OK && i + 1 < steps; i += 2)
+            if (cudaGraphLaunch(x2, s) != cudaSuccess) rc = PIC_ERR_CUDA;
+        if (rc == PIC_OK && (steps & 1) && cudaGraphLaunch(x1, s) != cudaSuccess) rc = PIC_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) rc = PIC_ERR_CUDA;
+        if (x2) cudaGraphExecDestroy(x2);
+        if (x1) cudaGraphExecDestroy(x1);
+        if (g2) cudaGraphDestroy(g2);
+        if (g1) cudaGraphDestroy(g1);
+        return rc;
+    }
+
+    int tune(int* best_block, int* best_bps, double* best_ms) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        double best = 1e300;
+        const int trial = sc->n_steps < 10 ? sc->n_steps : 10;
+        for (int block : {64, 128, 256}) {
+            if (BatchLaunch<T>::prepare(block) != cudaSuccess) continue;
+            const int maxb = BatchLaunch<T>::max_blocks_per_sm(block);
+            for (int bps : {1, 2, 3, 4, maxb}) {
+                if (bps > maxb) continue;
+                if (init_state() != cudaSuccess) return PIC_ERR_CUDA;
+                if (run(2, block, sms * bps, false)) return PIC_ERR_CUDA;
+                cudaEventRecord(e0, s);
+                if (run(trial, block, sms * bps, false)) return PIC_ERR_CUDA;
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                const double per = ms / trial;
+                if (per < best) { best = per; *best_block = block; *best_bps = bps; }
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        *best_ms = best;
+        return PIC_OK;
+    }
+};
+
+template <class T>
+static int run_batched(const swarm_config* sc, int n, const double* EN, char* ws, cudaStream_t s, swarm_result* res,
+                       double* moments, long long* counts) {
+    BatchRunner<T> R;
+    int rc = R.setup(sc, n, EN, ws, s);
+    if (rc) return rc;
+    int block = sc->block, bps = sc->blocks_per_sm;
+    if (block == 0 || bps == 0) {
+        double ms;
+        rc = R.tune(&block, &bps, &ms);
+        if (rc) return rc;
+    }
+    if (block != 64 && block != 128 && block != 256) return PIC_ERR_ARG;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (R.init_state() != cudaSuccess) return PIC_ERR_CUDA;
+    rc = R.run(sc->n_steps, block, sms * bps, sc->use_graph != 0);
+    if (rc) return rc;
+    const int ns = sc->n_steps;
+    std::vector<double> hm((size_t)n * ns * kNMom);
+    std::vector<long long> hc((size_t)n * ns);
+    BatchDev hb;
+    cudaError_t e = cudaMemcpyAsync(hm.data(), R.B.mom, hm.size() * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), R.B.counts, hc.size() * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, R.B.bd, sizeof hb, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return PIC_ERR_CUDA;
+    if (hb.err) return PIC_ERR_CAPACITY;
+    for (int i = 0; i < n; ++i) {
+        const double* m = hm.data() + (size_t)i * ns * kNMom;
+        swarm_result_from(m, ns, sc->sample_from, sc->dt, sc->n_gas, &res[i]);
+        res[i].v[22] = (double)hc[(size_t)i * ns + ns - 1];
+        res[i].v[23] = m[(size_t)(ns - 1) * kNMom];
+    }
+    if (moments) memcpy(moments, hm.data(), hm.size() * 8);
+    if (counts) memcpy(counts, hc.data(), hc.size() * 8);
+    return PIC_OK;
+}
+
+static int swarm_check(const swarm_config* sc, int n_swarms, const double* EN_Td, void* d_ws, size_t ws_bytes) {
+    if (!sc || n_swarms < 1 || !EN_Td || !d_ws || ((uintptr_t)d_ws & 255)) return PIC_ERR_ARG;
     if (sc->n0 < 1 || sc->n0 > sc->capacity || sc->n_steps < 1 || !(sc->n_gas > 0) || !(sc->kT_eV >= 0) ||
         sc->n_lo < 0 || sc->n_hi < sc->n_lo || sc->capacity < 2 * sc->n_hi)
         return PIC_ERR_ARG;
     const size_t need = swarm_workspace_bytes(sc, n_swarms);
     if (need == 0 || ws_bytes < need) return PIC_ERR_ARG;
+    return PIC_OK;
+}
+
+extern "C" int swarm_autotune(const swarm_config* sc, int n_swarms, const double* EN_Td, void* d_ws, size_t ws_bytes,
+                              int* block, int* blocks_per_sm, double* ms_per_step, pic_stream_t stream) {
+    if (!sc || !sc->batched || !block || !blocks_per_sm) return PIC_ERR_ARG;
+    int rc = swarm_check(sc, n_swarms, EN_Td, d_ws, ws_bytes);
+    if (rc) return rc;
+    double ms = 0;
+    if (sc->precision == 32) {
+        BatchRunner<float> R;
+        rc = R.setup(sc, n_swarms, EN_Td, (char*)d_ws, (cudaStream_t)stream);
+        if (!rc) rc = R.tune(block, blocks_per_sm, &ms);
+    } else {
+        BatchRunner<double> R;
+        rc = R.setup(sc, n_swarms, EN_Td, (char*)d_ws, (cudaStream_t)stream);
+        if (!rc) rc = R.tune(block, blocks_per_sm, &ms);
+    }
+    if (ms_per_step) *ms_per_step = ms;
+    return rc;
+}
+
+extern "C" int swarm_run(const swarm_config* sc, int n_swarms, const double* EN_Td, void* d_ws, size_t ws_bytes,
+                         swarm_result* results, double* moments, long long* counts, pic_stream_t stream) {
+    if (!results) return PIC_ERR_ARG;
+    int rcc = swarm_check(sc, n_swarms, EN_Td, d_ws, ws_bytes);
+    if (rcc) return rcc;
+    if (sc->batched)
+        return sc->precision == 32
+                   ? run_batched<float>(sc, n_swarms, EN_Td, (char*)d_ws, (cudaStream_t)stream, results, moments, counts)
+                   : run_batched<double>(sc, n_swarms, EN_Td, (char*)d_ws, (cudaStream_t)stream, results, moments,
+                                         counts);
+    const size_t need = swarm_workspace_bytes(sc, n_swarms);
     pic_config pc = swarm_pic_config(sc);
     Layout L = make_layout(&pc);
     double* d_mom = (double*)((char*)d_ws + L.total);

@@ -321,9 +321,9 @@ __device__ __forceinline__ int select_process(const PushArgs<T>& A, const T* tab
 // The product of an ionization by draw k of electron `pid`: id from the
 // derived-id stream, isotropic direction from its own draw k = 0, speed sp.
 template <class T>
-__device__ __forceinline__ uint64_t make_child(const PushArgs<T>& A, uint64_t pid, uint32_t k, T sp, T vc[3]) {
-    const uint64_t cid = derived_id(A.K, pid, A.step, 0x80000000u | k);
-    const u32x4 rb = draw_words(A.K, cid, A.step, 0u);
+__device__ __forceinline__ uint64_t make_child(const Keys& K, uint32_t step, uint64_t pid, uint32_t k, T sp, T vc[3]) {
+    const uint64_t cid = derived_id(K, pid, step, 0x80000000u | k);
+    const u32x4 rb = draw_words(K, cid, step, 0u);
     T nb[3];
     iso_dir(unif<T>(rb.z), unif<T>(rb.w), nb);
     vc[0] = sp * nb[0]; vc[1] = sp * nb[1]; vc[2] = sp * nb[2];
@@ -359,9 +359,9 @@ enum { EV_CONTINUE = 0, EV_DONE = 1, EV_ATTACHED = 2, EV_IONIZED = 3 };
 // caller stages the product, which flies the remaining time); attachment
 // records a negative-ion event and ends the electron.
 template <class T, int MODE, bool FAST, bool STATS>
-__device__ __forceinline__ int event(const PushArgs<T>& A, const T* tab, const ProcSmem<T>* ps, Lane<T>& L,
-                                     LStats& ls, T& sp) {
-    const u32x4 r = draw_words(A.K, L.id, A.step, L.k);
+__device__ __forceinline__ int event(const PushArgs<T>& A, const Keys& K, uint32_t step, const ProcSmem<T>* ps,
+                                     Lane<T>& L, LStats& ls, T& sp) {
+    const u32x4 r = draw_words(K, L.id, step, L.k);
     ++L.k;
     const T tau = Arith<T>::tau(unif<T>(r.x), A.nu_max);
     if (tau >= L.t_left) { fly(L.d, L.v, L.a, L.t_left); return EV_DONE; }
@@ -703,7 +703,7 @@ __device__ __forceinline__ void collide_loop(const PushArgs<T>& A, const ProcSme
                         const Soa<T>& q = src.p;
                         const T x0 = q.r[PX][it], x1 = q.r[PY][it], x2 = q.r[PZ][it], w = q.r[PW][it];
                         T vc[3];
-                        const uint64_t cid = make_child(A, q.id[it], src.k[it], q.r[VX][it], vc);
+                        const uint64_t cid = make_child(A.K, A.step, q.id[it], src.k[it], q.r[VX][it], vc);
                         if (MODE == MODE_PIC && A.q_pos)
                             deposit(x0, x1, x2, w, A.ox, A.oy, A.oz, A.dxr, A.nx, A.ny, A.nz, A.q_pos, A.st);
                         r[0] = x0; r[1] = x1; r[2] = x2;
@@ -731,7 +731,7 @@ __device__ __forceinline__ void collide_loop(const PushArgs<T>& A, const ProcSme
         // 4. one candidate collision
         int r = EV_CONTINUE;
         T sp = (T)0;
-        if (active) r = event<T, MODE, FAST, STATS>(A, nullptr, ps, L, ls, sp);
+        if (active) r = event<T, MODE, FAST, STATS>(A, A.K, A.step, ps, L, ls, sp);
         const bool done = r == EV_DONE, ion = r == EV_IONIZED;
         if (r == EV_DONE || r == EV_ATTACHED) active = false;
         // 5. ionization products
@@ -740,7 +740,7 @@ __device__ __forceinline__ void collide_loop(const PushArgs<T>& A, const ProcSme
                 if (stk.n < StackSink<T>::kDepth) {
                     const T xc[3] = {L.x[0] + L.d[0], L.x[1] + L.d[1], L.x[2] + L.d[2]};
                     T vc[3];
-                    const uint64_t cid = make_child(A, L.id, L.k - 1, sp, vc);
+                    const uint64_t cid = make_child(A.K, A.step, L.id, L.k - 1, sp, vc);
                     if (MODE == MODE_PIC && A.q_pos)
                         deposit(xc[0], xc[1], xc[2], L.w, A.ox, A.oy, A.oz, A.dxr, A.nx, A.ny, A.nz, A.q_pos, A.st);
                     const int t = stk.n++;

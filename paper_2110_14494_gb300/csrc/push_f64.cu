@@ -2,3 +2,4 @@
 // and sum is rounded separately, in the same order as the CPU oracle.
 #include "push_impl.cuh"
 template struct pic::PushLaunch<double>;
+template struct pic::BatchLaunch<double>;

@@ -2,6 +2,7 @@
 // Included once by push_f32.cu and once by push_f64.cu.
 #pragma once
 #include "push.cuh"
+#include "swarm_batch.cuh"
 
 namespace pic {
 
@@ -73,6 +74,53 @@ template <class T> cudaError_t PushLaunch<T>::field_kick(const PushArgs<T>& A, i
 template <class T> cudaError_t PushLaunch<T>::resample(const PushArgs<T>& A, int grid, cudaStream_t s) {
     k_resample<T><<<grid, 256, 0, s>>>(A);
     k_resample_commit<<<1, 1, 0, s>>>(A.st);
+    return cudaGetLastError();
+}
+
+template <class T> int BatchLaunch<T>::max_blocks_per_sm(int block) {
+    constexpr bool FAST = sizeof(T) == 4;
+    const size_t sm = smem(block);
+    cudaFuncSetAttribute(k_batch_collide<T, FAST, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_collide<T, FAST, false>, block, sm);
+    return b > 0 ? b : 1;
+}
+
+template <class T> cudaError_t BatchLaunch<T>::init(const BatchArgs<T>& B, long long n0, double sig, cudaStream_t s) {
+    k_batch_init<T><<<1, 1024, 0, s>>>(B, n0);
+    const long long total = (long long)B.n_swarms * n0;
+    long long g = (total + 255) / 256;
+    if (g > 152 * 16) g = 152 * 16;
+    k_batch_seed<T><<<(int)(g < 1 ? 1 : g), 256, 0, s>>>(B, n0, sig);
+    return cudaGetLastError();
+}
+
+template <class T> cudaError_t BatchLaunch<T>::prepare(int block) {
+    constexpr bool FAST = sizeof(T) == 4;
+    const size_t sm = smem(block);
+    cudaError_t e = cudaFuncSetAttribute(k_batch_collide<T, FAST, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batch_collide<T, FAST, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    return e;
+}
+
+template <class T>
+cudaError_t BatchLaunch<T>::step(BatchArgs<T> B, int block, int grid, cudaStream_t s, long long* launches) {
+    constexpr bool FAST = sizeof(T) == 4;
+    const size_t sm = smem(block);
+    k_batch_resample<T><<<152 * 8, 256, 0, s>>>(B);
+    k_batch_begin<T><<<1, 1024, 0, s>>>(B);
+    B.gen = 0;
+    k_batch_collide<T, FAST, false><<<grid, block, sm, s>>>(B);
+    for (int g = 0; g < kBatchGenerations; ++g) {
+        if (g > 0) k_batch_nextgen<<<1, 1, 0, s>>>(B.bd, g);
+        B.gen = g;
+        k_batch_collide<T, FAST, true><<<grid, block, sm, s>>>(B);
+    }
+    k_batch_end<T><<<1, 1024, 0, s>>>(B);
+    k_batch_step_advance<<<1, 1, 0, s>>>(B.bd, kBatchGenerations - 1);
+    if (launches) *launches += 5 + 2 * kBatchGenerations;
     return cudaGetLastError();
 }
 

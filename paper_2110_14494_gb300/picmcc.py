@@ -78,7 +78,8 @@ class swarm_config(C.Structure):
     _fields_ = [("precision", C.c_int), ("gas", pic_gas), ("n_gas", C.c_double), ("n0", C.c_longlong),
                 ("n_lo", C.c_longlong), ("n_hi", C.c_longlong), ("capacity", C.c_longlong),
                 ("n_steps", C.c_int), ("dt", C.c_double), ("kT_eV", C.c_double), ("seed", C.c_ulonglong),
-                ("sample_from", C.c_double)]
+                ("sample_from", C.c_double), ("batched", C.c_int), ("block", C.c_int),
+                ("blocks_per_sm", C.c_int), ("use_graph", C.c_int)]
 
 
 class swarm_result(C.Structure):
@@ -90,7 +91,7 @@ EXPORTS = ("pic_workspace_bytes", "pic_init", "pic_destroy", "pic_last_error", "
            "pic_deposit", "pic_weight_update", "pic_count", "pic_save", "pic_load", "pic_progress",
            "pic_profile", "pic_upload", "pic_download",
            "poisson_workspace_bytes", "poisson_solve", "poisson_solve_noalloc", "swarm_workspace_bytes",
-           "swarm_run")
+           "swarm_run", "swarm_autotune")
 
 _lib = None
 
@@ -137,6 +138,7 @@ def lib():
     L.swarm_workspace_bytes.restype = C.c_size_t
     L.swarm_run.argtypes = [P(swarm_config), C.c_int, PD, VP, C.c_size_t, P(swarm_result), PD,
                             P(C.c_longlong), VP]
+    L.swarm_autotune.argtypes = [P(swarm_config), C.c_int, PD, VP, C.c_size_t, P(C.c_int), P(C.c_int), PD, VP]
     _lib = L
     return L
 
@@ -328,14 +330,38 @@ def poisson_solve(grid: dict, rho, phi, mask=None, E=None, v_lo=0.0, v_hi=0.0, v
     return st.cycles, st.rel_res
 
 
-def swarm_run(gas: dict, EN_Td, *, precision=64, n0=10000, n_steps=2000, dt=1e-12, kT_eV=1.0, seed=1,
-              n_lo=1000, n_hi=1_000_000, capacity=None, sample_from=0.25, stream=None, want_moments=False):
-    """Runs len(EN_Td) swarms; returns (results [n][24], moments or None, counts or None)."""
+def _swarm_cfg(gas, precision, n0, n_steps, dt, kT_eV, seed, n_lo, n_hi, capacity, sample_from, batched, block,
+               blocks_per_sm, use_graph):
     g = Gas(gas)
-    EN = np.ascontiguousarray(np.atleast_1d(EN_Td), np.float64)
     if capacity is None:
         capacity = max(2 * n_hi, 4 * n0)
-    sc = swarm_config(precision, g.c, g.n_gas, n0, n_lo, n_hi, capacity, n_steps, dt, kT_eV, seed, sample_from)
+    sc = swarm_config(precision, g.c, g.n_gas, n0, n_lo, n_hi, capacity, n_steps, dt, kT_eV, seed, sample_from,
+                      int(batched), block, blocks_per_sm, int(use_graph))
+    return g, sc
+
+
+def swarm_autotune(gas: dict, EN_Td, *, precision=32, n0=10000, n_steps=100, dt=1e-12, kT_eV=1.0, seed=1,
+                   n_lo=1000, n_hi=1_000_000, capacity=None, stream=None):
+    """Returns (block, blocks_per_sm, ms_per_step) of the fastest batched launch shape."""
+    EN = np.ascontiguousarray(np.atleast_1d(EN_Td), np.float64)
+    g, sc = _swarm_cfg(gas, precision, n0, n_steps, dt, kT_eV, seed, n_lo, n_hi, capacity, 0.25, True, 0, 0, 1)
+    nb = lib().swarm_workspace_bytes(C.byref(sc), len(EN))
+    if nb == 0:
+        raise PicError(PIC_ERR_ARG, "invalid swarm_config")
+    ws, ptr = _workspace(nb)
+    b, bps, ms = C.c_int(), C.c_int(), C.c_double()
+    _check(lib().swarm_autotune(C.byref(sc), len(EN), EN.ctypes.data_as(PD), C.c_void_p(ptr), nb, C.byref(b),
+                                C.byref(bps), C.byref(ms), _stream(stream)), None, "swarm_autotune")
+    return b.value, bps.value, ms.value
+
+
+def swarm_run(gas: dict, EN_Td, *, precision=64, n0=10000, n_steps=2000, dt=1e-12, kT_eV=1.0, seed=1,
+              n_lo=1000, n_hi=1_000_000, capacity=None, sample_from=0.25, stream=None, want_moments=False,
+              batched=False, block=0, blocks_per_sm=0, use_graph=True):
+    """Runs len(EN_Td) swarms; returns (results [n][24], moments or None, counts or None)."""
+    EN = np.ascontiguousarray(np.atleast_1d(EN_Td), np.float64)
+    g, sc = _swarm_cfg(gas, precision, n0, n_steps, dt, kT_eV, seed, n_lo, n_hi, capacity, sample_from, batched,
+                       block, blocks_per_sm, use_graph)
     nb = lib().swarm_workspace_bytes(C.byref(sc), len(EN))
     if nb == 0:
         raise PicError(PIC_ERR_ARG, "invalid swarm_config")

@@ -227,12 +227,12 @@ def test_adaptive_time_step_bounds():
     from paper_2110_14494_gb300 import PicContext
     grid = W.grid_spec(32, 32, 32, 2e-5)
     gas = W.synthetic_air()
-    mu = 0.06
+    mu = 0.5   # a mobility estimate large enough that dt_drt < 2 ps while the first 2 ps step is still stable
     ctx = PicContext(gas, grid, precision=32, capacity=2_000_000, seed=SEED, dt=2e-12, coupled=True, v_lo=0.0,
                      v_hi=1000.0, v_mask=1000.0, adaptive_dt=True, cfl=0.5, mobility=mu, max_growth=1.2,
-                     boundary=1)
+                     boundary=1, growth_trigger=1.25, particle_cap=600_000)
     L = 32 * 2e-5
-    ctx.seed_gaussian(2e21, 8e-5, (0.5 * L, 0.5 * L, 0.5 * L), 2e4)
+    ctx.seed_gaussian(2e20, 8e-5, (0.5 * L, 0.5 * L, 0.5 * L), 2e3)
     dts = []
     for _ in range(12):
         st = ctx.step(1, stats=True)
@@ -240,7 +240,7 @@ def test_adaptive_time_step_bounds():
     for (dt_a, _), (dt_b, ne) in zip(dts[:-1], dts[1:]):
         assert dt_b <= 2e-12 * (1 + 1e-12)
         assert dt_b <= 2.0 * dt_a * (1 + 1e-12)
-    # a dense plasma (ne ~ 1e21) has a dielectric relaxation time below 2 ps
+    # a dense plasma (ne ~ 2e20) has a dielectric relaxation time eps0/(e ne mu) below 2 ps
     ne_max = max(ne for _, ne in dts[:-1])
-    assert ne_max > 1e20
+    assert ne_max > 5e19
     assert min(dt for dt, _ in dts[1:]) <= 8.8541878128e-12 / (1.602176634e-19 * ne_max * mu) * 1.5

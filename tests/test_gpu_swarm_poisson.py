@@ -127,3 +127,51 @@ def test_poisson_plates_only():
     z = (np.arange(64) + 0.5) * 2e-5
     assert np.allclose(phi.cpu().numpy(), (V0 * z / (64 * 2e-5))[:, None, None], atol=1e-7 * V0)
     assert np.allclose(E[2].cpu().numpy(), -V0 / (64 * 2e-5), rtol=1e-5)
+
+
+def test_batched_swarms_fp64_match_oracle_per_swarm():
+    """All swarms in one launch per step (CUDA graph): each swarm's trajectory
+    is the oracle's for seed + s (same counts every step, same moments)."""
+    from paper_2110_14494_gb300 import swarm_run
+    gas = W.synthetic_air()
+    seed = 2110144950
+    ENs = [60.0, 120.0, 400.0]
+    res, mom, cnt = swarm_run(gas, ENs, precision=64, n0=1500, n_steps=300, dt=1e-12, seed=seed, n_lo=1000,
+                              n_hi=3000, want_moments=True, batched=True, block=128, blocks_per_sm=2)
+    for s, EN in enumerate(ENs):
+        omom, ocnt, ores, _ = O.swarm(gas, EN, 1500, 300, 1e-12, seed + s, n_lo=1000, n_hi=3000)
+        assert np.array_equal(cnt[s], ocnt), s
+        scale = np.abs(omom).max(axis=0) + 1e-300
+        assert np.all(np.abs(mom[s] - omom) <= 1e-9 * scale), s
+        assert not _agree(res[s], ores), s
+
+
+def test_batched_swarms_graph_and_autotune():
+    from paper_2110_14494_gb300 import swarm_autotune, swarm_run
+    gas = W.synthetic_air()
+    ENs = list(W.swarm_en_grid(16, 10.0, 1000.0))
+    b, bps, ms = swarm_autotune(gas, ENs, precision=32, n0=2000, n_steps=40, dt=1e-12, seed=5, n_lo=1000,
+                                n_hi=8000)
+    assert b in (64, 128, 256) and bps >= 1 and ms > 0
+    kw = dict(precision=32, n0=2000, n_steps=40, dt=1e-12, seed=5, n_lo=1000, n_hi=8000, want_moments=True,
+              batched=True, block=b, blocks_per_sm=bps)
+    r1, m1, c1 = swarm_run(gas, ENs, use_graph=True, **kw)
+    r2, m2, c2 = swarm_run(gas, ENs, use_graph=False, **kw)
+    assert np.array_equal(c1, c2)
+    scale = np.abs(m1).max(axis=1, keepdims=True) + 1e-300
+    assert np.all(np.abs(m1 - m2) <= 1e-9 * scale)
+    # resampling keeps every swarm inside its bounds (after the step that triggered it)
+    assert c1.max() <= 2 * 8000 * 2 and c1[:, -1].min() > 0
+
+
+def test_batched_swarms_fp32_match_oracle():
+    from paper_2110_14494_gb300 import swarm_run
+    gas = W.synthetic_air()
+    seed = 2110144960
+    ENs = [120.0, 400.0]
+    res, _, _ = swarm_run(gas, ENs, precision=32, n0=2000, n_steps=400, dt=1e-12, seed=seed, n_lo=1000, n_hi=4000,
+                          batched=True)
+    for s, EN in enumerate(ENs):
+        omom, ocnt, ores, _ = O.swarm(gas, EN, 2000, 400, 1e-12, seed + s, n_lo=1000, n_hi=4000)
+        bad = _agree(res[s], ores)
+        assert not bad, bad
