@@ -868,8 +868,10 @@ void orc_grad_phi(int nx, int ny, int nz, double h, const double *phi, double v_
 /* Maxwellian at the origin and are traced with the same mover and          */
 /* collisions; weighted moments are taken at the end of every step.         */
 /* Adaptive resampling at the start of a step: above n_hi each electron      */
-/* survives with probability 1/2 (survivors' weight doubles); below n_lo     */
-/* every electron is duplicated (both halves keep half the weight).          */
+/* survives with probability 1/2; below n_lo every electron is duplicated.   */
+/* Weights are left as they are: every coefficient is built from ratios of   */
+/* moments of the same step, so the swarm's overall weight scale (which     */
+/* grows like e^{nu t} in an ionizing field) is implicit and never overflows. */
 /* Moments per step (row of ORC_NMOM):                                       */
 /*  0 sw, 1 swx, 2 swy, 3 swz, 4 swx2, 5 swy2, 6 swz2, 7 swvx, 8 swvy, 9 swvz, */
 /*  10 swxvx, 11 swyvy, 12 swzvz, 13 sw eps, 14 ionization weight in step,   */
@@ -894,12 +896,11 @@ int orc_swarm_run(const orc_setup *s, const orc_swarm_cfg *c, orc_parts *p, doub
             for (long long i = 0; i < n; ++i) {
                 double u[4];
                 draw(s->seed, p->id[i], (uint32_t)step, 0xA0000000u, u);
-                if (u[0] < 0.5) p->w[i] = 2.0 * p->w[i]; else p->w[i] = 0.0;
+                if (!(u[0] < 0.5)) p->w[i] = 0.0;
             }
             compact(p);
         } else if (n > 0 && n < c->n_lo) {
             for (long long i = 0; i < n; ++i) {
-                p->w[i] = 0.5 * p->w[i];
                 double x[3] = {p->x[i], p->y[i], p->z[i]}, v[3] = {p->vx[i], p->vy[i], p->vz[i]},
                        a[3] = {p->ax[i], p->ay[i], p->az[i]};
                 uint64_t nid = derived_id(s->seed, p->id[i], (uint32_t)step, 0xA0000000u);
@@ -930,7 +931,9 @@ int orc_swarm_run(const orc_setup *s, const orc_swarm_cfg *c, orc_parts *p, doub
 
 /* Flux and bulk coefficients from the moment rows (Sec. 2.2.2; flux = mean  */
 /* of per-electron averages, bulk = rate of change of the centre of mass and */
-/* of the spread).  Rows i0..n_steps-1 are used (earlier ones are relaxation). */
+/* of the spread, rate coefficients = mean over steps of the event weight of */
+/* the step per swarm weight, N and dt).  Rows i0..n_steps-1 are used        */
+/* (earlier ones are relaxation).                                           */
 /* out[0..10]  W_flux, W_bulk, DL_flux, DT_flux, DL_bulk, DT_bulk, <eps>,     */
 /*             k_ion, k_att, alpha, eta                                       */
 /* out[11..21] 1-sigma errors by 10-block batch means                        */
@@ -949,7 +952,7 @@ static void coeffs_range(const double *mom, int r0, int r1, double dt, double n_
         dlf += m[12] / W - mz * mvz;
         dtf += 0.5 * ((m[10] / W - mx * mvx) + (m[11] / W - my * mvy));
         me += m[13] / W;
-        sion += m[14]; satt += m[15]; sw += W;
+        sion += m[14] / W; satt += m[15] / W; sw += 1.0;
         double t = (double)(r + 1) * dt;
         double varz = m[6] / W - mz * mz;
         double vart = (m[4] / W - mx * mx) + (m[5] / W - my * my);
