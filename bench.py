@@ -52,6 +52,11 @@ def parse():
     ap.add_argument("--trace", action="store_true", help="per-step statistics (diagnostics, slower kernels)")
     ap.add_argument("--boundary", type=int, default=1, help="0: reflect at the domain faces, 1: absorb (outflow)")
     ap.add_argument("--fixed-dt", action="store_true", help="keep dt = 2 ps (no time-step control)")
+    ap.add_argument("--workload", default="streamer", choices=["streamer", "swarms"],
+                    help="streamer: the coupled 128^3 step (headline); swarms: 256 batched swarms")
+    ap.add_argument("--swarm-block", type=int, default=0, help="batched swarms: block size (0 = autotune)")
+    ap.add_argument("--swarm-bps", type=int, default=0, help="batched swarms: blocks per SM (0 = autotune)")
+    ap.add_argument("--no-f64", action="store_true", help="batched swarms: skip the float64 comparison")
     return ap.parse_args()
 
 
@@ -203,10 +208,60 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_swarms(args):
+    """256 swarms, E/N log-spaced 10-1000 Td, 1e4 float32 electrons each, adaptive
+    resampling in [1e3, 1e6], dt = 1 ps: batched (one launch per step, CUDA graph,
+    autotuned launch shape) against the plain float64 path (swarms one after
+    another) on a subset."""
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    import workloads as W
+    from paper_2110_14494_gb300 import swarm_autotune, swarm_run
+    gas = W.synthetic_air()
+    ENs = W.swarm_en_grid(256, 10.0, 1000.0)
+    steps = args.steps if args.steps != 1990 else 5000
+    t0 = time.perf_counter()
+    if args.swarm_block and args.swarm_bps:
+        b, bps, ms_trial = args.swarm_block, args.swarm_bps, None
+    else:
+        b, bps, ms_trial = swarm_autotune(gas, ENs, precision=32, n0=10000, n_steps=steps, dt=1e-12,
+                                          seed=2110144943, n_lo=1000, n_hi=1_000_000)
+    t_tune = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res, mom, cnt = swarm_run(gas, ENs, precision=32, n0=10000, n_steps=steps, dt=1e-12, seed=2110144943, n_lo=1000,
+                              n_hi=1_000_000, want_moments=True, batched=True, block=b, blocks_per_sm=bps)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    updates = float(cnt.sum())
+    # plain float64 path (one swarm after another) on 4 of the 256 E/N values, 500 steps
+    sub = ENs[::64]
+    t0 = time.perf_counter()
+    if args.no_f64:
+        c64, w64 = np.zeros(1), 1.0
+    else:
+        r64, _, c64 = swarm_run(gas, sub, precision=64, n0=10000, n_steps=500, dt=1e-12, seed=2110144943,
+                                n_lo=1000, n_hi=1_000_000, want_moments=True)
+    w64 = time.perf_counter() - t0
+    out = {"metric": "batched swarms particle-updates/s (256 E/N, float32, one launch per step)",
+           "value": updates / wall, "unit": UNIT, "n_gpus": 1, "steps": steps, "wall_s": wall,
+           "tuning": {"block": b, "blocks_per_sm": bps, "trial_ms_per_step": ms_trial, "tune_s": t_tune},
+           "particles_per_step": {"mean": float(cnt.mean(axis=0).mean() * 256), "final": int(cnt[:, -1].sum())},
+           "plain_f64_sequential": {"value": float(c64.sum()) / w64, "unit": UNIT, "swarms": len(sub),
+                                    "steps": 500, "wall_s": w64},
+           "results_sample": {f"{ENs[i]:.1f}Td": {"W_flux": res[i][0], "W_bulk": res[i][1], "alpha": res[i][9],
+                                                  "eta": res[i][10], "mean_eps": res[i][6]}
+                              for i in (0, 64, 128, 192, 255)}}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "swarms":
+        return run_swarms(args)
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

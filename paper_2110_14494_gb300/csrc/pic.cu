@@ -1450,7 +1450,7 @@ static size_t swarm_extra(const swarm_config* sc) {
 }
 
 struct BatchLayout {
-    size_t total, ctx, ctx_bytes, buf[2], cq[2], csw[2], cnt_in, cnt_out, prefix, bd, Ez, mom, counts;
+    size_t total, ctx, ctx_bytes, buf[2], cq[2], csw[2], cnt_in, cnt_out, prefix, bd, Ez, mom, counts, zref, zhist;
     long long segs, cap_child;
 };
 
@@ -1484,6 +1484,8 @@ static BatchLayout batch_layout(const swarm_config* sc, int n) {
     L.Ez = take((size_t)n * 8);
     L.mom = take((size_t)n * sc->n_steps * kNMom * 8);
     L.counts = take((size_t)n * sc->n_steps * 8);
+    L.zref = take((size_t)n * 8);
+    L.zhist = take((size_t)n * sc->n_steps * 8);
     L.total = o;
     return L;
 }
@@ -1500,8 +1502,9 @@ extern "C" size_t swarm_workspace_bytes(const swarm_config* sc, int n_swarms) {
 }
 
 // Flux = time average of per-step electron averages; bulk = least-squares
-// slopes of the centre of mass and of the spread; rate coefficients =
-// event weight / (N * integral of the swarm weight); errors from 10 blocks.
+// slopes of the centre of mass and of the spread; rate coefficients = time
+// average of (event weight of the step) / (N dt swarm weight); errors from
+// 10-block batch means.
 static void swarm_coeffs(const double* mom, int r0, int r1, double dt, double n_gas, double* o) {
     const int n = r1 - r0;
     double wf = 0, dlf = 0, dtf = 0, me = 0, sion = 0, satt = 0, sw = 0;
@@ -1515,9 +1518,9 @@ static void swarm_coeffs(const double* mom, int r0, int r1, double dt, double n_
         dlf += m[12] / W - mz * vz;
         dtf += 0.5 * ((m[10] / W - mx * vx) + (m[11] / W - my * vy));
         me += m[13] / W;
-        sion += m[14];
-        satt += m[15];
-        sw += W;
+        sion += m[14] / W;
+        satt += m[15] / W;
+        sw += 1.0;
         const double t = (double)(r + 1) * dt;
         const double varz = m[6] / W - mz * mz;
         const double vart = (m[4] / W - mx * mx) + (m[5] / W - my * my);
@@ -1657,6 +1660,8 @@ template <class T> struct BatchRunner {
         B.Ez = (const double*)(ws + L.Ez);
         B.mom = (double*)(ws + L.mom);
         B.counts = (long long*)(ws + L.counts);
+        B.zref = (double*)(ws + L.zref);
+        B.zref_hist = (double*)(ws + L.zhist);
         B.n_steps = sc->n_steps;
         B.n_lo = sc->n_lo;
         B.n_hi = sc->n_hi;
@@ -1764,15 +1769,25 @@ static int run_batched(const swarm_config* sc, int n, const double* EN, char* ws
     rc = R.run(sc->n_steps, block, sms * bps, sc->use_graph != 0);
     if (rc) return rc;
     const int ns = sc->n_steps;
-    std::vector<double> hm((size_t)n * ns * kNMom);
+    std::vector<double> hm((size_t)n * ns * kNMom), hz((size_t)n * ns);
     std::vector<long long> hc((size_t)n * ns);
     BatchDev hb;
     cudaError_t e = cudaMemcpyAsync(hm.data(), R.B.mom, hm.size() * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hz.data(), R.B.zref_hist, hz.size() * 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), R.B.counts, hc.size() * 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, R.B.bd, sizeof hb, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return PIC_ERR_CUDA;
     if (hb.err) return PIC_ERR_CAPACITY;
+    // z moments back to the origin: z = dz + r
+    for (size_t r = 0; r < (size_t)n * ns; ++r) {
+        double* m = hm.data() + r * kNMom;
+        const double ref = hz[r];
+        const double m0 = m[0], m3 = m[3], m9 = m[9];
+        m[6] = m[6] + 2.0 * ref * m3 + ref * ref * m0;
+        m[3] = m3 + ref * m0;
+        m[12] = m[12] + ref * m9;
+    }
     for (int i = 0; i < n; ++i) {
         const double* m = hm.data() + (size_t)i * ns * kNMom;
         swarm_result_from(m, ns, sc->sample_from, sc->dt, sc->n_gas, &res[i]);

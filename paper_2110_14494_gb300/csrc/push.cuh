@@ -471,9 +471,9 @@ __global__ void __launch_bounds__(256) k_field_kick(const PushArgs<T> A) {
 
 // Swarm resampling in place (decided from the count after the previous step):
 // above n_hi each electron survives with probability 1/2 (draw keyed by id,
-// step and 0xA0000000) and doubles its weight, the others get weight 0;
-// below n_lo every electron is halved and a copy with a derived id is
-// appended after the last one.
+// step and 0xA0000000), the others get weight 0; below n_lo every electron
+// gets a copy with a derived id, appended after the last one.  Weights are
+// not rescaled: the coefficients are ratios of moments of the same step.
 template <class T>
 __global__ void k_resample(const PushArgs<T> A) {
     const long long n = (long long)A.st->n_in;
@@ -485,15 +485,12 @@ __global__ void k_resample(const PushArgs<T> A) {
     }
     const Soa<T>& p = A.in;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const T w = p.r[PW][i];
         if (thin) {
             const u32x4 r = draw_words(A.K, p.id[i], A.step, 0xA0000000u);
-            p.r[PW][i] = unif<T>(r.x) < (T)0.5 ? (T)2 * w : (T)0;
+            if (!(unif<T>(r.x) < (T)0.5)) p.r[PW][i] = (T)0;
         } else {
             const long long j = n + i;
             for (int f = 0; f < 10; ++f) p.r[f][j] = p.r[f][i];
-            p.r[PW][i] = (T)0.5 * w;
-            p.r[PW][j] = (T)0.5 * w;
             p.id[j] = derived_id(A.K, p.id[i], A.step, 0xA0000000u);
         }
     }

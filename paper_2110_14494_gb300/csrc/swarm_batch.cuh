@@ -37,7 +37,9 @@ template <class T> struct BatchArgs {
     BatchDev* bd;
     uint64_t seed;              // swarm s: seed + s
     const double* Ez;           // [n_swarms] field along z (negative: electrons drift to +z)
-    double* mom;                // [n_swarms][n_steps][kNMom]
+    double* mom;                // [n_swarms][n_steps][kNMom], z moments about the step's reference zref
+    double* zref;               // [n_swarms] reference z of the current step (previous centre of mass)
+    double* zref_hist;          // [n_swarms][n_steps] reference used for each step's moments
     long long* counts;          // [n_swarms][n_steps]
     int n_steps;
     long long n_lo, n_hi;
@@ -80,15 +82,12 @@ template <class T> __global__ void k_batch_resample(const BatchArgs<T> B) {
         const long long i = s * B.cap_s + (it - B.prefix[s]);
         const Keys K = dev_keys(B.seed + (uint64_t)s);
         const Soa<T>& p = B.in;
-        const T w = p.r[PW][i];
         if (thin) {
             const u32x4 r = draw_words(K, p.id[i], step, 0xA0000000u);
-            p.r[PW][i] = unif<T>(r.x) < (T)0.5 ? (T)2 * w : (T)0;
+            if (!(unif<T>(r.x) < (T)0.5)) p.r[PW][i] = (T)0;
         } else {
             const long long j = i + n;
             for (int f = 0; f < 10; ++f) p.r[f][j] = p.r[f][i];
-            p.r[PW][i] = (T)0.5 * w;
-            p.r[PW][j] = (T)0.5 * w;
             p.id[j] = derived_id(K, p.id[i], step, 0xA0000000u);
         }
     }
@@ -126,10 +125,12 @@ template <class T> __device__ void scan_counts(const BatchArgs<T>& B) {
 // After resampling: duplicated swarms double their counts, prefix sums of the
 // step's work items, cursors and output counters reset.  One block.
 template <class T> __global__ void k_batch_begin(const BatchArgs<T> B) {
+    const uint32_t step = B.bd->step;
     for (int s = threadIdx.x; s < B.n_swarms; s += blockDim.x) {
         const long long n = B.cnt_in[s];
         if (n > 0 && n < B.n_lo && 2 * n <= B.cap_s) B.cnt_in[s] = 2 * n;
         B.cnt_out[s] = 0;
+        if (step >= 1 && (int)step <= B.n_steps) B.zref_hist[(size_t)s * B.n_steps + (step - 1)] = B.zref[s];
     }
     __syncthreads();
     scan_counts(B);
@@ -156,7 +157,11 @@ template <class T> __global__ void k_batch_end(const BatchArgs<T> B) {
         unsigned long long n = B.cnt_out[s];
         if (n > (unsigned long long)B.cap_s) n = (unsigned long long)B.cap_s;
         B.cnt_in[s] = (long long)n;
-        if (step >= 1 && (int)step <= B.n_steps) B.counts[(size_t)s * B.n_steps + (step - 1)] = (long long)n;
+        if (step >= 1 && (int)step <= B.n_steps) {
+            B.counts[(size_t)s * B.n_steps + (step - 1)] = (long long)n;
+            const double* row = B.mom + ((size_t)s * B.n_steps + (step - 1)) * kNMom;
+            if (row[0] > 0.0) B.zref[s] += row[3] / row[0];
+        }
     }
     __syncthreads();
     scan_counts(B);
@@ -167,6 +172,7 @@ template <class T> __global__ void k_batch_init(const BatchArgs<T> B, long long 
     for (int s = threadIdx.x; s < B.n_swarms; s += blockDim.x) {
         B.cnt_in[s] = n0;
         B.cnt_out[s] = 0;
+        B.zref[s] = 0.0;
     }
     __syncthreads();
     scan_counts(B);
@@ -209,38 +215,82 @@ static __global__ void k_batch_step_advance(BatchDev* bd, int g_last) {
     bd->step += 1;
 }
 
-// Adds a lane's moment contributions to its swarm's row (all lanes call):
-// a warp-wide reduction when all 32 lanes carry electrons of one swarm (the
-// common case: items are contiguous per swarm), per-lane atomics otherwise.
+constexpr long long kWarpChunk = 1024;  // largest warp-private item range
+
+template <class T> struct BatchStage {
+    T in[32 * kRow];
+    T out[kOut * kRow];
+    T ch[kCh * kRow];
+    uint64_t in_id[32], out_id[kOut], ch_id[kCh];
+    uint32_t ch_k[kCh];
+    int in_s[32], out_s[kOut], ch_s[kCh];
+    double macc[14];   // the warp's running moment sums for swarm macc_s (step macc_t)
+    int macc_s;
+};
+
+// Moment contributions of the lanes' electrons (all lanes call).  When all
+// 32 lanes carry electrons of one swarm (the common case: items are
+// contiguous per swarm) the warp reduces them and keeps the running sums in
+// its stage, writing them to the swarm's row only when the warp moves on to
+// another swarm (or ends); mixed warps add per lane.
+template <class T> __device__ __forceinline__ void macc_flush(const BatchArgs<T>& B, BatchStage<T>* sg, uint32_t step) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    if (sg->macc_s >= 0 && lane < 14) {
+        double* row = B.mom + ((size_t)sg->macc_s * B.n_steps + (step - 1)) * kNMom;
+        if (sg->macc[lane] != 0.0) atomicAdd(row + lane, sg->macc[lane]);
+        sg->macc[lane] = 0.0;
+    }
+    __syncwarp();
+}
+
 template <class T>
-__device__ __forceinline__ void swarm_moments(const BatchArgs<T>& B, bool live, int s, const T x[3], const T v[3],
-                                              T wt, uint32_t step) {
-    double m[14];
+__device__ __forceinline__ void swarm_moments(const BatchArgs<T>& B, BatchStage<T>* sg, bool live, int s, const T x[3],
+                                              const T v[3], T wt, uint32_t step) {
+    // z about the swarm's reference point: the moments of a drifting swarm
+    // stay small, so float sums lose nothing to cancellation
+    T m[14];
     if (live) {
-        const double w = wt, X = x[0], Y = x[1], Z = x[2], U = v[0], V = v[1], W = v[2];
+        const T w = wt, X = x[0], Y = x[1], Z = x[2] - (T)B.zref[s], U = v[0], V = v[1], W = v[2];
         m[0] = w; m[1] = w * X; m[2] = w * Y; m[3] = w * Z;
         m[4] = w * X * X; m[5] = w * Y * Y; m[6] = w * Z * Z;
         m[7] = w * U; m[8] = w * V; m[9] = w * W;
         m[10] = w * X * U; m[11] = w * Y * V; m[12] = w * Z * W;
-        m[13] = w * (0.5 * kMe * (U * U + V * V + W * W) / kQ);
+        m[13] = w * ((T)(0.5 * kMe / kQ) * (U * U + V * V + W * W));
     } else {
-        for (int q = 0; q < 14; ++q) m[q] = 0.0;
+        for (int q = 0; q < 14; ++q) m[q] = (T)0;
     }
-    const unsigned grp = __match_any_sync(kFull, live ? s : -1);
-    const bool uniform = __all_sync(kFull, live && grp == kFull);
-    if (uniform) {
+    // segmented warp reduction: one pass per distinct swarm among the lanes
+    // (one pass in the common case), the sums kept in the warp's stage for
+    // the swarm it works on and added directly for any other
+    unsigned todo = __ballot_sync(kFull, live);
+    while (todo) {
+        const int leader = __ffs(todo) - 1;
+        const int sg_s = __shfl_sync(kFull, s, leader);
+        const bool mine = live && s == sg_s;
+        todo &= ~__ballot_sync(kFull, mine);
+        T red[14];
         for (int q = 0; q < 14; ++q) {
-            double v2 = m[q];
+            T v2 = mine ? m[q] : (T)0;
             for (int o = 16; o > 0; o >>= 1) v2 += __shfl_xor_sync(kFull, v2, o);
-            m[q] = v2;
+            red[q] = v2;
         }
-        if ((threadIdx.x & 31) == 0) {
-            double* row = B.mom + ((size_t)s * B.n_steps + (step - 1)) * kNMom;
-            for (int q = 0; q < 14; ++q) atomicAdd(row + q, m[q]);
+        if (sg->macc_s != sg_s && (sg->macc_s < 0 || todo == 0)) {
+            // the warp has moved on to another swarm: write the old sums out
+            macc_flush(B, sg, step);
+            if ((threadIdx.x & 31) == 0) sg->macc_s = sg_s;
+            __syncwarp();
         }
-    } else if (live) {
-        double* row = B.mom + ((size_t)s * B.n_steps + (step - 1)) * kNMom;
-        for (int q = 0; q < 14; ++q) atomicAdd(row + q, m[q]);
+        const int lane = threadIdx.x & 31;
+        double add = 0.0;
+        for (int k = 0; k < 14; ++k)
+            if (k == lane) add = (double)red[k];
+        if (sg->macc_s == sg_s) {
+            if (lane < 14) sg->macc[lane] += add;
+        } else if (lane < 14 && add != 0.0) {
+            atomicAdd(B.mom + ((size_t)sg_s * B.n_steps + (step - 1)) * kNMom + lane, add);
+        }
+        __syncwarp();
     }
 }
 
@@ -252,15 +302,6 @@ __device__ __forceinline__ void flush_event_weights(const BatchArgs<T>& B, int s
     if (ls.w_att != 0.0) atomicAdd(row + 15, ls.w_att);
     ls.w_ion = ls.w_att = 0.0;
 }
-
-template <class T> struct BatchStage {
-    T in[32 * kRow];
-    T out[kOut * kRow];
-    T ch[kCh * kRow];
-    uint64_t in_id[32], out_id[kOut], ch_id[kCh];
-    uint32_t ch_k[kCh];
-    int in_s[32], out_s[kOut], ch_s[kCh];
-};
 
 template <class T> constexpr size_t batch_smem(int warps) { return (size_t)warps * sizeof(BatchStage<T>); }
 
@@ -299,7 +340,7 @@ __device__ __forceinline__ void batch_flush_out(const BatchArgs<T>& B, BatchStag
             atomicOr(&B.bd->err, kErrOutCapacity);
         }
     }
-    swarm_moments(B, stored, s, x, v, w, step);
+    swarm_moments(B, sg, stored, s, x, v, w, step);
     __syncwarp();
     const int rest = n - cnt;
     if (lane < rest) {
@@ -365,6 +406,9 @@ __global__ void __launch_bounds__(256) k_batch_collide(const BatchArgs<T> B) {
     __syncthreads();
     BatchStage<T>* sg = reinterpret_cast<BatchStage<T>*>(smem_raw) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
+    if (lane < 14) sg->macc[lane] = 0.0;
+    if (lane == 0) sg->macc_s = -1;
+    __syncwarp();
     const unsigned lt = (1u << lane) - 1u;
     const uint32_t step = B.bd->step;
     const int srcq = B.gen & 1, dstq = srcq ^ 1;
@@ -383,7 +427,8 @@ __global__ void __launch_bounds__(256) k_batch_collide(const BatchArgs<T> B) {
     ls.zero();
     Lane<T> L;
     Keys K = dev_keys(B.seed);
-    int s_cur = -1;
+    int s_cur = -1, s_cache = -1;
+    long long w_next = 0, w_end = 0;
     bool active = false, dry = false;
     int in_head = 0, in_count = 0, n_out = 0, n_ch = 0;
     StackSink<T> stk;
@@ -427,15 +472,32 @@ __global__ void __launch_bounds__(256) k_batch_collide(const BatchArgs<T> B) {
         }
         if (in_head >= in_count && !dry) {
             __syncwarp();
-            unsigned long long b = 0;
-            if (lane == 0) b = atomicAdd(cursor, 32ull);
-            b = __shfl_sync(kFull, b, 0);
-            if ((long long)b >= n_items) {
+            if (w_next >= w_end) {
+                // a new warp-private range: large while much work is left (so a
+                // warp's electrons share a swarm), shrinking towards 32 at the end
+                unsigned long long b = 0, g = 32;
+                if (lane == 0) {
+                    const unsigned long long seen = *(volatile unsigned long long*)cursor;
+                    const long long rem = n_items - (long long)seen;
+                    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+                    long long want_g = rem > 0 ? rem / (4 * warps) : 32;
+                    want_g = want_g < 32 ? 32 : (want_g > kWarpChunk ? kWarpChunk : want_g);
+                    g = (unsigned long long)(want_g & ~31ll);
+                    b = atomicAdd(cursor, g);
+                }
+                b = __shfl_sync(kFull, b, 0);
+                g = __shfl_sync(kFull, g, 0);
+                w_next = (long long)b;
+                w_end = (long long)(b + g) < n_items ? (long long)(b + g) : n_items;
+            }
+            const long long b = w_next;
+            if (b >= n_items) {
                 dry = true;
                 in_head = in_count = 0;
             } else {
-                const long long left = n_items - (long long)b;
+                const long long left = w_end - b;
                 const int cnt = left < 32 ? (int)left : 32;
+                w_next = b + cnt;
                 if (lane < cnt) {
                     const long long it = (long long)b + lane;
                     T* r = sg->in + lane * kRow;
@@ -452,7 +514,9 @@ __global__ void __launch_bounds__(256) k_batch_collide(const BatchArgs<T> B) {
                         sg->in_id[lane] = cid;
                         sg->in_s[lane] = s;
                     } else {
-                        const int s = swarm_of(B.prefix, B.n_swarms, it);
+                        int s = s_cache;
+                        if (s < 0 || it < B.prefix[s] || it >= B.prefix[s + 1]) s = swarm_of(B.prefix, B.n_swarms, it);
+                        s_cache = s;
                         const long long i = s * B.cap_s + (it - B.prefix[s]);
                         for (int f = 0; f < 6; ++f) r[f] = B.in.r[f][i];
                         r[9] = B.in.r[PW][i];
@@ -537,6 +601,7 @@ __global__ void __launch_bounds__(256) k_batch_collide(const BatchArgs<T> B) {
     }
     if (n_out > 0) batch_flush_out(B, sg, n_out, n_out, step);
     if (!CHILD && n_ch > 0) batch_flush_children(B, sg, n_ch, n_ch, 0);
+    macc_flush(B, sg, step);
     flush_event_weights(B, s_cur, step, ls);
 }
 

@@ -158,8 +158,10 @@ def test_batched_swarms_graph_and_autotune():
     r1, m1, c1 = swarm_run(gas, ENs, use_graph=True, **kw)
     r2, m2, c2 = swarm_run(gas, ENs, use_graph=False, **kw)
     assert np.array_equal(c1, c2)
+    # float32 warp partial sums depend on which electrons share a flush (set
+    # by the order warps take work), so the moments agree to float rounding
     scale = np.abs(m1).max(axis=1, keepdims=True) + 1e-300
-    assert np.all(np.abs(m1 - m2) <= 1e-9 * scale)
+    assert np.all(np.abs(m1 - m2) <= 1e-6 * scale)
     # resampling keeps every swarm inside its bounds (after the step that triggered it)
     assert c1.max() <= 2 * 8000 * 2 and c1[:, -1].min() > 0
 
