@@ -212,14 +212,22 @@ int pic_load(pic_ctx *ctx, const void *host_blob, size_t bytes);
 /* -lap(phi) = rho / eps0 (Sec. 2.5; the sign printed there is read as a
  * typo) on the cell-centred grid: Dirichlet phi = v_lo at the z = origin
  * face and v_hi at the top face (ghost 2 phi_b - phi), homogeneous Neumann on
- * the x and y faces, cells with mask != 0 held at v_mask.  Geometric
- * multigrid V-cycles on the error equation in float32 inside a float64
- * residual (defect correction) until ||b - A phi|| / ||b|| <= rtol.
- * E = -grad(phi) by central differences at cell centres (float32). */
+ * the x and y faces, cells with mask != 0 held at v_mask.  Flexible CG
+ * preconditioned by a float32 geometric-multigrid V(2,2)-cycle until the
+ * CG residual satisfies ||b - A phi|| / ||b|| <= rtol; the Krylov part runs
+ * in float64 or, with precision 32, in float32 on a correction to a
+ * float-pair potential (see poisson_config).  E = -grad(phi) by central
+ * differences at cell centres (float32).  Coupled PIC contexts use the
+ * float64 variant with precision 64 and the float-pair one with 32. */
 typedef struct poisson_config {
     int nx, ny, nz;           /* as for pic_config with coupled != 0; unsupported sizes give PIC_ERR_ARG */
     double dx;
     double v_lo, v_hi, v_mask;
+    int precision;            /* 0 or 64: CG in float64; 32: the potential as a pair of floats (about
+                                 48 bits) with the correction found by CG in float32 and iterative
+                                 refinement: no float64 arithmetic in the iterations.  Both use the
+                                 float32 V-cycle preconditioner.  The pair residual bounds the reachable
+                                 rtol near 1e-9 relative for 32. */
 } poisson_config;
 
 typedef struct poisson_stats {
@@ -241,8 +249,8 @@ int poisson_solve(const poisson_config *pc, const double *rho, const uint8_t *ma
  * deployment convenience.  The multigrid scratch is a fixed 32 MiB device
  * array inside the library (held on every GPU that loads it until the
  * process exits), enough for grids of up to about 0.95 million cells (96^3
- * fits, 100^3 does not); larger grids return PIC_ERR_CAPACITY and touch
- * nothing.  The first call on
+ * fits, 100^3 does not, at either precision); larger grids return
+ * PIC_ERR_CAPACITY and touch nothing.  The first call on
  * a device looks up that array's device address (cudaGetSymbolAddress) with
  * the device current, so make the first call on each device outside any
  * stream capture.  Every call shares the one array: calls that can overlap

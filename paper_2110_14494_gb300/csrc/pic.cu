@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -219,6 +220,15 @@ __global__ void k_fixed_to_rho(const long long* __restrict__ qe, const long long
         const double ne = (double)qe[c] * inv, np = (double)qp[c] * inv, nn = (double)qn[c] * inv;
         rho[c] = kQ * (np - nn - ne);
     }
+}
+
+// Right-hand side of the float32 solve: h^2 rho / eps0 in float, the three
+// fixed-point charges combined in 64-bit integers first (exact) and
+// converted once.
+__global__ void k_fixed_to_hrho(const long long* __restrict__ qe, const long long* __restrict__ qp,
+                                const long long* __restrict__ qn, long long n, float scale, float* __restrict__ hrho) {
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+        hrho[c] = scale * __ll2float_rn(qp[c] - qn[c] - qe[c]);
 }
 
 // Next step's input count; cursors that ran past the capacity (an error
@@ -604,8 +614,8 @@ static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
     size_t total = 0;
-    size_t buf[2], cq[2], table, table64, E4, qe, qp, qn, st, cnt, start, sums, key, rank, msc, gas, rho, phi, phi_prev, mg,
-        hostio;
+    size_t buf[2], cq[2], table, table64, E4, qe, qp, qn, st, cnt, start, sums, key, rank, msc, gas, rho, phi, phi_prev,
+        phi_x, mg, hostio;
 };
 
 static size_t real_size(int prec) { return prec == 64 ? 8 : 4; }
@@ -647,7 +657,8 @@ static Layout make_layout(const pic_config* c) {
     L.rho = take(ncell * 8);
     L.phi = take(ncell * 8);
     L.phi_prev = take(ncell * 8);
-    L.mg = take(MG::bytes(c->nx, c->ny, c->nz));
+    L.phi_x = take(ncell * 8);
+    L.mg = take(MG::bytes(c->nx, c->ny, c->nz, c->precision == 32, false));
     L.hostio = 0;
     L.total = o;
     return L;
@@ -733,6 +744,15 @@ struct pic_ctx {
     unsigned long long* qn() { return (unsigned long long*)(ws + L.qn); }
     double* rho() { return (double*)(ws + L.rho); }
     double* phi() { return (double*)(ws + L.phi); }
+    // float32 contexts keep the potential as float pairs ([hi][lo], n each)
+    // in three rotating slots: the current solution, the previous one and
+    // the warm-start guess.
+    int ph_cur = 0, ph_prev = 1, ph_free = 2;
+    float* ph_hi(int slot) {
+        const size_t o = slot == 0 ? L.phi : (slot == 1 ? L.phi_prev : L.phi_x);
+        return (float*)(ws + o);
+    }
+    float* ph_lo(int slot) { return ph_hi(slot) + g.ncell(); }
     MergeScratch msc() {
         MergeScratch m;
         const size_t cap = (size_t)cfg.capacity;
@@ -853,6 +873,8 @@ extern "C" int pic_init(const pic_config* cfg, void* d_ws, size_t ws_bytes, cons
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.qp, 0, ncell * 8, c->s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.qn, 0, ncell * 8, c->s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.phi, 0, ncell * 8, c->s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.phi_prev, 0, ncell * 8, c->s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.phi_x, 0, ncell * 8, c->s);
     if (e != cudaSuccess) { rc = c->cuda_fail(e, "pic_init"); delete c; return rc; }
     rc = build_table(c);
     if (rc) { delete c; return rc; }
@@ -863,7 +885,7 @@ extern "C" int pic_init(const pic_config* cfg, void* d_ws, size_t ws_bytes, cons
                                   : PushLaunch<double>::blocks_per_sm(MODE_PIC, c->n_bins);
     c->grid_push = sms * bps;
     if (cfg->coupled) {
-        c->mg.carve(c->ws + L.mg, cfg->nx, cfg->ny, cfg->nz);
+        c->mg.carve(c->ws + L.mg, cfg->nx, cfg->ny, cfg->nz, c->prec == 32, false);
         c->mg.persistent = true;
     }
     *out = c;
@@ -1076,7 +1098,37 @@ static void fixed_to_rho(pic_ctx* c, double* rho) {
 
 // Coupled field: rho from the fixed-point grids, multigrid Poisson (warm
 // started from the previous potential), packed E for the next gather.
+static int solve_field_pair(pic_ctx* c) {
+    const long long n = c->g.ncell();
+    const double dV = c->g.dx * c->g.dx * c->g.dx;
+    const double scale = kQ / (4294967296.0 * dV) * c->g.dx * c->g.dx / kEps0;
+    k_fixed_to_hrho<<<grid_n(n), 256, 0, c->s>>>((const long long*)c->qe(), (const long long*)c->qp(),
+                                                  (const long long*)c->qn(), n, (float)scale, (float*)c->rho());
+    ++c->launches;
+    const long long l0 = c->mg.launches;
+    // guess in the free slot; the solution goes to the previous one's slot
+    c->mg.extrapolate_pair(c->ph_hi(c->ph_cur), c->ph_lo(c->ph_cur), c->ph_hi(c->ph_prev), c->ph_lo(c->ph_prev),
+                           c->ph_hi(c->ph_free), c->ph_lo(c->ph_free), (int)n, c->n_solves >= 2, c->s);
+    c->n_solves++;
+    double hn[2];
+    int rc = c->mg.solve_mixed(c->rho(), false, c->mask, c->ph_hi(c->ph_free), c->ph_lo(c->ph_free),
+                               c->ph_hi(c->ph_prev), c->ph_lo(c->ph_prev), c->n_solves <= 2, c->g.dx,
+                               c->cfg.v_lo, c->cfg.v_hi,
+                               c->cfg.v_mask, c->cfg.poisson_rtol, c->cfg.poisson_max_cycles,
+                               (float*)(c->ws + c->L.E4), nullptr, nullptr, nullptr, c->s, &c->last_cycles,
+                               &c->last_rel, hn);
+    if (rc == PIC_ERR_CUDA) return c->fail(rc, "poisson solve: CUDA error");
+    if (rc == PIC_ERR_TIMEOUT) return c->fail(rc, "poisson solve: cycle limit reached");
+    if (rc) return c->fail(rc, "poisson solve");
+    std::swap(c->ph_cur, c->ph_prev);
+    c->launches += c->mg.launches - l0;
+    c->field_valid = 1;
+    c->field_uniform = 0;
+    return PIC_OK;
+}
+
 static int solve_field(pic_ctx* c) {
+    if (c->prec == 32) return solve_field_pair(c);
     fixed_to_rho(c, c->rho());
     k_extrapolate<<<grid_n(c->g.ncell()), 256, 0, c->s>>>(c->phi(), (double*)(c->ws + c->L.phi_prev), c->g.ncell(),
                                                            c->n_solves >= 2 ? 1 : 0);
@@ -1341,6 +1393,29 @@ extern "C" int pic_deposit(pic_ctx* c, int64_t* q_e, int64_t* q_pos, int64_t* q_
 }
 
 // ---------------------------------------------------------------- checkpoint
+// The blob holds the potential in float64; float32 contexts convert from and
+// to their float pairs on the host (hi + lo is exact in float64).
+static cudaError_t save_phi(pic_ctx* c, double* out) {
+    const size_t n = (size_t)c->g.ncell();
+    if (c->prec != 32) return cudaMemcpy(out, c->phi(), n * 8, cudaMemcpyDeviceToHost);
+    std::vector<float> hl(2 * n);
+    cudaError_t e = cudaMemcpy(hl.data(), c->ph_hi(c->ph_cur), 2 * n * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return e;
+    for (size_t i = 0; i < n; ++i) out[i] = (double)hl[i] + (double)hl[n + i];
+    return cudaSuccess;
+}
+
+static cudaError_t load_phi(pic_ctx* c, const double* in) {
+    const size_t n = (size_t)c->g.ncell();
+    if (c->prec != 32) return cudaMemcpy(c->phi(), in, n * 8, cudaMemcpyHostToDevice);
+    std::vector<float> hl(2 * n);
+    for (size_t i = 0; i < n; ++i) {
+        hl[i] = (float)in[i];
+        hl[n + i] = (float)(in[i] - (double)hl[i]);
+    }
+    return cudaMemcpy(c->ph_hi(c->ph_cur), hl.data(), 2 * n * 4, cudaMemcpyHostToDevice);
+}
+
 struct BlobHead {
     uint64_t magic;
     int32_t prec, a_valid;
@@ -1377,7 +1452,7 @@ extern "C" int pic_save(pic_ctx* c, void* blob, size_t* bytes) {
     p += ncell * 8;
     if (e == cudaSuccess) e = cudaMemcpy(p, c->qn(), ncell * 8, cudaMemcpyDeviceToHost);
     p += ncell * 8;
-    if (e == cudaSuccess) e = cudaMemcpy(p, c->phi(), ncell * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = save_phi(c, (double*)p);
     if (e != cudaSuccess) return c->cuda_fail(e, "save");
     *bytes = need;
     return PIC_OK;
@@ -1408,7 +1483,7 @@ extern "C" int pic_load(pic_ctx* c, const void* blob, size_t bytes) {
     p += ncell * 8;
     if (e == cudaSuccess) e = cudaMemcpy(c->qn(), p, ncell * 8, cudaMemcpyHostToDevice);
     p += ncell * 8;
-    if (e == cudaSuccess) e = cudaMemcpy(c->phi(), p, ncell * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = load_phi(c, (const double*)p);
     if (e != cudaSuccess) return c->cuda_fail(e, "load");
     k_set_count<<<1, 1, 0, c->s>>>(c->st(), (unsigned long long)n);
     c->n_host = (long long)n;

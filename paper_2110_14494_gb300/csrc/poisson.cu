@@ -205,25 +205,61 @@ __global__ void k_update_p(double* __restrict__ p, const float* __restrict__ z, 
     if (c < n) p[c] = b != 0.0 ? (double)z[c] + b * p[c] : (double)z[c];
 }
 
+// Neighbour sum of the correction e, which is zero on electrode cells at
+// every level (they are never updated, and prolongation writes 0 there), so
+// the masks of the neighbours need not be read: all six loads are issued
+// together.  Domain faces add nothing to the sum and change the diagonal as
+// in nb_sum; the additions run in the same order, so the result is the same.
+__device__ __forceinline__ float nb_sum_e(const float* __restrict__ e, int i, int j, int k, int nx, int ny, int nz,
+                                          int c, float& diag) {
+    const int pl = nx * ny;
+    const float xm = i > 0 ? e[c - 1] : 0.0f, xp = i < nx - 1 ? e[c + 1] : 0.0f;
+    const float ym = j > 0 ? e[c - nx] : 0.0f, yp = j < ny - 1 ? e[c + nx] : 0.0f;
+    const float zm = k > 0 ? e[c - pl] : 0.0f, zp = k < nz - 1 ? e[c + pl] : 0.0f;
+    diag = 6.0f - (float)((i == 0) + (i == nx - 1) + (j == 0) + (j == ny - 1)) + (float)((k == 0) + (k == nz - 1));
+    return ((((xm + xp) + ym) + yp) + zm) + zp;
+}
+
+__device__ __forceinline__ float inv_diag(float diag) { return diag == 6.0f ? (1.0f / 6.0f) : 1.0f / diag; }
+
 // One colour of red-black Gauss-Seidel for A e = g (masked cells stay 0).
-// Thread (ii, j, k) handles cell i = 2 ii + ((j + k + colour) & 1).
-__global__ void k_smooth(float* __restrict__ e, const float* __restrict__ g, const uint8_t* __restrict__ mask, int nx,
-                         int ny, int nz, int color) {
-    const int j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
-    const int i = 2 * (blockIdx.x * BX + threadIdx.x) + ((j + k + color) & 1);
-    if (i >= nx || j >= ny) return;
-    const int c = lin(i, j, k, nx, ny);
-    if (mask[c]) return;
-    float diag;
-    const float s = nb_sum(e, mask, i, j, k, nx, ny, nz, c, diag);
-    e[c] = (g[c] + s) / diag;
+// Thread (ii, j) handles ZS planes k0 .. k0 + ZS - 1, at each the cell
+// i = 2 ii + ((j + k + colour) & 1).  All loads of the ZS cells (the other
+// colour, not written by this launch) are issued before the first store.
+// Large levels take ZS = 4 (fewer, longer threads); small ones ZS = 1 (more
+// parallelism).
+template <int ZS>
+__global__ void __launch_bounds__(BX * BY) k_smooth(float* __restrict__ e, const float* __restrict__ g,
+                                                    const uint8_t* __restrict__ mask, int nx, int ny, int nz,
+                                                    int color) {
+    const int j = blockIdx.y * BY + threadIdx.y, k0 = blockIdx.z * ZS, ii = blockIdx.x * BX + threadIdx.x;
+    if (j >= ny) return;
+    float s[ZS], gv[ZS], dg[ZS];
+    uint8_t mv[ZS];
+    int cc[ZS];
+#pragma unroll
+    for (int d = 0; d < ZS; ++d) {
+        const int k = k0 + d;
+        const int i = 2 * ii + ((j + k + color) & 1);
+        const bool ok = i < nx && k < nz;
+        cc[d] = ok ? lin(i, j, k, nx, ny) : -1;
+        s[d] = ok ? nb_sum_e(e, i, j, k, nx, ny, nz, cc[d], dg[d]) : 0.0f;
+        gv[d] = ok ? g[cc[d]] : 0.0f;
+        mv[d] = ok ? mask[cc[d]] : 1;
+    }
+#pragma unroll
+    for (int d = 0; d < ZS; ++d)
+        if (cc[d] >= 0 && !mv[d]) e[cc[d]] = (gv[d] + s[d]) * inv_diag(dg[d]);
 }
 
 // Coarse right-hand side: g_c = 4 * mean of the 8 fine residuals g - A e
-// (h^2 scaling: the coarse cell is twice as wide).
+// (h^2 scaling: the coarse cell is twice as wide).  After a black half-sweep
+// the residual of every black cell is zero (its value was just solved for
+// from red neighbours that have not changed since), so with black_zero set
+// only the four red children are evaluated.
 __global__ void k_resid_restrict(const float* __restrict__ e, const float* __restrict__ g,
                                  const uint8_t* __restrict__ mask, int nx, int ny, int nz, float* __restrict__ gc,
-                                 const uint8_t* __restrict__ maskc) {
+                                 const uint8_t* __restrict__ maskc, int black_zero) {
     const int cx = nx / 2, cy = ny / 2;
     const int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y, K = blockIdx.z;
     if (I >= cx || J >= cy) return;
@@ -233,11 +269,13 @@ __global__ void k_resid_restrict(const float* __restrict__ e, const float* __res
 #pragma unroll
     for (int d = 0; d < 8; ++d) {
         const int i = 2 * I + (d & 1), j = 2 * J + ((d >> 1) & 1), k = 2 * K + (d >> 2);
+        // children of a coarse cell: (i + j + k) has the parity of d's bit count
+        if (black_zero && (__popc(d) & 1)) continue;
         const int c = lin(i, j, k, nx, ny);
-        if (mask[c]) continue;
         float diag;
-        const float s = nb_sum(e, mask, i, j, k, nx, ny, nz, c, diag);
-        acc += g[c] - (diag * e[c] - s);
+        const float s = nb_sum_e(e, i, j, k, nx, ny, nz, c, diag);
+        const float r = g[c] - (diag * e[c] - s);
+        acc += mask[c] ? 0.0f : r;
     }
     gc[q] = 0.5f * acc;
 }
@@ -252,26 +290,47 @@ __device__ __forceinline__ float cval(const float* ec, int I, int J, int K, int 
     return sgn * ec[lin(I, J, K, cx, cy)];
 }
 
-// e_f += trilinear interpolation of e_c (weights 3/4, 1/4 per axis).
+// e_f += trilinear interpolation of e_c (weights 3/4, 1/4 per axis).  One
+// thread per coarse cell writes its eight children from the 3x3x3 coarse
+// neighbourhood; all loads are issued before the arithmetic.
 __global__ void k_prolong_add(const float* __restrict__ ec, float* __restrict__ ef, const uint8_t* __restrict__ mask,
                               int nx, int ny, int nz) {
-    CELL3D
-    if (!in) return;
-    if (mask[c]) { ef[c] = 0.0f; return; }
     const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
-    const int I = i >> 1, J = j >> 1, K = k >> 1;
-    const int si = (i & 1) ? 1 : -1, sj = (j & 1) ? 1 : -1, sk = (k & 1) ? 1 : -1;
-    float acc = 0.0f;
+    const int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y, K = blockIdx.z;
+    if (I >= cx || J >= cy) return;
+    float v[3][3][3];
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+    for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = 0; b < 2; ++b)
+        for (int b = 0; b < 3; ++b)
 #pragma unroll
-            for (int d = 0; d < 2; ++d) {
-                const float wgt = (a ? 0.25f : 0.75f) * (b ? 0.25f : 0.75f) * (d ? 0.25f : 0.75f);
-                acc += wgt * cval(ec, I + (d ? si : 0), J + (b ? sj : 0), K + (a ? sk : 0), cx, cy, cz);
-            }
-    ef[c] += acc;
+            for (int d = 0; d < 3; ++d) v[a][b][d] = cval(ec, I + d - 1, J + b - 1, K + a - 1, cx, cy, cz);
+    float fe[8];
+    uint8_t fm[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int c = lin(2 * I + (q & 1), 2 * J + ((q >> 1) & 1), 2 * K + (q >> 2), nx, ny);
+        fe[q] = ef[c];
+        fm[q] = mask[c];
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int di = q & 1, dj = (q >> 1) & 1, dk = q >> 2;
+        // the near coarse neighbour along each axis: -1 for the low child, +1 for the high one
+        const int si = di ? 2 : 0, sj = dj ? 2 : 0, sk = dk ? 2 : 0;
+        float acc = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int d = 0; d < 2; ++d) {
+                    const float wgt = (a ? 0.25f : 0.75f) * (b ? 0.25f : 0.75f) * (d ? 0.25f : 0.75f);
+                    acc += wgt * v[a ? sk : 1][b ? sj : 1][d ? si : 1];
+                }
+        const int c = lin(2 * I + di, 2 * J + dj, 2 * K + dk, nx, ny);
+        ef[c] = fm[q] ? 0.0f : fe[q] + acc;
+    }
 }
 
 // Coarse mask: a coarse cell is held at zero if any of its 8 children is.
@@ -293,18 +352,21 @@ __global__ void k_copy_mask(const uint8_t* __restrict__ m, uint8_t* __restrict__
 
 // The small levels of the hierarchy (from level t down to the coarsest; the
 // first of them has at most kTailCells cells) run as one block in shared
-// memory: zero, pre-smooth, restrict, ... coarse sweeps ... prolong,
-// post-smooth, with block barriers between the phases instead of kernel
-// launches.  The block reads g and the masks of level t from global memory
-// and writes back e of level t.
+// memory: pre-smooth, restrict, ... coarse sweeps ... prolong, post-smooth,
+// with barriers between the phases instead of kernel launches.  Threads map
+// to cells through a fixed 3D decomposition (no integer division); levels of
+// at most kWarpCells cells run on warp 0 alone with warp barriers.  The block
+// reads g and the masks of level t from global memory and writes back e of
+// level t.
 constexpr int kTailCells = 8192;
+constexpr int kWarpCells = 64;
 
 struct TailLevels {
     float* e_first;          // global e of level `first`
     const float* g_first;    // global g of level `first`
     const uint8_t* m[12];    // global masks
     int nx[12], ny[12], nz[12], off[12];  // shared-memory offsets (cells)
-    int first, last, pre, post, coarse, total;
+    int first, last, warp_from, pre, post, coarse, total;
 };
 
 struct TailSmem {
@@ -313,19 +375,110 @@ struct TailSmem {
     uint8_t* m;
 };
 
-__device__ void tail_smooth(const TailLevels& T, const TailSmem& S, int l, int color) {
-    const int nx = T.nx[l], ny = T.ny[l], nz = T.nz[l], n = nx * ny * nz, o = T.off[l];
+// Thread decomposition of a phase: thread owns (tx + a sx, ty + b sy, tz + c sz).
+struct Dec {
+    int tx, ty, tz, sx, sy, sz;
+    bool on;
+};
+__device__ __forceinline__ Dec dec_block() {
+    const int t = threadIdx.x;
+    return Dec{t & 7, (t >> 3) & 7, t >> 6, 8, 8, 16, true};
+}
+__device__ __forceinline__ Dec dec_warp() {
+    const int t = threadIdx.x;
+    return Dec{t & 1, (t >> 1) & 3, (t >> 3) & 3, 2, 4, 4, t < 32};
+}
+template <bool WARP> __device__ __forceinline__ void tail_sync() {
+    if (WARP) __syncwarp(); else __syncthreads();
+}
+
+template <bool WARP> __device__ void tail_half(const TailLevels& T, const TailSmem& S, int l, int color, const Dec& D) {
+    const int nx = T.nx[l], ny = T.ny[l], nz = T.nz[l], hx = (nx + 1) / 2, o = T.off[l];
     float* e = S.e + o;
     const float* g = S.g + o;
     const uint8_t* m = S.m + o;
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
-        const int i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
-        if (((i + j + k) & 1) != color || m[c]) continue;
-        float diag;
-        const float s = nb_sum(e, m, i, j, k, nx, ny, nz, c, diag);
-        e[c] = (g[c] + s) / diag;
-    }
-    __syncthreads();
+    if (D.on)
+        for (int k = D.tz; k < nz; k += D.sz)
+            for (int j = D.ty; j < ny; j += D.sy)
+                for (int ii = D.tx; ii < hx; ii += D.sx) {
+                    const int i = 2 * ii + ((j + k + color) & 1);
+                    if (i >= nx) continue;
+                    const int c = lin(i, j, k, nx, ny);
+                    float diag;
+                    const float s = nb_sum_e(e, i, j, k, nx, ny, nz, c, diag);
+                    if (!m[c]) e[c] = (g[c] + s) * inv_diag(diag);
+                }
+    tail_sync<WARP>();
+}
+
+// Residual of level l restricted into the right-hand side of level l + 1.
+template <bool WARP> __device__ void tail_restrict(const TailLevels& T, const TailSmem& S, int l, const Dec& D) {
+    const int nx = T.nx[l], ny = T.ny[l], nz = T.nz[l];
+    const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
+    const float* e = S.e + T.off[l];
+    const float* g = S.g + T.off[l];
+    const uint8_t* m = S.m + T.off[l];
+    float* gc = S.g + T.off[l + 1];
+    const uint8_t* mc = S.m + T.off[l + 1];
+    const bool black_zero = T.pre > 0;
+    if (D.on)
+        for (int K = D.tz; K < cz; K += D.sz)
+            for (int J = D.ty; J < cy; J += D.sy)
+                for (int I = D.tx; I < cx; I += D.sx) {
+                    const int q = lin(I, J, K, cx, cy);
+                    float acc = 0.0f;
+                    if (!mc[q])
+                        for (int d = 0; d < 8; ++d) {
+                            if (black_zero && (__popc(d) & 1)) continue;
+                            const int i = 2 * I + (d & 1), j = 2 * J + ((d >> 1) & 1), k = 2 * K + (d >> 2);
+                            const int c = lin(i, j, k, nx, ny);
+                            if (m[c]) continue;
+                            float diag;
+                            const float s = nb_sum_e(e, i, j, k, nx, ny, nz, c, diag);
+                            acc += g[c] - (diag * e[c] - s);
+                        }
+                    gc[q] = 0.5f * acc;
+                }
+    tail_sync<WARP>();
+}
+
+// e_l += trilinear interpolation of e_{l+1}.
+template <bool WARP> __device__ void tail_prolong(const TailLevels& T, const TailSmem& S, int l, const Dec& D) {
+    const int nx = T.nx[l], ny = T.ny[l], nz = T.nz[l];
+    const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
+    float* e = S.e + T.off[l];
+    const float* ec = S.e + T.off[l + 1];
+    const uint8_t* m = S.m + T.off[l];
+    if (D.on)
+        for (int k = D.tz; k < nz; k += D.sz)
+            for (int j = D.ty; j < ny; j += D.sy)
+                for (int i = D.tx; i < nx; i += D.sx) {
+                    const int c = lin(i, j, k, nx, ny);
+                    if (m[c]) continue;
+                    const int I = i >> 1, J = j >> 1, K = k >> 1;
+                    const int si = (i & 1) ? 1 : -1, sj = (j & 1) ? 1 : -1, sk = (k & 1) ? 1 : -1;
+                    float acc = 0.0f;
+                    for (int a = 0; a < 2; ++a)
+                        for (int b = 0; b < 2; ++b)
+                            for (int d = 0; d < 2; ++d) {
+                                const float wgt = (a ? 0.25f : 0.75f) * (b ? 0.25f : 0.75f) * (d ? 0.25f : 0.75f);
+                                acc += wgt * cval(ec, I + (d ? si : 0), J + (b ? sj : 0), K + (a ? sk : 0), cx, cy, cz);
+                            }
+                    e[c] += acc;
+                }
+    tail_sync<WARP>();
+}
+
+template <bool WARP> __device__ void tail_down(const TailLevels& T, const TailSmem& S, int l, const Dec& D) {
+    for (int s = 0; s < T.pre; ++s) { tail_half<WARP>(T, S, l, 0, D); tail_half<WARP>(T, S, l, 1, D); }
+    tail_restrict<WARP>(T, S, l, D);
+}
+template <bool WARP> __device__ void tail_up(const TailLevels& T, const TailSmem& S, int l, const Dec& D) {
+    tail_prolong<WARP>(T, S, l, D);
+    for (int s = 0; s < T.post; ++s) { tail_half<WARP>(T, S, l, 1, D); tail_half<WARP>(T, S, l, 0, D); }
+}
+template <bool WARP> __device__ void tail_coarse(const TailLevels& T, const TailSmem& S, const Dec& D) {
+    for (int s = 0; s < T.coarse; ++s) { tail_half<WARP>(T, S, T.last, 0, D); tail_half<WARP>(T, S, T.last, 1, D); }
 }
 
 __global__ void __launch_bounds__(1024) k_tail_vcycle(const TailLevels T) {
@@ -337,67 +490,25 @@ __global__ void __launch_bounds__(1024) k_tail_vcycle(const TailLevels T) {
     {
         const int n0 = T.nx[T.first] * T.ny[T.first] * T.nz[T.first];
         for (int c = threadIdx.x; c < n0; c += blockDim.x) S.g[T.off[T.first] + c] = T.g_first[c];
+        for (int c = threadIdx.x; c < T.total; c += blockDim.x) S.e[c] = 0.0f;
         for (int l = T.first; l <= T.last; ++l) {
             const int n = T.nx[l] * T.ny[l] * T.nz[l];
             for (int c = threadIdx.x; c < n; c += blockDim.x) S.m[T.off[l] + c] = T.m[l][c];
         }
     }
     __syncthreads();
-    for (int l = T.first; l <= T.last; ++l) {
-        const int n = T.nx[l] * T.ny[l] * T.nz[l];
-        for (int c = threadIdx.x; c < n; c += blockDim.x) S.e[T.off[l] + c] = 0.0f;
-        __syncthreads();
-        if (l == T.last) {
-            for (int s = 0; s < T.coarse; ++s) { tail_smooth(T, S, l, 0); tail_smooth(T, S, l, 1); }
-            break;
-        }
-        for (int s = 0; s < T.pre; ++s) { tail_smooth(T, S, l, 0); tail_smooth(T, S, l, 1); }
-        // residual restricted to level l + 1 (h^2 scaling: 4 x mean of 8)
-        const int nx = T.nx[l], ny = T.ny[l], nz = T.nz[l];
-        const int cx = nx / 2, cy = ny / 2, cz = nz / 2, ncz = cx * cy * cz;
-        const float* e = S.e + T.off[l];
-        const float* g = S.g + T.off[l];
-        const uint8_t* m = S.m + T.off[l];
-        for (int q = threadIdx.x; q < ncz; q += blockDim.x) {
-            float* gc = S.g + T.off[l + 1];
-            if (S.m[T.off[l + 1] + q]) { gc[q] = 0.0f; continue; }
-            const int I = q % cx, J = (q / cx) % cy, K = q / (cx * cy);
-            float acc = 0.0f;
-            for (int d = 0; d < 8; ++d) {
-                const int i = 2 * I + (d & 1), j = 2 * J + ((d >> 1) & 1), k = 2 * K + (d >> 2);
-                const int c = lin(i, j, k, nx, ny);
-                if (m[c]) continue;
-                float diag;
-                const float s = nb_sum(e, m, i, j, k, nx, ny, nz, c, diag);
-                acc += g[c] - (diag * e[c] - s);
-            }
-            gc[q] = 0.5f * acc;
-        }
-        __syncthreads();
+    const Dec DB = dec_block(), DW = dec_warp();
+    const int wl = T.warp_from;  // first level run by warp 0 alone (last + 1: none)
+    for (int l = T.first; l < wl && l < T.last; ++l) tail_down<false>(T, S, l, DB);
+    if (wl > T.last) {
+        tail_coarse<false>(T, S, DB);
+    } else if (threadIdx.x < 32) {
+        for (int l = wl; l < T.last; ++l) tail_down<true>(T, S, l, DW);
+        tail_coarse<true>(T, S, DW);
+        for (int l = T.last - 1; l >= wl; --l) tail_up<true>(T, S, l, DW);
     }
-    for (int l = T.last - 1; l >= T.first; --l) {
-        const int nx = T.nx[l], ny = T.ny[l], nz = T.nz[l], n = nx * ny * nz;
-        const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
-        float* e = S.e + T.off[l];
-        const float* ec = S.e + T.off[l + 1];
-        const uint8_t* m = S.m + T.off[l];
-        for (int c = threadIdx.x; c < n; c += blockDim.x) {
-            if (m[c]) { e[c] = 0.0f; continue; }
-            const int i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
-            const int I = i >> 1, J = j >> 1, K = k >> 1;
-            const int si = (i & 1) ? 1 : -1, sj = (j & 1) ? 1 : -1, sk = (k & 1) ? 1 : -1;
-            float acc = 0.0f;
-            for (int a = 0; a < 2; ++a)
-                for (int b = 0; b < 2; ++b)
-                    for (int d = 0; d < 2; ++d) {
-                        const float wgt = (a ? 0.25f : 0.75f) * (b ? 0.25f : 0.75f) * (d ? 0.25f : 0.75f);
-                        acc += wgt * cval(ec, I + (d ? si : 0), J + (b ? sj : 0), K + (a ? sk : 0), cx, cy, cz);
-                    }
-            e[c] += acc;
-        }
-        __syncthreads();
-        for (int s = 0; s < T.post; ++s) { tail_smooth(T, S, l, 1); tail_smooth(T, S, l, 0); }
-    }
+    __syncthreads();
+    for (int l = (wl > T.last ? T.last : wl) - 1; l >= T.first; --l) tail_up<false>(T, S, l, DB);
     const int n0 = T.nx[T.first] * T.ny[T.first] * T.nz[T.first];
     for (int c = threadIdx.x; c < n0; c += blockDim.x) T.e_first[c] = S.e[T.off[T.first] + c];
 }
@@ -420,15 +531,23 @@ __global__ void k_grad(const double* __restrict__ phi, int nx, int ny, int nz, d
     if (E4) { E4[4 * c] = (T)ex; E4[4 * c + 1] = (T)ey; E4[4 * c + 2] = (T)ez; E4[4 * c + 3] = (T)0; }
 }
 
+#include "poisson_mixed.cuh"
+
 dim3 grid3(int nx, int ny, int nz) { return dim3((nx + BX - 1) / BX, (ny + BY - 1) / BY, nz); }
-dim3 grid3_half(int nx, int ny, int nz) { return dim3((nx / 2 + BX - 1) / BX, (ny + BY - 1) / BY, nz); }
+const dim3 kBlk(BX, BY, 1);
+constexpr long long kSmoothDeep = 1ll << 20;  // levels with at least this many cells use 4 planes per thread
+void smooth_half(float* e, const float* g, const uint8_t* m, int nx, int ny, int nz, int color, cudaStream_t s) {
+    const int zs = (long long)nx * ny * nz >= kSmoothDeep ? 4 : 1;
+    const dim3 gr(((nx + 1) / 2 + BX - 1) / BX, (ny + BY - 1) / BY, (nz + zs - 1) / zs);
+    if (zs == 4) k_smooth<4><<<gr, kBlk, 0, s>>>(e, g, m, nx, ny, nz, color);
+    else k_smooth<1><<<gr, kBlk, 0, s>>>(e, g, m, nx, ny, nz, color);
+}
 dim3 grid_flat(long long n) { return dim3((unsigned)((n + BX * BY - 1) / (BX * BY))); }
 dim3 grid_red(long long n) {
     long long b = (n + BX * BY - 1) / (BX * BY);
     return dim3((unsigned)(b < 1216 ? b : 1216));
 }
 dim3 grid3_red(int nx, int ny, int nz) { return dim3((nx + BX - 1) / BX, (ny + BY - 1) / BY, nz < kZRed ? nz : kZRed); }
-const dim3 kBlk(BX, BY, 1);
 
 }  // namespace
 
@@ -457,35 +576,63 @@ bool MG::supported(int nx_, int ny_, int nz_) {
     return (long long)m.lx[L] * m.ly[L] * m.lz[L] * 9 <= 200 * 1024;
 }
 
-size_t MG::bytes(int nx_, int ny_, int nz_) {
+size_t MG::bytes(int nx_, int ny_, int nz_, bool mixed_, bool pair_copy) {
     MG m;
-    m.plan(nx_, ny_, nz_);
-    size_t b = align256(S_N * 8);
-    const size_t n0 = (size_t)nx_ * ny_ * nz_;
-    b += 3 * align256(n0 * 8);  // r, p, q in float64
-    for (int l = 0; l < m.levels; ++l) {
-        const size_t n = (size_t)m.lx[l] * m.ly[l] * m.lz[l];
-        b += 2 * align256(n * sizeof(float)) + align256(n);
-    }
-    return b;
+    return m.carve(nullptr, nx_, ny_, nz_, mixed_, pair_copy);
 }
 
-void MG::carve(void* base, int nx_, int ny_, int nz_) {
+// Lays the buffers out from base (base null: sizes only); returns the bytes.
+size_t MG::carve(void* base, int nx_, int ny_, int nz_, bool mixed_, bool pair_copy) {
     plan(nx_, ny_, nz_);
-    char* p = (char*)base;
-    norms = (double*)p;
-    p += align256(S_N * 8);
+    mixed = mixed_;
+    uintptr_t p = (uintptr_t)base;
+    const uintptr_t p0 = p;
+    auto take = [&](size_t nb) {
+        void* r = (void*)p;
+        p += align256(nb);
+        return r;
+    };
+    norms = (double*)take(S_N * 8);
     const size_t n0 = (size_t)nx_ * ny_ * nz_;
-    r64 = (double*)p; p += align256(n0 * 8);
-    p64 = (double*)p; p += align256(n0 * 8);
-    q64 = (double*)p; p += align256(n0 * 8);
+    if (mixed_) {
+        d32 = (float*)take(n0 * 4);
+        p32[0] = (float*)take(n0 * 4);
+        p32[1] = (float*)take(n0 * 4);
+        q32 = (float*)take(n0 * 4);
+        phi_pair = pair_copy ? (float*)take(2 * n0 * 4) : nullptr;
+        ctr = (unsigned*)take(8 * sizeof(unsigned));
+        const size_t b3 = (size_t)((nx_ + BX - 1) / BX) * ((ny_ + BY - 1) / BY) * ((nz_ + ZC - 1) / ZC);
+        const size_t bf = (n0 + kFlatBlock * kFlatPer - 1) / (kFlatBlock * kFlatPer);
+        part = (double*)take(2 * 8 * (b3 > bf ? b3 : bf));
+        r64 = p64 = q64 = nullptr;
+    } else {
+        r64 = (double*)take(n0 * 8);
+        p64 = (double*)take(n0 * 8);
+        q64 = (double*)take(n0 * 8);
+    }
     for (int l = 0; l < levels; ++l) {
         const size_t n = (size_t)lx[l] * ly[l] * lz[l];
-        e[l] = (float*)p; p += align256(n * sizeof(float));
-        g[l] = (float*)p; p += align256(n * sizeof(float));
-        m[l] = (uint8_t*)p; p += align256(n);
+        e[l] = (float*)take(n * sizeof(float));
+        g[l] = (float*)take(n * sizeof(float));
+        m[l] = (uint8_t*)take(n);
     }
+    return (size_t)(p - p0);
 }
+
+// First level handled by the single-block tail: at most kTailCells cells,
+// and the tail's levels must fit in shared memory together.
+int MG::tail_level() const {
+    int t = 0;
+    while (t < levels - 1 && (long long)lx[t] * ly[t] * lz[t] > kTailCells) ++t;
+    while (t < levels - 1) {
+        long long cells = 0;
+        for (int l = t; l < levels; ++l) cells += (long long)lx[l] * ly[l] * lz[l];
+        if (cells * 9 <= 200 * 1024) break;
+        ++t;
+    }
+    return t;
+}
+
 
 cudaError_t MG::build_masks(const uint8_t* mask, cudaStream_t s) {
     const long long n0 = (long long)lx[0] * ly[0] * lz[0];
@@ -499,25 +646,17 @@ cudaError_t MG::build_masks(const uint8_t* mask, cudaStream_t s) {
 // One V(pre, post)-cycle on A e0 = g0; e0 is overwritten.  Levels above the
 // tail run as separate kernels; the tail runs as one block.
 void MG::vcycle(cudaStream_t s) {
-    int t = 0;
-    while (t < levels - 1 && (long long)lx[t] * ly[t] * lz[t] > kTailCells) ++t;
-    // the tail's shared memory must fit: keep full levels above it otherwise
-    while (t < levels - 1) {
-        long long cells = 0;
-        for (int l = t; l < levels; ++l) cells += (long long)lx[l] * ly[l] * lz[l];
-        if (cells * 9 <= 200 * 1024) break;
-        ++t;
-    }
+    const int t = tail_level();
     launches += (long long)t * (1 + 2 * pre + 2 * post + 1) + 1;
     for (int l = 0; l < t; ++l) {
         const long long n = (long long)lx[l] * ly[l] * lz[l];
         cudaMemsetAsync(e[l], 0, n * sizeof(float), s);
         for (int it = 0; it < pre; ++it) {
-            k_smooth<<<grid3_half(lx[l], ly[l], lz[l]), kBlk, 0, s>>>(e[l], g[l], m[l], lx[l], ly[l], lz[l], 0);
-            k_smooth<<<grid3_half(lx[l], ly[l], lz[l]), kBlk, 0, s>>>(e[l], g[l], m[l], lx[l], ly[l], lz[l], 1);
+            smooth_half(e[l], g[l], m[l], lx[l], ly[l], lz[l], 0, s);
+            smooth_half(e[l], g[l], m[l], lx[l], ly[l], lz[l], 1, s);
         }
-        k_resid_restrict<<<grid3(lx[l + 1], ly[l + 1], lz[l + 1]), kBlk, 0, s>>>(e[l], g[l], m[l], lx[l], ly[l],
-                                                                                 lz[l], g[l + 1], m[l + 1]);
+        k_resid_restrict<<<grid3(lx[l + 1], ly[l + 1], lz[l + 1]), kBlk, 0, s>>>(
+            e[l], g[l], m[l], lx[l], ly[l], lz[l], g[l + 1], m[l + 1], pre > 0 ? 1 : 0);
     }
     TailLevels T;
     int off = 0;
@@ -531,6 +670,8 @@ void MG::vcycle(cudaStream_t s) {
     T.g_first = g[t];
     T.first = t;
     T.last = levels - 1;
+    T.warp_from = levels;
+    for (int l = levels - 1; l >= t && (long long)lx[l] * ly[l] * lz[l] <= kWarpCells; --l) T.warp_from = l;
     T.pre = pre;
     T.post = post;
     T.coarse = coarse_sweeps;
@@ -539,10 +680,11 @@ void MG::vcycle(cudaStream_t s) {
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_tail_vcycle, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_tail_vcycle<<<1, 1024, smem, s>>>(T);
     for (int l = t - 1; l >= 0; --l) {
-        k_prolong_add<<<grid3(lx[l], ly[l], lz[l]), kBlk, 0, s>>>(e[l + 1], e[l], m[l], lx[l], ly[l], lz[l]);
+        k_prolong_add<<<grid3(lx[l + 1], ly[l + 1], lz[l + 1]), kBlk, 0, s>>>(e[l + 1], e[l], m[l], lx[l], ly[l],
+                                                                              lz[l]);
         for (int it = 0; it < post; ++it) {
-            k_smooth<<<grid3_half(lx[l], ly[l], lz[l]), kBlk, 0, s>>>(e[l], g[l], m[l], lx[l], ly[l], lz[l], 1);
-            k_smooth<<<grid3_half(lx[l], ly[l], lz[l]), kBlk, 0, s>>>(e[l], g[l], m[l], lx[l], ly[l], lz[l], 0);
+            smooth_half(e[l], g[l], m[l], lx[l], ly[l], lz[l], 1, s);
+            smooth_half(e[l], g[l], m[l], lx[l], ly[l], lz[l], 0, s);
         }
     }
 }
@@ -564,6 +706,8 @@ void MG::iteration(cudaStream_t s, double* phi, const uint8_t* mk, bool first) {
 void MG::release() {
     for (int q = 0; q < 2; ++q)
         if (g_iter[q]) { cudaGraphExecDestroy(g_iter[q]); g_iter[q] = nullptr; }
+    for (int q = 0; q < 3; ++q)
+        if (g_mx[q]) { cudaGraphExecDestroy(g_mx[q]); g_mx[q] = nullptr; }
     if (cap_stream) { cudaStreamDestroy(cap_stream); cap_stream = nullptr; }
 }
 
@@ -633,34 +777,191 @@ int MG::solve(const double* rho, const uint8_t* mask, double* phi, double h, dou
     return rc;
 }
 
+
+// ------------------------------------------------------------------ mixed precision
+namespace {
+dim3 grid_mx3(int nx, int ny, int nz) { return dim3((nx + BX - 1) / BX, (ny + BY - 1) / BY, (nz + ZC - 1) / ZC); }
+dim3 grid_mxf(long long n) {
+    const long long b = (n / 4 + kFlatBlock * kFlatPer - 1) / (kFlatBlock * kFlatPer);
+    return dim3((unsigned)(b > 0 ? b : 1));
+}
+float2 pair_of(double v) {
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+}
+}  // namespace
+
+// One flexible-CG iteration on the float32 correction (it: index within the
+// current refinement pass; the direction vectors alternate between p32[0]
+// and p32[1] so the new direction can be formed while the old one is read).
+void MG::iteration_mixed(cudaStream_t s, int it) {
+    const int nx = lx[0], ny = ly[0], nz = lz[0], n = nx * ny * nz;
+    const int cur = it & 1, first = it == 0 ? 1 : 0;
+    vcycle(s);
+    k_mx_dots<<<grid_mxf(n), kFlatBlock, 0, s>>>(e[0], g[0], q32, n, first, part, ctr + 1, norms);
+    k_mx_dir_apply<<<grid_mx3(nx, ny, nz), kBlk, 0, s>>>(e[0], p32[cur ^ 1], p32[cur], q32, m[0], nx, ny, nz, first,
+                                                         part, ctr + 2, norms);
+    k_mx_update<<<grid_mxf(n), kFlatBlock, 0, s>>>(p32[cur], q32, d32, g[0], n, first, part, ctr + 3, norms);
+    launches += 3;
+}
+
+void MG::extrapolate_pair(const float* ch, const float* cl, const float* ph, const float* pl, float* oh, float* ol,
+                          int n, bool have_prev, cudaStream_t s) {
+    k_mx_extrapolate<<<grid_mxf(n), kFlatBlock, 0, s>>>(ch, cl, ph, pl, oh, ol, n, have_prev ? 1 : 0);
+    ++launches;
+}
+
+int MG::solve_mixed(const void* rho, bool rho64, const uint8_t* mask, float* phi_hi, float* phi_lo, float* out_hi,
+                    float* out_lo, bool fix_mask, double h, double v_lo, double v_hi, double v_mask, double rtol, int max_cycles,
+                    float* E4, float* Ex, float* Ey, float* Ez, cudaStream_t s, int* cycles_out, double* rel_out,
+                    double* host_norms) {
+    if (!mixed) return PIC_ERR_STATE;
+    const int nx = lx[0], ny = ly[0], nz = lz[0], n = nx * ny * nz;
+    if (!persistent || !masks_ready) {
+        if (build_masks(mask, s) != cudaSuccess) return PIC_ERR_CUDA;
+        masks_ready = true;
+    }
+    const MxBoundary bc{pair_of(v_lo), pair_of(v_hi), pair_of(v_mask)};
+    const double h2e = h * h / kEps0;
+    const dim3 g3 = grid_mx3(nx, ny, nz), gf = grid_mxf(n);
+    if (cudaMemsetAsync(ctr, 0, 8 * sizeof(unsigned), s) != cudaSuccess) return PIC_ERR_CUDA;
+    if (fix_mask) {
+        k_mx_fix_mask<<<(n + 255) / 256, 256, 0, s>>>(m[0], phi_hi, phi_lo, n, bc.v_mask);
+        ++launches;
+    }
+    auto resid = [&]() {
+        if (rho64)
+            k_mx_resid<double><<<g3, kBlk, 0, s>>>((const double*)rho, h2e, m[0], phi_hi, phi_lo, nx, ny, nz, bc, g[0],
+                                                   part, ctr, norms);
+        else
+            k_mx_resid<float><<<g3, kBlk, 0, s>>>((const float*)rho, 1.0, m[0], phi_hi, phi_lo, nx, ny, nz, bc, g[0],
+                                                  part, ctr, norms);
+        ++launches;
+    };
+    resid();
+    int cyc = 0, it = 0, rc = PIC_OK;
+    double bn = 1.0, rn = 0.0, r_pass = 0.0;
+    for (;;) {
+        if (cudaMemcpyAsync(host_norms, norms, 2 * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return PIC_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return PIC_ERR_CUDA;
+        bn = host_norms[S_B2] > 0.0 ? sqrt(host_norms[S_B2]) : 1.0;
+        rn = sqrt(host_norms[S_R2]);
+        if (it == 0) r_pass = rn;
+        if (rn / bn <= rtol) break;
+        if (cyc >= max_cycles) { rc = PIC_ERR_TIMEOUT; break; }
+        if (it > 0 && rn <= kRefineDrop * r_pass) {
+            // iterative refinement: fold the correction into phi, re-form r
+            k_mx_commit<<<gf, kFlatBlock, 0, s>>>(phi_hi, phi_lo, d32, n);
+            ++launches;
+            resid();
+            it = 0;
+            continue;
+        }
+        const int gi = it == 0 ? 0 : 1 + (it & 1);
+        if (persistent) {
+            if (!g_mx[gi]) {
+                if (!cap_stream && cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+                    return PIC_ERR_CUDA;
+                cudaGraph_t gr = nullptr;
+                const long long l0 = launches;
+                if (cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                    return PIC_ERR_CUDA;
+                iteration_mixed(cap_stream, it);
+                if (cudaStreamEndCapture(cap_stream, &gr) != cudaSuccess) return PIC_ERR_CUDA;
+                if (cudaGraphInstantiate(&g_mx[gi], gr, 0) != cudaSuccess) { cudaGraphDestroy(gr); return PIC_ERR_CUDA; }
+                cudaGraphDestroy(gr);
+                graph_kernels_mx[gi] = launches - l0;
+                launches = l0;
+            }
+            if (cudaGraphLaunch(g_mx[gi], s) != cudaSuccess) return PIC_ERR_CUDA;
+            launches += graph_kernels_mx[gi];
+        } else {
+            iteration_mixed(s, it);
+        }
+        ++it;
+        ++cyc;
+    }
+    if (cycles_out) *cycles_out = cyc;
+    if (rel_out) *rel_out = rn / bn;
+    const float* dd = it > 0 ? d32 : nullptr;
+    const float inv2h = (float)(1.0 / (2.0 * h));
+    if (out_hi) {
+        k_mx_grad<<<g3, kBlk, 0, s>>>(phi_hi, phi_lo, dd, out_hi, out_lo, nx, ny, nz, inv2h, bc, Ex, Ey, Ez, E4);
+        ++launches;
+    } else {
+        if (dd) {
+            k_mx_commit<<<gf, kFlatBlock, 0, s>>>(phi_hi, phi_lo, dd, n);
+            ++launches;
+        }
+        if (Ex || E4) {
+            k_mx_grad<<<g3, kBlk, 0, s>>>(phi_hi, phi_lo, nullptr, nullptr, nullptr, nx, ny, nz, inv2h, bc, Ex,
+                                                 Ey, Ez, E4);
+            ++launches;
+        }
+    }
+    if (cudaGetLastError() != cudaSuccess) return PIC_ERR_CUDA;
+    return rc;
+}
+
 }  // namespace pic
 
 // ------------------------------------------------------------------ C ABI
 using pic::MG;
 
+namespace {
+bool poisson_args_ok(const poisson_config* pc, const double* rho, const double* phi, const float* Ex, const float* Ey,
+                     const float* Ez, double rtol, int max_cycles) {
+    if (!pc || !rho || !phi || pc->nx < 2 || pc->ny < 2 || pc->nz < 2 || !(pc->dx > 0) || !(rtol > 0) ||
+        max_cycles < 0)
+        return false;
+    if (pc->precision != 0 && pc->precision != 32 && pc->precision != 64) return false;
+    if ((Ex == nullptr) != (Ey == nullptr) || (Ex == nullptr) != (Ez == nullptr)) return false;
+    return MG::supported(pc->nx, pc->ny, pc->nz);
+}
+
+size_t poisson_bytes(const poisson_config* pc) { return MG::bytes(pc->nx, pc->ny, pc->nz, pc->precision == 32, true); }
+
+// The solve behind both entry points, on a workspace of poisson_bytes(pc).
+int poisson_run(const poisson_config* pc, const double* rho, const uint8_t* mask, double* phi, float* Ex, float* Ey,
+                float* Ez, double rtol, int max_cycles, void* ws, poisson_stats* st, cudaStream_t s) {
+    MG mg;
+    const bool mixed = pc->precision == 32;
+    mg.carve(ws, pc->nx, pc->ny, pc->nz, mixed, true);
+    double hn[2];
+    int cycles = 0;
+    double rel = 0.0;
+    int rc;
+    if (mixed) {
+        const int n = pc->nx * pc->ny * pc->nz;
+        float* hi = mg.phi_pair;
+        float* lo = mg.phi_pair + n;
+        pic::k_mx_split<<<(n + 255) / 256, 256, 0, s>>>(phi, hi, lo, n);
+        rc = mg.solve_mixed(rho, true, mask, hi, lo, nullptr, nullptr, true, pc->dx, pc->v_lo, pc->v_hi, pc->v_mask, rtol,
+                            max_cycles, nullptr, Ex, Ey, Ez, s, &cycles, &rel, hn);
+        if (rc != PIC_ERR_CUDA) pic::k_mx_join<<<(n + 255) / 256, 256, 0, s>>>(hi, lo, phi, n);
+        if (cudaGetLastError() != cudaSuccess) rc = PIC_ERR_CUDA;
+    } else {
+        rc = mg.solve(rho, mask, phi, pc->dx, pc->v_lo, pc->v_hi, pc->v_mask, rtol, max_cycles, 32, nullptr, Ex, Ey,
+                      Ez, s, &cycles, &rel, hn);
+    }
+    if (st) { st->cycles = cycles; st->rel_res = rel; }
+    return rc;
+}
+}  // namespace
+
 extern "C" size_t poisson_workspace_bytes(const poisson_config* pc) {
-    if (!pc || !MG::supported(pc->nx, pc->ny, pc->nz)) return 0;
-    return MG::bytes(pc->nx, pc->ny, pc->nz);
+    if (!pc || (pc->precision != 0 && pc->precision != 32 && pc->precision != 64) ||
+        !MG::supported(pc->nx, pc->ny, pc->nz))
+        return 0;
+    return poisson_bytes(pc);
 }
 
 extern "C" int poisson_solve(const poisson_config* pc, const double* rho, const uint8_t* mask, double* phi, float* Ex,
                              float* Ey, float* Ez, double rtol, int max_cycles, void* ws, size_t ws_bytes,
                              poisson_stats* st, pic_stream_t stream) {
-    if (!pc || !rho || !phi || !ws || pc->nx < 2 || pc->ny < 2 || pc->nz < 2 || !(pc->dx > 0) || !(rtol > 0) ||
-        max_cycles < 0)
-        return PIC_ERR_ARG;
-    if (!MG::supported(pc->nx, pc->ny, pc->nz)) return PIC_ERR_ARG;
-    if (ws_bytes < MG::bytes(pc->nx, pc->ny, pc->nz) || ((uintptr_t)ws & 255)) return PIC_ERR_ARG;
-    if ((Ex == nullptr) != (Ey == nullptr) || (Ex == nullptr) != (Ez == nullptr)) return PIC_ERR_ARG;
-    MG mg;
-    mg.carve(ws, pc->nx, pc->ny, pc->nz);
-    double hn[2];
-    int cycles = 0;
-    double rel = 0.0;
-    int rc = mg.solve(rho, mask, phi, pc->dx, pc->v_lo, pc->v_hi, pc->v_mask, rtol, max_cycles, 32, nullptr, Ex, Ey, Ez,
-                      (cudaStream_t)stream, &cycles, &rel, hn);
-    if (st) { st->cycles = cycles; st->rel_res = rel; }
-    return rc;
+    if (!ws || !poisson_args_ok(pc, rho, phi, Ex, Ey, Ez, rtol, max_cycles)) return PIC_ERR_ARG;
+    if (ws_bytes < poisson_bytes(pc) || ((uintptr_t)ws & 255)) return PIC_ERR_ARG;
+    return poisson_run(pc, rho, mask, phi, Ex, Ey, Ez, rtol, max_cycles, ws, st, (cudaStream_t)stream);
 }
 
 // ------------------------------------------------------------------ no-allocation variant
@@ -699,22 +1000,10 @@ static int noalloc_scratch(void** out) {
 extern "C" int poisson_solve_noalloc(const poisson_config* pc, const double* rho, const uint8_t* mask, double* phi,
                                      float* Ex, float* Ey, float* Ez, double rtol, int max_cycles, poisson_stats* st,
                                      pic_stream_t stream) {
-    if (!pc || !rho || !phi || pc->nx < 2 || pc->ny < 2 || pc->nz < 2 || !(pc->dx > 0) || !(rtol > 0) ||
-        max_cycles < 0)
-        return PIC_ERR_ARG;
-    if ((Ex == nullptr) != (Ey == nullptr) || (Ex == nullptr) != (Ez == nullptr)) return PIC_ERR_ARG;
-    if (!MG::supported(pc->nx, pc->ny, pc->nz)) return PIC_ERR_ARG;
-    if (MG::bytes(pc->nx, pc->ny, pc->nz) > kNoAllocScratchBytes) return PIC_ERR_CAPACITY;
+    if (!poisson_args_ok(pc, rho, phi, Ex, Ey, Ez, rtol, max_cycles)) return PIC_ERR_ARG;
+    if (poisson_bytes(pc) > kNoAllocScratchBytes) return PIC_ERR_CAPACITY;
     void* ws = nullptr;
     int rc = noalloc_scratch(&ws);
     if (rc) return rc;
-    MG mg;
-    mg.carve(ws, pc->nx, pc->ny, pc->nz);
-    double hn[2];
-    int cycles = 0;
-    double rel = 0.0;
-    rc = mg.solve(rho, mask, phi, pc->dx, pc->v_lo, pc->v_hi, pc->v_mask, rtol, max_cycles, 32, nullptr, Ex, Ey, Ez,
-                  (cudaStream_t)stream, &cycles, &rel, hn);
-    if (st) { st->cycles = cycles; st->rel_res = rel; }
-    return rc;
+    return poisson_run(pc, rho, mask, phi, Ex, Ey, Ez, rtol, max_cycles, ws, st, (cudaStream_t)stream);
 }

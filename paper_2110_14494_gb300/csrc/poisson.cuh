@@ -29,14 +29,42 @@ struct MG {
     void release();
     void iteration(cudaStream_t s, double* phi, const uint8_t* mk, bool first);
 
+    // Mixed-precision solve: float-pair potential, float32 Krylov vectors,
+    // deterministic last-block reductions (scratch: ctr counters, part sums).
+    bool mixed = false;
+    float* d32 = nullptr;
+    float* p32[2] = {nullptr, nullptr};
+    float* q32 = nullptr;
+    float* phi_pair = nullptr;  // [2][n] pair copy for callers that hold phi in float64
+    unsigned* ctr = nullptr;
+    double* part = nullptr;
+    cudaGraphExec_t g_mx[3] = {nullptr, nullptr, nullptr};  // first, odd, even iterations
+    long long graph_kernels_mx[3] = {0, 0, 0};
+    void iteration_mixed(cudaStream_t s, int it);
+    // out = 2 cur - prev (have_prev) or cur, pair format: the warm start.
+    void extrapolate_pair(const float* cur_hi, const float* cur_lo, const float* prev_hi, const float* prev_lo,
+                          float* out_hi, float* out_lo, int n, bool have_prev, cudaStream_t s);
+    // rho: h^2 rho / eps0 as float (rho64 false) or rho as float64 (rho64
+    // true).  phi (pair) is the initial guess; with out_hi set the solution
+    // goes there and phi keeps the guess, else phi is updated in place.
+    // fix_mask: set phi = v_mask on electrode cells first (needed once per
+    // potential buffer; later solves keep it).
+    int solve_mixed(const void* rho, bool rho64, const uint8_t* mask, float* phi_hi, float* phi_lo, float* out_hi,
+                    float* out_lo, bool fix_mask, double h, double v_lo, double v_hi, double v_mask, double rtol, int max_cycles,
+                    float* E4, float* Ex, float* Ey, float* Ez, cudaStream_t s, int* cycles_out, double* rel_out,
+                    double* host_norms);
+
     void plan(int nx, int ny, int nz);
     // The coarsest level must be small enough for the single-block tail
     // (its cells and those of nothing else fit in shared memory).
     static bool supported(int nx, int ny, int nz);
-    static size_t bytes(int nx, int ny, int nz);
-    void carve(void* base, int nx, int ny, int nz);
+    // Workspace of the float64 solve (mixed false) or of the mixed one
+    // (pair_copy: with room for the pair copy of a float64 potential).
+    static size_t bytes(int nx, int ny, int nz, bool mixed = false, bool pair_copy = false);
+    size_t carve(void* base, int nx, int ny, int nz, bool mixed = false, bool pair_copy = false);
     cudaError_t build_masks(const uint8_t* mask, cudaStream_t s);
     void vcycle(cudaStream_t s);
+    int tail_level() const;
     // Returns PIC_OK, PIC_ERR_TIMEOUT or PIC_ERR_CUDA.  packed_prec selects the
     // element type (32: float, 64: double) of the optional packed field E4.
     int solve(const double* rho, const uint8_t* mask, double* phi, double h, double v_lo, double v_hi, double v_mask,

@@ -67,7 +67,7 @@ class pic_profile_times(C.Structure):
 
 class poisson_config(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dx", C.c_double), ("v_lo", C.c_double),
-                ("v_hi", C.c_double), ("v_mask", C.c_double)]
+                ("v_hi", C.c_double), ("v_mask", C.c_double), ("precision", C.c_int)]
 
 
 class poisson_stats(C.Structure):
@@ -317,9 +317,10 @@ class PicContext:
 
 
 def poisson_solve(grid: dict, rho, phi, mask=None, E=None, v_lo=0.0, v_hi=0.0, v_mask=0.0, rtol=1e-6,
-                  max_cycles=100, stream=None):
-    """rho, phi: float64 CUDA tensors [nz][ny][nx]; E: optional tuple of three float32 tensors."""
-    pc = poisson_config(grid["nx"], grid["ny"], grid["nz"], grid["dx"], v_lo, v_hi, v_mask)
+                  max_cycles=100, stream=None, precision=64):
+    """rho, phi: float64 CUDA tensors [nz][ny][nx]; E: optional tuple of three float32 tensors.
+    precision 64: CG in float64; 32: float-pair potential with float32 CG and refinement."""
+    pc = poisson_config(grid["nx"], grid["ny"], grid["nz"], grid["dx"], v_lo, v_hi, v_mask, precision)
     nb = lib().poisson_workspace_bytes(C.byref(pc))
     ws, ptr = _workspace(nb)
     st = poisson_stats()

@@ -57,7 +57,13 @@ def test_host_argument_validation(L):
     pc = P.poisson_config(1, 8, 8, 1e-5, 0, 0, 0)
     assert L.poisson_workspace_bytes(C.byref(pc)) == 0
     pc.nx = 8
+    b64 = L.poisson_workspace_bytes(C.byref(pc))
+    assert b64 > 0
+    pc.precision = 32
     assert L.poisson_workspace_bytes(C.byref(pc)) > 0
+    pc.precision = 16
+    assert L.poisson_workspace_bytes(C.byref(pc)) == 0
+    pc.precision = 0
     assert L.poisson_solve(C.byref(pc), None, None, None, None, None, None, 1e-6, 10, None, 0, None, None) == \
         P.PIC_ERR_ARG
     sc = P.swarm_config(64, gas.c, 2.45e25, 100, 10, 1000, 2000, 10, 1e-12, 1.0, 1, 0.25)

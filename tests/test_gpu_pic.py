@@ -244,3 +244,29 @@ def test_adaptive_time_step_bounds():
     ne_max = max(ne for _, ne in dts[:-1])
     assert ne_max > 5e19
     assert min(dt for dt, _ in dts[1:]) <= 8.8541878128e-12 / (1.602176634e-19 * ne_max * mu) * 1.5
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_coupled_field_matches_oracle_solve(prec):
+    """The coupled context's own solve (float64 CG, or the float-pair solve in
+    single precision with its three rotating potential slots), read back from a
+    checkpoint, against the oracle's solution for the same charge (none) and
+    electrode."""
+    grid = W.grid_spec(32, 32, 48, 5e-5)
+    V0 = 2000.0
+    mask = W.needle_mask(grid, 0.8e-3, 0.15e-3)
+    rtol = 1e-11 if prec == 64 else 1e-8
+    ctx = _ctx(W.synthetic_air(), grid, prec, capacity=1024, seed=SEED, dt=1e-12, mask=mask, coupled=True,
+               v_lo=0.0, v_hi=V0, v_mask=V0, poisson_rtol=rtol)
+    ref, _, _ = O.poisson(grid, np.zeros((48, 32, 32)), mask, V0, 0.0, V0, rtol=1e-12)
+    for _ in range(3):  # exercises the warm start and the slot rotation
+        ctx.step(1)
+        blob = ctx.save()
+        n = 32 * 32 * 48
+        phi = np.frombuffer(blob, np.float64, count=n, offset=len(blob) - 8 * n).reshape(48, 32, 32)
+        err = np.linalg.norm(phi - ref) / np.linalg.norm(ref)
+        assert err < (1e-8 if prec == 64 else 1e-5), err
+    ctx.load(blob)
+    ctx.step(1)
+    phi2 = np.frombuffer(ctx.save(), np.float64, count=n, offset=len(blob) - 8 * n).reshape(48, 32, 32)
+    assert np.linalg.norm(phi2 - ref) / np.linalg.norm(ref) < (1e-8 if prec == 64 else 1e-5)

@@ -177,3 +177,66 @@ def test_batched_swarms_fp32_match_oracle():
         omom, ocnt, ores, _ = O.swarm(gas, EN, 2000, 400, 1e-12, seed + s, n_lo=1000, n_hi=4000)
         bad = _agree(res[s], ores)
         assert not bad, bad
+
+
+def test_poisson_pair_precision_matches_oracle():
+    """Float-pair potential, float32 CG with refinement (precision 32): the
+    needle problem from a cold start (several refinement passes) against the
+    oracle's float64 CG solution."""
+    from paper_2110_14494_gb300 import poisson_solve
+    grid = W.grid_spec(32, 32, 48, 5e-5)
+    V0 = 2000.0
+    mask = W.needle_mask(grid, 0.8e-3, 0.15e-3)
+    rho = W.random_rho(grid, 7, 2e-2)
+    ref, rr, it = O.poisson(grid, rho, mask, V0, 0.0, V0, rtol=1e-12)
+    rt = torch.as_tensor(rho).cuda()
+    mt = torch.as_tensor(mask).cuda()
+    phi = torch.zeros_like(rt)
+    E = tuple(torch.zeros(rho.shape, dtype=torch.float32, device="cuda") for _ in range(3))
+    cyc, rel = poisson_solve(grid, rt, phi, mask=mt, E=E, v_lo=0.0, v_hi=V0, v_mask=V0, rtol=1e-8, max_cycles=100,
+                             precision=32)
+    assert rel <= 1e-8 and cyc < 40, (cyc, rel)
+    p = phi.cpu().numpy()
+    assert np.linalg.norm(p - ref) / np.linalg.norm(ref) < 1e-5
+    assert np.all(p[mask != 0] == V0)
+    Er = O.grad_phi(grid, ref, 0.0, V0)
+    for a, b in zip(E, Er):
+        assert np.abs(a.cpu().numpy() - b).max() <= 1e-5 * np.abs(b).max() + 1e-3
+
+
+def test_poisson_pair_precision_plates_and_warm_start():
+    """Plates only: the linear potential to float-pair accuracy; a warm start
+    at the solution needs no iteration."""
+    from paper_2110_14494_gb300 import poisson_solve
+    grid = W.grid_spec(16, 16, 64, 2e-5)
+    V0 = 2560.0
+    rho = torch.zeros((64, 16, 16), dtype=torch.float64, device="cuda")
+    phi = torch.zeros_like(rho)
+    E = tuple(torch.zeros((64, 16, 16), dtype=torch.float32, device="cuda") for _ in range(3))
+    poisson_solve(grid, rho, phi, E=E, v_hi=V0, rtol=1e-8, max_cycles=100, precision=32)
+    z = (np.arange(64) + 0.5) * 2e-5
+    exact = (V0 * z / (64 * 2e-5))[:, None, None]
+    assert np.abs(phi.cpu().numpy() - exact).max() < 1e-6 * V0
+    assert np.allclose(E[2].cpu().numpy(), -V0 / (64 * 2e-5), rtol=1e-5)
+    phi2 = torch.as_tensor(np.broadcast_to(exact, (64, 16, 16)).copy()).cuda()
+    cyc, rel = poisson_solve(grid, rho, phi2, v_hi=V0, rtol=1e-8, max_cycles=100, precision=32)
+    assert cyc == 0 and rel <= 1e-8, (cyc, rel)
+
+
+def test_poisson_pair_precision_agrees_with_float64_solve():
+    """The two precisions of the GPU solve on a 64^3 needle with a streamer-like
+    charge: solutions within the tolerance they were solved to."""
+    from paper_2110_14494_gb300 import poisson_solve
+    grid = W.grid_spec(64, 64, 64, 4e-5)
+    L = 64 * 4e-5
+    V0 = 20e5 * L
+    mask = torch.as_tensor(W.needle_mask(grid, 1.0e-3, 0.2e-3)).cuda()
+    rho = torch.as_tensor(W.random_rho(grid, 11, 5e-2)).cuda()
+    out = []
+    for prec in (64, 32):
+        phi = torch.zeros_like(rho)
+        cyc, rel = poisson_solve(grid, rho, phi, mask=mask, v_lo=0.0, v_hi=V0, v_mask=V0, rtol=1e-8,
+                                 max_cycles=100, precision=prec)
+        assert rel <= 1e-8
+        out.append(phi.cpu().numpy())
+    assert np.linalg.norm(out[0] - out[1]) / np.linalg.norm(out[0]) < 1e-6
