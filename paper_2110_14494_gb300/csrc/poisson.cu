@@ -488,13 +488,36 @@ __global__ void __launch_bounds__(1024) k_tail_vcycle(const TailLevels T) {
     S.g = S.e + T.total;
     S.m = reinterpret_cast<uint8_t*>(S.g + T.total);
     {
+        // global loads in batches of kTailLoad per thread, issued before
+        // their stores (the first level has at most kTailCells cells)
+        constexpr int kTailLoad = kTailCells / 1024;
         const int n0 = T.nx[T.first] * T.ny[T.first] * T.nz[T.first];
-        for (int c = threadIdx.x; c < n0; c += blockDim.x) S.g[T.off[T.first] + c] = T.g_first[c];
-        for (int c = threadIdx.x; c < T.total; c += blockDim.x) S.e[c] = 0.0f;
+        float gv[kTailLoad];
+#pragma unroll
+        for (int u = 0; u < kTailLoad; ++u) {
+            const int c = threadIdx.x + u * 1024;
+            gv[u] = c < n0 ? T.g_first[c] : 0.0f;
+        }
         for (int l = T.first; l <= T.last; ++l) {
             const int n = T.nx[l] * T.ny[l] * T.nz[l];
-            for (int c = threadIdx.x; c < n; c += blockDim.x) S.m[T.off[l] + c] = T.m[l][c];
+            uint8_t mv[kTailLoad];
+#pragma unroll
+            for (int u = 0; u < kTailLoad; ++u) {
+                const int c = threadIdx.x + u * 1024;
+                mv[u] = c < n ? T.m[l][c] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < kTailLoad; ++u) {
+                const int c = threadIdx.x + u * 1024;
+                if (c < n) S.m[T.off[l] + c] = mv[u];
+            }
         }
+#pragma unroll
+        for (int u = 0; u < kTailLoad; ++u) {
+            const int c = threadIdx.x + u * 1024;
+            if (c < n0) S.g[T.off[T.first] + c] = gv[u];
+        }
+        for (int c = threadIdx.x; c < T.total; c += blockDim.x) S.e[c] = 0.0f;
     }
     __syncthreads();
     const Dec DB = dec_block(), DW = dec_warp();
