@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--swarm-block", type=int, default=0, help="batched swarms: block size (0 = autotune)")
     ap.add_argument("--swarm-bps", type=int, default=0, help="batched swarms: blocks per SM (0 = autotune)")
     ap.add_argument("--no-f64", action="store_true", help="batched swarms: skip the float64 comparison")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="after the timed steps, run this many more inside an NVTX range named 'prof' "
+                         "(untimed; for ncu --nvtx --nvtx-include prof/)")
     return ap.parse_args()
 
 
@@ -341,6 +344,14 @@ def main():
                       "phases_ms": phases, "parents_per_launch": parents_per_launch, "push_ms": push_ms,
                       "achieved_GBs": achieved, "n_trace": n_trace, "launches": prof["n_launches"]}),
           file=sys.stderr, flush=True)
+
+    if args.profile_steps > 0:
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("prof")
+        for _ in range(args.profile_steps):
+            ctx.step(1)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
 
     # end to end through the C ABI with host buffers: each step uploads the
     # particle state from pinned host memory, steps, and downloads it again

@@ -314,6 +314,50 @@ int swarm_run(const swarm_config *sc, int n_swarms, const double *EN_Td, void *d
               size_t workspace_bytes, swarm_result *results, double *moments, long long *counts,
               pic_stream_t stream);
 
+/* ---------------------------------------------------------------- surrogate */
+/* Transport-data surrogate: the flux transport data that the local-field
+ * fluid model reads (Sec. 2.2.4: mobility, diffusion, ionization and
+ * attachment coefficients and mean energy versus the field, computed there by
+ * Monte Carlo swarms) represented by a network 2 -> 128 -> 128 -> 6 with tanh
+ * hidden units and a linear output, fitted to swarm_run results.  Inputs and
+ * targets are standardized by the caller (two inputs: log10 E/N and the O2
+ * fraction; six targets: the logarithms of mu N, D_L N, D_T N, alpha / N,
+ * eta / N and the mean energy).  The 128 x 128 layer runs on the tensor cores
+ * in BF16 with FP32 accumulation, everything else in FP32.
+ *
+ * params: device float32 [MLP_NPARAMS] in the order W1[128][2], b1[128],
+ * W2[128][128], b2[128], W3[6][128], b3[6] (W[o][i] multiplies input i of
+ * unit o).  x: device float32 [n][2]; y, t: device float32 [n][6].
+ * Workspaces are caller-allocated, 256-byte aligned, sized by
+ * mlp_workspace_bytes(n) (n = 0: forward only).  Calls are stream-ordered
+ * and asynchronous.  Errors: PIC_ERR_ARG for null or misaligned pointers,
+ * a short workspace or a training n that is not a multiple of 64 (of 256
+ * above 256); PIC_ERR_CUDA if a launch fails. */
+#define MLP_NI 2
+#define MLP_NH 128
+#define MLP_NO 6
+#define MLP_NPARAMS 17670
+
+size_t mlp_workspace_bytes(int n_max);
+
+/* y = network(x) for n points (any n >= 0). */
+int mlp_forward(const float *params, const float *x, float *y, long long n, void *d_workspace,
+                size_t workspace_bytes, pic_stream_t stream);
+
+/* Mean squared error L = sum (y - t)^2 / (6 n) over the batch and its
+ * gradient with respect to params (device float32 [MLP_NPARAMS]); loss: device
+ * float32 scalar or NULL. */
+int mlp_loss_grad(const float *params, const float *x, const float *t, int n, float *grad, float *loss,
+                  void *d_workspace, size_t workspace_bytes, pic_stream_t stream);
+
+/* n_steps full-batch Adam steps (Kingma & Ba 2015, Algorithm 1) on params,
+ * with first and second moment estimates m, v (device float32 [MLP_NPARAMS],
+ * zero before the first step) and step0 steps already taken.  loss: device
+ * float32 scalar receiving the batch loss before the last update, or NULL. */
+int mlp_train(float *params, float *m, float *v, int step0, const float *x, const float *t, int n, int n_steps,
+              float lr, float beta1, float beta2, float eps, float *loss, void *d_workspace,
+              size_t workspace_bytes, pic_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,6 +23,7 @@ UNITS = {
     "push_f64.cu": ["--fmad=false"],
     "pic.cu": ["--fmad=false"],
     "poisson.cu": [],
+    "mlp.cu": [],
 }
 
 

@@ -91,7 +91,7 @@ EXPORTS = ("pic_workspace_bytes", "pic_init", "pic_destroy", "pic_last_error", "
            "pic_deposit", "pic_weight_update", "pic_count", "pic_save", "pic_load", "pic_progress",
            "pic_profile", "pic_upload", "pic_download",
            "poisson_workspace_bytes", "poisson_solve", "poisson_solve_noalloc", "swarm_workspace_bytes",
-           "swarm_run", "swarm_autotune")
+           "swarm_run", "swarm_autotune", "mlp_workspace_bytes", "mlp_forward", "mlp_loss_grad", "mlp_train")
 
 _lib = None
 
@@ -139,6 +139,12 @@ def lib():
     L.swarm_run.argtypes = [P(swarm_config), C.c_int, PD, VP, C.c_size_t, P(swarm_result), PD,
                             P(C.c_longlong), VP]
     L.swarm_autotune.argtypes = [P(swarm_config), C.c_int, PD, VP, C.c_size_t, P(C.c_int), P(C.c_int), PD, VP]
+    L.mlp_workspace_bytes.argtypes = [C.c_int]
+    L.mlp_workspace_bytes.restype = C.c_size_t
+    L.mlp_forward.argtypes = [VP, VP, VP, C.c_longlong, VP, C.c_size_t, VP]
+    L.mlp_loss_grad.argtypes = [VP, VP, VP, C.c_int, VP, VP, VP, C.c_size_t, VP]
+    L.mlp_train.argtypes = [VP, VP, VP, C.c_int, VP, VP, C.c_int, C.c_int, C.c_float, C.c_float, C.c_float,
+                            C.c_float, VP, VP, C.c_size_t, VP]
     _lib = L
     return L
 
@@ -376,3 +382,49 @@ def swarm_run(gas: dict, EN_Td, *, precision=64, n0=10000, n_steps=2000, dt=1e-1
     _check(rc, None, "swarm_run")
     out = np.array([[r.v[i] for i in range(PIC_SWARM_NRES)] for r in res])
     return out, mom, cnt
+
+
+MLP_NI, MLP_NH, MLP_NO, MLP_NPARAMS = 2, 128, 6, 17670
+
+
+def _mlp_ws(n):
+    nb = lib().mlp_workspace_bytes(n)
+    if nb == 0:
+        raise PicError(PIC_ERR_ARG, f"mlp: unsupported batch size {n}")
+    return _workspace(nb)
+
+
+def mlp_forward(params, x, y=None, stream=None):
+    """params: float32 CUDA [17670]; x: float32 CUDA [n][2] (standardized); returns y [n][6]."""
+    import torch
+    n = int(x.shape[0])
+    if y is None:
+        y = torch.empty((n, MLP_NO), dtype=torch.float32, device=x.device)
+    ws, ptr = _mlp_ws(0)
+    _check(lib().mlp_forward(_ptr(params), _ptr(x), _ptr(y), n, C.c_void_p(ptr), lib().mlp_workspace_bytes(0),
+                             _stream(stream)), None, "mlp_forward")
+    return y
+
+
+def mlp_loss_grad(params, x, t, stream=None):
+    """Returns (loss tensor [1], grad tensor [17670]) on the device."""
+    import torch
+    n = int(x.shape[0])
+    g = torch.empty(MLP_NPARAMS, dtype=torch.float32, device=x.device)
+    loss = torch.empty(1, dtype=torch.float32, device=x.device)
+    ws, ptr = _mlp_ws(n)
+    _check(lib().mlp_loss_grad(_ptr(params), _ptr(x), _ptr(t), n, _ptr(g), _ptr(loss), C.c_void_p(ptr),
+                               lib().mlp_workspace_bytes(n), _stream(stream)), None, "mlp_loss_grad")
+    return loss, g
+
+
+def mlp_train(params, m, v, step0, x, t, n_steps, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """n_steps full-batch Adam steps in place on params, m, v; returns the loss tensor [1]."""
+    import torch
+    n = int(x.shape[0])
+    loss = torch.empty(1, dtype=torch.float32, device=x.device)
+    ws, ptr = _mlp_ws(n)
+    _check(lib().mlp_train(_ptr(params), _ptr(m), _ptr(v), int(step0), _ptr(x), _ptr(t), n, int(n_steps), lr,
+                           beta1, beta2, eps, _ptr(loss), C.c_void_p(ptr), lib().mlp_workspace_bytes(n),
+                           _stream(stream)), None, "mlp_train")
+    return loss

@@ -14,7 +14,7 @@ def _declared():
     src = open(os.path.join(ROOT, "include", "picmcc.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     names = set(re.findall(r"^\s*(?:const\s+)?[\w ]+?\**\s*\b(\w+)\s*\(", src, flags=re.M))
-    return {n for n in names if n.startswith(("pic_", "poisson_", "swarm_"))}
+    return {n for n in names if n.startswith(("pic_", "poisson_", "swarm_", "mlp_"))}
 
 
 @pytest.fixture(scope="module")
@@ -70,3 +70,15 @@ def test_host_argument_validation(L):
     assert L.swarm_workspace_bytes(C.byref(sc), 1) > 0
     sc.n_steps = 0
     assert L.swarm_workspace_bytes(C.byref(sc), 1) == 0
+
+
+def test_mlp_host_validation(L):
+    """Batch sizes the training kernels do not tile are refused on the host."""
+    assert L.mlp_workspace_bytes(0) > 0
+    assert L.mlp_workspace_bytes(4096) > L.mlp_workspace_bytes(0)
+    for bad in (-1, 32, 100, 320):
+        assert L.mlp_workspace_bytes(bad) == 0, bad
+    from paper_2110_14494_gb300 import picmcc as P
+    assert L.mlp_train(None, None, None, 0, None, None, 64, 1, 1e-3, 0.9, 0.999, 1e-8, None, None, 0, None) == \
+        P.PIC_ERR_ARG
+    assert L.mlp_forward(None, None, None, 10, None, 0, None) == P.PIC_ERR_ARG

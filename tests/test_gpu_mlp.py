@@ -1,0 +1,116 @@
+"""GPU transport-data surrogate (BF16 tensor-core network, FP32 accumulate)
+against the FP64 CPU oracle, through the C ABI.
+
+Tolerances: the 128 x 128 layer rounds its operands to BF16 (relative
+2^-9 each) and tanh is the hardware approximation (~5e-4), so outputs and
+gradients are compared norm-wise per parameter block at 2e-2 relative; Adam's
+first step, lr g / (|g| + eps), is compared where the oracle's gradient is
+well above that error."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import mlp as M
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2110_14494_gb300 import build
+    build.build()
+
+
+def _problem(n, seed=1):
+    r = np.random.default_rng(seed)
+    th = W.mlp_init(30 + seed)
+    th[M.OFF["b1"]:M.OFF["b1"] + 128] = r.normal(0, 0.3, 128)
+    th[M.OFF["b2"]:M.OFF["b2"] + 128] = r.normal(0, 0.3, 128)
+    th[M.OFF["b3"]:M.OFF["b3"] + 6] = r.normal(0, 0.3, 6)
+    th = th.astype(np.float32).astype(np.float64)  # the values the GPU holds
+    x = r.normal(0, 1, (n, 2)).astype(np.float32).astype(np.float64)
+    t = r.normal(0, 1, (n, 6)).astype(np.float32).astype(np.float64)
+    return th, x, t
+
+
+def _dev(a):
+    return torch.as_tensor(np.asarray(a, np.float32)).cuda()
+
+
+@pytest.mark.parametrize("n", [1, 37, 4096 + 5])
+def test_forward_matches_oracle(n):
+    from paper_2110_14494_gb300 import mlp_forward
+    th, x, _ = _problem(n)
+    y = mlp_forward(_dev(th), _dev(x)).cpu().numpy()
+    ref = M.forward(th, x)
+    assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 2e-2
+    assert np.abs(y - ref).max() < 5e-2 * np.abs(ref).max()
+
+
+def test_gradient_matches_oracle():
+    """The backward kernels (two BF16 tensor-core products per batch plus the
+    FP32 output and input layers) against backpropagation in FP64."""
+    from paper_2110_14494_gb300 import mlp_loss_grad
+    th, x, t = _problem(512, seed=2)
+    loss, g = mlp_loss_grad(_dev(th), _dev(x), _dev(t))
+    g = g.cpu().numpy().astype(np.float64)
+    lref, gref = M.loss_grad(th, x, t)
+    assert abs(loss.item() - lref) <= 1e-2 * lref
+    for name in M.SHAPES:
+        a, b = M.unpack(g)[name], M.unpack(gref)[name]
+        assert np.linalg.norm(a - b) <= 2e-2 * np.linalg.norm(b), name
+
+
+def test_adam_steps_match_oracle():
+    """Three full-batch Adam steps on the GPU against the oracle's updates."""
+    from paper_2110_14494_gb300 import mlp_train
+    th, x, t = _problem(256, seed=3)
+    p, m, v = _dev(th), torch.zeros(M.N_PARAMS, device="cuda"), torch.zeros(M.N_PARAMS, device="cuda")
+    mlp_train(p, m, v, 0, _dev(x), _dev(t), 1, lr=1e-3)
+    ref = th.copy()
+    mr, vr = np.zeros(M.N_PARAMS), np.zeros(M.N_PARAMS)
+    _, g = M.loss_grad(th, x, t)
+    M.adam(ref, mr, vr, g, 1, lr=1e-3)
+    d_gpu = p.cpu().numpy().astype(np.float64) - th
+    d_ref = ref - th
+    strong = np.abs(g) > 0.1 * np.abs(g).max()
+    # first step: every parameter with a clear gradient moves by lr against it
+    assert np.allclose(d_gpu[strong], d_ref[strong], rtol=2e-2, atol=2e-6)
+    assert np.mean(np.sign(d_gpu) == np.sign(d_ref)) > 0.97
+
+
+def test_training_follows_oracle():
+    """200 full-batch steps from the same start: both reduce the loss of a
+    smooth target by the same factor within 25 %."""
+    from paper_2110_14494_gb300 import mlp_loss_grad, mlp_train
+    r = np.random.default_rng(6)
+    x = r.uniform(-1, 1, (256, 2))
+    t = np.stack([np.sin(2 * x[:, 0]), x[:, 1] ** 2, x[:, 0] * x[:, 1], np.cos(x[:, 1]), x[:, 0], -x[:, 1]], 1)
+    th = W.mlp_init(21).astype(np.float32).astype(np.float64)
+    p, m, v = _dev(th), torch.zeros(M.N_PARAMS, device="cuda"), torch.zeros(M.N_PARAMS, device="cuda")
+    xd, td = _dev(x), _dev(t)
+    l0 = mlp_loss_grad(p, xd, td)[0].item()
+    mlp_train(p, m, v, 0, xd, td, 200, lr=3e-3)
+    l_gpu = mlp_loss_grad(p, xd, td)[0].item()
+    ref, mr, vr = th.copy(), np.zeros(M.N_PARAMS), np.zeros(M.N_PARAMS)
+    M.train(ref, mr, vr, 0, x, t, 200, lr=3e-3)
+    l_ref = M.loss_grad(ref, x, t)[0]
+    assert l_gpu < 0.05 * l0 and l_ref < 0.05 * l0
+    assert abs(np.log(l_gpu / l_ref)) < np.log(1.25) + 0.3, (l0, l_gpu, l_ref)
+
+
+def test_inference_on_many_points_sampled():
+    """2^20 query points; a random sample checked against the oracle."""
+    from paper_2110_14494_gb300 import mlp_forward
+    th, _, _ = _problem(1, seed=4)
+    r = np.random.default_rng(7)
+    n = 1 << 20
+    x = r.normal(0, 1, (n, 2)).astype(np.float32)
+    y = mlp_forward(_dev(th), _dev(x)).cpu().numpy()
+    idx = r.choice(n, 2000, replace=False)
+    ref = M.forward(th, x[idx].astype(np.float64))
+    assert np.linalg.norm(y[idx] - ref) / np.linalg.norm(ref) < 2e-2
+    assert np.isfinite(y).all()

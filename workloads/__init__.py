@@ -253,3 +253,33 @@ def swarm_en_grid(n: int = 256, lo: float = 10.0, hi: float = 1000.0) -> np.ndar
     """E/N values in Td, log-spaced: lo * (hi/lo)^(i/(n-1))."""
     i = np.arange(n, dtype=np.float64)
     return lo * np.power(hi / lo, i / max(n - 1, 1))
+
+
+# ---------------------------------------------------------------- surrogate
+MLP_SHAPES = (("W1", (128, 2)), ("b1", (128,)), ("W2", (128, 128)), ("b2", (128,)), ("W3", (6, 128)),
+              ("b3", (6,)))
+
+
+def mlp_init(offset: int) -> np.ndarray:
+    """Initial parameters of the 2-128-128-6 surrogate as one float64 vector in
+    the order W1, b1, W2, b2, W3, b3 (W[o][i]): Glorot-uniform weights
+    U(-a, a), a = sqrt(6 / (fan_in + fan_out)), zero biases."""
+    r = rng(offset)
+    parts = []
+    for name, shape in MLP_SHAPES:
+        if name[0] == "W":
+            a = np.sqrt(6.0 / (shape[0] + shape[1]))
+            parts.append(r.uniform(-a, a, size=shape).ravel())
+        else:
+            parts.append(np.zeros(shape).ravel())
+    return np.concatenate(parts)
+
+
+def mlp_query_points(n: int, offset: int, en_lo: float = 10.0, en_hi: float = 1000.0, f_lo: float = 0.1,
+                     f_hi: float = 0.3) -> np.ndarray:
+    """n points (E/N in Td, O2 fraction) uniform in (log10 E/N, f) over the box."""
+    r = rng(offset)
+    u = r.random((n, 2))
+    en = 10.0 ** (np.log10(en_lo) + u[:, 0] * (np.log10(en_hi) - np.log10(en_lo)))
+    f = f_lo + u[:, 1] * (f_hi - f_lo)
+    return np.stack([en, f], axis=1)
