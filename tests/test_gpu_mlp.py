@@ -114,3 +114,54 @@ def test_inference_on_many_points_sampled():
     ref = M.forward(th, x[idx].astype(np.float64))
     assert np.linalg.norm(y[idx] - ref) / np.linalg.norm(ref) < 2e-2
     assert np.isfinite(y).all()
+
+
+def test_surrogate_gain_over_swarms():
+    """The trained surrogate against the method without it.  Training table:
+    batched swarms at 64 E/N values (20-800 Td) x 4 O2 fractions; judge: 12
+    fresh swarms at random (E/N, f) from another seed.  The surrogate must
+    (i) predict the well-determined log targets (mu N, D_L N, D_T N, mean
+    energy, and alpha / N above 300 Td) of the held-out swarms within their
+    scatter, no worse than bilinear interpolation in the same table, and
+    (ii) answer queries at least 1e4 times faster than running a swarm."""
+    import time
+    from paper_2110_14494_gb300 import surrogate as S
+    from paper_2110_14494_gb300 import swarm_run
+    kw = dict(precision=32, n0=2000, n_steps=400, dt=1e-12, n_lo=500, n_hi=20000, seed=11)
+    EN = 20.0 * 40.0 ** (np.arange(64) / 63)
+    fr = np.array([0.1, 0.1667, 0.2333, 0.3])
+    X, Y, _ = S.swarm_points(lambda f: W.synthetic_air(o2_frac=f), EN, fr, W.N_GAS, **kw)
+    sur = S.Surrogate(W.mlp_init(40), X, Y)
+    trace, secs = sur.fit(4000, lr=2e-3)
+    assert trace[-1][1] < 0.05, trace[-4:]
+    q = W.mlp_query_points(12, 41, en_lo=25.0, en_hi=700.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    held = []
+    for k in range(len(q)):
+        res, _, _ = swarm_run(W.synthetic_air(o2_frac=q[k, 1]), q[k:k + 1, 0], batched=True, **dict(kw, seed=500 + k))
+        held.append(S.targets(res, q[k:k + 1, 0], W.N_GAS)[0])
+    torch.cuda.synchronize()
+    swarm_qps = len(q) / (time.perf_counter() - t0)
+    held = np.array(held)
+    pred = sur.predict(q[:, 0], q[:, 1])
+    table = Y.reshape(len(fr), len(EN), 6)
+    lin = S.table_interp(EN, fr, table, q[:, 0], q[:, 1])
+    cols = [0, 1, 2, 5]
+    err_s = np.sqrt(np.mean((pred[:, cols] - held[:, cols]) ** 2))
+    err_t = np.sqrt(np.mean((lin[:, cols] - held[:, cols]) ** 2))
+    hi = q[:, 0] > 300
+    err_a = np.sqrt(np.mean((pred[hi, 3] - held[hi, 3]) ** 2)) if hi.any() else 0.0
+    print("surrogate", err_s, "table", err_t, "alpha", err_a, "loss", trace[-1])
+    assert err_s < 0.08 and err_a < 0.15, (err_s, err_a)
+    assert err_s < 1.5 * err_t + 0.02, (err_s, err_t)
+    # query throughput: 2^20 standardized points on the device
+    xs = torch.as_tensor(sur.sx.fwd(S.features(W.mlp_query_points(1 << 20, 42)[:, 0], 0.2)).astype(np.float32)).cuda()
+    sur.predict_std(xs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(5):
+        sur.predict_std(xs)
+    torch.cuda.synchronize()
+    mlp_qps = 5 * (1 << 20) / (time.perf_counter() - t0)
+    assert mlp_qps > 1e4 * swarm_qps, (mlp_qps, swarm_qps)
