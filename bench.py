@@ -319,10 +319,25 @@ def run_mlp(args):
         if i >= max(args.warmup, 3):
             times.append(a.elapsed_time(b))
     ms = float(np.median(times))
+    # the pre-Blackwell tensor-core kernel (mma.sync) on the same points
+    from paper_2110_14494_gb300 import mlp_forward
+    times_mma = []
+    for i in range(max(args.warmup, 3) + 10):
+        flush.fill_(i & 0xff)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        mlp_forward(sur.params, xs, y, variant=1)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if i >= max(args.warmup, 3):
+            times_mma.append(a.elapsed_time(b))
+    ms_mma = float(np.median(times_mma))
     flop = 2.0 * (2 * 128 + 128 * 128 + 128 * 6)
     out = {"metric": "surrogate queries/s on 2^24 points (2-128-128-6, BF16 tensor cores, FP32 accumulate)",
            "value": n_q / (ms * 1e-3), "unit": "queries/s", "n_gpus": 1, "ms_per_batch": ms,
            "tflops": n_q * flop / (ms * 1e-3) / 1e12, "flop_per_query": flop,
+           "kernel": "tcgen05 (TMEM accumulators)", "mma_sync_kernel": {"ms_per_batch": ms_mma,
+                                                                    "value": n_q / (ms_mma * 1e-3)},
            "data": {"points": int(len(X)), "swarm_steps": steps, "electrons": 10000, "seconds": t_data},
            "training": {"adam_steps": n_train, "seconds": t_train, "ms_per_step": 1e3 * t_train / n_train,
                         "loss_first": trace[0][1], "loss_last": trace[-1][1]},

@@ -340,9 +340,17 @@ int swarm_run(const swarm_config *sc, int n_swarms, const double *EN_Td, void *d
 
 size_t mlp_workspace_bytes(int n_max);
 
-/* y = network(x) for n points (any n >= 0). */
+/* y = network(x) for n points (any n >= 0), on the tcgen05 tensor cores
+ * with the accumulators in tensor memory (h1 and h2 rounded to BF16). */
 int mlp_forward(const float *params, const float *x, float *y, long long n, void *d_workspace,
                 size_t workspace_bytes, pic_stream_t stream);
+
+/* The same with the kernel chosen: variant 0 = tcgen05 (as mlp_forward),
+ * 1 = warp-level mma.sync (the pre-Blackwell tensor-core path, kept for
+ * comparison).  If an internal wait on the tensor cores expires (it should
+ * not), the affected outputs are NaN. */
+int mlp_forward_variant(const float *params, const float *x, float *y, long long n, int variant,
+                        void *d_workspace, size_t workspace_bytes, pic_stream_t stream);
 
 /* Mean squared error L = sum (y - t)^2 / (6 n) over the batch and its
  * gradient with respect to params (device float32 [MLP_NPARAMS]); loss: device

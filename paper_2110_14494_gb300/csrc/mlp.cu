@@ -416,6 +416,270 @@ __global__ void __launch_bounds__(kInfWarps * 32) k_infer(const float* __restric
     }
 }
 
+// ------------------------------------------------------------------ inference on tcgen05
+// Fused forward pass on the fifth-generation tensor cores.  A block of 256
+// threads takes 128 points at a time (thread t: point t % 128, hidden units
+// 64 (t / 128) .. 64 (t / 128) + 63):
+//   1. layer 1 in FP32, tanh in packed BF16, written as the A operand (128
+//      points x 128 units) in shared memory;
+//   2. one thread issues eight 128 x 128 x 16 MMAs (A: h1, B: W2 resident in
+//      shared memory) into a 128-column FP32 accumulator in tensor memory;
+//   3. the accumulator rows are read back (row = point = TMEM lane), bias and
+//      tanh applied, and h2 written over the A operand;
+//   4. eight 128 x 16 x 16 MMAs against W3 (padded to 16 outputs) into the
+//      first 16 accumulator columns; the first half of the threads read the
+//      six outputs back, add b3 and store.
+// Operands use the canonical K-major layout without swizzle: core matrices
+// of 8 rows x 16 bytes stored contiguously, the next core matrix along K at
+// +128 bytes, the next 8-row group at +2048 bytes (the same strides for the
+// 16-row W3 tile, 4 KB).  Every MMA reads at most start + 15 x 2048 + 255
+// bytes, inside its 32 KB (4 KB) tile.  Waits on the MMA completion barrier are
+// bounded; on expiry the block writes NaN outputs, records the error and
+// leaves, releasing its tensor memory.
+constexpr int kTcThreads = 256, kTcRows = 128;
+constexpr uint32_t kTile = kTcRows * NH * 2;   // one 128 x 128 BF16 operand: 32 KB
+constexpr uint32_t kLbo = 128, kSbo = 2048;    // core-matrix strides (bytes) along K and along M/N
+constexpr uint32_t kB2Bytes = 16 * NH * 2;     // W3 padded to 16 rows: 4 KB
+constexpr long long kWaitLimit = 1ll << 26;
+
+struct TcSmem {
+    alignas(1024) unsigned char w2[kTile];   // B of layer 2: row o (output unit), K = input unit
+    alignas(1024) unsigned char a[kTile];    // A: row = point, K = unit (h1, then h2)
+    alignas(1024) unsigned char w3[kB2Bytes];
+    float w1[NH * NI], b1[NH], b2[NH], b3[NO];
+    alignas(8) unsigned long long bar;
+    uint32_t tmem;
+    int abort;
+};
+
+// byte offset of element (row r, k) in a K-major no-swizzle operand
+__host__ __device__ constexpr uint32_t kmajor_off(uint32_t r, uint32_t k) {
+    return (r >> 3) * kSbo + (k >> 3) * kLbo + (r & 7) * 16 + (k & 7) * 2;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: start address, leading (K) and stride
+// (M/N) byte offsets in 16-byte units, the fixed version bits 46-47 = 1,
+// no swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16
+// A and B (bits 7-9 = 1, 10-12 = 1), both K-major, N / 8 in bits 17-22,
+// M / 16 in bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16(uint32_t m, uint32_t n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((m >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+                 : "memory");
+}
+
+// Bounded wait for the barrier phase with the given parity; false on expiry.
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
+    for (long long it = 0; it < kWaitLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
+        "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// tanh of two floats as packed BF16 (hardware approximation)
+__device__ __forceinline__ uint32_t tanh_bf16x2(float lo, float hi) {
+    uint32_t in = pack_bf16(lo, hi), out;
+    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(out) : "r"(in));
+    return out;
+}
+
+__global__ void __launch_bounds__(kTcThreads) k_infer_tc(const float* __restrict__ th,
+                                                         const __nv_bfloat16* __restrict__ w2b,
+                                                         const float* __restrict__ x, float* __restrict__ y,
+                                                         long long n, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char tc_raw[];
+    // align the operand tiles to 1024 bytes
+    TcSmem& S = *reinterpret_cast<TcSmem*>(tc_raw + ((1024 - (smem_u32(tc_raw) & 1023)) & 1023));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row = tid & (kTcRows - 1), half = tid >> 7;
+    // operands and parameters
+    for (int k = tid; k < NH * NH; k += kTcThreads) {
+        const int o = k / NH, i = k % NH;
+        *reinterpret_cast<__nv_bfloat16*>(S.w2 + kmajor_off(o, i)) = w2b[k];
+    }
+    for (int k = tid; k < 16 * NH; k += kTcThreads) {
+        const int o = k / NH, i = k % NH;
+        *reinterpret_cast<__nv_bfloat16*>(S.w3 + kmajor_off(o, i)) =
+            __float2bfloat16_rn(o < NO ? th[OFF_W3 + o * NH + i] : 0.0f);
+    }
+    for (int k = tid; k < NH * NI; k += kTcThreads) S.w1[k] = th[OFF_W1 + k];
+    for (int k = tid; k < NH; k += kTcThreads) {
+        S.b1[k] = th[OFF_B1 + k];
+        S.b2[k] = th[OFF_B2 + k];
+    }
+    if (tid < NO) S.b3[tid] = th[OFF_B3 + tid];
+    const uint32_t bar = smem_u32(&S.bar);
+    if (tid == 0) {
+        S.abort = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&S.tmem)),
+                     "r"(128)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S.tmem;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    const uint32_t a_addr = smem_u32(S.a), w2_addr = smem_u32(S.w2), w3_addr = smem_u32(S.w3);
+    uint32_t parity = 0;
+    const long long n_tiles = (n + kTcRows - 1) / kTcRows;
+    for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const long long p = tile * kTcRows + row;
+        const bool valid = p < n;
+        // 1. layer 1 into the A operand (this thread: 64 units of its point)
+        {
+            const float x0 = valid ? x[p * NI] : 0.0f, x1 = valid ? x[p * NI + 1] : 0.0f;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int u0 = half * 64 + c * 8;
+                uint32_t w[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int u = u0 + 2 * e;
+                    const float z0 = fmaf(S.w1[u * NI + 1], x1, fmaf(S.w1[u * NI], x0, S.b1[u]));
+                    const float z1 = fmaf(S.w1[(u + 1) * NI + 1], x1, fmaf(S.w1[(u + 1) * NI], x0, S.b1[u + 1]));
+                    w[e] = tanh_bf16x2(z0, z1);
+                }
+                *reinterpret_cast<uint4*>(S.a + kmajor_off(row, u0)) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        fence_async_smem();
+        __syncthreads();
+        // 2. h1 W2^T into the accumulator
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int kk = 0; kk < NH / 16; ++kk)
+                tc_mma(tmem, sdesc(a_addr + kk * 2 * kLbo, kLbo, kSbo), sdesc(w2_addr + kk * 2 * kLbo, kLbo, kSbo),
+                       idesc_bf16(128, 128), kk > 0 ? 1u : 0u);
+            tc_commit(bar);
+        }
+        if (!bar_wait(bar, parity)) S.abort = 1;
+        parity ^= 1;
+        tc_fence_after();
+        __syncthreads();
+        if (S.abort) break;
+        // 3. bias, tanh, h2 over the A operand
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch) {
+            const int c0 = half * 64 + ch * 32;
+            float acc[32];
+            tmem_ld32(tmem + lane_base + (uint32_t)c0, acc);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                uint32_t w[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int q = c * 8 + 2 * e;
+                    w[e] = tanh_bf16x2(acc[q] + S.b2[c0 + q], acc[q + 1] + S.b2[c0 + q + 1]);
+                }
+                *reinterpret_cast<uint4*>(S.a + kmajor_off(row, c0 + c * 8)) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        tc_fence_before();
+        fence_async_smem();
+        __syncthreads();
+        // 4. h2 W3^T (16 padded outputs) into accumulator columns 0..15
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int kk = 0; kk < NH / 16; ++kk)
+                tc_mma(tmem, sdesc(a_addr + kk * 2 * kLbo, kLbo, kSbo), sdesc(w3_addr + kk * 2 * kLbo, kLbo, kSbo),
+                       idesc_bf16(128, 16), kk > 0 ? 1u : 0u);
+            tc_commit(bar);
+        }
+        if (!bar_wait(bar, parity)) S.abort = 1;
+        parity ^= 1;
+        tc_fence_after();
+        __syncthreads();
+        if (S.abort) break;
+        if (half == 0) {
+            float o8[8];
+            tmem_ld8(tmem + lane_base, o8);
+            if (valid)
+#pragma unroll
+                for (int o = 0; o < NO; ++o) y[p * NO + o] = o8[o] + S.b3[o];
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+    if (S.abort) {
+        // a wait expired: mark this block's remaining outputs and report
+        if (tid == 0) atomicOr(err, 1);
+        for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+            const long long p = tile * kTcRows + row;
+            if (half == 0 && p < n)
+                for (int o = 0; o < NO; ++o) y[p * NO + o] = __int_as_float(0x7fc00000);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(128) : "memory");
+    }
+}
+
 }  // namespace mlp
 
 // ------------------------------------------------------------------ C ABI
@@ -428,7 +692,7 @@ size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 struct TrainWs {
     __nv_bfloat16 *w2b, *w2t, *h1b, *h1t, *dz2b, *dz2t;
     float *h1, *z2, *dh1, *gw2, *head, *l1, *loss;
-    int* step;
+    int *step, *err;
     int splits, n_head, n_l1;
 };
 
@@ -459,6 +723,7 @@ size_t carve(void* base, int n, TrainWs* w) {
     w->l1 = (float*)take((size_t)w->n_l1 * kL1Part * 4);
     w->loss = (float*)take(64);
     w->step = (int*)take(64);
+    w->err = (int*)take(64);
     return (size_t)(p - p0);
 }
 
@@ -494,31 +759,50 @@ extern "C" size_t mlp_workspace_bytes(int n_max) {
     return carve(nullptr, n_max > 0 ? n_max : 64, &w);
 }
 
-extern "C" int mlp_forward(const float* params, const float* x, float* y, long long n, void* ws, size_t ws_bytes,
-                           pic_stream_t stream) {
-    if (!params || !x || !y || n < 0 || !ws || ((uintptr_t)ws & 255) || ws_bytes < mlp_workspace_bytes(0))
+extern "C" int mlp_forward_variant(const float* params, const float* x, float* y, long long n, int variant,
+                                   void* ws, size_t ws_bytes, pic_stream_t stream) {
+    if (!params || !x || !y || n < 0 || !ws || ((uintptr_t)ws & 255) || ws_bytes < mlp_workspace_bytes(0) ||
+        (variant != 0 && variant != 1))
         return PIC_ERR_ARG;
     if (n == 0) return PIC_OK;
     cudaStream_t s = (cudaStream_t)stream;
     TrainWs w;
     carve(ws, 64, &w);
     k_prep<<<(NH * NH + 255) / 256, 256, 0, s>>>(params, w.w2b, w.w2t);
-    static bool attr = false;
-    const int smem = (int)sizeof(InfSmem);
-    if (!attr) {
-        if (cudaFuncSetAttribute(k_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-            return PIC_ERR_CUDA;
-        attr = true;
-    }
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_infer, kInfWarps * 32, smem);
-    const long long tiles = (n + 15) / 16;
-    long long blocks = (long long)sms * (per_sm > 0 ? per_sm : 1);
-    if (blocks * kInfWarps > tiles) blocks = (tiles + kInfWarps - 1) / kInfWarps;
-    k_infer<<<(unsigned)blocks, kInfWarps * 32, smem, s>>>(params, w.w2b, x, y, n);
+    if (variant == 0) {
+        const int smem = (int)sizeof(TcSmem) + 1024;
+        if (cudaFuncSetAttribute(k_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+            return PIC_ERR_CUDA;
+        // blocks per SM from the shared memory each needs (plus the 1 KB the
+        // runtime reserves per block); each block also holds 128 of the 512
+        // tensor-memory columns, so at most 4
+        int smem_sm = 0;
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        per_sm = smem_sm / (smem + 1024);
+        per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
+        const long long tiles = (n + kTcRows - 1) / kTcRows;
+        long long blocks = (long long)sms * per_sm;
+        if (blocks > tiles) blocks = tiles;
+        k_infer_tc<<<(unsigned)blocks, kTcThreads, smem, s>>>(params, w.w2b, x, y, n, w.err);
+    } else {
+        const int smem = (int)sizeof(InfSmem);
+        if (cudaFuncSetAttribute(k_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+            return PIC_ERR_CUDA;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_infer, kInfWarps * 32, smem);
+        const long long tiles = (n + 15) / 16;
+        long long blocks = (long long)sms * (per_sm > 0 ? per_sm : 1);
+        if (blocks * kInfWarps > tiles) blocks = (tiles + kInfWarps - 1) / kInfWarps;
+        k_infer<<<(unsigned)blocks, kInfWarps * 32, smem, s>>>(params, w.w2b, x, y, n);
+    }
     return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ERR_CUDA;
+}
+
+extern "C" int mlp_forward(const float* params, const float* x, float* y, long long n, void* ws, size_t ws_bytes,
+                           pic_stream_t stream) {
+    return mlp_forward_variant(params, x, y, n, 0, ws, ws_bytes, stream);
 }
 
 extern "C" int mlp_loss_grad(const float* params, const float* x, const float* t, int n, float* grad, float* loss,

@@ -91,7 +91,8 @@ EXPORTS = ("pic_workspace_bytes", "pic_init", "pic_destroy", "pic_last_error", "
            "pic_deposit", "pic_weight_update", "pic_count", "pic_save", "pic_load", "pic_progress",
            "pic_profile", "pic_upload", "pic_download",
            "poisson_workspace_bytes", "poisson_solve", "poisson_solve_noalloc", "swarm_workspace_bytes",
-           "swarm_run", "swarm_autotune", "mlp_workspace_bytes", "mlp_forward", "mlp_loss_grad", "mlp_train")
+           "swarm_run", "swarm_autotune", "mlp_workspace_bytes", "mlp_forward", "mlp_forward_variant", "mlp_loss_grad",
+           "mlp_train")
 
 _lib = None
 
@@ -142,6 +143,7 @@ def lib():
     L.mlp_workspace_bytes.argtypes = [C.c_int]
     L.mlp_workspace_bytes.restype = C.c_size_t
     L.mlp_forward.argtypes = [VP, VP, VP, C.c_longlong, VP, C.c_size_t, VP]
+    L.mlp_forward_variant.argtypes = [VP, VP, VP, C.c_longlong, C.c_int, VP, C.c_size_t, VP]
     L.mlp_loss_grad.argtypes = [VP, VP, VP, C.c_int, VP, VP, VP, C.c_size_t, VP]
     L.mlp_train.argtypes = [VP, VP, VP, C.c_int, VP, VP, C.c_int, C.c_int, C.c_float, C.c_float, C.c_float,
                             C.c_float, VP, VP, C.c_size_t, VP]
@@ -394,15 +396,16 @@ def _mlp_ws(n):
     return _workspace(nb)
 
 
-def mlp_forward(params, x, y=None, stream=None):
-    """params: float32 CUDA [17670]; x: float32 CUDA [n][2] (standardized); returns y [n][6]."""
+def mlp_forward(params, x, y=None, stream=None, variant=0):
+    """params: float32 CUDA [17670]; x: float32 CUDA [n][2] (standardized); returns y [n][6].
+    variant 0: tcgen05 kernel; 1: mma.sync kernel."""
     import torch
     n = int(x.shape[0])
     if y is None:
         y = torch.empty((n, MLP_NO), dtype=torch.float32, device=x.device)
     ws, ptr = _mlp_ws(0)
-    _check(lib().mlp_forward(_ptr(params), _ptr(x), _ptr(y), n, C.c_void_p(ptr), lib().mlp_workspace_bytes(0),
-                             _stream(stream)), None, "mlp_forward")
+    _check(lib().mlp_forward_variant(_ptr(params), _ptr(x), _ptr(y), n, int(variant), C.c_void_p(ptr),
+                                     lib().mlp_workspace_bytes(0), _stream(stream)), None, "mlp_forward")
     return y
 
 

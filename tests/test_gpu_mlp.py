@@ -40,11 +40,13 @@ def _dev(a):
     return torch.as_tensor(np.asarray(a, np.float32)).cuda()
 
 
+@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("n", [1, 37, 4096 + 5])
-def test_forward_matches_oracle(n):
+def test_forward_matches_oracle(n, variant):
+    """variant 0: tcgen05 (TMEM accumulators, h1 and h2 in BF16); 1: mma.sync."""
     from paper_2110_14494_gb300 import mlp_forward
     th, x, _ = _problem(n)
-    y = mlp_forward(_dev(th), _dev(x)).cpu().numpy()
+    y = mlp_forward(_dev(th), _dev(x), variant=variant).cpu().numpy()
     ref = M.forward(th, x)
     assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 2e-2
     assert np.abs(y - ref).max() < 5e-2 * np.abs(ref).max()
@@ -102,15 +104,17 @@ def test_training_follows_oracle():
     assert abs(np.log(l_gpu / l_ref)) < np.log(1.25) + 0.3, (l0, l_gpu, l_ref)
 
 
-def test_inference_on_many_points_sampled():
-    """2^20 query points; a random sample checked against the oracle."""
+@pytest.mark.parametrize("variant", [0, 1])
+def test_inference_on_many_points_sampled(variant):
+    """2^20 + 77 query points (several blocks' worth of tiles and a ragged
+    tail); a random sample checked against the oracle."""
     from paper_2110_14494_gb300 import mlp_forward
     th, _, _ = _problem(1, seed=4)
     r = np.random.default_rng(7)
-    n = 1 << 20
+    n = (1 << 20) + 77
     x = r.normal(0, 1, (n, 2)).astype(np.float32)
-    y = mlp_forward(_dev(th), _dev(x)).cpu().numpy()
-    idx = r.choice(n, 2000, replace=False)
+    y = mlp_forward(_dev(th), _dev(x), variant=variant).cpu().numpy()
+    idx = np.concatenate([r.choice(n, 2000, replace=False), np.arange(n - 77, n)])
     ref = M.forward(th, x[idx].astype(np.float64))
     assert np.linalg.norm(y[idx] - ref) / np.linalg.norm(ref) < 2e-2
     assert np.isfinite(y).all()
