@@ -97,6 +97,19 @@ typedef struct pic_config {
     double cfl;               /* dt v_90 <= cfl dx, v_90 the 90 % quantile of the speeds (paper: 0.5) */
     double mobility;          /* electron mobility for dt_drt = eps0 / (e n_e,max mu_e), m^2/(V s) */
     double max_growth;        /* electrons may grow by at most this factor per step (paper: 1.2) */
+    /* photoionization (Sec. 2.4): discrete Monte Carlo photons.  Each ionization
+     * by an electron of weight w emits, with probability xi p_q / (p + p_q), one
+     * photon of weight w in an isotropic direction; its absorption distance
+     * follows Zheleznyak's function f(r) = (exp(-a r) - exp(-b r)) / (r ln(b/a)),
+     * a = chi_min p_O2, b = chi_max p_O2.  A photon absorbed inside the domain
+     * and outside the electrode creates an electron at rest and a positive ion
+     * there (after the step).  photo_xi = 0 disables it; it needs a grid. */
+    double photo_xi;          /* proportionality factor xi (paper: 0.075) */
+    double photo_pq;          /* quenching pressure p_q, Pa (paper: 40 mbar = 4000 Pa) */
+    double pressure;          /* gas pressure p, Pa */
+    double p_o2;              /* O2 partial pressure, Pa */
+    double chi_min, chi_max;  /* absorption coefficients per O2 pressure, 1/(m Pa) (Zheleznyak:
+                                 0.035 and 2 per mm Torr = 0.2625 and 15.0 per m Pa) */
 } pic_config;
 
 /* Host-side particle arrays (float64, any n).  Positions m, velocities m/s,
@@ -121,6 +134,7 @@ typedef struct pic_step_stats {
     double dt_last;                    /* time step of the last step, s */
     double t_total;                    /* simulated time since init, s */
     double ne_max;                     /* largest cell electron density after the last step, m^-3 */
+    long long n_photo;                 /* photoelectrons created (photons absorbed in the gas) */
 } pic_step_stats;
 
 typedef struct pic_ctx pic_ctx;

@@ -54,7 +54,8 @@ class Setup(C.Structure):
                 ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
                 ("dx", C.c_double), ("ox", C.c_double), ("oy", C.c_double), ("oz", C.c_double),
                 ("mask", PU8), ("Ex", PF), ("Ey", PF), ("Ez", PF), ("E0", C.c_double * 3),
-                ("boundary", C.c_int)]
+                ("boundary", C.c_int), ("photo_prob", C.c_double), ("chi_a", C.c_double),
+                ("chi_b", C.c_double)]
 
 
 class Parts(C.Structure):
@@ -65,7 +66,7 @@ class Parts(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [(k, C.c_longlong) for k in ("n_start", "n_children", "n_end", "n_attached",
-                                             "n_absorbed", "n_null", "n_clamped", "n_events")] + \
+                                             "n_absorbed", "n_null", "n_clamped", "n_events", "n_photo")] + \
                [("n_coll", C.c_longlong * 16), ("w_ion", C.c_double), ("w_att", C.c_double),
                 ("w_absorbed", C.c_double)]
 
@@ -114,6 +115,7 @@ def lib():
             L.orc_swarm_coefficients.argtypes = [PD, C.c_int, C.c_int, C.c_double, C.c_double, PD]
             L.orc_swarm_coefficients.restype = C.c_int
             L.orc_gather_field.argtypes = [C.POINTER(Setup), C.c_longlong, PD, PD, PD, PD]
+            L.orc_photon_draws.argtypes = [C.POINTER(Setup), C.c_uint64, C.c_uint32, C.c_int, PINT, PD, PD]
             L.orc_rates_at_energy.argtypes = [C.POINTER(Setup), C.c_longlong, PD, PD]
             L.orc_draw.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, PD]
             L.orc_derived_id.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32]
@@ -164,7 +166,8 @@ class Model:
     """Holds an orc_setup and the arrays it points to."""
 
     def __init__(self, gas: dict, dt: float, seed: int, prec: int = 64, grid: dict | None = None,
-                 field=None, E0=(0.0, 0.0, 0.0), mask=None, boundary: int = 0):
+                 field=None, E0=(0.0, 0.0, 0.0), mask=None, boundary: int = 0, photo=None):
+        """photo: None, or dict(xi, pq, pressure, p_o2, chi_min, chi_max) (Pa and 1/(m Pa))."""
         self.gas = gas
         self.nu, self.nu_max = rate_table(gas)
         self._keep = [np.ascontiguousarray(gas["eps"], np.float64), self.nu,
@@ -190,6 +193,10 @@ class Model:
             s.Ex, s.Ey, s.Ez = (_p(f, PF) for f in fs)
         s.E0[0], s.E0[1], s.E0[2] = E0
         s.boundary = boundary
+        if photo is not None and photo["xi"] > 0:
+            s.photo_prob = photo["xi"] * photo["pq"] / (photo["pressure"] + photo["pq"])
+            s.chi_a = photo["chi_min"] * photo["p_o2"]
+            s.chi_b = photo["chi_max"] * photo["p_o2"]
         self.s = s
         self.grid = grid
 
@@ -325,3 +332,13 @@ def swarm(gas: dict, EN_Td: float, n0: int, n_steps: int, dt: float, seed: int,
 
 RES_NAMES = ("W_flux", "W_bulk", "DL_flux", "DT_flux", "DL_bulk", "DT_bulk", "mean_eps",
              "k_ion", "k_att", "alpha", "eta")
+
+
+def photon_draws(m: "Model", pid: int, step: int, n: int):
+    """n photon draws of electron id pid at step `step` (draw indices 1..n):
+    (emitted [n] bool, distance [n] m, direction [n][3])."""
+    em = np.zeros(n, np.int32)
+    r = np.zeros(n)
+    d = np.zeros((n, 3))
+    lib().orc_photon_draws(C.byref(m.s), C.c_uint64(pid), step, n, _p(em, PINT), _p(r, PD), _p(d, PD))
+    return em.astype(bool), r, d

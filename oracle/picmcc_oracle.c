@@ -103,6 +103,10 @@ typedef struct orc_setup {
     const float *Ex, *Ey, *Ez;/* [nz][ny][nx] cell-centred field (V/m) or NULL = uniform E0 */
     double E0[3];
     int boundary;             /* 0 = specular reflection, 1 = absorb at domain faces */
+    /* photoionization (Sec. 2.4): photon emission probability per ionization
+     * xi p_q / (p + p_q) (0 = off) and the absorption coefficient range
+     * [chi_a, chi_b] = [chi_min, chi_max] p_O2, 1/m */
+    double photo_prob, chi_a, chi_b;
 } orc_setup;
 
 typedef struct orc_parts {
@@ -112,7 +116,7 @@ typedef struct orc_parts {
 } orc_parts;
 
 typedef struct orc_stats {
-    long long n_start, n_children, n_end, n_attached, n_absorbed, n_null, n_clamped, n_events;
+    long long n_start, n_children, n_end, n_attached, n_absorbed, n_null, n_clamped, n_events, n_photo;
     long long n_coll[ORC_MAX_PROC];
     double w_ion, w_att, w_absorbed;
 } orc_stats;
@@ -332,10 +336,74 @@ static int append(orc_parts *p, const double *x, const double *v, const double *
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Photoionization, Sec. 2.4 (discrete Monte Carlo photons).  Per ionization  */
+/* event (draw index k of the ionizing electron), draw (id, step,            */
+/* 0xD0000000 | k): u0 < photo_prob emits one photon of the electron's       */
+/* weight.  Absorption distance from Zheleznyak's function                   */
+/*   f(r) = (exp(-a r) - exp(-b r)) / (r ln(b/a)),                            */
+/* which equals the integral over chi in [a, b] of                            */
+/*   [1 / (chi ln(b/a))] * chi exp(-chi r):                                    */
+/* chi is drawn log-uniform on [a, b] (chi = a exp(u1 ln(b/a))) and then r     */
+/* exponential with rate chi (r = -ln(u2) / chi).  Direction isotropic:       */
+/* cos(theta) = 1 - 2 u3, azimuth 2 pi u0' of draw (id, step, 0xE0000000 | k). */
+/* A photon absorbed inside the domain and outside the electrode records a   */
+/* positive ion there and a photoelectron (id derived with tag 0xD0000000|k) */
+/* that joins the electrons at rest after the step.                          */
+/* Pins: the distance distribution against 1 - (E1(a r) - E1(b r))/ln(b/a)    */
+/* (scipy's exponential integral), the emission fraction, isotropy, charge   */
+/* neutrality of each photoionization.                                       */
+/* ------------------------------------------------------------------------ */
+static void photon_draw(const orc_setup *s, uint64_t id, uint32_t step, uint32_t k, int *emit, double *r,
+                        double n[3])
+{
+    double u[4], u2[4];
+    draw(s->seed, id, step, 0xD0000000u | k, u);
+    *emit = u[0] < s->photo_prob;
+    if (!*emit) return;
+    double chi = s->chi_a * exp(u[1] * log(s->chi_b / s->chi_a));
+    *r = -log(u[2]) / chi;
+    draw(s->seed, id, step, 0xE0000000u | k, u2);
+    iso_dir(u[3], u2[0], n);
+}
+
+static void photo_emit(const orc_setup *s, const double *x, double w, uint64_t id, uint32_t step, uint32_t k,
+                       orc_parts *ph, int64_t *q_pos)
+{
+    int emit;
+    double r, n[3];
+    photon_draw(s, id, step, k, &emit, &r, n);
+    if (!emit) return;
+    double xp[3] = {x[0] + r * n[0], x[1] + r * n[1], x[2] + r * n[2]};
+    double lo[3] = {s->ox, s->oy, s->oz};
+    int nn[3] = {s->nx, s->ny, s->nz};
+    for (int d = 0; d < 3; ++d) {
+        double h = lo[d] + (double)nn[d] * s->dx;
+        if (!(xp[d] >= lo[d] && xp[d] <= h)) return;
+    }
+    if (s->mask && s->mask[cell_of(s, xp[0], xp[1], xp[2])]) return;
+    if (q_pos) deposit_one(s, xp[0], xp[1], xp[2], w, q_pos);
+    double zero[3] = {0.0, 0.0, 0.0};
+    append(ph, xp, zero, zero, w, derived_id(s->seed, id, step, 0xD0000000u | k));
+}
+
+/* Test helper: n photon draws of electron `id` at step `step` with draw
+ * indices 1..n; emitted[k], r[k] and dir[3k..3k+2] per draw. */
+void orc_photon_draws(const orc_setup *s, uint64_t id, uint32_t step, int n, int *emitted, double *r, double *dir)
+{
+    for (int k = 0; k < n; ++k) {
+        double rr = 0.0, nd[3] = {0.0, 0.0, 0.0};
+        photon_draw(s, id, step, (uint32_t)(k + 1), &emitted[k], &rr, nd);
+        r[k] = rr;
+        dir[3 * k] = nd[0]; dir[3 * k + 1] = nd[1]; dir[3 * k + 2] = nd[2];
+    }
+}
+
 /* Advances particle i by t_left, appending ionization products to p (their
- * remaining time goes to tl[]).  Returns 0, or -3 when p is full. */
+ * remaining time goes to tl[]) and photoelectrons to ph.  Returns 0, or -3
+ * when p or ph is full. */
 static int advance(const orc_setup *s, orc_parts *p, long long i, double t_left, uint32_t step,
-                   double *tl, int64_t *q_pos, int64_t *q_neg, orc_stats *st)
+                   double *tl, int64_t *q_pos, int64_t *q_neg, orc_stats *st, orc_parts *ph)
 {
     double x[3] = {p->x[i], p->y[i], p->z[i]};
     double v[3] = {p->vx[i], p->vy[i], p->vz[i]};
@@ -390,6 +458,7 @@ static int advance(const orc_setup *s, orc_parts *p, long long i, double t_left,
             else { tl[p->n - 1] = t_left; st->n_children++; }
             st->w_ion += w;
             if (s->nx > 0 && q_pos) deposit_one(s, x[0], x[1], x[2], w, q_pos);
+            if (s->nx > 0 && s->photo_prob > 0.0 && ph) photo_emit(s, x, w, id, step, k, ph, q_pos);
         } else { /* attachment */
             st->w_att += w;
             st->n_attached++;
@@ -474,6 +543,18 @@ int orc_step(const orc_setup *s, orc_parts *p, uint32_t step, int first, int64_t
     st->n_start = n0;
     double *tl = (double *)calloc((size_t)(p->cap > 0 ? p->cap : 1), sizeof(double));
     if (!tl) return -2;
+    /* photoelectrons of the step, kept apart until the step ends */
+    orc_parts ph;
+    memset(&ph, 0, sizeof ph);
+    double *phb = NULL;
+    if (s->photo_prob > 0.0 && s->nx > 0) {
+        ph.cap = p->cap > 0 ? p->cap : 1;
+        phb = (double *)calloc((size_t)ph.cap * 10, sizeof(double));
+        ph.id = (uint64_t *)calloc((size_t)ph.cap, sizeof(uint64_t));
+        if (!phb || !ph.id) { free(tl); free(phb); free(ph.id); return -2; }
+        double **f[10] = {&ph.x, &ph.y, &ph.z, &ph.vx, &ph.vy, &ph.vz, &ph.ax, &ph.ay, &ph.az, &ph.w};
+        for (int q = 0; q < 10; ++q) *f[q] = phb + (size_t)q * ph.cap;
+    }
     int rc = 0;
     const double qm = Q_E / M_ELEC;
     for (long long i = 0; i < n0; ++i) {
@@ -487,15 +568,26 @@ int orc_step(const orc_setup *s, orc_parts *p, uint32_t step, int first, int64_t
             if (!first) *vv[d] = *vv[d] + 0.5 * s->dt * (an[d] - *ao[d]);
             *ao[d] = an[d];
         }
-        int r = advance(s, p, i, s->dt, step, tl, q_pos, q_neg, st);
+        int r = advance(s, p, i, s->dt, step, tl, q_pos, q_neg, st, phb ? &ph : NULL);
         if (r) rc = r;
     }
     for (long long i = n0; i < p->n; ++i) {
-        int r = advance(s, p, i, tl[i], step, tl, q_pos, q_neg, st);
+        int r = advance(s, p, i, tl[i], step, tl, q_pos, q_neg, st, phb ? &ph : NULL);
         if (r) rc = r;
     }
     for (long long i = 0; i < p->n; ++i) boundaries(s, p, i, st);
     compact(p);
+    /* photoelectrons join at rest with the acceleration of the field at their
+     * position (their first half-kick then adds nothing) */
+    for (long long j = 0; j < ph.n; ++j) {
+        double xp[3] = {ph.x[j], ph.y[j], ph.z[j]}, E[3], a[3], v0[3] = {0.0, 0.0, 0.0};
+        gather(s, xp[0], xp[1], xp[2], E);
+        for (int d = 0; d < 3; ++d) a[d] = -qm * E[d];
+        if (append(p, xp, v0, a, ph.w[j], ph.id[j]) != 0) rc = -3;
+        st->n_photo++;
+    }
+    free(phb);
+    free(ph.id);
     if (q_e && s->nx > 0) orc_deposit(s, p, q_e);
     st->n_end = p->n;
     free(tl);

@@ -27,6 +27,7 @@ enum : unsigned {
     kErrOverflow = 4u,       // fixed-point deposit out of range
     kErrStack = 8u,          // descendant stack exhausted inside one step
     kErrSplitCapacity = 16u, // merge/split output full
+    kErrPhotoCapacity = 32u, // photoelectron queue full
 };
 
 // ---------------------------------------------------------------- Philox4x32-10
@@ -114,12 +115,15 @@ struct DevState {
     unsigned long long n_events, n_null, n_clamped, n_absorbed, n_attached, n_children, n_processed;
     unsigned long long n_coll[kMaxProc];
     double w_ion, w_att, w_absorbed;
+    unsigned long long n_photons; // photoelectrons created
     long long pred_total;         // merge/split: predicted count in 2^-24 units
     unsigned long long n_updates; // cumulative parents + queued children advanced
     unsigned long long n_parents; // cumulative parents advanced
     unsigned long long n_fetch;   // work cursor of the parent kernel (items handed to warps)
     unsigned long long n_fetch_c; // work cursor of the children kernel
     unsigned long long n_spill;   // products spilled to the second queue (a descendant stack ran full)
+    unsigned long long n_photo;   // photoelectrons queued in this step, not yet appended
+    unsigned long long n_photo_src; // emitted photons queued, paths not yet drawn
     // end-of-step statistics for the time-step control
     long long qe_max;             // largest fixed-point electron deposit of a cell
     unsigned long long qe_sum;    // sum of the deposit (two's complement)

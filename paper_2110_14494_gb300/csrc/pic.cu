@@ -615,10 +615,12 @@ static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 struct Layout {
     size_t total = 0;
     size_t buf[2], cq[2], table, table64, E4, qe, qp, qn, st, cnt, start, sums, key, rank, msc, gas, rho, phi, phi_prev,
-        phi_x, mg, hostio;
+        phi_x, mg, photo, hostio;
 };
 
 static size_t real_size(int prec) { return prec == 64 ? 8 : 4; }
+
+static long long photo_cap(const pic_config* c);
 
 static Layout make_layout(const pic_config* c) {
     Layout L;
@@ -659,6 +661,14 @@ static Layout make_layout(const pic_config* c) {
     L.phi_prev = take(ncell * 8);
     L.phi_x = take(ncell * 8);
     L.mg = take(MG::bytes(c->nx, c->ny, c->nz, c->precision == 32, false));
+    {
+        const size_t np = (size_t)photo_cap(c);
+        L.photo = o;
+        for (int f = 0; f < 8; ++f) take(np * R);
+        take(np * 8);
+        take(np * 8);
+        take(np * 4);
+    }
     L.hostio = 0;
     L.total = o;
     return L;
@@ -802,7 +812,23 @@ static int validate(const pic_config* c) {
     if (c->coupled && (!(c->poisson_rtol > 0) || c->poisson_max_cycles < 1)) return PIC_ERR_ARG;
     if (c->coupled && !MG::supported(c->nx, c->ny, c->nz)) return PIC_ERR_ARG;
     if (c->adaptive_dt && (!(c->cfl > 0) || c->mobility < 0 || !(c->max_growth > 1.0))) return PIC_ERR_ARG;
+    if (c->photo_xi < 0) return PIC_ERR_ARG;
+    if (c->photo_xi > 0) {
+        if (!(c->photo_pq > 0) || !(c->pressure > 0) || !(c->p_o2 > 0) || !(c->chi_min > 0) ||
+            !(c->chi_max > c->chi_min))
+            return PIC_ERR_ARG;
+        // one photon per ionization at most
+        if (c->photo_xi * c->photo_pq / (c->pressure + c->photo_pq) > 1.0) return PIC_ERR_ARG;
+    }
     return PIC_OK;
+}
+
+// Photoelectron queue slots (photons absorbed in the gas, appended after each
+// step or product generation).
+static long long photo_cap(const pic_config* c) {
+    if (!(c->photo_xi > 0)) return 0;
+    const long long q = c->capacity / 8;
+    return q > 4096 ? q : 4096;
 }
 
 extern "C" size_t pic_workspace_bytes(const pic_config* cfg) {
@@ -931,7 +957,22 @@ template <class T> static PushArgs<T> make_args(pic_ctx* c, int mode) {
     A.q_pos = c->qp();
     A.q_neg = c->qn();
     A.boundary = c->cfg.boundary;
-    (void)mode;
+    if (mode == MODE_PIC && c->cfg.photo_xi > 0) {
+        const pic_config& f = c->cfg;
+        const double a = f.chi_min * f.p_o2, b = f.chi_max * f.p_o2;
+        A.photo_prob = (T)(f.photo_xi * f.photo_pq / (f.pressure + f.photo_pq));
+        A.chi_a = (T)a;
+        A.chi_log = (T)log(b / a);
+        const long long np = photo_cap(&f);
+        const size_t R = sizeof(T);
+        char* p = c->ws + c->L.photo;
+        T** arr[8] = {&A.pe_x, &A.pe_y, &A.pe_z, &A.pe_w, &A.ph_x, &A.ph_y, &A.ph_z, &A.ph_w};
+        for (int q = 0; q < 8; ++q) { *arr[q] = (T*)p; p += al256(np * R); }
+        A.pe_id = (uint64_t*)p; p += al256(np * 8);
+        A.ph_id = (uint64_t*)p; p += al256(np * 8);
+        A.pe_k = (uint32_t*)p;
+        A.cap_photo = np;
+    }
     return A;
 }
 
@@ -948,7 +989,7 @@ static int check_err(pic_ctx* c, const DevState& h) {
     cudaMemsetAsync(&c->st()->err, 0, sizeof(unsigned), c->s);
     char msg[160];
     snprintf(msg, sizeof msg, "device error flags 0x%x (1 output full, 2 child queue full, 4 fixed-point overflow, "
-             "8 descendant stack, 16 split output full)", h.err);
+             "8 descendant stack, 16 split output full, 32 photoelectron queue full)", h.err);
     if (h.err & kErrOverflow) return c->fail(PIC_ERR_OVERFLOW, msg);
     return c->fail(PIC_ERR_CAPACITY, msg);
 }
@@ -1244,6 +1285,12 @@ static void next_dt(pic_ctx* c, const DevState& h) {
 // step will leave.
 template <class T> static int extra_generations(pic_ctx* c, PushArgs<T>& A, int mode, bool stats) {
     for (int gen = 1;; ++gen) {
+        if (A.cap_photo > 0) {
+            // photoelectrons of the generations so far join the output
+            cudaError_t e = PushLaunch<T>::photo_append(A, 152 * 2, c->s);
+            if (e != cudaSuccess) return c->cuda_fail(e, "photoelectrons");
+            c->launches += 3;
+        }
         if (c->cfg.adaptive_dt && mode == MODE_PIC) {
             DevState* st = c->st();
             cudaMemsetAsync(&st->qe_max, 0, sizeof(long long) + sizeof(unsigned long long) + sizeof(st->vhist), c->s);
@@ -1370,6 +1417,7 @@ extern "C" int pic_step(pic_ctx* c, int n_steps, pic_step_stats* stats) {
         stats->dt_last = c->dt_prev;
         stats->t_total = c->t_total;
         stats->ne_max = c->ne_max;
+        stats->n_photo = (long long)h.n_photons;
     }
     return erc;
 }

@@ -50,6 +50,16 @@ template <class T> struct PushArgs {
     const uint8_t* mask;
     unsigned long long *q_e, *q_pos, *q_neg;
     int boundary;
+    // photoionization (Sec. 2.4): emission probability per ionization, the
+    // absorption coefficient range [chi_a, chi_a e^chi_log] (1/m), and the
+    // queue of photoelectrons appended after the step
+    T photo_prob, chi_a, chi_log;
+    T *pe_x, *pe_y, *pe_z, *pe_w;   // emitted photons: origin and weight
+    uint64_t* pe_id;                // emitting electron and draw index
+    uint32_t* pe_k;
+    T *ph_x, *ph_y, *ph_z, *ph_w;   // photoelectrons
+    uint64_t* ph_id;
+    long long cap_photo;
     // swarm mode
     double* mom;               // [kNMom] accumulators of this step
     long long n_lo, n_hi;
@@ -351,6 +361,46 @@ template <class T> struct Lane {
 
 enum { EV_CONTINUE = 0, EV_DONE = 1, EV_ATTACHED = 2, EV_IONIZED = 3 };
 
+// Electrode mask of the cell containing x (cell index by correctly rounded
+// (x - origin) / dx, folded into the grid).
+template <class T> __device__ __forceinline__ bool masked_at(const PushArgs<T>& A, const T x[3]) {
+    const int i = fold_idx((int)floor(div_rn(sub_rn(x[0], A.ox), A.dxr)), A.nx);
+    const int j = fold_idx((int)floor(div_rn(sub_rn(x[1], A.oy), A.dxr)), A.ny);
+    const int k = fold_idx((int)floor(div_rn(sub_rn(x[2], A.oz), A.dxr)), A.nz);
+    return A.mask[((long long)k * A.ny + j) * A.nx + i] != 0;
+}
+
+// Photon of an ionization event (Sec. 2.4, discrete Monte Carlo model), in
+// two parts.  In the collision loop only the emission test: draw (id, step,
+// 0xD0000000 | k) of the event's draw index k, u0 < photo_prob emits one
+// photon of the electron's weight; an emitted photon's origin (position,
+// weight, id, k) goes to a queue.  After each launch k_photo_resolve draws
+// its path: the absorption coefficient chi log-uniform on [a, b] (u1) and an
+// exponential path with rate chi (u2).  This mixture has exactly Zheleznyak's
+// absorption density: f(r) = (e^-ar - e^-br) / (r ln(b/a)) = integral over
+// chi in [a, b] of [1 / (chi ln(b/a))] chi e^(-chi r).  Direction: cos(theta)
+// = 1 - 2 u3 and azimuth 2 pi u0' of draw (id, step, 0xE0000000 | k).  A
+// photon absorbed inside the domain and outside the electrode records a
+// positive ion there and queues a photoelectron (id derived with tag
+// 0xD0000000 | k).
+template <class T>
+__device__ __forceinline__ void photo_test(const PushArgs<T>& A, const Keys& K, uint32_t step, uint64_t id,
+                                           uint32_t k, const T x[3], T w) {
+    const u32x4 r = draw_words(K, id, step, 0xD0000000u | k);
+    if (!(unif<T>(r.x) < A.photo_prob)) return;
+    const unsigned long long slot = atomicAdd(&A.st->n_photo_src, 1ull);
+    if ((long long)slot >= A.cap_photo) {
+        atomicOr(&A.st->err, kErrPhotoCapacity);
+        return;
+    }
+    A.pe_x[slot] = x[0];
+    A.pe_y[slot] = x[1];
+    A.pe_z[slot] = x[2];
+    A.pe_w[slot] = w;
+    A.pe_id[slot] = id;
+    A.pe_k[slot] = k;
+}
+
 // One candidate collision of the null-collision method (Sec. 2.1.1): flight
 // time tau = -ln(u0) / nu_max; if it ends the step, fly to the end; else fly
 // tau, pick the process with u1 nu_max against the cumulative rates at the
@@ -403,6 +453,10 @@ __device__ __forceinline__ int event(const PushArgs<T>& A, const Keys& K, uint32
     if (kind == PIC_PROC_IONIZATION) {
         sp = sp2;
         ls.w_ion += (double)L.w;
+        if (MODE == MODE_PIC && A.photo_prob > (T)0) {
+            const T xe[3] = {L.x[0] + L.d[0], L.x[1] + L.d[1], L.x[2] + L.d[2]};
+            photo_test(A, K, step, L.id, L.k - 1, xe, L.w);
+        }
         return EV_IONIZED;
     }
     return EV_CONTINUE;
@@ -427,12 +481,7 @@ __device__ __forceinline__ bool boundaries(const PushArgs<T>& A, T x[3], T v[3],
         if (x[d] < lo[d]) x[d] = lo[d];
         if (x[d] > hi[d]) x[d] = hi[d];
     }
-    if (!out && A.mask) {
-        int i = fold_idx((int)floor(div_rn(sub_rn(x[0], A.ox), A.dxr)), A.nx);
-        int j = fold_idx((int)floor(div_rn(sub_rn(x[1], A.oy), A.dxr)), A.ny);
-        int k = fold_idx((int)floor(div_rn(sub_rn(x[2], A.oz), A.dxr)), A.nz);
-        if (A.mask[((long long)k * A.ny + j) * A.nx + i]) out = true;
-    }
+    if (!out && A.mask && masked_at(A, x)) out = true;
     if (out) { ++ls.absorbed; ls.w_abs += (double)w; }
     return !out;
 }
@@ -467,6 +516,77 @@ __global__ void __launch_bounds__(256) k_field_kick(const PushArgs<T> A) {
             A.in.r[AX + d][i] = an;
         }
     }
+}
+
+// Path of every photon emitted in the launch before (see photo_test): the
+// absorbed ones inside the gas deposit their ion and queue a photoelectron.
+template <class T>
+__global__ void __launch_bounds__(256) k_photo_resolve(const PushArgs<T> A) {
+    const unsigned long long nq = A.st->n_photo_src;
+    const long long n = (long long)nq < A.cap_photo ? (long long)nq : A.cap_photo;
+    const uint32_t step = A.step;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const uint64_t id = A.pe_id[i];
+        const uint32_t k = A.pe_k[i];
+        const T w = A.pe_w[i];
+        const u32x4 r = draw_words(A.K, id, step, 0xD0000000u | k);
+        const T chi = A.chi_a * exp(unif<T>(r.y) * A.chi_log);
+        const T dist = -log(unif<T>(r.z)) / chi;
+        const u32x4 r2 = draw_words(A.K, id, step, 0xE0000000u | k);
+        T n3[3];
+        iso_dir(unif<T>(r.w), unif<T>(r2.x), n3);
+        const T xp[3] = {A.pe_x[i] + dist * n3[0], A.pe_y[i] + dist * n3[1], A.pe_z[i] + dist * n3[2]};
+        const T lo[3] = {A.ox, A.oy, A.oz}, hi[3] = {A.hx, A.hy, A.hz};
+        bool in = true;
+        for (int d = 0; d < 3; ++d)
+            if (!(xp[d] >= lo[d] && xp[d] <= hi[d])) in = false;
+        if (!in || (A.mask && masked_at(A, xp))) continue;
+        if (A.q_pos) deposit(xp[0], xp[1], xp[2], w, A.ox, A.oy, A.oz, A.dxr, A.nx, A.ny, A.nz, A.q_pos, A.st);
+        const unsigned long long slot = atomicAdd(&A.st->n_photo, 1ull);
+        if ((long long)slot >= A.cap_photo) {
+            atomicOr(&A.st->err, kErrPhotoCapacity);
+            continue;
+        }
+        A.ph_x[slot] = xp[0];
+        A.ph_y[slot] = xp[1];
+        A.ph_z[slot] = xp[2];
+        A.ph_w[slot] = w;
+        A.ph_id[slot] = derived_id(A.K, id, step, 0xD0000000u | k);
+    }
+}
+
+// Photoelectrons queued by k_photo_resolve join the output buffer at rest, with
+// the acceleration of the field at their position (so the next step's
+// half-kick adds nothing they did not experience), and their charge is
+// deposited with the electrons of the step.
+template <class T>
+__global__ void __launch_bounds__(256) k_photo_append(const PushArgs<T> A) {
+    const unsigned long long nq = A.st->n_photo;
+    const long long n = (long long)nq < A.cap_photo ? (long long)nq : A.cap_photo;
+    const T qm = (T)(kQ / kMe);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const T x[3] = {A.ph_x[i], A.ph_y[i], A.ph_z[i]};
+        const T w = A.ph_w[i];
+        T E[3];
+        gather(A, x, E);
+        const T v[3] = {(T)0, (T)0, (T)0};
+        const T a[3] = {-qm * E[0], -qm * E[1], -qm * E[2]};
+        const unsigned long long slot = atomicAdd(&A.st->n_out, 1ull);
+        if ((long long)slot >= A.cap_out) {
+            atomicOr(&A.st->err, kErrOutCapacity);
+            continue;
+        }
+        store(A.out, slot, x, v, a, w, A.ph_id[i]);
+        if (A.q_e) deposit(x[0], x[1], x[2], w, A.ox, A.oy, A.oz, A.dxr, A.nx, A.ny, A.nz, A.q_e, A.st);
+    }
+}
+
+// Closes the photoelectron queue of the launch before.
+static __global__ void k_photo_done(DevState* st, long long cap) {
+    const unsigned long long n = st->n_photo;
+    st->n_photons += n < (unsigned long long)cap ? n : (unsigned long long)cap;
+    st->n_photo = 0;
+    st->n_photo_src = 0;
 }
 
 // Swarm resampling in place (decided from the count after the previous step):
@@ -860,6 +980,7 @@ template <class T> struct PushLaunch {
                                cudaStream_t s);
     static cudaError_t field_kick(const PushArgs<T>& A, int grid, cudaStream_t s);
     static cudaError_t resample(const PushArgs<T>& A, int grid, cudaStream_t s);
+    static cudaError_t photo_append(const PushArgs<T>& A, int grid, cudaStream_t s);
     static size_t smem_bytes(int n_bins);
     static int blocks_per_sm(int mode, int n_bins);
 };

@@ -71,6 +71,13 @@ template <class T> cudaError_t PushLaunch<T>::field_kick(const PushArgs<T>& A, i
     return cudaGetLastError();
 }
 
+template <class T> cudaError_t PushLaunch<T>::photo_append(const PushArgs<T>& A, int grid, cudaStream_t s) {
+    k_photo_resolve<T><<<grid, 256, 0, s>>>(A);
+    k_photo_append<T><<<grid, 256, 0, s>>>(A);
+    k_photo_done<<<1, 1, 0, s>>>(A.st, A.cap_photo);
+    return cudaGetLastError();
+}
+
 template <class T> cudaError_t PushLaunch<T>::resample(const PushArgs<T>& A, int grid, cudaStream_t s) {
     k_resample<T><<<grid, 256, 0, s>>>(A);
     k_resample_commit<<<1, 1, 0, s>>>(A.st);

@@ -43,7 +43,20 @@ class pic_config(C.Structure):
                 ("sort_interval", C.c_int), ("coupled", C.c_int), ("v_lo", C.c_double), ("v_hi", C.c_double),
                 ("v_mask", C.c_double), ("poisson_rtol", C.c_double), ("poisson_max_cycles", C.c_int),
                 ("adaptive_dt", C.c_int), ("cfl", C.c_double), ("mobility", C.c_double),
-                ("max_growth", C.c_double)]
+                ("max_growth", C.c_double), ("photo_xi", C.c_double), ("photo_pq", C.c_double),
+                ("pressure", C.c_double), ("p_o2", C.c_double), ("chi_min", C.c_double), ("chi_max", C.c_double)]
+
+
+# Zheleznyak's absorption coefficients, 0.035 and 2 per (mm Torr), in 1/(m Pa)
+TORR = 101325.0 / 760.0
+ZHELEZNYAK_CHI_MIN = 0.035 / (1e-3 * TORR)
+ZHELEZNYAK_CHI_MAX = 2.0 / (1e-3 * TORR)
+K_BOLTZMANN = 1.380649e-23
+
+
+def gas_pressure(n_gas: float, T: float = 300.0) -> float:
+    """Ideal-gas pressure (Pa) of number density n_gas (m^-3) at temperature T (K)."""
+    return n_gas * K_BOLTZMANN * T
 
 
 class pic_particles_host(C.Structure):
@@ -57,7 +70,7 @@ class pic_step_stats(C.Structure):
                                             "n_processed", "n_weight_updates", "n_sorts")] + \
                [("w_ion", C.c_double), ("w_att", C.c_double), ("w_absorbed", C.c_double),
                 ("poisson_cycles", C.c_int), ("poisson_rel_res", C.c_double), ("dt_last", C.c_double),
-                ("t_total", C.c_double), ("ne_max", C.c_double)]
+                ("t_total", C.c_double), ("ne_max", C.c_double), ("n_photo", C.c_longlong)]
 
 
 class pic_profile_times(C.Structure):
@@ -207,7 +220,8 @@ class PicContext:
     def __init__(self, gas: dict, grid: dict, *, precision=32, capacity=1 << 20, seed=1, dt=1e-12, mask=None,
                  n_ppc=75, w_min=1.0, growth_trigger=0.0, particle_cap=0, boundary=0, sort_interval=0,
                  coupled=False, v_lo=0.0, v_hi=0.0, v_mask=0.0, poisson_rtol=1e-6, poisson_max_cycles=100,
-                 adaptive_dt=False, cfl=0.5, mobility=0.06, max_growth=1.2, stream=None):
+                 adaptive_dt=False, cfl=0.5, mobility=0.06, max_growth=1.2, photo_xi=0.0, photo_pq=4000.0,
+                 pressure=None, p_o2=None, chi_min=ZHELEZNYAK_CHI_MIN, chi_max=ZHELEZNYAK_CHI_MAX, stream=None):
         import torch
         self.gas = Gas(gas)
         c = pic_config()
@@ -220,6 +234,11 @@ class PicContext:
         c.v_lo, c.v_hi, c.v_mask, c.poisson_rtol, c.poisson_max_cycles = v_lo, v_hi, v_mask, poisson_rtol, \
             poisson_max_cycles
         c.adaptive_dt, c.cfl, c.mobility, c.max_growth = int(adaptive_dt), cfl, mobility, max_growth
+        # photoionization: pressure from the gas density at 300 K unless given; p_O2 = 20 % of it
+        p = pressure if pressure is not None else gas_pressure(float(gas["n_gas"]))
+        c.photo_xi, c.photo_pq, c.pressure = photo_xi, photo_pq, p
+        c.p_o2 = p_o2 if p_o2 is not None else 0.2 * p
+        c.chi_min, c.chi_max = chi_min, chi_max
         self.cfg = c
         self.grid = grid
         self.ncell = grid["nx"] * grid["ny"] * grid["nz"]

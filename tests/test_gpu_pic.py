@@ -270,3 +270,56 @@ def test_coupled_field_matches_oracle_solve(prec):
     ctx.step(1)
     phi2 = np.frombuffer(ctx.save(), np.float64, count=n, offset=len(blob) - 8 * n).reshape(48, 32, 32)
     assert np.linalg.norm(phi2 - ref) / np.linalg.norm(ref) < (1e-8 if prec == 64 else 1e-5)
+
+
+def _photo_kw(prob):
+    from paper_2110_14494_gb300 import picmcc as P
+    pq, p = 4000.0, 101325.0
+    return dict(photo_xi=prob * (p + pq) / pq, photo_pq=pq, pressure=p, p_o2=0.2 * p,
+                chi_min=P.ZHELEZNYAK_CHI_MIN, chi_max=P.ZHELEZNYAK_CHI_MAX)
+
+
+def _photo_oracle(kw):
+    return dict(xi=kw["photo_xi"], pq=kw["photo_pq"], pressure=kw["pressure"], p_o2=kw["p_o2"],
+                chi_min=kw["chi_min"], chi_max=kw["chi_max"])
+
+
+@pytest.mark.parametrize("prec,steps", [(64, 3), (32, 1)])
+def test_step_with_photoionization_matches_oracle(prec, steps):
+    """Sec. 2.4: photons of ionization events (emission probability 0.5 here,
+    for many of them) from the same draws on both sides: the photoelectrons
+    (derived ids, at rest at the absorption point), their ions and every
+    other electron agree with the oracle."""
+    gas, F, mk, p0 = _setup(6000 if prec == 64 else 20000, prec, 4, vmax=7e6)
+    dt = 2e-12
+    kw = _photo_kw(0.5)
+    # photoelectron queue: capacity / 8 slots
+    ctx = _ctx(gas, GRID, prec, capacity=400000, seed=SEED, dt=dt, mask=mk, **kw)
+    ctx.set_field(*_field_dev(F))
+    ctx.set_particles(p0)
+    st = ctx.step(steps, stats=True)
+    n = GRID["nx"] * GRID["ny"] * GRID["nz"]
+    qe, qp = (torch.zeros(n, dtype=torch.int64, device="cuda") for _ in range(2))
+    ctx.deposit(q_e=qe, q_pos=qp)
+    gpu = ctx.get_particles()
+    m = O.Model(gas, dt, SEED, prec, GRID, F, mask=mk, photo=_photo_oracle(kw))
+    P = O.Particles(400000, p0)
+    rq_pos = np.zeros(n, np.int64)
+    n_photo = 0
+    for s in range(1, steps + 1):
+        rq_e = np.zeros(n, np.int64)
+        rc, ost = O.step(m, P, s, s == 1, rq_e, rq_pos, None)
+        assert rc == 0
+        n_photo += ost.n_photo
+    ref = P.view()
+    assert n_photo > 20
+    if prec == 64:
+        assert st.n_photo == n_photo
+        nc, og, orf, bad, worst = compare_sets(gpu, ref, GRID["dx"], 1e-12, v_floor=1.0)
+        assert og == 0 and orf == 0 and bad == 0, (og, orf, bad, worst)
+        for a, b in ((qe, rq_e), (qp, rq_pos)):
+            assert np.abs(a.cpu().numpy() - b).max() <= 64
+    else:
+        assert abs(st.n_photo - n_photo) <= max(2, 1e-3 * n_photo)
+        nc, og, orf, bad, worst = compare_sets(gpu, ref, GRID["dx"], 1e-5, v_floor=1e5)
+        assert worst["gross"] + og + orf <= 1e-4 * len(ref["id"]) + 4, (og, orf, worst)
