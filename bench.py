@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--trace", action="store_true", help="per-step statistics (diagnostics, slower kernels)")
     ap.add_argument("--boundary", type=int, default=1, help="0: reflect at the domain faces, 1: absorb (outflow)")
     ap.add_argument("--fixed-dt", action="store_true", help="keep dt = 2 ps (no time-step control)")
-    ap.add_argument("--workload", default="streamer", choices=["streamer", "swarms", "mlp"],
+    ap.add_argument("--workload", default="streamer", choices=["streamer", "streamer-full", "swarms", "mlp"],
                     help="streamer: the coupled 128^3 step (headline); swarms: 256 batched swarms")
     ap.add_argument("--swarm-block", type=int, default=0, help="batched swarms: block size (0 = autotune)")
     ap.add_argument("--swarm-bps", type=int, default=0, help="batched swarms: blocks per SM (0 = autotune)")
@@ -372,18 +372,31 @@ def main():
     import workloads as W
     from paper_2110_14494_gb300 import PicContext
 
-    wl = workload(args.grid, args.n_initial)
+    full = args.workload == "streamer-full"
+    if full:
+        # a bounded sample of the 15 ns run (about 7500 steps): --steps sets it
+        wl = W.streamer_full()
+        if args.steps == 1990:
+            args.steps = 300
+        # the 128^3 figures stand for the host and e2e legs; pinned host copies of 3.2e8 slots are not made
+        args.no_e2e = True
+    else:
+        wl = workload(args.grid, args.n_initial)
     g = wl["grid"]
     gas = W.synthetic_air()
     mask = W.needle_mask(g, wl["needle_length"], wl["needle_radius"])
-    cap = args.cap or (int(wl["particle_cap"] * 1.6) if args.grid == 128 else int(max(8 * args.n_initial, 1 << 20)))
+    if full or args.grid == 128:
+        cap = args.cap or int(wl["particle_cap"] * 1.6)
+    else:
+        cap = args.cap or int(max(8 * args.n_initial, 1 << 20))
+    photo = dict(photo_xi=wl["photo_xi"], photo_pq=wl["photo_pq"]) if full else {}
     w0 = wl["seed_n0"] * np.pi ** 1.5 * wl["seed_radius"] ** 3 / wl["n_initial"]
     ctx = PicContext(gas, g, precision=args.precision, capacity=cap, seed=2110144940 + rank, dt=wl["dt"],
                      mask=mask, n_ppc=wl["n_ppc"], w_min=wl["w_min"], growth_trigger=wl["growth_trigger"],
                      particle_cap=wl["particle_cap"], sort_interval=20, coupled=True, v_lo=wl["v_bottom"],
                      boundary=args.boundary, adaptive_dt=not args.fixed_dt, cfl=0.5, mobility=0.06,
                      max_growth=1.2,
-                     v_hi=wl["v_top"], v_mask=wl["v_top"], poisson_rtol=1e-6, poisson_max_cycles=200)
+                     v_hi=wl["v_top"], v_mask=wl["v_top"], poisson_rtol=1e-6, poisson_max_cycles=200, **photo)
     n0 = ctx.seed_gaussian(wl["seed_n0"], wl["seed_radius"], wl["seed_center"], w0)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -484,14 +497,17 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == 32 else "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.grid == 128 else f"streamer-{args.grid}^3",
-                       "grid": [g["nx"], g["ny"], g["nz"]], "dx_um": 20, "n_initial": n0,
+            "config": {"workload": ("streamer-256x256x512-fp32-photoionization (first %d steps of the 15 ns run)"
+                                    % args.steps) if full else
+                       (WORKLOAD if args.grid == 128 else f"streamer-{args.grid}^3"),
+                       "grid": [g["nx"], g["ny"], g["nz"]], "dx_um": round(g["dx"] * 1e6, 3), "n_initial": n0,
                        "particle_cap": wl["particle_cap"],
                        "dt": "fixed 2 ps" if args.fixed_dt else "adaptive <= 2 ps (CFL 0.5 on the 90% speed, "
                              "dielectric relaxation with mu_e = 0.06 m^2/Vs, electron growth <= 20%/step)",
                        "simulated_ns": round(fin.t_total * 1e9, 4), "last_dt_ps": round(fin.dt_last * 1e12, 4),
                        "ne_max": fin.ne_max, "boundary": "absorbing faces" if args.boundary == 1 else "reflecting",
                        "poisson": "multigrid-preconditioned CG, rtol 1e-6, every step",
+                       "photoionization": "xi 0.075, p_q 40 mbar, Zheleznyak absorption" if full else "off",
                        "l2": "flushed between timed steps (256 MB write outside the timed events)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "particles_trace": n_trace},

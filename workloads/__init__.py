@@ -158,6 +158,24 @@ def needle_mask(g: dict, length: float, radius: float) -> np.ndarray:
     return np.ascontiguousarray((rod | cap).astype(np.uint8))
 
 
+def streamer_full() -> dict:
+    """The full-size streamer: a 10 mm plate-plate gap at 15.6 kV on 256 x 256 x
+    512 cells of 19.53 um (5 x 5 x 10 mm), a 2 mm needle of 0.2 mm radius
+    hanging from the top plate, photoionization on (xi = 0.075, p_q = 40 mbar,
+    1 bar-equivalent density at 300 K, 20 % O2), up to 2e8 super-particles,
+    dt <= 2 ps.  The seed is not specified for this case; it is the 128^3
+    workload's Gaussian (peak 1e19 m^-3, 0.1 mm radius) at the needle tip."""
+    dx = 10e-3 / 512
+    g = grid_spec(256, 256, 512, dx)
+    L = 512 * dx
+    needle_len, needle_r = 2e-3, 0.2e-3
+    tip = (0.5 * 256 * dx, 0.5 * 256 * dx, L - needle_len)
+    return dict(grid=g, L=L, v_bottom=0.0, v_top=15.6e3, needle_length=needle_len, needle_radius=needle_r,
+                seed_n0=1e19, seed_radius=1e-4, seed_center=tip, n_initial=1_000_000,
+                particle_cap=200_000_000, dt=2e-12, n_ppc=75, w_min=1.0, growth_trigger=1.25,
+                photo_xi=0.075, photo_pq=4000.0, t_end=15e-9)
+
+
 def streamer_128() -> dict:
     """The 128^3 streamer workload: 20 um cells, plates at 0 V / 5.12 kV (20 kV/cm),
     a 0.5 mm needle of 0.1 mm radius hanging from the top plate, a Gaussian
