@@ -110,6 +110,16 @@ typedef struct pic_config {
     double p_o2;              /* O2 partial pressure, Pa */
     double chi_min, chi_max;  /* absorption coefficients per O2 pressure, 1/(m Pa) (Zheleznyak:
                                  0.035 and 2 per mm Torr = 0.2625 and 15.0 per m Pa) */
+    /* geometry 1: axisymmetric (Sec. 2.1.1-2.1.2).  Electrons still move in 3D
+     * (x, y, z); the field, densities and electrode live on an (r, z) mesh of
+     * nx radial cells from the axis x = y = 0 (origin[0] = origin[1] = 0,
+     * ny = 1).  The gathered field is projected, a = (a_r x/r, a_r y/r, a_z);
+     * deposits go to ring cells of volume 2 pi r dr dz; the coupled solve is
+     * the axisymmetric Poisson equation (see poisson_axi_solve); domain faces
+     * are the cylinder r = nx dx and the z planes. */
+    int geometry;             /* 0: 3D Cartesian, 1: axisymmetric */
+    int weight_interval;      /* also update weights every this many steps (paper: 10 in axisymmetric runs;
+                                 0 = only on growth) */
 } pic_config;
 
 /* Host-side particle arrays (float64, any n).  Positions m, velocities m/s,
@@ -257,6 +267,22 @@ size_t poisson_workspace_bytes(const poisson_config *pc);
 int poisson_solve(const poisson_config *pc, const double *rho, const uint8_t *mask, double *phi,
                   float *Ex, float *Ey, float *Ez, double rtol, int max_cycles, void *d_workspace,
                   size_t workspace_bytes, poisson_stats *stats, pic_stream_t stream);
+
+/* Axisymmetric variant (the paper's axisymmetric geometry, Sec. 2.1.1-2.1.2
+ * and 2.5): -(1/r) d/dr (r dphi/dr) - d2phi/dz2 = rho / eps0 on nr x nz square
+ * cells of side dx, cell i centred at r = (i + 1/2) dx from the axis; the
+ * outer cylinder r = nr dx homogeneous Neumann, z faces Dirichlet v_lo / v_hi,
+ * mask cells at v_mask.  Each row is the ring cell's flux balance divided by
+ * 2 pi dx (symmetric); flexible CG in float64 with a float64 multigrid
+ * V-cycle preconditioner until the CG residual satisfies ||b - A phi|| /
+ * ||b|| <= rtol.  rho, phi: device float64 [nz][nr]; mask: device uint8
+ * [nz][nr] or NULL; Er, Ez: optional device float32 [nz][nr] (both or
+ * neither).  Sizes must halve to a coarsest level of at most 4096 cells.
+ * Errors as poisson_solve. */
+size_t poisson_axi_workspace_bytes(int nr, int nz);
+int poisson_axi_solve(int nr, int nz, double dx, double v_lo, double v_hi, double v_mask, const double *rho,
+                      const uint8_t *mask, double *phi, float *Er, float *Ez, double rtol, int max_cycles,
+                      void *d_workspace, size_t workspace_bytes, poisson_stats *stats, pic_stream_t stream);
 
 /* Same solve as poisson_solve, for callers that cannot allocate device
  * memory (no workspace argument).  The paper has no counterpart: this is a

@@ -55,7 +55,7 @@ class Setup(C.Structure):
                 ("dx", C.c_double), ("ox", C.c_double), ("oy", C.c_double), ("oz", C.c_double),
                 ("mask", PU8), ("Ex", PF), ("Ey", PF), ("Ez", PF), ("E0", C.c_double * 3),
                 ("boundary", C.c_int), ("photo_prob", C.c_double), ("chi_a", C.c_double),
-                ("chi_b", C.c_double)]
+                ("chi_b", C.c_double), ("axi", C.c_int)]
 
 
 class Parts(C.Structure):
@@ -109,6 +109,11 @@ def lib():
             L.orc_poisson_cg.restype = C.c_int
             L.orc_grad_phi.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, PD, C.c_double,
                                        C.c_double, PD, PD, PD]
+            L.orc_poisson_axi.argtypes = [C.c_int, C.c_int, C.c_double, PD, PU8, C.c_double, C.c_double,
+                                          C.c_double, PD, C.c_double, C.c_int, PD, PINT]
+            L.orc_poisson_axi.restype = C.c_int
+            L.orc_grad_axi.argtypes = [C.c_int, C.c_int, C.c_double, PD, C.c_double, C.c_double, PD, PD]
+            L.orc_fixed_to_rho_axi.argtypes = [C.c_int, C.c_int, C.c_double, PI64, PI64, PI64, PD]
             L.orc_swarm_run.argtypes = [C.POINTER(Setup), C.POINTER(SwarmCfg), C.POINTER(Parts), PD,
                                         C.POINTER(C.c_longlong)]
             L.orc_swarm_run.restype = C.c_int
@@ -166,7 +171,7 @@ class Model:
     """Holds an orc_setup and the arrays it points to."""
 
     def __init__(self, gas: dict, dt: float, seed: int, prec: int = 64, grid: dict | None = None,
-                 field=None, E0=(0.0, 0.0, 0.0), mask=None, boundary: int = 0, photo=None):
+                 field=None, E0=(0.0, 0.0, 0.0), mask=None, boundary: int = 0, photo=None, axi: bool = False):
         """photo: None, or dict(xi, pq, pressure, p_o2, chi_min, chi_max) (Pa and 1/(m Pa))."""
         self.gas = gas
         self.nu, self.nu_max = rate_table(gas)
@@ -193,6 +198,7 @@ class Model:
             s.Ex, s.Ey, s.Ez = (_p(f, PF) for f in fs)
         s.E0[0], s.E0[1], s.E0[2] = E0
         s.boundary = boundary
+        s.axi = int(axi)
         if photo is not None and photo["xi"] > 0:
             s.photo_prob = photo["xi"] * photo["pq"] / (photo["pressure"] + photo["pq"])
             s.chi_a = photo["chi_min"] * photo["p_o2"]
@@ -290,6 +296,34 @@ def grad_phi(grid: dict, phi, v_lo, v_hi):
     E = [np.zeros(nx * ny * nz) for _ in range(3)]
     lib().orc_grad_phi(nx, ny, nz, h, _p(phi, PD), v_lo, v_hi, *(_p(e, PD) for e in E))
     return tuple(e.reshape(nz, ny, nx) for e in E)
+
+
+def poisson_axi(nr: int, nz: int, h: float, rho, mask, v_mask, v_lo, v_hi, rtol=1e-12, max_iter=200000,
+                phi0=None):
+    """Axisymmetric solve on [nz][nr] ring cells; returns (phi, rel_res, iterations)."""
+    rho = np.ascontiguousarray(rho, np.float64).ravel()
+    phi = np.zeros(nr * nz) if phi0 is None else np.ascontiguousarray(phi0, np.float64).ravel().copy()
+    mk = None if mask is None else np.ascontiguousarray(mask, np.uint8).ravel()
+    rr, it = C.c_double(), C.c_int()
+    rc = lib().orc_poisson_axi(nr, nz, h, _p(rho, PD), _p(mk, PU8), v_mask, v_lo, v_hi, _p(phi, PD), rtol,
+                               max_iter, C.byref(rr), C.byref(it))
+    if rc:
+        raise RuntimeError("orc_poisson_axi failed")
+    return phi.reshape(nz, nr), rr.value, it.value
+
+
+def grad_axi(nr: int, nz: int, h: float, phi, v_lo, v_hi):
+    phi = np.ascontiguousarray(phi, np.float64).ravel()
+    Er, Ez = np.zeros(nr * nz), np.zeros(nr * nz)
+    lib().orc_grad_axi(nr, nz, h, _p(phi, PD), v_lo, v_hi, _p(Er, PD), _p(Ez, PD))
+    return Er.reshape(nz, nr), Ez.reshape(nz, nr)
+
+
+def fixed_to_rho_axi(nr: int, nz: int, dx: float, q_e, q_pos, q_neg) -> np.ndarray:
+    q_e, q_pos, q_neg = (np.ascontiguousarray(a, np.int64) for a in (q_e, q_pos, q_neg))
+    rho = np.zeros(q_e.size)
+    lib().orc_fixed_to_rho_axi(nr, nz, dx, _p(q_e, PI64), _p(q_pos, PI64), _p(q_neg, PI64), _p(rho, PD))
+    return rho
 
 
 def gather_field(m: Model, x, y, z) -> np.ndarray:

@@ -25,6 +25,7 @@
 #define M_ELEC 9.1093837015e-31
 #define EPS_0 8.8541878128e-12
 #define TWO_PI 6.283185307179586476925286766559
+#define M_PI_ORC 3.14159265358979323846264338327950
 
 #define ORC_MAX_PROC 16
 #define ORC_NMOM 16
@@ -107,6 +108,11 @@ typedef struct orc_setup {
      * xi p_q / (p + p_q) (0 = off) and the absorption coefficient range
      * [chi_a, chi_b] = [chi_min, chi_max] p_O2, 1/m */
     double photo_prob, chi_a, chi_b;
+    /* axisymmetric geometry (Sec. 2.1.1-2.1.2): particles move in 3D, the
+     * field, densities and mask live on the (r, z) mesh of nx radial cells
+     * from the axis x = y = 0 (ny = 1); the field arrays hold E_r (Ex) and
+     * E_z (Ez) */
+    int axi;
 } orc_setup;
 
 typedef struct orc_parts {
@@ -189,9 +195,34 @@ static void axis_interp(double x, double o, double dx, int n, int *i0, int *i1, 
     *f = (n > 1) ? s - (double)i : 0.0;
 }
 
+/* Axisymmetric field at a 3D position: E_r and E_z bilinear in (r, z) at the
+ * cell centres, the radial part projected: (E_r x/r, E_r y/r, E_z), and 0 on
+ * the axis (Sec. 2.1.1). */
+static void gather_axi(const orc_setup *s, double x, double y, double z, double E[3])
+{
+    double r = sqrt(x * x + y * y);
+    int ir[2], iz[2];
+    double fr, fz;
+    axis_interp(r, s->ox, s->dx, s->nx, &ir[0], &ir[1], &fr);
+    axis_interp(z, s->oz, s->dx, s->nz, &iz[0], &iz[1], &fz);
+    double gr[2] = {1.0 - fr, fr}, gz[2] = {1.0 - fz, fz};
+    double er = 0.0, ez = 0.0;
+    for (int c = 0; c < 4; ++c) {
+        int dz = c >> 1, dr = c & 1;
+        long long idx = (long long)iz[dz] * s->nx + ir[dr];
+        er += (gz[dz] * gr[dr]) * (double)s->Ex[idx];
+        ez += (gz[dz] * gr[dr]) * (double)s->Ez[idx];
+    }
+    double inv = r > 0.0 ? er / r : 0.0;
+    E[0] = inv * x;
+    E[1] = inv * y;
+    E[2] = ez;
+}
+
 static void gather(const orc_setup *s, double x, double y, double z, double E[3])
 {
     if (s->Ex == NULL) { E[0] = s->E0[0]; E[1] = s->E0[1]; E[2] = s->E0[2]; return; }
+    if (s->axi) { gather_axi(s, x, y, z, E); return; }
     int ix[2], iy[2], iz[2];
     double fx, fy, fz;
     axis_interp(x, s->ox, s->dx, s->nx, &ix[0], &ix[1], &fx);
@@ -220,10 +251,27 @@ static void gather(const orc_setup *s, double x, double y, double z, double E[3]
 /* ------------------------------------------------------------------------ */
 static int fold(int i, int n) { return i < 0 ? 0 : (i >= n ? n - 1 : i); }
 
+/* The mesh point of a particle position: itself, or on an axisymmetric mesh
+ * (r, centre of the single y cell, z) with r = sqrt(x^2 + y^2) evaluated in
+ * the precision s->prec. */
+static void grid_point(const orc_setup *s, double *x, double *y)
+{
+    if (!s->axi) return;
+    if (s->prec == 32) {
+        float xf = (float)*x, yf = (float)*y;
+        *x = (double)sqrtf(xf * xf + yf * yf);
+        *y = (double)((float)s->oy + 0.5f * (float)s->dx);
+    } else {
+        *x = sqrt(*x * *x + *y * *y);
+        *y = s->oy + 0.5 * s->dx;
+    }
+}
+
 static void deposit_one(const orc_setup *s, double x, double y, double z, double w, int64_t *q)
 {
     int64_t qc[8];
     int i0, j0, k0;
+    grid_point(s, &x, &y);
     if (s->prec == 32) {
         float xf = (float)x, yf = (float)y, zf = (float)z, wf = (float)w;
         float dxf = (float)s->dx;
@@ -278,6 +326,7 @@ void orc_deposit(const orc_setup *s, const orc_parts *p, int64_t *q)
 static long long cell_of(const orc_setup *s, double x, double y, double z)
 {
     int ii, jj, kk;
+    grid_point(s, &x, &y);
     if (s->prec == 32) {
         float dxf = (float)s->dx;
         ii = (int)floorf(((float)x - (float)s->ox) / dxf);
@@ -377,10 +426,11 @@ static void photo_emit(const orc_setup *s, const double *x, double w, uint64_t i
     double xp[3] = {x[0] + r * n[0], x[1] + r * n[1], x[2] + r * n[2]};
     double lo[3] = {s->ox, s->oy, s->oz};
     int nn[3] = {s->nx, s->ny, s->nz};
-    for (int d = 0; d < 3; ++d) {
+    for (int d = s->axi ? 2 : 0; d < 3; ++d) {
         double h = lo[d] + (double)nn[d] * s->dx;
         if (!(xp[d] >= lo[d] && xp[d] <= h)) return;
     }
+    if (s->axi && !(sqrt(xp[0] * xp[0] + xp[1] * xp[1]) <= (double)s->nx * s->dx)) return;
     if (s->mask && s->mask[cell_of(s, xp[0], xp[1], xp[2])]) return;
     if (q_pos) deposit_one(s, xp[0], xp[1], xp[2], w, q_pos);
     double zero[3] = {0.0, 0.0, 0.0};
@@ -484,7 +534,28 @@ static void boundaries(const orc_setup *s, orc_parts *p, long long i, orc_stats 
     double lo[3] = {s->ox, s->oy, s->oz};
     int n[3] = {s->nx, s->ny, s->nz};
     int out = 0;
+    if (s->axi) {
+        /* the cylinder r = R: outflow, or specular reflection r -> 2R - r with
+         * the radial velocity reversed */
+        double R = (double)s->nx * s->dx;
+        double r = sqrt(p->x[i] * p->x[i] + p->y[i] * p->y[i]);
+        if (s->boundary == 1) {
+            if (r > R) out = 1;
+        } else {
+            for (int it = 0; it < 8 && r > R; ++it) {
+                double rn = 2.0 * R - r, sc = rn / r;
+                double ux = p->x[i] / r, uy = p->y[i] / r;
+                double vr = p->vx[i] * ux + p->vy[i] * uy;
+                p->x[i] *= sc;
+                p->y[i] *= sc;
+                p->vx[i] -= 2.0 * vr * ux;
+                p->vy[i] -= 2.0 * vr * uy;
+                r = fabs(rn);
+            }
+        }
+    }
     for (int d = 0; d < 3; ++d) {
+        if (s->axi && d < 2) continue;
         double l = lo[d], h = lo[d] + (double)n[d] * s->dx;
         if (s->boundary == 1) {
             if (*X[d] < l || *X[d] > h) out = 1;
@@ -632,8 +703,11 @@ long long orc_seed_gaussian(const orc_setup *s, double n0, double radius, double
                 double xc = s->ox + ((double)i + 0.5) * s->dx;
                 double yc = s->oy + ((double)j + 0.5) * s->dx;
                 double zc = s->oz + ((double)k + 0.5) * s->dx;
-                double r2 = (xc - cx) * (xc - cx) + (yc - cy) * (yc - cy) + (zc - cz) * (zc - cz);
-                double expct = n0 * exp(-r2 / (radius * radius)) * dV / w0;
+                /* axisymmetric: ring cell at radius xc, volume pi (2i + 1) dx^3, centre on the axis */
+                double r2 = s->axi ? xc * xc + (zc - cz) * (zc - cz)
+                                   : (xc - cx) * (xc - cx) + (yc - cy) * (yc - cy) + (zc - cz) * (zc - cz);
+                double dVc = s->axi ? M_PI_ORC * (double)(2 * i + 1) * s->dx * s->dx * s->dx : dV;
+                double expct = n0 * exp(-r2 / (radius * radius)) * dVc / w0;
                 double fl = floor(expct);
                 long long cnt = (long long)fl;
                 uint32_t ctr[4] = {(uint32_t)c, 0u, 0u, 0xB0000000u}, o[4];
@@ -645,6 +719,12 @@ long long orc_seed_gaussian(const orc_setup *s, double n0, double radius, double
                     double x[3] = {s->ox + ((double)i + unif(o[0])) * s->dx,
                                    s->oy + ((double)j + unif(o[1])) * s->dx,
                                    s->oz + ((double)k + unif(o[2])) * s->dx};
+                    if (s->axi) {
+                        /* uniform in the ring: r^2 uniform in [i^2, (i+1)^2] dx^2, angle uniform */
+                        double r = s->dx * sqrt((double)i * i + unif(o[0]) * (double)(2 * i + 1));
+                        x[0] = r * cos(TWO_PI * unif(o[1]));
+                        x[1] = r * sin(TWO_PI * unif(o[1]));
+                    }
                     if (append(p, x, zero, zero, w0, nid++) != 0) return -3;
                 }
             }
@@ -937,6 +1017,149 @@ int orc_poisson_cg(int nx, int ny, int nz, double h, const double *rho, const ui
 
 /* E = -grad(phi) at cell centres by central differences, with the same ghost
  * values as the Poisson stencil (Neumann: mirror; Dirichlet: 2 phi_b - phi). */
+/* ------------------------------------------------------------------------ */
+/* Axisymmetric Poisson (Sec. 2.5 in the axisymmetric geometry of Sec. 2.1.2):  */
+/* -(1/r) d/dr (r dphi/dr) - d2phi/dz2 = rho / eps0 on nr x nz square ring     */
+/* cells of side h, cell i at r = (i + 1/2) h.  Integrating over the ring cell */
+/* and dividing by 2 pi h gives a symmetric system: face coefficients r_face/h */
+/* = i (inner, zero on the axis), i + 1 (outer), i + 1/2 (each axial face);    */
+/* right-hand side (i + 1/2) h^2 rho / eps0.  Outer cylinder: no flux; z faces */
+/* Dirichlet v_lo, v_hi (ghost 2v - phi); mask cells at v_mask.  Solved by CG  */
+/* with a Jacobi preconditioner (deliberately not multigrid) to ||r||/||b|| <= */
+/* rtol.  Pins: plates only gives phi linear in z; the discrete Gauss law (the */
+/* boundary fluxes balance the charge); O(h^2) convergence to a Bessel-sine    */
+/* manufactured solution.                                                     */
+/* ------------------------------------------------------------------------ */
+typedef struct { int nr, nz; const uint8_t *mask; } agrid;
+
+static void axi_coef(int i, int nr, double *ci, double *co, double *cz)
+{
+    *ci = (double)i;
+    *co = (i + 1 < nr) ? (double)(i + 1) : 0.0;
+    *cz = (double)i + 0.5;
+}
+
+/* y = A x on the unmasked unknowns (homogeneous boundary values). */
+static void axi_apply(const agrid *g, const double *x, double *y)
+{
+    for (int k = 0; k < g->nz; ++k)
+        for (int i = 0; i < g->nr; ++i) {
+            long long c = (long long)k * g->nr + i;
+            if (g->mask && g->mask[c]) { y[c] = 0.0; continue; }
+            double ci, co, cz;
+            axi_coef(i, g->nr, &ci, &co, &cz);
+            double diag = ci + co + 2.0 * cz + (k == 0 ? cz : 0.0) + (k == g->nz - 1 ? cz : 0.0);
+            double v = diag * x[c];
+            if (i > 0 && !(g->mask && g->mask[c - 1])) v -= ci * x[c - 1];
+            if (i + 1 < g->nr && !(g->mask && g->mask[c + 1])) v -= co * x[c + 1];
+            if (k > 0 && !(g->mask && g->mask[c - g->nr])) v -= cz * x[c - g->nr];
+            if (k + 1 < g->nz && !(g->mask && g->mask[c + g->nr])) v -= cz * x[c + g->nr];
+            y[c] = v;
+        }
+}
+
+int orc_poisson_axi(int nr, int nz, double h, const double *rho, const uint8_t *mask, double v_mask,
+                    double v_lo, double v_hi, double *phi, double rtol, int max_iter, double *rel_res,
+                    int *iters)
+{
+    agrid g = {nr, nz, mask};
+    long long n = (long long)nr * nz;
+    double *b = calloc((size_t)n, sizeof(double)), *r = calloc((size_t)n, sizeof(double));
+    double *z = calloc((size_t)n, sizeof(double)), *pp = calloc((size_t)n, sizeof(double));
+    double *q = calloc((size_t)n, sizeof(double)), *dg = calloc((size_t)n, sizeof(double));
+    if (!b || !r || !z || !pp || !q || !dg) return -2;
+    double h2e = h * h / EPS_0;
+    for (int k = 0; k < nz; ++k)
+        for (int i = 0; i < nr; ++i) {
+            long long c = (long long)k * nr + i;
+            if (mask && mask[c]) { phi[c] = v_mask; continue; }
+            double ci, co, cz;
+            axi_coef(i, nr, &ci, &co, &cz);
+            dg[c] = ci + co + 2.0 * cz + (k == 0 ? cz : 0.0) + (k == nz - 1 ? cz : 0.0);
+            double bb = cz * h2e * rho[c];
+            if (k == 0) bb += 2.0 * cz * v_lo;
+            if (k == nz - 1) bb += 2.0 * cz * v_hi;
+            if (mask) {
+                if (i > 0 && mask[c - 1]) bb += ci * v_mask;
+                if (i + 1 < nr && mask[c + 1]) bb += co * v_mask;
+                if (k > 0 && mask[c - nr]) bb += cz * v_mask;
+                if (k + 1 < nz && mask[c + nr]) bb += cz * v_mask;
+            }
+            b[c] = bb;
+        }
+    axi_apply(&g, phi, q);
+    double bn = 0.0, rz = 0.0;
+    for (long long c = 0; c < n; ++c) {
+        if (mask && mask[c]) { r[c] = 0.0; z[c] = 0.0; pp[c] = 0.0; continue; }
+        r[c] = b[c] - q[c];
+        z[c] = r[c] / dg[c];
+        pp[c] = z[c];
+        rz += r[c] * z[c];
+        bn += b[c] * b[c];
+    }
+    bn = sqrt(bn);
+    if (bn == 0.0) bn = 1.0;
+    int it = 0;
+    double rn = 0.0;
+    for (; it < max_iter; ++it) {
+        rn = 0.0;
+        for (long long c = 0; c < n; ++c) rn += r[c] * r[c];
+        rn = sqrt(rn);
+        if (rn / bn <= rtol) break;
+        axi_apply(&g, pp, q);
+        double pq = 0.0;
+        for (long long c = 0; c < n; ++c) pq += pp[c] * q[c];
+        double alpha = rz / pq;
+        for (long long c = 0; c < n; ++c) {
+            if (mask && mask[c]) continue;
+            phi[c] += alpha * pp[c];
+            r[c] -= alpha * q[c];
+        }
+        double rz2 = 0.0;
+        for (long long c = 0; c < n; ++c) {
+            if (mask && mask[c]) continue;
+            z[c] = r[c] / dg[c];
+            rz2 += r[c] * z[c];
+        }
+        double beta = rz2 / rz;
+        rz = rz2;
+        for (long long c = 0; c < n; ++c) pp[c] = (mask && mask[c]) ? 0.0 : z[c] + beta * pp[c];
+    }
+    *rel_res = rn / bn;
+    *iters = it;
+    free(b); free(r); free(z); free(pp); free(q); free(dg);
+    return it < max_iter ? 0 : -5;
+}
+
+/* E_r, E_z at cell centres: central differences, mirror at the axis and the
+ * outer cylinder, Dirichlet ghosts at the plates. */
+void orc_grad_axi(int nr, int nz, double h, const double *phi, double v_lo, double v_hi, double *Er, double *Ez)
+{
+    for (int k = 0; k < nz; ++k)
+        for (int i = 0; i < nr; ++i) {
+            long long c = (long long)k * nr + i;
+            double pc = phi[c];
+            double rm = i > 0 ? phi[c - 1] : pc, rp = i + 1 < nr ? phi[c + 1] : pc;
+            double zm = k > 0 ? phi[c - nr] : 2.0 * v_lo - pc, zp = k + 1 < nz ? phi[c + nr] : 2.0 * v_hi - pc;
+            Er[c] = -(rp - rm) / (2.0 * h);
+            Ez[c] = -(zp - zm) / (2.0 * h);
+        }
+}
+
+/* Densities of ring cells: n = q / (2^32 pi (2i + 1) dx^3) (the volume 2 pi r dr dz
+ * of Sec. 2.1.2 at r = (i + 1/2) dx); rho = e (n_pos - n_neg - n_e). */
+void orc_fixed_to_rho_axi(int nr, int nz, double dx, const int64_t *q_e, const int64_t *q_pos,
+                          const int64_t *q_neg, double *rho)
+{
+    for (int k = 0; k < nz; ++k)
+        for (int i = 0; i < nr; ++i) {
+            long long c = (long long)k * nr + i;
+            double inv = 1.0 / (4294967296.0 * (M_PI_ORC * (double)(2 * i + 1) * dx * dx * dx));
+            double ne = (double)q_e[c] * inv, np = (double)q_pos[c] * inv, nn = (double)q_neg[c] * inv;
+            rho[c] = Q_E * (np - nn - ne);
+        }
+}
+
 void orc_grad_phi(int nx, int ny, int nz, double h, const double *phi, double v_lo, double v_hi,
                   double *Ex, double *Ey, double *Ez)
 {

@@ -4,5 +4,6 @@ fixed-point CIC deposit, super-particle merge/split, multigrid Poisson and
 Monte Carlo swarms, behind the C ABI of include/picmcc.h, and a BF16
 surrogate of the swarms' transport data."""
 from . import picmcc  # noqa: F401
-from .picmcc import (PicContext, PicError, mlp_forward, mlp_loss_grad, mlp_train, poisson_solve,  # noqa: F401
+from .picmcc import (PicContext, PicError, mlp_forward, mlp_loss_grad, mlp_train, poisson_axi_solve,  # noqa: F401
+                     poisson_solve,
                      swarm_autotune, swarm_run)

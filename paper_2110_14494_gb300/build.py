@@ -24,6 +24,7 @@ UNITS = {
     "pic.cu": ["--fmad=false"],
     "poisson.cu": [],
     "mlp.cu": [],
+    "poisson_axi.cu": [],
 }
 
 

@@ -17,6 +17,7 @@ constexpr int kMaxProc = PIC_MAX_PROC;
 constexpr int kTableStride = 8;            // processes per table row (7 used + total)
 constexpr int kNMom = PIC_SWARM_NMOM;
 constexpr unsigned kFull = 0xffffffffu;
+constexpr double kPi = 3.14159265358979323846;
 constexpr int kVBinsPerOctave = 6;
 constexpr int kVBins = 20 * kVBinsPerOctave;  // 2^10 .. 2^30 m/s
 
@@ -134,6 +135,7 @@ struct DevState {
 struct Grid {
     int nx, ny, nz;
     double dx, ox, oy, oz;
+    int axi;  // 1: axisymmetric (r, z) grid, nx radial cells from the axis x = y = 0, ny = 1
     __host__ __device__ long long ncell() const { return (long long)nx * ny * nz; }
 };
 

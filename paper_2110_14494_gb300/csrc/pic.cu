@@ -14,6 +14,7 @@
 
 #include "common.cuh"
 #include "poisson.cuh"
+#include "poisson_axi.cuh"
 #include "push.cuh"
 #include "swarm_batch.cuh"
 
@@ -147,9 +148,12 @@ __global__ void k_seed_count(Grid g, const uint8_t* __restrict__ mask, double n0
         const double xc = g.ox + ((double)i + 0.5) * g.dx;
         const double yc = g.oy + ((double)j + 0.5) * g.dx;
         const double zc = g.oz + ((double)k + 0.5) * g.dx;
-        const double r2 = (xc - cx) * (xc - cx) + (yc - cy) * (yc - cy) + (zc - cz) * (zc - cz);
+        // axisymmetric: ring cell at radius xc around the axis, centre on the axis
+        const double r2 = g.axi ? xc * xc + (zc - cz) * (zc - cz)
+                                : (xc - cx) * (xc - cx) + (yc - cy) * (yc - cy) + (zc - cz) * (zc - cz);
+        const double dVc = g.axi ? kPi * (double)(2 * i + 1) * g.dx * g.dx * g.dx : dV;
         // same operation order as the definition: n0 exp(-r2 / R^2) dV / w0
-        const double expct = n0 * exp(-r2 / R2) * dV / w0;
+        const double expct = n0 * exp(-r2 / R2) * dVc / w0;
         const double fl = floor(expct);
         long long m = (long long)fl;
         const u32x4 o = philox(u32x4{(uint32_t)c, 0u, 0u, 0xB0000000u}, K.init0, K.init1);
@@ -171,8 +175,17 @@ __global__ void k_seed_write(Grid g, const uint32_t* __restrict__ cnt, const uin
             const long long s = (long long)off[c] + q;
             if (s >= cap) { atomicOr(&st->err, kErrOutCapacity); return; }
             const u32x4 o = philox(u32x4{(uint32_t)c, q + 1u, 0u, 0xB0000000u}, K.init0, K.init1);
-            p.r[PX][s] = (T)(g.ox + ((double)i + unif<double>(o.x)) * g.dx);
-            p.r[PY][s] = (T)(g.oy + ((double)j + unif<double>(o.y)) * g.dx);
+            if (g.axi) {
+                // uniform in the ring: r^2 uniform in [i^2, (i+1)^2] dx^2, angle uniform
+                const double r = g.dx * sqrt((double)i * i + unif<double>(o.x) * (double)(2 * i + 1));
+                double sn, cs;
+                sincospi(2.0 * unif<double>(o.y), &sn, &cs);
+                p.r[PX][s] = (T)(r * cs);
+                p.r[PY][s] = (T)(r * sn);
+            } else {
+                p.r[PX][s] = (T)(g.ox + ((double)i + unif<double>(o.x)) * g.dx);
+                p.r[PY][s] = (T)(g.oy + ((double)j + unif<double>(o.y)) * g.dx);
+            }
             p.r[PZ][s] = (T)(g.oz + ((double)k + unif<double>(o.z)) * g.dx);
             for (int d = VX; d <= AZ; ++d) p.r[d][s] = (T)0;
             p.r[PW][s] = (T)w0;
@@ -215,9 +228,12 @@ __global__ void k_pack_field(const float* __restrict__ Ex, const float* __restri
 
 // n = q / (2^32 dV); rho = e (n_pos - n_neg - n_e).
 __global__ void k_fixed_to_rho(const long long* __restrict__ qe, const long long* __restrict__ qp,
-                               const long long* __restrict__ qn, long long n, double inv, double* __restrict__ rho) {
+                               const long long* __restrict__ qn, long long n, double inv, double* __restrict__ rho,
+                               int nr) {
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
-        const double ne = (double)qe[c] * inv, np = (double)qp[c] * inv, nn = (double)qn[c] * inv;
+        // axisymmetric (nr > 0): ring volume pi (2i + 1) dx^3, inv = 1 / (2^32 pi dx^3)
+        const double iv = nr > 0 ? inv / (double)(2 * (int)(c % nr) + 1) : inv;
+        const double ne = (double)qe[c] * iv, np = (double)qp[c] * iv, nn = (double)qn[c] * iv;
         rho[c] = kQ * (np - nn - ne);
     }
 }
@@ -261,7 +277,7 @@ __global__ void k_end_step(DevState* st, long long* count_slot, long long cap) {
 // relaxation time and the growth limit).
 template <class T>
 __global__ void k_step_stats(const Soa<T> p, const DevState* stc, const unsigned long long* __restrict__ qe,
-                             long long ncell, DevState* st) {
+                             long long ncell, int nr, DevState* st) {
     __shared__ unsigned int h[kVBins];
     for (int b = threadIdx.x; b < kVBins; b += blockDim.x) h[b] = 0;
     __syncthreads();
@@ -278,7 +294,9 @@ __global__ void k_step_stats(const Soa<T> p, const DevState* stc, const unsigned
     long long mx = LLONG_MIN, sm = 0;
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += stride) {
         const long long q = (long long)qe[c];
-        mx = q > mx ? q : mx;
+        // axisymmetric (nr > 0): the maximum of q / (2i + 1), proportional to the density
+        const long long qd = nr > 0 ? q / (2 * (long long)(c % nr) + 1) : q;
+        mx = qd > mx ? qd : mx;
         sm += q;
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -322,7 +340,7 @@ __device__ __forceinline__ uint32_t cell_index(T x, T y, T z, T ox, T oy, T oz, 
 
 struct GridT {
     double ox, oy, oz, dx;
-    int nx, ny, nz;
+    int nx, ny, nz, axi;
 };
 
 // ---------------------------------------------------------------- cell sort
@@ -331,8 +349,12 @@ __global__ void k_cell_count(const Soa<T> p, const DevState* st, GridT g, uint32
                              uint32_t* __restrict__ key, uint32_t* __restrict__ rank) {
     const long long n = (long long)st->n_in;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const uint32_t c = cell_index<T>(p.r[PX][i], p.r[PY][i], p.r[PZ][i], (T)g.ox, (T)g.oy, (T)g.oz, (T)g.dx, g.nx,
-                                         g.ny, g.nz);
+        T x = p.r[PX][i], y = p.r[PY][i];
+        if (g.axi) {
+            x = sqrt(x * x + y * y);
+            y = (T)g.oy + (T)0.5 * (T)g.dx;
+        }
+        const uint32_t c = cell_index<T>(x, y, p.r[PZ][i], (T)g.ox, (T)g.oy, (T)g.oz, (T)g.dx, g.nx, g.ny, g.nz);
         key[i] = c;
         rank[i] = atomicAdd(&cnt[c], 1u);
     }
@@ -660,7 +682,7 @@ static Layout make_layout(const pic_config* c) {
     L.phi = take(ncell * 8);
     L.phi_prev = take(ncell * 8);
     L.phi_x = take(ncell * 8);
-    L.mg = take(MG::bytes(c->nx, c->ny, c->nz, c->precision == 32, false));
+    L.mg = take(c->geometry == 1 ? AxiMG::bytes(c->nx, c->nz) : MG::bytes(c->nx, c->ny, c->nz, c->precision == 32, false));
     {
         const size_t np = (size_t)photo_cap(c);
         L.photo = o;
@@ -697,6 +719,7 @@ struct pic_ctx {
     double thr[8], mratio[8];
     int grid_push = 0;
     MG mg;
+    AxiMG amg;  // coupled solve of axisymmetric contexts
     std::string err;
     long long n_wu = 0, n_sorts = 0;
     int last_cycles = 0;
@@ -798,7 +821,12 @@ extern "C" const char* pic_last_error(const pic_ctx* ctx) { return ctx ? ctx->er
 static int validate(const pic_config* c) {
     if (!c) return PIC_ERR_ARG;
     if (c->precision != 32 && c->precision != 64) return PIC_ERR_ARG;
-    if (c->nx < 2 || c->ny < 2 || c->nz < 2 || !(c->dx > 0) || c->capacity < 1) return PIC_ERR_ARG;
+    if (c->geometry != 0 && c->geometry != 1) return PIC_ERR_ARG;
+    // axisymmetric: one y cell, the axis at x = y = 0
+    if (c->geometry == 1 && (c->ny != 1 || c->origin[0] != 0.0 || c->origin[1] != 0.0)) return PIC_ERR_ARG;
+    if (c->nx < 2 || (c->geometry == 0 && c->ny < 2) || c->nz < 2 || !(c->dx > 0) || c->capacity < 1)
+        return PIC_ERR_ARG;
+    if (c->weight_interval < 0) return PIC_ERR_ARG;
     if (c->nx > 2046 || c->ny > 2046 || c->nz > 2046) return PIC_ERR_ARG;
     if ((long long)c->nx * c->ny * c->nz > 0x7fffffffLL) return PIC_ERR_ARG;
     if (c->capacity > 0x7fffffffLL) return PIC_ERR_ARG;
@@ -810,7 +838,8 @@ static int validate(const pic_config* c) {
     for (int k = 0; k < g.n_proc; ++k)
         if (g.kind[k] < 0 || g.kind[k] > 3) return PIC_ERR_ARG;
     if (c->coupled && (!(c->poisson_rtol > 0) || c->poisson_max_cycles < 1)) return PIC_ERR_ARG;
-    if (c->coupled && !MG::supported(c->nx, c->ny, c->nz)) return PIC_ERR_ARG;
+    if (c->coupled && c->geometry == 0 && !MG::supported(c->nx, c->ny, c->nz)) return PIC_ERR_ARG;
+    if (c->coupled && c->geometry == 1 && !AxiMG::supported(c->nx, c->nz)) return PIC_ERR_ARG;
     if (c->adaptive_dt && (!(c->cfl > 0) || c->mobility < 0 || !(c->max_growth > 1.0))) return PIC_ERR_ARG;
     if (c->photo_xi < 0) return PIC_ERR_ARG;
     if (c->photo_xi > 0) {
@@ -889,7 +918,8 @@ extern "C" int pic_init(const pic_config* cfg, void* d_ws, size_t ws_bytes, cons
     c->s = (cudaStream_t)stream;
     c->ws = (char*)d_ws;
     c->L = L;
-    c->g = Grid{cfg->nx, cfg->ny, cfg->nz, cfg->dx, cfg->origin[0], cfg->origin[1], cfg->origin[2]};
+    c->g = Grid{cfg->nx, cfg->ny, cfg->nz, cfg->dx, cfg->origin[0], cfg->origin[1], cfg->origin[2],
+                cfg->geometry == 1 ? 1 : 0};
     c->K = make_keys(cfg->seed);
     c->mask = d_mask;
     c->dt_cur = c->dt_prev = c->dt_next = cfg->dt;
@@ -911,8 +941,13 @@ extern "C" int pic_init(const pic_config* cfg, void* d_ws, size_t ws_bytes, cons
                                   : PushLaunch<double>::blocks_per_sm(MODE_PIC, c->n_bins);
     c->grid_push = sms * bps;
     if (cfg->coupled) {
-        c->mg.carve(c->ws + L.mg, cfg->nx, cfg->ny, cfg->nz, c->prec == 32, false);
-        c->mg.persistent = true;
+        if (c->g.axi) {
+            c->amg.carve(c->ws + L.mg, cfg->nx, cfg->nz);
+            c->amg.persistent = true;
+        } else {
+            c->mg.carve(c->ws + L.mg, cfg->nx, cfg->ny, cfg->nz, c->prec == 32, false);
+            c->mg.persistent = true;
+        }
     }
     *out = c;
     return PIC_OK;
@@ -957,6 +992,7 @@ template <class T> static PushArgs<T> make_args(pic_ctx* c, int mode) {
     A.q_pos = c->qp();
     A.q_neg = c->qn();
     A.boundary = c->cfg.boundary;
+    A.axi = c->g.axi;
     if (mode == MODE_PIC && c->cfg.photo_xi > 0) {
         const pic_config& f = c->cfg;
         const double a = f.chi_min * f.p_o2, b = f.chi_max * f.p_o2;
@@ -1001,6 +1037,8 @@ template <class T> static void deposit_current(pic_ctx* c, unsigned long long* q
 extern "C" int pic_seed_gaussian(pic_ctx* c, double n0, double radius, const double center[3], double w0,
                                  long long* n_out) {
     if (!c || !center || !(n0 >= 0) || !(radius > 0) || !(w0 > 0)) return PIC_ERR_ARG;
+    if (c->g.axi && (center[0] != 0.0 || center[1] != 0.0))
+        return c->fail(PIC_ERR_ARG, "axisymmetric seed: the centre must be on the axis");
     const long long ncell = c->g.ncell();
     uint32_t* cnt = (uint32_t*)(c->ws + c->L.cnt);
     uint32_t* off = (uint32_t*)(c->ws + c->L.start);
@@ -1132,9 +1170,11 @@ extern "C" int pic_set_field(pic_ctx* c, const float* Ex, const float* Ey, const
 
 static void fixed_to_rho(pic_ctx* c, double* rho) {
     const long long n = c->g.ncell();
-    const double dV = c->g.dx * c->g.dx * c->g.dx;
+    // cell volume dx^3, or pi dx^3 times (2i + 1) for the ring cells of an axisymmetric grid
+    const double dV = c->g.dx * c->g.dx * c->g.dx * (c->g.axi ? kPi : 1.0);
     k_fixed_to_rho<<<grid_n(n), 256, 0, c->s>>>((const long long*)c->qe(), (const long long*)c->qp(),
-                                                 (const long long*)c->qn(), n, 1.0 / (4294967296.0 * dV), rho);
+                                                 (const long long*)c->qn(), n, 1.0 / (4294967296.0 * dV), rho,
+                                                 c->g.axi ? c->g.nx : 0);
 }
 
 // Coupled field: rho from the fixed-point grids, multigrid Poisson (warm
@@ -1168,7 +1208,30 @@ static int solve_field_pair(pic_ctx* c) {
     return PIC_OK;
 }
 
+// Axisymmetric coupled field: rho in the ring cells, the (r, z) solve warm
+// started from the extrapolated potential (float64 in both precisions),
+// packed (E_r, 0, E_z).
+static int solve_field_axi(pic_ctx* c) {
+    fixed_to_rho(c, c->rho());
+    k_extrapolate<<<grid_n(c->g.ncell()), 256, 0, c->s>>>(c->phi(), (double*)(c->ws + c->L.phi_prev), c->g.ncell(),
+                                                           c->n_solves >= 2 ? 1 : 0);
+    c->n_solves++;
+    c->launches += 2;
+    const long long l0 = c->amg.launches;
+    double hn[2];
+    int rc = c->amg.solve(c->rho(), c->mask, c->phi(), c->g.dx, c->cfg.v_lo, c->cfg.v_hi, c->cfg.v_mask,
+                          c->cfg.poisson_rtol, c->cfg.poisson_max_cycles, c->prec, c->ws + c->L.E4, nullptr,
+                          nullptr, c->s, &c->last_cycles, &c->last_rel, hn);
+    if (rc == PIC_ERR_CUDA) return c->fail(rc, "axisymmetric poisson solve: CUDA error");
+    if (rc == PIC_ERR_TIMEOUT) return c->fail(rc, "axisymmetric poisson solve: cycle limit reached");
+    c->launches += c->amg.launches - l0;
+    c->field_valid = 1;
+    c->field_uniform = 0;
+    return PIC_OK;
+}
+
 static int solve_field(pic_ctx* c) {
+    if (c->g.axi) return solve_field_axi(c);
     if (c->prec == 32) return solve_field_pair(c);
     fixed_to_rho(c, c->rho());
     k_extrapolate<<<grid_n(c->g.ncell()), 256, 0, c->s>>>(c->phi(), (double*)(c->ws + c->L.phi_prev), c->g.ncell(),
@@ -1193,7 +1256,7 @@ template <class T> static int sort_by_cell(pic_ctx* c) {
     uint32_t* cnt = (uint32_t*)(c->ws + c->L.cnt);
     uint32_t* start = (uint32_t*)(c->ws + c->L.start);
     cudaMemsetAsync(cnt, 0, (ncell + 1) * 4, c->s);
-    GridT g{c->g.ox, c->g.oy, c->g.oz, c->g.dx, c->g.nx, c->g.ny, c->g.nz};
+    GridT g{c->g.ox, c->g.oy, c->g.oz, c->g.dx, c->g.nx, c->g.ny, c->g.nz, c->g.axi};
     const int grid = grid_n(c->cfg.capacity);
     k_cell_count<T><<<grid, 256, 0, c->s>>>(c->soa<T>(c->cur), c->st(), g, cnt, (uint32_t*)(c->ws + c->L.key),
                                              (uint32_t*)(c->ws + c->L.rank));
@@ -1266,7 +1329,7 @@ static void next_dt(pic_ctx* c, const DevState& h) {
             break;
         }
     }
-    const double ne_max = (double)h.qe_max / (4294967296.0 * dV);
+    const double ne_max = (double)h.qe_max / (4294967296.0 * dV * (c->g.axi ? kPi : 1.0));
     const double w_now = (double)(long long)h.qe_sum / 4294967296.0;
     double dt = c->cfg.dt;
     if (v90 > 0.0) dt = fmin(dt, c->cfg.cfl * c->g.dx / v90);
@@ -1294,7 +1357,8 @@ template <class T> static int extra_generations(pic_ctx* c, PushArgs<T>& A, int 
         if (c->cfg.adaptive_dt && mode == MODE_PIC) {
             DevState* st = c->st();
             cudaMemsetAsync(&st->qe_max, 0, sizeof(long long) + sizeof(unsigned long long) + sizeof(st->vhist), c->s);
-            k_step_stats<T><<<152 * 4, 256, 0, c->s>>>(A.out, st, c->qe(), c->g.ncell(), st);
+            k_step_stats<T><<<152 * 4, 256, 0, c->s>>>(A.out, st, c->qe(), c->g.ncell(), c->g.axi ? c->g.nx : 0,
+                                                       st);
             c->launches += 1;
         }
         DevState h;
@@ -1366,9 +1430,12 @@ extern "C" int pic_step(pic_ctx* c, int n_steps, pic_step_stats* stats) {
         c->accumulate(1, 2, &c->pt.ms_children, &c->pt.n_children);
         bool sorted = false;
         c->mark(3);
-        if (c->cfg.growth_trigger > 0) {
+        if (c->cfg.growth_trigger > 0 || c->cfg.weight_interval > 0) {
             c->n_host = c->n_next;
-            if ((double)c->n_host > c->cfg.growth_trigger * (double)c->n_last_wu && c->n_host > 0) {
+            const bool grown = c->cfg.growth_trigger > 0 &&
+                               (double)c->n_host > c->cfg.growth_trigger * (double)c->n_last_wu;
+            const bool every = c->cfg.weight_interval > 0 && (c->step % (uint32_t)c->cfg.weight_interval) == 0;
+            if ((grown || every) && c->n_host > 0) {
                 rc = pic_weight_update(c);
                 if (rc) return rc;
                 sorted = true;
@@ -1445,7 +1512,7 @@ extern "C" int pic_deposit(pic_ctx* c, int64_t* q_e, int64_t* q_pos, int64_t* q_
 // to their float pairs on the host (hi + lo is exact in float64).
 static cudaError_t save_phi(pic_ctx* c, double* out) {
     const size_t n = (size_t)c->g.ncell();
-    if (c->prec != 32) return cudaMemcpy(out, c->phi(), n * 8, cudaMemcpyDeviceToHost);
+    if (c->prec != 32 || c->g.axi) return cudaMemcpy(out, c->phi(), n * 8, cudaMemcpyDeviceToHost);
     std::vector<float> hl(2 * n);
     cudaError_t e = cudaMemcpy(hl.data(), c->ph_hi(c->ph_cur), 2 * n * 4, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return e;
@@ -1455,7 +1522,7 @@ static cudaError_t save_phi(pic_ctx* c, double* out) {
 
 static cudaError_t load_phi(pic_ctx* c, const double* in) {
     const size_t n = (size_t)c->g.ncell();
-    if (c->prec != 32) return cudaMemcpy(c->phi(), in, n * 8, cudaMemcpyHostToDevice);
+    if (c->prec != 32 || c->g.axi) return cudaMemcpy(c->phi(), in, n * 8, cudaMemcpyHostToDevice);
     std::vector<float> hl(2 * n);
     for (size_t i = 0; i < n; ++i) {
         hl[i] = (float)in[i];

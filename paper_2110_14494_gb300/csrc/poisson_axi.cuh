@@ -1,0 +1,36 @@
+// Axisymmetric Poisson solve on an (r, z) mesh (see poisson_axi.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pic {
+
+struct AxiMG {
+    static constexpr int kMaxLevels = 14;
+    int levels = 0;
+    int lr[kMaxLevels], lz[kMaxLevels];
+    double* e[kMaxLevels];
+    double* g[kMaxLevels];
+    uint8_t* m[kMaxLevels];
+    double *norms = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
+    int pre = 2, post = 2, coarse_sweeps = 64;
+    long long launches = 0;
+    bool persistent = false, masks_ready = false;
+
+    void plan(int nr, int nz);
+    // The coarsest level is solved by one block: at most 4096 cells.
+    static bool supported(int nr, int nz);
+    static size_t bytes(int nr, int nz);
+    size_t carve(void* base, int nr, int nz);
+    cudaError_t build_masks(const uint8_t* mask, cudaStream_t s);
+    void vcycle(cudaStream_t s);
+    // rho: charge density (C/m^3) [nz][nr]; phi: initial guess and solution;
+    // E4 (optional): packed [nz][nr][4] (E_r, 0, E_z, 0) in float (packed_prec
+    // 32) or double (64); Er, Ez: optional float planes.  Returns PIC_OK,
+    // PIC_ERR_TIMEOUT or PIC_ERR_CUDA.
+    int solve(const double* rho, const uint8_t* mask, double* phi, double h, double v_lo, double v_hi,
+              double v_mask, double rtol, int max_cycles, int packed_prec, void* E4, float* Er, float* Ez,
+              cudaStream_t s, int* cycles_out, double* rel_out, double* host_norms);
+};
+
+}  // namespace pic

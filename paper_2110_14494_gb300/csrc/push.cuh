@@ -50,6 +50,7 @@ template <class T> struct PushArgs {
     const uint8_t* mask;
     unsigned long long *q_e, *q_pos, *q_neg;
     int boundary;
+    int axi;                   // axisymmetric grid (see grid_pt)
     // photoionization (Sec. 2.4): emission probability per ionization, the
     // absorption coefficient range [chi_a, chi_a e^chi_log] (1/m), and the
     // queue of photoelectrons appended after the step
@@ -219,9 +220,53 @@ template <> struct Ld4<double> {
     }
 };
 
+// Point of the grid that a particle position maps to.  Cartesian grids: the
+// position itself.  Axisymmetric grids (Sec. 2.1.1: particles move in 3D,
+// the field and densities live on an (r, z) mesh): (r, centre of the single
+// y cell, z) with r = sqrt(x^2 + y^2), so cell indices, deposits and masks of
+// the Cartesian code address the ring cell (i_r, 0, k).
+template <class T> __device__ __forceinline__ void grid_pt(const PushArgs<T>& A, const T x[3], T g[3]) {
+    if (A.axi) {
+        g[0] = sqrt(x[0] * x[0] + x[1] * x[1]);
+        g[1] = A.oy + (T)0.5 * A.dxr;
+        g[2] = x[2];
+    } else {
+        g[0] = x[0]; g[1] = x[1]; g[2] = x[2];
+    }
+}
+
+// Axisymmetric gather: E_r and E_z bilinear in (r, z) at cell centres
+// (packed as (E_r, 0, E_z)), projected on x and y: E = (E_r x / r, E_r y / r,
+// E_z) (Sec. 2.1.1), zero radial part on the axis.
+template <class T>
+__device__ __forceinline__ void gather_axi(const PushArgs<T>& A, const T x[3], T E[3]) {
+    const T r = sqrt(x[0] * x[0] + x[1] * x[1]);
+    int ir[2], iz[2];
+    T fr, fz;
+    axis_w(r, A.ox, A.dxr, A.nx, ir[0], ir[1], fr);
+    axis_w(x[2], A.oz, A.dxr, A.nz, iz[0], iz[1], fz);
+    const T gr[2] = {(T)1 - fr, fr}, gz[2] = {(T)1 - fz, fz};
+    T er = (T)0, ez = (T)0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int dz = c >> 1, dr = c & 1;
+        const long long idx = (long long)iz[dz] * A.nx + ir[dr];
+        T e[3];
+        Ld4<T>::get(A.E4 + 4 * idx, e);
+        const T g = gz[dz] * gr[dr];
+        er += g * e[0];
+        ez += g * e[2];
+    }
+    const T inv = r > (T)0 ? er / r : (T)0;
+    E[0] = inv * x[0];
+    E[1] = inv * x[1];
+    E[2] = ez;
+}
+
 template <class T>
 __device__ __forceinline__ void gather(const PushArgs<T>& A, const T x[3], T E[3]) {
     if (A.E4 == nullptr) { E[0] = A.E0[0]; E[1] = A.E0[1]; E[2] = A.E0[2]; return; }
+    if (A.axi) { gather_axi(A, x, E); return; }
     int ix[2], iy[2], iz[2];
     T fx, fy, fz;
     axis_w(x[0], A.ox, A.dxr, A.nx, ix[0], ix[1], fx);
@@ -281,6 +326,15 @@ __device__ __forceinline__ void deposit(const T x, const T y, const T z, const T
         const int ii = fold_idx(i0 + dxx, nx), jj = fold_idx(j0 + dy, ny), kk = fold_idx(k0 + dz, nz);
         if (qc != 0) atomicAdd(q + (((long long)kk * ny + jj) * nx + ii), (unsigned long long)qc);
     }
+}
+
+// Deposit of weight w at particle position x (through grid_pt).
+template <class T>
+__device__ __forceinline__ void deposit_at(const PushArgs<T>& A, T x0, T x1, T x2, T w, unsigned long long* q) {
+    const T x[3] = {x0, x1, x2};
+    T g[3];
+    grid_pt(A, x, g);
+    deposit(g[0], g[1], g[2], w, A.ox, A.oy, A.oz, A.dxr, A.nx, A.ny, A.nz, q, A.st);
 }
 
 // ------------------------------------------------------------------ rates
@@ -363,7 +417,9 @@ enum { EV_CONTINUE = 0, EV_DONE = 1, EV_ATTACHED = 2, EV_IONIZED = 3 };
 
 // Electrode mask of the cell containing x (cell index by correctly rounded
 // (x - origin) / dx, folded into the grid).
-template <class T> __device__ __forceinline__ bool masked_at(const PushArgs<T>& A, const T x[3]) {
+template <class T> __device__ __forceinline__ bool masked_at(const PushArgs<T>& A, const T xp[3]) {
+    T x[3];
+    grid_pt(A, xp, x);
     const int i = fold_idx((int)floor(div_rn(sub_rn(x[0], A.ox), A.dxr)), A.nx);
     const int j = fold_idx((int)floor(div_rn(sub_rn(x[1], A.oy), A.dxr)), A.ny);
     const int k = fold_idx((int)floor(div_rn(sub_rn(x[2], A.oz), A.dxr)), A.nz);
@@ -429,8 +485,7 @@ __device__ __forceinline__ int event(const PushArgs<T>& A, const Keys& K, uint32
         ls.w_att += (double)L.w;
         ++ls.attached;
         if (MODE == MODE_PIC && A.q_neg)
-            deposit(L.x[0] + L.d[0], L.x[1] + L.d[1], L.x[2] + L.d[2], L.w, A.ox, A.oy, A.oz, A.dxr, A.nx, A.ny,
-                    A.nz, A.q_neg, A.st);
+            deposit_at(A, L.x[0] + L.d[0], L.x[1] + L.d[1], L.x[2] + L.d[2], L.w, A.q_neg);
         return EV_ATTACHED;
     }
     T n[3];
@@ -467,8 +522,29 @@ template <class T>
 __device__ __forceinline__ bool boundaries(const PushArgs<T>& A, T x[3], T v[3], T w, LStats& ls) {
     const T lo[3] = {A.ox, A.oy, A.oz}, hi[3] = {A.hx, A.hy, A.hz};
     bool out = false;
+    if (A.axi) {
+        // the cylinder r = R of an axisymmetric grid: outflow, or specular
+        // reflection (r -> 2R - r, radial velocity reversed)
+        const T R = A.hx;
+        T r = sqrt(x[0] * x[0] + x[1] * x[1]);
+        if (A.boundary == 1) {
+            if (r > R) out = true;
+        } else {
+            for (int it = 0; it < 8 && r > R; ++it) {
+                const T rn = (T)2 * R - r, s = rn / r;
+                const T ux = x[0] / r, uy = x[1] / r;
+                const T vr = v[0] * ux + v[1] * uy;
+                x[0] *= s;
+                x[1] *= s;
+                v[0] -= (T)2 * vr * ux;
+                v[1] -= (T)2 * vr * uy;
+                r = fabs(rn);
+            }
+        }
+    }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
+        if (A.axi && d < 2) continue;
         if (A.boundary == 1) {
             if (x[d] < lo[d] || x[d] > hi[d]) out = true;
             continue;
@@ -536,12 +612,13 @@ __global__ void __launch_bounds__(256) k_photo_resolve(const PushArgs<T> A) {
         T n3[3];
         iso_dir(unif<T>(r.w), unif<T>(r2.x), n3);
         const T xp[3] = {A.pe_x[i] + dist * n3[0], A.pe_y[i] + dist * n3[1], A.pe_z[i] + dist * n3[2]};
-        const T lo[3] = {A.ox, A.oy, A.oz}, hi[3] = {A.hx, A.hy, A.hz};
+            const T lo[3] = {A.ox, A.oy, A.oz}, hi[3] = {A.hx, A.hy, A.hz};
         bool in = true;
-        for (int d = 0; d < 3; ++d)
+        for (int d = A.axi ? 2 : 0; d < 3; ++d)
             if (!(xp[d] >= lo[d] && xp[d] <= hi[d])) in = false;
+        if (A.axi && !(sqrt(xp[0] * xp[0] + xp[1] * xp[1]) <= A.hx)) in = false;
         if (!in || (A.mask && masked_at(A, xp))) continue;
-        if (A.q_pos) deposit(xp[0], xp[1], xp[2], w, A.ox, A.oy, A.oz, A.dxr, A.nx, A.ny, A.nz, A.q_pos, A.st);
+        if (A.q_pos) deposit_at(A, xp[0], xp[1], xp[2], w, A.q_pos);
         const unsigned long long slot = atomicAdd(&A.st->n_photo, 1ull);
         if ((long long)slot >= A.cap_photo) {
             atomicOr(&A.st->err, kErrPhotoCapacity);
@@ -577,7 +654,7 @@ __global__ void __launch_bounds__(256) k_photo_append(const PushArgs<T> A) {
             continue;
         }
         store(A.out, slot, x, v, a, w, A.ph_id[i]);
-        if (A.q_e) deposit(x[0], x[1], x[2], w, A.ox, A.oy, A.oz, A.dxr, A.nx, A.ny, A.nz, A.q_e, A.st);
+        if (A.q_e) deposit_at(A, x[0], x[1], x[2], w, A.q_e);
     }
 }
 
@@ -688,7 +765,7 @@ __device__ __forceinline__ void flush_out(const PushArgs<T>& A, Stage<T>* sg, in
             if ((long long)slot < A.cap_out) {
                 store(A.out, slot, x, v, a, w, id);
                 if (MODE == MODE_PIC) {
-                    if (A.q_e) deposit(x[0], x[1], x[2], w, A.ox, A.oy, A.oz, A.dxr, A.nx, A.ny, A.nz, A.q_e, A.st);
+                    if (A.q_e) deposit_at(A, x[0], x[1], x[2], w, A.q_e);
                 } else {
                     M.add(x, v, w);
                 }
@@ -822,7 +899,7 @@ __device__ __forceinline__ void collide_loop(const PushArgs<T>& A, const ProcSme
                         T vc[3];
                         const uint64_t cid = make_child(A.K, A.step, q.id[it], src.k[it], q.r[VX][it], vc);
                         if (MODE == MODE_PIC && A.q_pos)
-                            deposit(x0, x1, x2, w, A.ox, A.oy, A.oz, A.dxr, A.nx, A.ny, A.nz, A.q_pos, A.st);
+                            deposit_at(A, x0, x1, x2, w, A.q_pos);
                         r[0] = x0; r[1] = x1; r[2] = x2;
                         r[3] = vc[0]; r[4] = vc[1]; r[5] = vc[2];
                         r[6] = q.r[AX][it]; r[7] = q.r[AY][it]; r[8] = q.r[AZ][it];
@@ -859,7 +936,7 @@ __device__ __forceinline__ void collide_loop(const PushArgs<T>& A, const ProcSme
                     T vc[3];
                     const uint64_t cid = make_child(A.K, A.step, L.id, L.k - 1, sp, vc);
                     if (MODE == MODE_PIC && A.q_pos)
-                        deposit(xc[0], xc[1], xc[2], L.w, A.ox, A.oy, A.oz, A.dxr, A.nx, A.ny, A.nz, A.q_pos, A.st);
+                        deposit_at(A, xc[0], xc[1], xc[2], L.w, A.q_pos);
                     const int t = stk.n++;
                     for (int d = 0; d < 3; ++d) { stk.x[t][d] = xc[d]; stk.v[t][d] = vc[d]; }
                     stk.w[t] = L.w;
@@ -963,12 +1040,15 @@ __global__ void __launch_bounds__(kCollideThreads) k_children(const PushArgs<T> 
 // Deposit of the current particle set (no push).
 template <class T>
 __global__ void __launch_bounds__(256) k_deposit(const Soa<T> p, const DevState* st, T ox, T oy, T oz, T dx, int nx,
-                                                 int ny, int nz, unsigned long long* q, DevState* stw) {
+                                                 int ny, int nz, int axi, unsigned long long* q, DevState* stw) {
     const unsigned long long n = st->n_in;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (long long)n; i += stride) {
         const T w = p.r[PW][i];
-        if (w > (T)0) deposit(p.r[PX][i], p.r[PY][i], p.r[PZ][i], w, ox, oy, oz, dx, nx, ny, nz, q, stw);
+        if (!(w > (T)0)) continue;
+        const T x = p.r[PX][i], y = p.r[PY][i];
+        if (axi) deposit(sqrt(x * x + y * y), oy + (T)0.5 * dx, p.r[PZ][i], w, ox, oy, oz, dx, nx, ny, nz, q, stw);
+        else deposit(x, y, p.r[PZ][i], w, ox, oy, oz, dx, nx, ny, nz, q, stw);
     }
 }
 

@@ -62,7 +62,7 @@ cudaError_t PushLaunch<T>::children(const PushArgs<T>& A, int mode, bool stats, 
 template <class T>
 cudaError_t PushLaunch<T>::deposit(const Soa<T>& p, DevState* st, const Grid& g, unsigned long long* q, int grid,
                                    cudaStream_t s) {
-    k_deposit<T><<<grid, 256, 0, s>>>(p, st, (T)g.ox, (T)g.oy, (T)g.oz, (T)g.dx, g.nx, g.ny, g.nz, q, st);
+    k_deposit<T><<<grid, 256, 0, s>>>(p, st, (T)g.ox, (T)g.oy, (T)g.oz, (T)g.dx, g.nx, g.ny, g.nz, g.axi, q, st);
     return cudaGetLastError();
 }
 

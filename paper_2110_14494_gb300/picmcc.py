@@ -44,7 +44,8 @@ class pic_config(C.Structure):
                 ("v_mask", C.c_double), ("poisson_rtol", C.c_double), ("poisson_max_cycles", C.c_int),
                 ("adaptive_dt", C.c_int), ("cfl", C.c_double), ("mobility", C.c_double),
                 ("max_growth", C.c_double), ("photo_xi", C.c_double), ("photo_pq", C.c_double),
-                ("pressure", C.c_double), ("p_o2", C.c_double), ("chi_min", C.c_double), ("chi_max", C.c_double)]
+                ("pressure", C.c_double), ("p_o2", C.c_double), ("chi_min", C.c_double), ("chi_max", C.c_double),
+                ("geometry", C.c_int), ("weight_interval", C.c_int)]
 
 
 # Zheleznyak's absorption coefficients, 0.035 and 2 per (mm Torr), in 1/(m Pa)
@@ -105,7 +106,7 @@ EXPORTS = ("pic_workspace_bytes", "pic_init", "pic_destroy", "pic_last_error", "
            "pic_profile", "pic_upload", "pic_download",
            "poisson_workspace_bytes", "poisson_solve", "poisson_solve_noalloc", "swarm_workspace_bytes",
            "swarm_run", "swarm_autotune", "mlp_workspace_bytes", "mlp_forward", "mlp_forward_variant", "mlp_loss_grad",
-           "mlp_train")
+           "mlp_train", "poisson_axi_workspace_bytes", "poisson_axi_solve")
 
 _lib = None
 
@@ -153,6 +154,10 @@ def lib():
     L.swarm_run.argtypes = [P(swarm_config), C.c_int, PD, VP, C.c_size_t, P(swarm_result), PD,
                             P(C.c_longlong), VP]
     L.swarm_autotune.argtypes = [P(swarm_config), C.c_int, PD, VP, C.c_size_t, P(C.c_int), P(C.c_int), PD, VP]
+    L.poisson_axi_workspace_bytes.argtypes = [C.c_int, C.c_int]
+    L.poisson_axi_workspace_bytes.restype = C.c_size_t
+    L.poisson_axi_solve.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, VP, VP, VP, VP,
+                                    VP, C.c_double, C.c_int, VP, C.c_size_t, P(poisson_stats), VP]
     L.mlp_workspace_bytes.argtypes = [C.c_int]
     L.mlp_workspace_bytes.restype = C.c_size_t
     L.mlp_forward.argtypes = [VP, VP, VP, C.c_longlong, VP, C.c_size_t, VP]
@@ -221,7 +226,8 @@ class PicContext:
                  n_ppc=75, w_min=1.0, growth_trigger=0.0, particle_cap=0, boundary=0, sort_interval=0,
                  coupled=False, v_lo=0.0, v_hi=0.0, v_mask=0.0, poisson_rtol=1e-6, poisson_max_cycles=100,
                  adaptive_dt=False, cfl=0.5, mobility=0.06, max_growth=1.2, photo_xi=0.0, photo_pq=4000.0,
-                 pressure=None, p_o2=None, chi_min=ZHELEZNYAK_CHI_MIN, chi_max=ZHELEZNYAK_CHI_MAX, stream=None):
+                 pressure=None, p_o2=None, chi_min=ZHELEZNYAK_CHI_MIN, chi_max=ZHELEZNYAK_CHI_MAX, geometry=0,
+                 weight_interval=0, stream=None):
         import torch
         self.gas = Gas(gas)
         c = pic_config()
@@ -239,6 +245,7 @@ class PicContext:
         c.photo_xi, c.photo_pq, c.pressure = photo_xi, photo_pq, p
         c.p_o2 = p_o2 if p_o2 is not None else 0.2 * p
         c.chi_min, c.chi_max = chi_min, chi_max
+        c.geometry, c.weight_interval = geometry, weight_interval
         self.cfg = c
         self.grid = grid
         self.ncell = grid["nx"] * grid["ny"] * grid["nz"]
@@ -355,6 +362,21 @@ def poisson_solve(grid: dict, rho, phi, mask=None, E=None, v_lo=0.0, v_hi=0.0, v
     rc = lib().poisson_solve(C.byref(pc), _ptr(rho), _ptr(mask), _ptr(phi), _ptr(Ex), _ptr(Ey), _ptr(Ez), rtol,
                              max_cycles, C.c_void_p(ptr), nb, C.byref(st), _stream(stream))
     _check(rc, None, "poisson_solve")
+    return st.cycles, st.rel_res
+
+
+def poisson_axi_solve(nr: int, nz: int, dx: float, rho, phi, mask=None, E=None, v_lo=0.0, v_hi=0.0, v_mask=0.0,
+                      rtol=1e-6, max_cycles=100, stream=None):
+    """Axisymmetric solve; rho, phi: float64 CUDA tensors [nz][nr]; E: optional (Er, Ez) float32 tensors."""
+    nb = lib().poisson_axi_workspace_bytes(nr, nz)
+    if nb == 0:
+        raise PicError(PIC_ERR_ARG, "poisson_axi_solve: unsupported grid")
+    ws, ptr = _workspace(nb)
+    st = poisson_stats()
+    Er, Ez = E if E is not None else (None, None)
+    rc = lib().poisson_axi_solve(nr, nz, dx, v_lo, v_hi, v_mask, _ptr(rho), _ptr(mask), _ptr(phi), _ptr(Er),
+                                 _ptr(Ez), rtol, max_cycles, C.c_void_p(ptr), nb, C.byref(st), _stream(stream))
+    _check(rc, None, "poisson_axi_solve")
     return st.cycles, st.rel_res
 
 

@@ -1,0 +1,166 @@
+"""GPU axisymmetric mode (the paper's axisymmetric geometry, Sec. 2.1.1-2.1.2,
+2.5) against the FP64 CPU oracle: the (r, z) Poisson solve, particle steps
+with the projected field, ring-cell deposits and densities, seeding and a
+coupled run with weight updates every ten steps.  Tolerances as for the 3D
+path: 1e-12 per particle in float64, 1e-5 in float32 with decision flips
+counted; the solve to 1e-6 of the oracle's solution."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from tests.gpu_common import compare_sets
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+special = pytest.importorskip("scipy.special")
+
+SEED = 2110144960
+G = W.axi_grid(24, 40, 2e-5)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2110_14494_gb300 import build
+    build.build()
+
+
+def _ctx(prec, **kw):
+    from paper_2110_14494_gb300 import PicContext
+    return PicContext(W.synthetic_air(), G, precision=prec, geometry=1, **kw)
+
+
+def test_poisson_axi_matches_oracle():
+    from paper_2110_14494_gb300 import poisson_axi_solve
+    nr, nz, h, V = 32, 64, 5e-5, 2000.0
+    g = W.axi_grid(nr, nz, h)
+    mask = W.needle_mask_axi(g, 1.0e-3, 0.3e-3)[:, 0, :]
+    r = np.random.default_rng(3)
+    rho = 1e-2 * (np.exp(-((np.arange(nz)[:, None] - 20) ** 2 + np.arange(nr)[None, :] ** 2) / 40.0)
+                  + 0.1 * r.normal(size=(nz, nr)))
+    ref, rr, it = O.poisson_axi(nr, nz, h, rho, mask, V, 0.0, V)
+    rt, mt = torch.as_tensor(rho).cuda(), torch.as_tensor(mask).cuda()
+    phi = torch.zeros_like(rt)
+    E = tuple(torch.zeros((nz, nr), dtype=torch.float32, device="cuda") for _ in range(2))
+    cyc, rel = poisson_axi_solve(nr, nz, h, rt, phi, mask=mt, E=E, v_lo=0.0, v_hi=V, v_mask=V, rtol=1e-10,
+                                 max_cycles=100)
+    assert rel <= 1e-10 and cyc < 40, (cyc, rel)
+    p = phi.cpu().numpy()
+    assert np.linalg.norm(p - ref) / np.linalg.norm(ref) < 1e-6
+    Er, Ez = O.grad_axi(nr, nz, h, ref, 0.0, V)
+    for a, b in zip(E, (Er, Ez)):
+        assert np.abs(a.cpu().numpy() - b).max() <= 1e-5 * np.abs(b).max() + 1e-3
+
+
+def test_poisson_axi_bessel_solution():
+    from paper_2110_14494_gb300 import poisson_axi_solve
+    R, L, nr = 1e-3, 2e-3, 64
+    nz, h = 2 * nr, R / nr
+    j1 = special.jn_zeros(1, 1)[0]
+    lam = (j1 / R) ** 2 + (np.pi / L) ** 2
+    rc, zc = (np.arange(nr) + 0.5) * h, (np.arange(nz) + 0.5) * h
+    ex = special.j0(j1 * rc / R)[None, :] * np.sin(np.pi * zc / L)[:, None]
+    rho = torch.as_tensor(O.EPS_0 * lam * ex).cuda()
+    phi = torch.zeros_like(rho)
+    poisson_axi_solve(nr, nz, h, rho, phi, rtol=1e-10, max_cycles=100)
+    assert np.abs(phi.cpu().numpy() - ex).max() < 5e-4
+
+
+def _setup(n, prec, off, vmax=3e6):
+    F = W.smooth_field_axi(G, 300 + off, e0=3e6)
+    mk = W.needle_mask_axi(G, 0.3e-3, 0.08e-3)
+    p0 = W.random_particles_axi(n, G, 400 + off, vmax=vmax, w_range=(1.0, 500.0))
+    return F, mk, p0
+
+
+@pytest.mark.parametrize("steps,boundary", [(1, 0), (5, 0), (5, 1)])
+def test_axi_step_fp64_matches_oracle(steps, boundary):
+    F, mk, p0 = _setup(6000, 64, 1)
+    dt = 2e-12
+    ctx = _ctx(64, capacity=60000, seed=SEED, dt=dt, mask=mk, boundary=boundary)
+    ctx.set_field(*(torch.as_tensor(f).cuda() for f in F))
+    ctx.set_particles(p0)
+    st = ctx.step(steps, stats=True)
+    n = G["nx"] * G["nz"]
+    qe, qp, qn = (torch.zeros(n, dtype=torch.int64, device="cuda") for _ in range(3))
+    rho = torch.zeros(n, dtype=torch.float64, device="cuda")
+    ctx.deposit(q_e=qe, q_pos=qp, q_neg=qn, rho=rho)
+    gpu = ctx.get_particles()
+    m = O.Model(W.synthetic_air(), dt, SEED, 64, G, F, mask=mk, boundary=boundary, axi=True)
+    P = O.Particles(60000, p0)
+    rq_pos, rq_neg = np.zeros(n, np.int64), np.zeros(n, np.int64)
+    for s in range(1, steps + 1):
+        rq_e = np.zeros(n, np.int64)
+        rc, ost = O.step(m, P, s, s == 1, rq_e, rq_pos, rq_neg)
+        assert rc == 0
+    ref = P.view()
+    nc, og, orf, bad, worst = compare_sets(gpu, ref, G["dx"], 1e-12, v_floor=1.0)
+    assert og == 0 and orf == 0 and bad == 0, (og, orf, bad, worst)
+    assert st.n_children > 0 and st.n_absorbed >= 0
+    for a, b in ((qe, rq_e), (qp, rq_pos), (qn, rq_neg)):
+        assert np.abs(a.cpu().numpy() - b).max() <= 64
+    rref = O.fixed_to_rho_axi(G["nx"], G["nz"], G["dx"], qe.cpu().numpy(), qp.cpu().numpy(), qn.cpu().numpy())
+    assert np.allclose(rho.cpu().numpy(), rref, rtol=1e-12, atol=0)
+
+
+def test_axi_step_fp32_matches_oracle():
+    F, mk, p0 = _setup(60000, 32, 2)
+    dt = 2e-12
+    ctx = _ctx(32, capacity=300000, seed=SEED, dt=dt, mask=mk)
+    ctx.set_field(*(torch.as_tensor(f).cuda() for f in F))
+    ctx.set_particles(p0)
+    ctx.step(1)
+    gpu = ctx.get_particles()
+    m = O.Model(W.synthetic_air(), dt, SEED, 32, G, F, mask=mk, axi=True)
+    P = O.Particles(300000, p0)
+    rc, ost = O.step(m, P, 1, True)
+    assert rc == 0
+    ref = P.view()
+    nc, og, orf, bad, worst = compare_sets(gpu, ref, G["dx"], 1e-5, v_floor=1e5)
+    assert worst["gross"] + og + orf <= 1e-5 * len(ref["id"]) + 2, (og, orf, worst)
+    assert bad <= 1e-3 * len(ref["id"]), (bad, worst)
+
+
+def test_axi_seed_matches_oracle():
+    mk = W.needle_mask_axi(G, 0.3e-3, 0.08e-3)
+    ctx = _ctx(64, capacity=400000, seed=SEED, dt=2e-12, mask=mk)
+    L = G["nz"] * G["dx"]
+    c = (0.0, 0.0, L - 0.3e-3)
+    n = ctx.seed_gaussian(1e20, 1e-4, c, 2000.0)
+    gpu = ctx.get_particles()
+    m = O.Model(W.synthetic_air(), 2e-12, SEED, 64, G, mask=mk, axi=True)
+    ref = O.seed_gaussian(m, 1e20, 1e-4, c, 2000.0, 400000).view()
+    assert n == len(ref["id"]) and n > 1000
+    nc, og, orf, bad, worst = compare_sets(gpu, ref, G["dx"], 1e-12, v_floor=1.0)
+    assert og == 0 and orf == 0 and bad == 0, worst
+    r = np.hypot(gpu["x"], gpu["y"])
+    assert r.max() <= G["nx"] * G["dx"]
+
+
+def test_axi_coupled_run_with_periodic_weight_updates():
+    """Coupled axisymmetric run: solve, push, deposit and weight updates every
+    ten steps; the solve meets its tolerance and the weights stay sane."""
+    g = W.axi_grid(64, 128, 2e-5)
+    L, V = 128 * 2e-5, 20e5 * 128 * 2e-5
+    mk = W.needle_mask_axi(g, 0.5e-3, 0.1e-3)
+    from paper_2110_14494_gb300 import PicContext
+    ctx = PicContext(W.synthetic_air(), g, precision=32, geometry=1, capacity=4_000_000, seed=SEED, dt=2e-12,
+                     mask=mk, n_ppc=75, w_min=1.0, growth_trigger=1.25, weight_interval=10,
+                     particle_cap=1_000_000, coupled=True, v_lo=0.0, v_hi=V, v_mask=V, poisson_rtol=1e-6,
+                     boundary=1, adaptive_dt=True)
+    n0 = ctx.seed_gaussian(1e19, 1e-4, (0.0, 0.0, L - 0.5e-3), 100.0)
+    assert n0 > 1000
+    wu = 0
+    for _ in range(30):
+        st = ctx.step(1, stats=True)
+        assert st.poisson_rel_res <= 1e-6
+        wu += st.n_weight_updates
+    assert wu >= 3
+    p = ctx.get_particles()
+    assert np.all(p["w"] > 0) and np.isfinite(p["x"]).all()
+    # merging toward 75 per ring cell keeps the weight (only collisions and
+    # absorption change it) and bounds the count by the occupied cells
+    assert 0.2 * 100.0 * n0 < p["w"].sum() < 50 * 100.0 * n0
+    assert len(p["w"]) <= 3 * 75 * g["nx"] * g["nz"]

@@ -301,3 +301,55 @@ def mlp_query_points(n: int, offset: int, en_lo: float = 10.0, en_hi: float = 10
     en = 10.0 ** (np.log10(en_lo) + u[:, 0] * (np.log10(en_hi) - np.log10(en_lo)))
     f = f_lo + u[:, 1] * (f_hi - f_lo)
     return np.stack([en, f], axis=1)
+
+
+# ---------------------------------------------------------------- axisymmetric
+def axi_grid(nr: int, nz: int, dx: float) -> dict:
+    """(r, z) mesh as a grid with one y cell and the axis at x = y = 0."""
+    return grid_spec(nr, 1, nz, dx)
+
+
+def needle_mask_axi(g: dict, length: float, radius: float) -> np.ndarray:
+    """uint8 [nz][1][nr] mask of the ring cells whose centre (r_i, z_k) lies in a
+    rod electrode on the axis hanging from the top plate, with a hemispherical
+    cap whose lowest point is at z = L - length."""
+    nr, nz, dx = g["nx"], g["nz"], g["dx"]
+    oz = g["origin"][2]
+    rc = (np.arange(nr) + 0.5) * dx
+    zc = oz + (np.arange(nz) + 0.5) * dx
+    zcap = oz + nz * dx - length + radius
+    Z, R = np.meshgrid(zc, rc, indexing="ij")
+    rod = (R <= radius) & (Z >= zcap)
+    cap = (R ** 2 + (Z - zcap) ** 2) <= radius ** 2
+    return np.ascontiguousarray((rod | cap).astype(np.uint8)[:, None, :])
+
+
+def random_particles_axi(n: int, g: dict, offset: int, vmax: float = 3e6, w_range=(1.0, 100.0),
+                         id_base: int = 0) -> dict:
+    """Particles uniform in the cylinder r < nr dx, z in the grid (3D positions),
+    isotropic Gaussian velocities of scale vmax/3, float32-representable."""
+    r = rng(offset)
+    R, L, oz = g["nx"] * g["dx"], g["nz"] * g["dx"], g["origin"][2]
+    rad = R * np.sqrt(r.random(n)) * 0.999
+    th = r.random(n) * 2 * np.pi
+    f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    p = dict(x=f32(rad * np.cos(th)), y=f32(rad * np.sin(th)), z=f32(oz + L * (0.001 + 0.998 * r.random(n))))
+    for k in ("vx", "vy", "vz"):
+        p[k] = f32(r.normal(0, vmax / 3, n))
+    for k in ("ax", "ay", "az"):
+        p[k] = np.zeros(n)
+    p["w"] = f32(r.uniform(*w_range, n))
+    p["id"] = np.arange(id_base, id_base + n, dtype=np.uint64)
+    return p
+
+
+def smooth_field_axi(g: dict, offset: int, e0: float = 2e6) -> tuple:
+    """A smooth random axisymmetric field on the (r, z) mesh as float32 planes
+    [nz][1][nr]: (E_r, 0, E_z), with E_r vanishing on the axis."""
+    r = rng(offset)
+    nr, nz = g["nx"], g["nz"]
+    z, x = np.meshgrid((np.arange(nz) + 0.5) / nz, (np.arange(nr) + 0.5) / nr, indexing="ij")
+    er = e0 * x * (r.normal() + 0.5 * np.sin(2 * np.pi * (z + r.random())))
+    ez = e0 * (r.normal() + 0.5 * np.cos(np.pi * x) * np.sin(2 * np.pi * z + r.random()))
+    return (np.ascontiguousarray(er[:, None, :].astype(np.float32)), np.zeros((nz, 1, nr), np.float32),
+            np.ascontiguousarray(ez[:, None, :].astype(np.float32)))
