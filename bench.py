@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--trace", action="store_true", help="per-step statistics (diagnostics, slower kernels)")
     ap.add_argument("--boundary", type=int, default=1, help="0: reflect at the domain faces, 1: absorb (outflow)")
     ap.add_argument("--fixed-dt", action="store_true", help="keep dt = 2 ps (no time-step control)")
-    ap.add_argument("--workload", default="streamer", choices=["streamer", "streamer-full", "swarms", "mlp"],
+    ap.add_argument("--workload", default="streamer",
+                    choices=["streamer", "streamer-full", "streamer-axi", "swarms", "mlp"],
                     help="streamer: the coupled 128^3 step (headline); swarms: 256 batched swarms")
     ap.add_argument("--swarm-block", type=int, default=0, help="batched swarms: block size (0 = autotune)")
     ap.add_argument("--swarm-bps", type=int, default=0, help="batched swarms: blocks per SM (0 = autotune)")
@@ -373,7 +374,11 @@ def main():
     from paper_2110_14494_gb300 import PicContext
 
     full = args.workload == "streamer-full"
-    if full:
+    axi = args.workload == "streamer-axi"
+    if axi:
+        wl = W.streamer_axi()
+        args.no_e2e = True
+    elif full:
         # a bounded sample of the 15 ns run (about 7500 steps): --steps sets it
         wl = W.streamer_full()
         if args.steps == 1990:
@@ -384,13 +389,15 @@ def main():
         wl = workload(args.grid, args.n_initial)
     g = wl["grid"]
     gas = W.synthetic_air()
-    mask = W.needle_mask(g, wl["needle_length"], wl["needle_radius"])
-    if full or args.grid == 128:
+    mask = (W.needle_mask_axi if axi else W.needle_mask)(g, wl["needle_length"], wl["needle_radius"])
+    if full or axi or args.grid == 128:
         cap = args.cap or int(wl["particle_cap"] * 1.6)
     else:
         cap = args.cap or int(max(8 * args.n_initial, 1 << 20))
-    photo = dict(photo_xi=wl["photo_xi"], photo_pq=wl["photo_pq"]) if full else {}
-    w0 = wl["seed_n0"] * np.pi ** 1.5 * wl["seed_radius"] ** 3 / wl["n_initial"]
+    photo = dict(photo_xi=wl["photo_xi"], photo_pq=wl["photo_pq"]) if (full or axi) else {}
+    if axi:
+        photo.update(geometry=1, weight_interval=wl["weight_interval"])
+    w0 = wl["w0"] if axi else wl["seed_n0"] * np.pi ** 1.5 * wl["seed_radius"] ** 3 / wl["n_initial"]
     ctx = PicContext(gas, g, precision=args.precision, capacity=cap, seed=2110144940 + rank, dt=wl["dt"],
                      mask=mask, n_ppc=wl["n_ppc"], w_min=wl["w_min"], growth_trigger=wl["growth_trigger"],
                      particle_cap=wl["particle_cap"], sort_interval=20, coupled=True, v_lo=wl["v_bottom"],
@@ -499,7 +506,8 @@ def main():
             "data": "synthetic",
             "config": {"workload": ("streamer-256x256x512-fp32-photoionization (first %d steps of the 15 ns run)"
                                     % args.steps) if full else
-                       (WORKLOAD if args.grid == 128 else f"streamer-{args.grid}^3"),
+                       ("streamer-axisymmetric-512x512-fp32-photoionization" if axi else
+                        (WORKLOAD if args.grid == 128 else f"streamer-{args.grid}^3")),
                        "grid": [g["nx"], g["ny"], g["nz"]], "dx_um": round(g["dx"] * 1e6, 3), "n_initial": n0,
                        "particle_cap": wl["particle_cap"],
                        "dt": "fixed 2 ps" if args.fixed_dt else "adaptive <= 2 ps (CFL 0.5 on the 90% speed, "
@@ -507,7 +515,7 @@ def main():
                        "simulated_ns": round(fin.t_total * 1e9, 4), "last_dt_ps": round(fin.dt_last * 1e12, 4),
                        "ne_max": fin.ne_max, "boundary": "absorbing faces" if args.boundary == 1 else "reflecting",
                        "poisson": "multigrid-preconditioned CG, rtol 1e-6, every step",
-                       "photoionization": "xi 0.075, p_q 40 mbar, Zheleznyak absorption" if full else "off",
+                       "photoionization": "xi 0.075, p_q 40 mbar, Zheleznyak absorption" if (full or axi) else "off",
                        "l2": "flushed between timed steps (256 MB write outside the timed events)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "particles_trace": n_trace},

@@ -176,6 +176,23 @@ def streamer_full() -> dict:
                 photo_xi=0.075, photo_pq=4000.0, t_end=15e-9)
 
 
+def streamer_axi() -> dict:
+    """Axisymmetric streamer in the paper's cylindrical domain (Sec. 2.3): 10 mm
+    radius x 10 mm gap on 512 x 512 (r, z) cells of 19.53 um, a 2 mm rod of
+    0.2 mm radius on the axis hanging from the top plate (tip near z = 7.8 mm),
+    15.6 kV, the paper's seed (Eq. 7 read with a negative exponent: peak
+    1e16 m^-3, 0.1 mm radius at the tip, weight-one particles), photoionization
+    on, weight updates every 10 steps, dt <= 2 ps."""
+    dx = 10e-3 / 512
+    g = axi_grid(512, 512, dx)
+    L = 512 * dx
+    needle_len, needle_r = 2e-3, 0.2e-3
+    return dict(grid=g, L=L, v_bottom=0.0, v_top=15.6e3, needle_length=needle_len, needle_radius=needle_r,
+                seed_n0=1e16, seed_radius=1e-4, seed_center=(0.0, 0.0, L - needle_len), w0=1.0,
+                particle_cap=20_000_000, dt=2e-12, n_ppc=75, w_min=1.0, growth_trigger=1.25, weight_interval=10,
+                photo_xi=0.075, photo_pq=4000.0)
+
+
 def streamer_128() -> dict:
     """The 128^3 streamer workload: 20 um cells, plates at 0 V / 5.12 kV (20 kV/cm),
     a 0.5 mm needle of 0.1 mm radius hanging from the top plate, a Gaussian
