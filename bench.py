@@ -34,6 +34,10 @@ METRIC = "electron push+MCC+deposit particle-updates/s on 1 GB300; % of HBM roof
 UNIT = "particle-updates/s"
 BYTES_PER_UPDATE = 96          # float32 state x,v,a,w (40 B) + id (8 B), read and written
 WORKLOAD = "streamer-128^3-fp32"
+# DRAM bytes (read + write) per parent of the collision kernel in this workload's steady state, from the
+# ncu capture summarised in profiles/k_push_streamer128.md (49.1 MB per launch of ~8.4e5 parents); scaled
+# to the run's mean launch for roofline.traffic.  Only valid for the kernel build and workload it was taken on.
+PUSH_DRAM_BYTES_PER_PARENT = 58.5
 
 
 def parse():
@@ -520,7 +524,13 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "particles_trace": n_trace},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None, "kernel": "k_push<float,PIC>",
+                         "frac": achieved / hbm,
+                         "traffic": (PUSH_DRAM_BYTES_PER_PARENT * parents_per_launch
+                                     if (args.workload == "streamer" and args.grid == 128 and args.precision == 32)
+                                     else None),
+                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per parent, "
+                                           "profiles/k_push_streamer128.md, scaled to the mean launch",
+                         "kernel": "k_push<float,PIC>",
                          "peak_source": peak_kind,
                          "bytes_per_update": BYTES_PER_UPDATE, "parents_per_launch": parents_per_launch,
                          "ms_per_launch": push_ms},
