@@ -191,6 +191,19 @@ int pic_set_field(pic_ctx *ctx, const float *Ex, const float *Ey, const float *E
  * the n_steps and synchronises the stream. */
 int pic_step(pic_ctx *ctx, int n_steps, pic_step_stats *stats);
 
+/* Coupled solve settings of a live context (Sec. 2.5): the relative residual
+ * target, the V-cycle limit per solve, and how float32 contexts drive their
+ * iterations.  device_loop != 0 (the default): from the third solve on, each
+ * solve is one CUDA graph whose conditional nodes run the CG loop on the
+ * device, without host synchronisation; a solve that reaches max_cycles
+ * raises a device flag that pic_step reports as PIC_ERR_TIMEOUT when it next
+ * reads the device state (at the latest when it returns).  device_loop == 0:
+ * the host reads the residual after every iteration and fails at once.  Both
+ * take the same decisions on the same values, so they give identical
+ * results.  Float64 and axisymmetric contexts always drive from the host.
+ * rtol must be positive and max_cycles at least 1; errors: PIC_ERR_ARG. */
+int pic_set_poisson(pic_ctx *ctx, double rtol, int max_cycles, int device_loop);
+
 /* Deposits the current electrons and returns the fixed-point grids (units of
  * 2^-32 physical particles per cell, int64) and the space charge
  * rho = e (n_pos - n_neg - n_e) in C/m^3.  Any output may be NULL; all are

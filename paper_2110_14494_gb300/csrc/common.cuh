@@ -29,6 +29,7 @@ enum : unsigned {
     kErrStack = 8u,          // descendant stack exhausted inside one step
     kErrSplitCapacity = 16u, // merge/split output full
     kErrPhotoCapacity = 32u, // photoelectron queue full
+    kErrPoissonLimit = 64u,  // a device-driven coupled solve reached its cycle limit
 };
 
 // ---------------------------------------------------------------- Philox4x32-10
@@ -129,6 +130,10 @@ struct DevState {
     long long qe_max;             // largest fixed-point electron deposit of a cell
     unsigned long long qe_sum;    // sum of the deposit (two's complement)
     unsigned int vhist[kVBins];   // speeds, kVBinsPerOctave bins per octave from 2^10 m/s
+    // report of the last device-driven coupled solve
+    int poisson_cycles, poisson_pad;
+    double poisson_rel;
+    unsigned long long dev_kernels;  // kernels run by device-side loops (cumulative)
 };
 
 // Uniform grid description (cell-centred, cubic cells).

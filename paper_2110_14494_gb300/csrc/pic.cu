@@ -730,24 +730,64 @@ struct pic_ctx {
     double w_prev = 0, ne_max = 0, t_total = 0;
     long long n_solves = 0;   // coupled solves so far (the warm start extrapolates after two)
     long long launches = 0;   // kernels launched by pic_step (for the profile)
-    // per-phase timing
+    unsigned long long dev_kernels_seen = 0;  // DevState::dev_kernels already counted in launches
+    // Float32 coupled field solve as one graph per current-potential slot
+    // (prologue, device-driven solve, report); used from the third solve on.
+    cudaGraphExec_t fgraph[3] = {nullptr, nullptr, nullptr};
+    long long fgraph_kernels[3] = {0, 0, 0};
+    cudaStream_t fcap = nullptr;
+    bool fgraph_off = false;     // the graph could not be recorded: host-driven solves
+    bool last_on_device = false; // the last solve reported through DevState
+    // Per-phase timing: events recorded on the stream at the phase marks and
+    // resolved later (at pic_profile, or once many are pending), so that
+    // timing adds no host synchronisation to the steps.
     int prof = 0;
-    cudaEvent_t ev[8] = {};
     pic_profile_times pt = {};
+    struct Pending {
+        cudaEvent_t a, b;
+        double* ms;
+        long long* n;
+    };
+    std::vector<cudaEvent_t> ev_free, ev_used;
+    std::vector<Pending> pending;
+    cudaEvent_t cur_ev[8] = {};
     void mark(int i) {
-        if (prof) cudaEventRecord(ev[i], s);
+        if (!prof) return;
+        cudaEvent_t e = nullptr;
+        if (!ev_free.empty()) {
+            e = ev_free.back();
+            ev_free.pop_back();
+        } else if (cudaEventCreate(&e) != cudaSuccess) {
+            cur_ev[i] = nullptr;
+            return;
+        }
+        ev_used.push_back(e);
+        cur_ev[i] = e;
+        cudaEventRecord(e, s);
     }
     void accumulate(int a, int b, double* ms, long long* n) {
-        if (!prof) return;
-        float t = 0.f;
-        if (cudaEventSynchronize(ev[b]) == cudaSuccess && cudaEventElapsedTime(&t, ev[a], ev[b]) == cudaSuccess) {
-            *ms += t;
-            ++*n;
+        if (prof && cur_ev[a] && cur_ev[b]) pending.push_back(Pending{cur_ev[a], cur_ev[b], ms, n});
+    }
+    // Adds the pending phase times (waits for their events); call between steps.
+    void resolve_times() {
+        for (const Pending& q : pending) {
+            float t = 0.f;
+            if (cudaEventSynchronize(q.b) == cudaSuccess && cudaEventElapsedTime(&t, q.a, q.b) == cudaSuccess) {
+                *q.ms += t;
+                ++*q.n;
+            }
         }
+        pending.clear();
+        ev_free.insert(ev_free.end(), ev_used.begin(), ev_used.end());
+        ev_used.clear();
+        for (int i = 0; i < 8; ++i) cur_ev[i] = nullptr;
     }
     ~pic_ctx() {
-        for (int i = 0; i < 8; ++i)
-            if (ev[i]) cudaEventDestroy(ev[i]);
+        for (cudaEvent_t e : ev_free) cudaEventDestroy(e);
+        for (cudaEvent_t e : ev_used) cudaEventDestroy(e);
+        for (int q = 0; q < 3; ++q)
+            if (fgraph[q]) cudaGraphExecDestroy(fgraph[q]);
+        if (fcap) cudaStreamDestroy(fcap);
         mg.release();
     }
 
@@ -1023,10 +1063,11 @@ static int read_state(pic_ctx* c, DevState* h) {
 static int check_err(pic_ctx* c, const DevState& h) {
     if (!h.err) return PIC_OK;
     cudaMemsetAsync(&c->st()->err, 0, sizeof(unsigned), c->s);
-    char msg[160];
+    char msg[192];
     snprintf(msg, sizeof msg, "device error flags 0x%x (1 output full, 2 child queue full, 4 fixed-point overflow, "
-             "8 descendant stack, 16 split output full, 32 photoelectron queue full)", h.err);
+             "8 descendant stack, 16 split output full, 32 photoelectron queue full, 64 poisson cycle limit)", h.err);
     if (h.err & kErrOverflow) return c->fail(PIC_ERR_OVERFLOW, msg);
+    if (h.err == kErrPoissonLimit) return c->fail(PIC_ERR_TIMEOUT, "poisson solve: cycle limit reached");
     return c->fail(PIC_ERR_CAPACITY, msg);
 }
 
@@ -1177,9 +1218,71 @@ static void fixed_to_rho(pic_ctx* c, double* rho) {
                                                  c->g.axi ? c->g.nx : 0);
 }
 
+// The steady-state float32 field solve as one graph launch: h^2 rho / eps0
+// from the fixed-point grids, the extrapolated warm start, and the
+// device-driven mixed solve, which reports its cycles, residual and any
+// cycle-limit flag into DevState (checked at the next state read-back).
+// The graph for the current potential slot is recorded on first use.
+// Returns PIC_ERR_STATE when the graph cannot be recorded.
+static int solve_field_pair_graph(pic_ctx* c) {
+    const long long n = c->g.ncell();
+    const int slot = c->ph_cur;
+    if (!c->fgraph[slot]) {
+        if ((!c->fcap && cudaStreamCreateWithFlags(&c->fcap, cudaStreamNonBlocking) != cudaSuccess) ||
+            c->mg.prepare_capture() != PIC_OK) {
+            cudaGetLastError();
+            return PIC_ERR_STATE;
+        }
+        if (cudaStreamBeginCapture(c->fcap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            return PIC_ERR_STATE;
+        }
+        const double dV = c->g.dx * c->g.dx * c->g.dx;
+        const double scale = kQ / (4294967296.0 * dV) * c->g.dx * c->g.dx / kEps0;
+        k_fixed_to_hrho<<<grid_n(n), 256, 0, c->fcap>>>((const long long*)c->qe(), (const long long*)c->qp(),
+                                                         (const long long*)c->qn(), n, (float)scale, (float*)c->rho());
+        c->mg.extrapolate_pair(c->ph_hi(c->ph_cur), c->ph_lo(c->ph_cur), c->ph_hi(c->ph_prev),
+                               c->ph_lo(c->ph_prev), c->ph_hi(c->ph_free), c->ph_lo(c->ph_free), (int)n, true,
+                               c->fcap);
+        DevState* st = c->st();
+        long long fixed = 0;
+        const int rc = c->mg.capture_solve_mixed(
+            c->fcap, (const float*)c->rho(), c->ph_hi(c->ph_free), c->ph_lo(c->ph_free), c->ph_hi(c->ph_prev),
+            c->ph_lo(c->ph_prev), c->g.dx, c->cfg.v_lo, c->cfg.v_hi, c->cfg.v_mask, c->cfg.poisson_rtol,
+            c->cfg.poisson_max_cycles, (float*)(c->ws + c->L.E4), &st->poisson_cycles, &st->poisson_rel, &st->err,
+            kErrPoissonLimit, &st->dev_kernels, &fixed);
+        cudaGraph_t gr = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(c->fcap, &gr);
+        cudaGraphExec_t gx = nullptr;
+        if (rc != PIC_OK || e != cudaSuccess || !gr || cudaGraphInstantiate(&gx, gr, 0) != cudaSuccess) {
+            if (gr) cudaGraphDestroy(gr);
+            cudaGetLastError();
+            return PIC_ERR_STATE;
+        }
+        cudaGraphDestroy(gr);
+        c->fgraph[slot] = gx;
+        c->fgraph_kernels[slot] = fixed + 2;
+    }
+    const cudaError_t e = cudaGraphLaunch(c->fgraph[slot], c->s);
+    if (e != cudaSuccess) return c->cuda_fail(e, "field solve graph");
+    c->n_solves++;
+    std::swap(c->ph_cur, c->ph_prev);
+    c->launches += c->fgraph_kernels[slot];
+    c->last_on_device = true;
+    c->field_valid = 1;
+    c->field_uniform = 0;
+    return PIC_OK;
+}
+
 // Coupled field: rho from the fixed-point grids, multigrid Poisson (warm
 // started from the previous potential), packed E for the next gather.
 static int solve_field_pair(pic_ctx* c) {
+    if (c->n_solves >= 2 && !c->fgraph_off) {
+        const int rc = solve_field_pair_graph(c);
+        if (rc != PIC_ERR_STATE) return rc;
+        c->fgraph_off = true;
+    }
+    c->last_on_device = false;
     const long long n = c->g.ncell();
     const double dV = c->g.dx * c->g.dx * c->g.dx;
     const double scale = kQ / (4294967296.0 * dV) * c->g.dx * c->g.dx / kEps0;
@@ -1460,6 +1563,7 @@ extern "C" int pic_step(pic_ctx* c, int n_steps, pic_step_stats* stats) {
             c->mark(6);
             c->accumulate(5, 6, &c->pt.ms_field, &c->pt.n_field);
         }
+        if (c->pending.size() >= 4096) c->resolve_times();
     }
     rc = read_state(c, &h);
     if (rc) return rc;
@@ -1479,6 +1583,10 @@ extern "C" int pic_step(pic_ctx* c, int n_steps, pic_step_stats* stats) {
         stats->w_absorbed = h.w_absorbed;
         stats->n_weight_updates = c->n_wu - wu0;
         stats->n_sorts = c->n_sorts - so0;
+        if (c->last_on_device) {
+            c->last_cycles = h.poisson_cycles;
+            c->last_rel = h.poisson_rel;
+        }
         stats->poisson_cycles = c->last_cycles;
         stats->poisson_rel_res = c->last_rel;
         stats->dt_last = c->dt_prev;
@@ -2061,15 +2169,33 @@ extern "C" int pic_progress(pic_ctx* c, long long* updates, long long* parents, 
     return PIC_OK;
 }
 
+extern "C" int pic_set_poisson(pic_ctx* c, double rtol, int max_cycles, int device_loop) {
+    if (!c || !(rtol > 0.0) || max_cycles < 1) return PIC_ERR_ARG;
+    // recorded graphs hold the old settings
+    for (int q = 0; q < 3; ++q)
+        if (c->fgraph[q]) {
+            cudaGraphExecDestroy(c->fgraph[q]);
+            c->fgraph[q] = nullptr;
+        }
+    c->cfg.poisson_rtol = rtol;
+    c->cfg.poisson_max_cycles = max_cycles;
+    c->fgraph_off = device_loop == 0;
+    return PIC_OK;
+}
+
 extern "C" int pic_profile(pic_ctx* c, int enable, pic_profile_times* out) {
     if (!c) return PIC_ERR_ARG;
+    DevState h;
+    const int rc = read_state(c, &h);
+    if (rc) return rc;
+    // kernels run inside device-side loops are counted on the device
+    if (h.dev_kernels >= c->dev_kernels_seen) c->launches += (long long)(h.dev_kernels - c->dev_kernels_seen);
+    c->dev_kernels_seen = h.dev_kernels;
+    c->resolve_times();
     c->pt.n_launches = c->launches;
     if (out) *out = c->pt;
     memset(&c->pt, 0, sizeof c->pt);
     c->launches = 0;
-    if (enable && !c->ev[0])
-        for (int i = 0; i < 8; ++i)
-            if (cudaEventCreate(&c->ev[i]) != cudaSuccess) return c->fail(PIC_ERR_CUDA, "event create");
     c->prof = enable ? 1 : 0;
     return PIC_OK;
 }

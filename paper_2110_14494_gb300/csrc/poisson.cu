@@ -624,11 +624,13 @@ size_t MG::carve(void* base, int nx_, int ny_, int nz_, bool mixed_, bool pair_c
         q32 = (float*)take(n0 * 4);
         phi_pair = pair_copy ? (float*)take(2 * n0 * 4) : nullptr;
         ctr = (unsigned*)take(8 * sizeof(unsigned));
+        loop = (MxLoop*)take(sizeof(MxLoop));
         const size_t b3 = (size_t)((nx_ + BX - 1) / BX) * ((ny_ + BY - 1) / BY) * ((nz_ + ZC - 1) / ZC);
         const size_t bf = (n0 + kFlatBlock * kFlatPer - 1) / (kFlatBlock * kFlatPer);
         part = (double*)take(2 * 8 * (b3 > bf ? b3 : bf));
         r64 = p64 = q64 = nullptr;
     } else {
+        loop = nullptr;
         r64 = (double*)take(n0 * 8);
         p64 = (double*)take(n0 * 8);
         q64 = (double*)take(n0 * 8);
@@ -729,6 +731,8 @@ void MG::iteration(cudaStream_t s, double* phi, const uint8_t* mk, bool first) {
 void MG::release() {
     for (int q = 0; q < 2; ++q)
         if (g_iter[q]) { cudaGraphExecDestroy(g_iter[q]); g_iter[q] = nullptr; }
+    for (int q = 0; q < 2; ++q)
+        if (cap_body[q]) { cudaStreamDestroy(cap_body[q]); cap_body[q] = nullptr; }
     for (int q = 0; q < 3; ++q)
         if (g_mx[q]) { cudaGraphExecDestroy(g_mx[q]); g_mx[q] = nullptr; }
     if (cap_stream) { cudaStreamDestroy(cap_stream); cap_stream = nullptr; }
@@ -909,7 +913,8 @@ int MG::solve_mixed(const void* rho, bool rho64, const uint8_t* mask, float* phi
     const float* dd = it > 0 ? d32 : nullptr;
     const float inv2h = (float)(1.0 / (2.0 * h));
     if (out_hi) {
-        k_mx_grad<<<g3, kBlk, 0, s>>>(phi_hi, phi_lo, dd, out_hi, out_lo, nx, ny, nz, inv2h, bc, Ex, Ey, Ez, E4);
+        k_mx_grad<<<g3, kBlk, 0, s>>>(phi_hi, phi_lo, dd, out_hi, out_lo, nx, ny, nz, inv2h, bc, Ex, Ey, Ez, E4,
+                                      nullptr);
         ++launches;
     } else {
         if (dd) {
@@ -918,12 +923,115 @@ int MG::solve_mixed(const void* rho, bool rho64, const uint8_t* mask, float* phi
         }
         if (Ex || E4) {
             k_mx_grad<<<g3, kBlk, 0, s>>>(phi_hi, phi_lo, nullptr, nullptr, nullptr, nx, ny, nz, inv2h, bc, Ex,
-                                                 Ey, Ez, E4);
+                                                 Ey, Ez, E4, nullptr);
             ++launches;
         }
     }
     if (cudaGetLastError() != cudaSuccess) return PIC_ERR_CUDA;
     return rc;
+}
+
+// ------------------------------------------------------------------ device-driven solve
+namespace {
+// Adds a conditional node with handle h at the capture point of stream cs
+// (which must be capturing) and makes it the stream's only dependency;
+// bodies receives its body graphs (owned by the node).
+cudaError_t add_conditional(cudaStream_t cs, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                            unsigned size, cudaGraph_t* bodies) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* ed = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(cs, &st, nullptr, &g, &deps, &ed, &nd);
+    if (e != cudaSuccess) return e;
+    if (st != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = type;
+    p.conditional.size = size;
+    cudaGraphNode_t node = nullptr;
+    e = cudaGraphAddNode(&node, g, deps, ed, nd, &p);
+    if (e != cudaSuccess) return e;
+    for (unsigned q = 0; q < size; ++q) bodies[q] = p.conditional.phGraph_out[q];
+    return cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+// Ends a capture into a body graph (the graph stays owned by its node).
+cudaError_t end_body_capture(cudaStream_t s) {
+    cudaGraph_t g = nullptr;
+    return cudaStreamEndCapture(s, &g);
+}
+}  // namespace
+
+int MG::prepare_capture() {
+    for (int q = 0; q < 2; ++q)
+        if (!cap_body[q] && cudaStreamCreateWithFlags(&cap_body[q], cudaStreamNonBlocking) != cudaSuccess)
+            return PIC_ERR_CUDA;
+    return PIC_OK;
+}
+
+int MG::capture_solve_mixed(cudaStream_t cs, const float* rho, float* phi_hi, float* phi_lo, float* out_hi,
+                            float* out_lo, double h, double v_lo, double v_hi, double v_mask, double rtol,
+                            int max_cycles, float* E4, int* cycles_dst, double* rel_dst, unsigned* err_dst,
+                            unsigned err_bit, unsigned long long* kernels_dst, long long* fixed_kernels) {
+    if (!mixed || !loop || !out_hi || !masks_ready) return PIC_ERR_STATE;
+    const int nx = lx[0], ny = ly[0], nz = lz[0], n = nx * ny * nz;
+    const MxBoundary bc{pair_of(v_lo), pair_of(v_hi), pair_of(v_mask)};
+    const dim3 g3 = grid_mx3(nx, ny, nz), gf = grid_mxf(n);
+    if (!cap_body[0] || !cap_body[1]) return PIC_ERR_STATE;
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    cudaGraph_t top = nullptr;
+    if (cudaStreamGetCaptureInfo(cs, &st, nullptr, &top) != cudaSuccess || st != cudaStreamCaptureStatusActive)
+        return PIC_ERR_CUDA;
+    cudaGraphConditionalHandle h_loop, h_branch;
+    if (cudaGraphConditionalHandleCreate(&h_loop, top, 1u, cudaGraphCondAssignDefault) != cudaSuccess)
+        return PIC_ERR_CUDA;
+    auto resid = [&](cudaStream_t q) {
+        k_mx_resid<float><<<g3, kBlk, 0, q>>>(rho, 1.0, m[0], phi_hi, phi_lo, nx, ny, nz, bc, g[0], part, ctr, norms);
+        ++launches;
+    };
+    cudaMemsetAsync(ctr, 0, 8 * sizeof(unsigned), cs);
+    cudaMemsetAsync(loop, 0, sizeof(MxLoop), cs);
+    resid(cs);
+    cudaGraph_t body = nullptr;
+    if (add_conditional(cs, h_loop, cudaGraphCondTypeWhile, 1, &body) != cudaSuccess) return PIC_ERR_CUDA;
+    if (cudaGraphConditionalHandleCreate(&h_branch, body, 4u, cudaGraphCondAssignDefault) != cudaSuccess)
+        return PIC_ERR_CUDA;
+    // loop body: the decision, then the switch over the branches
+    if (cudaStreamBeginCaptureToGraph(cap_body[0], body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+        cudaSuccess)
+        return PIC_ERR_CUDA;
+    k_mx_decide<<<1, 1, 0, cap_body[0]>>>(norms, loop, rtol, max_cycles, h_loop, h_branch);
+    cudaGraph_t br[4] = {nullptr, nullptr, nullptr, nullptr};
+    const cudaError_t e_sw = add_conditional(cap_body[0], h_branch, cudaGraphCondTypeSwitch, 4, br);
+    if (end_body_capture(cap_body[0]) != cudaSuccess || e_sw != cudaSuccess) return PIC_ERR_CUDA;
+    // branches: iterations with index 0 (first), 2 (even) and 1 (odd), then the refinement
+    const int its[3] = {0, 2, 1};
+    int kb[4];
+    for (int b = 0; b < 4; ++b) {
+        if (cudaStreamBeginCaptureToGraph(cap_body[1], br[b], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return PIC_ERR_CUDA;
+        const long long l0 = launches;
+        if (b < 3) {
+            iteration_mixed(cap_body[1], its[b]);
+        } else {
+            k_mx_commit<<<gf, kFlatBlock, 0, cap_body[1]>>>(phi_hi, phi_lo, d32, n);
+            ++launches;
+            resid(cap_body[1]);
+        }
+        kb[b] = (int)(launches - l0);
+        if (end_body_capture(cap_body[1]) != cudaSuccess) return PIC_ERR_CUDA;
+    }
+    const float inv2h = (float)(1.0 / (2.0 * h));
+    k_mx_grad<<<g3, kBlk, 0, cs>>>(phi_hi, phi_lo, d32, out_hi, out_lo, nx, ny, nz, inv2h, bc, nullptr, nullptr,
+                                   nullptr, E4, loop);
+    k_mx_report<<<1, 1, 0, cs>>>(loop, cycles_dst, rel_dst, err_dst, err_bit, kernels_dst,
+                                 make_int4(kb[0], kb[1], kb[2], kb[3]));
+    if (fixed_kernels) *fixed_kernels = 3;  // residual, gradient, report
+    return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ERR_CUDA;
 }
 
 }  // namespace pic

@@ -5,6 +5,16 @@
 
 namespace pic {
 
+// State of the flexible-CG loop of a device-driven mixed solve (device
+// memory): iteration index since the last refinement, cycles, decisions
+// taken, cycle-limit flag, branch counts, the residual norm at the last
+// refinement and the last relative residual.
+struct MxLoop {
+    int it, cyc, trips, timeout;
+    int n_branch[4];
+    double r_pass, rel;
+};
+
 struct MG {
     static constexpr int kMaxLevels = 12;
     int levels = 0;
@@ -23,6 +33,7 @@ struct MG {
     bool persistent = false;
     bool masks_ready = false;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t cap_body[2] = {nullptr, nullptr};  // captures into conditional-node bodies
     cudaGraphExec_t g_iter[2] = {nullptr, nullptr};  // [0] first iteration, [1] later ones
     const void* g_key[3] = {nullptr, nullptr, nullptr};
     long long graph_kernels[2] = {0, 0};
@@ -40,7 +51,26 @@ struct MG {
     double* part = nullptr;
     cudaGraphExec_t g_mx[3] = {nullptr, nullptr, nullptr};  // first, odd, even iterations
     long long graph_kernels_mx[3] = {0, 0, 0};
+    MxLoop* loop = nullptr;
+    // Creates the streams capture_solve_mixed records the loop bodies on
+    // (call before the caller's capture begins).
+    int prepare_capture();
     void iteration_mixed(cudaStream_t s, int it);
+    // Records the whole mixed solve on stream cs, which must be capturing a
+    // graph: the residual, a device-side while loop (a decision kernel, then
+    // a switch over the first / even / odd CG iteration and the refinement),
+    // the gradient and a report.  The report writes the cycles and the
+    // relative residual to cycles_dst / rel_dst, ORs err_bit into *err_dst
+    // when the cycle limit was reached, and adds the kernels the loop ran to
+    // *kernels_dst.  No host synchronisation.  rho is h^2 rho / eps0 in
+    // float; the solution goes to out (phi keeps the guess).  *fixed_kernels
+    // gets the kernels recorded outside the loop.  Returns PIC_OK, or
+    // PIC_ERR_CUDA when the graph could not be recorded (callers then use
+    // solve_mixed).
+    int capture_solve_mixed(cudaStream_t cs, const float* rho, float* phi_hi, float* phi_lo, float* out_hi,
+                            float* out_lo, double h, double v_lo, double v_hi, double v_mask, double rtol,
+                            int max_cycles, float* E4, int* cycles_dst, double* rel_dst, unsigned* err_dst,
+                            unsigned err_bit, unsigned long long* kernels_dst, long long* fixed_kernels);
     // out = 2 cur - prev (have_prev) or cur, pair format: the warm start.
     void extrapolate_pair(const float* cur_hi, const float* cur_lo, const float* prev_hi, const float* prev_lo,
                           float* out_hi, float* out_lo, int n, bool have_prev, cudaStream_t s);

@@ -433,12 +433,16 @@ __global__ void __launch_bounds__(kFlatBlock) k_mx_extrapolate(const float* __re
 
 // E = -grad(phi + delta) at cell centres (ghost rules as k_grad); with
 // out_hi set, also writes phi + delta there in the pair format.  delta may
-// be null.  E4 (if set) gets one 16-byte store per cell.
+// be null, and is ignored when the device-driven loop state L (optional)
+// says no iteration ran since the last refinement.  E4 (if set) gets one
+// 16-byte store per cell.
 __global__ void __launch_bounds__(BX * BY) k_mx_grad(const float* __restrict__ hi, const float* __restrict__ lo,
                                                      const float* __restrict__ dl, float* __restrict__ out_hi,
                                                      float* __restrict__ out_lo, int nx, int ny, int nz, float inv2h,
                                                      MxBoundary bc, float* __restrict__ Ex, float* __restrict__ Ey,
-                                                     float* __restrict__ Ez, float* __restrict__ E4) {
+                                                     float* __restrict__ Ez, float* __restrict__ E4,
+                                                     const MxLoop* __restrict__ L) {
+    if (L && L->it == 0) dl = nullptr;
     auto PH = [&](int x) {
         const float2 v = make_float2(__ldg(hi + x), __ldg(lo + x));
         return dl ? df_add_f(v, __ldg(dl + x)) : v;
@@ -486,6 +490,54 @@ __global__ void __launch_bounds__(BX * BY) k_mx_grad(const float* __restrict__ h
         if (E4) reinterpret_cast<float4*>(E4)[c] = make_float4(ex, ey, ez, 0.0f);
         if (out_hi) { out_hi[c] = pc.x; out_lo[c] = pc.y; }
     }
+}
+
+// ---------------------------------------------------------------- device-driven loop
+// One decision of the mixed solve's loop, the same as the host loop takes
+// it: record the residual norm when a refinement pass starts; stop when
+// ||r|| / ||b|| <= rtol or the cycle limit is reached (flagged); branch 3
+// (commit the correction and re-form the residual) when the float32
+// residual has dropped by kRefineDrop; else the CG iteration branch for the
+// current index (0 first, 1 even, 2 odd).  The trip bound is a safeguard:
+// every refinement is followed by an iteration or a stop, so the loop ends
+// within 2 max_cycles + 1 trips.
+__global__ void k_mx_decide(const double* __restrict__ sc, MxLoop* L, double rtol, int max_cycles,
+                            cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_branch) {
+    const double bn = sc[S_B2] > 0.0 ? sqrt(sc[S_B2]) : 1.0;
+    const double rn = sqrt(sc[S_R2]);
+    if (L->it == 0) L->r_pass = rn;
+    L->rel = rn / bn;
+    unsigned branch = 4;  // no branch
+    bool stop = false;
+    if (rn / bn <= rtol) {
+        stop = true;
+    } else if (L->cyc >= max_cycles || L->trips > 2 * max_cycles + 2) {
+        stop = true;
+        L->timeout = 1;
+    } else if (L->it > 0 && rn <= kRefineDrop * L->r_pass) {
+        branch = 3;
+        L->it = 0;
+    } else {
+        branch = L->it == 0 ? 0u : 1u + (unsigned)(L->it & 1);
+        ++L->it;
+        ++L->cyc;
+    }
+    ++L->trips;
+    if (branch < 4) ++L->n_branch[branch];
+    cudaGraphSetConditional(h_branch, branch);
+    if (stop) cudaGraphSetConditional(h_loop, 0u);
+}
+
+// Results of a device-driven solve: cycles, relative residual, the
+// cycle-limit flag, and the kernels its loop ran (kb: per branch).
+__global__ void k_mx_report(const MxLoop* __restrict__ L, int* cycles, double* rel, unsigned* err, unsigned bit,
+                            unsigned long long* kernels, int4 kb) {
+    *cycles = L->cyc;
+    *rel = L->rel;
+    if (L->timeout) *err |= bit;
+    *kernels += (unsigned long long)L->trips + (unsigned long long)L->n_branch[0] * kb.x +
+                (unsigned long long)L->n_branch[1] * kb.y + (unsigned long long)L->n_branch[2] * kb.z +
+                (unsigned long long)L->n_branch[3] * kb.w;
 }
 
 // float64 <-> float pair, for callers that hold the potential in float64.

@@ -103,7 +103,7 @@ class swarm_result(C.Structure):
 EXPORTS = ("pic_workspace_bytes", "pic_init", "pic_destroy", "pic_last_error", "pic_status_string",
            "pic_seed_gaussian", "pic_set_particles", "pic_get_particles", "pic_set_field", "pic_step",
            "pic_deposit", "pic_weight_update", "pic_count", "pic_save", "pic_load", "pic_progress",
-           "pic_profile", "pic_upload", "pic_download",
+           "pic_profile", "pic_upload", "pic_download", "pic_set_poisson",
            "poisson_workspace_bytes", "poisson_solve", "poisson_solve_noalloc", "swarm_workspace_bytes",
            "swarm_run", "swarm_autotune", "mlp_workspace_bytes", "mlp_forward", "mlp_forward_variant", "mlp_loss_grad",
            "mlp_train", "poisson_axi_workspace_bytes", "poisson_axi_solve")
@@ -134,6 +134,7 @@ def lib():
     L.pic_get_particles.argtypes = [VP, P(pic_particles_host), C.c_longlong, P(C.c_longlong)]
     L.pic_set_field.argtypes = [VP, VP, VP, VP, PD]
     L.pic_step.argtypes = [VP, C.c_int, P(pic_step_stats)]
+    L.pic_set_poisson.argtypes = [VP, C.c_double, C.c_int, C.c_int]
     L.pic_deposit.argtypes = [VP, VP, VP, VP, VP]
     L.pic_weight_update.argtypes = [VP]
     L.pic_count.argtypes = [VP, P(C.c_longlong)]
@@ -321,6 +322,13 @@ class PicContext:
         u, p, s = C.c_longlong(), C.c_longlong(), C.c_longlong()
         _check(lib().pic_progress(self.h, C.byref(u), C.byref(p), C.byref(s)), self.h, "pic_progress")
         return u.value, p.value, s.value
+
+    def set_poisson(self, rtol, max_cycles, device_loop=True):
+        """Coupled solve settings: residual target, V-cycle limit, and whether
+        float32 contexts run the CG loop on the device (graph conditional
+        nodes) or check the residual from the host after every iteration."""
+        _check(lib().pic_set_poisson(self.h, float(rtol), int(max_cycles), int(bool(device_loop))), self.h,
+               "pic_set_poisson")
 
     def profile(self, enable=True):
         t = pic_profile_times()

@@ -1,0 +1,88 @@
+"""The float32 coupled field solve driven on the device (one CUDA graph per
+solve whose conditional nodes run the flexible-CG loop, Sec. 2.5) against
+the same solve driven from the host: identical decisions on identical values,
+so the particle sets, the potentials and the reported cycles and residuals
+agree bit for bit; the cycle limit is still reported."""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests.gpu_common import by_id
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+SEED = 2110144940
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2110_14494_gb300 import build
+    build.build()
+
+
+def _streamer_ctx(device_loop, rtol=1e-6, grid_n=32):
+    """A small needle-plane streamer: a Gaussian seed below a charged needle,
+    coupled float32 solve, weight updates on growth."""
+    from paper_2110_14494_gb300 import PicContext
+    grid = W.grid_spec(grid_n, grid_n, grid_n + 16, 2.5e-5)
+    mask = W.needle_mask(grid, 0.35e-3, 0.08e-3)
+    V0 = 4000.0
+    ctx = PicContext(W.synthetic_air(), grid, precision=32, capacity=400_000, seed=SEED, dt=2e-12, mask=mask,
+                     coupled=True, v_lo=0.0, v_hi=V0, v_mask=V0, poisson_rtol=rtol, poisson_max_cycles=60,
+                     boundary=1, growth_trigger=1.5, particle_cap=150_000)
+    ctx.set_poisson(rtol, 60, device_loop=device_loop)
+    L = grid_n * 2.5e-5
+    ctx.seed_gaussian(5e19, 6e-5, (0.5 * L, 0.5 * L, 0.45 * (grid_n + 16) * 2.5e-5), 2e3)
+    return ctx
+
+
+def _phi(ctx, n):
+    blob = ctx.save()
+    return np.frombuffer(blob, np.float64, count=n, offset=len(blob) - 8 * n).copy()
+
+
+def test_device_loop_matches_host_loop():
+    n = 32 * 32 * 48
+    a = _streamer_ctx(True)
+    b = _streamer_ctx(False)
+    for step in range(8):
+        sa = a.step(1, stats=True)
+        sb = b.step(1, stats=True)
+        assert sa.poisson_cycles == sb.poisson_cycles, step
+        assert sa.poisson_rel_res == sb.poisson_rel_res, step
+        assert sa.poisson_rel_res <= 1e-6
+        assert sa.n_end == sb.n_end, step
+    assert np.array_equal(_phi(a, n), _phi(b, n))
+    pa, pb = by_id(a.get_particles()), by_id(b.get_particles())
+    for k in pa:
+        assert np.array_equal(pa[k], pb[k]), k
+
+
+def test_device_loop_reports_cycle_limit():
+    from paper_2110_14494_gb300 import PicError
+    for device_loop in (True, False):
+        ctx = _streamer_ctx(device_loop)
+        ctx.step(3)                      # the third solve already runs as a graph on the device loop
+        ctx.set_poisson(1e-14, 1, device_loop=device_loop)   # unreachable: the float pair bounds it near 1e-9
+        with pytest.raises(PicError) as ei:
+            ctx.step(2)
+        assert "cycle limit" in str(ei.value)
+
+
+def test_device_loop_counts_its_kernels():
+    a = _streamer_ctx(True)
+    b = _streamer_ctx(False)
+    for c in (a, b):
+        c.step(2)
+        c.profile(True)
+        c.step(4)
+    pa, pb = a.profile(False), b.profile(False)
+    # the same work; the device-driven solve adds one decision kernel per loop
+    # trip and one report kernel per solve, and counts its branches' kernels
+    # on the device
+    assert pb["n_launches"] > 0
+    assert pb["n_launches"] < pa["n_launches"] <= pb["n_launches"] + 4 * 10
