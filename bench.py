@@ -38,6 +38,14 @@ WORKLOAD = "streamer-128^3-fp32"
 # ncu capture summarised in profiles/k_push_streamer128.md (49.1 MB per launch of ~8.4e5 parents); scaled
 # to the run's mean launch for roofline.traffic.  Only valid for the kernel build and workload it was taken on.
 PUSH_DRAM_BYTES_PER_PARENT = 58.5
+# The collision kernels (parents and children) issue about this many warp
+# instructions per collision draw (a candidate event, or the last draw that
+# ends the step): ncu smsp__inst_executed.sum over three steady-state steps /
+# (updates x draws per update), from profiles/k_push_streamer128.md
+# (3.905e8 / (1.890e6 x 9.985)).
+PUSH_WARP_INST_PER_DRAW = 20.7
+ISSUE_SLOTS_PER_SM = 4   # warp schedulers per SM, one warp instruction each per clock
+N_SMS = 152
 
 
 def parse():
@@ -100,6 +108,23 @@ def peaks():
         d = json.load(open(p))
         return d.get("hbm_gbs"), "measured"
     return 6800.0, "fallback"
+
+
+def issue_roofline(draws_per_update, updates_per_step, collide_ms_per_step, clk):
+    """The collision kernels' binding limit: warp-instruction issue.  The
+    algorithmic work is one draw per candidate collision of the null-collision
+    method (nu_max dt per electron-step, measured) plus the draw that ends the
+    step; each costs PUSH_WARP_INST_PER_DRAW warp instructions (ncu, parents
+    and children kernels of steady-state steps).  Peak: 4 issue slots x 152
+    SMs x the median SM clock sampled while timing."""
+    mhz = clk.get("sm_mhz") or 2070.0
+    peak = ISSUE_SLOTS_PER_SM * N_SMS * mhz * 1e6 / 1e9
+    ach = PUSH_WARP_INST_PER_DRAW * draws_per_update * updates_per_step / (collide_ms_per_step * 1e-3) / 1e9
+    return {"bound": "issue", "kernel": "k_push + k_children <float,PIC>", "unit": "Gwarp-inst/s",
+            "achieved": ach, "peak": peak, "frac": ach / peak, "draws_per_update": draws_per_update,
+            "warp_inst_per_draw": PUSH_WARP_INST_PER_DRAW,
+            "source": "draws measured over 10 steps after the timed region; instructions per draw from ncu "
+                      "(profiles/k_push_streamer128.md); peak at the sampled median SM clock"}
 
 
 class Clocks:
@@ -450,6 +475,10 @@ def main():
     ms_max, upd_all = aggregate(ms, u1 - u0, dist, device="cuda")
     fin = ctx.step(0, stats=True)
     value = upd_all / (ms_max * 1e-3)
+    # collision draws per particle-update, sampled after the timed region
+    # (the statistics counters stay off while timing)
+    smp = ctx.step(10, stats=True)
+    draws_per_update = (smp.n_events + smp.n_processed) / max(smp.n_processed, 1)
 
     # dominant kernel: the parent push (gather + push + MCC + deposit)
     parents_per_launch = (p1 - p0) / max(prof["n_push"], 1)
@@ -463,12 +492,16 @@ def main():
           file=sys.stderr, flush=True)
 
     if args.profile_steps > 0:
+        ua = ctx.progress()[0]
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("prof")
         for _ in range(args.profile_steps):
             ctx.step(1)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
+        print(json.dumps({"diag": "profiled steps", "steps": args.profile_steps,
+                          "updates": ctx.progress()[0] - ua, "draws_per_update": draws_per_update}),
+              file=sys.stderr, flush=True)
 
     # end to end through the C ABI with host buffers: each step uploads the
     # particle state from pinned host memory, steps, and downloads it again
@@ -534,6 +567,8 @@ def main():
                          "peak_source": peak_kind,
                          "bytes_per_update": BYTES_PER_UPDATE, "parents_per_launch": parents_per_launch,
                          "ms_per_launch": push_ms},
+            "alu": issue_roofline(draws_per_update, (u1 - u0) / args.steps,
+                                  (prof["ms_push"] + prof["ms_children"]) / args.steps, clk),
             "phases_ms": phases,
             "gpu_launches": int(prof["n_launches"]),
             "clocks": clk,

@@ -808,6 +808,10 @@ int MG::solve(const double* rho, const uint8_t* mask, double* phi, double h, dou
 // ------------------------------------------------------------------ mixed precision
 namespace {
 dim3 grid_mx3(int nx, int ny, int nz) { return dim3((nx + BX - 1) / BX, (ny + BY - 1) / BY, (nz + ZC - 1) / ZC); }
+// the float4 stencil kernels: four x cells per thread (nx % 4 == 0)
+dim3 grid_mx3v(int nx, int ny, int nz) {
+    return dim3((nx / 4 + BX - 1) / BX, (ny + BY - 1) / BY, (nz + ZC - 1) / ZC);
+}
 dim3 grid_mxf(long long n) {
     const long long b = (n / 4 + kFlatBlock * kFlatPer - 1) / (kFlatBlock * kFlatPer);
     return dim3((unsigned)(b > 0 ? b : 1));
@@ -826,7 +830,11 @@ void MG::iteration_mixed(cudaStream_t s, int it) {
     const int cur = it & 1, first = it == 0 ? 1 : 0;
     vcycle(s);
     k_mx_dots<<<grid_mxf(n), kFlatBlock, 0, s>>>(e[0], g[0], q32, n, first, part, ctr + 1, norms);
-    k_mx_dir_apply<<<grid_mx3(nx, ny, nz), kBlk, 0, s>>>(e[0], p32[cur ^ 1], p32[cur], q32, m[0], nx, ny, nz, first,
+    if (nx % 4 == 0)
+        k_mx_dir_apply4<<<grid_mx3v(nx, ny, nz), kBlk, 0, s>>>(e[0], p32[cur ^ 1], p32[cur], q32, m[0], nx, ny, nz,
+                                                               first, part, ctr + 2, norms);
+    else
+        k_mx_dir_apply<<<grid_mx3(nx, ny, nz), kBlk, 0, s>>>(e[0], p32[cur ^ 1], p32[cur], q32, m[0], nx, ny, nz, first,
                                                          part, ctr + 2, norms);
     k_mx_update<<<grid_mxf(n), kFlatBlock, 0, s>>>(p32[cur], q32, d32, g[0], n, first, part, ctr + 3, norms);
     launches += 3;

@@ -107,15 +107,20 @@ __device__ bool grid_sums(const float (&v)[NV], double* part, unsigned* ctr, dou
     __threadfence();
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-        // four independent loads per round, added in a fixed order
+        // sixteen independent loads per round (one round trip covers the
+        // partials of up to 16 blocks per thread), added in a fixed order
         double s = 0.0;
-        for (unsigned x0 = t; x0 < nb; x0 += 4u * nthr) {
-            double a[4];
+        for (unsigned x0 = t; x0 < nb; x0 += 16u * nthr) {
+            double a[16];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < 16; ++u) {
                 const unsigned x = x0 + u * nthr;
                 a[u] = x < nb ? __ldcg(part + (size_t)x * NV + q) : 0.0;
             }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) a[u] += a[u + 8];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] += a[u + 4];
             s += (a[0] + a[1]) + (a[2] + a[3]);
         }
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
@@ -373,6 +378,100 @@ __global__ void __launch_bounds__(BX * BY) k_mx_dir_apply(const float* __restric
         p_cur[c] = pc;
         q[c] = qq;
         acc[0] += pc * qq;
+    }
+    double tot[1];
+    if (grid_sums<1>(acc, part, ctr, tot) && threadIdx.x == 0 && threadIdx.y == 0) {
+        const double gam = tot[0];
+        sc[S_GAM] = gam;
+        sc[S_ALPHA] = gam > 0.0 ? sc[S_RHO] / gam : 0.0;
+    }
+}
+
+// The same as k_mx_dir_apply for nx % 4 == 0, with four consecutive x cells
+// per thread (16-byte loads and stores): lane l of a warp holds x = 4 (32 b
+// + l) .. + 3 of one row; the x neighbours across float4 boundaries come
+// from the adjacent lanes, and the warp's end lanes load them.  Each cell's
+// p and q are the scalar kernel's (same operations in the same order); the
+// partial sums of p.q group the cells differently.
+__device__ __forceinline__ float4 ld4g(const float* p, int c) { return __ldg(reinterpret_cast<const float4*>(p + c)); }
+__device__ __forceinline__ float4 pdir4(const float* z, const float* pp, float beta, bool use_prev, int c) {
+    const float4 zz = ld4g(z, c);
+    if (!use_prev) return zz;
+    const float4 q = ld4g(pp, c);
+    return make_float4(fmaf(beta, q.x, zz.x), fmaf(beta, q.y, zz.y), fmaf(beta, q.z, zz.z), fmaf(beta, q.w, zz.w));
+}
+__device__ __forceinline__ float f4c(const float4& v, int e) { return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w)); }
+
+__global__ void __launch_bounds__(BX * BY) k_mx_dir_apply4(const float* __restrict__ z,
+                                                           const float* __restrict__ p_prev,
+                                                           float* __restrict__ p_cur, float* __restrict__ q,
+                                                           const uint8_t* __restrict__ mask, int nx, int ny, int nz,
+                                                           int first, double* part, unsigned* ctr, double* sc) {
+    const float beta = first ? 0.0f : (float)sc[S_BETA];
+    const bool use_prev = beta != 0.0f;
+    const int lane = threadIdx.x;
+    const int i0 = 4 * (blockIdx.x * BX + threadIdx.x), j = blockIdx.y * BY + threadIdx.y, k0 = blockIdx.z * ZC;
+    const bool in = i0 < nx && j < ny;
+    const int pl = nx * ny;
+    const int c0 = in ? lin(i0, j, 0, nx, ny) : 0;
+    float4 col[ZC + 2], ym[ZC], yp[ZC];
+    float xl[ZC], xr[ZC];
+    uchar4 mk[ZC];
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int d = 0; d < ZC + 2; ++d) {
+        const int k = k0 - 1 + d;
+        col[d] = (in && k >= 0 && k < nz) ? pdir4(z, p_prev, beta, use_prev, c0 + k * pl) : zero4;
+    }
+#pragma unroll
+    for (int d = 0; d < ZC; ++d) {
+        const int k = k0 + d;
+        const bool ok = in && k < nz;
+        const int c = c0 + (ok ? k : 0) * pl;
+        ym[d] = ok && j > 0 ? pdir4(z, p_prev, beta, use_prev, c - nx) : zero4;
+        yp[d] = ok && j < ny - 1 ? pdir4(z, p_prev, beta, use_prev, c + nx) : zero4;
+        xl[d] = 0.0f;
+        xr[d] = 0.0f;
+        if (ok && lane == 0 && i0 > 0) {
+            const float a = __ldg(z + c - 1);
+            xl[d] = use_prev ? fmaf(beta, __ldg(p_prev + c - 1), a) : a;
+        }
+        if (ok && lane == BX - 1 && i0 + 4 < nx) {
+            const float a = __ldg(z + c + 4);
+            xr[d] = use_prev ? fmaf(beta, __ldg(p_prev + c + 4), a) : a;
+        }
+        mk[d] = ok ? *reinterpret_cast<const uchar4*>(mask + c) : make_uchar4(1, 1, 1, 1);
+    }
+    float acc[1] = {0.0f};
+#pragma unroll
+    for (int d = 0; d < ZC; ++d) {
+        const int k = k0 + d;
+        const float4 pc = col[d + 1];
+        float left = __shfl_up_sync(kFull, pc.w, 1), right = __shfl_down_sync(kFull, pc.x, 1);
+        if (lane == 0) left = xl[d];
+        if (lane == BX - 1) right = xr[d];
+        if (!in || k >= nz) continue;
+        const float fz = (float)((k == 0) + (k == nz - 1));
+        const float fy = (float)((j == 0) + (j == ny - 1));
+        const unsigned char mm[4] = {mk[d].x, mk[d].y, mk[d].z, mk[d].w};
+        float qv[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int i = i0 + e;
+            const float c = f4c(pc, e);
+            float xm = e == 0 ? left : f4c(pc, e - 1);
+            float xp = e == 3 ? right : f4c(pc, e + 1);
+            if (i == 0) xm = 0.0f;
+            if (i == nx - 1) xp = 0.0f;
+            const float diag = 6.0f - ((float)((i == 0) + (i == nx - 1)) + fy) + fz;
+            float qq = diag * c - (((((xm + xp) + f4c(ym[d], e)) + f4c(yp[d], e)) + f4c(col[d], e)) + f4c(col[d + 2], e));
+            if (mm[e]) qq = 0.0f;
+            qv[e] = qq;
+            acc[0] += c * qq;
+        }
+        const int c = c0 + k * pl;
+        *reinterpret_cast<float4*>(p_cur + c) = pc;
+        *reinterpret_cast<float4*>(q + c) = make_float4(qv[0], qv[1], qv[2], qv[3]);
     }
     double tot[1];
     if (grid_sums<1>(acc, part, ctr, tot) && threadIdx.x == 0 && threadIdx.y == 0) {
