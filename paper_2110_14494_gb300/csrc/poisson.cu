@@ -227,14 +227,16 @@ __device__ __forceinline__ float inv_diag(float diag) { return diag == 6.0f ? (1
 // i = 2 ii + ((j + k + colour) & 1).  All loads of the ZS cells (the other
 // colour, not written by this launch) are issued before the first store.
 // Large levels take ZS = 4 (fewer, longer threads); small ones ZS = 1 (more
-// parallelism).
+// parallelism).  With omega != 1 the update is over-relaxed:
+// e + omega ((g + s) / diag - e).
 template <int ZS>
 __global__ void __launch_bounds__(BX * BY) k_smooth(float* __restrict__ e, const float* __restrict__ g,
                                                     const uint8_t* __restrict__ mask, int nx, int ny, int nz,
-                                                    int color) {
+                                                    int color, float omega) {
     const int j = blockIdx.y * BY + threadIdx.y, k0 = blockIdx.z * ZS, ii = blockIdx.x * BX + threadIdx.x;
     if (j >= ny) return;
-    float s[ZS], gv[ZS], dg[ZS];
+    const bool relax = omega != 1.0f;
+    float s[ZS], gv[ZS], dg[ZS], eo[ZS];
     uint8_t mv[ZS];
     int cc[ZS];
 #pragma unroll
@@ -246,10 +248,76 @@ __global__ void __launch_bounds__(BX * BY) k_smooth(float* __restrict__ e, const
         s[d] = ok ? nb_sum_e(e, i, j, k, nx, ny, nz, cc[d], dg[d]) : 0.0f;
         gv[d] = ok ? g[cc[d]] : 0.0f;
         mv[d] = ok ? mask[cc[d]] : 1;
+        eo[d] = ok && relax ? e[cc[d]] : 0.0f;
     }
 #pragma unroll
     for (int d = 0; d < ZS; ++d)
-        if (cc[d] >= 0 && !mv[d]) e[cc[d]] = (gv[d] + s[d]) * inv_diag(dg[d]);
+        if (cc[d] >= 0 && !mv[d]) {
+            const float v = (gv[d] + s[d]) * inv_diag(dg[d]);
+            e[cc[d]] = relax ? fmaf(omega, v - eo[d], eo[d]) : v;
+        }
+}
+
+__device__ __forceinline__ float diag_at(int i, int j, int k, int nx, int ny, int nz) {
+    return 6.0f - (float)((i == 0) + (i == nx - 1) + (j == 0) + (j == ny - 1)) + (float)((k == 0) + (k == nz - 1));
+}
+
+// The first full red-black sweep of a V-cycle level, from e = 0, in one
+// pass that needs no e: colour 0 cells get g * inv_diag (their neighbours
+// are still 0), colour 1 cells get (g + sum of those colour-0 values at
+// their neighbours) * inv_diag.  The same operations in the same order as a
+// zero fill followed by two smooth_half launches, so the values are
+// identical.  Thread (ii, j, k) takes the x pair (2 ii, 2 ii + 1) of row
+// (j, k); the colour-0 value of the adjacent pair comes from the next or
+// previous lane.  Electrode cells get 0.  With omega != 1 both values are
+// scaled by omega (over-relaxation from e = 0).
+__device__ __forceinline__ float first_red(const float* __restrict__ g, const uint8_t* __restrict__ mask, int i, int j,
+                                           int k, int nx, int ny, int nz, float omega) {
+    const int c = lin(i, j, k, nx, ny);
+    const float zero = 0.0f;
+    const float s = ((((zero + zero) + zero) + zero) + zero) + zero;
+    const float v = (g[c] + s) * inv_diag(diag_at(i, j, k, nx, ny, nz));
+    return mask[c] ? 0.0f : (omega != 1.0f ? omega * v : v);
+}
+__global__ void __launch_bounds__(BX * BY) k_sweep_first(float* __restrict__ e, const float* __restrict__ g,
+                                                         const uint8_t* __restrict__ mask, int nx, int ny, int nz,
+                                                         float omega) {
+    const int ii = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
+    const int lane = threadIdx.x;
+    const int par = (j + k) & 1;       // x offset of the colour-0 cell in the pair
+    const int i0 = 2 * ii + par;       // colour 0
+    const int i1 = 2 * ii + (1 - par); // colour 1
+    const bool in = j < ny && 2 * ii < nx;
+    const bool ok0 = in && i0 < nx, ok1 = in && i1 < nx;
+    // colour-0 value of this pair, shared with the neighbouring lanes
+    const float r0 = ok0 ? first_red(g, mask, i0, j, k, nx, ny, nz, omega) : 0.0f;
+    // the colour-1 cell's x neighbours: one is this pair's colour-0 cell, the
+    // other the adjacent pair's (previous pair when i1 < i0, else next)
+    const float prev = __shfl_up_sync(kFull, r0, 1), next = __shfl_down_sync(kFull, r0, 1);
+    if (!in) return;
+    if (ok0) e[lin(i0, j, k, nx, ny)] = r0;
+    if (!ok1) return;
+    const int c1 = lin(i1, j, k, nx, ny);
+    if (mask[c1]) {
+        e[c1] = 0.0f;
+        return;
+    }
+    // x neighbours of i1: i1 - 1 and i1 + 1
+    float xm, xp;
+    if (par == 1) {  // i1 = 2 ii: left neighbour in the previous pair, right one is i0
+        xm = i1 > 0 ? (lane > 0 ? prev : first_red(g, mask, i1 - 1, j, k, nx, ny, nz, omega)) : 0.0f;
+        xp = i0 < nx ? r0 : 0.0f;
+    } else {         // i1 = 2 ii + 1: left neighbour is i0, right one in the next pair
+        xm = r0;
+        xp = i1 < nx - 1 ? (lane < BX - 1 ? next : first_red(g, mask, i1 + 1, j, k, nx, ny, nz, omega)) : 0.0f;
+    }
+    const float ym = j > 0 ? first_red(g, mask, i1, j - 1, k, nx, ny, nz, omega) : 0.0f;
+    const float yp = j < ny - 1 ? first_red(g, mask, i1, j + 1, k, nx, ny, nz, omega) : 0.0f;
+    const float zm = k > 0 ? first_red(g, mask, i1, j, k - 1, nx, ny, nz, omega) : 0.0f;
+    const float zp = k < nz - 1 ? first_red(g, mask, i1, j, k + 1, nx, ny, nz, omega) : 0.0f;
+    const float s = ((((xm + xp) + ym) + yp) + zm) + zp;
+    const float v = (g[c1] + s) * inv_diag(diag_at(i1, j, k, nx, ny, nz));
+    e[c1] = omega != 1.0f ? omega * v : v;
 }
 
 // Coarse right-hand side: g_c = 4 * mean of the 8 fine residuals g - A e
@@ -333,15 +401,17 @@ __global__ void k_prolong_add(const float* __restrict__ ec, float* __restrict__ 
     }
 }
 
-// Coarse mask: a coarse cell is held at zero if any of its 8 children is.
-__global__ void k_restrict_mask(const uint8_t* __restrict__ m, int nx, int ny, int nz, uint8_t* __restrict__ mc) {
+// Coarse mask: a coarse cell is held at zero if at least min_children of
+// its 8 children are (1: any child).
+__global__ void k_restrict_mask(const uint8_t* __restrict__ m, int nx, int ny, int nz, uint8_t* __restrict__ mc,
+                                int min_children) {
     const int cx = nx / 2, cy = ny / 2;
     const int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y, K = blockIdx.z;
     if (I >= cx || J >= cy) return;
-    uint8_t v = 0;
+    int v = 0;
 #pragma unroll
-    for (int d = 0; d < 8; ++d) v |= m[lin(2 * I + (d & 1), 2 * J + ((d >> 1) & 1), 2 * K + (d >> 2), nx, ny)];
-    mc[lin(I, J, K, cx, cy)] = v ? 1 : 0;
+    for (int d = 0; d < 8; ++d) v += m[lin(2 * I + (d & 1), 2 * J + ((d >> 1) & 1), 2 * K + (d >> 2), nx, ny)] ? 1 : 0;
+    mc[lin(I, J, K, cx, cy)] = v >= min_children ? 1 : 0;
 }
 
 __global__ void k_copy_mask(const uint8_t* __restrict__ m, uint8_t* __restrict__ out, int n) {
@@ -367,6 +437,7 @@ struct TailLevels {
     const uint8_t* m[12];    // global masks
     int nx[12], ny[12], nz[12], off[12];  // shared-memory offsets (cells)
     int first, last, warp_from, pre, post, coarse, total;
+    float omega;             // over-relaxation of the pre- and post-smoothing sweeps
 };
 
 struct TailSmem {
@@ -392,7 +463,8 @@ template <bool WARP> __device__ __forceinline__ void tail_sync() {
     if (WARP) __syncwarp(); else __syncthreads();
 }
 
-template <bool WARP> __device__ void tail_half(const TailLevels& T, const TailSmem& S, int l, int color, const Dec& D) {
+template <bool WARP>
+__device__ void tail_half(const TailLevels& T, const TailSmem& S, int l, int color, const Dec& D, float omega) {
     const int nx = T.nx[l], ny = T.ny[l], nz = T.nz[l], hx = (nx + 1) / 2, o = T.off[l];
     float* e = S.e + o;
     const float* g = S.g + o;
@@ -406,7 +478,10 @@ template <bool WARP> __device__ void tail_half(const TailLevels& T, const TailSm
                     const int c = lin(i, j, k, nx, ny);
                     float diag;
                     const float s = nb_sum_e(e, i, j, k, nx, ny, nz, c, diag);
-                    if (!m[c]) e[c] = (g[c] + s) * inv_diag(diag);
+                    if (!m[c]) {
+                        const float v = (g[c] + s) * inv_diag(diag);
+                        e[c] = omega != 1.0f ? fmaf(omega, v - e[c], e[c]) : v;
+                    }
                 }
     tail_sync<WARP>();
 }
@@ -470,15 +545,18 @@ template <bool WARP> __device__ void tail_prolong(const TailLevels& T, const Tai
 }
 
 template <bool WARP> __device__ void tail_down(const TailLevels& T, const TailSmem& S, int l, const Dec& D) {
-    for (int s = 0; s < T.pre; ++s) { tail_half<WARP>(T, S, l, 0, D); tail_half<WARP>(T, S, l, 1, D); }
+    for (int s = 0; s < T.pre; ++s) { tail_half<WARP>(T, S, l, 0, D, T.omega); tail_half<WARP>(T, S, l, 1, D, T.omega); }
     tail_restrict<WARP>(T, S, l, D);
 }
 template <bool WARP> __device__ void tail_up(const TailLevels& T, const TailSmem& S, int l, const Dec& D) {
     tail_prolong<WARP>(T, S, l, D);
-    for (int s = 0; s < T.post; ++s) { tail_half<WARP>(T, S, l, 1, D); tail_half<WARP>(T, S, l, 0, D); }
+    for (int s = 0; s < T.post; ++s) { tail_half<WARP>(T, S, l, 1, D, T.omega); tail_half<WARP>(T, S, l, 0, D, T.omega); }
 }
 template <bool WARP> __device__ void tail_coarse(const TailLevels& T, const TailSmem& S, const Dec& D) {
-    for (int s = 0; s < T.coarse; ++s) { tail_half<WARP>(T, S, T.last, 0, D); tail_half<WARP>(T, S, T.last, 1, D); }
+    for (int s = 0; s < T.coarse; ++s) {
+        tail_half<WARP>(T, S, T.last, 0, D, 1.0f);
+        tail_half<WARP>(T, S, T.last, 1, D, 1.0f);
+    }
 }
 
 __global__ void __launch_bounds__(1024) k_tail_vcycle(const TailLevels T) {
@@ -559,11 +637,12 @@ __global__ void k_grad(const double* __restrict__ phi, int nx, int ny, int nz, d
 dim3 grid3(int nx, int ny, int nz) { return dim3((nx + BX - 1) / BX, (ny + BY - 1) / BY, nz); }
 const dim3 kBlk(BX, BY, 1);
 constexpr long long kSmoothDeep = 1ll << 20;  // levels with at least this many cells use 4 planes per thread
-void smooth_half(float* e, const float* g, const uint8_t* m, int nx, int ny, int nz, int color, cudaStream_t s) {
+void smooth_half(float* e, const float* g, const uint8_t* m, int nx, int ny, int nz, int color, float omega,
+                 cudaStream_t s) {
     const int zs = (long long)nx * ny * nz >= kSmoothDeep ? 4 : 1;
     const dim3 gr(((nx + 1) / 2 + BX - 1) / BX, (ny + BY - 1) / BY, (nz + zs - 1) / zs);
-    if (zs == 4) k_smooth<4><<<gr, kBlk, 0, s>>>(e, g, m, nx, ny, nz, color);
-    else k_smooth<1><<<gr, kBlk, 0, s>>>(e, g, m, nx, ny, nz, color);
+    if (zs == 4) k_smooth<4><<<gr, kBlk, 0, s>>>(e, g, m, nx, ny, nz, color, omega);
+    else k_smooth<1><<<gr, kBlk, 0, s>>>(e, g, m, nx, ny, nz, color, omega);
 }
 dim3 grid_flat(long long n) { return dim3((unsigned)((n + BX * BY - 1) / (BX * BY))); }
 dim3 grid_red(long long n) {
@@ -664,7 +743,8 @@ cudaError_t MG::build_masks(const uint8_t* mask, cudaStream_t s) {
     launches += levels;
     k_copy_mask<<<(unsigned)((n0 + 255) / 256), 256, 0, s>>>(mask, m[0], (int)n0);
     for (int l = 1; l < levels; ++l)
-        k_restrict_mask<<<grid3(lx[l], ly[l], lz[l]), kBlk, 0, s>>>(m[l - 1], lx[l - 1], ly[l - 1], lz[l - 1], m[l]);
+        k_restrict_mask<<<grid3(lx[l], ly[l], lz[l]), kBlk, 0, s>>>(m[l - 1], lx[l - 1], ly[l - 1], lz[l - 1], m[l],
+                                                                    mask_min_children);
     return cudaGetLastError();
 }
 
@@ -672,13 +752,20 @@ cudaError_t MG::build_masks(const uint8_t* mask, cudaStream_t s) {
 // tail run as separate kernels; the tail runs as one block.
 void MG::vcycle(cudaStream_t s) {
     const int t = tail_level();
-    launches += (long long)t * (1 + 2 * pre + 2 * post + 1) + 1;
+    // per level: pre-smoothing (the first sweep from zero is one kernel), restriction, prolongation,
+    // post-smoothing; then the tail
+    launches += (long long)t * ((pre > 0 ? 2 * pre - 1 : 0) + 2 * post + 2) + 1;
     for (int l = 0; l < t; ++l) {
         const long long n = (long long)lx[l] * ly[l] * lz[l];
-        cudaMemsetAsync(e[l], 0, n * sizeof(float), s);
-        for (int it = 0; it < pre; ++it) {
-            smooth_half(e[l], g[l], m[l], lx[l], ly[l], lz[l], 0, s);
-            smooth_half(e[l], g[l], m[l], lx[l], ly[l], lz[l], 1, s);
+        if (pre > 0) {
+            k_sweep_first<<<dim3(((lx[l] + 1) / 2 + BX - 1) / BX, (ly[l] + BY - 1) / BY, lz[l]), kBlk, 0, s>>>(
+                e[l], g[l], m[l], lx[l], ly[l], lz[l], omega);
+        } else {
+            cudaMemsetAsync(e[l], 0, n * sizeof(float), s);
+        }
+        for (int it = 1; it < pre; ++it) {
+            smooth_half(e[l], g[l], m[l], lx[l], ly[l], lz[l], 0, omega, s);
+            smooth_half(e[l], g[l], m[l], lx[l], ly[l], lz[l], 1, omega, s);
         }
         k_resid_restrict<<<grid3(lx[l + 1], ly[l + 1], lz[l + 1]), kBlk, 0, s>>>(
             e[l], g[l], m[l], lx[l], ly[l], lz[l], g[l + 1], m[l + 1], pre > 0 ? 1 : 0);
@@ -700,6 +787,7 @@ void MG::vcycle(cudaStream_t s) {
     T.pre = pre;
     T.post = post;
     T.coarse = coarse_sweeps;
+    T.omega = omega;
     T.total = off;
     const size_t smem = (size_t)off * (2 * sizeof(float) + 1);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_tail_vcycle, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -708,8 +796,8 @@ void MG::vcycle(cudaStream_t s) {
         k_prolong_add<<<grid3(lx[l + 1], ly[l + 1], lz[l + 1]), kBlk, 0, s>>>(e[l + 1], e[l], m[l], lx[l], ly[l],
                                                                               lz[l]);
         for (int it = 0; it < post; ++it) {
-            smooth_half(e[l], g[l], m[l], lx[l], ly[l], lz[l], 1, s);
-            smooth_half(e[l], g[l], m[l], lx[l], ly[l], lz[l], 0, s);
+            smooth_half(e[l], g[l], m[l], lx[l], ly[l], lz[l], 1, omega, s);
+            smooth_half(e[l], g[l], m[l], lx[l], ly[l], lz[l], 0, omega, s);
         }
     }
 }

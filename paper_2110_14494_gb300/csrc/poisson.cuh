@@ -25,6 +25,8 @@ struct MG {
     double* norms = nullptr;  // CG scalars: ||b||^2, ||r||^2, rho, gamma, z.r, z.q, alpha, beta
     double *r64 = nullptr, *p64 = nullptr, *q64 = nullptr;  // CG vectors (float64)
     int pre = 2, post = 2, coarse_sweeps = 8;
+    float omega = 1.0f;          // over-relaxation of the pre- and post-smoothing sweeps (1: Gauss-Seidel)
+    int mask_min_children = 1;   // a coarse cell is an electrode cell if this many of its children are
     long long launches = 0;  // kernels launched so far
     // Reusable state for a solver owned by a long-lived caller (a PIC context):
     // the coarse masks are built once, and each CG iteration (V-cycle plus
