@@ -735,6 +735,8 @@ struct pic_ctx {
     // (prologue, device-driven solve, report); used from the third solve on.
     cudaGraphExec_t fgraph[3] = {nullptr, nullptr, nullptr};
     long long fgraph_kernels[3] = {0, 0, 0};
+    cudaGraphExec_t agraph = nullptr;  // the same for axisymmetric contexts (one potential buffer)
+    long long agraph_kernels = 0;
     cudaStream_t fcap = nullptr;
     bool fgraph_off = false;     // the graph could not be recorded: host-driven solves
     bool last_on_device = false; // the last solve reported through DevState
@@ -787,7 +789,9 @@ struct pic_ctx {
         for (cudaEvent_t e : ev_used) cudaEventDestroy(e);
         for (int q = 0; q < 3; ++q)
             if (fgraph[q]) cudaGraphExecDestroy(fgraph[q]);
+        if (agraph) cudaGraphExecDestroy(agraph);
         if (fcap) cudaStreamDestroy(fcap);
+        amg.release();
         mg.release();
     }
 
@@ -1311,10 +1315,65 @@ static int solve_field_pair(pic_ctx* c) {
     return PIC_OK;
 }
 
+// The steady-state axisymmetric field solve as one graph launch: ring-cell
+// charge density, extrapolated warm start and the device-driven (r, z) solve
+// reporting into DevState.  Returns PIC_ERR_STATE when the graph cannot be
+// recorded.
+static int solve_field_axi_graph(pic_ctx* c) {
+    const long long n = c->g.ncell();
+    if (!c->agraph) {
+        if ((!c->fcap && cudaStreamCreateWithFlags(&c->fcap, cudaStreamNonBlocking) != cudaSuccess) ||
+            c->amg.prepare_capture() != PIC_OK) {
+            cudaGetLastError();
+            return PIC_ERR_STATE;
+        }
+        if (cudaStreamBeginCapture(c->fcap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            return PIC_ERR_STATE;
+        }
+        const double dV = c->g.dx * c->g.dx * c->g.dx * kPi;
+        k_fixed_to_rho<<<grid_n(n), 256, 0, c->fcap>>>((const long long*)c->qe(), (const long long*)c->qp(),
+                                                        (const long long*)c->qn(), n, 1.0 / (4294967296.0 * dV),
+                                                        c->rho(), c->g.nx);
+        k_extrapolate<<<grid_n(n), 256, 0, c->fcap>>>(c->phi(), (double*)(c->ws + c->L.phi_prev), n, 1);
+        DevState* st = c->st();
+        long long fixed = 0;
+        const int rc = c->amg.capture_solve(c->fcap, c->rho(), c->phi(), c->g.dx, c->cfg.v_lo, c->cfg.v_hi,
+                                            c->cfg.v_mask, c->cfg.poisson_rtol, c->cfg.poisson_max_cycles, c->prec,
+                                            c->ws + c->L.E4, &st->poisson_cycles, &st->poisson_rel, &st->err,
+                                            kErrPoissonLimit, &st->dev_kernels, &fixed);
+        cudaGraph_t gr = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(c->fcap, &gr);
+        cudaGraphExec_t gx = nullptr;
+        if (rc != PIC_OK || e != cudaSuccess || !gr || cudaGraphInstantiate(&gx, gr, 0) != cudaSuccess) {
+            if (gr) cudaGraphDestroy(gr);
+            cudaGetLastError();
+            return PIC_ERR_STATE;
+        }
+        cudaGraphDestroy(gr);
+        c->agraph = gx;
+        c->agraph_kernels = fixed + 2;
+    }
+    const cudaError_t e = cudaGraphLaunch(c->agraph, c->s);
+    if (e != cudaSuccess) return c->cuda_fail(e, "axisymmetric field solve graph");
+    c->n_solves++;
+    c->launches += c->agraph_kernels;
+    c->last_on_device = true;
+    c->field_valid = 1;
+    c->field_uniform = 0;
+    return PIC_OK;
+}
+
 // Axisymmetric coupled field: rho in the ring cells, the (r, z) solve warm
 // started from the extrapolated potential (float64 in both precisions),
 // packed (E_r, 0, E_z).
 static int solve_field_axi(pic_ctx* c) {
+    if (c->n_solves >= 2 && !c->fgraph_off) {
+        const int rc = solve_field_axi_graph(c);
+        if (rc != PIC_ERR_STATE) return rc;
+        c->fgraph_off = true;
+    }
+    c->last_on_device = false;
     fixed_to_rho(c, c->rho());
     k_extrapolate<<<grid_n(c->g.ncell()), 256, 0, c->s>>>(c->phi(), (double*)(c->ws + c->L.phi_prev), c->g.ncell(),
                                                            c->n_solves >= 2 ? 1 : 0);
@@ -2177,6 +2236,10 @@ extern "C" int pic_set_poisson(pic_ctx* c, double rtol, int max_cycles, int devi
             cudaGraphExecDestroy(c->fgraph[q]);
             c->fgraph[q] = nullptr;
         }
+    if (c->agraph) {
+        cudaGraphExecDestroy(c->agraph);
+        c->agraph = nullptr;
+    }
     c->cfg.poisson_rtol = rtol;
     c->cfg.poisson_max_cycles = max_cycles;
     c->fgraph_off = device_loop == 0;

@@ -18,6 +18,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "graph_util.cuh"
 #include "poisson.cuh"
 
 namespace pic {
@@ -1028,38 +1029,6 @@ int MG::solve_mixed(const void* rho, bool rho64, const uint8_t* mask, float* phi
 }
 
 // ------------------------------------------------------------------ device-driven solve
-namespace {
-// Adds a conditional node with handle h at the capture point of stream cs
-// (which must be capturing) and makes it the stream's only dependency;
-// bodies receives its body graphs (owned by the node).
-cudaError_t add_conditional(cudaStream_t cs, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
-                            unsigned size, cudaGraph_t* bodies) {
-    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
-    cudaGraph_t g = nullptr;
-    const cudaGraphNode_t* deps = nullptr;
-    const cudaGraphEdgeData* ed = nullptr;
-    size_t nd = 0;
-    cudaError_t e = cudaStreamGetCaptureInfo(cs, &st, nullptr, &g, &deps, &ed, &nd);
-    if (e != cudaSuccess) return e;
-    if (st != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
-    cudaGraphNodeParams p = {};
-    p.type = cudaGraphNodeTypeConditional;
-    p.conditional.handle = h;
-    p.conditional.type = type;
-    p.conditional.size = size;
-    cudaGraphNode_t node = nullptr;
-    e = cudaGraphAddNode(&node, g, deps, ed, nd, &p);
-    if (e != cudaSuccess) return e;
-    for (unsigned q = 0; q < size; ++q) bodies[q] = p.conditional.phGraph_out[q];
-    return cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
-}
-
-// Ends a capture into a body graph (the graph stays owned by its node).
-cudaError_t end_body_capture(cudaStream_t s) {
-    cudaGraph_t g = nullptr;
-    return cudaStreamEndCapture(s, &g);
-}
-}  // namespace
 
 int MG::prepare_capture() {
     for (int q = 0; q < 2; ++q)
@@ -1077,10 +1046,8 @@ int MG::capture_solve_mixed(cudaStream_t cs, const float* rho, float* phi_hi, fl
     const MxBoundary bc{pair_of(v_lo), pair_of(v_hi), pair_of(v_mask)};
     const dim3 g3 = grid_mx3(nx, ny, nz), gf = grid_mxf(n);
     if (!cap_body[0] || !cap_body[1]) return PIC_ERR_STATE;
-    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
-    cudaGraph_t top = nullptr;
-    if (cudaStreamGetCaptureInfo(cs, &st, nullptr, &top) != cudaSuccess || st != cudaStreamCaptureStatusActive)
-        return PIC_ERR_CUDA;
+    cudaGraph_t top = capturing_graph(cs);
+    if (!top) return PIC_ERR_CUDA;
     cudaGraphConditionalHandle h_loop, h_branch;
     if (cudaGraphConditionalHandleCreate(&h_loop, top, 1u, cudaGraphCondAssignDefault) != cudaSuccess)
         return PIC_ERR_CUDA;

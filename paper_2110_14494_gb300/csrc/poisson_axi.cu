@@ -21,6 +21,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "graph_util.cuh"
 #include "poisson_axi.cuh"
 #include "../../include/picmcc.h"
 
@@ -312,6 +313,7 @@ size_t AxiMG::carve(void* base, int nr, int nz) {
     };
     const size_t n0 = (size_t)nr * nz;
     norms = (double*)take(A_N * 8);
+    loop = (AxiLoop*)take(sizeof(AxiLoop));
     r = (double*)take(n0 * 8);
     p = (double*)take(n0 * 8);
     q = (double*)take(n0 * 8);
@@ -396,6 +398,114 @@ int AxiMG::solve(const double* rho, const uint8_t* mask, double* phi, double h, 
         ++launches;
     }
     return cudaGetLastError() == cudaSuccess ? rc : PIC_ERR_CUDA;
+}
+
+// One decision of the device-driven loop, as the host loop takes it: stop
+// when ||r|| / ||b|| <= rtol or the cycle limit is reached (flagged), else
+// branch 0 (first CG iteration) or 1 (later ones).  The trip bound is a
+// safeguard: every trip either iterates or stops.
+__global__ void k_axi_decide(const double* __restrict__ sc, AxiLoop* L, double rtol, int max_cycles,
+                             cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_branch) {
+    const double bn = sc[A_B2] > 0.0 ? sqrt(sc[A_B2]) : 1.0;
+    const double rn = sqrt(sc[A_R2]);
+    L->rel = rn / bn;
+    unsigned branch = 2;  // no branch
+    bool stop = false;
+    if (rn / bn <= rtol) {
+        stop = true;
+    } else if (L->cyc >= max_cycles || L->trips > max_cycles + 1) {
+        stop = true;
+        L->timeout = 1;
+    } else {
+        branch = L->cyc == 0 ? 0u : 1u;
+        ++L->cyc;
+    }
+    ++L->trips;
+    if (branch < 2) ++L->n_branch[branch];
+    cudaGraphSetConditional(h_branch, branch);
+    if (stop) cudaGraphSetConditional(h_loop, 0u);
+}
+
+__global__ void k_axi_report(const AxiLoop* __restrict__ L, int* cycles, double* rel, unsigned* err, unsigned bit,
+                             unsigned long long* kernels, int kb0, int kb1) {
+    *cycles = L->cyc;
+    *rel = L->rel;
+    if (L->timeout) *err |= bit;
+    *kernels += (unsigned long long)L->trips + (unsigned long long)L->n_branch[0] * kb0 +
+                (unsigned long long)L->n_branch[1] * kb1;
+}
+
+int AxiMG::prepare_capture() {
+    for (int q = 0; q < 2; ++q)
+        if (!cap_body[q] && cudaStreamCreateWithFlags(&cap_body[q], cudaStreamNonBlocking) != cudaSuccess)
+            return PIC_ERR_CUDA;
+    return PIC_OK;
+}
+
+void AxiMG::release() {
+    for (int q = 0; q < 2; ++q)
+        if (cap_body[q]) { cudaStreamDestroy(cap_body[q]); cap_body[q] = nullptr; }
+}
+
+int AxiMG::capture_solve(cudaStream_t cs, const double* rho, double* phi, double h, double v_lo, double v_hi,
+                         double v_mask, double rtol, int max_cycles, int packed_prec, void* E4, int* cycles_dst,
+                         double* rel_dst, unsigned* err_dst, unsigned err_bit, unsigned long long* kernels_dst,
+                         long long* fixed_kernels) {
+    if (!loop || !masks_ready || !cap_body[0] || !cap_body[1]) return PIC_ERR_STATE;
+    const int nr = lr[0], nz = lz[0], n = nr * nz;
+    const double h2e = h * h / kEps0;
+    const int nb = (n + 255) / 256;
+    cudaGraph_t top = capturing_graph(cs);
+    if (!top) return PIC_ERR_CUDA;
+    cudaGraphConditionalHandle h_loop, h_branch;
+    if (cudaGraphConditionalHandleCreate(&h_loop, top, 1u, cudaGraphCondAssignDefault) != cudaSuccess)
+        return PIC_ERR_CUDA;
+    cudaMemsetAsync(norms, 0, A_N * 8, cs);
+    cudaMemsetAsync(loop, 0, sizeof(AxiLoop), cs);
+    k_axi_resid<<<agrid(nr, nz), kABlk, 0, cs>>>(phi, rho, m[0], nr, nz, h2e, v_lo, v_hi, v_mask, r, g[0], norms);
+    cudaGraph_t body = nullptr;
+    if (add_conditional(cs, h_loop, cudaGraphCondTypeWhile, 1, &body) != cudaSuccess) return PIC_ERR_CUDA;
+    if (cudaGraphConditionalHandleCreate(&h_branch, body, 2u, cudaGraphCondAssignDefault) != cudaSuccess)
+        return PIC_ERR_CUDA;
+    if (cudaStreamBeginCaptureToGraph(cap_body[0], body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+        cudaSuccess)
+        return PIC_ERR_CUDA;
+    k_axi_decide<<<1, 1, 0, cap_body[0]>>>(norms, loop, rtol, max_cycles, h_loop, h_branch);
+    cudaGraph_t br[2] = {nullptr, nullptr};
+    const cudaError_t e_sw = add_conditional(cap_body[0], h_branch, cudaGraphCondTypeSwitch, 2, br);
+    if (end_body_capture(cap_body[0]) != cudaSuccess || e_sw != cudaSuccess) return PIC_ERR_CUDA;
+    int kb[2];
+    for (int b = 0; b < 2; ++b) {
+        if (cudaStreamBeginCaptureToGraph(cap_body[1], br[b], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return PIC_ERR_CUDA;
+        const int first = b == 0 ? 1 : 0;
+        const long long l0 = launches;
+        cudaStream_t q = cap_body[1];
+        vcycle(q);
+        k_axi_dot2<<<nb, dim3(256, 1, 1), 0, q>>>(e[0], r, this->q, n, norms, first ? 0 : 1);
+        k_axi_beta<<<1, 1, 0, q>>>(norms, first);
+        k_axi_update_p<<<nb, 256, 0, q>>>(p, e[0], n, norms);
+        k_axi_apply<<<agrid(nr, nz), kABlk, 0, q>>>(p, m[0], nr, nz, this->q, norms);
+        k_axi_alpha<<<1, 1, 0, q>>>(norms);
+        k_axi_update_xr<<<nb, dim3(256, 1, 1), 0, q>>>(phi, r, p, this->q, g[0], n, norms);
+        launches += 6;
+        kb[b] = (int)(launches - l0);
+        if (end_body_capture(q) != cudaSuccess) return PIC_ERR_CUDA;
+    }
+    long long fixed = 2;  // residual, report
+    if (E4) {
+        if (packed_prec == 64)
+            k_axi_grad<double><<<agrid(nr, nz), kABlk, 0, cs>>>(phi, nr, nz, h, v_lo, v_hi, nullptr, nullptr,
+                                                                 (double*)E4);
+        else
+            k_axi_grad<float><<<agrid(nr, nz), kABlk, 0, cs>>>(phi, nr, nz, h, v_lo, v_hi, nullptr, nullptr,
+                                                                (float*)E4);
+        ++fixed;
+    }
+    k_axi_report<<<1, 1, 0, cs>>>(loop, cycles_dst, rel_dst, err_dst, err_bit, kernels_dst, kb[0], kb[1]);
+    if (fixed_kernels) *fixed_kernels = fixed;
+    return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ERR_CUDA;
 }
 
 }  // namespace pic

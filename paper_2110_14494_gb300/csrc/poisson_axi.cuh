@@ -5,6 +5,13 @@
 
 namespace pic {
 
+// Loop state of a device-driven axisymmetric solve (device memory).
+struct AxiLoop {
+    int cyc, trips, timeout, pad;
+    int n_branch[2];
+    double rel;
+};
+
 struct AxiMG {
     static constexpr int kMaxLevels = 14;
     int levels = 0;
@@ -16,6 +23,21 @@ struct AxiMG {
     int pre = 2, post = 2, coarse_sweeps = 64;
     long long launches = 0;
     bool persistent = false, masks_ready = false;
+    AxiLoop* loop = nullptr;
+    cudaStream_t cap_body[2] = {nullptr, nullptr};
+    // Streams for recording loop bodies (call before the caller's capture).
+    int prepare_capture();
+    void release();
+    // Records the solve on the capturing stream cs: residual, a device-side
+    // while loop (decision, then a switch over the first and the later CG
+    // iterations), the gradient and a report of cycles, relative residual,
+    // cycle-limit flag (err_bit into *err_dst) and the loop's kernels (added
+    // to *kernels_dst).  No host synchronisation.  Returns PIC_OK or
+    // PIC_ERR_CUDA / PIC_ERR_STATE (callers then use solve).
+    int capture_solve(cudaStream_t cs, const double* rho, double* phi, double h, double v_lo, double v_hi,
+                      double v_mask, double rtol, int max_cycles, int packed_prec, void* E4, int* cycles_dst,
+                      double* rel_dst, unsigned* err_dst, unsigned err_bit, unsigned long long* kernels_dst,
+                      long long* fixed_kernels);
 
     void plan(int nr, int nz);
     // The coarsest level is solved by one block: at most 4096 cells.

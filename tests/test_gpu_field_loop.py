@@ -86,3 +86,47 @@ def test_device_loop_counts_its_kernels():
     # on the device
     assert pb["n_launches"] > 0
     assert pb["n_launches"] < pa["n_launches"] <= pb["n_launches"] + 4 * 10
+
+
+def _axi_ctx(device_loop, prec=64):
+    """A small axisymmetric needle-plane run (ring cells, float64 multigrid CG)."""
+    from paper_2110_14494_gb300 import PicContext
+    g = W.axi_grid(64, 128, 2e-5)
+    L, V = 128 * 2e-5, 20e5 * 128 * 2e-5
+    mk = W.needle_mask_axi(g, 0.5e-3, 0.1e-3)
+    ctx = PicContext(W.synthetic_air(), g, precision=prec, geometry=1, capacity=1_000_000, seed=SEED, dt=2e-12,
+                     mask=mk, coupled=True, v_lo=0.0, v_hi=V, v_mask=V, poisson_rtol=1e-8, poisson_max_cycles=80,
+                     boundary=1)
+    ctx.set_poisson(1e-8, 80, device_loop=device_loop)
+    ctx.seed_gaussian(1e19, 1e-4, (0.0, 0.0, L - 0.5e-3), 100.0)
+    return ctx
+
+
+def test_axi_device_loop_matches_host_loop():
+    """The axisymmetric solve adds its block sums with atomics, so the two
+    drivers agree to rounding, not bit for bit: the same cycle counts, the
+    residuals within 1e-3 of each other, and float64 particles within 1e-9
+    after six coupled steps."""
+    a, b = _axi_ctx(True), _axi_ctx(False)
+    for step in range(6):
+        sa, sb = a.step(1, stats=True), b.step(1, stats=True)
+        assert sa.poisson_cycles == sb.poisson_cycles, step
+        assert sa.poisson_rel_res <= 1e-8 and sb.poisson_rel_res <= 1e-8
+        assert abs(sa.poisson_rel_res - sb.poisson_rel_res) <= 1e-3 * sb.poisson_rel_res + 1e-14
+        assert sa.n_end == sb.n_end, step
+    pa, pb = by_id(a.get_particles()), by_id(b.get_particles())
+    assert np.array_equal(pa["id"], pb["id"])
+    for k in ("x", "y", "z"):
+        assert np.abs(pa[k] - pb[k]).max() <= 1e-9 * 128 * 2e-5, k
+    for k in ("vx", "vy", "vz"):
+        assert np.abs(pa[k] - pb[k]).max() <= 1e-9 * (np.abs(pb[k]).max() + 1e5), k
+
+
+def test_axi_device_loop_reports_cycle_limit():
+    from paper_2110_14494_gb300 import PicError
+    ctx = _axi_ctx(True)
+    ctx.step(3)
+    ctx.set_poisson(1e-15, 1, device_loop=True)
+    with pytest.raises(PicError) as ei:
+        ctx.step(2)
+    assert "cycle limit" in str(ei.value)
