@@ -188,7 +188,10 @@ int pic_set_field(pic_ctx *ctx, const float *Ex, const float *Ey, const float *E
  * and of ion-producing events; on schedule the cell sort and the weight
  * update (Sec. 2.1.2); with cfg.coupled the space charge and Poisson solve
  * that give the next step's field.  stats (host, optional) accumulates over
- * the n_steps and synchronises the stream. */
+ * the n_steps and synchronises the stream.  Each step reads the device
+ * counters once after its collisions (and reports any error flag then);
+ * without stats the call returns once the last step's field solve is
+ * enqueued. */
 int pic_step(pic_ctx *ctx, int n_steps, pic_step_stats *stats);
 
 /* Coupled solve settings of a live context (Sec. 2.5): the relative residual
@@ -197,7 +200,8 @@ int pic_step(pic_ctx *ctx, int n_steps, pic_step_stats *stats);
  * solve is one CUDA graph whose conditional nodes run the CG loop on the
  * device, without host synchronisation; a solve that reaches max_cycles
  * raises a device flag that pic_step reports as PIC_ERR_TIMEOUT when it next
- * reads the device state (at the latest when it returns).  device_loop == 0:
+ * reads the device state (after the collisions of the next step, or before
+ * returning when statistics are asked for).  device_loop == 0:
  * the host reads the residual after every iteration and fails at once.  Both
  * take the same decisions on the same values, so they give identical
  * results.  Float64 and axisymmetric contexts always drive from the host.

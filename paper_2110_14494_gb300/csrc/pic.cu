@@ -1526,6 +1526,9 @@ template <class T> static int extra_generations(pic_ctx* c, PushArgs<T>& A, int 
         DevState h;
         int rc = read_state(c, &h);
         if (rc) return rc;
+        // error flags raised so far (this step's kernels, or the previous step's field solve)
+        rc = check_err(c, h);
+        if (rc) return rc;
         const unsigned long long pending = (gen & 1) ? h.n_spill : h.n_child;
         c->n_next = (long long)(h.n_out < (unsigned long long)c->cfg.capacity ? h.n_out : c->cfg.capacity);
         if (!pending) {
@@ -1590,10 +1593,10 @@ extern "C" int pic_step(pic_ctx* c, int n_steps, pic_step_stats* stats) {
         if (c->cfg.adaptive_dt) c->dt_cur = c->dt_next;
         c->accumulate(0, 1, &c->pt.ms_push, &c->pt.n_push);
         c->accumulate(1, 2, &c->pt.ms_children, &c->pt.n_children);
+        c->n_host = c->n_next;  // the step's count, read back after its collisions
         bool sorted = false;
         c->mark(3);
         if (c->cfg.growth_trigger > 0 || c->cfg.weight_interval > 0) {
-            c->n_host = c->n_next;
             const bool grown = c->cfg.growth_trigger > 0 &&
                                (double)c->n_host > c->cfg.growth_trigger * (double)c->n_last_wu;
             const bool every = c->cfg.weight_interval > 0 && (c->step % (uint32_t)c->cfg.weight_interval) == 0;
@@ -1624,6 +1627,10 @@ extern "C" int pic_step(pic_ctx* c, int n_steps, pic_step_stats* stats) {
         }
         if (c->pending.size() >= 4096) c->resolve_times();
     }
+    // Every step read the device state after its collisions and checked the
+    // error flags; without statistics the call returns without waiting for
+    // the last field solve, whose flags the next read reports.
+    if (!want && n_steps > 0) return PIC_OK;
     rc = read_state(c, &h);
     if (rc) return rc;
     const int erc = check_err(c, h);
