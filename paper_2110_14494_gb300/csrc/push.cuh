@@ -711,25 +711,25 @@ static __global__ void k_resample_commit(DevState* st) {
 // filled with one coalesced load of 32 consecutive work items, finished
 // electrons wait in the output stage until 32 are there and are then
 // reflected at the faces, tested against the electrode, appended with one
-// cursor increment, stored and deposited by 32 lanes together, and
-// ionization products are staged and queued the same way.
+// cursor increment, stored and deposited by 32 lanes together.  An
+// ionization product is built at once (derived id, direction from its own
+// draw, positive-ion event of its birth) and pushed on the lane's stack;
+// the lane finishes its stack before it takes the next work item, flying
+// each product for the remaining time with the acceleration of the electron
+// the stack started from.  A product that finds the stack full waits, as a
+// compact entry, in the queue of the next (children) launch.
 //
 // CHILD = false: work item = one electron of the input buffer (already kicked
 // by k_field_kick), flying dt.  CHILD = true: work item = one queued
-// ionization product; staging it builds the product (derived id, direction
-// from its own draw) and records the positive-ion event of its birth; it
-// flies its remaining time with the parent's acceleration.  Products of
-// products are built at once and finished from the lane's stack.
+// ionization product, built when it is staged.
 constexpr int kRow = 11;    // padded row of a stage entry: x y z vx vy vz ax ay az w t
 constexpr int kOut = 64;    // output stage capacity (flushed at 32)
-constexpr int kCh = 64;     // product stage capacity (flushed at 32)
+constexpr int kCh = 64;     // product stage capacity of the batched swarm kernel (flushed at 32)
 
 template <class T> struct Stage {
     T in[32 * kRow];
     T out[kOut * kRow];
-    T ch[kCh * kRow];       // x y z sp ax ay az w t
-    uint64_t in_id[32], out_id[kOut], ch_id[kCh];
-    uint32_t ch_k[kCh];
+    uint64_t in_id[32], out_id[kOut];
 };
 
 template <class T> constexpr size_t collide_smem() {
@@ -784,41 +784,6 @@ __device__ __forceinline__ void flush_out(const PushArgs<T>& A, Stage<T>* sg, in
     n = rest;
 }
 
-// Queues staged ionization products [0, cnt) for the children kernel.
-template <class T>
-__device__ __forceinline__ void flush_children(const PushArgs<T>& A, Stage<T>* sg, int& n, int cnt) {
-    const int lane = threadIdx.x & 31;
-    __syncwarp();
-    unsigned long long s0 = 0;
-    if (lane == 0) s0 = atomicAdd(&A.st->n_child, (unsigned long long)cnt);
-    s0 = __shfl_sync(kFull, s0, 0);
-    if (lane < cnt) {
-        const unsigned long long s = s0 + lane;
-        if ((long long)s < A.cap_child) {
-            const T* r = sg->ch + lane * kRow;
-            const Soa<T>& q = A.cq.p;
-            q.r[PX][s] = r[0]; q.r[PY][s] = r[1]; q.r[PZ][s] = r[2];
-            q.r[VX][s] = r[3];
-            q.r[AX][s] = r[4]; q.r[AY][s] = r[5]; q.r[AZ][s] = r[6];
-            q.r[PW][s] = r[7];
-            A.cq.t_left[s] = r[8];
-            q.id[s] = sg->ch_id[lane];
-            A.cq.k[s] = sg->ch_k[lane];
-        } else {
-            atomicOr(&A.st->err, kErrChildCapacity);
-        }
-    }
-    __syncwarp();
-    const int rest = n - cnt;
-    if (lane < rest) {
-        for (int f = 0; f < 9; ++f) sg->ch[lane * kRow + f] = sg->ch[(cnt + lane) * kRow + f];
-        sg->ch_id[lane] = sg->ch_id[cnt + lane];
-        sg->ch_k[lane] = sg->ch_k[cnt + lane];
-    }
-    __syncwarp();
-    n = rest;
-}
-
 template <class T, int MODE, bool FAST, bool STATS, bool CHILD>
 __device__ __forceinline__ void collide_loop(const PushArgs<T>& A, const ProcSmem<T>* ps, Stage<T>* sg) {
     const int lane = threadIdx.x & 31;
@@ -826,11 +791,14 @@ __device__ __forceinline__ void collide_loop(const PushArgs<T>& A, const ProcSme
     long long n_items;
     unsigned long long* cursor;
     const ChildQ<T>& src = (A.gen & 1) ? A.cq2 : A.cq;
-    const ChildQ<T>& dst = (A.gen & 1) ? A.cq : A.cq2;
-    unsigned long long* dst_cnt = (A.gen & 1) ? &A.st->n_child : &A.st->n_spill;
+    // products the stack cannot take: the parents' go to the queue of the
+    // first children launch, a children launch's to the other queue
+    const ChildQ<T>& dst = CHILD ? ((A.gen & 1) ? A.cq : A.cq2) : A.cq;
+    unsigned long long* dst_cnt = CHILD ? ((A.gen & 1) ? &A.st->n_child : &A.st->n_spill) : &A.st->n_child;
     if (CHILD) {
         n_items = (long long)((A.gen & 1) ? A.st->n_spill : A.st->n_child);
         if (n_items > A.cap_child) n_items = A.cap_child;
+        if (n_items == 0) return;  // the stacks took every product (uniform over the grid)
         cursor = &A.st->n_fetch_c;
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&A.st->n_updates, (unsigned long long)n_items);
     } else {
@@ -844,11 +812,12 @@ __device__ __forceinline__ void collide_loop(const PushArgs<T>& A, const ProcSme
     StackSink<T> stk;
     Lane<T> L;
     bool active = false, dry = false;
-    int in_head = 0, in_count = 0, n_out = 0, n_ch = 0;
+    int in_head = 0, in_count = 0, n_out = 0;
+    unsigned popped = 0;  // products taken from the stack (counted as updates)
     for (;;) {
         // 1. idle lanes take staged electrons (a lane's own stack first)
         bool want = !active;
-        if (CHILD && want && stk.n > 0) {
+        if (want && stk.n > 0) {
             --stk.n;
             const int t = stk.n;
             for (int d = 0; d < 3; ++d) { L.x[d] = stk.x[t][d]; L.v[d] = stk.v[t][d]; L.d[d] = (T)0; }
@@ -859,6 +828,7 @@ __device__ __forceinline__ void collide_loop(const PushArgs<T>& A, const ProcSme
             active = true;
             want = false;
             ++ls.processed;
+            ++popped;
         }
         const unsigned need = __ballot_sync(kFull, want);
         const int avail = in_count - in_head;
@@ -918,7 +888,7 @@ __device__ __forceinline__ void collide_loop(const PushArgs<T>& A, const ProcSme
             __syncwarp();
         }
         // 3. termination
-        if (!__any_sync(kFull, active || (CHILD && stk.n > 0))) {
+        if (!__any_sync(kFull, active || stk.n > 0)) {
             if (dry && in_head >= in_count) break;
             continue;
         }
@@ -929,54 +899,34 @@ __device__ __forceinline__ void collide_loop(const PushArgs<T>& A, const ProcSme
         const bool done = r == EV_DONE, ion = r == EV_IONIZED;
         if (r == EV_DONE || r == EV_ATTACHED) active = false;
         // 5. ionization products
-        if (CHILD) {
-            if (ion) {
-                if (stk.n < StackSink<T>::kDepth) {
-                    const T xc[3] = {L.x[0] + L.d[0], L.x[1] + L.d[1], L.x[2] + L.d[2]};
-                    T vc[3];
-                    const uint64_t cid = make_child(A.K, A.step, L.id, L.k - 1, sp, vc);
-                    if (MODE == MODE_PIC && A.q_pos)
-                        deposit_at(A, xc[0], xc[1], xc[2], L.w, A.q_pos);
-                    const int t = stk.n++;
-                    for (int d = 0; d < 3; ++d) { stk.x[t][d] = xc[d]; stk.v[t][d] = vc[d]; }
-                    stk.w[t] = L.w;
-                    stk.id[t] = cid;
-                    stk.t[t] = L.t_left;
+        if (ion) {
+            if (stk.n < StackSink<T>::kDepth) {
+                const T xc[3] = {L.x[0] + L.d[0], L.x[1] + L.d[1], L.x[2] + L.d[2]};
+                T vc[3];
+                const uint64_t cid = make_child(A.K, A.step, L.id, L.k - 1, sp, vc);
+                if (MODE == MODE_PIC && A.q_pos)
+                    deposit_at(A, xc[0], xc[1], xc[2], L.w, A.q_pos);
+                const int t = stk.n++;
+                for (int d = 0; d < 3; ++d) { stk.x[t][d] = xc[d]; stk.v[t][d] = vc[d]; }
+                stk.w[t] = L.w;
+                stk.id[t] = cid;
+                stk.t[t] = L.t_left;
+                ++ls.children;
+            } else {  // stack full: the compact entry waits for the next generation
+                const unsigned long long q = atomicAdd(dst_cnt, 1ull);
+                if ((long long)q < A.cap_child) {
+                    const Soa<T>& d = dst.p;
+                    d.r[PX][q] = L.x[0] + L.d[0]; d.r[PY][q] = L.x[1] + L.d[1]; d.r[PZ][q] = L.x[2] + L.d[2];
+                    d.r[VX][q] = sp;
+                    d.r[AX][q] = L.a[0]; d.r[AY][q] = L.a[1]; d.r[AZ][q] = L.a[2];
+                    d.r[PW][q] = L.w;
+                    d.id[q] = L.id;
+                    dst.t_left[q] = L.t_left;
+                    dst.k[q] = L.k - 1;
                     ++ls.children;
-                } else {  // stack full: the compact entry waits for the next generation
-                    const unsigned long long q = atomicAdd(dst_cnt, 1ull);
-                    if ((long long)q < A.cap_child) {
-                        const Soa<T>& d = dst.p;
-                        d.r[PX][q] = L.x[0] + L.d[0]; d.r[PY][q] = L.x[1] + L.d[1]; d.r[PZ][q] = L.x[2] + L.d[2];
-                        d.r[VX][q] = sp;
-                        d.r[AX][q] = L.a[0]; d.r[AY][q] = L.a[1]; d.r[AZ][q] = L.a[2];
-                        d.r[PW][q] = L.w;
-                        d.id[q] = L.id;
-                        dst.t_left[q] = L.t_left;
-                        dst.k[q] = L.k - 1;
-                        ++ls.children;
-                    } else {
-                        atomicOr(&A.st->err, kErrChildCapacity);
-                    }
+                } else {
+                    atomicOr(&A.st->err, kErrChildCapacity);
                 }
-            }
-        } else {
-            const unsigned im = __ballot_sync(kFull, ion);
-            if (im) {
-                if (ion) {
-                    const int e = n_ch + __popc(im & lt);
-                    T* q = sg->ch + e * kRow;
-                    q[0] = L.x[0] + L.d[0]; q[1] = L.x[1] + L.d[1]; q[2] = L.x[2] + L.d[2];
-                    q[3] = sp;
-                    q[4] = L.a[0]; q[5] = L.a[1]; q[6] = L.a[2];
-                    q[7] = L.w;
-                    q[8] = L.t_left;
-                    sg->ch_id[e] = L.id;
-                    sg->ch_k[e] = L.k - 1;
-                    ++ls.children;
-                }
-                n_ch += __popc(im);
-                if (n_ch >= 32) flush_children(A, sg, n_ch, 32);
             }
         }
         // 6. finished electrons
@@ -996,7 +946,11 @@ __device__ __forceinline__ void collide_loop(const PushArgs<T>& A, const ProcSme
         }
     }
     if (n_out > 0) flush_out<T, MODE>(A, sg, n_out, n_out, ls, M);
-    if (!CHILD && n_ch > 0) flush_children(A, sg, n_ch, n_ch);
+    {
+        unsigned pw = popped;
+        for (int o = 16; o > 0; o >>= 1) pw += __shfl_xor_sync(kFull, pw, o);
+        if (lane == 0 && pw) atomicAdd(&A.st->n_updates, (unsigned long long)pw);
+    }
     if (STATS) flush_stats(A, ls, A.n_proc);
     if (MODE == MODE_SWARM) {
         M.m[14] += ls.w_ion;

@@ -130,3 +130,22 @@ def test_axi_device_loop_reports_cycle_limit():
     with pytest.raises(PicError) as ei:
         ctx.step(2)
     assert "cycle limit" in str(ei.value)
+
+
+def test_device_loop_refinement_branch_matches_host_loop():
+    """At rtol 1e-9 the float32 correction must be committed and the pair
+    residual re-formed (iterative refinement) within a solve: the device
+    loop's refinement branch against the host loop, bit for bit."""
+    n = 32 * 32 * 48
+    a = _streamer_ctx(True, rtol=1e-9)
+    b = _streamer_ctx(False, rtol=1e-9)
+    for step in range(5):
+        sa = a.step(1, stats=True)
+        sb = b.step(1, stats=True)
+        assert sa.poisson_cycles == sb.poisson_cycles, step
+        assert sa.poisson_rel_res == sb.poisson_rel_res, step
+        assert sa.poisson_rel_res <= 1e-9
+    assert np.array_equal(_phi(a, n), _phi(b, n))
+    pa, pb = by_id(a.get_particles()), by_id(b.get_particles())
+    for k in pa:
+        assert np.array_equal(pa[k], pb[k]), k
