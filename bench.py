@@ -37,13 +37,13 @@ WORKLOAD = "streamer-128^3-fp32"
 # DRAM bytes (read + write) per parent of the collision kernel in this workload's steady state, from the
 # ncu capture summarised in profiles/k_push_streamer128.md (49.1 MB per launch of ~8.4e5 parents); scaled
 # to the run's mean launch for roofline.traffic.  Only valid for the kernel build and workload it was taken on.
-PUSH_DRAM_BYTES_PER_PARENT = 60.4
+PUSH_DRAM_BYTES_PER_PARENT = 61.9
 # The collision kernels (parents and children) issue about this many warp
 # instructions per collision draw (a candidate event, or the last draw that
 # ends the step): ncu smsp__inst_executed.sum over three steady-state steps /
 # (updates x draws per update), from profiles/k_push_streamer128.md
-# (4.078e8 / (1.890e6 x 9.985)).
-PUSH_WARP_INST_PER_DRAW = 21.6
+# (4.191e8 / (1.890e6 x 9.985)).
+PUSH_WARP_INST_PER_DRAW = 22.2
 ISSUE_SLOTS_PER_SM = 4   # warp schedulers per SM, one warp instruction each per clock
 N_SMS = 152
 

@@ -1022,6 +1022,7 @@ template <class T> static PushArgs<T> make_args(pic_ctx* c, int mode) {
     A.K = c->K;
     A.step = c->step;
     A.first = c->a_valid ? 0 : 1;
+    A.kick_on_load = 0;
     A.cap_out = c->cfg.capacity;
     A.cap_child = c->cfg.capacity;
     A.nx = c->g.nx; A.ny = c->g.ny; A.nz = c->g.nz;
@@ -1550,9 +1551,10 @@ template <class T> static int one_step(pic_ctx* c, bool stats) {
     PushArgs<T> A = make_args<T>(c, MODE_PIC);
     cudaMemsetAsync(c->qe(), 0, (size_t)c->g.ncell() * 8, c->s);
     c->mark(0);
-    c->launches += 4;
-    cudaError_t e = PushLaunch<T>::field_kick(A, grid_n(c->cfg.capacity), c->s);
-    if (e == cudaSuccess) e = PushLaunch<T>::parents(A, MODE_PIC, stats, c->grid_push, c->s);
+    c->launches += 3;
+    // the gather and half-kick of Eq. 2 are done as the collision kernel loads each parent
+    A.kick_on_load = 1;
+    cudaError_t e = PushLaunch<T>::parents(A, MODE_PIC, stats, c->grid_push, c->s);
     c->mark(1);
     if (e == cudaSuccess) e = PushLaunch<T>::children(A, MODE_PIC, stats, c->grid_push, c->s);
     c->mark(2);

@@ -41,6 +41,7 @@ template <class T> struct PushArgs {
     Keys K;
     uint32_t step;
     int first;                 // previous acceleration unknown: no half-kick
+    int kick_on_load;          // parents get the gather and half-kick when the collision kernel loads them
     long long cap_out, cap_child;
     // grid (PIC mode)
     int nx, ny, nz;
@@ -594,6 +595,20 @@ __global__ void __launch_bounds__(256) k_field_kick(const PushArgs<T> A) {
     }
 }
 
+// The same half-kick for one loaded electron (f = x y z vx vy vz ax ay az w),
+// done by the collision kernel as it stages its parents.
+template <class T> __device__ __forceinline__ void half_kick(const PushArgs<T>& A, T f[10]) {
+    const T qm = (T)(kQ / kMe);
+    T E[3];
+    gather(A, f, E);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const T an = -qm * E[d];
+        if (!A.first) f[VX + d] = f[VX + d] + (T)0.5 * A.dt_kick * (an - f[AX + d]);
+        f[AX + d] = an;
+    }
+}
+
 // Path of every photon emitted in the launch before (see photo_test): the
 // absorbed ones inside the gas deposit their ion and queue a photoelectron.
 template <class T>
@@ -877,7 +892,10 @@ __device__ __forceinline__ void collide_loop(const PushArgs<T>& A, const ProcSme
                         r[10] = src.t_left[it];
                         sg->in_id[lane] = cid;
                     } else {
-                        for (int f = 0; f < 10; ++f) r[f] = A.in.r[f][it];
+                        T f[10];
+                        for (int q = 0; q < 10; ++q) f[q] = A.in.r[q][it];
+                        if (MODE == MODE_PIC && A.kick_on_load) half_kick(A, f);
+                        for (int q = 0; q < 10; ++q) r[q] = f[q];
                         r[10] = A.dt;
                         sg->in_id[lane] = A.in.id[it];
                     }
