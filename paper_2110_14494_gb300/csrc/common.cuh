@@ -134,6 +134,9 @@ struct DevState {
     int poisson_cycles, poisson_pad;
     double poisson_rel;
     unsigned long long dev_kernels;  // kernels run by device-side loops (cumulative)
+    unsigned long long n_big;        // weight update: cells left to the block-per-cell merge
+    unsigned long long n_occ;        // weight update: occupied cells listed
+    unsigned long long n_occ_fetch;  // weight update: work cursor over the listed cells
 };
 
 // Uniform grid description (cell-centred, cubic cells).

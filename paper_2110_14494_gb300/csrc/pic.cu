@@ -382,26 +382,96 @@ __device__ __forceinline__ double omega_of(long long W, int n_ppc, double w_min)
     return fmax((double)W / kS24 / (double)n_ppc, w_min);
 }
 
+// Exact float64 operations done with integer instructions (the float64 pipe
+// of this part is narrow): the same results as the float64 conversions.
+// float -> double (exact: rebias the exponent, widen the significand).
+__device__ __forceinline__ double f2d_exact(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 255u) return (double)x;  // zero, subnormal, inf, NaN: the conversion instruction
+    const unsigned long long b = ((unsigned long long)(u >> 31) << 63) | ((unsigned long long)(e + 896u) << 52) |
+                                 ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)b);
+}
+__device__ __forceinline__ double to_d(float x) { return f2d_exact(x); }
+__device__ __forceinline__ double to_d(double x) { return x; }
+// unif<double>(w) = (2 (w >> 9) + 1) 2^-24, built from its bits
+__device__ __forceinline__ double unif_d_exact(uint32_t w) {
+    const unsigned v = 2u * (w >> 9) + 1u;  // odd, below 2^24
+    const int pb = 31 - __clz(v);           // leading bit
+    const unsigned long long mant = ((unsigned long long)v << (52 - pb)) & 0xfffffffffffffull;
+    return __longlong_as_double((long long)(((unsigned long long)(pb - 24 + 1023) << 52) | mant));
+}
+// rint(w 2^24) of a float weight, rounded to nearest even: the value of
+// __double2ll_rn((double)w * 2^24) by integer arithmetic
+__device__ __forceinline__ long long fix24(float w) {
+    const unsigned u = __float_as_uint(w);
+    const int e = (int)((u >> 23) & 0xffu);
+    if (e == 0 || e == 255) return __double2ll_rn((double)w * kS24);
+    const long long m = (long long)((u & 0x7fffffu) | 0x800000u);  // w = m 2^(e - 150)
+    const int sh = e - 126;                                         // w 2^24 = m 2^sh
+    long long r;
+    if (sh >= 0) {
+        r = m << sh;
+    } else if (sh < -25) {
+        r = 0;
+    } else {
+        const int k = -sh;
+        const long long q = m >> k, rem = m & ((1ll << k) - 1), half = 1ll << (k - 1);
+        r = q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
+    }
+    return (u >> 31) ? -r : r;
+}
+__device__ __forceinline__ long long fix24(double w) { return __double2ll_rn(w * kS24); }
+// x < lo and x > hi of a float against float64 thresholds, as float compares
+// (the thresholds rounded up, respectively down, to float: exact equivalents)
+__device__ __forceinline__ bool lt_d(float x, double lo) { return x < __double2float_ru(lo); }
+__device__ __forceinline__ bool lt_d(double x, double lo) { return x < lo; }
+__device__ __forceinline__ bool gt_d(float x, double hi) { return x > __double2float_rd(hi); }
+__device__ __forceinline__ bool gt_d(double x, double hi) { return x > hi; }
+
+// Predicted particle count after the merge and split, in 2^-24 units:
+// sum over cells of W / omega.  A warp takes 32 consecutive cells (one load
+// of their bounds per lane) and sums the weights of each occupied one with
+// all its lanes; the fixed-point sums are exact, so their order is free.
+// The occupied cells are listed in occ (any order) for the merge kernel.
 template <class T>
 __global__ void k_cell_weight(const Soa<T> p, const uint32_t* __restrict__ start, long long ncell, int n_ppc,
-                              double w_min, DevState* st) {
+                              double w_min, uint32_t* __restrict__ occ_list, DevState* st) {
+    const int lane = threadIdx.x & 31;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     long long acc = 0;
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += (long long)gridDim.x * blockDim.x) {
-        const uint32_t s0 = start[c], s1 = start[c + 1];
-        if (s0 == s1) continue;
-        long long W = 0;
-        for (uint32_t t = s0; t < s1; ++t) W += __double2ll_rn((double)p.r[PW][t] * kS24);
-        const double om = omega_of(W, n_ppc, w_min);
-        acc += __double2ll_rn((double)W / om);
+    for (long long c0 = gw * 32; c0 < ncell; c0 += nw * 32) {
+        const long long cl = c0 + lane;
+        const uint32_t a0 = cl < ncell ? start[cl] : 0u, a1 = cl < ncell ? start[cl + 1] : 0u;
+        unsigned occ = __ballot_sync(kFull, a1 > a0);
+        if (occ) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(&st->n_occ, (unsigned long long)__popc(occ));
+            base = __shfl_sync(kFull, base, 0);
+            if (a1 > a0) occ_list[base + __popc(occ & ((1u << lane) - 1u))] = (uint32_t)cl;
+        }
+        long long Wc = 0;  // this lane's cell, for the divisions done in parallel below
+        while (occ) {
+            const int b = __ffs(occ) - 1;
+            occ &= occ - 1;
+            const uint32_t s0 = __shfl_sync(kFull, a0, b), s1 = __shfl_sync(kFull, a1, b);
+            long long W = 0;
+            for (uint32_t t = s0 + lane; t < s1; t += 32) W += fix24(p.r[PW][t]);
+            for (int o = 16; o > 0; o >>= 1) W += __shfl_xor_sync(kFull, W, o);
+            if (lane == b) Wc = W;
+        }
+        if (a1 > a0) acc += __double2ll_rn((double)Wc / omega_of(Wc, n_ppc, w_min));
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-    if ((threadIdx.x & 31) == 0 && acc) atomicAdd((unsigned long long*)&st->pred_total, (unsigned long long)acc);
+    if (lane == 0 && acc) atomicAdd((unsigned long long*)&st->pred_total, (unsigned long long)acc);
 }
 
 template <class T> __device__ __forceinline__ double speed2_key(const Soa<T>& p, long long i) {
     const T a = p.r[VX][i], b = p.r[VY][i], c = p.r[VZ][i];
     const T r = (a * a + b * b) + c * c;
-    return (double)r;
+    return to_d(r);
 }
 
 struct MergeScratch {
@@ -427,12 +497,15 @@ template <class T>
 __global__ void __launch_bounds__(256) k_merge_split(Soa<T> p, long long n, const uint32_t* __restrict__ start,
                                                      long long ncell, int n_ppc, double w_min, double scale,
                                                      MergeScratch sc, Keys K, uint32_t step, long long cap,
-                                                     DevState* st) {
+                                                     const uint32_t* __restrict__ cells, DevState* st) {
     __shared__ int m_sh, m2_sh;
     __shared__ long long wsum_sh;
     __shared__ unsigned long long sk[kSortMax], sid[kSortMax];
     __shared__ uint32_t six[kSortMax];
-    for (long long c = blockIdx.x; c < ncell; c += gridDim.x) {
+    // every cell, or only the listed ones (cells the warp kernel left to this one)
+    const long long nc = cells ? (long long)st->n_big : ncell;
+    for (long long ci = blockIdx.x; ci < nc; ci += gridDim.x) {
+        const long long c = cells ? (long long)cells[ci] : ci;
         const uint32_t s0 = start[c], s1 = start[c + 1];
         if (s0 == s1) continue;
         if (threadIdx.x == 0) { m_sh = 0; wsum_sh = 0; }
@@ -597,6 +670,168 @@ __global__ void __launch_bounds__(256) k_merge_split(Soa<T> p, long long n, cons
             }
         }
         __syncthreads();
+    }
+}
+
+// The same merge and split with one warp per cell (eight cells per block at
+// a time, warp barriers only), for cells with at most kWarpSort merge
+// candidates: warps take the occupied cells listed by k_cell_weight one at a
+// time from a shared cursor, gather a cell's candidates
+// with a ballot into its shared arrays, sorts them once by the same bitonic
+// network (warp-synchronous stages), and pairs and draws exactly as above,
+// round after round; the survivors (kept in their sorted order) and the odd
+// one form the next round's list, which the block kernel's sort would leave
+// unchanged.  Cells with more candidates are listed for k_merge_split (their
+// split is left to it too).
+constexpr int kWarpSort = 256;
+constexpr int kWarpPairs = kWarpSort / 2 / 32;
+
+template <class T>
+__global__ void __launch_bounds__(256) k_merge_split_warp(Soa<T> p, long long n, const uint32_t* __restrict__ start,
+                                                          const uint32_t* __restrict__ occ_list, int n_ppc,
+                                                          double w_min, double scale, Keys K, uint32_t step,
+                                                          long long cap, uint32_t* big, DevState* st) {
+    __shared__ unsigned long long wsk[8][kWarpSort], wsid[8][kWarpSort];
+    __shared__ uint32_t wsix[8][kWarpSort];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned long long* sk = wsk[w];
+    unsigned long long* sid = wsid[w];
+    uint32_t* six = wsix[w];
+    const unsigned long long n_occ = st->n_occ;
+    // warps take the occupied cells one at a time from a shared cursor, so
+    // dense cells (long merges) spread over the whole GPU
+    for (;;) {
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(&st->n_occ_fetch, 1ull);
+        it = __shfl_sync(kFull, it, 0);
+        if (it >= n_occ) break;
+        const long long c = (long long)occ_list[it];
+        const uint32_t s0 = start[c], s1 = start[c + 1];
+        long long Wp = 0;
+        for (uint32_t t = s0 + lane; t < s1; t += 32) Wp += fix24(p.r[PW][t]);
+        for (int o = 16; o > 0; o >>= 1) Wp += __shfl_xor_sync(kFull, Wp, o);
+        const double om = omega_of(Wp, n_ppc, w_min) * scale;
+        const double lo = 2.0 * om / 3.0, hi = 1.5 * om;
+        int m = 0;
+        for (uint32_t b = s0; b < s1; b += 32) {
+            const uint32_t t = b + lane;
+            const bool cand = t < s1 && lt_d(p.r[PW][t], lo);
+            const unsigned bal = __ballot_sync(kFull, cand);
+            if (cand) {
+                const int q = m + __popc(bal & lt);
+                if (q < kWarpSort) {
+                    sk[q] = (unsigned long long)__double_as_longlong(speed2_key(p, t));
+                    sid[q] = p.id[t];
+                    six[q] = t;
+                }
+            }
+            m += __popc(bal);
+        }
+        if (m > kWarpSort) {
+            if (lane == 0) big[atomicAdd(&st->n_big, 1ull)] = (uint32_t)c;
+            continue;
+        }
+        __syncwarp();
+        for (uint32_t round = 0; m >= 2; ++round) {
+            if (round == 0) {
+                // the survivors of later rounds stay in (key, id) order: pairs of a
+                // sorted list keep one member each, and the odd last one is the largest
+                int P = 1;
+                while (P < m) P <<= 1;
+                for (int t = m + lane; t < P; t += 32) { sk[t] = ~0ull; sid[t] = ~0ull; six[t] = 0; }
+                __syncwarp();
+                for (int kk = 2; kk <= P; kk <<= 1)
+                    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+                        for (int t = lane; t < P; t += 32) {
+                            const int u = t ^ jj;
+                            if (u > t) {
+                                const bool up = (t & kk) == 0;
+                                const bool gt = sk[t] > sk[u] || (sk[t] == sk[u] && sid[t] > sid[u]);
+                                if (gt == up) {
+                                    const unsigned long long x1 = sk[t], x2 = sid[t];
+                                    const uint32_t x3 = six[t];
+                                    sk[t] = sk[u]; sid[t] = sid[u]; six[t] = six[u];
+                                    sk[u] = x1; sid[u] = x2; six[u] = x3;
+                                }
+                            }
+                        }
+                        __syncwarp();
+                    }
+            }
+            // pair q = lane + 32 j; all pairs are read before any slot is rewritten
+            unsigned long long rk[kWarpPairs], rid[kWarpPairs];
+            uint32_t rix[kWarpPairs];
+            bool rok[kWarpPairs];
+#pragma unroll
+            for (int j = 0; j < kWarpPairs; ++j) {
+                const int q = lane + 32 * j;
+                rok[j] = false;
+                rk[j] = 0; rid[j] = 0; rix[j] = 0;
+                if (q < m / 2) {
+                    const uint32_t ia = six[2 * q], ib = six[2 * q + 1];
+                    const uint64_t da = sid[2 * q], db = sid[2 * q + 1];
+                    const T wa = p.r[PW][ia], wb = p.r[PW][ib];
+                    const uint64_t mid = da < db ? da : db;
+                    const u32x4 o = draw_words(K, mid, step, 0xC0000000u | round);
+                    const double u = unif_d_exact(o.x);
+                    const double dwa = to_d(wa);
+                    const bool keep_a = u * (dwa + to_d(wb)) < dwa;
+                    const uint32_t keep = keep_a ? ia : ib, drop = keep_a ? ib : ia;
+                    const T ws = wa + wb;
+                    p.r[PW][keep] = ws;
+                    p.r[PW][drop] = (T)0;
+                    if (lt_d(ws, lo)) {
+                        rok[j] = true;
+                        rk[j] = keep_a ? sk[2 * q] : sk[2 * q + 1];
+                        rid[j] = keep_a ? da : db;
+                        rix[j] = keep;
+                    }
+                }
+            }
+            const bool odd = (m & 1) != 0;
+            const unsigned long long lk = odd ? sk[m - 1] : 0ull, lid = odd ? sid[m - 1] : 0ull;
+            const uint32_t lix = odd ? six[m - 1] : 0u;
+            __syncwarp();
+            // order-preserving compaction of the survivors, then the odd one
+            int m2 = 0;
+#pragma unroll
+            for (int j = 0; j < kWarpPairs; ++j) {
+                const unsigned bal = __ballot_sync(kFull, rok[j]);
+                if (rok[j]) {
+                    const int t = m2 + __popc(bal & lt);
+                    sk[t] = rk[j]; sid[t] = rid[j]; six[t] = rix[j];
+                }
+                m2 += __popc(bal);
+            }
+            if (odd) {
+                if (lane == 0) { sk[m2] = lk; sid[m2] = lid; six[m2] = lix; }
+                ++m2;
+            }
+            __syncwarp();
+            if (m2 == m) break;
+            m = m2;
+        }
+        // split
+        for (uint32_t t = s0 + lane; t < s1; t += 32) {
+            const T wt = p.r[PW][t];
+            if (!gt_d(wt, hi)) continue;
+            int mm = 0;
+            double wc = (double)wt;
+            while (wc > hi) { wc *= 0.5; ++mm; }
+            const T wn = (T)ldexp((double)wt, -mm);
+            p.r[PW][t] = wn;
+            const unsigned long long copies = (1ull << mm) - 1ull;
+            const unsigned long long base = atomicAdd(&st->n_extra, copies);
+            for (unsigned long long q = 0; q < copies; ++q) {
+                const long long d = n + (long long)(base + q);
+                if (d >= cap) { atomicOr(&st->err, kErrSplitCapacity); break; }
+                for (int f = 0; f < 10; ++f) p.r[f][d] = p.r[f][t];
+                p.r[PW][d] = wn;
+                p.id[d] = derived_id(K, p.id[t], step, 0x40000000u | (uint32_t)(q + 1));
+            }
+        }
+        __syncwarp();
     }
 }
 
@@ -1442,16 +1677,25 @@ template <class T> static int weight_update(pic_ctx* c) {
     DevState h;
     cudaMemsetAsync(&c->st()->pred_total, 0, 8, c->s);
     cudaMemsetAsync(&c->st()->n_extra, 0, 8, c->s);
+    cudaMemsetAsync(&c->st()->n_big, 0, 3 * 8, c->s);  // n_big, n_occ, n_occ_fetch
+    // the occupied cells are listed in the count array (free once the starts are formed)
+    uint32_t* occ_list = (uint32_t*)(c->ws + c->L.cnt);
     k_cell_weight<T><<<grid_n(ncell), 256, 0, c->s>>>(c->soa<T>(c->cur), start, ncell, c->cfg.n_ppc, c->cfg.w_min,
-                                                       c->st());
+                                                       occ_list, c->st());
     rc = read_state(c, &h);
     if (rc) return rc;
     const long long n = c->n_host;
     double scale = 1.0;
     const long long capp = c->cfg.particle_cap;
     if (capp > 0 && h.pred_total > capp * 16777216LL) scale = (double)h.pred_total / ((double)capp * 16777216.0);
-    k_merge_split<T><<<152 * 8, 256, 0, c->s>>>(c->soa<T>(c->cur), n, start, ncell, c->cfg.n_ppc, c->cfg.w_min, scale,
-                                                 c->msc(), c->K, c->step, c->cfg.capacity, c->st());
+    // cells with up to kWarpSort merge candidates take one warp each; the
+    // others are listed (in the key array, free after the sort) for one block each
+    uint32_t* big = (uint32_t*)(c->ws + c->L.key);
+    k_merge_split_warp<T><<<152 * 4, 256, 0, c->s>>>(c->soa<T>(c->cur), n, start, occ_list, c->cfg.n_ppc,
+                                                      c->cfg.w_min, scale, c->K, c->step, c->cfg.capacity, big,
+                                                      c->st());
+    k_merge_split<T><<<152 * 2, 256, 0, c->s>>>(c->soa<T>(c->cur), n, start, ncell, c->cfg.n_ppc, c->cfg.w_min, scale,
+                                                 c->msc(), c->K, c->step, c->cfg.capacity, big, c->st());
     rc = read_state(c, &h);
     if (rc) return rc;
     const long long ntot = n + (long long)h.n_extra;
@@ -1464,7 +1708,7 @@ template <class T> static int weight_update(pic_ctx* c) {
     if (rc) return rc;
     c->n_last_wu = c->n_host;
     c->n_wu++;
-    c->launches += 4;
+    c->launches += 5;
     return check_err(c, h);
 }
 

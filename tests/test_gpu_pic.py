@@ -163,6 +163,39 @@ def test_weight_update_matches_oracle(prec):
         assert np.array_equal(gpu[k], ref[k]), k
 
 
+@pytest.mark.parametrize("prec", [64, 32])
+def test_weight_update_crowded_cells_match_oracle(prec):
+    """Cells with more merge candidates than one warp sorts (600: the block's
+    shared-memory sort; 2500: its global-memory ranking) beside ordinary
+    ones: the same merged and split set as the oracle, bit for bit."""
+    grid = W.grid_spec(4, 4, 4, 1e-4)
+    p0 = W.random_particles(3000, grid, 43, w_range=(1.0, 3.0))
+    rng = np.random.default_rng(11)
+    for n_c, cell, seed in ((600, (1, 2, 1), 5), (2500, (3, 0, 2), 6)):
+        q = W.random_particles(n_c, grid, seed, w_range=(1.0, 1.0))
+        u = np.random.default_rng(seed).uniform(0.05, 0.95, (3, n_c))
+        for d, k in enumerate(("x", "y", "z")):
+            q[k] = ((cell[d] + u[d]) * 1e-4).astype(np.float32).astype(np.float64)
+        q["id"] = q["id"] + (1 << 40) * seed
+        for k in p0:
+            p0[k] = np.concatenate([p0[k], q[k]])
+    p0["w"][:40] = rng.uniform(100, 900, 40).astype(np.float32).astype(np.float64)
+    gas = W.synthetic_air()
+    ctx = _ctx(gas, grid, prec, capacity=60000, seed=SEED, n_ppc=10, w_min=1.0, particle_cap=0)
+    ctx.set_particles(p0)
+    ctx.weight_update()
+    gpu = by_id(ctx.get_particles())
+    m = O.Model(gas, 1e-12, SEED, prec, grid)
+    P = O.Particles(60000, p0)
+    rc, ms = O.merge_split(m, P, 0, n_ppc=10, w_min=1.0, cap=0)
+    assert rc == 0
+    ref = by_id(P.view())
+    assert len(ref["id"]) < len(p0["id"])  # the crowded cells were merged
+    assert np.array_equal(gpu["id"], ref["id"])
+    for k in ("x", "y", "z", "vx", "vy", "vz", "w"):
+        assert np.array_equal(gpu[k], ref[k]), k
+
+
 def test_checkpoint_resume_is_bit_identical():
     gas, F, mk, p0 = _setup(5000, 32, 4)
     Fd = _field_dev(F)
