@@ -483,8 +483,8 @@ struct MergeScratch {
     uint32_t* sidx;
 };
 
-constexpr int kSortMax = 2048;                  // candidates sorted in shared memory (else in global)
-constexpr int kPairsPerThread = kSortMax / 2 / 256;
+constexpr int kSortMax = 8192;  // candidates sorted in (dynamic) shared memory (else ranked in global memory)
+constexpr size_t kMergeSmem = (size_t)kSortMax * (8 + 8 + 4);
 
 // One block per occupied cell.  Merge: candidates w < (2/3) omega ordered by
 // (|v|^2, id) are paired (0,1), (2,3), ...; the pair's weights are summed and
@@ -492,7 +492,10 @@ constexpr int kPairsPerThread = kSortMax / 2 / 256;
 // (draw keyed by the smaller id, the step and the round); rounds repeat while
 // two or more candidates remain.  Split: w > (3/2) omega is halved m times
 // (m minimal with w / 2^m <= (3/2) omega) and 2^m - 1 identical copies are
-// appended after the n sorted particles.
+// appended after the n sorted particles.  In shared memory the candidates are
+// sorted once: the survivors of a round (one member of each pair of a sorted
+// list, then the odd last one) are written back in their order, which is the
+// order a new sort would give.
 template <class T>
 __global__ void __launch_bounds__(256) k_merge_split(Soa<T> p, long long n, const uint32_t* __restrict__ start,
                                                      long long ncell, int n_ppc, double w_min, double scale,
@@ -500,8 +503,12 @@ __global__ void __launch_bounds__(256) k_merge_split(Soa<T> p, long long n, cons
                                                      const uint32_t* __restrict__ cells, DevState* st) {
     __shared__ int m_sh, m2_sh;
     __shared__ long long wsum_sh;
-    __shared__ unsigned long long sk[kSortMax], sid[kSortMax];
-    __shared__ uint32_t six[kSortMax];
+    __shared__ int wtot[8];
+    extern __shared__ __align__(16) unsigned char merge_raw[];
+    unsigned long long* sk = reinterpret_cast<unsigned long long*>(merge_raw);
+    unsigned long long* sid = sk + kSortMax;
+    uint32_t* six = reinterpret_cast<uint32_t*>(sid + kSortMax);
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
     // every cell, or only the listed ones (cells the warp kernel left to this one)
     const long long nc = cells ? (long long)st->n_big : ncell;
     for (long long ci = blockIdx.x; ci < nc; ci += gridDim.x) {
@@ -511,7 +518,7 @@ __global__ void __launch_bounds__(256) k_merge_split(Soa<T> p, long long n, cons
         if (threadIdx.x == 0) { m_sh = 0; wsum_sh = 0; }
         __syncthreads();
         long long Wp = 0;
-        for (uint32_t t = s0 + threadIdx.x; t < s1; t += blockDim.x) Wp += __double2ll_rn((double)p.r[PW][t] * kS24);
+        for (uint32_t t = s0 + threadIdx.x; t < s1; t += blockDim.x) Wp += fix24(p.r[PW][t]);
         for (int o = 16; o > 0; o >>= 1) Wp += __shfl_xor_sync(kFull, Wp, o);
         if ((threadIdx.x & 31) == 0) atomicAdd((unsigned long long*)&wsum_sh, (unsigned long long)Wp);
         __syncthreads();
@@ -519,7 +526,7 @@ __global__ void __launch_bounds__(256) k_merge_split(Soa<T> p, long long n, cons
         const double lo = 2.0 * om / 3.0, hi = 1.5 * om;
         // candidates
         for (uint32_t t = s0 + threadIdx.x; t < s1; t += blockDim.x) {
-            if ((double)p.r[PW][t] < lo) {
+            if (lt_d(p.r[PW][t], lo)) {
                 const int q = atomicAdd(&m_sh, 1);
                 sc.key[s0 + q] = speed2_key(p, t);
                 sc.id[s0 + q] = p.id[t];
@@ -535,8 +542,7 @@ __global__ void __launch_bounds__(256) k_merge_split(Soa<T> p, long long n, cons
                 sid[t] = sc.id[s0 + t];
                 six[t] = sc.idx[s0 + t];
             }
-            __syncthreads();
-            for (uint32_t round = 0; m >= 2; ++round) {
+            {
                 int P = 1;
                 while (P < m) P <<= 1;
                 for (int t = m + threadIdx.x; t < P; t += blockDim.x) { sk[t] = ~0ull; sid[t] = ~0ull; six[t] = 0; }
@@ -558,45 +564,58 @@ __global__ void __launch_bounds__(256) k_merge_split(Soa<T> p, long long n, cons
                         }
                         __syncthreads();
                     }
-                // pair (0,1), (2,3), ...; results held in registers until all pairs are read
-                unsigned long long rk[kPairsPerThread], rid[kPairsPerThread];
-                uint32_t rix[kPairsPerThread];
-                int nres = 0;
-                for (int q = threadIdx.x; q < m / 2; q += blockDim.x) {
-                    const uint32_t ia = six[2 * q], ib = six[2 * q + 1];
-                    const uint64_t da = sid[2 * q], db = sid[2 * q + 1];
-                    const T wa = p.r[PW][ia], wb = p.r[PW][ib];
-                    const uint64_t mid = da < db ? da : db;
-                    const u32x4 o = draw_words(K, mid, step, 0xC0000000u | round);
-                    const double u = unif<double>(o.x);
-                    const bool keep_a = u * ((double)wa + (double)wb) < (double)wa;
-                    const uint32_t keep = keep_a ? ia : ib, drop = keep_a ? ib : ia;
-                    const T ws = wa + wb;
-                    p.r[PW][keep] = ws;
-                    p.r[PW][drop] = (T)0;
-                    if ((double)ws < lo) {
-                        rk[nres] = keep_a ? sk[2 * q] : sk[2 * q + 1];
-                        rid[nres] = keep_a ? da : db;
-                        rix[nres] = keep;
-                        ++nres;
-                    }
-                }
-                unsigned long long lk = 0, lid = 0;
-                uint32_t lix = 0;
+            }
+            for (uint32_t round = 0; m >= 2; ++round) {
                 const bool odd = (m & 1) != 0;
-                if (odd && threadIdx.x == 0) { lk = sk[m - 1]; lid = sid[m - 1]; lix = six[m - 1]; }
-                if (threadIdx.x == 0) m2_sh = 0;
-                __syncthreads();
-                for (int r = 0; r < nres; ++r) {
-                    const int t = atomicAdd(&m2_sh, 1);
-                    sk[t] = rk[r]; sid[t] = rid[r]; six[t] = rix[r];
+                const unsigned long long lk = odd ? sk[m - 1] : 0ull, lid = odd ? sid[m - 1] : 0ull;
+                const uint32_t lix = odd ? six[m - 1] : 0u;
+                int m2 = 0;
+                // pairs in chunks of 256 (one per thread): all of a chunk's pairs are
+                // read before its survivors are written, in pair order, below them
+                for (int q0 = 0; q0 < m / 2; q0 += 256) {
+                    const int q = q0 + threadIdx.x;
+                    bool ok = false;
+                    unsigned long long rk = 0, rid = 0;
+                    uint32_t rix = 0;
+                    if (q < m / 2) {
+                        const uint32_t ia = six[2 * q], ib = six[2 * q + 1];
+                        const uint64_t da = sid[2 * q], db = sid[2 * q + 1];
+                        const T wa = p.r[PW][ia], wb = p.r[PW][ib];
+                        const uint64_t mid = da < db ? da : db;
+                        const u32x4 o = draw_words(K, mid, step, 0xC0000000u | round);
+                        const double u = unif_d_exact(o.x);
+                        const double dwa = to_d(wa);
+                        const bool keep_a = u * (dwa + to_d(wb)) < dwa;
+                        const uint32_t keep = keep_a ? ia : ib, drop = keep_a ? ib : ia;
+                        const T ws = wa + wb;
+                        p.r[PW][keep] = ws;
+                        p.r[PW][drop] = (T)0;
+                        if (lt_d(ws, lo)) {
+                            ok = true;
+                            rk = keep_a ? sk[2 * q] : sk[2 * q + 1];
+                            rid = keep_a ? da : db;
+                            rix = keep;
+                        }
+                    }
+                    const unsigned bal = __ballot_sync(kFull, ok);
+                    if (lane == 0) wtot[wq] = __popc(bal);
+                    __syncthreads();
+                    int off = m2, tot = 0;
+                    for (int x = 0; x < 8; ++x) {
+                        if (x < wq) off += wtot[x];
+                        tot += wtot[x];
+                    }
+                    if (ok) {
+                        const int t = off + __popc(bal & ((1u << lane) - 1u));
+                        sk[t] = rk; sid[t] = rid; six[t] = rix;
+                    }
+                    m2 += tot;
+                    __syncthreads();
                 }
-                if (odd && threadIdx.x == 0) {
-                    const int t = atomicAdd(&m2_sh, 1);
-                    sk[t] = lk; sid[t] = lid; six[t] = lix;
+                if (odd) {
+                    if (threadIdx.x == 0) { sk[m2] = lk; sid[m2] = lid; six[m2] = lix; }
+                    ++m2;
                 }
-                __syncthreads();
-                const int m2 = m2_sh;
                 __syncthreads();
                 if (m2 == m) break;
                 m = m2;
@@ -1694,8 +1713,10 @@ template <class T> static int weight_update(pic_ctx* c) {
     k_merge_split_warp<T><<<152 * 4, 256, 0, c->s>>>(c->soa<T>(c->cur), n, start, occ_list, c->cfg.n_ppc,
                                                       c->cfg.w_min, scale, c->K, c->step, c->cfg.capacity, big,
                                                       c->st());
-    k_merge_split<T><<<152 * 2, 256, 0, c->s>>>(c->soa<T>(c->cur), n, start, ncell, c->cfg.n_ppc, c->cfg.w_min, scale,
-                                                 c->msc(), c->K, c->step, c->cfg.capacity, big, c->st());
+    cudaFuncSetAttribute(k_merge_split<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMergeSmem);
+    k_merge_split<T><<<152 * 2, 256, kMergeSmem, c->s>>>(c->soa<T>(c->cur), n, start, ncell, c->cfg.n_ppc,
+                                                          c->cfg.w_min, scale, c->msc(), c->K, c->step,
+                                                          c->cfg.capacity, big, c->st());
     rc = read_state(c, &h);
     if (rc) return rc;
     const long long ntot = n + (long long)h.n_extra;

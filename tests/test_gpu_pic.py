@@ -165,13 +165,13 @@ def test_weight_update_matches_oracle(prec):
 
 @pytest.mark.parametrize("prec", [64, 32])
 def test_weight_update_crowded_cells_match_oracle(prec):
-    """Cells with more merge candidates than one warp sorts (600: the block's
-    shared-memory sort; 2500: its global-memory ranking) beside ordinary
-    ones: the same merged and split set as the oracle, bit for bit."""
+    """Cells with more merge candidates than one warp sorts (600 and 2500: the
+    block's shared-memory sort; 9000: its global-memory ranking) beside
+    ordinary ones: the same merged and split set as the oracle, bit for bit."""
     grid = W.grid_spec(4, 4, 4, 1e-4)
     p0 = W.random_particles(3000, grid, 43, w_range=(1.0, 3.0))
     rng = np.random.default_rng(11)
-    for n_c, cell, seed in ((600, (1, 2, 1), 5), (2500, (3, 0, 2), 6)):
+    for n_c, cell, seed in ((600, (1, 2, 1), 5), (2500, (3, 0, 2), 6), (9000, (0, 3, 3), 7)):
         q = W.random_particles(n_c, grid, seed, w_range=(1.0, 1.0))
         u = np.random.default_rng(seed).uniform(0.05, 0.95, (3, n_c))
         for d, k in enumerate(("x", "y", "z")):
