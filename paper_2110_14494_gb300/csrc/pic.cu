@@ -1245,6 +1245,7 @@ extern "C" int pic_init(const pic_config* cfg, void* d_ws, size_t ws_bytes, cons
         } else {
             c->mg.carve(c->ws + L.mg, cfg->nx, cfg->ny, cfg->nz, c->prec == 32, false);
             c->mg.persistent = true;
+            c->mg.min_cycles = 2;
         }
     }
     *out = c;

@@ -914,6 +914,12 @@ float2 pair_of(double v) {
 // One flexible-CG iteration on the float32 correction (it: index within the
 // current refinement pass; the direction vectors alternate between p32[0]
 // and p32[1] so the new direction can be formed while the old one is read).
+int MG::mixed_min_cycles(int max_cycles) const {
+    int m = min_cycles < 2 ? min_cycles : 2;
+    if (m < 0) m = 0;
+    return m < max_cycles ? m : max_cycles;
+}
+
 void MG::iteration_mixed(cudaStream_t s, int it) {
     const int nx = lx[0], ny = ly[0], nz = lz[0], n = nx * ny * nz;
     const int cur = it & 1, first = it == 0 ? 1 : 0;
@@ -965,15 +971,20 @@ int MG::solve_mixed(const void* rho, bool rho64, const uint8_t* mask, float* phi
     resid();
     int cyc = 0, it = 0, rc = PIC_OK;
     double bn = 1.0, rn = 0.0, r_pass = 0.0;
+    const int min_c = mixed_min_cycles(max_cycles);
     for (;;) {
-        if (cudaMemcpyAsync(host_norms, norms, 2 * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return PIC_ERR_CUDA;
-        if (cudaStreamSynchronize(s) != cudaSuccess) return PIC_ERR_CUDA;
-        bn = host_norms[S_B2] > 0.0 ? sqrt(host_norms[S_B2]) : 1.0;
-        rn = sqrt(host_norms[S_R2]);
+        // the first min_c iterations run without a test between them (no read-back)
+        if (cyc == 0 || cyc >= min_c) {
+            if (cudaMemcpyAsync(host_norms, norms, 2 * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+                return PIC_ERR_CUDA;
+            if (cudaStreamSynchronize(s) != cudaSuccess) return PIC_ERR_CUDA;
+            bn = host_norms[S_B2] > 0.0 ? sqrt(host_norms[S_B2]) : 1.0;
+            rn = sqrt(host_norms[S_R2]);
+        }
         if (it == 0) r_pass = rn;
-        if (rn / bn <= rtol) break;
+        if (cyc >= min_c && rn / bn <= rtol) break;
         if (cyc >= max_cycles) { rc = PIC_ERR_TIMEOUT; break; }
-        if (it > 0 && rn <= kRefineDrop * r_pass) {
+        if (cyc >= min_c && it > 0 && rn <= kRefineDrop * r_pass) {
             // iterative refinement: fold the correction into phi, re-form r
             k_mx_commit<<<gf, kFlatBlock, 0, s>>>(phi_hi, phi_lo, d32, n);
             ++launches;
@@ -1058,6 +1069,12 @@ int MG::capture_solve_mixed(cudaStream_t cs, const float* rho, float* phi_hi, fl
     cudaMemsetAsync(ctr, 0, 8 * sizeof(unsigned), cs);
     cudaMemsetAsync(loop, 0, sizeof(MxLoop), cs);
     resid(cs);
+    // the first iterations (index 0, then 1) without tests, as in the host loop
+    const int min_c = mixed_min_cycles(max_cycles);
+    if (min_c > 0) {
+        k_mx_prime<<<1, 1, 0, cs>>>(norms, loop, min_c);
+        for (int q = 0; q < min_c; ++q) iteration_mixed(cs, q);
+    }
     cudaGraph_t body = nullptr;
     if (add_conditional(cs, h_loop, cudaGraphCondTypeWhile, 1, &body) != cudaSuccess) return PIC_ERR_CUDA;
     if (cudaGraphConditionalHandleCreate(&h_branch, body, 4u, cudaGraphCondAssignDefault) != cudaSuccess)
@@ -1093,7 +1110,7 @@ int MG::capture_solve_mixed(cudaStream_t cs, const float* rho, float* phi_hi, fl
                                    nullptr, E4, loop);
     k_mx_report<<<1, 1, 0, cs>>>(loop, cycles_dst, rel_dst, err_dst, err_bit, kernels_dst,
                                  make_int4(kb[0], kb[1], kb[2], kb[3]));
-    if (fixed_kernels) *fixed_kernels = 3;  // residual, gradient, report
+    if (fixed_kernels) *fixed_kernels = 3 + (min_c > 0 ? 1 : 0);  // residual, gradient, report, prime
     return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ERR_CUDA;
 }
 

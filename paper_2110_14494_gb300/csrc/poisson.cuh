@@ -26,6 +26,12 @@ struct MG {
     double *r64 = nullptr, *p64 = nullptr, *q64 = nullptr;  // CG vectors (float64)
     int pre = 2, post = 2, coarse_sweeps = 8;
     float omega = 1.0f;          // over-relaxation of the pre- and post-smoothing sweeps (1: Gauss-Seidel)
+    // mixed solve: CG iterations run before the first convergence or
+    // refinement test (0 to 2; at most max_cycles).  A coupled PIC context
+    // takes 2 (its warm-started solves nearly always need two), so that the
+    // graph runs them without a loop trip; stateless solves take 0.
+    int min_cycles = 0;
+    int mixed_min_cycles(int max_cycles) const;
     int mask_min_children = 1;   // a coarse cell is an electrode cell if this many of its children are
     long long launches = 0;  // kernels launched so far
     // Reusable state for a solver owned by a long-lived caller (a PIC context):

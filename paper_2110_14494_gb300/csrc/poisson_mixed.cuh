@@ -627,6 +627,17 @@ __global__ void k_mx_decide(const double* __restrict__ sc, MxLoop* L, double rto
     if (stop) cudaGraphSetConditional(h_loop, 0u);
 }
 
+// State after the first min_c iterations, which the graph runs back to back
+// (as the host loop does: no test between them): the residual norm of the
+// pass start, and the counters of the loop.
+__global__ void k_mx_prime(const double* __restrict__ sc, MxLoop* L, int min_c) {
+    L->r_pass = sqrt(sc[S_R2]);
+    L->it = min_c;
+    L->cyc = min_c;
+    L->n_branch[0] = min_c > 0 ? 1 : 0;
+    L->n_branch[2] = min_c > 1 ? 1 : 0;
+}
+
 // Results of a device-driven solve: cycles, relative residual, the
 // cycle-limit flag, and the kernels its loop ran (kb: per branch).
 __global__ void k_mx_report(const MxLoop* __restrict__ L, int* cycles, double* rel, unsigned* err, unsigned bit,
