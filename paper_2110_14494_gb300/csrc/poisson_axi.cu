@@ -370,13 +370,18 @@ int AxiMG::solve(const double* rho, const uint8_t* mask, double* phi, double h, 
     int cyc = 0, rc = PIC_OK;
     double bn = 1.0, rn = 0.0;
     const int nb = (n + 255) / 256;
+    const int min_c = min_cycles_for(max_cycles);
     for (;;) {
-        if (cudaMemcpyAsync(host_norms, norms, 2 * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) return PIC_ERR_CUDA;
-        if (cudaStreamSynchronize(s) != cudaSuccess) return PIC_ERR_CUDA;
-        bn = host_norms[A_B2] > 0.0 ? sqrt(host_norms[A_B2]) : 1.0;
-        rn = sqrt(host_norms[A_R2]);
-        if (rn / bn <= rtol) break;
-        if (cyc >= max_cycles) { rc = PIC_ERR_TIMEOUT; break; }
+        // the first min_c iterations run without a test between them (no read-back)
+        if (cyc >= min_c) {
+            if (cudaMemcpyAsync(host_norms, norms, 2 * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+                return PIC_ERR_CUDA;
+            if (cudaStreamSynchronize(s) != cudaSuccess) return PIC_ERR_CUDA;
+            bn = host_norms[A_B2] > 0.0 ? sqrt(host_norms[A_B2]) : 1.0;
+            rn = sqrt(host_norms[A_R2]);
+            if (rn / bn <= rtol) break;
+            if (cyc >= max_cycles) { rc = PIC_ERR_TIMEOUT; break; }
+        }
         const int first = cyc == 0 ? 1 : 0;
         vcycle(s);
         k_axi_dot2<<<nb, dim3(256, 1, 1), 0, s>>>(e[0], r, q, n, norms, first ? 0 : 1);
@@ -435,6 +440,19 @@ __global__ void k_axi_report(const AxiLoop* __restrict__ L, int* cycles, double*
                 (unsigned long long)L->n_branch[1] * kb1;
 }
 
+int AxiMG::min_cycles_for(int max_cycles) const {
+    int m = min_cycles < 2 ? min_cycles : 2;
+    if (m < 0) m = 0;
+    return m < max_cycles ? m : max_cycles;
+}
+
+// Counters after the first min_c iterations, run back to back as in the host loop.
+__global__ void k_axi_prime(AxiLoop* L, int min_c) {
+    L->cyc = min_c;
+    L->n_branch[0] = min_c > 0 ? 1 : 0;
+    L->n_branch[1] = min_c > 1 ? min_c - 1 : 0;
+}
+
 int AxiMG::prepare_capture() {
     for (int q = 0; q < 2; ++q)
         if (!cap_body[q] && cudaStreamCreateWithFlags(&cap_body[q], cudaStreamNonBlocking) != cudaSuccess)
@@ -463,6 +481,22 @@ int AxiMG::capture_solve(cudaStream_t cs, const double* rho, double* phi, double
     cudaMemsetAsync(norms, 0, A_N * 8, cs);
     cudaMemsetAsync(loop, 0, sizeof(AxiLoop), cs);
     k_axi_resid<<<agrid(nr, nz), kABlk, 0, cs>>>(phi, rho, m[0], nr, nz, h2e, v_lo, v_hi, v_mask, r, g[0], norms);
+    auto iteration = [&](cudaStream_t q, int first) {
+        vcycle(q);
+        k_axi_dot2<<<nb, dim3(256, 1, 1), 0, q>>>(e[0], r, this->q, n, norms, first ? 0 : 1);
+        k_axi_beta<<<1, 1, 0, q>>>(norms, first);
+        k_axi_update_p<<<nb, 256, 0, q>>>(p, e[0], n, norms);
+        k_axi_apply<<<agrid(nr, nz), kABlk, 0, q>>>(p, m[0], nr, nz, this->q, norms);
+        k_axi_alpha<<<1, 1, 0, q>>>(norms);
+        k_axi_update_xr<<<nb, dim3(256, 1, 1), 0, q>>>(phi, r, p, this->q, g[0], n, norms);
+        launches += 6;
+    };
+    // the first iterations without tests, as in the host loop
+    const int min_c = min_cycles_for(max_cycles);
+    if (min_c > 0) {
+        k_axi_prime<<<1, 1, 0, cs>>>(loop, min_c);
+        for (int it = 0; it < min_c; ++it) iteration(cs, it == 0 ? 1 : 0);
+    }
     cudaGraph_t body = nullptr;
     if (add_conditional(cs, h_loop, cudaGraphCondTypeWhile, 1, &body) != cudaSuccess) return PIC_ERR_CUDA;
     if (cudaGraphConditionalHandleCreate(&h_branch, body, 2u, cudaGraphCondAssignDefault) != cudaSuccess)
@@ -479,21 +513,12 @@ int AxiMG::capture_solve(cudaStream_t cs, const double* rho, double* phi, double
         if (cudaStreamBeginCaptureToGraph(cap_body[1], br[b], nullptr, nullptr, 0,
                                           cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             return PIC_ERR_CUDA;
-        const int first = b == 0 ? 1 : 0;
         const long long l0 = launches;
-        cudaStream_t q = cap_body[1];
-        vcycle(q);
-        k_axi_dot2<<<nb, dim3(256, 1, 1), 0, q>>>(e[0], r, this->q, n, norms, first ? 0 : 1);
-        k_axi_beta<<<1, 1, 0, q>>>(norms, first);
-        k_axi_update_p<<<nb, 256, 0, q>>>(p, e[0], n, norms);
-        k_axi_apply<<<agrid(nr, nz), kABlk, 0, q>>>(p, m[0], nr, nz, this->q, norms);
-        k_axi_alpha<<<1, 1, 0, q>>>(norms);
-        k_axi_update_xr<<<nb, dim3(256, 1, 1), 0, q>>>(phi, r, p, this->q, g[0], n, norms);
-        launches += 6;
+        iteration(cap_body[1], b == 0 ? 1 : 0);
         kb[b] = (int)(launches - l0);
-        if (end_body_capture(q) != cudaSuccess) return PIC_ERR_CUDA;
+        if (end_body_capture(cap_body[1]) != cudaSuccess) return PIC_ERR_CUDA;
     }
-    long long fixed = 2;  // residual, report
+    long long fixed = 2 + (min_c > 0 ? 1 : 0);  // residual, report, prime
     if (E4) {
         if (packed_prec == 64)
             k_axi_grad<double><<<agrid(nr, nz), kABlk, 0, cs>>>(phi, nr, nz, h, v_lo, v_hi, nullptr, nullptr,

@@ -24,6 +24,12 @@ struct AxiMG {
     long long launches = 0;
     bool persistent = false, masks_ready = false;
     AxiLoop* loop = nullptr;
+    // CG iterations run before the first convergence test (0 to 2, at most
+    // max_cycles).  0 for every caller: the coupled axisymmetric solves often
+    // converge in fewer than two, where a forced pair costs more than the
+    // loop trips it saves.
+    int min_cycles = 0;
+    int min_cycles_for(int max_cycles) const;
     cudaStream_t cap_body[2] = {nullptr, nullptr};
     // Streams for recording loop bodies (call before the caller's capture).
     int prepare_capture();
