@@ -284,12 +284,16 @@ __global__ void k_step_stats(const Soa<T> p, const DevState* stc, const unsigned
     const long long n = (long long)stc->n_out;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        if (!(p.r[PW][i] > (T)0)) continue;
-        const float vx = (float)p.r[VX][i], vy = (float)p.r[VY][i], vz = (float)p.r[VZ][i];
-        const float v2 = vx * vx + vy * vy + vz * vz;
-        int b = v2 > 0.0f ? (int)floorf((0.5f * log2f(v2) - 10.0f) * kVBinsPerOctave) : 0;
-        b = b < 0 ? 0 : (b >= kVBins ? kVBins - 1 : b);
-        atomicAdd(&h[b], 1u);
+        int b = -1;
+        if (p.r[PW][i] > (T)0) {
+            const float vx = (float)p.r[VX][i], vy = (float)p.r[VY][i], vz = (float)p.r[VZ][i];
+            const float v2 = vx * vx + vy * vy + vz * vz;
+            b = v2 > 0.0f ? (int)floorf((0.5f * log2f(v2) - 10.0f) * kVBinsPerOctave) : 0;
+            b = b < 0 ? 0 : (b >= kVBins ? kVBins - 1 : b);
+        }
+        // lanes with the same bin add once (most electrons share a few bins)
+        const unsigned grp = __match_any_sync(__activemask(), b);
+        if (b >= 0 && __ffs(grp) - 1 == (int)(threadIdx.x & 31)) atomicAdd(&h[b], (unsigned)__popc(grp));
     }
     long long mx = LLONG_MIN, sm = 0;
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += stride) {
