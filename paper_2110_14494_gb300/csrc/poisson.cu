@@ -820,7 +820,7 @@ void MG::iteration(cudaStream_t s, double* phi, const uint8_t* mk, bool first) {
 void MG::release() {
     for (int q = 0; q < 2; ++q)
         if (g_iter[q]) { cudaGraphExecDestroy(g_iter[q]); g_iter[q] = nullptr; }
-    for (int q = 0; q < 2; ++q)
+    for (int q = 0; q < 3; ++q)
         if (cap_body[q]) { cudaStreamDestroy(cap_body[q]); cap_body[q] = nullptr; }
     for (int q = 0; q < 3; ++q)
         if (g_mx[q]) { cudaGraphExecDestroy(g_mx[q]); g_mx[q] = nullptr; }
@@ -1042,7 +1042,7 @@ int MG::solve_mixed(const void* rho, bool rho64, const uint8_t* mask, float* phi
 // ------------------------------------------------------------------ device-driven solve
 
 int MG::prepare_capture() {
-    for (int q = 0; q < 2; ++q)
+    for (int q = 0; q < 3; ++q)
         if (!cap_body[q] && cudaStreamCreateWithFlags(&cap_body[q], cudaStreamNonBlocking) != cudaSuccess)
             return PIC_ERR_CUDA;
     return PIC_OK;
@@ -1056,12 +1056,10 @@ int MG::capture_solve_mixed(cudaStream_t cs, const float* rho, float* phi_hi, fl
     const int nx = lx[0], ny = ly[0], nz = lz[0], n = nx * ny * nz;
     const MxBoundary bc{pair_of(v_lo), pair_of(v_hi), pair_of(v_mask)};
     const dim3 g3 = grid_mx3(nx, ny, nz), gf = grid_mxf(n);
-    if (!cap_body[0] || !cap_body[1]) return PIC_ERR_STATE;
+    if (!cap_body[0] || !cap_body[1] || !cap_body[2]) return PIC_ERR_STATE;
     cudaGraph_t top = capturing_graph(cs);
     if (!top) return PIC_ERR_CUDA;
     cudaGraphConditionalHandle h_loop, h_branch;
-    if (cudaGraphConditionalHandleCreate(&h_loop, top, 1u, cudaGraphCondAssignDefault) != cudaSuccess)
-        return PIC_ERR_CUDA;
     auto resid = [&](cudaStream_t q) {
         k_mx_resid<float><<<g3, kBlk, 0, q>>>(rho, 1.0, m[0], phi_hi, phi_lo, nx, ny, nz, bc, g[0], part, ctr, norms);
         ++launches;
@@ -1071,12 +1069,30 @@ int MG::capture_solve_mixed(cudaStream_t cs, const float* rho, float* phi_hi, fl
     resid(cs);
     // the first iterations (index 0, then 1) without tests, as in the host loop
     const int min_c = mixed_min_cycles(max_cycles);
+    cudaGraph_t body = nullptr;
     if (min_c > 0) {
         k_mx_prime<<<1, 1, 0, cs>>>(norms, loop, min_c);
         for (int q = 0; q < min_c; ++q) iteration_mixed(cs, q);
+        // the loop only when those did not reach the tolerance (an if node
+        // is cheaper than a loop trip that only decides to stop)
+        cudaGraphConditionalHandle h_more;
+        if (cudaGraphConditionalHandleCreate(&h_more, top, 0u, cudaGraphCondAssignDefault) != cudaSuccess)
+            return PIC_ERR_CUDA;
+        k_mx_check<<<1, 1, 0, cs>>>(norms, loop, rtol, max_cycles, h_more);
+        cudaGraph_t ifb = nullptr;
+        if (add_conditional(cs, h_more, cudaGraphCondTypeIf, 1, &ifb) != cudaSuccess) return PIC_ERR_CUDA;
+        if (cudaGraphConditionalHandleCreate(&h_loop, ifb, 1u, cudaGraphCondAssignDefault) != cudaSuccess)
+            return PIC_ERR_CUDA;
+        if (cudaStreamBeginCaptureToGraph(cap_body[2], ifb, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+            cudaSuccess)
+            return PIC_ERR_CUDA;
+        const cudaError_t e_w = add_conditional(cap_body[2], h_loop, cudaGraphCondTypeWhile, 1, &body);
+        if (end_body_capture(cap_body[2]) != cudaSuccess || e_w != cudaSuccess) return PIC_ERR_CUDA;
+    } else {
+        if (cudaGraphConditionalHandleCreate(&h_loop, top, 1u, cudaGraphCondAssignDefault) != cudaSuccess)
+            return PIC_ERR_CUDA;
+        if (add_conditional(cs, h_loop, cudaGraphCondTypeWhile, 1, &body) != cudaSuccess) return PIC_ERR_CUDA;
     }
-    cudaGraph_t body = nullptr;
-    if (add_conditional(cs, h_loop, cudaGraphCondTypeWhile, 1, &body) != cudaSuccess) return PIC_ERR_CUDA;
     if (cudaGraphConditionalHandleCreate(&h_branch, body, 4u, cudaGraphCondAssignDefault) != cudaSuccess)
         return PIC_ERR_CUDA;
     // loop body: the decision, then the switch over the branches
@@ -1110,7 +1126,7 @@ int MG::capture_solve_mixed(cudaStream_t cs, const float* rho, float* phi_hi, fl
                                    nullptr, E4, loop);
     k_mx_report<<<1, 1, 0, cs>>>(loop, cycles_dst, rel_dst, err_dst, err_bit, kernels_dst,
                                  make_int4(kb[0], kb[1], kb[2], kb[3]));
-    if (fixed_kernels) *fixed_kernels = 3 + (min_c > 0 ? 1 : 0);  // residual, gradient, report, prime
+    if (fixed_kernels) *fixed_kernels = 3 + (min_c > 0 ? 2 : 0);  // residual, gradient, report, prime, check
     return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ERR_CUDA;
 }
 

@@ -41,7 +41,7 @@ struct MG {
     bool persistent = false;
     bool masks_ready = false;
     cudaStream_t cap_stream = nullptr;
-    cudaStream_t cap_body[2] = {nullptr, nullptr};  // captures into conditional-node bodies
+    cudaStream_t cap_body[3] = {nullptr, nullptr, nullptr};  // captures into conditional-node bodies
     cudaGraphExec_t g_iter[2] = {nullptr, nullptr};  // [0] first iteration, [1] later ones
     const void* g_key[3] = {nullptr, nullptr, nullptr};
     long long graph_kernels[2] = {0, 0};

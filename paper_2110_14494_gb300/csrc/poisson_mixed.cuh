@@ -638,6 +638,23 @@ __global__ void k_mx_prime(const double* __restrict__ sc, MxLoop* L, int min_c) 
     L->n_branch[2] = min_c > 1 ? 1 : 0;
 }
 
+// After the untested first iterations: whether the loop must run at all
+// (the stop tests of k_mx_decide; its own first trip repeats them).
+__global__ void k_mx_check(const double* __restrict__ sc, MxLoop* L, double rtol, int max_cycles,
+                           cudaGraphConditionalHandle h_more) {
+    const double bn = sc[S_B2] > 0.0 ? sqrt(sc[S_B2]) : 1.0;
+    const double rn = sqrt(sc[S_R2]);
+    L->rel = rn / bn;
+    bool more = true;
+    if (rn / bn <= rtol) {
+        more = false;
+    } else if (L->cyc >= max_cycles) {
+        more = false;
+        L->timeout = 1;
+    }
+    cudaGraphSetConditional(h_more, more ? 1u : 0u);
+}
+
 // Results of a device-driven solve: cycles, relative residual, the
 // cycle-limit flag, and the kernels its loop ran (kb: per branch).
 __global__ void k_mx_report(const MxLoop* __restrict__ L, int* cycles, double* rel, unsigned* err, unsigned bit,
