@@ -27,6 +27,28 @@ namespace {
 
 constexpr int BX = 32, BY = 4;
 
+// Kernels of the V-cycle and of the CG iteration are launched with
+// programmatic dependent launch: their blocks may be scheduled while the
+// previous kernel's last blocks still run, and each waits here for that grid
+// (and its memory) before its first access.  Without the launch attribute
+// the wait returns at once.
+__device__ __forceinline__ void pdl_wait() { cudaGridDependencySynchronize(); }
+
+template <class... P, class... A>
+void launch_pdl(void (*k)(P...), dim3 g, dim3 b, size_t smem, cudaStream_t s, A... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = b;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 __device__ __forceinline__ int lin(int i, int j, int k, int nx, int ny) { return (k * ny + j) * nx + i; }
 
 // Block sum of a double into one atomicAdd (all threads of the block call).
@@ -234,6 +256,7 @@ template <int ZS>
 __global__ void __launch_bounds__(BX * BY) k_smooth(float* __restrict__ e, const float* __restrict__ g,
                                                     const uint8_t* __restrict__ mask, int nx, int ny, int nz,
                                                     int color, float omega) {
+    pdl_wait();
     const int j = blockIdx.y * BY + threadIdx.y, k0 = blockIdx.z * ZS, ii = blockIdx.x * BX + threadIdx.x;
     if (j >= ny) return;
     const bool relax = omega != 1.0f;
@@ -283,6 +306,7 @@ __device__ __forceinline__ float first_red(const float* __restrict__ g, const ui
 __global__ void __launch_bounds__(BX * BY) k_sweep_first(float* __restrict__ e, const float* __restrict__ g,
                                                          const uint8_t* __restrict__ mask, int nx, int ny, int nz,
                                                          float omega) {
+    pdl_wait();
     const int ii = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k = blockIdx.z;
     const int lane = threadIdx.x;
     const int par = (j + k) & 1;       // x offset of the colour-0 cell in the pair
@@ -329,6 +353,7 @@ __global__ void __launch_bounds__(BX * BY) k_sweep_first(float* __restrict__ e, 
 __global__ void k_resid_restrict(const float* __restrict__ e, const float* __restrict__ g,
                                  const uint8_t* __restrict__ mask, int nx, int ny, int nz, float* __restrict__ gc,
                                  const uint8_t* __restrict__ maskc, int black_zero) {
+    pdl_wait();
     const int cx = nx / 2, cy = ny / 2;
     const int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y, K = blockIdx.z;
     if (I >= cx || J >= cy) return;
@@ -364,6 +389,7 @@ __device__ __forceinline__ float cval(const float* ec, int I, int J, int K, int 
 // neighbourhood; all loads are issued before the arithmetic.
 __global__ void k_prolong_add(const float* __restrict__ ec, float* __restrict__ ef, const uint8_t* __restrict__ mask,
                               int nx, int ny, int nz) {
+    pdl_wait();
     const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
     const int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y, K = blockIdx.z;
     if (I >= cx || J >= cy) return;
@@ -561,6 +587,7 @@ template <bool WARP> __device__ void tail_coarse(const TailLevels& T, const Tail
 }
 
 __global__ void __launch_bounds__(1024) k_tail_vcycle(const TailLevels T) {
+    pdl_wait();
     extern __shared__ __align__(16) unsigned char tail_raw[];
     TailSmem S;
     S.e = reinterpret_cast<float*>(tail_raw);
@@ -642,8 +669,8 @@ void smooth_half(float* e, const float* g, const uint8_t* m, int nx, int ny, int
                  cudaStream_t s) {
     const int zs = (long long)nx * ny * nz >= kSmoothDeep ? 4 : 1;
     const dim3 gr(((nx + 1) / 2 + BX - 1) / BX, (ny + BY - 1) / BY, (nz + zs - 1) / zs);
-    if (zs == 4) k_smooth<4><<<gr, kBlk, 0, s>>>(e, g, m, nx, ny, nz, color, omega);
-    else k_smooth<1><<<gr, kBlk, 0, s>>>(e, g, m, nx, ny, nz, color, omega);
+    if (zs == 4) launch_pdl(k_smooth<4>, gr, kBlk, 0, s, e, g, m, nx, ny, nz, color, omega);
+    else launch_pdl(k_smooth<1>, gr, kBlk, 0, s, e, g, m, nx, ny, nz, color, omega);
 }
 dim3 grid_flat(long long n) { return dim3((unsigned)((n + BX * BY - 1) / (BX * BY))); }
 dim3 grid_red(long long n) {
@@ -759,8 +786,8 @@ void MG::vcycle(cudaStream_t s) {
     for (int l = 0; l < t; ++l) {
         const long long n = (long long)lx[l] * ly[l] * lz[l];
         if (pre > 0) {
-            k_sweep_first<<<dim3(((lx[l] + 1) / 2 + BX - 1) / BX, (ly[l] + BY - 1) / BY, lz[l]), kBlk, 0, s>>>(
-                e[l], g[l], m[l], lx[l], ly[l], lz[l], omega);
+            launch_pdl(k_sweep_first, dim3(((lx[l] + 1) / 2 + BX - 1) / BX, (ly[l] + BY - 1) / BY, lz[l]), kBlk, 0,
+                       s, e[l], (const float*)g[l], (const uint8_t*)m[l], lx[l], ly[l], lz[l], omega);
         } else {
             cudaMemsetAsync(e[l], 0, n * sizeof(float), s);
         }
@@ -768,8 +795,9 @@ void MG::vcycle(cudaStream_t s) {
             smooth_half(e[l], g[l], m[l], lx[l], ly[l], lz[l], 0, omega, s);
             smooth_half(e[l], g[l], m[l], lx[l], ly[l], lz[l], 1, omega, s);
         }
-        k_resid_restrict<<<grid3(lx[l + 1], ly[l + 1], lz[l + 1]), kBlk, 0, s>>>(
-            e[l], g[l], m[l], lx[l], ly[l], lz[l], g[l + 1], m[l + 1], pre > 0 ? 1 : 0);
+        launch_pdl(k_resid_restrict, grid3(lx[l + 1], ly[l + 1], lz[l + 1]), kBlk, 0, s, (const float*)e[l],
+                   (const float*)g[l], (const uint8_t*)m[l], lx[l], ly[l], lz[l], g[l + 1], (const uint8_t*)m[l + 1],
+                   pre > 0 ? 1 : 0);
     }
     TailLevels T;
     int off = 0;
@@ -792,10 +820,10 @@ void MG::vcycle(cudaStream_t s) {
     T.total = off;
     const size_t smem = (size_t)off * (2 * sizeof(float) + 1);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_tail_vcycle, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_tail_vcycle<<<1, 1024, smem, s>>>(T);
+    launch_pdl(k_tail_vcycle, dim3(1), dim3(1024), smem, s, T);
     for (int l = t - 1; l >= 0; --l) {
-        k_prolong_add<<<grid3(lx[l + 1], ly[l + 1], lz[l + 1]), kBlk, 0, s>>>(e[l + 1], e[l], m[l], lx[l], ly[l],
-                                                                              lz[l]);
+        launch_pdl(k_prolong_add, grid3(lx[l + 1], ly[l + 1], lz[l + 1]), kBlk, 0, s, (const float*)e[l + 1], e[l],
+                   (const uint8_t*)m[l], lx[l], ly[l], lz[l]);
         for (int it = 0; it < post; ++it) {
             smooth_half(e[l], g[l], m[l], lx[l], ly[l], lz[l], 1, omega, s);
             smooth_half(e[l], g[l], m[l], lx[l], ly[l], lz[l], 0, omega, s);
@@ -924,14 +952,17 @@ void MG::iteration_mixed(cudaStream_t s, int it) {
     const int nx = lx[0], ny = ly[0], nz = lz[0], n = nx * ny * nz;
     const int cur = it & 1, first = it == 0 ? 1 : 0;
     vcycle(s);
-    k_mx_dots<<<grid_mxf(n), kFlatBlock, 0, s>>>(e[0], g[0], q32, n, first, part, ctr + 1, norms);
+    launch_pdl(k_mx_dots, grid_mxf(n), dim3(kFlatBlock), 0, s, (const float*)e[0], (const float*)g[0],
+               (const float*)q32, n, first, part, ctr + 1, norms);
     if (nx % 4 == 0)
-        k_mx_dir_apply4<<<grid_mx3v(nx, ny, nz), kBlk, 0, s>>>(e[0], p32[cur ^ 1], p32[cur], q32, m[0], nx, ny, nz,
-                                                               first, part, ctr + 2, norms);
+        launch_pdl(k_mx_dir_apply4, grid_mx3v(nx, ny, nz), kBlk, 0, s, (const float*)e[0],
+                   (const float*)p32[cur ^ 1], p32[cur], q32, (const uint8_t*)m[0], nx, ny, nz, first, part, ctr + 2,
+                   norms);
     else
-        k_mx_dir_apply<<<grid_mx3(nx, ny, nz), kBlk, 0, s>>>(e[0], p32[cur ^ 1], p32[cur], q32, m[0], nx, ny, nz, first,
-                                                         part, ctr + 2, norms);
-    k_mx_update<<<grid_mxf(n), kFlatBlock, 0, s>>>(p32[cur], q32, d32, g[0], n, first, part, ctr + 3, norms);
+        launch_pdl(k_mx_dir_apply, grid_mx3(nx, ny, nz), kBlk, 0, s, (const float*)e[0], (const float*)p32[cur ^ 1],
+                   p32[cur], q32, (const uint8_t*)m[0], nx, ny, nz, first, part, ctr + 2, norms);
+    launch_pdl(k_mx_update, grid_mxf(n), dim3(kFlatBlock), 0, s, (const float*)p32[cur], (const float*)q32, d32,
+               g[0], n, first, part, ctr + 3, norms);
     launches += 3;
 }
 

@@ -303,6 +303,7 @@ __device__ __forceinline__ void st4(float* p, int v4, float4 v) { reinterpret_ca
 __global__ void __launch_bounds__(kFlatBlock) k_mx_dots(const float* __restrict__ z, const float* __restrict__ r,
                                                         const float* __restrict__ q, int n, int first, double* part,
                                                         unsigned* ctr, double* sc) {
+    pdl_wait();
     float acc[2] = {0.0f, 0.0f};
     FLAT4_LOOP(
         const float4 zz = ld4(z, v4); acc[0] += dot4(zz, ld4(r, v4)); if (!first) acc[1] += dot4(zz, ld4(q, v4));,
@@ -330,6 +331,7 @@ __global__ void __launch_bounds__(BX * BY) k_mx_dir_apply(const float* __restric
                                                           float* __restrict__ q, const uint8_t* __restrict__ mask,
                                                           int nx, int ny, int nz, int first, double* part,
                                                           unsigned* ctr, double* sc) {
+    pdl_wait();
     const float beta = first ? 0.0f : (float)sc[S_BETA];
     const bool use_prev = beta != 0.0f;
     auto P = [&](int x) { return use_prev ? fmaf(beta, __ldg(p_prev + x), __ldg(z + x)) : __ldg(z + x); };
@@ -407,6 +409,7 @@ __global__ void __launch_bounds__(BX * BY) k_mx_dir_apply4(const float* __restri
                                                            float* __restrict__ p_cur, float* __restrict__ q,
                                                            const uint8_t* __restrict__ mask, int nx, int ny, int nz,
                                                            int first, double* part, unsigned* ctr, double* sc) {
+    pdl_wait();
     const float beta = first ? 0.0f : (float)sc[S_BETA];
     const bool use_prev = beta != 0.0f;
     const int lane = threadIdx.x;
@@ -485,6 +488,7 @@ __global__ void __launch_bounds__(BX * BY) k_mx_dir_apply4(const float* __restri
 __global__ void __launch_bounds__(kFlatBlock) k_mx_update(const float* __restrict__ p, const float* __restrict__ q,
                                                           float* __restrict__ d, float* __restrict__ r, int n,
                                                           int first, double* part, unsigned* ctr, double* sc) {
+    pdl_wait();
     const float a = (float)sc[S_ALPHA];
     float acc[1] = {0.0f};
     FLAT4_LOOP(
