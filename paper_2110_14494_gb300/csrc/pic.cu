@@ -2561,22 +2561,40 @@ extern "C" int pic_upload(pic_ctx* c, long long n, const void* const* arrays, in
     return PIC_OK;
 }
 
-extern "C" int pic_download(pic_ctx* c, void* const* arrays, long long cap, long long* n_out) {
-    if (!c || !arrays) return PIC_ERR_ARG;
-    DevState h;
-    int rc = read_state(c, &h);
-    if (rc) return rc;
-    const long long n = c->n_host;
-    if (n_out) *n_out = n;
-    if (n > cap) return c->fail(PIC_ERR_CAPACITY, "host arrays too small");
+// Copies n particles of the current buffer to the host arrays (no wait).
+static cudaError_t download_async(pic_ctx* c, void* const* arrays, long long n) {
     const size_t R = real_size(c->prec), capd = (size_t)c->cfg.capacity;
     char* base = c->ws + c->L.buf[c->cur];
     for (int f = 0; f < 11 && n > 0; ++f) {
         if (!arrays[f]) continue;
         cudaError_t e = cudaMemcpyAsync(arrays[f], base + f * al256(capd * R), n * (f < 10 ? R : 8),
                                         cudaMemcpyDeviceToHost, c->s);
-        if (e != cudaSuccess) return c->cuda_fail(e, "download");
+        if (e != cudaSuccess) return e;
     }
-    cudaError_t e = cudaStreamSynchronize(c->s);
-    return e == cudaSuccess ? PIC_OK : c->cuda_fail(e, "download");
+    return cudaSuccess;
+}
+
+extern "C" int pic_download(pic_ctx* c, void* const* arrays, long long cap, long long* n_out) {
+    if (!c || !arrays) return PIC_ERR_ARG;
+    // The host count is known after every call that changes it; the device
+    // state and the particles are copied together and checked after one wait.
+    DevState h;
+    long long n = c->n_host;
+    const bool fits = n <= cap;
+    cudaError_t e = cudaMemcpyAsync(&h, c->st(), sizeof(DevState), cudaMemcpyDeviceToHost, c->s);
+    if (e == cudaSuccess && fits) e = download_async(c, arrays, n);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+    if (e != cudaSuccess) return c->cuda_fail(e, "download");
+    if ((long long)h.n_in != n) {  // not expected: copy again with the device count
+        n = (long long)h.n_in;
+        c->n_host = n;
+        if (n <= cap) {
+            e = download_async(c, arrays, n);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+            if (e != cudaSuccess) return c->cuda_fail(e, "download");
+        }
+    }
+    if (n_out) *n_out = n;
+    if (n > cap) return c->fail(PIC_ERR_CAPACITY, "host arrays too small");
+    return PIC_OK;
 }
