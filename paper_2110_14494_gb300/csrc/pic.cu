@@ -679,7 +679,7 @@ __global__ void __launch_bounds__(256) k_merge_split(Soa<T> p, long long n, cons
             if (!((double)w > hi)) continue;
             int mm = 0;
             double wc = (double)w;
-            while (wc > hi) { wc *= 0.5; ++mm; }
+            while (wc > hi && mm < 30) { wc *= 0.5; ++mm; }   // hi >= 1.5 w / N_ppc bounds mm far below 30
             const T wn = (T)ldexp((double)w, -mm);
             p.r[PW][t] = wn;
             const unsigned long long copies = (1ull << mm) - 1ull;
@@ -841,7 +841,7 @@ __global__ void __launch_bounds__(256) k_merge_split_warp(Soa<T> p, long long n,
             if (!gt_d(wt, hi)) continue;
             int mm = 0;
             double wc = (double)wt;
-            while (wc > hi) { wc *= 0.5; ++mm; }
+            while (wc > hi && mm < 30) { wc *= 0.5; ++mm; }   // hi >= 1.5 w / N_ppc bounds mm far below 30
             const T wn = (T)ldexp((double)wt, -mm);
             p.r[PW][t] = wn;
             const unsigned long long copies = (1ull << mm) - 1ull;
