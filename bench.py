@@ -487,7 +487,8 @@ def main():
     achieved = BYTES_PER_UPDATE * parents_per_launch / (push_ms * 1e-3) / 1e9
     phases = {k: round(prof[k], 3) for k in ("ms_push", "ms_children", "ms_field", "ms_reorder")}
     print(json.dumps({"diag": "device-timed", "value": value, "ms_per_step": ms_max / args.steps,
-                      "phases_ms": phases, "parents_per_launch": parents_per_launch, "push_ms": push_ms,
+                      "phases_ms": phases, "speculative_solves": [prof["n_speculative"], prof["n_undone"]],
+                      "parents_per_launch": parents_per_launch, "push_ms": push_ms,
                       "achieved_GBs": achieved, "n_trace": n_trace, "launches": prof["n_launches"]}),
           file=sys.stderr, flush=True)
 

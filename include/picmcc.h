@@ -229,6 +229,10 @@ typedef struct pic_profile_times {
     double ms_push, ms_children, ms_field, ms_reorder; /* accumulated milliseconds */
     long long n_push, n_children, n_field, n_reorder;  /* timed launches / phases */
     long long n_launches;                              /* kernels pic_step launched since the last clear */
+    /* float32 Cartesian coupled steps enqueue the next field solve before the
+     * host reads the step's counts; a step that then needs a weight update or
+     * further product generations undoes that solve and solves again */
+    long long n_speculative, n_undone;                 /* such solves, and those undone */
 } pic_profile_times;
 
 /* enable != 0 starts timing (cleared); out (optional) receives the

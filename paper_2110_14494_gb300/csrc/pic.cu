@@ -317,6 +317,9 @@ __global__ void k_step_stats(const Soa<T> p, const DevState* stc, const unsigned
         if (h[b]) atomicAdd(&st->vhist[b], h[b]);
 }
 
+// Clears error bits (a speculative field solve that was undone).
+__global__ void k_clear_err(DevState* st, unsigned bits) { st->err &= ~bits; }
+
 // Before children generation g >= 1: the queue it will spill into starts empty.
 __global__ void k_next_generation(DevState* st, int gen) {
     st->n_fetch_c = 0;
@@ -894,8 +897,8 @@ static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
     size_t total = 0;
-    size_t buf[2], cq[2], table, table64, E4, qe, qp, qn, st, cnt, start, sums, key, rank, msc, gas, rho, phi, phi_prev,
-        phi_x, mg, photo, hostio;
+    size_t buf[2], cq[2], table, table64, E4, E4b, qe, qp, qn, st, cnt, start, sums, key, rank, msc, gas, rho, phi,
+        phi_prev, phi_x, phi_y, mg, photo, hostio;
 };
 
 static size_t real_size(int prec) { return prec == 64 ? 8 : 4; }
@@ -924,6 +927,10 @@ static Layout make_layout(const pic_config* c) {
     L.table = take((size_t)nb * kTableStride * R);
     L.table64 = take((size_t)nb * kTableStride * 8);
     L.E4 = take(ncell * 4 * R);
+    // float32 Cartesian coupled contexts alternate between two packed fields
+    // (the solve writes the one the current push does not read)
+    const bool pair = c->coupled && c->precision == 32 && c->geometry == 0;
+    L.E4b = pair ? take(ncell * 4 * R) : L.E4;
     L.qe = take(ncell * 8);
     L.qp = take(ncell * 8);
     L.qn = take(ncell * 8);
@@ -940,6 +947,7 @@ static Layout make_layout(const pic_config* c) {
     L.phi = take(ncell * 8);
     L.phi_prev = take(ncell * 8);
     L.phi_x = take(ncell * 8);
+    L.phi_y = pair ? take(ncell * 8) : L.phi_x;
     L.mg = take(c->geometry == 1 ? AxiMG::bytes(c->nx, c->nz) : MG::bytes(c->nx, c->ny, c->nz, c->precision == 32, false));
     {
         const size_t np = (size_t)photo_cap(c);
@@ -991,8 +999,14 @@ struct pic_ctx {
     unsigned long long dev_kernels_seen = 0;  // DevState::dev_kernels already counted in launches
     // Float32 coupled field solve as one graph per current-potential slot
     // (prologue, device-driven solve, report); used from the third solve on.
-    cudaGraphExec_t fgraph[3] = {nullptr, nullptr, nullptr};
-    long long fgraph_kernels[3] = {0, 0, 0};
+    cudaGraphExec_t fgraph[4] = {nullptr, nullptr, nullptr, nullptr};
+    long long fgraph_kernels[4] = {0, 0, 0, 0};
+    // Speculative field solve (float32 Cartesian coupled steps): the step's
+    // device state is copied to pinned host memory and the solve is enqueued
+    // before the host looks at it.
+    DevState* hs = nullptr;
+    cudaEvent_t ev_state = nullptr;
+    bool spec_off = false;       // pinned memory or the event could not be had
     cudaGraphExec_t agraph = nullptr;  // the same for axisymmetric contexts (one potential buffer)
     long long agraph_kernels = 0;
     cudaStream_t fcap = nullptr;
@@ -1045,8 +1059,10 @@ struct pic_ctx {
     ~pic_ctx() {
         for (cudaEvent_t e : ev_free) cudaEventDestroy(e);
         for (cudaEvent_t e : ev_used) cudaEventDestroy(e);
-        for (int q = 0; q < 3; ++q)
+        for (int q = 0; q < 4; ++q)
             if (fgraph[q]) cudaGraphExecDestroy(fgraph[q]);
+        if (hs) cudaFreeHost(hs);
+        if (ev_state) cudaEventDestroy(ev_state);
         if (agraph) cudaGraphExecDestroy(agraph);
         if (fcap) cudaStreamDestroy(fcap);
         amg.release();
@@ -1080,12 +1096,24 @@ struct pic_ctx {
     double* rho() { return (double*)(ws + L.rho); }
     double* phi() { return (double*)(ws + L.phi); }
     // float32 contexts keep the potential as float pairs ([hi][lo], n each)
-    // in three rotating slots: the current solution, the previous one and
-    // the warm-start guess.
-    int ph_cur = 0, ph_prev = 1, ph_free = 2;
+    // in four rotating slots: the current solution, the previous one, the
+    // warm-start guess and the next solution.  A solve writes only the last
+    // two, so until the slots rotate the solve can be undone by the host
+    // alone.  Rotation (cur, prev, free, out) <- (out, cur, prev, free) keeps
+    // cur and out of opposite parity: the push reads packed field cur & 1 and
+    // the solve writes field out & 1.
+    int ph_cur = 0, ph_prev = 1, ph_free = 2, ph_out = 3;
     float* ph_hi(int slot) {
-        const size_t o = slot == 0 ? L.phi : (slot == 1 ? L.phi_prev : L.phi_x);
+        const size_t o = slot == 0 ? L.phi : (slot == 1 ? L.phi_prev : (slot == 2 ? L.phi_x : L.phi_y));
         return (float*)(ws + o);
+    }
+    char* E4p(int slot) { return ws + ((slot & 1) ? L.E4b : L.E4); }
+    void rotate_slots() {
+        const int o = ph_out;
+        ph_out = ph_free;
+        ph_free = ph_prev;
+        ph_prev = ph_cur;
+        ph_cur = o;
     }
     float* ph_lo(int slot) { return ph_hi(slot) + g.ncell(); }
     MergeScratch msc() {
@@ -1233,6 +1261,7 @@ extern "C" int pic_init(const pic_config* cfg, void* d_ws, size_t ws_bytes, cons
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.phi, 0, ncell * 8, c->s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.phi_prev, 0, ncell * 8, c->s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.phi_x, 0, ncell * 8, c->s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.phi_y, 0, ncell * 8, c->s);
     if (e != cudaSuccess) { rc = c->cuda_fail(e, "pic_init"); delete c; return rc; }
     rc = build_table(c);
     if (rc) { delete c; return rc; }
@@ -1289,7 +1318,7 @@ template <class T> static PushArgs<T> make_args(pic_ctx* c, int mode) {
     A.hx = (T)(c->g.ox + (double)c->g.nx * c->g.dx);
     A.hy = (T)(c->g.oy + (double)c->g.ny * c->g.dx);
     A.hz = (T)(c->g.oz + (double)c->g.nz * c->g.dx);
-    A.E4 = c->field_uniform ? nullptr : (const T*)(c->ws + c->L.E4);
+    A.E4 = c->field_uniform ? nullptr : (const T*)c->E4p(c->ph_cur);
     for (int d = 0; d < 3; ++d) A.E0[d] = (T)c->E0[d];
     A.mask = c->mask;
     A.q_e = c->qe();
@@ -1464,9 +1493,9 @@ extern "C" int pic_set_field(pic_ctx* c, const float* Ex, const float* Ey, const
         c->field_uniform = 0;
         const long long n = c->g.ncell();
         if (c->prec == 32)
-            k_pack_field<float><<<grid_n(n), 256, 0, c->s>>>(Ex, Ey, Ez, n, (float*)(c->ws + c->L.E4));
+            k_pack_field<float><<<grid_n(n), 256, 0, c->s>>>(Ex, Ey, Ez, n, (float*)c->E4p(c->ph_cur));
         else
-            k_pack_field<double><<<grid_n(n), 256, 0, c->s>>>(Ex, Ey, Ez, n, (double*)(c->ws + c->L.E4));
+            k_pack_field<double><<<grid_n(n), 256, 0, c->s>>>(Ex, Ey, Ez, n, (double*)c->E4p(c->ph_cur));
     }
     c->field_valid = 1;
     cudaError_t e = cudaGetLastError();
@@ -1511,9 +1540,9 @@ static int solve_field_pair_graph(pic_ctx* c) {
         DevState* st = c->st();
         long long fixed = 0;
         const int rc = c->mg.capture_solve_mixed(
-            c->fcap, (const float*)c->rho(), c->ph_hi(c->ph_free), c->ph_lo(c->ph_free), c->ph_hi(c->ph_prev),
-            c->ph_lo(c->ph_prev), c->g.dx, c->cfg.v_lo, c->cfg.v_hi, c->cfg.v_mask, c->cfg.poisson_rtol,
-            c->cfg.poisson_max_cycles, (float*)(c->ws + c->L.E4), &st->poisson_cycles, &st->poisson_rel, &st->err,
+            c->fcap, (const float*)c->rho(), c->ph_hi(c->ph_free), c->ph_lo(c->ph_free), c->ph_hi(c->ph_out),
+            c->ph_lo(c->ph_out), c->g.dx, c->cfg.v_lo, c->cfg.v_hi, c->cfg.v_mask, c->cfg.poisson_rtol,
+            c->cfg.poisson_max_cycles, (float*)c->E4p(c->ph_out), &st->poisson_cycles, &st->poisson_rel, &st->err,
             kErrPoissonLimit, &st->dev_kernels, &fixed);
         cudaGraph_t gr = nullptr;
         const cudaError_t e = cudaStreamEndCapture(c->fcap, &gr);
@@ -1530,7 +1559,7 @@ static int solve_field_pair_graph(pic_ctx* c) {
     const cudaError_t e = cudaGraphLaunch(c->fgraph[slot], c->s);
     if (e != cudaSuccess) return c->cuda_fail(e, "field solve graph");
     c->n_solves++;
-    std::swap(c->ph_cur, c->ph_prev);
+    c->rotate_slots();
     c->launches += c->fgraph_kernels[slot];
     c->last_on_device = true;
     c->field_valid = 1;
@@ -1554,21 +1583,21 @@ static int solve_field_pair(pic_ctx* c) {
                                                   (const long long*)c->qn(), n, (float)scale, (float*)c->rho());
     ++c->launches;
     const long long l0 = c->mg.launches;
-    // guess in the free slot; the solution goes to the previous one's slot
+    // guess in the free slot, solution in the out slot
     c->mg.extrapolate_pair(c->ph_hi(c->ph_cur), c->ph_lo(c->ph_cur), c->ph_hi(c->ph_prev), c->ph_lo(c->ph_prev),
                            c->ph_hi(c->ph_free), c->ph_lo(c->ph_free), (int)n, c->n_solves >= 2, c->s);
     c->n_solves++;
     double hn[2];
     int rc = c->mg.solve_mixed(c->rho(), false, c->mask, c->ph_hi(c->ph_free), c->ph_lo(c->ph_free),
-                               c->ph_hi(c->ph_prev), c->ph_lo(c->ph_prev), c->n_solves <= 2, c->g.dx,
+                               c->ph_hi(c->ph_out), c->ph_lo(c->ph_out), c->n_solves <= 2, c->g.dx,
                                c->cfg.v_lo, c->cfg.v_hi,
                                c->cfg.v_mask, c->cfg.poisson_rtol, c->cfg.poisson_max_cycles,
-                               (float*)(c->ws + c->L.E4), nullptr, nullptr, nullptr, c->s, &c->last_cycles,
+                               (float*)c->E4p(c->ph_out), nullptr, nullptr, nullptr, c->s, &c->last_cycles,
                                &c->last_rel, hn);
     if (rc == PIC_ERR_CUDA) return c->fail(rc, "poisson solve: CUDA error");
     if (rc == PIC_ERR_TIMEOUT) return c->fail(rc, "poisson solve: cycle limit reached");
     if (rc) return c->fail(rc, "poisson solve");
-    std::swap(c->ph_cur, c->ph_prev);
+    c->rotate_slots();
     c->launches += c->mg.launches - l0;
     c->field_valid = 1;
     c->field_uniform = 0;
@@ -1775,30 +1804,41 @@ static void next_dt(pic_ctx* c, const DevState& h) {
     c->dt_next = dt;
 }
 
+// The photoelectrons of the generations so far join the output, and the
+// time-step statistics of the particles are formed (adaptive dt).
+template <class T> static int generation_tail(pic_ctx* c, PushArgs<T>& A, int mode) {
+    if (A.cap_photo > 0) {
+        cudaError_t e = PushLaunch<T>::photo_append(A, 152 * 2, c->s);
+        if (e != cudaSuccess) return c->cuda_fail(e, "photoelectrons");
+        c->launches += 3;
+    }
+    if (c->cfg.adaptive_dt && mode == MODE_PIC) {
+        DevState* st = c->st();
+        cudaMemsetAsync(&st->qe_max, 0, sizeof(long long) + sizeof(unsigned long long) + sizeof(st->vhist), c->s);
+        k_step_stats<T><<<152 * 4, 256, 0, c->s>>>(A.out, st, c->qe(), c->g.ncell(), c->g.axi ? c->g.nx : 0, st);
+        c->launches += 1;
+    }
+    return PIC_OK;
+}
+
 // Further children generations while descendants spilled out of the lane
 // stacks (deep ionization cascades within one step).  Reads the device state
-// once (synchronising); afterwards c->n_next holds the particle count the
-// step will leave.
-template <class T> static int extra_generations(pic_ctx* c, PushArgs<T>& A, int mode, bool stats) {
+// once (synchronising), or starts from h0, the state already read after
+// generation_tail of generation 1; afterwards c->n_next holds the particle
+// count the step will leave.
+template <class T> static int extra_generations(pic_ctx* c, PushArgs<T>& A, int mode, bool stats,
+                                                const DevState* h0 = nullptr) {
     for (int gen = 1;; ++gen) {
-        if (A.cap_photo > 0) {
-            // photoelectrons of the generations so far join the output
-            cudaError_t e = PushLaunch<T>::photo_append(A, 152 * 2, c->s);
-            if (e != cudaSuccess) return c->cuda_fail(e, "photoelectrons");
-            c->launches += 3;
-        }
-        if (c->cfg.adaptive_dt && mode == MODE_PIC) {
-            DevState* st = c->st();
-            cudaMemsetAsync(&st->qe_max, 0, sizeof(long long) + sizeof(unsigned long long) + sizeof(st->vhist), c->s);
-            k_step_stats<T><<<152 * 4, 256, 0, c->s>>>(A.out, st, c->qe(), c->g.ncell(), c->g.axi ? c->g.nx : 0,
-                                                       st);
-            c->launches += 1;
-        }
         DevState h;
-        int rc = read_state(c, &h);
-        if (rc) return rc;
+        if (gen == 1 && h0) {
+            h = *h0;
+        } else {
+            int rc = generation_tail<T>(c, A, mode);
+            if (rc == PIC_OK) rc = read_state(c, &h);
+            if (rc) return rc;
+        }
         // error flags raised so far (this step's kernels, or the previous step's field solve)
-        rc = check_err(c, h);
+        const int rc = check_err(c, h);
         if (rc) return rc;
         const unsigned long long pending = (gen & 1) ? h.n_spill : h.n_child;
         c->n_next = (long long)(h.n_out < (unsigned long long)c->cfg.capacity ? h.n_out : c->cfg.capacity);
@@ -1816,7 +1856,79 @@ template <class T> static int extra_generations(pic_ctx* c, PushArgs<T>& A, int 
     return PIC_OK;
 }
 
-template <class T> static int one_step(pic_ctx* c, bool stats) {
+// Speculative field solve.  In float32 Cartesian coupled contexts whose
+// solve runs as a graph, the solve for the next step is enqueued right after
+// the step's statistics, before the host has read the step's counts (copied
+// to pinned memory behind an event), so the GPU does not wait for the host's
+// decisions.  Two outcomes change the charge the solve must see: a weight
+// update (merged and split particles are deposited again) and further
+// product generations.  When the counts call for either, the solve is
+// undone: it wrote only the guess and out potential slots and the packed
+// field the push does not read, so restoring the host's slot indices (and
+// the cycle-limit flag it may have raised) puts the context back as it was,
+// and the step goes on as without speculation.  Steps with a scheduled
+// weight update do not speculate.
+static bool can_speculate(pic_ctx* c) {
+    if (!c->cfg.coupled || c->prec != 32 || c->g.axi || c->fgraph_off || c->spec_off || c->n_solves < 2)
+        return false;
+    if (c->cfg.weight_interval > 0 && (c->step % (uint32_t)c->cfg.weight_interval) == 0) return false;
+    if (!c->hs && cudaHostAlloc((void**)&c->hs, sizeof(DevState), cudaHostAllocDefault) != cudaSuccess) c->hs = nullptr;
+    if (c->hs && !c->ev_state && cudaEventCreateWithFlags(&c->ev_state, cudaEventDisableTiming) != cudaSuccess)
+        c->ev_state = nullptr;
+    if (!c->hs || !c->ev_state) {
+        cudaGetLastError();
+        c->spec_off = true;
+        return false;
+    }
+    return true;
+}
+
+template <class T> static int speculative_tail(pic_ctx* c, PushArgs<T>& A, bool stats, bool* solved) {
+    int rc = generation_tail<T>(c, A, MODE_PIC);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(c->hs, c->st(), sizeof(DevState), cudaMemcpyDeviceToHost, c->s);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_state, c->s);
+    if (e != cudaSuccess) return c->cuda_fail(e, "state read-back");
+    const int slots[4] = {c->ph_cur, c->ph_prev, c->ph_free, c->ph_out};
+    const long long n_solves = c->n_solves;
+    const bool on_device = c->last_on_device;
+    const int cycles = c->last_cycles;
+    const double rel = c->last_rel;
+    c->mark(5);
+    rc = solve_field(c);
+    if (rc) return rc;
+    c->mark(6);
+    c->accumulate(5, 6, &c->pt.ms_field, &c->pt.n_field);
+    c->pt.n_speculative++;
+    e = cudaEventSynchronize(c->ev_state);
+    if (e != cudaSuccess) return c->cuda_fail(e, "state read-back");
+    const DevState h = *c->hs;
+    c->n_host = (long long)h.n_in;
+    const long long n_next = (long long)(h.n_out < (unsigned long long)c->cfg.capacity ? h.n_out : c->cfg.capacity);
+    const bool grown = c->cfg.growth_trigger > 0 && n_next > 0 &&
+                       (double)n_next > c->cfg.growth_trigger * (double)c->n_last_wu;
+    if (!h.err && !h.n_spill && !grown) {
+        c->n_next = n_next;
+        if (c->cfg.adaptive_dt) next_dt(c, h);
+        *solved = true;
+        return PIC_OK;
+    }
+    c->ph_cur = slots[0];
+    c->ph_prev = slots[1];
+    c->ph_free = slots[2];
+    c->ph_out = slots[3];
+    c->n_solves = n_solves;
+    c->last_on_device = on_device;
+    c->last_cycles = cycles;
+    c->last_rel = rel;
+    k_clear_err<<<1, 1, 0, c->s>>>(c->st(), kErrPoissonLimit);
+    c->launches += 1;
+    c->pt.n_undone++;
+    return extra_generations<T>(c, A, MODE_PIC, stats, &h);
+}
+
+template <class T> static int one_step(pic_ctx* c, bool stats, bool* solved) {
+    *solved = false;
     c->step++;
     PushArgs<T> A = make_args<T>(c, MODE_PIC);
     cudaMemsetAsync(c->qe(), 0, (size_t)c->g.ncell() * 8, c->s);
@@ -1829,7 +1941,8 @@ template <class T> static int one_step(pic_ctx* c, bool stats) {
     if (e == cudaSuccess) e = PushLaunch<T>::children(A, MODE_PIC, stats, c->grid_push, c->s);
     c->mark(2);
     if (e != cudaSuccess) return c->cuda_fail(e, "push");
-    int rc = extra_generations<T>(c, A, MODE_PIC, stats);
+    const int rc = can_speculate(c) ? speculative_tail<T>(c, A, stats, solved)
+                                    : extra_generations<T>(c, A, MODE_PIC, stats);
     if (rc) return rc;
     k_end_step<<<1, 1, 0, c->s>>>(c->st(), nullptr, c->cfg.capacity);
     c->cur = 1 - c->cur;
@@ -1858,7 +1971,8 @@ extern "C" int pic_step(pic_ctx* c, int n_steps, pic_step_stats* stats) {
         if (rc) return rc;
     }
     for (int it = 0; it < n_steps; ++it) {
-        rc = c->prec == 32 ? one_step<float>(c, want) : one_step<double>(c, want);
+        bool solved = false;  // the next step's field was solved within the step
+        rc = c->prec == 32 ? one_step<float>(c, want, &solved) : one_step<double>(c, want, &solved);
         if (rc) return rc;
         c->t_total += c->dt_cur;
         c->dt_prev = c->dt_cur;
@@ -1868,7 +1982,7 @@ extern "C" int pic_step(pic_ctx* c, int n_steps, pic_step_stats* stats) {
         c->n_host = c->n_next;  // the step's count, read back after its collisions
         bool sorted = false;
         c->mark(3);
-        if (c->cfg.growth_trigger > 0 || c->cfg.weight_interval > 0) {
+        if (!solved && (c->cfg.growth_trigger > 0 || c->cfg.weight_interval > 0)) {
             const bool grown = c->cfg.growth_trigger > 0 &&
                                (double)c->n_host > c->cfg.growth_trigger * (double)c->n_last_wu;
             const bool every = c->cfg.weight_interval > 0 && (c->step % (uint32_t)c->cfg.weight_interval) == 0;
@@ -1890,7 +2004,7 @@ extern "C" int pic_step(pic_ctx* c, int n_steps, pic_step_stats* stats) {
         }
         c->mark(4);
         c->accumulate(3, 4, &c->pt.ms_reorder, &c->pt.n_reorder);
-        if (c->cfg.coupled) {
+        if (c->cfg.coupled && !solved) {
             c->mark(5);
             rc = solve_field(c);
             if (rc) return rc;
@@ -2510,7 +2624,7 @@ extern "C" int pic_progress(pic_ctx* c, long long* updates, long long* parents, 
 extern "C" int pic_set_poisson(pic_ctx* c, double rtol, int max_cycles, int device_loop) {
     if (!c || !(rtol > 0.0) || max_cycles < 1) return PIC_ERR_ARG;
     // recorded graphs hold the old settings
-    for (int q = 0; q < 3; ++q)
+    for (int q = 0; q < 4; ++q)
         if (c->fgraph[q]) {
             cudaGraphExecDestroy(c->fgraph[q]);
             c->fgraph[q] = nullptr;

@@ -24,7 +24,7 @@ def built():
     build.build()
 
 
-def _streamer_ctx(device_loop, rtol=1e-6, grid_n=32):
+def _streamer_ctx(device_loop, rtol=1e-6, grid_n=32, growth_trigger=1.5):
     """A small needle-plane streamer: a Gaussian seed below a charged needle,
     coupled float32 solve, weight updates on growth."""
     from paper_2110_14494_gb300 import PicContext
@@ -33,7 +33,7 @@ def _streamer_ctx(device_loop, rtol=1e-6, grid_n=32):
     V0 = 4000.0
     ctx = PicContext(W.synthetic_air(), grid, precision=32, capacity=400_000, seed=SEED, dt=2e-12, mask=mask,
                      coupled=True, v_lo=0.0, v_hi=V0, v_mask=V0, poisson_rtol=rtol, poisson_max_cycles=60,
-                     boundary=1, growth_trigger=1.5, particle_cap=150_000)
+                     boundary=1, growth_trigger=growth_trigger, particle_cap=150_000)
     ctx.set_poisson(rtol, 60, device_loop=device_loop)
     L = grid_n * 2.5e-5
     ctx.seed_gaussian(5e19, 6e-5, (0.5 * L, 0.5 * L, 0.45 * (grid_n + 16) * 2.5e-5), 2e3)
@@ -74,13 +74,16 @@ def test_device_loop_reports_cycle_limit():
 
 
 def test_device_loop_counts_its_kernels():
-    a = _streamer_ctx(True)
-    b = _streamer_ctx(False)
+    # no weight updates: every speculative solve stands
+    a = _streamer_ctx(True, growth_trigger=0.0)
+    b = _streamer_ctx(False, growth_trigger=0.0)
     for c in (a, b):
         c.step(2)
         c.profile(True)
         c.step(4)
     pa, pb = a.profile(False), b.profile(False)
+    assert pa["n_speculative"] == 4 and pa["n_undone"] == 0
+    assert pb["n_speculative"] == 0
     # the same work; the device-driven solve adds one decision kernel per loop
     # trip and one report kernel per solve, and counts its branches' kernels
     # on the device
@@ -145,6 +148,63 @@ def test_device_loop_refinement_branch_matches_host_loop():
         assert sa.poisson_cycles == sb.poisson_cycles, step
         assert sa.poisson_rel_res == sb.poisson_rel_res, step
         assert sa.poisson_rel_res <= 1e-9
+    assert np.array_equal(_phi(a, n), _phi(b, n))
+    pa, pb = by_id(a.get_particles()), by_id(b.get_particles())
+    for k in pa:
+        assert np.array_equal(pa[k], pb[k]), k
+
+
+@pytest.mark.parametrize("photo", [False, True])
+def test_speculative_solve_is_undone_exactly(photo):
+    """The device-driven solve of a step is enqueued before the host has read
+    the step's counts; a step whose counts then call for a weight update (the
+    particles grew) or for further product generations (cascades deeper than
+    a lane's stack) undoes it and solves again after them.  Ionization at
+    2e12/s (four per electron per 2 ps step, so cascades overflow the lane
+    stacks) against attachment at 1.9e12/s (net growth e^0.2 per step, so the
+    fixed-point deposit stays far from overflow) and a growth trigger of 1.01
+    make both happen in most steps: particle sets, potentials, cycle counts
+    and residuals equal those of the host-driven run, which never
+    speculates, bit for bit."""
+    from paper_2110_14494_gb300 import PicContext
+    from paper_2110_14494_gb300 import picmcc as P
+    gas = W.multi_gas([W.single_process_gas(W.ELASTIC, 1e12 / W.N_GAS, mass=0.0),
+                       W.single_process_gas(W.IONIZATION, 2e12 / W.N_GAS, threshold=0.0),
+                       W.single_process_gas(W.ATTACHMENT, 1.9e12 / W.N_GAS)])
+    grid = W.grid_spec(32, 32, 48, 2.5e-5)
+    mask = W.needle_mask(grid, 0.35e-3, 0.08e-3)
+    V0 = 4000.0
+    kw = {}
+    if photo:
+        pq, p = 4000.0, 101325.0
+        kw = dict(photo_xi=0.05 * (p + pq) / pq, photo_pq=pq, pressure=p, p_o2=0.2 * p,
+                  chi_min=P.ZHELEZNYAK_CHI_MIN, chi_max=P.ZHELEZNYAK_CHI_MAX)
+
+    def ctx_(device_loop):
+        c = PicContext(gas, grid, precision=32, capacity=600_000, seed=SEED, dt=2e-12, mask=mask, coupled=True,
+                       v_lo=0.0, v_hi=V0, v_mask=V0, poisson_rtol=1e-6, poisson_max_cycles=80, boundary=1,
+                       growth_trigger=1.01, particle_cap=4000, **kw)
+        c.set_poisson(1e-6, 80, device_loop=device_loop)
+        L = 32 * 2.5e-5
+        c.seed_gaussian(5e17, 6e-5, (0.5 * L, 0.5 * L, 0.45 * 48 * 2.5e-5), 200.0)
+        return c
+
+    n = 32 * 32 * 48
+    a, b = ctx_(True), ctx_(False)
+    a.profile(True)
+    wu = 0
+    for step in range(6):
+        sa = a.step(1, stats=True)
+        sb = b.step(1, stats=True)
+        assert sa.n_end == sb.n_end, step
+        assert sa.n_children == sb.n_children, step
+        assert sa.poisson_cycles == sb.poisson_cycles, step
+        assert sa.poisson_rel_res == sb.poisson_rel_res, step
+        assert sa.n_weight_updates == sb.n_weight_updates, step
+        wu += sa.n_weight_updates
+    assert wu >= 3
+    pa = a.profile(False)
+    assert pa["n_speculative"] >= 4 and pa["n_undone"] >= 3, pa
     assert np.array_equal(_phi(a, n), _phi(b, n))
     pa, pb = by_id(a.get_particles()), by_id(b.get_particles())
     for k in pa:

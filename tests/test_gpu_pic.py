@@ -282,7 +282,7 @@ def test_adaptive_time_step_bounds():
 @pytest.mark.parametrize("prec", [64, 32])
 def test_coupled_field_matches_oracle_solve(prec):
     """The coupled context's own solve (float64 CG, or the float-pair solve in
-    single precision with its three rotating potential slots), read back from a
+    single precision with its four rotating potential slots), read back from a
     checkpoint, against the oracle's solution for the same charge (none) and
     electrode."""
     grid = W.grid_spec(32, 32, 48, 5e-5)
