@@ -137,6 +137,11 @@ struct DevState {
     unsigned long long n_big;        // weight update: cells left to the block-per-cell merge
     unsigned long long n_occ;        // weight update: occupied cells listed
     unsigned long long n_occ_fetch;  // weight update: work cursor over the listed cells
+    // gate of the float32 field-solve graph: a speculative solve (gate_spec)
+    // runs only when the step needs no weight update (count <= gate_thr) and
+    // no further product generations
+    double gate_thr;
+    int gate_spec, gate_pad;
 };
 
 // Uniform grid description (cell-centred, cubic cells).

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "graph_util.cuh"
 #include "poisson.cuh"
 #include "poisson_axi.cuh"
 #include "push.cuh"
@@ -319,6 +320,24 @@ __global__ void k_step_stats(const Soa<T> p, const DevState* stc, const unsigned
 
 // Clears error bits (a speculative field solve that was undone).
 __global__ void k_clear_err(DevState* st, unsigned bits) { st->err &= ~bits; }
+
+// Head of the float32 field-solve graph: a speculative solve goes ahead only
+// when the step that was just pushed needs neither a weight update (its
+// count above gate_thr) nor further product generations, and raised no error:
+// the test the host applies to the same values once it has read them.
+__global__ void k_solve_gate(const DevState* st, cudaGraphConditionalHandle h, unsigned long long cap) {
+    bool go = true;
+    if (st->gate_spec) {
+        const unsigned long long n = st->n_out < cap ? st->n_out : cap;
+        go = st->err == 0 && st->n_spill == 0 && !(n > 0 && (double)(long long)n > st->gate_thr);
+    }
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+__global__ void k_gate_set(DevState* st, int spec, double thr) {
+    st->gate_spec = spec;
+    st->gate_thr = thr;
+}
 
 // Before children generation g >= 1: the queue it will spill into starts empty.
 __global__ void k_next_generation(DevState* st, int gen) {
@@ -1007,6 +1026,10 @@ struct pic_ctx {
     DevState* hs = nullptr;
     cudaEvent_t ev_state = nullptr;
     bool spec_off = false;       // pinned memory or the event could not be had
+    bool spec_now = false;       // the solve being enqueued is speculative
+    int gate_spec = 0;           // the gate's settings in DevState (zero at init)
+    double gate_thr = 0.0;
+    cudaStream_t fbody = nullptr;  // records the gated body of the field-solve graph
     cudaGraphExec_t agraph = nullptr;  // the same for axisymmetric contexts (one potential buffer)
     long long agraph_kernels = 0;
     cudaStream_t fcap = nullptr;
@@ -1063,6 +1086,7 @@ struct pic_ctx {
             if (fgraph[q]) cudaGraphExecDestroy(fgraph[q]);
         if (hs) cudaFreeHost(hs);
         if (ev_state) cudaEventDestroy(ev_state);
+        if (fbody) cudaStreamDestroy(fbody);
         if (agraph) cudaGraphExecDestroy(agraph);
         if (fcap) cudaStreamDestroy(fcap);
         amg.release();
@@ -1522,6 +1546,7 @@ static int solve_field_pair_graph(pic_ctx* c) {
     const int slot = c->ph_cur;
     if (!c->fgraph[slot]) {
         if ((!c->fcap && cudaStreamCreateWithFlags(&c->fcap, cudaStreamNonBlocking) != cudaSuccess) ||
+            (!c->fbody && cudaStreamCreateWithFlags(&c->fbody, cudaStreamNonBlocking) != cudaSuccess) ||
             c->mg.prepare_capture() != PIC_OK) {
             cudaGetLastError();
             return PIC_ERR_STATE;
@@ -1530,20 +1555,34 @@ static int solve_field_pair_graph(pic_ctx* c) {
             cudaGetLastError();
             return PIC_ERR_STATE;
         }
-        const double dV = c->g.dx * c->g.dx * c->g.dx;
-        const double scale = kQ / (4294967296.0 * dV) * c->g.dx * c->g.dx / kEps0;
-        k_fixed_to_hrho<<<grid_n(n), 256, 0, c->fcap>>>((const long long*)c->qe(), (const long long*)c->qp(),
-                                                         (const long long*)c->qn(), n, (float)scale, (float*)c->rho());
-        c->mg.extrapolate_pair(c->ph_hi(c->ph_cur), c->ph_lo(c->ph_cur), c->ph_hi(c->ph_prev),
-                               c->ph_lo(c->ph_prev), c->ph_hi(c->ph_free), c->ph_lo(c->ph_free), (int)n, true,
-                               c->fcap);
+        // gate kernel, then the solve as the body of an if node
         DevState* st = c->st();
         long long fixed = 0;
-        const int rc = c->mg.capture_solve_mixed(
-            c->fcap, (const float*)c->rho(), c->ph_hi(c->ph_free), c->ph_lo(c->ph_free), c->ph_hi(c->ph_out),
-            c->ph_lo(c->ph_out), c->g.dx, c->cfg.v_lo, c->cfg.v_hi, c->cfg.v_mask, c->cfg.poisson_rtol,
-            c->cfg.poisson_max_cycles, (float*)c->E4p(c->ph_out), &st->poisson_cycles, &st->poisson_rel, &st->err,
-            kErrPoissonLimit, &st->dev_kernels, &fixed);
+        int rc = PIC_ERR_STATE;
+        const cudaGraph_t top = capturing_graph(c->fcap);
+        cudaGraphConditionalHandle h_go = 0;
+        cudaGraph_t body = nullptr;
+        if (top && cudaGraphConditionalHandleCreate(&h_go, top, 1u, cudaGraphCondAssignDefault) == cudaSuccess) {
+            k_solve_gate<<<1, 1, 0, c->fcap>>>(st, h_go, (unsigned long long)c->cfg.capacity);
+            if (add_conditional(c->fcap, h_go, cudaGraphCondTypeIf, 1, &body) == cudaSuccess &&
+                cudaStreamBeginCaptureToGraph(c->fbody, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+                    cudaSuccess) {
+                const double dV = c->g.dx * c->g.dx * c->g.dx;
+                const double scale = kQ / (4294967296.0 * dV) * c->g.dx * c->g.dx / kEps0;
+                k_fixed_to_hrho<<<grid_n(n), 256, 0, c->fbody>>>((const long long*)c->qe(), (const long long*)c->qp(),
+                                                                  (const long long*)c->qn(), n, (float)scale,
+                                                                  (float*)c->rho());
+                c->mg.extrapolate_pair(c->ph_hi(c->ph_cur), c->ph_lo(c->ph_cur), c->ph_hi(c->ph_prev),
+                                       c->ph_lo(c->ph_prev), c->ph_hi(c->ph_free), c->ph_lo(c->ph_free), (int)n, true,
+                                       c->fbody);
+                rc = c->mg.capture_solve_mixed(
+                    c->fbody, (const float*)c->rho(), c->ph_hi(c->ph_free), c->ph_lo(c->ph_free), c->ph_hi(c->ph_out),
+                    c->ph_lo(c->ph_out), c->g.dx, c->cfg.v_lo, c->cfg.v_hi, c->cfg.v_mask, c->cfg.poisson_rtol,
+                    c->cfg.poisson_max_cycles, (float*)c->E4p(c->ph_out), &st->poisson_cycles, &st->poisson_rel,
+                    &st->err, kErrPoissonLimit, &st->dev_kernels, &fixed);
+                if (end_body_capture(c->fbody) != cudaSuccess) rc = PIC_ERR_STATE;
+            }
+        }
         cudaGraph_t gr = nullptr;
         const cudaError_t e = cudaStreamEndCapture(c->fcap, &gr);
         cudaGraphExec_t gx = nullptr;
@@ -1554,7 +1593,16 @@ static int solve_field_pair_graph(pic_ctx* c) {
         }
         cudaGraphDestroy(gr);
         c->fgraph[slot] = gx;
-        c->fgraph_kernels[slot] = fixed + 2;
+        c->fgraph_kernels[slot] = fixed + 3;
+    }
+    // the gate's settings follow the solve's kind (they change rarely)
+    const int spec = c->spec_now ? 1 : 0;
+    const double thr = c->cfg.growth_trigger > 0 ? c->cfg.growth_trigger * (double)c->n_last_wu : HUGE_VAL;
+    if (spec != c->gate_spec || (spec && thr != c->gate_thr)) {
+        k_gate_set<<<1, 1, 0, c->s>>>(c->st(), spec, spec ? thr : c->gate_thr);
+        c->launches += 1;
+        c->gate_spec = spec;
+        if (spec) c->gate_thr = thr;
     }
     const cudaError_t e = cudaGraphLaunch(c->fgraph[slot], c->s);
     if (e != cudaSuccess) return c->cuda_fail(e, "field solve graph");
@@ -1895,11 +1943,15 @@ template <class T> static int speculative_tail(pic_ctx* c, PushArgs<T>& A, bool 
     const int cycles = c->last_cycles;
     const double rel = c->last_rel;
     c->mark(5);
+    c->spec_now = true;
     rc = solve_field(c);
+    c->spec_now = false;
     if (rc) return rc;
     c->mark(6);
     c->accumulate(5, 6, &c->pt.ms_field, &c->pt.n_field);
     c->pt.n_speculative++;
+    // a graph solve skips its body on the device when the host will undo it
+    const bool gated = c->last_on_device;
     e = cudaEventSynchronize(c->ev_state);
     if (e != cudaSuccess) return c->cuda_fail(e, "state read-back");
     const DevState h = *c->hs;
@@ -1921,8 +1973,12 @@ template <class T> static int speculative_tail(pic_ctx* c, PushArgs<T>& A, bool 
     c->last_on_device = on_device;
     c->last_cycles = cycles;
     c->last_rel = rel;
-    k_clear_err<<<1, 1, 0, c->s>>>(c->st(), kErrPoissonLimit);
-    c->launches += 1;
+    if (gated) {
+        c->launches -= c->fgraph_kernels[slots[0]] - 1;  // only the gate ran
+    } else {
+        k_clear_err<<<1, 1, 0, c->s>>>(c->st(), kErrPoissonLimit);
+        c->launches += 1;
+    }
     c->pt.n_undone++;
     return extra_generations<T>(c, A, MODE_PIC, stats, &h);
 }
