@@ -400,8 +400,9 @@ static int append(orc_parts *p, const double *x, const double *v, const double *
 /* positive ion there and a photoelectron (id derived with tag 0xD0000000|k) */
 /* that joins the electrons at rest after the step.                          */
 /* Pins: the distance distribution against 1 - (E1(a r) - E1(b r))/ln(b/a)    */
-/* (scipy's exponential integral), the emission fraction, isotropy, charge   */
-/* neutrality of each photoionization.                                       */
+/* (scipy's exponential integral), the emission fraction (also at the       */
+/* paper's printed xi and p_q), isotropy, charge neutrality of each         */
+/* photoionization.                                                          */
 /* ------------------------------------------------------------------------ */
 static void photon_draw(const orc_setup *s, uint64_t id, uint32_t step, uint32_t k, int *emit, double *r,
                         double n[3])
