@@ -191,7 +191,12 @@ int pic_set_field(pic_ctx *ctx, const float *Ex, const float *Ey, const float *E
  * the n_steps and synchronises the stream.  Each step reads the device
  * counters once after its collisions (and reports any error flag then);
  * without stats the call returns once the last step's field solve is
- * enqueued. */
+ * enqueued.  Float32 Cartesian coupled contexts enqueue that solve before
+ * the read (the counters are copied to pinned host memory behind an event)
+ * and undo it when the counts call for a weight update or further product
+ * generations: the results are those of the unspeculated order, bit for bit.
+ * A field solve's own error flag (cycle limit) is reported by the next call
+ * that reads the counters. */
 int pic_step(pic_ctx *ctx, int n_steps, pic_step_stats *stats);
 
 /* Coupled solve settings of a live context (Sec. 2.5): the relative residual
