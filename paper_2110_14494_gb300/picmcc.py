@@ -193,6 +193,36 @@ def _stream(stream=None):
     return C.c_void_p(s.cuda_stream)
 
 
+def _host_arrays(arrays, count: int, precision: int, what: str):
+    """Pointers of the 11 host arrays of pic_upload / pic_download (x, y, z,
+    vx, vy, vz, ax, ay, az, w in the context precision, then 64-bit ids),
+    after checking that each is a contiguous host array of that type holding
+    at least `count` entries: the library reads or writes that many through
+    the raw pointers."""
+    if len(arrays) != 11:
+        raise ValueError(f"{what}: 11 arrays expected, got {len(arrays)}")
+    real = np.float32 if precision == 32 else np.float64
+    ptrs = []
+    for i, a in enumerate(arrays):
+        ok_types = (real,) if i < 10 else (np.int64, np.uint64)
+        if hasattr(a, "data_ptr"):  # a torch tensor
+            import torch
+            tmap = {np.float32: torch.float32, np.float64: torch.float64, np.int64: torch.int64,
+                    np.uint64: getattr(torch, "uint64", torch.int64)}
+            good = (a.device.type == "cpu" and a.is_contiguous() and a.dtype in [tmap[t] for t in ok_types]
+                    and a.numel() >= count)
+            ptr = a.data_ptr()
+        else:
+            good = (isinstance(a, np.ndarray) and a.flags.c_contiguous and a.dtype.type in ok_types
+                    and a.size >= count)
+            ptr = a.ctypes.data if isinstance(a, np.ndarray) else 0
+        if not good:
+            kind = "float%d" % precision if i < 10 else "int64/uint64"
+            raise ValueError(f"{what}: array {i} must be a contiguous host {kind} array of at least {count} entries")
+        ptrs.append(ptr)
+    return (VP * 11)(*ptrs)
+
+
 def _workspace(nbytes: int):
     import torch
     t = torch.empty(max(int(nbytes), 256) + 256, dtype=torch.uint8, device="cuda")
@@ -286,6 +316,8 @@ class PicContext:
         n = len(p["x"])
         keep = {k: np.ascontiguousarray(p[k], np.float64) for k in self.FIELDS if k in p}
         ids = np.ascontiguousarray(p["id"], np.uint64)
+        if any(a.shape != (n,) for a in keep.values()) or ids.shape != (n,):
+            raise ValueError("set_particles: every field must be a 1-D array of len(p['x']) entries")
         hp = pic_particles_host(*[keep[k].ctypes.data_as(PD) if k in keep else None for k in self.FIELDS],
                                 ids.ctypes.data_as(PU64))
         _check(lib().pic_set_particles(self.h, n, C.byref(hp), int(accel_valid)), self.h, "pic_set_particles")
@@ -338,11 +370,11 @@ class PicContext:
 
     def upload(self, arrays, n, accel_valid=True):
         """arrays: 11 host tensors/arrays (pinned for asynchronous copies) in native precision."""
-        ptrs = (VP * 11)(*[a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data for a in arrays])
+        ptrs = _host_arrays(arrays, n, self.cfg.precision, "pic_upload")
         _check(lib().pic_upload(self.h, n, ptrs, int(accel_valid)), self.h, "pic_upload")
 
     def download(self, arrays, cap) -> int:
-        ptrs = (VP * 11)(*[a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data for a in arrays])
+        ptrs = _host_arrays(arrays, cap, self.cfg.precision, "pic_download")
         n = C.c_longlong()
         _check(lib().pic_download(self.h, ptrs, cap, C.byref(n)), self.h, "pic_download")
         return n.value

@@ -82,3 +82,26 @@ def test_mlp_host_validation(L):
     assert L.mlp_train(None, None, None, 0, None, None, 64, 1, 1e-3, 0.9, 0.999, 1e-8, None, None, 0, None) == \
         P.PIC_ERR_ARG
     assert L.mlp_forward(None, None, None, 10, None, 0, None) == P.PIC_ERR_ARG
+
+
+def test_host_exchange_arrays_are_checked_before_the_call():
+    """pic_upload / pic_download take raw host pointers: the binding refuses
+    arrays of the wrong type, layout or length before the library sees them."""
+    torch = pytest.importorskip("torch")
+    from paper_2110_14494_gb300 import picmcc as P
+    good32 = [np.zeros(100, np.float32) for _ in range(10)] + [np.zeros(100, np.int64)]
+    assert len(P._host_arrays(good32, 100, 32, "t")) == 11
+    good64 = [torch.zeros(100, dtype=torch.float64) for _ in range(10)] + [torch.zeros(100, dtype=torch.int64)]
+    assert len(P._host_arrays(good64, 80, 64, "t")) == 11
+    bad = [
+        good32[:10],                                                          # 10 arrays
+        [np.zeros(100, np.float64)] + good32[1:],                             # wrong precision
+        good32[:10] + [np.zeros(100, np.int32)],                              # 32-bit ids
+        good32[:3] + [np.zeros(99, np.float32)] + good32[4:],                 # too short
+        good32[:5] + [np.zeros(200, np.float32)[::2]] + good32[6:],           # strided
+        good32[:10] + [[0] * 100],                                            # not an array
+        [torch.zeros(100, dtype=torch.float32)[::1].t() for _ in range(10)] + [torch.zeros(100, dtype=torch.int16)],
+    ]
+    for arrays in bad:
+        with pytest.raises(ValueError):
+            P._host_arrays(arrays, 100, 32, "t")
