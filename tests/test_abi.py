@@ -105,3 +105,38 @@ def test_host_exchange_arrays_are_checked_before_the_call():
     for arrays in bad:
         with pytest.raises(ValueError):
             P._host_arrays(arrays, 100, 32, "t")
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets
+    that a C compiler gives the declaration in include/picmcc.h (a field added
+    on one side only would shift the others)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    import ctypes
+    from paper_2110_14494_gb300 import picmcc as P
+    names = [n for n in dir(P) if isinstance(getattr(P, n), type) and issubclass(getattr(P, n), ctypes.Structure)
+             and n.startswith(("pic_", "poisson_", "swarm_"))]
+    assert len(names) >= 9, names
+    src = ["#include <stdio.h>", "#include <stddef.h>", '#include "picmcc.h"', "int main(void) {"]
+    for s in names:
+        src.append(f'printf("{s} . %zu\\n", sizeof({s}));')
+        for f, _ in getattr(P, s)._fields_:
+            src.append(f'printf("{s} {f} %zu\\n", offsetof({s}, {f}));')
+    src.append("return 0; }")
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(src))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)])
+    got = {}
+    for line in subprocess.check_output([str(exe)]).decode().split("\n"):
+        if line:
+            s, f, v = line.split()
+            got[(s, f)] = int(v)
+    for s in names:
+        cls = getattr(P, s)
+        assert got[(s, ".")] == ctypes.sizeof(cls), s
+        for f, _ in cls._fields_:
+            assert got[(s, f)] == getattr(cls, f).offset, (s, f)
