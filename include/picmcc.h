@@ -16,11 +16,15 @@
  * Conventions for every call:
  *  - Status codes: PIC_OK (0) or a negative PIC_ERR_*; no exception ever
  *    crosses the ABI.  pic_last_error() gives a message for a context.
- *  - Memory: the library never allocates device memory.  The caller passes
- *    one device workspace of the size returned by the matching
- *    *_workspace_bytes() call (alignment 256 bytes) and owns it; all
- *    device-pointer arguments are caller-owned.  Host arrays are read during
- *    the call only.
+ *  - Memory: the library never allocates device memory with the CUDA
+ *    allocator.  The caller passes one device workspace of the size returned
+ *    by the matching *_workspace_bytes() call (alignment 256 bytes) and owns
+ *    it; all device-pointer arguments are caller-owned.  Host arrays are
+ *    read during the call only.  What a context creates for itself and
+ *    releases in pic_destroy: CUDA events, streams used to record CUDA
+ *    graphs, the recorded graphs, and (float32 coupled contexts) one pinned
+ *    host block holding a copy of its device counters.  poisson_solve_noalloc
+ *    uses a fixed device array inside the library (see there).
  *  - Streams: work is enqueued on the stream given at init (or per call);
  *    calls return without waiting unless they return data to the host
  *    (statistics, particle read-back, swarm results), which synchronise that
@@ -149,7 +153,8 @@ typedef struct pic_step_stats {
 
 typedef struct pic_ctx pic_ctx;
 
-/* Workspace size for pic_init. */
+/* Workspace size for pic_init (bytes); 0 when cfg is invalid (a size, the
+ * precision, the gas tables, or a coupled grid the multigrid cannot halve). */
 size_t pic_workspace_bytes(const pic_config *cfg);
 
 /* Creates a context over caller memory.  d_mask: [nz][ny][nx] electrode
@@ -159,8 +164,14 @@ size_t pic_workspace_bytes(const pic_config *cfg);
 int pic_init(const pic_config *cfg, void *d_workspace, size_t workspace_bytes, const uint8_t *d_mask,
              pic_stream_t stream, pic_ctx **out);
 
+/* Releases what the context created (see Memory above); the caller's
+ * workspace and mask are not touched.  NULL is ignored.  Synchronise the
+ * stream first if work of the context may still be running. */
 void pic_destroy(pic_ctx *ctx);
+/* Message of the last failed call on ctx (valid until the next call on
+ * ctx); "null context" for NULL. */
 const char *pic_last_error(const pic_ctx *ctx);
+/* Static text of a status code. */
 const char *pic_status_string(int status);
 
 /* Gaussian neutral seed (Sec. 2.3, Eq. 7 with a negative exponent):
@@ -171,14 +182,28 @@ const char *pic_status_string(int status);
 int pic_seed_gaussian(pic_ctx *ctx, double n0, double radius, const double center[3], double w0,
                       long long *n_out);
 
-/* Replaces the particle set with n host particles (ids must be unique). */
+/* Replaces the particle set with n host particles (float64 arrays of n
+ * entries, converted to the context precision; ids must be unique).
+ * x, y, z, w and id are required; any of vx..az may be NULL (zero).
+ * accel_valid != 0: ax, ay, az hold each particle's a(t) of Eq. 2 and the
+ * first step completes its velocity-Verlet half-kick; 0: the first step
+ * starts from the gathered field without one.  Synchronises.  Errors:
+ * PIC_ERR_ARG (a required array NULL, n < 0), PIC_ERR_CAPACITY
+ * (n > capacity). */
 int pic_set_particles(pic_ctx *ctx, long long n, const pic_particles_host *p, int accel_valid);
 
-/* Copies the particle set to host arrays of at least `cap` entries. */
+/* Copies the particles of positive weight, in buffer order, to float64 host
+ * arrays of at least `cap` entries (NULL arrays are skipped) and writes their
+ * number to n_out; with p == NULL only the number.  Synchronises.  Errors:
+ * PIC_ERR_CAPACITY when there are more than cap (nothing copied). */
 int pic_get_particles(pic_ctx *ctx, pic_particles_host *p, long long cap, long long *n_out);
 
-/* Sets the cell-centred field (V/m) from device arrays [nz][ny][nx] of
- * float; with Ex == NULL the field is uniform and equal to E_uniform. */
+/* Sets the cell-centred field (V/m) that the trilinear gather of Sec. 2.1.3
+ * interpolates, from device arrays [nz][ny][nx] of float; with Ex == NULL
+ * the field is uniform and equal to E_uniform (host, 3 values).  The arrays
+ * are read by stream-ordered work: keep them unchanged until the stream has
+ * passed this call.  Errors: PIC_ERR_ARG (Ey or Ez NULL with Ex set, or no
+ * E_uniform without Ex). */
 int pic_set_field(pic_ctx *ctx, const float *Ex, const float *Ey, const float *Ez, const double E_uniform[3]);
 
 /* Advances all electrons n_steps times (Sec. 2.1): trilinear gather, Verlet
@@ -213,16 +238,22 @@ int pic_step(pic_ctx *ctx, int n_steps, pic_step_stats *stats);
  * rtol must be positive and max_cycles at least 1; errors: PIC_ERR_ARG. */
 int pic_set_poisson(pic_ctx *ctx, double rtol, int max_cycles, int device_loop);
 
-/* Deposits the current electrons and returns the fixed-point grids (units of
+/* Deposits the current electrons (Sec. 2.1.3, cell-centred trilinear
+ * weights in 64-bit fixed point) and returns the fixed-point grids (units of
  * 2^-32 physical particles per cell, int64) and the space charge
- * rho = e (n_pos - n_neg - n_e) in C/m^3.  Any output may be NULL; all are
- * device arrays [nz][ny][nx]. */
+ * rho = e (n_pos - n_neg - n_e) in C/m^3 of Sec. 2.5.  Any output may be
+ * NULL; all are device arrays [nz][ny][nx].  Synchronises and reports device
+ * error flags (PIC_ERR_OVERFLOW for a fixed-point overflow). */
 int pic_deposit(pic_ctx *ctx, int64_t *q_e, int64_t *q_pos, int64_t *q_neg, double *rho);
 
-/* Runs the super-particle weight update now (Sec. 2.1.2, Eq. 3). */
+/* Runs the super-particle weight update now (Sec. 2.1.2, Eq. 3): cell sort,
+ * merge and split, compaction; reads the predicted count back
+ * (synchronises).  Errors: PIC_ERR_CAPACITY when splitting would exceed the
+ * capacity. */
 int pic_weight_update(pic_ctx *ctx);
 
-/* Number of live particles (synchronises). */
+/* Number of particles in the current set, zero-weight slots awaiting
+ * compaction included (synchronises). */
 int pic_count(pic_ctx *ctx, long long *n);
 
 /* Cumulative particle-updates (parents plus queued children advanced), of
@@ -241,20 +272,30 @@ typedef struct pic_profile_times {
 } pic_profile_times;
 
 /* enable != 0 starts timing (cleared); out (optional) receives the
- * accumulated times since the last clear, after which they are cleared. */
+ * accumulated times since the last clear, after which they are cleared.
+ * Synchronises (the phase events are resolved). */
 int pic_profile(pic_ctx *ctx, int enable, pic_profile_times *out);
 
 /* Native-precision particle exchange with host memory (use pinned memory for
  * asynchronous copies): arrays[0..9] = x, y, z, vx, vy, vz, ax, ay, az, w in
  * the context precision (float or double), arrays[10] = uint64 ids.
- * pic_upload replaces the particle set; pic_download writes the current set
- * (including any not-yet-compacted zero-weight slots, which callers skip) and
- * its size, and synchronises. */
+ * pic_upload replaces the particle set with n particles (accel_valid as
+ * for pic_set_particles; errors PIC_ERR_ARG for a null array, PIC_ERR_CAPACITY
+ * for n > capacity); the host arrays are read by stream-ordered copies, so
+ * keep them unchanged until the stream has passed the call.  pic_download
+ * writes the current set (including any not-yet-compacted zero-weight slots,
+ * which callers skip) and its size, and synchronises; PIC_ERR_CAPACITY (with
+ * *n_out set, nothing copied) when the set is larger than cap. */
 int pic_upload(pic_ctx *ctx, long long n, const void *const *arrays, int accel_valid);
 int pic_download(pic_ctx *ctx, void *const *arrays, long long cap, long long *n_out);
 
-/* Checkpoint: the particle set, ion grids, step counter and state flags
- * into a host blob; *bytes in: blob capacity (or 0 to query), out: size. */
+/* Checkpoint (no passage of the paper): the particle set, ion grids,
+ * potential, step counter, time-step state and flags into a host blob;
+ * *bytes in: blob capacity (or 0 to query), out: size; PIC_ERR_CAPACITY when
+ * the blob is too small.  pic_load restores a blob into a context created
+ * with the same precision and grid (PIC_ERR_ARG otherwise); a coupled
+ * context solves for its field again before the next step.  Both
+ * synchronise. */
 int pic_save(pic_ctx *ctx, void *host_blob, size_t *bytes);
 int pic_load(pic_ctx *ctx, const void *host_blob, size_t bytes);
 
@@ -285,6 +326,7 @@ typedef struct poisson_stats {
     double rel_res;
 } poisson_stats;
 
+/* Workspace size for poisson_solve; 0 for unsupported sizes. */
 size_t poisson_workspace_bytes(const poisson_config *pc);
 
 /* rho, mask, phi, Ex, Ey, Ez: device arrays [nz][ny][nx]; phi is the
@@ -364,6 +406,7 @@ typedef struct swarm_result {
     double v[PIC_SWARM_NRES];
 } swarm_result;
 
+/* Workspace size for swarm_run and swarm_autotune; 0 for invalid input. */
 size_t swarm_workspace_bytes(const swarm_config *sc, int n_swarms);
 
 /* Batched mode only: times short trial runs of the batched step for block
