@@ -4,7 +4,8 @@ The local-field fluid model of the paper reads flux transport data versus the
 reduced field (Sec. 2.2.4, computed there by Monte Carlo swarms).  This module
 builds such tables with the library's batched swarms, fits the 2-128-128-6
 network of ``mlp_train`` to them and answers queries with ``mlp_forward``;
-the swarm stays the fallback and the judge of the surrogate's error.
+where the network is not trusted, running a swarm remains the answer and
+the reference its error is measured against.
 
 Inputs: log10(E/N in Td) and the O2 fraction.  Targets: natural logarithms
 of mu N (1/(V m s)), D_L N and D_T N (1/(m s)), max(alpha / N, 1e-25 m^2),

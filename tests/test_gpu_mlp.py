@@ -122,7 +122,7 @@ def test_inference_on_many_points_sampled(variant):
 
 def test_surrogate_gain_over_swarms():
     """The trained surrogate against the method without it.  Training table:
-    batched swarms at 64 E/N values (20-800 Td) x 4 O2 fractions; judge: 12
+    batched swarms at 64 E/N values (20-800 Td) x 4 O2 fractions; held out: 12
     fresh swarms at random (E/N, f) from another seed.  The surrogate must
     (i) predict the well-determined log targets (mu N, D_L N, D_T N, mean
     energy, and alpha / N above 300 Td) of the held-out swarms within their
