@@ -353,8 +353,10 @@ int poisson_axi_solve(int nr, int nz, double dx, double v_lo, double v_hi, doubl
                       void *d_workspace, size_t workspace_bytes, poisson_stats *stats, pic_stream_t stream);
 
 /* Same solve as poisson_solve, for callers that cannot allocate device
- * memory (no workspace argument).  The paper has no counterpart: this is a
- * deployment convenience.  The multigrid scratch is a fixed 32 MiB device
+ * memory (no workspace argument): plugins handed only input and output
+ * pointers by a host application that owns every allocation, and loops that
+ * must not touch an allocator once running.  The paper has no counterpart:
+ * this is a deployment convenience.  The multigrid scratch is a fixed 32 MiB device
  * array inside the library (held on every GPU that loads it until the
  * process exits), enough for grids of up to about 0.95 million cells (96^3
  * fits, 100^3 does not, at either precision); larger grids return
@@ -374,8 +376,10 @@ int poisson_solve_noalloc(const poisson_config *pc, const double *rho, const uin
  * n0 electrons at the origin with Maxwellian velocities at temperature kT,
  * field E = -(E/N) N z-hat, and is advanced n_steps with the same collisions.
  * Weighted moments are accumulated at the end of every step; adaptive
- * resampling keeps counts in [n_lo, n_hi] (thinning with survival 1/2 and
- * doubled weight above, duplication with halved weight below).
+ * resampling keeps counts in [n_lo, n_hi]: above n_hi each electron survives
+ * with probability 1/2, below n_lo every electron is duplicated, and neither
+ * changes any weight (every coefficient is a ratio of sums taken at one step,
+ * in which a common weight factor cancels).
  * Results per swarm (swarm_result.v):
  *   0 W_flux  1 W_bulk  2 DL_flux  3 DT_flux  4 DL_bulk  5 DT_bulk
  *   6 <eps> (eV)  7 k_ion  8 k_att (m^3/s)  9 alpha  10 eta (1/m)

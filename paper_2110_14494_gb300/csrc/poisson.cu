@@ -1223,12 +1223,14 @@ extern "C" int poisson_solve(const poisson_config* pc, const double* rho, const 
 }
 
 // ------------------------------------------------------------------ no-allocation variant
-// Some callers cannot allocate device memory for a workspace: code running
-// where cudaMalloc is not permitted or not wanted (inside a region being
-// captured into a CUDA graph by a framework that forbids allocation, plugins
-// handed only input and output pointers by a host application, or
-// hard-real-time loops that must not touch the allocator).  For them the
-// multigrid hierarchy lives in a fixed device array owned by this library.
+// Some callers cannot allocate device memory for a workspace: plugins that a
+// host application hands only input and output pointers (the application owns
+// every allocation), code that runs under an allocator it may not bypass, and
+// hard-real-time loops that must not touch the allocator once running.  For
+// them the multigrid hierarchy lives in a fixed device array owned by this
+// library.  The solve itself is unchanged: it is poisson_run, as behind
+// poisson_solve, and like it reads the residual back on the host after each
+// iteration.
 //
 // The array is file-scope device memory of kNoAllocScratchBytes (32 MiB), held
 // by every GPU that loads the library until the process exits.  In host code

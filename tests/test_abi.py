@@ -140,3 +140,16 @@ def test_binding_structs_match_the_header(tmp_path):
         assert got[(s, ".")] == ctypes.sizeof(cls), s
         for f, _ in cls._fields_:
             assert got[(s, f)] == getattr(cls, f).offset, (s, f)
+
+
+def test_noalloc_scratch_limit(L):
+    """poisson_solve_noalloc works in a fixed 32 MiB device array: the
+    workspace of a 96^3 solve fits in it and that of a 100^3 solve does not, at
+    every precision (a change to the multigrid layout that moves the limit
+    fails here)."""
+    from paper_2110_14494_gb300 import picmcc as P
+    for prec in (0, 32, 64):
+        for n, fits in ((96, True), (100, False)):
+            pc = P.poisson_config(n, n, n, 1e-5, 0.0, 1.0, 1.0, prec)
+            b = L.poisson_workspace_bytes(C.byref(pc))
+            assert b > 0 and (b <= 32 << 20) == fits, (prec, n, b)
