@@ -1248,12 +1248,25 @@ int orc_swarm_run(const orc_setup *s, const orc_swarm_cfg *c, orc_parts *p, doub
 /* Flux and bulk coefficients from the moment rows (Sec. 2.2.2; flux = mean  */
 /* of per-electron averages, bulk = rate of change of the centre of mass and */
 /* of the spread, rate coefficients = mean over steps of the event weight of */
-/* the step per swarm weight, N and dt).  Rows i0..n_steps-1 are used        */
-/* (earlier ones are relaxation).                                           */
+/* the step per N and per time integral of the swarm weight over the step).  */
+/* Rows i0..n_steps-1 are used (earlier ones are relaxation).               */
 /* out[0..10]  W_flux, W_bulk, DL_flux, DT_flux, DL_bulk, DT_bulk, <eps>,     */
 /*             k_ion, k_att, alpha, eta                                       */
 /* out[11..21] 1-sigma errors by 10-block batch means                        */
 /* Pins: constant-nu closed forms (W = eE/(m nu), D_T = <vx^2>/nu, ...).       */
+/* Time integral of the swarm weight over one step, divided by dt.  Within a */
+/* step only collisions change the weight: it starts at W_end - (ionization */
+/* weight) + (attachment weight) and ends at W_end.  The logarithmic mean of */
+/* the two is exact when the weight grows or decays exponentially over the   */
+/* step (a constant net rate); equal ends give the weight itself.            */
+static double step_mean_weight(const double *m)
+{
+    double w1 = m[0], w0 = m[0] - m[14] + m[15];
+    if (!(w0 > 0.0) || !(w1 > 0.0)) return 0.5 * (w0 + w1);
+    if (fabs(w1 - w0) <= 1e-9 * w1) return 0.5 * (w0 + w1);
+    return (w1 - w0) / log(w1 / w0);
+}
+
 static void coeffs_range(const double *mom, int r0, int r1, double dt, double n_gas, double *o)
 {
     int n = r1 - r0;
@@ -1268,7 +1281,8 @@ static void coeffs_range(const double *mom, int r0, int r1, double dt, double n_
         dlf += m[12] / W - mz * mvz;
         dtf += 0.5 * ((m[10] / W - mx * mvx) + (m[11] / W - my * mvy));
         me += m[13] / W;
-        sion += m[14] / W; satt += m[15] / W; sw += 1.0;
+        double wm = step_mean_weight(m);
+        sion += m[14] / wm; satt += m[15] / wm; sw += 1.0;
         double t = (double)(r + 1) * dt;
         double varz = m[6] / W - mz * mz;
         double vart = (m[4] / W - mx * mx) + (m[5] / W - my * my);

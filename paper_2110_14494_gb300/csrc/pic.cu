@@ -2307,10 +2307,23 @@ extern "C" size_t swarm_workspace_bytes(const swarm_config* sc, int n_swarms) {
     return make_layout(&c).total + swarm_extra(sc);
 }
 
+// Swarm weight integrated over one step, per unit time.  Collisions alone
+// change the weight inside a step, so it began the step at W_end - w_ion +
+// w_att; over the step it is taken as exponential (a constant net rate), whose
+// mean is the logarithmic mean W0 x / ln(1 + x) with x = W_end / W0 - 1.
+static double step_weight_integral(const double* m) {
+    const double w_end = m[0];
+    const double w0 = w_end - m[14] + m[15];
+    if (!(w0 > 0.0) || !(w_end > 0.0)) return 0.5 * (w0 + w_end);
+    const double x = w_end / w0 - 1.0;
+    if (fabs(x) < 1e-9) return 0.5 * (w0 + w_end);
+    return w0 * x / log1p(x);
+}
+
 // Flux = time average of per-step electron averages; bulk = least-squares
 // slopes of the centre of mass and of the spread; rate coefficients = time
-// average of (event weight of the step) / (N dt swarm weight); errors from
-// 10-block batch means.
+// average of (event weight of the step) / (N x the step's integral of the
+// swarm weight over time); errors from 10-block batch means.
 static void swarm_coeffs(const double* mom, int r0, int r1, double dt, double n_gas, double* o) {
     const int n = r1 - r0;
     double wf = 0, dlf = 0, dtf = 0, me = 0, sion = 0, satt = 0, sw = 0;
@@ -2324,8 +2337,9 @@ static void swarm_coeffs(const double* mom, int r0, int r1, double dt, double n_
         dlf += m[12] / W - mz * vz;
         dtf += 0.5 * ((m[10] / W - mx * vx) + (m[11] / W - my * vy));
         me += m[13] / W;
-        sion += m[14] / W;
-        satt += m[15] / W;
+        const double Wt = step_weight_integral(m);
+        sion += m[14] / Wt;
+        satt += m[15] / Wt;
         sw += 1.0;
         const double t = (double)(r + 1) * dt;
         const double varz = m[6] / W - mz * mz;
