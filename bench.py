@@ -89,6 +89,31 @@ def workload(n_cells=128, n_initial=1_000_000):
     return wl
 
 
+def streamer_context(wl, precision=32, capacity=None, seed=2110144940, boundary=1, adaptive_dt=True, extra=None):
+    """The coupled streamer context the benchmark times (weight update on
+    1.25x growth, cell sort every 20 steps, Poisson every step at rtol 1e-6,
+    CFL 0.5 / dielectric relaxation / 20 % growth time-step control); the
+    parity tests build theirs with this too."""
+    import workloads as W
+    from paper_2110_14494_gb300 import PicContext
+    g = wl["grid"]
+    gas = W.synthetic_air()
+    axi = bool(extra and extra.get("geometry") == 1)
+    mask = (W.needle_mask_axi if axi else W.needle_mask)(g, wl["needle_length"], wl["needle_radius"])
+    cap = capacity or int(wl["particle_cap"] * 1.6)
+    return PicContext(gas, g, precision=precision, capacity=cap, seed=seed, dt=wl["dt"], mask=mask,
+                      n_ppc=wl["n_ppc"], w_min=wl["w_min"], growth_trigger=wl["growth_trigger"],
+                      particle_cap=wl["particle_cap"], sort_interval=20, coupled=True, v_lo=wl["v_bottom"],
+                      boundary=boundary, adaptive_dt=adaptive_dt, cfl=0.5, mobility=0.06, max_growth=1.2,
+                      v_hi=wl["v_top"], v_mask=wl["v_top"], poisson_rtol=1e-6, poisson_max_cycles=200,
+                      **(extra or {}))
+
+
+def seed_weight(wl):
+    """Uniform seed weight: the Gaussian's electron count over the initial super-particles."""
+    return wl["w0"] if "w0" in wl else wl["seed_n0"] * np.pi ** 1.5 * wl["seed_radius"] ** 3 / wl["n_initial"]
+
+
 def aggregate(ms: float, updates: float, dist=None, device="cpu"):
     """Whole-job figures of N replicas: the slowest rank's time and the sum of
     all ranks' particle-updates (weak scaling: every rank runs its own
@@ -427,8 +452,6 @@ def main():
     else:
         wl = workload(args.grid, args.n_initial)
     g = wl["grid"]
-    gas = W.synthetic_air()
-    mask = (W.needle_mask_axi if axi else W.needle_mask)(g, wl["needle_length"], wl["needle_radius"])
     if full or axi or args.grid == 128:
         cap = args.cap or int(wl["particle_cap"] * 1.6)
     else:
@@ -436,14 +459,9 @@ def main():
     photo = dict(photo_xi=wl["photo_xi"], photo_pq=wl["photo_pq"]) if (full or axi) else {}
     if axi:
         photo.update(geometry=1, weight_interval=wl["weight_interval"])
-    w0 = wl["w0"] if axi else wl["seed_n0"] * np.pi ** 1.5 * wl["seed_radius"] ** 3 / wl["n_initial"]
-    ctx = PicContext(gas, g, precision=args.precision, capacity=cap, seed=2110144940 + rank, dt=wl["dt"],
-                     mask=mask, n_ppc=wl["n_ppc"], w_min=wl["w_min"], growth_trigger=wl["growth_trigger"],
-                     particle_cap=wl["particle_cap"], sort_interval=20, coupled=True, v_lo=wl["v_bottom"],
-                     boundary=args.boundary, adaptive_dt=not args.fixed_dt, cfl=0.5, mobility=0.06,
-                     max_growth=1.2,
-                     v_hi=wl["v_top"], v_mask=wl["v_top"], poisson_rtol=1e-6, poisson_max_cycles=200, **photo)
-    n0 = ctx.seed_gaussian(wl["seed_n0"], wl["seed_radius"], wl["seed_center"], w0)
+    ctx = streamer_context(wl, args.precision, cap, 2110144940 + rank, boundary=args.boundary,
+                           adaptive_dt=not args.fixed_dt, extra=photo)
+    n0 = ctx.seed_gaussian(wl["seed_n0"], wl["seed_radius"], wl["seed_center"], seed_weight(wl))
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):

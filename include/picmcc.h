@@ -246,6 +246,26 @@ int pic_set_poisson(pic_ctx *ctx, double rtol, int max_cycles, int device_loop);
  * error flags (PIC_ERR_OVERFLOW for a fixed-point overflow). */
 int pic_deposit(pic_ctx *ctx, int64_t *q_e, int64_t *q_pos, int64_t *q_neg, double *rho);
 
+/* Copies the fixed-point grids as the last step left them, without a new
+ * deposit: q_e is the electron deposit the step's own kernels made at its end
+ * (Sec. 2.1.3; made again after a weight update), which is the charge a
+ * coupled solve used for the next field, and q_pos, q_neg are the ion grids.
+ * Device arrays [nz][ny][nx] of int64 (units of 2^-32 particles), any may be
+ * NULL.  Stream-ordered, does not synchronise.  Before the first step q_e
+ * holds whatever the last pic_deposit (or nothing: zeros) left. */
+int pic_get_deposit(pic_ctx *ctx, int64_t *q_e, int64_t *q_pos, int64_t *q_neg);
+
+/* Copies the cell-centred field (V/m) that the next step's trilinear gather
+ * (Sec. 2.1.3) reads into device float64 arrays [nz][ny][nx] (exact: the
+ * field is held in the context precision): the one given to pic_set_field,
+ * or in a coupled context the one solved from the charge of the last step
+ * (Sec. 2.5); pic_step with 0 steps makes a coupled context solve its first
+ * field.  Axisymmetric contexts give E_r, 0, E_z on [nz][1][nx].  Any output
+ * may be NULL.  Stream-ordered, does not synchronise.  Errors:
+ * PIC_ERR_STATE when the context has no field grid (none set yet, or a
+ * uniform field). */
+int pic_get_field(pic_ctx *ctx, double *Ex, double *Ey, double *Ez);
+
 /* Runs the super-particle weight update now (Sec. 2.1.2, Eq. 3): cell sort,
  * merge and split, compaction; reads the predicted count back
  * (synchronises).  Errors: PIC_ERR_CAPACITY when splitting would exceed the

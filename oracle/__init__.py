@@ -55,7 +55,8 @@ class Setup(C.Structure):
                 ("dx", C.c_double), ("ox", C.c_double), ("oy", C.c_double), ("oz", C.c_double),
                 ("mask", PU8), ("Ex", PF), ("Ey", PF), ("Ez", PF), ("E0", C.c_double * 3),
                 ("boundary", C.c_int), ("photo_prob", C.c_double), ("chi_a", C.c_double),
-                ("chi_b", C.c_double), ("axi", C.c_int)]
+                ("chi_b", C.c_double), ("axi", C.c_int), ("Ex64", PD), ("Ey64", PD), ("Ez64", PD),
+                ("dt_kick", C.c_double)]
 
 
 class Parts(C.Structure):
@@ -171,8 +172,11 @@ class Model:
     """Holds an orc_setup and the arrays it points to."""
 
     def __init__(self, gas: dict, dt: float, seed: int, prec: int = 64, grid: dict | None = None,
-                 field=None, E0=(0.0, 0.0, 0.0), mask=None, boundary: int = 0, photo=None, axi: bool = False):
-        """photo: None, or dict(xi, pq, pressure, p_o2, chi_min, chi_max) (Pa and 1/(m Pa))."""
+                 field=None, E0=(0.0, 0.0, 0.0), mask=None, boundary: int = 0, photo=None, axi: bool = False,
+                 dt_kick: float = 0.0):
+        """photo: None, or dict(xi, pq, pressure, p_o2, chi_min, chi_max) (Pa and 1/(m Pa)).
+        field: three [nz][ny][nx] arrays, float32 or float64 (all the same type).
+        dt_kick: length of the half-kick completing the previous step's Eq. 2 (0 = dt)."""
         self.gas = gas
         self.nu, self.nu_max = rate_table(gas)
         self._keep = [np.ascontiguousarray(gas["eps"], np.float64), self.nu,
@@ -193,9 +197,15 @@ class Model:
             self._keep.append(m)
             s.mask = _p(m, PU8)
         if field is not None:
-            fs = [np.ascontiguousarray(f, np.float32) for f in field]
-            self._keep += fs
-            s.Ex, s.Ey, s.Ez = (_p(f, PF) for f in fs)
+            if all(np.asarray(f).dtype == np.float64 for f in field):
+                fs = [np.ascontiguousarray(f, np.float64) for f in field]
+                self._keep += fs
+                s.Ex64, s.Ey64, s.Ez64 = (_p(f, PD) for f in fs)
+            else:
+                fs = [np.ascontiguousarray(f, np.float32) for f in field]
+                self._keep += fs
+                s.Ex, s.Ey, s.Ez = (_p(f, PF) for f in fs)
+        s.dt_kick = dt_kick
         s.E0[0], s.E0[1], s.E0[2] = E0
         s.boundary = boundary
         s.axi = int(axi)

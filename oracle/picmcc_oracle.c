@@ -113,6 +113,12 @@ typedef struct orc_setup {
      * from the axis x = y = 0 (ny = 1); the field arrays hold E_r (Ex) and
      * E_z (Ez) */
     int axi;
+    /* the same field in float64 (used instead of Ex, Ey, Ez when set) */
+    const double *Ex64, *Ey64, *Ez64;
+    /* length of the velocity-Verlet half-kick that completes Eq. 2 for the
+     * previous step: that step's dt, which differs from dt when the time step
+     * changes between steps (Sec. 2.1.4); 0 = dt */
+    double dt_kick;
 } orc_setup;
 
 typedef struct orc_parts {
@@ -182,6 +188,13 @@ static void rates_at(const orc_setup *s, double e, double *out, long long *clamp
 /* s = (x - origin)/dx - 1/2, clamped to [0, n-1] per axis.                   */
 /* Pin: a linear field is reproduced exactly inside the grid.               */
 /* ------------------------------------------------------------------------ */
+/* field value d at cell idx, from whichever precision was given */
+static double field_at(const orc_setup *s, int d, long long idx)
+{
+    if (s->Ex64) return (d == 0 ? s->Ex64 : (d == 1 ? s->Ey64 : s->Ez64))[idx];
+    return (double)(d == 0 ? s->Ex : (d == 1 ? s->Ey : s->Ez))[idx];
+}
+
 static void axis_interp(double x, double o, double dx, int n, int *i0, int *i1, double *f)
 {
     double s = (x - o) / dx - 0.5;
@@ -210,8 +223,8 @@ static void gather_axi(const orc_setup *s, double x, double y, double z, double 
     for (int c = 0; c < 4; ++c) {
         int dz = c >> 1, dr = c & 1;
         long long idx = (long long)iz[dz] * s->nx + ir[dr];
-        er += (gz[dz] * gr[dr]) * (double)s->Ex[idx];
-        ez += (gz[dz] * gr[dr]) * (double)s->Ez[idx];
+        er += (gz[dz] * gr[dr]) * field_at(s, 0, idx);
+        ez += (gz[dz] * gr[dr]) * field_at(s, 2, idx);
     }
     double inv = r > 0.0 ? er / r : 0.0;
     E[0] = inv * x;
@@ -221,7 +234,7 @@ static void gather_axi(const orc_setup *s, double x, double y, double z, double 
 
 static void gather(const orc_setup *s, double x, double y, double z, double E[3])
 {
-    if (s->Ex == NULL) { E[0] = s->E0[0]; E[1] = s->E0[1]; E[2] = s->E0[2]; return; }
+    if (s->Ex == NULL && s->Ex64 == NULL) { E[0] = s->E0[0]; E[1] = s->E0[1]; E[2] = s->E0[2]; return; }
     if (s->axi) { gather_axi(s, x, y, z, E); return; }
     int ix[2], iy[2], iz[2];
     double fx, fy, fz;
@@ -229,13 +242,12 @@ static void gather(const orc_setup *s, double x, double y, double z, double E[3]
     axis_interp(y, s->oy, s->dx, s->ny, &iy[0], &iy[1], &fy);
     axis_interp(z, s->oz, s->dx, s->nz, &iz[0], &iz[1], &fz);
     double gx[2] = {1.0 - fx, fx}, gy[2] = {1.0 - fy, fy}, gz[2] = {1.0 - fz, fz};
-    const float *F[3] = {s->Ex, s->Ey, s->Ez};
     for (int d = 0; d < 3; ++d) {
         double acc = 0.0;
         for (int c = 0; c < 8; ++c) {
             int dz = c >> 2, dy = (c >> 1) & 1, dxx = c & 1;
             long long idx = ((long long)iz[dz] * s->ny + iy[dy]) * s->nx + ix[dxx];
-            acc += ((gz[dz] * gy[dy]) * gx[dxx]) * (double)F[d][idx];
+            acc += ((gz[dz] * gy[dy]) * gx[dxx]) * field_at(s, d, idx);
         }
         E[d] = acc;
     }
@@ -629,6 +641,7 @@ int orc_step(const orc_setup *s, orc_parts *p, uint32_t step, int first, int64_t
     }
     int rc = 0;
     const double qm = Q_E / M_ELEC;
+    const double kick = s->dt_kick > 0.0 ? s->dt_kick : s->dt;
     for (long long i = 0; i < n0; ++i) {
         if (p->w[i] <= 0.0) continue;
         double E[3];
@@ -637,7 +650,7 @@ int orc_step(const orc_setup *s, orc_parts *p, uint32_t step, int first, int64_t
         double *ao[3] = {&p->ax[i], &p->ay[i], &p->az[i]};
         double *vv[3] = {&p->vx[i], &p->vy[i], &p->vz[i]};
         for (int d = 0; d < 3; ++d) {
-            if (!first) *vv[d] = *vv[d] + 0.5 * s->dt * (an[d] - *ao[d]);
+            if (!first) *vv[d] = *vv[d] + 0.5 * kick * (an[d] - *ao[d]);
             *ao[d] = an[d];
         }
         int r = advance(s, p, i, s->dt, step, tl, q_pos, q_neg, st, phb ? &ph : NULL);

@@ -158,4 +158,22 @@ template <class T> __device__ __forceinline__ T dmax(T a, T b) { return a > b ? 
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
+// Streaming multiprocessors of the current device, queried once per device
+// (launch shapes are sized in multiples of it).  A failed query gives 1: the
+// grids stay correct, only smaller.
+inline int device_sms() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) { cudaGetLastError(); dev = 0; }
+    if (cache[dev] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = 1;
+        }
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
+
 }  // namespace pic

@@ -108,7 +108,8 @@ static cudaError_t scan_exclusive(const uint32_t* in, uint32_t* out, long long n
     return cudaGetLastError();
 }
 
-static int grid_n(long long n, int cap_blocks = 152 * 16) {
+static int grid_n(long long n, int cap_blocks = 0) {
+    if (cap_blocks <= 0) cap_blocks = device_sms() * 16;
     long long b = (n + 255) / 256;
     if (b > cap_blocks) b = cap_blocks;
     return b < 1 ? 1 : (int)b;
@@ -1526,6 +1527,40 @@ extern "C" int pic_set_field(pic_ctx* c, const float* Ex, const float* Ey, const
     return e == cudaSuccess ? PIC_OK : c->cuda_fail(e, "set field");
 }
 
+// Unpacks the packed field [n][4] (context precision) into float64 planes.
+template <class T>
+__global__ void k_unpack_field(const T* __restrict__ E4, long long n, double* __restrict__ Ex, double* __restrict__ Ey,
+                               double* __restrict__ Ez) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        if (Ex) Ex[c] = (double)E4[4 * c];
+        if (Ey) Ey[c] = (double)E4[4 * c + 1];
+        if (Ez) Ez[c] = (double)E4[4 * c + 2];
+    }
+}
+
+extern "C" int pic_get_field(pic_ctx* c, double* Ex, double* Ey, double* Ez) {
+    if (!c) return PIC_ERR_ARG;
+    if (!c->field_valid || c->field_uniform)
+        return c->fail(PIC_ERR_STATE, "no field grid: set one, or step a coupled context (or call pic_step with 0 steps)");
+    const long long n = c->g.ncell();
+    if (c->prec == 32)
+        k_unpack_field<float><<<grid_n(n), 256, 0, c->s>>>((const float*)c->E4p(c->ph_cur), n, Ex, Ey, Ez);
+    else
+        k_unpack_field<double><<<grid_n(n), 256, 0, c->s>>>((const double*)c->E4p(c->ph_cur), n, Ex, Ey, Ez);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PIC_OK : c->cuda_fail(e, "get field");
+}
+
+extern "C" int pic_get_deposit(pic_ctx* c, int64_t* q_e, int64_t* q_pos, int64_t* q_neg) {
+    if (!c) return PIC_ERR_ARG;
+    const size_t n = (size_t)c->g.ncell();
+    cudaError_t e = cudaSuccess;
+    if (q_e) e = cudaMemcpyAsync(q_e, c->qe(), n * 8, cudaMemcpyDeviceToDevice, c->s);
+    if (e == cudaSuccess && q_pos) e = cudaMemcpyAsync(q_pos, c->qp(), n * 8, cudaMemcpyDeviceToDevice, c->s);
+    if (e == cudaSuccess && q_neg) e = cudaMemcpyAsync(q_neg, c->qn(), n * 8, cudaMemcpyDeviceToDevice, c->s);
+    return e == cudaSuccess ? PIC_OK : c->cuda_fail(e, "deposit copy");
+}
+
 static void fixed_to_rho(pic_ctx* c, double* rho) {
     const long long n = c->g.ncell();
     // cell volume dx^3, or pi dx^3 times (2i + 1) for the ring cells of an axisymmetric grid
@@ -1792,11 +1827,11 @@ template <class T> static int weight_update(pic_ctx* c) {
     // cells with up to kWarpSort merge candidates take one warp each; the
     // others are listed (in the key array, free after the sort) for one block each
     uint32_t* big = (uint32_t*)(c->ws + c->L.key);
-    k_merge_split_warp<T><<<152 * 4, 256, 0, c->s>>>(c->soa<T>(c->cur), n, start, occ_list, c->cfg.n_ppc,
+    k_merge_split_warp<T><<<device_sms() * 4, 256, 0, c->s>>>(c->soa<T>(c->cur), n, start, occ_list, c->cfg.n_ppc,
                                                       c->cfg.w_min, scale, c->K, c->step, c->cfg.capacity, big,
                                                       c->st());
     cudaFuncSetAttribute(k_merge_split<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMergeSmem);
-    k_merge_split<T><<<152 * 2, 256, kMergeSmem, c->s>>>(c->soa<T>(c->cur), n, start, ncell, c->cfg.n_ppc,
+    k_merge_split<T><<<device_sms() * 2, 256, kMergeSmem, c->s>>>(c->soa<T>(c->cur), n, start, ncell, c->cfg.n_ppc,
                                                           c->cfg.w_min, scale, c->msc(), c->K, c->step,
                                                           c->cfg.capacity, big, c->st());
     rc = read_state(c, &h);
@@ -1856,14 +1891,14 @@ static void next_dt(pic_ctx* c, const DevState& h) {
 // time-step statistics of the particles are formed (adaptive dt).
 template <class T> static int generation_tail(pic_ctx* c, PushArgs<T>& A, int mode) {
     if (A.cap_photo > 0) {
-        cudaError_t e = PushLaunch<T>::photo_append(A, 152 * 2, c->s);
+        cudaError_t e = PushLaunch<T>::photo_append(A, device_sms() * 2, c->s);
         if (e != cudaSuccess) return c->cuda_fail(e, "photoelectrons");
         c->launches += 3;
     }
     if (c->cfg.adaptive_dt && mode == MODE_PIC) {
         DevState* st = c->st();
         cudaMemsetAsync(&st->qe_max, 0, sizeof(long long) + sizeof(unsigned long long) + sizeof(st->vhist), c->s);
-        k_step_stats<T><<<152 * 4, 256, 0, c->s>>>(A.out, st, c->qe(), c->g.ncell(), c->g.axi ? c->g.nx : 0, st);
+        k_step_stats<T><<<device_sms() * 4, 256, 0, c->s>>>(A.out, st, c->qe(), c->g.ncell(), c->g.axi ? c->g.nx : 0, st);
         c->launches += 1;
     }
     return PIC_OK;

@@ -97,7 +97,7 @@ template <class T> cudaError_t BatchLaunch<T>::init(const BatchArgs<T>& B, long 
     k_batch_init<T><<<1, 1024, 0, s>>>(B, n0);
     const long long total = (long long)B.n_swarms * n0;
     long long g = (total + 255) / 256;
-    if (g > 152 * 16) g = 152 * 16;
+    if (g > device_sms() * 16) g = device_sms() * 16;
     k_batch_seed<T><<<(int)(g < 1 ? 1 : g), 256, 0, s>>>(B, n0, sig);
     return cudaGetLastError();
 }
@@ -116,7 +116,7 @@ template <class T>
 cudaError_t BatchLaunch<T>::step(BatchArgs<T> B, int block, int grid, cudaStream_t s, long long* launches) {
     constexpr bool FAST = sizeof(T) == 4;
     const size_t sm = smem(block);
-    k_batch_resample<T><<<152 * 8, 256, 0, s>>>(B);
+    k_batch_resample<T><<<device_sms() * 8, 256, 0, s>>>(B);
     k_batch_begin<T><<<1, 1024, 0, s>>>(B);
     B.gen = 0;
     k_batch_collide<T, FAST, false><<<grid, block, sm, s>>>(B);

@@ -104,7 +104,7 @@ class swarm_result(C.Structure):
 EXPORTS = ("pic_workspace_bytes", "pic_init", "pic_destroy", "pic_last_error", "pic_status_string",
            "pic_seed_gaussian", "pic_set_particles", "pic_get_particles", "pic_set_field", "pic_step",
            "pic_deposit", "pic_weight_update", "pic_count", "pic_save", "pic_load", "pic_progress",
-           "pic_profile", "pic_upload", "pic_download", "pic_set_poisson",
+           "pic_profile", "pic_upload", "pic_download", "pic_set_poisson", "pic_get_field", "pic_get_deposit",
            "poisson_workspace_bytes", "poisson_solve", "poisson_solve_noalloc", "swarm_workspace_bytes",
            "swarm_run", "swarm_autotune", "mlp_workspace_bytes", "mlp_forward", "mlp_forward_variant", "mlp_loss_grad",
            "mlp_train", "poisson_axi_workspace_bytes", "poisson_axi_solve")
@@ -137,6 +137,8 @@ def lib():
     L.pic_step.argtypes = [VP, C.c_int, P(pic_step_stats)]
     L.pic_set_poisson.argtypes = [VP, C.c_double, C.c_int, C.c_int]
     L.pic_deposit.argtypes = [VP, VP, VP, VP, VP]
+    L.pic_get_deposit.argtypes = [VP, VP, VP, VP]
+    L.pic_get_field.argtypes = [VP, VP, VP, VP]
     L.pic_weight_update.argtypes = [VP]
     L.pic_count.argtypes = [VP, P(C.c_longlong)]
     L.pic_save.argtypes = [VP, VP, P(C.c_size_t)]
@@ -342,6 +344,19 @@ class PicContext:
 
     def deposit(self, q_e=None, q_pos=None, q_neg=None, rho=None):
         _check(lib().pic_deposit(self.h, _ptr(q_e), _ptr(q_pos), _ptr(q_neg), _ptr(rho)), self.h, "pic_deposit")
+
+    def get_deposit(self, q_e=None, q_pos=None, q_neg=None):
+        """The fixed-point grids as the last step left them (int64 CUDA tensors), no new deposit."""
+        _check(lib().pic_get_deposit(self.h, _ptr(q_e), _ptr(q_pos), _ptr(q_neg)), self.h, "pic_get_deposit")
+
+    def get_field(self, Ex=None, Ey=None, Ez=None):
+        """The field the next gather reads, into float64 CUDA tensors [nz][ny][nx] (new ones if none given)."""
+        import torch
+        if Ex is None and Ey is None and Ez is None:
+            shape = (self.grid["nz"], self.grid["ny"], self.grid["nx"])
+            Ex, Ey, Ez = (torch.empty(shape, dtype=torch.float64, device="cuda") for _ in range(3))
+        _check(lib().pic_get_field(self.h, _ptr(Ex), _ptr(Ey), _ptr(Ez)), self.h, "pic_get_field")
+        return Ex, Ey, Ez
 
     def weight_update(self):
         _check(lib().pic_weight_update(self.h), self.h, "pic_weight_update")

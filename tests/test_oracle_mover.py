@@ -94,3 +94,47 @@ def test_specular_reflection_at_faces():
     assert np.isclose(v["x"][0], 0.5e-4, rtol=1e-12) and v["vx"][0] == 1e7
     # y: 3.9e-4 + 0.2e-4 = 4.1e-4 -> 2L - y = 3.9e-4
     assert np.isclose(v["y"][0], 2 * L - 4.1e-4, rtol=1e-12) and v["vy"][0] == -2e6
+
+
+def test_gather_of_a_float64_field_is_exact_for_a_linear_field():
+    """The same gather from float64 nodes: a linear field is reproduced to
+    rounding (no float32 node error left)."""
+    grid = W.grid_spec(6, 5, 7, 1e-4, origin=(1e-4, -2e-4, 3e-4))
+    G = np.array([[1e8, -2e8, 3e8], [0.5e8, 1e8, -1e8], [2e8, 0.0, 1e8]])
+    c0 = np.array([1e4, -3e4, 2e4])
+    z, y, x = np.meshgrid(*(grid["origin"][d] + (np.arange(n) + 0.5) * grid["dx"]
+                            for d, n in ((2, 7), (1, 5), (0, 6))), indexing="ij")
+    F = tuple(np.ascontiguousarray(c0[d] + G[d][0] * x + G[d][1] * y + G[d][2] * z) for d in range(3))
+    m = O.Model(W.zero_gas(), 1e-12, 1, 64, grid, F)
+    rng = np.random.default_rng(1)
+    lo = np.array(grid["origin"]) + 0.5 * grid["dx"]
+    hi = np.array(grid["origin"]) + (np.array([6, 5, 7]) - 0.5) * grid["dx"]
+    X = lo + (hi - lo) * rng.random((200, 3))
+    E = O.gather_field(m, X[:, 0], X[:, 1], X[:, 2])
+    Ee = c0 + X @ G.T
+    assert np.allclose(E, Ee, rtol=1e-13, atol=1e-13 * np.abs(Ee).max())
+
+
+def test_verlet_half_kick_uses_the_previous_steps_length():
+    """Eq. 2 over a step of length dt1 followed by one of dt2: the correction at
+    the start of the second step is dt1/2 (a(t) + a(t + dt1)) - dt1 a(t), then
+    the second flight adds dt2 a(t + dt1)."""
+    g = W.zero_gas()
+    grid = W.grid_spec(4, 4, 4, 1e-3)
+    dt1, dt2 = 1e-11, 0.6e-11
+    E1 = tuple(np.full((4, 4, 4), v, np.float32) for v in (2e5, -1e5, 5e4))
+    E2 = tuple((f * np.float32(-3.0)).astype(np.float32) for f in E1)
+    p0 = W.random_particles(20, grid, 2, vmax=1e4, box=([1.5e-3] * 3, [2.5e-3] * 3))
+    p = O.Particles(40, p0)
+    O.step(O.Model(g, dt1, 3, 64, grid, E1), p, 1, True)
+    O.step(O.Model(g, dt2, 3, 64, grid, E2, dt_kick=dt1), p, 2, False)
+    v = p.view()
+    a1 = -QM * np.array([float(f[0, 0, 0]) for f in E1])
+    a2 = -QM * np.array([float(f[0, 0, 0]) for f in E2])
+    for d, (xk, vk) in enumerate((("x", "vx"), ("y", "vy"), ("z", "vz"))):
+        x1 = p0[xk] + dt1 * p0[vk] + 0.5 * dt1 * dt1 * a1[d]
+        v1 = p0[vk] + 0.5 * dt1 * (a1[d] + a2[d])
+        x2 = x1 + dt2 * v1 + 0.5 * dt2 * dt2 * a2[d]
+        v2 = v1 + dt2 * a2[d]
+        assert np.allclose(v[xk], x2, rtol=1e-12, atol=1e-18)
+        assert np.allclose(v[vk], v2, rtol=1e-12, atol=1e-9)
