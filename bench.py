@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = "electron push+MCC+deposit particle-updates/s on 1 GB300; % of HBM roofline"
 UNIT = "particle-updates/s"
 BYTES_PER_UPDATE = 96          # float32 state x,v,a,w (40 B) + id (8 B), read and written
+BYTES_PER_CHILD = 48           # an ionization product is born in registers: its state is written once
 WORKLOAD = "streamer-128^3-fp32"
 # DRAM bytes (read + write) per parent of the collision kernel in this workload's steady state, from the
 # ncu capture summarised in profiles/k_push_streamer128.md (49.1 MB per launch of ~8.4e5 parents); scaled
@@ -45,7 +46,12 @@ PUSH_DRAM_BYTES_PER_PARENT = 61.9
 # (4.191e8 / (1.890e6 x 9.985)).
 PUSH_WARP_INST_PER_DRAW = 22.2
 ISSUE_SLOTS_PER_SM = 4   # warp schedulers per SM, one warp instruction each per clock
-N_SMS = 152
+
+
+def n_sms():
+    """Streaming multiprocessors of the current CUDA device."""
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
 
 
 def parse():
@@ -69,7 +75,8 @@ def parse():
                     help="streamer: the coupled 128^3 step (headline); swarms: 256 batched swarms")
     ap.add_argument("--swarm-block", type=int, default=0, help="batched swarms: block size (0 = autotune)")
     ap.add_argument("--swarm-bps", type=int, default=0, help="batched swarms: blocks per SM (0 = autotune)")
-    ap.add_argument("--no-f64", action="store_true", help="batched swarms: skip the float64 comparison")
+    ap.add_argument("--no-f64", action="store_true",
+                    help="skip the float64 comparison (streamer: the float64 arm; batched swarms: the plain path)")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="after the timed steps, run this many more inside an NVTX range named 'prof' "
                          "(untimed; for ncu --nvtx --nvtx-include prof/)")
@@ -114,6 +121,102 @@ def seed_weight(wl):
     return wl["w0"] if "w0" in wl else wl["seed_n0"] * np.pi ** 1.5 * wl["seed_radius"] ** 3 / wl["n_initial"]
 
 
+def grid_bytes_per_step(g, real_bytes):
+    """Grid bytes the step must move once: the three field components read by
+    the gather and the three int64 deposit grids (electrons, positive and
+    negative ions)."""
+    ncell = g["nx"] * g["ny"] * g["nz"]
+    return ncell * (3 * real_bytes + 3 * 8)
+
+
+def timed_steps(ctx, args, stream, flush, local, rank, dist=None, label=""):
+    """W untimed steps, then K steps each bracketed by CUDA events on the
+    context stream, the L2 flushed before each outside the events; clocks
+    sampled meanwhile.  Returns the summed milliseconds, phase profile,
+    clocks, particle counts every 25 steps and the progress counters."""
+    import torch
+    for _ in range(args.warmup):
+        ctx.step(1)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    u0, p0, s0 = ctx.progress()
+    ctx.profile(True)
+    clocks = Clocks(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    n_trace, recent_n = [], []
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i & 0xff)
+        ev[i][0].record(stream)
+        try:
+            st = ctx.step(1, stats=args.trace)
+        except Exception:
+            print(json.dumps({"failed_at_step": i, "arm": label, "recent": recent_n[-40:]}), file=sys.stderr,
+                  flush=True)
+            raise
+        ev[i][1].record(stream)
+        if args.trace:
+            recent_n.append((i, st.n_start, st.n_end, st.n_children, st.n_weight_updates, st.n_absorbed,
+                             st.poisson_cycles, round(st.dt_last * 1e12, 4), "%.3g" % st.ne_max))
+        if i % 25 == 0:
+            n_trace.append(ctx.count())
+        if (i + 1) % 200 == 0 and rank == 0:
+            torch.cuda.synchronize()
+            recent = sum(a.elapsed_time(b) for a, b in ev[i - 199:i + 1])
+            print(json.dumps({"progress": i + 1, "arm": label, "n": n_trace[-1], "ms_last_200": round(recent, 2),
+                              "wall_s": round(time.perf_counter() - t_wall, 2)}), file=sys.stderr, flush=True)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    prof = ctx.profile(False)
+    u1, p1, s1 = ctx.progress()
+    return dict(ms=ms, prof=prof, clk=clk, n_trace=n_trace, u0=u0, p0=p0, u1=u1, p1=p1)
+
+
+def streamer_results(ctx, g, st):
+    """Results a streamer run states: electron count, electron and positive-ion
+    charge (C), the largest cell electron density (m^-3) and the head, the
+    lowest cell centre whose electron density is at least a tenth of that
+    maximum (mm from the lower plate)."""
+    import torch
+    ncell = g["nx"] * g["ny"] * g["nz"]
+    q = [torch.zeros(ncell, dtype=torch.int64, device="cuda") for _ in range(2)]
+    ctx.get_deposit(q[0], q[1])
+    qe, qp = (a.cpu().numpy() for a in q)
+    scale = 1.602176634e-19 / 2.0 ** 32
+    dV = g["dx"] ** 3
+    ne = (qe.astype(np.float64) / 2.0 ** 32 / dV).reshape(g["nz"], g["ny"], g["nx"])
+    ne_max = float(ne.max())
+    rows = np.nonzero((ne >= 0.1 * ne_max).any(axis=(1, 2)))[0] if ne_max > 0 else np.zeros(0, int)
+    head = float(g["origin"][2] + (rows.min() + 0.5) * g["dx"]) * 1e3 if len(rows) else float("nan")
+    return {"electrons": int(ctx.count()), "electron_charge_C": float(qe.sum()) * scale,
+            "ion_charge_C": float(qp.sum()) * scale, "ne_max_m3": ne_max, "head_z_mm": head,
+            "simulated_ns": st.t_total * 1e9}
+
+
+def fp64_arm(args, wl, cap, seed, stream, flush, local, rank, results32):
+    """The plain float64 GPU path on the same workload (same seed, steps and
+    launch shapes), timed the same way, with the relative difference of each
+    stated result from the float32 run."""
+    import gc
+    ctx = streamer_context(wl, 64, cap, seed, boundary=args.boundary, adaptive_dt=not args.fixed_dt)
+    ctx.seed_gaussian(wl["seed_n0"], wl["seed_radius"], wl["seed_center"], seed_weight(wl))
+    r = timed_steps(ctx, args, stream, flush, local, rank, label="fp64")
+    fin = ctx.step(0, stats=True)
+    res = streamer_results(ctx, wl["grid"], fin)
+    diff = {k: (results32[k] - v) / v if v else None for k, v in res.items() if k in results32}
+    out = {"value": (r["u1"] - r["u0"]) / (r["ms"] * 1e-3), "unit": UNIT, "ms_per_step": r["ms"] / args.steps,
+           "phases_ms": {k: round(r["prof"][k], 3) for k in ("ms_push", "ms_children", "ms_field", "ms_reorder")},
+           "results": res, "results_fp32": results32, "fp32_minus_fp64_relative": diff,
+           "note": "same seed and schedule; the two runs take different collision decisions after the first "
+                   "rounding-level flips, so the differences mix precision with Monte Carlo noise"}
+    ctx.close()
+    del ctx
+    gc.collect()
+    return out
+
+
 def aggregate(ms: float, updates: float, dist=None, device="cpu"):
     """Whole-job figures of N replicas: the slowest rank's time and the sum of
     all ranks' particle-updates (weak scaling: every rank runs its own
@@ -135,15 +238,15 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def issue_roofline(draws_per_update, updates_per_step, collide_ms_per_step, clk):
+def issue_roofline(draws_per_update, updates_per_step, collide_ms_per_step, clk, sms=152):
     """The collision kernels' binding limit: warp-instruction issue.  The
     algorithmic work is one draw per candidate collision of the null-collision
     method (nu_max dt per electron-step, measured) plus the draw that ends the
     step; each costs PUSH_WARP_INST_PER_DRAW warp instructions (ncu, parents
-    and children kernels of steady-state steps).  Peak: 4 issue slots x 152
-    SMs x the median SM clock sampled while timing."""
+    and children kernels of steady-state steps).  Peak: 4 issue slots x the
+    device's SMs x the median SM clock sampled while timing."""
     mhz = clk.get("sm_mhz") or 2070.0
-    peak = ISSUE_SLOTS_PER_SM * N_SMS * mhz * 1e6 / 1e9
+    peak = ISSUE_SLOTS_PER_SM * sms * mhz * 1e6 / 1e9
     ach = PUSH_WARP_INST_PER_DRAW * draws_per_update * updates_per_step / (collide_ms_per_step * 1e-3) / 1e9
     return {"bound": "issue", "kernel": "k_push + k_children <float,PIC>", "unit": "Gwarp-inst/s",
             "achieved": ach, "peak": peak, "frac": ach / peak, "draws_per_update": draws_per_update,
@@ -202,24 +305,29 @@ def parse_clocks(lines):
             "samples": len(sm)}
 
 
-def cpu_baseline(wl, budget_s=12.0, sample=20000, seed=2110144940):
-    """The oracle, as it stands, on a random sample of the seeded particles in
-    the plates' background field (one thread)."""
+def _oracle_sample(job):
+    """One oracle process: `sample` of the seeded electrons (the disjoint slice
+    `part` of `parts`), push+MCC+deposit steps in the plates' field given as a
+    grid (so the trilinear gather runs) for about budget_s seconds.  Returns
+    (particle-updates, seconds, steps)."""
+    wl, sample, part, parts, budget_s, seed = job
     import oracle as O
     import workloads as W
     g = wl["grid"]
     gas = W.synthetic_air()
     mask = W.needle_mask(g, wl["needle_length"], wl["needle_radius"])
-    w0 = wl["seed_n0"] * np.pi ** 1.5 * wl["seed_radius"] ** 3 / wl["n_initial"]
-    E0 = (0.0, 0.0, -(wl["v_top"] - wl["v_bottom"]) / wl["L"])
-    m = O.Model(gas, wl["dt"], seed, 64, g, None, E0=E0, mask=mask)
-    full = O.seed_gaussian(m, wl["seed_n0"], wl["seed_radius"], wl["seed_center"], w0, 2 * wl["n_initial"])
+    shape = (g["nz"], g["ny"], g["nx"])
+    Ez = -(wl["v_top"] - wl["v_bottom"]) / wl["L"]
+    field = (np.zeros(shape, np.float32), np.zeros(shape, np.float32), np.full(shape, Ez, np.float32))
+    m = O.Model(gas, wl["dt"], seed, 64, g, field, mask=mask, boundary=1)
+    full = O.seed_gaussian(m, wl["seed_n0"], wl["seed_radius"], wl["seed_center"], seed_weight(wl),
+                           2 * wl["n_initial"])
     v = full.view()
-    pick = np.sort(np.random.default_rng(1).choice(full.n, size=min(sample, full.n), replace=False))
+    order = np.random.default_rng(1).permutation(full.n)
+    pick = np.sort(order[part * sample:(part + 1) * sample])
     p = O.Particles(8 * sample, {k: v[k][pick] for k in v})
     n_cell = g["nx"] * g["ny"] * g["nz"]
-    upd, t = 0, 0.0
-    step = 0
+    upd, t, step = 0, 0.0, 0
     while t < budget_s and step < 1000:
         step += 1
         q = np.zeros(n_cell, np.int64)
@@ -227,9 +335,31 @@ def cpu_baseline(wl, budget_s=12.0, sample=20000, seed=2110144940):
         rc, st = O.step(m, p, step, step == 1, q, None, None)
         t += time.perf_counter() - t0
         upd += st.n_start + st.n_children
-    return {"value": upd / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{len(pick)} of the {full.n} seeded electrons, {step} steps of push+MCC+deposit in the "
-                      f"plates' background field (no Poisson), {t:.1f} s single-threaded"}
+    return upd, t, step
+
+
+def cpu_baseline(wl, budget_s=8.0, sample=20000, seed=2110144940, cores=None):
+    """The oracle, as it stands, on the host cores: one process alone, then
+    one process per core at once on disjoint samples of the seeded electrons
+    (spawned processes: no CUDA state is inherited)."""
+    import multiprocessing as mp
+    cores = cores or os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(1) as pool:
+        u1, t1, s1 = pool.map(_oracle_sample, [(wl, sample, 0, 1, budget_s, seed)])[0]
+    jobs = [(wl, sample, i, cores, budget_s, seed) for i in range(cores)]
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_sample, jobs)
+    wall = time.perf_counter() - t0
+    u_all = sum(r[0] for r in res)
+    t_max = max(r[1] for r in res)
+    return {"value": u_all / t_max, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_core": {"value": u1 / t1, "cores": 1, "steps": s1, "seconds": round(t1, 2)},
+            "sample": f"{sample} of the seeded electrons per process ({cores} processes on disjoint samples, "
+                      f"one alone for the single-core figure), push+MCC+deposit steps with the trilinear gather "
+                      f"of the plates' field on the 128^3 grid (no Poisson), about {budget_s:.0f} s each; "
+                      f"value = all processes' updates / the longest process time ({wall:.1f} s wall)"}
 
 
 def run_reference(args):
@@ -435,7 +565,6 @@ def main():
     import __graft_entry__ as ge
     ge.build()
     import workloads as W
-    from paper_2110_14494_gb300 import PicContext
 
     full = args.workload == "streamer-full"
     axi = args.workload == "streamer-axi"
@@ -464,45 +593,13 @@ def main():
     n0 = ctx.seed_gaussian(wl["seed_n0"], wl["seed_radius"], wl["seed_center"], seed_weight(wl))
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    for _ in range(args.warmup):
-        ctx.step(1)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    u0, p0, s0 = ctx.progress()
-    ctx.profile(True)
-    clocks = Clocks(local)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    n_trace = []
-    t_wall = time.perf_counter()
-    recent_n = []
-    for i in range(args.steps):
-        flush.fill_(i & 0xff)
-        ev[i][0].record(stream)
-        try:
-            st = ctx.step(1, stats=args.trace)
-        except Exception:
-            print(json.dumps({"failed_at_step": i, "recent": recent_n[-40:]}), file=sys.stderr, flush=True)
-            raise
-        ev[i][1].record(stream)
-        if args.trace:
-            recent_n.append((i, st.n_start, st.n_end, st.n_children, st.n_weight_updates, st.n_absorbed,
-                             st.poisson_cycles, round(st.dt_last * 1e12, 4), "%.3g" % st.ne_max))
-        if i % 25 == 0:
-            n_trace.append(ctx.count())
-        if (i + 1) % 200 == 0 and rank == 0:
-            torch.cuda.synchronize()
-            recent = sum(a.elapsed_time(b) for a, b in ev[i - 199:i + 1])
-            print(json.dumps({"progress": i + 1, "n": n_trace[-1], "ms_last_200": round(recent, 2),
-                              "wall_s": round(time.perf_counter() - t_wall, 2)}), file=sys.stderr, flush=True)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
-    prof = ctx.profile(False)
-    u1, p1, s1 = ctx.progress()
+    r = timed_steps(ctx, args, stream, flush, local, rank, dist)
+    ms, prof, clk, n_trace = r["ms"], r["prof"], r["clk"], r["n_trace"]
+    u0, p0, u1, p1 = r["u0"], r["p0"], r["u1"], r["p1"]
     ms_max, upd_all = aggregate(ms, u1 - u0, dist, device="cuda")
     fin = ctx.step(0, stats=True)
     value = upd_all / (ms_max * 1e-3)
+    results32 = streamer_results(ctx, g, fin) if not axi else None
     # collision draws per particle-update, sampled after the timed region
     # (the statistics counters stay off while timing)
     smp = ctx.step(10, stats=True)
@@ -510,9 +607,16 @@ def main():
 
     # dominant kernel: the parent push (gather + push + MCC + deposit)
     parents_per_launch = (p1 - p0) / max(prof["n_push"], 1)
+    children_per_launch = (u1 - u0 - (p1 - p0)) / max(prof["n_push"], 1)
     push_ms = prof["ms_push"] / max(prof["n_push"], 1)
     hbm, peak_kind = peaks()
-    achieved = BYTES_PER_UPDATE * parents_per_launch / (push_ms * 1e-3) / 1e9
+    R = 4 if args.precision == 32 else 8
+    grid_bytes = grid_bytes_per_step(g, R)
+    launch_bytes = (BYTES_PER_UPDATE * parents_per_launch + BYTES_PER_CHILD * children_per_launch
+                    + grid_bytes) if args.precision == 32 else None
+    if launch_bytes is None:
+        launch_bytes = 176 * parents_per_launch + 88 * children_per_launch + grid_bytes
+    achieved = launch_bytes / (push_ms * 1e-3) / 1e9
     phases = {k: round(prof[k], 3) for k in ("ms_push", "ms_children", "ms_field", "ms_reorder")}
     print(json.dumps({"diag": "device-timed", "value": value, "ms_per_step": ms_max / args.steps,
                       "phases_ms": phases, "speculative_solves": [prof["n_speculative"], prof["n_undone"]],
@@ -561,6 +665,10 @@ def main():
                "h2d_bytes_per_step": int(h2d / args.e2e_steps), "d2h_bytes_per_step": int(d2h / args.e2e_steps),
                "steps": args.e2e_steps}
 
+    f64 = None
+    if args.precision == 32 and not (full or axi) and not args.no_f64 and rank == 0:
+        f64 = fp64_arm(args, wl, cap, 2110144940 + rank, stream, flush, local, rank, results32)
+        print(json.dumps({"diag": "fp64 arm", **f64}), file=sys.stderr, flush=True)
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(wl)
@@ -588,16 +696,22 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm,
                          "traffic": (PUSH_DRAM_BYTES_PER_PARENT * parents_per_launch
-                                     if (args.workload == "streamer" and args.grid == 128 and args.precision == 32)
+                                     if (args.workload == "streamer" and args.grid == 128 and args.precision == 32
+                                         and PUSH_DRAM_BYTES_PER_PARENT)
                                      else None),
                          "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per parent, "
                                            "profiles/k_push_streamer128.md, scaled to the mean launch",
-                         "kernel": "k_push<float,PIC>",
+                         "kernel": "k_push<%s,PIC>" % ("float" if args.precision == 32 else "double"),
                          "peak_source": peak_kind,
-                         "bytes_per_update": BYTES_PER_UPDATE, "parents_per_launch": parents_per_launch,
+                         "algorithmic_bytes_per_launch": launch_bytes,
+                         "bytes_per_update": BYTES_PER_UPDATE if args.precision == 32 else 176,
+                         "bytes_per_child": BYTES_PER_CHILD if args.precision == 32 else 88,
+                         "grid_bytes_per_launch": grid_bytes,
+                         "parents_per_launch": parents_per_launch, "children_per_launch": children_per_launch,
                          "ms_per_launch": push_ms},
             "alu": issue_roofline(draws_per_update, (u1 - u0) / args.steps,
-                                  (prof["ms_push"] + prof["ms_children"]) / args.steps, clk),
+                                  (prof["ms_push"] + prof["ms_children"]) / args.steps, clk, n_sms()),
+            "fp64": f64,
             "phases_ms": phases,
             "gpu_launches": int(prof["n_launches"]),
             "clocks": clk,

@@ -145,14 +145,23 @@ def test_coupled_streamer_128_matches_oracle(prec):
                               phi0=phi)
         assert rel <= 1.5e-6, (done, rel)
         assert np.all(phi.reshape(mask.shape)[mask > 0] == V)
+        # the field is the central-difference gradient of that potential: the oracle's gradient of the
+        # GPU's own potential, to the float32 rounding of the field (float64 contexts: float64 rounding)
+        Eg = O.grad_phi(g, phi.reshape(g["nz"], g["ny"], g["nx"]), 0.0, V)
+        emax = max(np.abs(e).max() for e in Eg)
+        gtol = 2e-6 if prec == 32 else 1e-12
+        for a, b in zip(next_field, Eg):
+            assert np.abs(a.ravel() - b.ravel()).max() <= gtol * emax, (done, np.abs(a.ravel() - b.ravel()).max() / emax)
         if k == 10:
             phi_ref, rel_ref, _ = O.poisson(g, rho_ref.reshape(g["nz"], g["ny"], g["nx"]), mask, V, 0.0, V,
                                             rtol=1e-10)
             d = np.linalg.norm(phi - phi_ref.ravel()) / np.linalg.norm(phi_ref)
-            print(f"step {done}: potential vs the oracle's CG {d:.2e} (solve residual {rel:.2e})")
-            assert d <= 1e-5, d
             Er = O.grad_phi(g, phi_ref, 0.0, V)
-            emax = max(np.abs(e).max() for e in Er)
-            for a, b in zip(next_field, Er):
-                assert np.abs(a - b).max() <= 1e-4 * emax, (done, np.abs(a - b).max() / emax)
+            de = max(np.abs(a.ravel() - b.ravel()).max() for a, b in zip(next_field, Er)) / emax
+            print(f"step {done}: potential vs the oracle's CG {d:.2e}, field {de:.2e} of max |E| "
+                  f"(solve residual {rel:.2e})")
+            # a residual of 1e-6 leaves an error whose central differences reach ~1e-4 of the peak field at the
+            # needle tip (measured 1.0e-4 at step 11); the bound is the solve tolerance's, not the gradient's
+            assert d <= 1e-5, d
+            assert de <= 5e-4, de
         dt_prev = st.dt_last
