@@ -1330,6 +1330,9 @@ template <class T> static PushArgs<T> make_args(pic_ctx* c, int mode) {
     A.eps_lo = (T)c->cfg.gas.eps[0];
     A.eps_hi = (T)c->cfg.gas.eps[c->n_bins - 1];
     A.nu_max = (T)c->nu_max;
+    A.tau_scale = (T)(-0.69314718055994530942 / c->nu_max);
+    A.inv_dl2 = (T)(0.69314718055994530942 * c->inv_dl);
+    A.l0t = (T)(c->l0 * c->inv_dl);
     A.dt = (T)c->dt_cur;
     A.dt_kick = (T)c->dt_prev;
     A.K = c->K;

@@ -36,6 +36,8 @@ template <class T> struct PushArgs {
     T l0, inv_dl;              // ln(eps_0), (n_bins-1) / (ln eps_last - ln eps_0), in T
     T eps_lo, eps_hi;          // eV
     T nu_max;
+    T tau_scale;               // -ln 2 / nu_max: single-precision flight times from base-2 logarithms
+    T inv_dl2, l0t;            // ln 2 * inv_dl and l0 * inv_dl: table coordinate from a base-2 logarithm
     T dt;                      // duration of this step
     T dt_kick;                 // duration of the previous step (the half-kick completes its Eq. 2)
     Keys K;
@@ -339,6 +341,35 @@ __device__ __forceinline__ void deposit_at(const PushArgs<T>& A, T x0, T x1, T x
 }
 
 // ------------------------------------------------------------------ rates
+// Arithmetic of one candidate collision.  Double precision follows the
+// oracle's operations.  Single precision takes the hardware base-2 logarithm
+// (absolute error near 1e-7) and multiplies by precomputed constants instead
+// of dividing: a flight time then carries an absolute error near 1e-7 / nu_max
+// (far below a cell crossing), a table coordinate one near 1e-5 of a bin, and
+// the scattering cosine a reciprocal square root.
+template <class T> struct EvArith;
+template <> struct EvArith<double> {
+    static __device__ __forceinline__ double flight(const PushArgs<double>& A, double u0) {
+        return -log(u0) / A.nu_max;
+    }
+    static __device__ __forceinline__ double coord(const PushArgs<double>& A, double e) {
+        return (log(e) - A.l0) * A.inv_dl;
+    }
+    static __device__ __forceinline__ double cosine(double dot, double v2) {
+        const double sp = sqrt(v2);
+        return sp > 0.0 ? dot / sp : 0.0;
+    }
+};
+template <> struct EvArith<float> {
+    static __device__ __forceinline__ float flight(const PushArgs<float>& A, float u0) {
+        return __log2f(u0) * A.tau_scale;
+    }
+    static __device__ __forceinline__ float coord(const PushArgs<float>& A, float e) {
+        return fmaf(__log2f(e), A.inv_dl2, -A.l0t);
+    }
+    static __device__ __forceinline__ float cosine(float dot, float v2) { return v2 > 0.0f ? dot * rsqrtf(v2) : 0.0f; }
+};
+
 // Index and fraction in the table, linear in ln(eps), clamped at both ends.
 template <class T>
 __device__ __forceinline__ void table_pos(const PushArgs<T>& A, T e, int& j, T& f, LStats& ls) {
@@ -349,7 +380,7 @@ __device__ __forceinline__ void table_pos(const PushArgs<T>& A, T e, int& j, T& 
         j = A.n_bins - 2; f = (T)1;
         if (e > A.eps_hi) ++ls.clamped;
     } else {
-        T t = (Arith<T>::lg(e) - A.l0) * A.inv_dl;
+        T t = EvArith<T>::coord(A, e);
         int jj = (int)floor(t);
         if (jj > A.n_bins - 2) jj = A.n_bins - 2;
         if (jj < 0) jj = 0;
@@ -463,14 +494,15 @@ __device__ __forceinline__ void photo_test(const PushArgs<T>& A, const Keys& K, 
 // tau, pick the process with u1 nu_max against the cumulative rates at the
 // electron's energy (none = null collision) and scatter isotropically with
 // u2, u3.  Ionization returns EV_IONIZED with the product's speed in sp (the
-// caller stages the product, which flies the remaining time); attachment
-// records a negative-ion event and ends the electron.
+// caller queues the product, which flies the remaining time, and its
+// positive-ion event); attachment returns EV_ATTACHED (the caller records the
+// negative-ion event at the electron's position) and ends the electron.
 template <class T, int MODE, bool FAST, bool STATS>
 __device__ __forceinline__ int event(const PushArgs<T>& A, const Keys& K, uint32_t step, const ProcSmem<T>* ps,
                                      Lane<T>& L, LStats& ls, T& sp) {
     const u32x4 r = draw_words(K, L.id, step, L.k);
     ++L.k;
-    const T tau = Arith<T>::tau(unif<T>(r.x), A.nu_max);
+    const T tau = EvArith<T>::flight(A, unif<T>(r.x));
     if (tau >= L.t_left) { fly(L.d, L.v, L.a, L.t_left); return EV_DONE; }
     fly(L.d, L.v, L.a, tau);
     L.t_left -= tau;
@@ -483,10 +515,8 @@ __device__ __forceinline__ int event(const PushArgs<T>& A, const Keys& K, uint32
     if (STATS) ++ls.coll[p & 7];
     const int kind = ps->kind[p];
     if (kind == PIC_PROC_ATTACHMENT) {
-        ls.w_att += (double)L.w;
+        if (MODE == MODE_SWARM || STATS) ls.w_att += (double)L.w;
         ++ls.attached;
-        if (MODE == MODE_PIC && A.q_neg)
-            deposit_at(A, L.x[0] + L.d[0], L.x[1] + L.d[1], L.x[2] + L.d[2], L.w, A.q_neg);
         return EV_ATTACHED;
     }
     T n[3];
@@ -495,9 +525,7 @@ __device__ __forceinline__ int event(const PushArgs<T>& A, const Keys& K, uint32
     // excitation loss, or half of what ionization leaves
     T e2;
     if (kind == PIC_PROC_ELASTIC) {
-        const T sp = sqrt(v2);
-        T cchi = (T)0;
-        if (sp > (T)0) cchi = (v[0] * n[0] + v[1] * n[1] + v[2] * n[2]) / sp;
+        const T cchi = EvArith<T>::cosine(v[0] * n[0] + v[1] * n[1] + v[2] * n[2], v2);
         e2 = dmax(e * ((T)1 - (T)2 * ps->mratio[p] * ((T)1 - cchi)), (T)0);
     } else if (kind == PIC_PROC_EXCITATION) {
         e2 = dmax(e - ps->thr[p], (T)0);
@@ -508,11 +536,7 @@ __device__ __forceinline__ int event(const PushArgs<T>& A, const Keys& K, uint32
     v[0] = sp2 * n[0]; v[1] = sp2 * n[1]; v[2] = sp2 * n[2];
     if (kind == PIC_PROC_IONIZATION) {
         sp = sp2;
-        ls.w_ion += (double)L.w;
-        if (MODE == MODE_PIC && A.photo_prob > (T)0) {
-            const T xe[3] = {L.x[0] + L.d[0], L.x[1] + L.d[1], L.x[2] + L.d[2]};
-            photo_test(A, K, step, L.id, L.k - 1, xe, L.w);
-        }
+        if (MODE == MODE_SWARM || STATS) ls.w_ion += (double)L.w;
         return EV_IONIZED;
     }
     return EV_CONTINUE;
@@ -740,11 +764,18 @@ static __global__ void k_resample_commit(DevState* st) {
 constexpr int kRow = 11;    // padded row of a stage entry: x y z vx vy vz ax ay az w t
 constexpr int kOut = 64;    // output stage capacity (flushed at 32)
 constexpr int kCh = 64;     // product stage capacity of the batched swarm kernel (flushed at 32)
+constexpr int kPQ = 40;     // warp queue of ionization products (built 32 at a time)
+constexpr int kPQRow = 9;   // x y z, product speed, ax ay az of the ionizing electron, w, remaining time
+constexpr int kAtt = 32;    // warp buffer of attachment events awaiting their deposit
 
 template <class T> struct Stage {
     T in[32 * kRow];
     T out[kOut * kRow];
     uint64_t in_id[32], out_id[kOut];
+    T pq[kPQ * kPQRow];
+    uint64_t pq_id[kPQ];    // the ionizing electron
+    uint32_t pq_k[kPQ];     // index of its draw that ionized
+    T att[kAtt * 4];        // x y z w of negative-ion events
 };
 
 template <class T> constexpr size_t collide_smem() {
@@ -799,6 +830,39 @@ __device__ __forceinline__ void flush_out(const PushArgs<T>& A, Stage<T>* sg, in
     n = rest;
 }
 
+// An ionization product as a work item of the input stage: derived id and
+// direction from its own draw (make_child), its positive-ion event and, with
+// photoionization, the photon test of the ionizing event (Sec. 2.4).  e: the
+// compact entry (x y z, speed, a, w, remaining time) of electron pid's draw k.
+template <class T, int MODE>
+__device__ __forceinline__ void build_product(const PushArgs<T>& A, const T* e, uint64_t pid, uint32_t k, T* row,
+                                              uint64_t* rid) {
+    T vc[3];
+    *rid = make_child(A.K, A.step, pid, k, e[3], vc);
+    if (MODE == MODE_PIC) {
+        if (A.q_pos) deposit_at(A, e[0], e[1], e[2], e[7], A.q_pos);
+        if (A.photo_prob > (T)0) photo_test(A, A.K, A.step, pid, k, e, e[7]);
+    }
+    row[0] = e[0]; row[1] = e[1]; row[2] = e[2];
+    row[3] = vc[0]; row[4] = vc[1]; row[5] = vc[2];
+    row[6] = e[4]; row[7] = e[5]; row[8] = e[6];
+    row[9] = e[7];
+    row[10] = e[8];
+}
+
+// Deposits the buffered negative-ion events [0, n) of the warp, one per lane.
+template <class T>
+__device__ __forceinline__ void flush_att(const PushArgs<T>& A, Stage<T>* sg, int& n) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    if (lane < n) {
+        const T* a = sg->att + lane * 4;
+        deposit_at(A, a[0], a[1], a[2], a[3], A.q_neg);
+    }
+    __syncwarp();
+    n = 0;
+}
+
 template <class T, int MODE, bool FAST, bool STATS, bool CHILD>
 __device__ __forceinline__ void collide_loop(const PushArgs<T>& A, const ProcSmem<T>* ps, Stage<T>* sg) {
     const int lane = threadIdx.x & 31;
@@ -806,14 +870,14 @@ __device__ __forceinline__ void collide_loop(const PushArgs<T>& A, const ProcSme
     long long n_items;
     unsigned long long* cursor;
     const ChildQ<T>& src = (A.gen & 1) ? A.cq2 : A.cq;
-    // products the stack cannot take: the parents' go to the queue of the
+    // products the warp queue cannot take: the parents' go to the queue of the
     // first children launch, a children launch's to the other queue
     const ChildQ<T>& dst = CHILD ? ((A.gen & 1) ? A.cq : A.cq2) : A.cq;
     unsigned long long* dst_cnt = CHILD ? ((A.gen & 1) ? &A.st->n_child : &A.st->n_spill) : &A.st->n_child;
     if (CHILD) {
         n_items = (long long)((A.gen & 1) ? A.st->n_spill : A.st->n_child);
         if (n_items > A.cap_child) n_items = A.cap_child;
-        if (n_items == 0) return;  // the stacks took every product (uniform over the grid)
+        if (n_items == 0) return;  // the warp queues took every product
         cursor = &A.st->n_fetch_c;
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&A.st->n_updates, (unsigned long long)n_items);
     } else {
@@ -824,27 +888,15 @@ __device__ __forceinline__ void collide_loop(const PushArgs<T>& A, const ProcSme
     ls.zero();
     MomAcc<T> M;
     if (MODE == MODE_SWARM) M.zero();
-    StackSink<T> stk;
     Lane<T> L;
     bool active = false, dry = false;
-    int in_head = 0, in_count = 0, n_out = 0;
-    unsigned popped = 0;  // products taken from the stack (counted as updates)
+    // warp-uniform counters: input stage head and size, output stage size,
+    // queued products, buffered negative-ion events
+    int in_head = 0, in_count = 0, n_out = 0, n_pq = 0, n_att = 0;
+    unsigned built = 0;  // products this lane built from the warp queue (counted as updates)
     for (;;) {
-        // 1. idle lanes take staged electrons (a lane's own stack first)
-        bool want = !active;
-        if (want && stk.n > 0) {
-            --stk.n;
-            const int t = stk.n;
-            for (int d = 0; d < 3; ++d) { L.x[d] = stk.x[t][d]; L.v[d] = stk.v[t][d]; L.d[d] = (T)0; }
-            L.w = stk.w[t];
-            L.id = stk.id[t];
-            L.t_left = stk.t[t];
-            L.k = 1;
-            active = true;
-            want = false;
-            ++ls.processed;
-            ++popped;
-        }
+        // 1. idle lanes take staged work items
+        const bool want = !active;
         const unsigned need = __ballot_sync(kFull, want);
         const int avail = in_count - in_head;
         if (need && avail > 0) {
@@ -863,91 +915,111 @@ __device__ __forceinline__ void collide_loop(const PushArgs<T>& A, const ProcSme
             const int took = __popc(need) < avail ? __popc(need) : avail;
             in_head += took;
         }
-        // 2. refill the input stage with 32 work items once it is drained
-        if (in_head >= in_count && !dry) {
+        // 2. refill the input stage once it is drained: 32 queued products when
+        //    there are that many (the rest once the input has run dry), else 32
+        //    work items of the input; every lane prepares one entry
+        if (in_head >= in_count && (!dry || n_pq > 0)) {
+            int cnt = 0;
             __syncwarp();
-            unsigned long long b = 0;
-            if (lane == 0) b = atomicAdd(cursor, 32ull);
-            b = __shfl_sync(kFull, b, 0);
-            if ((long long)b >= n_items) {
-                dry = true;
-                in_head = in_count = 0;
-            } else {
-                const long long left = n_items - (long long)b;
-                const int cnt = left < 32 ? (int)left : 32;
+            if (n_pq >= 32 || (dry && n_pq > 0)) {
+                cnt = n_pq < 32 ? n_pq : 32;
                 if (lane < cnt) {
-                    const long long it = (long long)b + lane;
-                    T* r = sg->in + lane * kRow;
-                    if (CHILD) {
-                        const Soa<T>& q = src.p;
-                        const T x0 = q.r[PX][it], x1 = q.r[PY][it], x2 = q.r[PZ][it], w = q.r[PW][it];
-                        T vc[3];
-                        const uint64_t cid = make_child(A.K, A.step, q.id[it], src.k[it], q.r[VX][it], vc);
-                        if (MODE == MODE_PIC && A.q_pos)
-                            deposit_at(A, x0, x1, x2, w, A.q_pos);
-                        r[0] = x0; r[1] = x1; r[2] = x2;
-                        r[3] = vc[0]; r[4] = vc[1]; r[5] = vc[2];
-                        r[6] = q.r[AX][it]; r[7] = q.r[AY][it]; r[8] = q.r[AZ][it];
-                        r[9] = w;
-                        r[10] = src.t_left[it];
-                        sg->in_id[lane] = cid;
-                    } else {
-                        T f[10];
-                        for (int q = 0; q < 10; ++q) f[q] = A.in.r[q][it];
-                        if (MODE == MODE_PIC && A.kick_on_load) half_kick(A, f);
-                        for (int q = 0; q < 10; ++q) r[q] = f[q];
-                        r[10] = A.dt;
-                        sg->in_id[lane] = A.in.id[it];
+                    const int j = n_pq - cnt + lane;
+                    build_product<T, MODE>(A, sg->pq + j * kPQRow, sg->pq_id[j], sg->pq_k[j], sg->in + lane * kRow,
+                                           &sg->in_id[lane]);
+                    ++built;
+                }
+                n_pq -= cnt;
+            } else {
+                unsigned long long b = 0;
+                if (lane == 0) b = atomicAdd(cursor, 32ull);
+                b = __shfl_sync(kFull, b, 0);
+                if ((long long)b >= n_items) {
+                    dry = true;
+                } else {
+                    const long long left = n_items - (long long)b;
+                    cnt = left < 32 ? (int)left : 32;
+                    if (lane < cnt) {
+                        const long long it = (long long)b + lane;
+                        T* r = sg->in + lane * kRow;
+                        if (CHILD) {
+                            const Soa<T>& q = src.p;
+                            const T e[kPQRow] = {q.r[PX][it], q.r[PY][it], q.r[PZ][it], q.r[VX][it], q.r[AX][it],
+                                                 q.r[AY][it], q.r[AZ][it], q.r[PW][it], src.t_left[it]};
+                            build_product<T, MODE>(A, e, q.id[it], src.k[it], r, &sg->in_id[lane]);
+                        } else {
+                            T f[10];
+                            for (int q = 0; q < 10; ++q) f[q] = A.in.r[q][it];
+                            if (MODE == MODE_PIC && A.kick_on_load) half_kick(A, f);
+                            for (int q = 0; q < 10; ++q) r[q] = f[q];
+                            r[10] = A.dt;
+                            sg->in_id[lane] = A.in.id[it];
+                        }
                     }
                 }
-                in_head = 0;
-                in_count = cnt;
             }
+            in_head = 0;
+            in_count = cnt;
             __syncwarp();
         }
         // 3. termination
-        if (!__any_sync(kFull, active || stk.n > 0)) {
-            if (dry && in_head >= in_count) break;
+        if (!__any_sync(kFull, active)) {
+            if (dry && in_head >= in_count && n_pq == 0) break;
             continue;
         }
         // 4. one candidate collision
         int r = EV_CONTINUE;
         T sp = (T)0;
         if (active) r = event<T, MODE, FAST, STATS>(A, A.K, A.step, ps, L, ls, sp);
-        const bool done = r == EV_DONE, ion = r == EV_IONIZED;
-        if (r == EV_DONE || r == EV_ATTACHED) active = false;
-        // 5. ionization products
-        if (ion) {
-            if (stk.n < StackSink<T>::kDepth) {
-                const T xc[3] = {L.x[0] + L.d[0], L.x[1] + L.d[1], L.x[2] + L.d[2]};
-                T vc[3];
-                const uint64_t cid = make_child(A.K, A.step, L.id, L.k - 1, sp, vc);
-                if (MODE == MODE_PIC && A.q_pos)
-                    deposit_at(A, xc[0], xc[1], xc[2], L.w, A.q_pos);
-                const int t = stk.n++;
-                for (int d = 0; d < 3; ++d) { stk.x[t][d] = xc[d]; stk.v[t][d] = vc[d]; }
-                stk.w[t] = L.w;
-                stk.id[t] = cid;
-                stk.t[t] = L.t_left;
-                ++ls.children;
-            } else {  // stack full: the compact entry waits for the next generation
-                const unsigned long long q = atomicAdd(dst_cnt, 1ull);
-                if ((long long)q < A.cap_child) {
-                    const Soa<T>& d = dst.p;
-                    d.r[PX][q] = L.x[0] + L.d[0]; d.r[PY][q] = L.x[1] + L.d[1]; d.r[PZ][q] = L.x[2] + L.d[2];
-                    d.r[VX][q] = sp;
-                    d.r[AX][q] = L.a[0]; d.r[AY][q] = L.a[1]; d.r[AZ][q] = L.a[2];
-                    d.r[PW][q] = L.w;
-                    d.id[q] = L.id;
-                    dst.t_left[q] = L.t_left;
-                    dst.k[q] = L.k - 1;
+        const bool done = r == EV_DONE, ion = r == EV_IONIZED, att = r == EV_ATTACHED;
+        if (done || att) active = false;
+        // 5. ionization products wait in the warp queue as compact entries (the
+        //    queue of the next launch when it is full)
+        const unsigned im = __ballot_sync(kFull, ion);
+        if (im) {
+            if (ion) {
+                const int slot = n_pq + __popc(im & lt);
+                const T e[kPQRow] = {L.x[0] + L.d[0], L.x[1] + L.d[1], L.x[2] + L.d[2], sp,
+                                     L.a[0], L.a[1], L.a[2], L.w, L.t_left};
+                if (slot < kPQ) {
+                    T* q = sg->pq + slot * kPQRow;
+                    for (int f = 0; f < kPQRow; ++f) q[f] = e[f];
+                    sg->pq_id[slot] = L.id;
+                    sg->pq_k[slot] = L.k - 1;
                     ++ls.children;
                 } else {
-                    atomicOr(&A.st->err, kErrChildCapacity);
+                    const unsigned long long q = atomicAdd(dst_cnt, 1ull);
+                    if ((long long)q < A.cap_child) {
+                        const Soa<T>& d = dst.p;
+                        d.r[PX][q] = e[0]; d.r[PY][q] = e[1]; d.r[PZ][q] = e[2];
+                        d.r[VX][q] = sp;
+                        d.r[AX][q] = e[4]; d.r[AY][q] = e[5]; d.r[AZ][q] = e[6];
+                        d.r[PW][q] = L.w;
+                        d.id[q] = L.id;
+                        dst.t_left[q] = L.t_left;
+                        dst.k[q] = L.k - 1;
+                        ++ls.children;
+                    } else {
+                        atomicOr(&A.st->err, kErrChildCapacity);
+                    }
                 }
             }
+            n_pq += __popc(im);
+            if (n_pq > kPQ) n_pq = kPQ;
         }
-        // 6. finished electrons
+        // 6. negative-ion events wait for a deposit by 32 lanes at once
+        if (MODE == MODE_PIC) {
+            const unsigned am = __ballot_sync(kFull, att);
+            if (am && A.q_neg) {
+                if (n_att + __popc(am) > kAtt) flush_att(A, sg, n_att);
+                if (att) {
+                    T* q = sg->att + (n_att + __popc(am & lt)) * 4;
+                    q[0] = L.x[0] + L.d[0]; q[1] = L.x[1] + L.d[1]; q[2] = L.x[2] + L.d[2]; q[3] = L.w;
+                }
+                n_att += __popc(am);
+            }
+        }
+        // 7. finished electrons
         const unsigned dm = __ballot_sync(kFull, done);
         if (dm) {
             if (done) {
@@ -964,8 +1036,9 @@ __device__ __forceinline__ void collide_loop(const PushArgs<T>& A, const ProcSme
         }
     }
     if (n_out > 0) flush_out<T, MODE>(A, sg, n_out, n_out, ls, M);
+    if (MODE == MODE_PIC && n_att > 0) flush_att(A, sg, n_att);
     {
-        unsigned pw = popped;
+        unsigned pw = built;
         for (int o = 16; o > 0; o >>= 1) pw += __shfl_xor_sync(kFull, pw, o);
         if (lane == 0 && pw) atomicAdd(&A.st->n_updates, (unsigned long long)pw);
     }
@@ -994,16 +1067,19 @@ template <class T> __device__ __forceinline__ Stage<T>* warp_stage(unsigned char
 }
 
 constexpr int kCollideThreads = 128;
+// Resident blocks per SM the collision kernels are compiled for: seven (28
+// warps, 72 registers) in single precision, four in double precision.
+template <class T> constexpr int collide_min_blocks() { return sizeof(T) == 4 ? 7 : 4; }
 
 template <class T, int MODE, bool FAST, bool STATS>
-__global__ void __launch_bounds__(kCollideThreads) k_push(const PushArgs<T> A) {
+__global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<T>()) k_push(const PushArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const ProcSmem<T>* ps = stage_proc(smem_raw, A);
     collide_loop<T, MODE, FAST, STATS, false>(A, ps, warp_stage<T>(smem_raw));
 }
 
 template <class T, int MODE, bool FAST, bool STATS>
-__global__ void __launch_bounds__(kCollideThreads) k_children(const PushArgs<T> A) {
+__global__ void __launch_bounds__(kCollideThreads, collide_min_blocks<T>()) k_children(const PushArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const ProcSmem<T>* ps = stage_proc(smem_raw, A);
     collide_loop<T, MODE, FAST, STATS, true>(A, ps, warp_stage<T>(smem_raw));
