@@ -35,16 +35,16 @@ UNIT = "particle-updates/s"
 BYTES_PER_UPDATE = 96          # float32 state x,v,a,w (40 B) + id (8 B), read and written
 BYTES_PER_CHILD = 48           # an ionization product is born in registers: its state is written once
 WORKLOAD = "streamer-128^3-fp32"
-# DRAM bytes (read + write) per parent of the collision kernel in this workload's steady state, from the
-# ncu capture summarised in profiles/k_push_streamer128.md (49.1 MB per launch of ~8.4e5 parents); scaled
-# to the run's mean launch for roofline.traffic.  Only valid for the kernel build and workload it was taken on.
-PUSH_DRAM_BYTES_PER_PARENT = 61.9
+# DRAM bytes (read + write) per particle-update of the collision kernel in this workload's steady state, from
+# the ncu capture summarised in profiles/k_push_streamer128.md (39.6 MB per launch of ~7.9e5 updates); scaled to
+# the run's mean launch for roofline.traffic.  Only valid for the kernel build and workload it was taken on.
+PUSH_DRAM_BYTES_PER_UPDATE = 49.9
 # The collision kernels (parents and children) issue about this many warp
 # instructions per collision draw (a candidate event, or the last draw that
 # ends the step): ncu smsp__inst_executed.sum over three steady-state steps /
 # (updates x draws per update), from profiles/k_push_streamer128.md
-# (4.191e8 / (1.890e6 x 9.985)).
-PUSH_WARP_INST_PER_DRAW = 22.2
+# (4.243e8 / (2.380e6 x 9.311)).
+PUSH_WARP_INST_PER_DRAW = 19.15
 ISSUE_SLOTS_PER_SM = 4   # warp schedulers per SM, one warp instruction each per clock
 
 
@@ -71,12 +71,17 @@ def parse():
     ap.add_argument("--boundary", type=int, default=1, help="0: reflect at the domain faces, 1: absorb (outflow)")
     ap.add_argument("--fixed-dt", action="store_true", help="keep dt = 2 ps (no time-step control)")
     ap.add_argument("--workload", default="streamer",
-                    choices=["streamer", "streamer-full", "streamer-axi", "swarms", "mlp"],
+                    choices=["streamer", "streamer-full", "streamer-axi", "swarms", "mlp", "c1"],
                     help="streamer: the coupled 128^3 step (headline); swarms: 256 batched swarms")
     ap.add_argument("--swarm-block", type=int, default=0, help="batched swarms: block size (0 = autotune)")
     ap.add_argument("--swarm-bps", type=int, default=0, help="batched swarms: blocks per SM (0 = autotune)")
     ap.add_argument("--no-f64", action="store_true",
                     help="skip the float64 comparison (streamer: the float64 arm; batched swarms: the plain path)")
+    ap.add_argument("--vcycle", default="2,2",
+                    help="pre,post smoothing sweeps of the coupled solve's V-cycle preconditioner")
+    ap.add_argument("--host-solve", action="store_true",
+                    help="drive the field solve's CG loop from the host (every solve kernel an ordinary launch, "
+                         "for per-kernel profiles; the same kernels and results)")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="after the timed steps, run this many more inside an NVTX range named 'prof' "
                          "(untimed; for ncu --nvtx --nvtx-include prof/)")
@@ -414,6 +419,82 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+C1_SWARM = dict(n0=10_000, n_steps=2000, dt=1e-12, n_lo=5_000, n_hi=20_000)
+
+
+def _oracle_c1(job):
+    """One oracle process of the 120 Td swarm (its first `steps` steps, seed):
+    (particle-updates, seconds)."""
+    EN, steps, seed = job
+    import oracle as O
+    import workloads as W
+    t0 = time.perf_counter()
+    mom, cnt, res, m = O.swarm(W.synthetic_air(), EN, C1_SWARM["n0"], steps, C1_SWARM["dt"], seed,
+                               n_lo=C1_SWARM["n_lo"], n_hi=C1_SWARM["n_hi"])
+    t = time.perf_counter() - t0
+    return float(C1_SWARM["n0"] + cnt[:-1].sum()), t
+
+
+def run_c1(args):
+    """The 120 Td swarm: 1e4 float64 electrons, 2000 steps of 1 ps in a uniform
+    field (E/N = 120 Td, 80:20 N2:O2 synthetic air at 2.45e25 m^-3), resampling
+    keeping 5e3-2e4 electrons; flux and bulk drift, mean energy, alpha and eta.
+    The single swarm is too small to fill the GPU, so 64 replicas (different
+    seeds) also run together in one launch per step.  CPU baseline: the oracle
+    on the first 600 steps of the same swarm, one process and one per core."""
+    import multiprocessing as mp
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    import workloads as W
+    from paper_2110_14494_gb300 import swarm_run
+    gas = W.synthetic_air()
+    seed = 2110144941
+    kw = dict(precision=64, want_moments=True, **C1_SWARM)
+    swarm_run(gas, [120.0], seed=seed, **dict(kw, n_steps=60))      # warm-up (module load, launch shapes)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res, mom, cnt = swarm_run(gas, [120.0], seed=seed, **kw)
+    torch.cuda.synchronize()
+    wall1 = time.perf_counter() - t0
+    upd1 = float(C1_SWARM["n0"] + cnt[0][:-1].sum())
+    reps = 64
+    swarm_run(gas, [120.0] * reps, seed=seed + 1000, batched=True, **dict(kw, n_steps=60))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rr, _, cr = swarm_run(gas, [120.0] * reps, seed=seed + 1000, batched=True, **kw)
+    torch.cuda.synchronize()
+    wall64 = time.perf_counter() - t0
+    upd64 = float(reps * C1_SWARM["n0"] + cr[:, :-1].sum())
+    names = {"W_flux": 0, "W_bulk": 1, "mean_eps": 6, "alpha": 9, "eta": 10}
+    coeff = {k: {"value": float(res[0][i]), "sigma": float(res[0][11 + i]),
+                 "replicas_mean": float(rr[:, i].mean()), "replicas_std": float(rr[:, i].std(ddof=1)),
+                 "replicas_mean_batch_sigma": float(rr[:, 11 + i].mean())} for k, i in names.items()}
+    base = None
+    if not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(1) as pool:
+            u1, t1 = pool.map(_oracle_c1, [(120.0, 600, seed)])[0]
+        with ctx.Pool(cores) as pool:
+            rs = pool.map(_oracle_c1, [(120.0, 600, seed + 1 + i) for i in range(cores)])
+        base = {"value": sum(r[0] for r in rs) / max(r[1] for r in rs), "unit": UNIT, "cores": cores,
+                "kind": "oracle", "single_core": {"value": u1 / t1, "cores": 1, "seconds": round(t1, 2)},
+                "sample": "the first 600 of the 2000 steps of the 120 Td swarm per process (one alone, then one "
+                          "per core with different seeds)"}
+    out = {"metric": "120 Td float64 swarm particle-updates/s (64 replicas, one launch per step)",
+           "value": upd64 / wall64, "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": "swarm-120Td-fp64-1e4x2000", "E_N_Td": 120.0, "electrons": C1_SWARM["n0"],
+                      "steps": C1_SWARM["n_steps"], "dt_ps": 1.0, "resampling": [C1_SWARM["n_lo"], C1_SWARM["n_hi"]],
+                      "replicas": reps, "timing": "wall clock around the swarm_run call (host-synchronising), "
+                                                  "after a warm-up run"},
+           "single_swarm": {"value": upd1 / wall1, "unit": UNIT, "seconds": wall1, "updates": upd1},
+           "replicas": {"value": upd64 / wall64, "unit": UNIT, "seconds": wall64, "updates": upd64},
+           "coefficients": coeff, "cpu_baseline": base}
+    print(json.dumps(out))
+
+
 def run_swarms(args):
     """256 swarms, E/N log-spaced 10-1000 Td, 1e4 float32 electrons each, adaptive
     resampling in [1e3, 1e6], dt = 1 ps: batched (one launch per step, CUDA graph,
@@ -429,15 +510,16 @@ def run_swarms(args):
     steps = args.steps if args.steps != 1990 else 5000
     t0 = time.perf_counter()
     if args.swarm_block and args.swarm_bps:
-        b, bps, ms_trial = args.swarm_block, args.swarm_bps, None
+        b, bps, chunk, mode, ms_trial = args.swarm_block, args.swarm_bps, 1024, 2, None
     else:
-        b, bps, ms_trial = swarm_autotune(gas, ENs, precision=32, n0=10000, n_steps=steps, dt=1e-12,
-                                          seed=2110144943, n_lo=1000, n_hi=1_000_000)
+        b, bps, chunk, mode, ms_trial = swarm_autotune(gas, ENs, precision=32, n0=10000, n_steps=steps, dt=1e-12,
+                                                       seed=2110144943, n_lo=1000, n_hi=1_000_000)
     t_tune = time.perf_counter() - t0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     res, mom, cnt = swarm_run(gas, ENs, precision=32, n0=10000, n_steps=steps, dt=1e-12, seed=2110144943, n_lo=1000,
-                              n_hi=1_000_000, want_moments=True, batched=True, block=b, blocks_per_sm=bps)
+                              n_hi=1_000_000, want_moments=True, batched=True, block=b, blocks_per_sm=bps,
+                              warp_chunk=chunk, use_graph=mode)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     updates = float(cnt.sum())
@@ -452,7 +534,9 @@ def run_swarms(args):
     w64 = time.perf_counter() - t0
     out = {"metric": "batched swarms particle-updates/s (256 E/N, float32, one launch per step)",
            "value": updates / wall, "unit": UNIT, "n_gpus": 1, "steps": steps, "wall_s": wall,
-           "tuning": {"block": b, "blocks_per_sm": bps, "trial_ms_per_step": ms_trial, "tune_s": t_tune},
+           "tuning": {"block": b, "blocks_per_sm": bps, "warp_chunk": chunk,
+                      "launch": {0: "kernels per step", 1: "step graph replayed", 2: "one persistent launch"}[mode],
+                      "trial_ms_per_step": ms_trial, "tune_s": t_tune},
            "particles_per_step": {"mean": float(cnt.mean(axis=0).mean() * 256), "final": int(cnt[:, -1].sum())},
            "plain_f64_sequential": {"value": float(c64.sum()) / w64, "unit": UNIT, "swarms": len(sub),
                                     "steps": 500, "wall_s": w64},
@@ -464,10 +548,11 @@ def run_swarms(args):
 
 def run_mlp(args):
     """Transport-data surrogate: 4096 training points from batched swarms (256
-    E/N values 10-1000 Td x 16 O2 fractions 0.1-0.3), full-batch Adam on the
-    GPU, inference on 2^24 query points, and the error against 64 fresh
-    held-out swarms at random (E/N, f) next to bilinear interpolation in the
-    training table (the method without the network)."""
+    E/N values 10-1000 Td x 16 O2 fractions 0.1-0.3, one batched call, each
+    swarm with its own gas composition), full-batch Adam on the GPU,
+    inference on 2^24 query points, and the error against 64 fresh held-out
+    swarms at random (E/N, f) (one batched call) next to bilinear
+    interpolation in the training table (the method without the network)."""
     import torch
     import __graft_entry__ as ge
     ge.build()
@@ -480,7 +565,7 @@ def run_mlp(args):
     fr = np.linspace(0.1, 0.3, 16)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    X, Y, _ = S.swarm_points(lambda f: W.synthetic_air(o2_frac=f), EN, fr, W.N_GAS, seed=2110144944, **kw)
+    X, Y, _ = S.swarm_points(W.synthetic_air(), EN, fr, W.N_GAS, seed=2110144944, **kw)
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
     sur = S.Surrogate(W.mlp_init(44), X, Y)
@@ -490,14 +575,10 @@ def run_mlp(args):
     q = W.mlp_query_points(64, 45)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    held = []
-    for k in range(len(q)):
-        res, _, _ = swarm_run(W.synthetic_air(o2_frac=q[k, 1]), q[k:k + 1, 0], batched=True, seed=2110145000 + k,
-                              **kw)
-        held.append(S.targets(res, q[k:k + 1, 0], W.N_GAS)[0])
+    res, _, _ = swarm_run(W.synthetic_air(), q[:, 0], o2_frac=q[:, 1], batched=True, seed=2110145000, **kw)
+    held = S.targets(res, q[:, 0], W.N_GAS)
     torch.cuda.synchronize()
     t_held = time.perf_counter() - t0
-    held = np.array(held)
     pred = sur.predict(q[:, 0], q[:, 1])
     lin = S.table_interp(EN, fr, Y.reshape(len(fr), len(EN), 6), q[:, 0], q[:, 1])
 
@@ -561,6 +642,8 @@ def main():
         return run_swarms(args)
     if args.workload == "mlp":
         return run_mlp(args)
+    if args.workload == "c1":
+        return run_c1(args)
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -598,6 +681,11 @@ def main():
         photo.update(geometry=1, weight_interval=wl["weight_interval"])
     ctx = streamer_context(wl, args.precision, cap, 2110144940 + rank, boundary=args.boundary,
                            adaptive_dt=not args.fixed_dt, extra=photo)
+    if args.host_solve:
+        ctx.set_poisson(1e-6, 200, device_loop=False)
+    vpre, vpost = (int(v) for v in args.vcycle.split(","))
+    if (vpre, vpost) != (2, 2) and not axi:
+        ctx.set_multigrid(vpre, vpost)
     n0 = ctx.seed_gaussian(wl["seed_n0"], wl["seed_radius"], wl["seed_center"], seed_weight(wl))
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -696,18 +784,17 @@ def main():
                              "dielectric relaxation with mu_e = 0.06 m^2/Vs, electron growth <= 20%/step)",
                        "simulated_ns": round(fin.t_total * 1e9, 4), "last_dt_ps": round(fin.dt_last * 1e12, 4),
                        "ne_max": fin.ne_max, "boundary": "absorbing faces" if args.boundary == 1 else "reflecting",
-                       "poisson": "multigrid-preconditioned CG, rtol 1e-6, every step",
+                       "poisson": "multigrid-preconditioned CG (V(%d,%d)-cycle), rtol 1e-6, every step" % (vpre, vpost),
                        "photoionization": "xi 0.075, p_q 40 mbar, Zheleznyak absorption" if (full or axi) else "off",
                        "l2": "flushed between timed steps (256 MB write outside the timed events)",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "particles_trace": n_trace},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm,
-                         "traffic": (PUSH_DRAM_BYTES_PER_PARENT * parents_per_launch
-                                     if (args.workload == "streamer" and args.grid == 128 and args.precision == 32
-                                         and PUSH_DRAM_BYTES_PER_PARENT)
+                         "traffic": (PUSH_DRAM_BYTES_PER_UPDATE * (parents_per_launch + children_per_launch)
+                                     if (args.workload == "streamer" and args.grid == 128 and args.precision == 32)
                                      else None),
-                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per parent, "
+                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per particle-update, "
                                            "profiles/k_push_streamer128.md, scaled to the mean launch",
                          "kernel": "k_push<%s,PIC>" % ("float" if args.precision == 32 else "double"),
                          "peak_source": peak_kind,

@@ -71,6 +71,8 @@ typedef struct pic_gas {
     const double *threshold; /* [n_proc] energy loss / ionization energy, eV */
     const double *density;   /* [n_proc] number density of the target species, m^-3 */
     const double *mass;      /* [n_proc] target mass for elastic recoil, kg (0 = infinite) */
+    const int *species;      /* [n_proc] target species, 0 = N2, 1 = O2 (NULL: untagged); swarm_run reads it
+                                when it is given per-swarm O2 fractions */
 } pic_gas;
 
 typedef struct pic_config {
@@ -237,6 +239,15 @@ int pic_step(pic_ctx *ctx, int n_steps, pic_step_stats *stats);
  * results.  Float64 and axisymmetric contexts always drive from the host.
  * rtol must be positive and max_cycles at least 1; errors: PIC_ERR_ARG. */
 int pic_set_poisson(pic_ctx *ctx, double rtol, int max_cycles, int device_loop);
+
+/* Smoothing of the V-cycle that preconditions the Cartesian coupled solve
+ * (Sec. 2.5): pre_sweeps red-black Gauss-Seidel sweeps before each
+ * restriction and post_sweeps after each prolongation, on every level
+ * (default 2 and 2).  Fewer sweeps make each CG iteration cheaper and may
+ * need more iterations for the same rtol; the solution's tolerance is
+ * unchanged.  Each in 1..4; errors: PIC_ERR_ARG, PIC_ERR_STATE for an
+ * axisymmetric context (its solve keeps V(2,2)). */
+int pic_set_multigrid(pic_ctx *ctx, int pre_sweeps, int post_sweeps);
 
 /* Deposits the current electrons (Sec. 2.1.3, cell-centred trilinear
  * weights in 64-bit fixed point) and returns the fixed-point grids (units of
@@ -418,12 +429,19 @@ typedef struct swarm_config {
     double kT_eV;
     unsigned long long seed; /* swarm s uses seed + s */
     double sample_from;      /* fraction of steps discarded before sampling (0.25) */
-    /* batched mode: all swarms advance together, one launch per step for
-     * every swarm, the step replayed from a CUDA graph */
+    /* batched mode: all swarms advance together over per-swarm segments of
+     * shared buffers; warps take item ranges of any swarm from one cursor */
     int batched;             /* 0: swarms one after another; 1: batched */
     int block;               /* batched: threads per block (64, 128 or 256); 0 = autotune */
     int blocks_per_sm;       /* batched: resident blocks per SM; 0 = autotune */
-    int use_graph;           /* batched: 1 = capture the step in a CUDA graph */
+    int use_graph;           /* batched: how the steps are launched.  0: kernels per step (resampling, prefix
+                                sums, parents, three product generations, counts); 1: that step recorded once
+                                in a CUDA graph and replayed; 2: one persistent kernel for every step (grid-wide
+                                barriers between the phases, as many product generations as a step needs),
+                                a cooperative launch recorded in a CUDA graph.  With block == 0 the autotuner
+                                picks 1 or 2 too. */
+    int warp_chunk;          /* batched: largest item range a warp takes at once (multiple of 32, 32..8192;
+                                0 = 1024, or the autotuned value when block == 0) */
 } swarm_config;
 
 typedef struct swarm_result {
@@ -433,19 +451,28 @@ typedef struct swarm_result {
 /* Workspace size for swarm_run and swarm_autotune; 0 for invalid input. */
 size_t swarm_workspace_bytes(const swarm_config *sc, int n_swarms);
 
-/* Batched mode only: times short trial runs of the batched step for block
- * sizes {64, 128, 256} and blocks per SM {1, 2, 3, 4, max} and returns the
- * fastest pair (and its ms per step).  Uses the same workspace as swarm_run;
- * the trial state is discarded. */
-int swarm_autotune(const swarm_config *sc, int n_swarms, const double *EN_Td, void *d_workspace,
-                   size_t workspace_bytes, int *block, int *blocks_per_sm, double *ms_per_step,
-                   pic_stream_t stream);
+/* Batched mode only: times short trial runs of the batched step and returns
+ * the fastest launch shape and its ms per step: block sizes {64, 128, 256} x
+ * blocks per SM {1, 2, 3, 4, max}, then the warp item range {256, 512, 1024,
+ * 2048} and the launch mode {1, 2} (see use_graph) for the best pair.  Uses
+ * the same workspace and arguments as swarm_run; the trial state is
+ * discarded.  Outputs may not be NULL. */
+int swarm_autotune(const swarm_config *sc, int n_swarms, const double *EN_Td, const double *o2_frac,
+                   void *d_workspace, size_t workspace_bytes, int *block, int *blocks_per_sm, int *warp_chunk,
+                   int *use_graph, double *ms_per_step, pic_stream_t stream);
 
-/* EN_Td: host [n_swarms]; results: host [n_swarms]; moments (optional):
- * host [n_swarms][n_steps][16]; counts (optional): host [n_swarms][n_steps]. */
-int swarm_run(const swarm_config *sc, int n_swarms, const double *EN_Td, void *d_workspace,
-              size_t workspace_bytes, swarm_result *results, double *moments, long long *counts,
-              pic_stream_t stream);
+/* EN_Td: host [n_swarms]; o2_frac: host [n_swarms] O2 fractions of the gas of
+ * each swarm (Sec. 2.3 uses 0.2), or NULL for the gas as given: with it, the
+ * target density of process k of swarm s is n_gas (1 - o2_frac[s]) for N2
+ * targets and n_gas o2_frac[s] for O2 targets (gas.species must be set;
+ * PIC_ERR_ARG otherwise), and each swarm gets its own rate table and nu_max.
+ * results: host [n_swarms]; moments (optional): host [n_swarms][n_steps][16];
+ * counts (optional): host [n_swarms][n_steps].  Errors: PIC_ERR_CAPACITY when
+ * a buffer or product queue ran full, PIC_ERR_TIMEOUT when a grid-wide
+ * barrier of the persistent kernel gave up waiting (the launch ended early). */
+int swarm_run(const swarm_config *sc, int n_swarms, const double *EN_Td, const double *o2_frac,
+              void *d_workspace, size_t workspace_bytes, swarm_result *results, double *moments,
+              long long *counts, pic_stream_t stream);
 
 /* ---------------------------------------------------------------- surrogate */
 /* Transport-data surrogate: the flux transport data that the local-field

@@ -30,7 +30,21 @@ enum : unsigned {
     kErrSplitCapacity = 16u, // merge/split output full
     kErrPhotoCapacity = 32u, // photoelectron queue full
     kErrPoissonLimit = 64u,  // a device-driven coupled solve reached its cycle limit
+    kErrBarrier = 128u,      // a grid-wide barrier of a persistent kernel gave up waiting
 };
+
+// Global loads with acquire semantics at GPU scope (flags written by other
+// blocks of the same launch).
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
 
 // ---------------------------------------------------------------- Philox4x32-10
 // Ten rounds of two 32x32 -> 64-bit multiplications (multipliers 0xD2511F53,

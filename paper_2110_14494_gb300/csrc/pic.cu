@@ -2295,6 +2295,7 @@ static size_t swarm_extra(const swarm_config* sc) {
 
 struct BatchLayout {
     size_t total, ctx, ctx_bytes, buf[2], cq[2], csw[2], cnt_in, cnt_out, prefix, bd, Ez, mom, counts, zref, zhist;
+    size_t tabs, numax, tau, dens, nmx, tab64;  // per-swarm rate tables
     long long segs, cap_child;
 };
 
@@ -2330,8 +2331,26 @@ static BatchLayout batch_layout(const swarm_config* sc, int n) {
     L.counts = take((size_t)n * sc->n_steps * 8);
     L.zref = take((size_t)n * 8);
     L.zhist = take((size_t)n * sc->n_steps * 8);
+    const int nb = sc->gas.n_bins, np = sc->gas.n_proc > 0 ? sc->gas.n_proc : 1;
+    L.tabs = take((size_t)n * nb * kTableStride * R);
+    L.numax = take((size_t)n * R);
+    L.tau = take((size_t)n * R);
+    L.dens = take((size_t)n * np * 8);
+    L.nmx = take((size_t)n * 8);
+    L.tab64 = take((size_t)nb * kTableStride * 8);
     L.total = o;
     return L;
+}
+
+// Target densities of the processes of a swarm with O2 fraction f: n_gas f
+// for O2 targets, n_gas (1 - f) for the others (Sec. 2.3: the gas is N2 and
+// O2); without fractions, the gas's own densities.
+static void swarm_densities(const swarm_config* sc, const double* o2_frac, int s, double* out) {
+    for (int k = 0; k < sc->gas.n_proc; ++k) {
+        if (!o2_frac) { out[k] = sc->gas.density[k]; continue; }
+        const double f = o2_frac[s];
+        out[k] = sc->gas.species[k] == 1 ? sc->n_gas * f : sc->n_gas * (1.0 - f);
+    }
 }
 
 extern "C" size_t swarm_workspace_bytes(const swarm_config* sc, int n_swarms) {
@@ -2479,7 +2498,48 @@ template <class T> struct BatchRunner {
         if (cap) cudaStreamDestroy(cap);
     }
 
-    int setup(const swarm_config* sc_, int n_, const double* EN, char* ws, cudaStream_t s_) {
+    // Rate table, nu_max and flight-time scale of every swarm's gas (its own
+    // O2 fraction, or the gas as given), built on the device.
+    int build_tables(char* ws, const double* o2) {
+        const int nb = c->n_bins, np = c->n_proc;
+        const double* d_gas = (const double*)(c->ws + c->L.gas);  // node energies, then cross sections
+        std::vector<double> dens((size_t)n * np);
+        for (int i = 0; i < n; ++i) swarm_densities(sc, o2, i, dens.data() + (size_t)i * np);
+        double* d_dens = (double*)(ws + L.dens);
+        unsigned long long* d_nmx = (unsigned long long*)(ws + L.nmx);
+        T* tabs = (T*)(ws + L.tabs);
+        cudaError_t e = cudaMemcpyAsync(d_dens, dens.data(), dens.size() * 8, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_nmx, 0, (size_t)n * 8, s);
+        for (int i = 0; i < n && e == cudaSuccess; ++i) {
+            k_rate_table<T><<<(nb + 127) / 128, 128, 0, s>>>(d_gas, d_gas + nb, d_dens + (size_t)i * np, np, nb,
+                                                             tabs + (size_t)i * nb * kTableStride,
+                                                             (double*)(ws + L.tab64), d_nmx + i);
+            e = cudaGetLastError();
+        }
+        std::vector<unsigned long long> bits((size_t)n);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(bits.data(), d_nmx, (size_t)n * 8, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return PIC_ERR_CUDA;
+        std::vector<T> numax((size_t)n), tau((size_t)n);
+        for (int i = 0; i < n; ++i) {
+            double v;
+            memcpy(&v, &bits[i], 8);
+            if (!(v > 0.0)) return PIC_ERR_ARG;
+            numax[i] = (T)v;
+            tau[i] = (T)(-0.69314718055994530942 / v);
+        }
+        e = cudaMemcpyAsync(ws + L.numax, numax.data(), (size_t)n * sizeof(T), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ws + L.tau, tau.data(), (size_t)n * sizeof(T), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return PIC_ERR_CUDA;
+        B.tab_s = tabs;
+        B.tab_stride = (long long)nb * kTableStride;
+        B.numax_s = (const T*)(ws + L.numax);
+        B.tau_s = (const T*)(ws + L.tau);
+        return PIC_OK;
+    }
+
+    int setup(const swarm_config* sc_, int n_, const double* EN, const double* o2, char* ws, cudaStream_t s_) {
         sc = sc_;
         n = n_;
         s = s_;
@@ -2490,6 +2550,9 @@ template <class T> struct BatchRunner {
         if (rc) return rc;
         memset(&B, 0, sizeof B);
         B.P = make_args<T>(c, MODE_SWARM);
+        B.warp_chunk = sc->warp_chunk > 0 ? sc->warp_chunk : kWarpChunk;
+        rc = build_tables(ws, o2);
+        if (rc) return rc;
         const size_t R = sizeof(T);
         for (int b = 0; b < 2; ++b) {
             Soa<T>& q = b == 0 ? B.in : B.out;
@@ -2536,8 +2599,38 @@ template <class T> struct BatchRunner {
         return BatchLaunch<T>::init(B, sc->n0, sqrt(sc->kT_eV * kQ / kMe), s);
     }
 
-    // Runs `steps` steps directly or from a two-step CUDA graph.
-    int run(int steps, int block, int grid, bool graph) {
+    // All `steps` steps in one persistent cooperative kernel, recorded in a
+    // CUDA graph (launched directly if the recording fails).  bps is capped
+    // at the blocks that can be resident together.
+    int run_persistent(int steps, int block, int bps) {
+        const int maxb = BatchLaunch<T>::persistent_blocks_per_sm(block);
+        if (maxb < 1) return PIC_ERR_CUDA;
+        const int grid = device_sms() * (bps < maxb ? bps : maxb);
+        if (!cap && cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return PIC_ERR_CUDA;
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t x = nullptr;
+        bool graphed = false;
+        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            const cudaError_t el = BatchLaunch<T>::run_persistent(B, steps, block, grid, cap);
+            const cudaError_t ee = cudaStreamEndCapture(cap, &g);
+            graphed = el == cudaSuccess && ee == cudaSuccess && g && cudaGraphInstantiate(&x, g, 0) == cudaSuccess;
+        }
+        cudaGetLastError();
+        cudaError_t e = graphed ? cudaGraphLaunch(x, s) : BatchLaunch<T>::run_persistent(B, steps, block, grid, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (x) cudaGraphExecDestroy(x);
+        if (g) cudaGraphDestroy(g);
+        return e == cudaSuccess ? PIC_OK : PIC_ERR_CUDA;
+    }
+
+    // Runs `steps` steps: kernels per step (mode 0), a two-step CUDA graph
+    // replayed (1), or one persistent kernel (2).
+    int run(int steps, int block, int bps, int mode) {
+        if (mode == 2) return run_persistent(steps, block, bps);
+        return run_steps(steps, block, device_sms() * bps, mode == 1);
+    }
+
+    int run_steps(int steps, int block, int grid, bool graph) {
         if (BatchLaunch<T>::prepare(block) != cudaSuccess) return PIC_ERR_CUDA;
         BatchArgs<T> Bo = B;
         std::swap(Bo.in, Bo.out);
@@ -2574,57 +2667,82 @@ template <class T> struct BatchRunner {
         return rc;
     }
 
-    int tune(int* best_block, int* best_bps, double* best_ms) {
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // ms per step of a short trial run (after two warm-up steps) of one
+    // launch shape; negative on a CUDA error.
+    double trial_ms(int block, int bps, long long chunk, int mode, cudaEvent_t e0, cudaEvent_t e1) {
+        const int trial = sc->n_steps < 10 ? sc->n_steps : 10;
+        B.warp_chunk = chunk;
+        if (init_state() != cudaSuccess) return -1.0;
+        if (run(2, block, bps, mode)) return -1.0;
+        cudaEventRecord(e0, s);
+        if (run(trial, block, bps, mode)) return -1.0;
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return -1.0;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms / trial;
+    }
+
+    // Launch-shape autotuner: block size x blocks per SM (graph replay,
+    // ranges of 1024 items), then the warp item range, then the launch mode.
+    int tune(int* best_block, int* best_bps, int* best_chunk, int* best_mode, double* best_ms) {
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         double best = 1e300;
-        const int trial = sc->n_steps < 10 ? sc->n_steps : 10;
+        int bb = 128, bp = 1, bm = 1;
+        long long bc = kWarpChunk;
+        int rc = PIC_OK;
         for (int block : {64, 128, 256}) {
             if (BatchLaunch<T>::prepare(block) != cudaSuccess) continue;
             const int maxb = BatchLaunch<T>::max_blocks_per_sm(block);
             for (int bps : {1, 2, 3, 4, maxb}) {
                 if (bps > maxb) continue;
-                if (init_state() != cudaSuccess) return PIC_ERR_CUDA;
-                if (run(2, block, sms * bps, false)) return PIC_ERR_CUDA;
-                cudaEventRecord(e0, s);
-                if (run(trial, block, sms * bps, false)) return PIC_ERR_CUDA;
-                cudaEventRecord(e1, s);
-                cudaEventSynchronize(e1);
-                float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                const double per = ms / trial;
-                if (per < best) { best = per; *best_block = block; *best_bps = bps; }
+                const double per = trial_ms(block, bps, kWarpChunk, 1, e0, e1);
+                if (per < 0) { rc = PIC_ERR_CUDA; break; }
+                if (per < best) { best = per; bb = block; bp = bps; }
             }
+            if (rc) break;
+        }
+        for (long long chunk : {256ll, 512ll, 2048ll}) {
+            if (rc) break;
+            const double per = trial_ms(bb, bp, chunk, 1, e0, e1);
+            if (per < 0) { rc = PIC_ERR_CUDA; break; }
+            if (per < best) { best = per; bc = chunk; }
+        }
+        if (!rc) {
+            const double per = trial_ms(bb, bp, bc, 2, e0, e1);
+            if (per < 0) rc = PIC_ERR_CUDA;
+            else if (per < best) { best = per; bm = 2; }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        B.warp_chunk = bc;
+        *best_block = bb;
+        *best_bps = bp;
+        *best_chunk = (int)bc;
+        *best_mode = bm;
         *best_ms = best;
-        return PIC_OK;
+        return rc;
     }
 };
 
 template <class T>
-static int run_batched(const swarm_config* sc, int n, const double* EN, char* ws, cudaStream_t s, swarm_result* res,
-                       double* moments, long long* counts) {
+static int run_batched(const swarm_config* sc, int n, const double* EN, const double* o2, char* ws, cudaStream_t s,
+                       swarm_result* res, double* moments, long long* counts) {
     BatchRunner<T> R;
-    int rc = R.setup(sc, n, EN, ws, s);
+    int rc = R.setup(sc, n, EN, o2, ws, s);
     if (rc) return rc;
-    int block = sc->block, bps = sc->blocks_per_sm;
+    int block = sc->block, bps = sc->blocks_per_sm, mode = sc->use_graph, chunk = sc->warp_chunk;
     if (block == 0 || bps == 0) {
         double ms;
-        rc = R.tune(&block, &bps, &ms);
+        rc = R.tune(&block, &bps, &chunk, &mode, &ms);
         if (rc) return rc;
     }
     if (block != 64 && block != 128 && block != 256) return PIC_ERR_ARG;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    R.B.warp_chunk = chunk > 0 ? chunk : kWarpChunk;
     if (R.init_state() != cudaSuccess) return PIC_ERR_CUDA;
-    rc = R.run(sc->n_steps, block, sms * bps, sc->use_graph != 0);
+    rc = R.run(sc->n_steps, block, bps, mode);
     if (rc) return rc;
     const int ns = sc->n_steps;
     std::vector<double> hm((size_t)n * ns * kNMom), hz((size_t)n * ns);
@@ -2636,6 +2754,7 @@ static int run_batched(const swarm_config* sc, int n, const double* EN, char* ws
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, R.B.bd, sizeof hb, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return PIC_ERR_CUDA;
+    if (hb.err & kErrBarrier) return PIC_ERR_TIMEOUT;
     if (hb.err) return PIC_ERR_CAPACITY;
     // z moments back to the origin: z = dz + r
     for (size_t r = 0; r < (size_t)n * ns; ++r) {
@@ -2657,45 +2776,56 @@ static int run_batched(const swarm_config* sc, int n, const double* EN, char* ws
     return PIC_OK;
 }
 
-static int swarm_check(const swarm_config* sc, int n_swarms, const double* EN_Td, void* d_ws, size_t ws_bytes) {
+static int swarm_check(const swarm_config* sc, int n_swarms, const double* EN_Td, const double* o2, void* d_ws,
+                       size_t ws_bytes) {
     if (!sc || n_swarms < 1 || !EN_Td || !d_ws || ((uintptr_t)d_ws & 255)) return PIC_ERR_ARG;
     if (sc->n0 < 1 || sc->n0 > sc->capacity || sc->n_steps < 1 || !(sc->n_gas > 0) || !(sc->kT_eV >= 0) ||
         sc->n_lo < 0 || sc->n_hi < sc->n_lo || sc->capacity < 2 * sc->n_hi)
         return PIC_ERR_ARG;
+    if (sc->batched && (sc->use_graph < 0 || sc->use_graph > 2 || sc->warp_chunk < 0 || sc->warp_chunk > 8192 ||
+                        (sc->warp_chunk % 32) != 0))
+        return PIC_ERR_ARG;
+    if (o2) {
+        if (!sc->gas.species) return PIC_ERR_ARG;
+        for (int i = 0; i < n_swarms; ++i)
+            if (!(o2[i] >= 0.0 && o2[i] <= 1.0)) return PIC_ERR_ARG;
+    }
     const size_t need = swarm_workspace_bytes(sc, n_swarms);
     if (need == 0 || ws_bytes < need) return PIC_ERR_ARG;
     return PIC_OK;
 }
 
-extern "C" int swarm_autotune(const swarm_config* sc, int n_swarms, const double* EN_Td, void* d_ws, size_t ws_bytes,
-                              int* block, int* blocks_per_sm, double* ms_per_step, pic_stream_t stream) {
-    if (!sc || !sc->batched || !block || !blocks_per_sm) return PIC_ERR_ARG;
-    int rc = swarm_check(sc, n_swarms, EN_Td, d_ws, ws_bytes);
+extern "C" int swarm_autotune(const swarm_config* sc, int n_swarms, const double* EN_Td, const double* o2_frac,
+                              void* d_ws, size_t ws_bytes, int* block, int* blocks_per_sm, int* warp_chunk,
+                              int* use_graph, double* ms_per_step, pic_stream_t stream) {
+    if (!sc || !sc->batched || !block || !blocks_per_sm || !warp_chunk || !use_graph || !ms_per_step)
+        return PIC_ERR_ARG;
+    int rc = swarm_check(sc, n_swarms, EN_Td, o2_frac, d_ws, ws_bytes);
     if (rc) return rc;
-    double ms = 0;
     if (sc->precision == 32) {
         BatchRunner<float> R;
-        rc = R.setup(sc, n_swarms, EN_Td, (char*)d_ws, (cudaStream_t)stream);
-        if (!rc) rc = R.tune(block, blocks_per_sm, &ms);
+        rc = R.setup(sc, n_swarms, EN_Td, o2_frac, (char*)d_ws, (cudaStream_t)stream);
+        if (!rc) rc = R.tune(block, blocks_per_sm, warp_chunk, use_graph, ms_per_step);
     } else {
         BatchRunner<double> R;
-        rc = R.setup(sc, n_swarms, EN_Td, (char*)d_ws, (cudaStream_t)stream);
-        if (!rc) rc = R.tune(block, blocks_per_sm, &ms);
+        rc = R.setup(sc, n_swarms, EN_Td, o2_frac, (char*)d_ws, (cudaStream_t)stream);
+        if (!rc) rc = R.tune(block, blocks_per_sm, warp_chunk, use_graph, ms_per_step);
     }
-    if (ms_per_step) *ms_per_step = ms;
     return rc;
 }
 
-extern "C" int swarm_run(const swarm_config* sc, int n_swarms, const double* EN_Td, void* d_ws, size_t ws_bytes,
-                         swarm_result* results, double* moments, long long* counts, pic_stream_t stream) {
+extern "C" int swarm_run(const swarm_config* sc, int n_swarms, const double* EN_Td, const double* o2_frac,
+                         void* d_ws, size_t ws_bytes, swarm_result* results, double* moments, long long* counts,
+                         pic_stream_t stream) {
     if (!results) return PIC_ERR_ARG;
-    int rcc = swarm_check(sc, n_swarms, EN_Td, d_ws, ws_bytes);
+    int rcc = swarm_check(sc, n_swarms, EN_Td, o2_frac, d_ws, ws_bytes);
     if (rcc) return rcc;
     if (sc->batched)
         return sc->precision == 32
-                   ? run_batched<float>(sc, n_swarms, EN_Td, (char*)d_ws, (cudaStream_t)stream, results, moments, counts)
-                   : run_batched<double>(sc, n_swarms, EN_Td, (char*)d_ws, (cudaStream_t)stream, results, moments,
-                                         counts);
+                   ? run_batched<float>(sc, n_swarms, EN_Td, o2_frac, (char*)d_ws, (cudaStream_t)stream, results,
+                                        moments, counts)
+                   : run_batched<double>(sc, n_swarms, EN_Td, o2_frac, (char*)d_ws, (cudaStream_t)stream, results,
+                                         moments, counts);
     const size_t need = swarm_workspace_bytes(sc, n_swarms);
     pic_config pc = swarm_pic_config(sc);
     Layout L = make_layout(&pc);
@@ -2703,8 +2833,11 @@ extern "C" int swarm_run(const swarm_config* sc, int n_swarms, const double* EN_
     long long* d_cnt = (long long*)((char*)d_ws + L.total + al256((size_t)sc->n_steps * kNMom * 8));
     std::vector<double> hm((size_t)sc->n_steps * kNMom);
     std::vector<long long> hc((size_t)sc->n_steps);
+    std::vector<double> dens((size_t)(sc->gas.n_proc > 0 ? sc->gas.n_proc : 1));
     for (int s = 0; s < n_swarms; ++s) {
         pc.seed = sc->seed + (unsigned long long)s;
+        swarm_densities(sc, o2_frac, s, dens.data());
+        pc.gas.density = dens.data();
         pic_ctx* c = nullptr;
         int rc = pic_init(&pc, d_ws, L.total, nullptr, stream, &c);
         if (rc) return rc;
@@ -2744,6 +2877,21 @@ extern "C" int pic_set_poisson(pic_ctx* c, double rtol, int max_cycles, int devi
     c->cfg.poisson_rtol = rtol;
     c->cfg.poisson_max_cycles = max_cycles;
     c->fgraph_off = device_loop == 0;
+    return PIC_OK;
+}
+
+extern "C" int pic_set_multigrid(pic_ctx* c, int pre_sweeps, int post_sweeps) {
+    if (!c || pre_sweeps < 1 || pre_sweeps > 4 || post_sweeps < 1 || post_sweeps > 4) return PIC_ERR_ARG;
+    if (c->g.axi) return c->fail(PIC_ERR_STATE, "the axisymmetric solve keeps its V(2,2)-cycle");
+    // recorded graphs hold the old cycle
+    for (int q = 0; q < 4; ++q)
+        if (c->fgraph[q]) {
+            cudaGraphExecDestroy(c->fgraph[q]);
+            c->fgraph[q] = nullptr;
+        }
+    c->mg.release();
+    c->mg.pre = pre_sweeps;
+    c->mg.post = post_sweeps;
     return PIC_OK;
 }
 

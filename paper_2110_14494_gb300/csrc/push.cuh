@@ -347,10 +347,19 @@ __device__ __forceinline__ void deposit_at(const PushArgs<T>& A, T x0, T x1, T x
 // of dividing: a flight time then carries an absolute error near 1e-7 / nu_max
 // (far below a cell crossing), a table coordinate one near 1e-5 of a bin, and
 // the scattering cosine a reciprocal square root.
+// The collision rates a candidate event is tested against: the table
+// ([n_bins][8]: the rates, zeros, their total), its maximum total nu_max and
+// -ln 2 / nu_max.  One gas for a PIC context; batched swarms of different
+// compositions each have their own.
+template <class T> struct Rates {
+    const T* tab;
+    T nu_max, tau_scale;
+};
+
 template <class T> struct EvArith;
 template <> struct EvArith<double> {
-    static __device__ __forceinline__ double flight(const PushArgs<double>& A, double u0) {
-        return -log(u0) / A.nu_max;
+    static __device__ __forceinline__ double flight(const Rates<double>& R, double u0) {
+        return -log(u0) / R.nu_max;
     }
     static __device__ __forceinline__ double coord(const PushArgs<double>& A, double e) {
         return (log(e) - A.l0) * A.inv_dl;
@@ -361,8 +370,8 @@ template <> struct EvArith<double> {
     }
 };
 template <> struct EvArith<float> {
-    static __device__ __forceinline__ float flight(const PushArgs<float>& A, float u0) {
-        return __log2f(u0) * A.tau_scale;
+    static __device__ __forceinline__ float flight(const Rates<float>& R, float u0) {
+        return __log2f(u0) * R.tau_scale;
     }
     static __device__ __forceinline__ float coord(const PushArgs<float>& A, float e) {
         return fmaf(__log2f(e), A.inv_dl2, -A.l0t);
@@ -392,13 +401,13 @@ __device__ __forceinline__ void table_pos(const PushArgs<T>& A, T e, int& j, T& 
 // Chooses the process for a candidate collision: the smallest k with
 // u1 nu_max < sum_{i<=k} nu_i(eps); -1 = null collision.
 template <class T, bool FAST>
-__device__ __forceinline__ int select_process(const PushArgs<T>& A, const T* tab, T e, T u1, LStats& ls) {
+__device__ __forceinline__ int select_process(const PushArgs<T>& A, const Rates<T>& R, T e, T u1, LStats& ls) {
     int j;
     T f;
     table_pos(A, e, j, f, ls);
-    const T* r0 = tab + j * kTableStride;
+    const T* r0 = R.tab + j * kTableStride;
     const T* r1 = r0 + kTableStride;
-    const T target = u1 * A.nu_max;
+    const T target = u1 * R.nu_max;
     if (FAST) {
         const T t0 = __ldg(r0 + 7), t1 = __ldg(r1 + 7);
         const T tot = t0 + f * (t1 - t0);
@@ -498,11 +507,11 @@ __device__ __forceinline__ void photo_test(const PushArgs<T>& A, const Keys& K, 
 // positive-ion event); attachment returns EV_ATTACHED (the caller records the
 // negative-ion event at the electron's position) and ends the electron.
 template <class T, int MODE, bool FAST, bool STATS>
-__device__ __forceinline__ int event(const PushArgs<T>& A, const Keys& K, uint32_t step, const ProcSmem<T>* ps,
-                                     Lane<T>& L, LStats& ls, T& sp) {
+__device__ __forceinline__ int event(const PushArgs<T>& A, const Rates<T>& R, const Keys& K, uint32_t step,
+                                     const ProcSmem<T>* ps, Lane<T>& L, LStats& ls, T& sp) {
     const u32x4 r = draw_words(K, L.id, step, L.k);
     ++L.k;
-    const T tau = EvArith<T>::flight(A, unif<T>(r.x));
+    const T tau = EvArith<T>::flight(R, unif<T>(r.x));
     if (tau >= L.t_left) { fly(L.d, L.v, L.a, L.t_left); return EV_DONE; }
     fly(L.d, L.v, L.a, tau);
     L.t_left -= tau;
@@ -510,7 +519,7 @@ __device__ __forceinline__ int event(const PushArgs<T>& A, const Keys& K, uint32
     T* v = L.v;
     const T v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
     const T e = Arith<T>::energy(v2);
-    const int p = select_process<T, FAST>(A, A.table, e, unif<T>(r.y), ls);
+    const int p = select_process<T, FAST>(A, R, e, unif<T>(r.y), ls);
     if (p < 0) { ++ls.nulls; return EV_CONTINUE; }
     if (STATS) ++ls.coll[p & 7];
     const int kind = ps->kind[p];
@@ -888,6 +897,7 @@ __device__ __forceinline__ void collide_loop(const PushArgs<T>& A, const ProcSme
     ls.zero();
     MomAcc<T> M;
     if (MODE == MODE_SWARM) M.zero();
+    const Rates<T> rates{A.table, A.nu_max, A.tau_scale};
     Lane<T> L;
     bool active = false, dry = false;
     // warp-uniform counters: input stage head and size, output stage size,
@@ -970,7 +980,7 @@ __device__ __forceinline__ void collide_loop(const PushArgs<T>& A, const ProcSme
         // 4. one candidate collision
         int r = EV_CONTINUE;
         T sp = (T)0;
-        if (active) r = event<T, MODE, FAST, STATS>(A, A.K, A.step, ps, L, ls, sp);
+        if (active) r = event<T, MODE, FAST, STATS>(A, rates, A.K, A.step, ps, L, ls, sp);
         const bool done = r == EV_DONE, ion = r == EV_IONIZED, att = r == EV_ATTACHED;
         if (done || att) active = false;
         // 5. ionization products wait in the warp queue as compact entries (the

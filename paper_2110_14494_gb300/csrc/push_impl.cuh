@@ -112,6 +112,38 @@ template <class T> cudaError_t BatchLaunch<T>::prepare(int block) {
     return e;
 }
 
+template <class T> int BatchLaunch<T>::persistent_blocks_per_sm(int block) {
+    constexpr bool FAST = sizeof(T) == 4;
+    const size_t sm = smem(block);
+    if (cudaFuncSetAttribute(k_batch_run<T, FAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+        return 0;
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_run<T, FAST>, block, sm) != cudaSuccess) return 0;
+    return b;
+}
+
+template <class T>
+cudaError_t BatchLaunch<T>::run_persistent(const BatchArgs<T>& B, int n_steps, int block, int grid, cudaStream_t s) {
+    constexpr bool FAST = sizeof(T) == 4;
+    const size_t sm = smem(block);
+    cudaError_t e = cudaFuncSetAttribute(k_batch_run<T, FAST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    // barrier arrivals, generation and abort flag start at zero
+    e = cudaMemsetAsync(&B.bd->bar_count, 0, 3 * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_batch_run<T, FAST>, B, n_steps);
+}
+
 template <class T>
 cudaError_t BatchLaunch<T>::step(BatchArgs<T> B, int block, int grid, cudaStream_t s, long long* launches) {
     constexpr bool FAST = sizeof(T) == 4;

@@ -15,12 +15,20 @@
 namespace pic {
 
 constexpr int kMaxSwarms = 4096;
-constexpr int kBatchGenerations = 3;  // children generations per step inside the graph
+constexpr int kBatchGenerations = 3;  // children generations per step inside the replayed graph
+constexpr int kMaxGenerations = 62;   // product generations per step of the persistent kernel
 
 struct BatchDev {
     unsigned long long fetch, fetch_c, n_child, n_spill;
     unsigned int err;
     unsigned int step;  // the step being run (1-based)
+    // persistent kernel: fetch cursors (parents, then generation g at g + 1)
+    // and product counts (gcnt[g]: products queued by generation g - 1, the
+    // parents at 0), zeroed at the start of every step
+    unsigned long long cur[kMaxGenerations + 1];
+    unsigned long long gcnt[kMaxGenerations + 1];
+    // grid barrier: arrivals, generation, abort flag
+    unsigned int bar_count, bar_gen, abort;
 };
 
 template <class T> struct BatchArgs {
@@ -44,7 +52,27 @@ template <class T> struct BatchArgs {
     int n_steps;
     long long n_lo, n_hi;
     int gen;
+    // collision rates of each swarm's gas: table of swarm s at tab_s + s *
+    // tab_stride (stride 0: one gas for all), nu_max and -ln 2 / nu_max
+    const T* tab_s;
+    long long tab_stride;
+    const T* numax_s;
+    const T* tau_s;
+    long long warp_chunk;       // largest item range a warp takes at once (a multiple of 32)
 };
+
+// The step's input and output buffers: B.in and B.out, or swapped (FLIP) on
+// the odd steps of the persistent kernel.
+template <class T, bool FLIP> __device__ __forceinline__ const Soa<T>& src_buf(const BatchArgs<T>& B) {
+    return FLIP ? B.out : B.in;
+}
+template <class T, bool FLIP> __device__ __forceinline__ const Soa<T>& dst_buf(const BatchArgs<T>& B) {
+    return FLIP ? B.in : B.out;
+}
+
+template <class T> __device__ __forceinline__ Rates<T> swarm_rates(const BatchArgs<T>& B, int s) {
+    return Rates<T>{B.tab_s + (long long)s * B.tab_stride, B.numax_s[s], B.tau_s[s]};
+}
 
 __device__ __forceinline__ Keys dev_keys(uint64_t seed) {
     Keys k;
@@ -69,10 +97,9 @@ __device__ __forceinline__ int swarm_of(const long long* pre, int n, long long i
 }
 
 // Resampling per swarm, in place (see k_resample): thinning above n_hi,
-// duplication below n_lo.
-template <class T> __global__ void k_batch_resample(const BatchArgs<T> B) {
+// duplication below n_lo.  Grid-stride over the step's items.
+template <class T, bool FLIP> __device__ void batch_resample(const BatchArgs<T>& B, uint32_t step) {
     const long long total = B.prefix[B.n_swarms];
-    const uint32_t step = B.bd->step;
     for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < total;
          it += (long long)gridDim.x * blockDim.x) {
         const int s = swarm_of(B.prefix, B.n_swarms, it);
@@ -81,7 +108,7 @@ template <class T> __global__ void k_batch_resample(const BatchArgs<T> B) {
         if (!thin && !dup) continue;
         const long long i = s * B.cap_s + (it - B.prefix[s]);
         const Keys K = dev_keys(B.seed + (uint64_t)s);
-        const Soa<T>& p = B.in;
+        const Soa<T>& p = src_buf<T, FLIP>(B);
         if (thin) {
             const u32x4 r = draw_words(K, p.id[i], step, 0xA0000000u);
             if (!(unif<T>(r.x) < (T)0.5)) p.r[PW][i] = (T)0;
@@ -92,6 +119,7 @@ template <class T> __global__ void k_batch_resample(const BatchArgs<T> B) {
         }
     }
 }
+template <class T> __global__ void k_batch_resample(const BatchArgs<T> B) { batch_resample<T, false>(B, B.bd->step); }
 
 // Exclusive prefix sums of the per-swarm counts (one block calls it).
 template <class T> __device__ void scan_counts(const BatchArgs<T>& B) {
@@ -124,8 +152,7 @@ template <class T> __device__ void scan_counts(const BatchArgs<T>& B) {
 
 // After resampling: duplicated swarms double their counts, prefix sums of the
 // step's work items, cursors and output counters reset.  One block.
-template <class T> __global__ void k_batch_begin(const BatchArgs<T> B) {
-    const uint32_t step = B.bd->step;
+template <class T> __device__ void batch_begin(const BatchArgs<T>& B, uint32_t step) {
     for (int s = threadIdx.x; s < B.n_swarms; s += blockDim.x) {
         const long long n = B.cnt_in[s];
         if (n > 0 && n < B.n_lo && 2 * n <= B.cap_s) B.cnt_in[s] = 2 * n;
@@ -140,7 +167,12 @@ template <class T> __global__ void k_batch_begin(const BatchArgs<T> B) {
         B.bd->n_child = 0;
         B.bd->n_spill = 0;
     }
+    for (int g = threadIdx.x; g <= kMaxGenerations; g += blockDim.x) {
+        B.bd->cur[g] = 0;
+        B.bd->gcnt[g] = 0;
+    }
 }
+template <class T> __global__ void k_batch_begin(const BatchArgs<T> B) { batch_begin(B, B.bd->step); }
 
 // Before children generation g >= 1.
 static __global__ void k_batch_nextgen(BatchDev* bd, int gen) {
@@ -151,8 +183,7 @@ static __global__ void k_batch_nextgen(BatchDev* bd, int gen) {
 
 // End of a step: counts recorded and made the next step's input counts, with
 // their prefix sums (used by the next step's resampling).  One block.
-template <class T> __global__ void k_batch_end(const BatchArgs<T> B) {
-    const uint32_t step = B.bd->step;
+template <class T> __device__ void batch_end(const BatchArgs<T>& B, uint32_t step) {
     for (int s = threadIdx.x; s < B.n_swarms; s += blockDim.x) {
         unsigned long long n = B.cnt_out[s];
         if (n > (unsigned long long)B.cap_s) n = (unsigned long long)B.cap_s;
@@ -166,6 +197,7 @@ template <class T> __global__ void k_batch_end(const BatchArgs<T> B) {
     __syncthreads();
     scan_counts(B);
 }
+template <class T> __global__ void k_batch_end(const BatchArgs<T> B) { batch_end(B, B.bd->step); }
 
 // Initial counts: n0 per swarm, prefix sums, step 1.  One block.
 template <class T> __global__ void k_batch_init(const BatchArgs<T> B, long long n0) {
@@ -215,7 +247,7 @@ static __global__ void k_batch_step_advance(BatchDev* bd, int g_last) {
     bd->step += 1;
 }
 
-constexpr long long kWarpChunk = 1024;  // largest warp-private item range
+constexpr long long kWarpChunk = 1024;  // default largest warp-private item range (BatchArgs::warp_chunk)
 
 template <class T> struct BatchStage {
     T in[32 * kRow];
@@ -307,7 +339,7 @@ template <class T> constexpr size_t batch_smem(int warps) { return (size_t)warps
 
 // Output flush for batched swarms: entries [0, cnt) appended to their swarms'
 // segments (one cursor increment per swarm group) and their moments added.
-template <class T>
+template <class T, bool FLIP>
 __device__ __forceinline__ void batch_flush_out(const BatchArgs<T>& B, BatchStage<T>* sg, int& n, int cnt,
                                                 uint32_t step) {
     const int lane = threadIdx.x & 31;
@@ -334,7 +366,7 @@ __device__ __forceinline__ void batch_flush_out(const BatchArgs<T>& B, BatchStag
     if (live) {
         const unsigned long long slot = base + __popc(grp & ((1u << lane) - 1u));
         if ((long long)slot < B.cap_s) {
-            store(B.out, (unsigned long long)(s * B.cap_s) + slot, x, v, a, w, id);
+            store(dst_buf<T, FLIP>(B), (unsigned long long)(s * B.cap_s) + slot, x, v, a, w, id);
             stored = true;
         } else {
             atomicOr(&B.bd->err, kErrOutCapacity);
@@ -354,11 +386,10 @@ __device__ __forceinline__ void batch_flush_out(const BatchArgs<T>& B, BatchStag
 
 template <class T>
 __device__ __forceinline__ void batch_flush_children(const BatchArgs<T>& B, BatchStage<T>* sg, int& n, int cnt,
-                                                     int dst) {
+                                                     int dst, unsigned long long* cnt_p) {
     const int lane = threadIdx.x & 31;
     __syncwarp();
     unsigned long long s0 = 0;
-    unsigned long long* cnt_p = dst ? &B.bd->n_spill : &B.bd->n_child;
     if (lane == 0) s0 = atomicAdd(cnt_p, (unsigned long long)cnt);
     s0 = __shfl_sync(kFull, s0, 0);
     if (lane < cnt) {
@@ -390,43 +421,28 @@ __device__ __forceinline__ void batch_flush_children(const BatchArgs<T>& B, Batc
     n = rest;
 }
 
-// The lane-refill collision loop of collide_loop, for batched swarms.
-// CHILD = false: items are the swarms' electrons; CHILD = true: products of
-// generation B.gen (queue B.gen & 1), whose own products are staged into the
-// other queue for the next generation.
-template <class T, bool FAST, bool CHILD>
-__global__ void __launch_bounds__(256) k_batch_collide(const BatchArgs<T> B) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ ProcSmem<T> ps;
-    if (threadIdx.x < 8) {
-        ps.thr[threadIdx.x] = B.P.thr[threadIdx.x];
-        ps.mratio[threadIdx.x] = B.P.mratio[threadIdx.x];
-        ps.kind[threadIdx.x] = B.P.kind[threadIdx.x];
-    }
-    __syncthreads();
-    BatchStage<T>* sg = reinterpret_cast<BatchStage<T>*>(smem_raw) + (threadIdx.x >> 5);
+// The lane-refill collision loop of collide_loop, for batched swarms: one
+// phase of a step.  CHILD = false: the work items are the swarms' electrons
+// (n_items of them); their products are staged per warp and queued in queue
+// dstq (append counter dst_cnt).  CHILD = true: the items are the products
+// queued in srcq; their own products stay on the lane's stack, and what it
+// cannot hold goes to queue dstq for the next generation.  Every warp takes
+// item ranges from `cursor` until the phase runs dry.
+template <class T, bool FAST, bool CHILD, bool FLIP>
+__device__ void batch_phase(const BatchArgs<T>& B, const ProcSmem<T>& ps, BatchStage<T>* sg, uint32_t step,
+                            long long n_items, unsigned long long* cursor, int srcq, int dstq,
+                            unsigned long long* dst_cnt) {
     const int lane = threadIdx.x & 31;
     if (lane < 14) sg->macc[lane] = 0.0;
     if (lane == 0) sg->macc_s = -1;
     __syncwarp();
     const unsigned lt = (1u << lane) - 1u;
-    const uint32_t step = B.bd->step;
-    const int srcq = B.gen & 1, dstq = srcq ^ 1;
-    long long n_items;
-    unsigned long long* cursor;
-    if (CHILD) {
-        n_items = (long long)(srcq ? B.bd->n_spill : B.bd->n_child);
-        if (n_items > B.cap_child) n_items = B.cap_child;
-        cursor = &B.bd->fetch_c;
-    } else {
-        n_items = B.prefix[B.n_swarms];
-        cursor = &B.bd->fetch;
-    }
     const T qm = (T)(kQ / kMe);
     LStats ls;
     ls.zero();
     Lane<T> L;
     Keys K = dev_keys(B.seed);
+    Rates<T> R = swarm_rates(B, 0);
     int s_cur = -1, s_cache = -1;
     long long w_next = 0, w_end = 0;
     bool active = false, dry = false;
@@ -457,6 +473,7 @@ __global__ void __launch_bounds__(256) k_batch_collide(const BatchArgs<T> B) {
                     flush_event_weights(B, s_cur, step, ls);
                     s_cur = s;
                     K = dev_keys(B.seed + (uint64_t)s);
+                    R = swarm_rates(B, s);
                 }
                 for (int d = 0; d < 3; ++d) { L.x[d] = r[d]; L.v[d] = r[3 + d]; L.d[d] = (T)0; }
                 L.a[0] = (T)0;
@@ -481,7 +498,7 @@ __global__ void __launch_bounds__(256) k_batch_collide(const BatchArgs<T> B) {
                     const long long rem = n_items - (long long)seen;
                     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
                     long long want_g = rem > 0 ? rem / (4 * warps) : 32;
-                    want_g = want_g < 32 ? 32 : (want_g > kWarpChunk ? kWarpChunk : want_g);
+                    want_g = want_g < 32 ? 32 : (want_g > B.warp_chunk ? B.warp_chunk : want_g);
                     g = (unsigned long long)(want_g & ~31ll);
                     b = atomicAdd(cursor, g);
                 }
@@ -518,10 +535,11 @@ __global__ void __launch_bounds__(256) k_batch_collide(const BatchArgs<T> B) {
                         if (s < 0 || it < B.prefix[s] || it >= B.prefix[s + 1]) s = swarm_of(B.prefix, B.n_swarms, it);
                         s_cache = s;
                         const long long i = s * B.cap_s + (it - B.prefix[s]);
-                        for (int f = 0; f < 6; ++f) r[f] = B.in.r[f][i];
-                        r[9] = B.in.r[PW][i];
+                        const Soa<T>& in = src_buf<T, FLIP>(B);
+                        for (int f = 0; f < 6; ++f) r[f] = in.r[f][i];
+                        r[9] = in.r[PW][i];
                         r[10] = B.P.dt;
-                        sg->in_id[lane] = B.in.id[i];
+                        sg->in_id[lane] = in.id[i];
                         sg->in_s[lane] = s;
                     }
                 }
@@ -536,7 +554,7 @@ __global__ void __launch_bounds__(256) k_batch_collide(const BatchArgs<T> B) {
         }
         int r = EV_CONTINUE;
         T sp = (T)0;
-        if (active) r = event<T, MODE_SWARM, FAST, false>(B.P, K, step, &ps, L, ls, sp);
+        if (active) r = event<T, MODE_SWARM, FAST, false>(B.P, R, K, step, &ps, L, ls, sp);
         const bool done = r == EV_DONE, ion = r == EV_IONIZED;
         if (r == EV_DONE || r == EV_ATTACHED) active = false;
         if (CHILD && ion) {
@@ -549,8 +567,7 @@ __global__ void __launch_bounds__(256) k_batch_collide(const BatchArgs<T> B) {
                 stk.id[t] = cid;
                 stk.t[t] = L.t_left;
             } else {  // stack full: queue the compact entry for the next generation
-                unsigned long long* cnt_p = dstq ? &B.bd->n_spill : &B.bd->n_child;
-                const unsigned long long q = atomicAdd(cnt_p, 1ull);
+                const unsigned long long q = atomicAdd(dst_cnt, 1ull);
                 if ((long long)q < B.cap_child) {
                     const ChildQ<T>& Q = B.cq[dstq];
                     Q.p.r[PX][q] = L.x[0] + L.d[0]; Q.p.r[PY][q] = L.x[1] + L.d[1]; Q.p.r[PZ][q] = L.x[2] + L.d[2];
@@ -581,7 +598,7 @@ __global__ void __launch_bounds__(256) k_batch_collide(const BatchArgs<T> B) {
                 sg->ch_s[e] = s_cur;
             }
             n_ch += __popc(im);
-            if (n_ch >= 32) batch_flush_children(B, sg, n_ch, 32, 0);
+            if (n_ch >= 32) batch_flush_children(B, sg, n_ch, 32, dstq, dst_cnt);
         }
         const unsigned dm = __ballot_sync(kFull, done);
         if (dm) {
@@ -596,13 +613,137 @@ __global__ void __launch_bounds__(256) k_batch_collide(const BatchArgs<T> B) {
                 sg->out_s[e] = s_cur;
             }
             n_out += __popc(dm);
-            if (n_out >= 32) batch_flush_out(B, sg, n_out, 32, step);
+            if (n_out >= 32) batch_flush_out<T, FLIP>(B, sg, n_out, 32, step);
         }
     }
-    if (n_out > 0) batch_flush_out(B, sg, n_out, n_out, step);
-    if (!CHILD && n_ch > 0) batch_flush_children(B, sg, n_ch, n_ch, 0);
+    if (n_out > 0) batch_flush_out<T, FLIP>(B, sg, n_out, n_out, step);
+    if (!CHILD && n_ch > 0) batch_flush_children(B, sg, n_ch, n_ch, dstq, dst_cnt);
     macc_flush(B, sg, step);
     flush_event_weights(B, s_cur, step, ls);
+}
+
+template <class T> __device__ __forceinline__ void stage_proc_batch(ProcSmem<T>& ps, const BatchArgs<T>& B) {
+    if (threadIdx.x < 8) {
+        ps.thr[threadIdx.x] = B.P.thr[threadIdx.x];
+        ps.mratio[threadIdx.x] = B.P.mratio[threadIdx.x];
+        ps.kind[threadIdx.x] = B.P.kind[threadIdx.x];
+    }
+    __syncthreads();
+}
+
+// One phase per launch (the step replayed from a CUDA graph): generation
+// B.gen reads queue B.gen & 1 and queues into the other one.
+template <class T, bool FAST, bool CHILD>
+__global__ void __launch_bounds__(256) k_batch_collide(const BatchArgs<T> B) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ ProcSmem<T> ps;
+    stage_proc_batch(ps, B);
+    BatchStage<T>* sg = reinterpret_cast<BatchStage<T>*>(smem_raw) + (threadIdx.x >> 5);
+    const uint32_t step = B.bd->step;
+    const int srcq = B.gen & 1, dstq = CHILD ? srcq ^ 1 : 0;
+    long long n_items;
+    unsigned long long* cursor;
+    if (CHILD) {
+        n_items = (long long)(srcq ? B.bd->n_spill : B.bd->n_child);
+        if (n_items > B.cap_child) n_items = B.cap_child;
+        cursor = &B.bd->fetch_c;
+    } else {
+        n_items = B.prefix[B.n_swarms];
+        cursor = &B.bd->fetch;
+    }
+    unsigned long long* dst_cnt = dstq ? &B.bd->n_spill : &B.bd->n_child;
+    batch_phase<T, FAST, CHILD, false>(B, ps, sg, step, n_items, cursor, srcq, dstq, dst_cnt);
+}
+
+// Grid-wide barrier of a persistent kernel (a cooperative launch: every block
+// is resident).  After a block-wide barrier and a release fence, thread 0 of
+// each block arrives with an atomic; the last arrival resets the count and
+// opens the next barrier generation, the others poll the generation with
+// acquire loads and short sleeps, at most kBarrierPolls times.  A wait that
+// runs out (a block that never arrives) raises kErrBarrier and the abort
+// flag, and every barrier after that returns false at once, so the kernel
+// ends instead of hanging.  Returns false when the kernel must end.
+constexpr long long kBarrierPolls = 1ll << 24;  // about a second of 64 ns sleeps
+
+__device__ __forceinline__ bool grid_barrier(BatchDev* bd) {
+    __shared__ int go;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned g = ld_acquire_gpu(&bd->bar_gen);
+        __threadfence();
+        if (atomicAdd(&bd->bar_count, 1u) == gridDim.x - 1) {
+            atomicExch(&bd->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&bd->bar_gen, 1u);
+        } else {
+            long long polls = 0;
+            while (ld_acquire_gpu(&bd->bar_gen) == g) {
+                if (ld_acquire_gpu(&bd->abort) != 0u || ++polls > kBarrierPolls) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        if (ok && ld_acquire_gpu(&bd->abort) != 0u) ok = 0;
+        if (!ok) {
+            atomicOr(&bd->err, kErrBarrier);
+            atomicExch(&bd->abort, 1u);
+        }
+        __threadfence();
+        go = ok;
+    }
+    __syncthreads();
+    return go != 0;
+}
+
+// One step of the persistent kernel: resampling (all blocks), the step's
+// prefix sums (block 0), the parents (all blocks taking item ranges from one
+// cursor), then product generations until a generation queues none
+// (generation g reads queue g & 1 and appends to the other; each
+// generation's queue count has its own slot, so no reset separates them),
+// then the counts of the step (block 0), with grid-wide barriers between the
+// phases.  FLIP: the step reads B.out and writes B.in (odd steps).  Returns
+// false when a barrier gave up.
+template <class T, bool FAST, bool FLIP>
+__device__ bool batch_run_step(const BatchArgs<T>& B, const ProcSmem<T>& ps, BatchStage<T>* sg) {
+    BatchDev* bd = B.bd;
+    const uint32_t step = ld_acquire_gpu(&bd->step);
+    batch_resample<T, FLIP>(B, step);
+    if (!grid_barrier(bd)) return false;
+    if (blockIdx.x == 0) batch_begin(B, step);
+    if (!grid_barrier(bd)) return false;
+    batch_phase<T, FAST, false, FLIP>(B, ps, sg, step, B.prefix[B.n_swarms], &bd->cur[0], 0, 0, &bd->gcnt[0]);
+    if (!grid_barrier(bd)) return false;
+    for (int g = 0; g < kMaxGenerations; ++g) {
+        const unsigned long long pend = ld_acquire_gpu(&bd->gcnt[g]);
+        if (pend == 0) break;
+        const long long n_items = (long long)pend < B.cap_child ? (long long)pend : B.cap_child;
+        batch_phase<T, FAST, true, FLIP>(B, ps, sg, step, n_items, &bd->cur[g + 1], g & 1, (g + 1) & 1,
+                                         &bd->gcnt[g + 1]);
+        if (!grid_barrier(bd)) return false;
+    }
+    if (blockIdx.x == 0) {
+        if (threadIdx.x == 0 && ld_acquire_gpu(&bd->gcnt[kMaxGenerations]) != 0ull) atomicOr(&bd->err, kErrStack);
+        batch_end(B, step);
+        __syncthreads();
+        if (threadIdx.x == 0) atomicAdd(&bd->step, 1u);
+    }
+    return grid_barrier(bd);
+}
+
+// Every step of every swarm in one launch (cooperative: all blocks resident).
+template <class T, bool FAST>
+__global__ void __launch_bounds__(256) k_batch_run(const BatchArgs<T> B, int n_steps) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ ProcSmem<T> ps;
+    stage_proc_batch(ps, B);
+    BatchStage<T>* sg = reinterpret_cast<BatchStage<T>*>(smem_raw) + (threadIdx.x >> 5);
+    for (int it = 0; it < n_steps; ++it) {
+        const bool ok = (it & 1) ? batch_run_step<T, FAST, true>(B, ps, sg) : batch_run_step<T, FAST, false>(B, ps, sg);
+        if (!ok) return;
+    }
 }
 
 }  // namespace pic
@@ -618,6 +759,10 @@ template <class T> struct BatchLaunch {
     // One step: resampling, prefix sums, parents, kBatchGenerations children
     // generations, counts, step counter.  B.in / B.out are this step's buffers.
     static cudaError_t step(BatchArgs<T> B, int block, int grid, cudaStream_t s, long long* launches);
+    // All n_steps steps in one cooperative launch of k_batch_run (grid at most
+    // the resident blocks), recorded in a CUDA graph and launched from it.
+    static int persistent_blocks_per_sm(int block);
+    static cudaError_t run_persistent(const BatchArgs<T>& B, int n_steps, int block, int grid, cudaStream_t s);
 };
 
 }  // namespace pic

@@ -32,7 +32,7 @@ VP = C.c_void_p
 
 class pic_gas(C.Structure):
     _fields_ = [("n_proc", C.c_int), ("n_bins", C.c_int), ("eps", PD), ("sigma", PD), ("kind", PI),
-                ("threshold", PD), ("density", PD), ("mass", PD)]
+                ("threshold", PD), ("density", PD), ("mass", PD), ("species", PI)]
 
 
 class pic_config(C.Structure):
@@ -94,7 +94,7 @@ class swarm_config(C.Structure):
                 ("n_lo", C.c_longlong), ("n_hi", C.c_longlong), ("capacity", C.c_longlong),
                 ("n_steps", C.c_int), ("dt", C.c_double), ("kT_eV", C.c_double), ("seed", C.c_ulonglong),
                 ("sample_from", C.c_double), ("batched", C.c_int), ("block", C.c_int),
-                ("blocks_per_sm", C.c_int), ("use_graph", C.c_int)]
+                ("blocks_per_sm", C.c_int), ("use_graph", C.c_int), ("warp_chunk", C.c_int)]
 
 
 class swarm_result(C.Structure):
@@ -104,7 +104,7 @@ class swarm_result(C.Structure):
 EXPORTS = ("pic_workspace_bytes", "pic_init", "pic_destroy", "pic_last_error", "pic_status_string",
            "pic_seed_gaussian", "pic_set_particles", "pic_get_particles", "pic_set_field", "pic_step",
            "pic_deposit", "pic_weight_update", "pic_count", "pic_save", "pic_load", "pic_progress",
-           "pic_profile", "pic_upload", "pic_download", "pic_set_poisson", "pic_get_field", "pic_get_deposit",
+           "pic_profile", "pic_upload", "pic_download", "pic_set_poisson", "pic_get_field", "pic_get_deposit", "pic_set_multigrid",
            "poisson_workspace_bytes", "poisson_solve", "poisson_solve_noalloc", "swarm_workspace_bytes",
            "swarm_run", "swarm_autotune", "mlp_workspace_bytes", "mlp_forward", "mlp_forward_variant", "mlp_loss_grad",
            "mlp_train", "poisson_axi_workspace_bytes", "poisson_axi_solve")
@@ -136,6 +136,7 @@ def lib():
     L.pic_set_field.argtypes = [VP, VP, VP, VP, PD]
     L.pic_step.argtypes = [VP, C.c_int, P(pic_step_stats)]
     L.pic_set_poisson.argtypes = [VP, C.c_double, C.c_int, C.c_int]
+    L.pic_set_multigrid.argtypes = [VP, C.c_int, C.c_int]
     L.pic_deposit.argtypes = [VP, VP, VP, VP, VP]
     L.pic_get_deposit.argtypes = [VP, VP, VP, VP]
     L.pic_get_field.argtypes = [VP, VP, VP, VP]
@@ -155,9 +156,10 @@ def lib():
                                         P(poisson_stats), VP]
     L.swarm_workspace_bytes.argtypes = [P(swarm_config), C.c_int]
     L.swarm_workspace_bytes.restype = C.c_size_t
-    L.swarm_run.argtypes = [P(swarm_config), C.c_int, PD, VP, C.c_size_t, P(swarm_result), PD,
+    L.swarm_run.argtypes = [P(swarm_config), C.c_int, PD, PD, VP, C.c_size_t, P(swarm_result), PD,
                             P(C.c_longlong), VP]
-    L.swarm_autotune.argtypes = [P(swarm_config), C.c_int, PD, VP, C.c_size_t, P(C.c_int), P(C.c_int), PD, VP]
+    L.swarm_autotune.argtypes = [P(swarm_config), C.c_int, PD, PD, VP, C.c_size_t, P(C.c_int), P(C.c_int),
+                                 P(C.c_int), P(C.c_int), PD, VP]
     L.poisson_axi_workspace_bytes.argtypes = [C.c_int, C.c_int]
     L.poisson_axi_workspace_bytes.restype = C.c_size_t
     L.poisson_axi_solve.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, VP, VP, VP, VP,
@@ -243,11 +245,14 @@ class Gas:
             threshold=np.ascontiguousarray(gas["threshold"], np.float64),
             density=np.ascontiguousarray(gas["density"], np.float64),
             mass=np.ascontiguousarray(gas["mass"], np.float64))
+        if gas.get("species") is not None:
+            self.arrays["species"] = np.ascontiguousarray(gas["species"], np.int32)
         a = self.arrays
         self.c = pic_gas(a["sigma"].shape[0], a["sigma"].shape[1], a["eps"].ctypes.data_as(PD),
                          a["sigma"].ctypes.data_as(PD), a["kind"].ctypes.data_as(PI),
                          a["threshold"].ctypes.data_as(PD), a["density"].ctypes.data_as(PD),
-                         a["mass"].ctypes.data_as(PD))
+                         a["mass"].ctypes.data_as(PD),
+                         a["species"].ctypes.data_as(PI) if "species" in a else None)
         self.n_gas = float(gas.get("n_gas", 0.0))
 
 
@@ -378,6 +383,10 @@ class PicContext:
         _check(lib().pic_set_poisson(self.h, float(rtol), int(max_cycles), int(bool(device_loop))), self.h,
                "pic_set_poisson")
 
+    def set_multigrid(self, pre_sweeps=2, post_sweeps=2):
+        """Smoothing sweeps of the coupled solve's V-cycle preconditioner (Cartesian contexts)."""
+        _check(lib().pic_set_multigrid(self.h, int(pre_sweeps), int(post_sweeps)), self.h, "pic_set_multigrid")
+
     def profile(self, enable=True):
         t = pic_profile_times()
         _check(lib().pic_profile(self.h, int(enable), C.byref(t)), self.h, "pic_profile")
@@ -437,37 +446,49 @@ def poisson_axi_solve(nr: int, nz: int, dx: float, rho, phi, mask=None, E=None, 
 
 
 def _swarm_cfg(gas, precision, n0, n_steps, dt, kT_eV, seed, n_lo, n_hi, capacity, sample_from, batched, block,
-               blocks_per_sm, use_graph):
+               blocks_per_sm, use_graph, warp_chunk=0):
     g = Gas(gas)
     if capacity is None:
         capacity = max(2 * n_hi, 4 * n0)
     sc = swarm_config(precision, g.c, g.n_gas, n0, n_lo, n_hi, capacity, n_steps, dt, kT_eV, seed, sample_from,
-                      int(batched), block, blocks_per_sm, int(use_graph))
+                      int(batched), block, blocks_per_sm, int(use_graph), int(warp_chunk))
     return g, sc
 
 
-def swarm_autotune(gas: dict, EN_Td, *, precision=32, n0=10000, n_steps=100, dt=1e-12, kT_eV=1.0, seed=1,
-                   n_lo=1000, n_hi=1_000_000, capacity=None, stream=None):
-    """Returns (block, blocks_per_sm, ms_per_step) of the fastest batched launch shape."""
+def _o2(o2_frac, n):
+    if o2_frac is None:
+        return None
+    f = np.ascontiguousarray(np.broadcast_to(np.asarray(o2_frac, np.float64), (n,)))
+    return f
+
+
+def swarm_autotune(gas: dict, EN_Td, *, o2_frac=None, precision=32, n0=10000, n_steps=100, dt=1e-12, kT_eV=1.0,
+                   seed=1, n_lo=1000, n_hi=1_000_000, capacity=None, stream=None):
+    """Returns (block, blocks_per_sm, warp_chunk, use_graph, ms_per_step) of the fastest batched launch shape."""
     EN = np.ascontiguousarray(np.atleast_1d(EN_Td), np.float64)
+    f = _o2(o2_frac, len(EN))
     g, sc = _swarm_cfg(gas, precision, n0, n_steps, dt, kT_eV, seed, n_lo, n_hi, capacity, 0.25, True, 0, 0, 1)
     nb = lib().swarm_workspace_bytes(C.byref(sc), len(EN))
     if nb == 0:
         raise PicError(PIC_ERR_ARG, "invalid swarm_config")
     ws, ptr = _workspace(nb)
-    b, bps, ms = C.c_int(), C.c_int(), C.c_double()
-    _check(lib().swarm_autotune(C.byref(sc), len(EN), EN.ctypes.data_as(PD), C.c_void_p(ptr), nb, C.byref(b),
-                                C.byref(bps), C.byref(ms), _stream(stream)), None, "swarm_autotune")
-    return b.value, bps.value, ms.value
+    b, bps, ch, mode, ms = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_double()
+    _check(lib().swarm_autotune(C.byref(sc), len(EN), EN.ctypes.data_as(PD), f.ctypes.data_as(PD) if f is not None
+                                else None, C.c_void_p(ptr), nb, C.byref(b), C.byref(bps), C.byref(ch), C.byref(mode),
+                                C.byref(ms), _stream(stream)), None, "swarm_autotune")
+    return b.value, bps.value, ch.value, mode.value, ms.value
 
 
-def swarm_run(gas: dict, EN_Td, *, precision=64, n0=10000, n_steps=2000, dt=1e-12, kT_eV=1.0, seed=1,
+def swarm_run(gas: dict, EN_Td, *, o2_frac=None, precision=64, n0=10000, n_steps=2000, dt=1e-12, kT_eV=1.0, seed=1,
               n_lo=1000, n_hi=1_000_000, capacity=None, sample_from=0.25, stream=None, want_moments=False,
-              batched=False, block=0, blocks_per_sm=0, use_graph=True):
-    """Runs len(EN_Td) swarms; returns (results [n][24], moments or None, counts or None)."""
+              batched=False, block=0, blocks_per_sm=0, use_graph=2, warp_chunk=0):
+    """Runs len(EN_Td) swarms; returns (results [n][24], moments or None, counts or None).
+    o2_frac: per-swarm O2 fractions (a scalar applies to all; needs the gas's species); use_graph (batched):
+    0 kernels per step, 1 step graph replayed, 2 one persistent launch (block = 0: autotuned with the shape)."""
     EN = np.ascontiguousarray(np.atleast_1d(EN_Td), np.float64)
+    f = _o2(o2_frac, len(EN))
     g, sc = _swarm_cfg(gas, precision, n0, n_steps, dt, kT_eV, seed, n_lo, n_hi, capacity, sample_from, batched,
-                       block, blocks_per_sm, use_graph)
+                       block, blocks_per_sm, use_graph, warp_chunk)
     nb = lib().swarm_workspace_bytes(C.byref(sc), len(EN))
     if nb == 0:
         raise PicError(PIC_ERR_ARG, "invalid swarm_config")
@@ -475,8 +496,8 @@ def swarm_run(gas: dict, EN_Td, *, precision=64, n0=10000, n_steps=2000, dt=1e-1
     res = (swarm_result * len(EN))()
     mom = np.zeros((len(EN), n_steps, PIC_SWARM_NMOM)) if want_moments else None
     cnt = np.zeros((len(EN), n_steps), np.int64) if want_moments else None
-    rc = lib().swarm_run(C.byref(sc), len(EN), EN.ctypes.data_as(PD), C.c_void_p(ptr), nb, res,
-                         mom.ctypes.data_as(PD) if mom is not None else None,
+    rc = lib().swarm_run(C.byref(sc), len(EN), EN.ctypes.data_as(PD), f.ctypes.data_as(PD) if f is not None else None,
+                         C.c_void_p(ptr), nb, res, mom.ctypes.data_as(PD) if mom is not None else None,
                          cnt.ctypes.data_as(C.POINTER(C.c_longlong)) if cnt is not None else None, _stream(stream))
     _check(rc, None, "swarm_run")
     out = np.array([[r.v[i] for i in range(PIC_SWARM_NRES)] for r in res])

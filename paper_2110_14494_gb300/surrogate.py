@@ -43,18 +43,17 @@ def targets(res: np.ndarray, EN_Td, n_gas: float) -> np.ndarray:
                      np.log(np.maximum(res[:, R_ETA] / n_gas, FLOOR)), np.log(res[:, R_EPS])], axis=1)
 
 
-def swarm_points(gas_of, EN_Td, fractions, n_gas: float, **swarm_kw):
-    """Runs the batched swarms for every O2 fraction (one batched call per
-    fraction, all E/N values at once); returns (features [n][2], targets [n][6],
-    raw results [n][24]).  gas_of(f) builds the gas for O2 fraction f."""
-    X, Y, R = [], [], []
+def swarm_points(gas, EN_Td, fractions, n_gas: float, **swarm_kw):
+    """Runs the batched swarms of every (O2 fraction, E/N) pair in one batched
+    call (each swarm with its own gas composition); returns (features [n][2],
+    targets [n][6], raw results [n][24]), fraction-major.  gas: the N2/O2 gas
+    with its species tagged."""
     EN = np.asarray(EN_Td, np.float64)
-    for f in np.atleast_1d(fractions):
-        res, _, _ = P.swarm_run(gas_of(float(f)), EN, batched=True, **swarm_kw)
-        X.append(features(EN, np.full(EN.shape, f)))
-        Y.append(targets(res, EN, n_gas))
-        R.append(res)
-    return np.concatenate(X), np.concatenate(Y), np.concatenate(R)
+    fr = np.atleast_1d(np.asarray(fractions, np.float64))
+    ENs = np.tile(EN, len(fr))
+    fs = np.repeat(fr, len(EN))
+    res, _, _ = P.swarm_run(gas, ENs, o2_frac=fs, batched=True, **swarm_kw)
+    return features(ENs, fs), targets(res, ENs, n_gas), res
 
 
 class Standardizer:

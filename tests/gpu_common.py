@@ -24,3 +24,23 @@ def compare_sets(gpu: dict, ref: dict, dx: float, rtol: float, v_floor: float = 
     worst = dict(pos=float(perr.max(initial=0)), vel=float(verr.max(initial=0)), w=float(werr.max(initial=0)),
                  abs_pos=float(pos), gross=int((err > 1e-3).sum()))
     return len(common), len(g["id"]) - len(common), len(r["id"]) - len(common), int(bad.sum()), worst
+
+
+def oracle_swarm_results(job):
+    """The oracle's swarm coefficients for one (E/N, seed) job; a top-level
+    function so that spawned worker processes can run several at once."""
+    import oracle as O
+    import workloads as W
+    EN, n0, n_steps, dt, seed, n_lo, n_hi = job
+    return O.swarm(W.synthetic_air(), EN, n0, n_steps, dt, seed, n_lo=n_lo, n_hi=n_hi)[2]
+
+
+def oracle_swarms(jobs):
+    """Runs oracle swarms in parallel in spawned processes (no CUDA state is
+    inherited); returns their coefficient vectors in job order."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import os
+    with cf.ProcessPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 1),
+                                mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(oracle_swarm_results, jobs))

@@ -1,11 +1,14 @@
 """GPU transport-data surrogate (BF16 tensor-core network, FP32 accumulate)
 against the FP64 CPU oracle, through the C ABI.
 
-Tolerances: the 128 x 128 layer rounds its operands to BF16 (relative
-2^-9 each) and tanh is the hardware approximation (~5e-4), so outputs and
-gradients are compared norm-wise per parameter block at 2e-2 relative; Adam's
-first step, lr g / (|g| + eps), is compared where the oracle's gradient is
-well above that error."""
+Tolerances, element by element: the tensor-core products round their
+operands to BF16 (relative error at most 2^-9 each), the hidden activations
+are held in BF16 and tanh is the hardware approximation.  `_fwd_bound` and
+`_grad_bound` carry these errors through the network to first order as
+independent roundings (the probabilistic rounding-error model: a sum of m
+rounded terms errs like sqrt(m), not m, unit roundoffs), and every output and
+gradient element must lie within six standard deviations of that model.  Adam's first step, lr g / (|g| + eps), is compared
+where the oracle's gradient is well above that error."""
 import numpy as np
 import pytest
 
@@ -40,6 +43,87 @@ def _dev(a):
     return torch.as_tensor(np.asarray(a, np.float32)).cuda()
 
 
+U_OP = 2.0 ** -9     # BF16 rounding of a tensor-core operand (relative, at most)
+# an activation held in BF16 after the approximate tanh (relative, at most): the float32 approximation
+# rounded to BF16 (the mma.sync path and training) 2^-8; the tcgen05 path evaluates tanh in BF16
+# (tanh.approx.bf16x2), the approximation's error and the BF16 result's rounding together 2^-7
+U_ACT = 2.0 ** -8
+U_ACT_BF16_TANH = 2.0 ** -7
+A_TANH = 2.0 ** -11  # absolute error of the approximate tanh
+K_SIGMA = 6.0        # element tolerance in standard deviations of the propagated rounding error
+
+
+def _layers(th, x):
+    P = M.unpack(th)
+    h1 = np.tanh(x @ P["W1"].T + P["b1"])
+    h2 = np.tanh(h1 @ P["W2"].T + P["b2"])
+    y = h2 @ P["W3"].T + P["b3"]
+    return P, h1, h2, y
+
+
+def _fwd_var(th, x, u_act=U_ACT):
+    """Variances of the errors of h1, h2 and y, taking each rounding as an
+    independent error uniform within its bound (variance bound^2 / 3):
+    BF16 activations and tanh, BF16 operands of the two tensor-core products."""
+    P, h1, h2, y = _layers(th, x)
+    W2s, W3s = P["W2"] ** 2, P["W3"] ** 2
+    v1 = ((u_act * h1) ** 2 + A_TANH ** 2) / 3
+    v2 = (v1 @ W2s.T + ((U_OP ** 2) / 3) * ((h1 ** 2) @ W2s.T)) * (1 - h2 ** 2) ** 2
+    v2 = v2 + ((u_act * h2) ** 2 + A_TANH ** 2) / 3
+    vy = v2 @ W3s.T + ((U_OP ** 2) / 3) * ((h2 ** 2) @ W3s.T)
+    return P, h1, h2, y, v1, v2, vy
+
+
+def _fwd_bound(th, x, variant=1):
+    return K_SIGMA * np.sqrt(_fwd_var(th, x, U_ACT_BF16_TANH if variant == 0 else U_ACT)[-1])
+
+
+def _bf16(a):
+    """Round float32 values to BF16 (nearest, ties to even), returned as float64."""
+    u = np.ascontiguousarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _w2_as_multiplied(th):
+    """The parameters with W2 as the tensor cores multiply it (BF16).  Its
+    rounding is one error shared by every point of a batch, so in a gradient
+    (a sum over points) it would add coherently; the gradient is compared with
+    the oracle's gradient at these parameters, leaving the per-point roundings
+    that the model below describes."""
+    out = th.copy()
+    o, n = M.OFF["W2"], M.NH * M.NH
+    out[o:o + n] = _bf16(th[o:o + n])
+    return out
+
+
+def _grad_bound(th, x, t):
+    """The same for each gradient element at parameters whose W2 is already
+    BF16: the forward errors of each point carried through the mean-squared-
+    error backpropagation, plus the BF16 rounding of the per-point operands of
+    the tensor-core products (delta2 and h1); these are independent between
+    points, so the sum over the batch adds their variances."""
+    P, h1, h2, y = _layers(th, x)
+    n = x.shape[0]
+    W2s, W3s = P["W2"] ** 2, P["W3"] ** 2
+    v1 = ((U_ACT * h1) ** 2 + A_TANH ** 2) / 3
+    v2 = (v1 @ W2s.T) * (1 - h2 ** 2) ** 2 + ((U_ACT * h2) ** 2 + A_TANH ** 2) / 3
+    vy = v2 @ W3s.T
+    d3 = 2.0 * (y - t) / (6 * n)
+    vd3 = vy * (2.0 / (6 * n)) ** 2
+    g3 = d3 @ P["W3"]
+    s2 = 1 - h2 ** 2
+    d2 = g3 * s2
+    vd2 = (vd3 @ W3s) * s2 ** 2 + (g3 * 2 * h2) ** 2 * v2 + (U_OP ** 2 / 3) * d2 ** 2
+    g2 = d2 @ P["W2"]
+    s1 = 1 - h1 ** 2
+    vd1 = (vd2 @ W2s) * s1 ** 2 + (g2 * 2 * h1) ** 2 * v1
+    var = dict(W3=vd3.T @ h2 ** 2 + (d3 ** 2).T @ v2, b3=vd3.sum(0),
+               W2=vd2.T @ h1 ** 2 + (d2 ** 2).T @ v1, b2=vd2.sum(0),
+               W1=vd1.T @ x ** 2, b1=vd1.sum(0))
+    return K_SIGMA * np.sqrt(M.pack(var))
+
+
 @pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("n", [1, 37, 4096 + 5])
 def test_forward_matches_oracle(n, variant):
@@ -48,8 +132,10 @@ def test_forward_matches_oracle(n, variant):
     th, x, _ = _problem(n)
     y = mlp_forward(_dev(th), _dev(x), variant=variant).cpu().numpy()
     ref = M.forward(th, x)
-    assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 2e-2
-    assert np.abs(y - ref).max() < 5e-2 * np.abs(ref).max()
+    bound = _fwd_bound(th, x, variant)
+    ratio = np.abs(y - ref) / bound
+    print(f"forward n={n} variant {variant}: error / bound max {ratio.max():.3f}, mean {ratio.mean():.3f}")
+    assert np.all(np.abs(y - ref) <= bound), ratio.max()
 
 
 def test_gradient_matches_oracle():
@@ -59,11 +145,15 @@ def test_gradient_matches_oracle():
     th, x, t = _problem(512, seed=2)
     loss, g = mlp_loss_grad(_dev(th), _dev(x), _dev(t))
     g = g.cpu().numpy().astype(np.float64)
-    lref, gref = M.loss_grad(th, x, t)
+    th2 = _w2_as_multiplied(th)
+    lref, gref = M.loss_grad(th2, x, t)
     assert abs(loss.item() - lref) <= 1e-2 * lref
+    bound = _grad_bound(th2, x, t)
+    ratio = np.abs(g - gref) / bound
     for name in M.SHAPES:
-        a, b = M.unpack(g)[name], M.unpack(gref)[name]
-        assert np.linalg.norm(a - b) <= 2e-2 * np.linalg.norm(b), name
+        r = M.unpack(ratio)[name]
+        print(f"gradient {name}: error / bound max {r.max():.3f}, mean {r.mean():.3f}")
+    assert np.all(np.abs(g - gref) <= bound), {k: float(v.max()) for k, v in M.unpack(ratio).items()}
 
 
 def test_adam_steps_match_oracle():
@@ -115,8 +205,9 @@ def test_inference_on_many_points_sampled(variant):
     x = r.normal(0, 1, (n, 2)).astype(np.float32)
     y = mlp_forward(_dev(th), _dev(x), variant=variant).cpu().numpy()
     idx = np.concatenate([r.choice(n, 2000, replace=False), np.arange(n - 77, n)])
-    ref = M.forward(th, x[idx].astype(np.float64))
-    assert np.linalg.norm(y[idx] - ref) / np.linalg.norm(ref) < 2e-2
+    xi = x[idx].astype(np.float64)
+    ref = M.forward(th, xi)
+    assert np.all(np.abs(y[idx] - ref) <= _fwd_bound(th, xi, variant))
     assert np.isfinite(y).all()
 
 
@@ -134,20 +225,17 @@ def test_surrogate_gain_over_swarms():
     kw = dict(precision=32, n0=2000, n_steps=400, dt=1e-12, n_lo=500, n_hi=20000, seed=11)
     EN = 20.0 * 40.0 ** (np.arange(64) / 63)
     fr = np.array([0.1, 0.1667, 0.2333, 0.3])
-    X, Y, _ = S.swarm_points(lambda f: W.synthetic_air(o2_frac=f), EN, fr, W.N_GAS, **kw)
+    X, Y, _ = S.swarm_points(W.synthetic_air(), EN, fr, W.N_GAS, **kw)
     sur = S.Surrogate(W.mlp_init(40), X, Y)
     trace, secs = sur.fit(4000, lr=2e-3)
     assert trace[-1][1] < 0.05, trace[-4:]
     q = W.mlp_query_points(12, 41, en_lo=25.0, en_hi=700.0)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    held = []
-    for k in range(len(q)):
-        res, _, _ = swarm_run(W.synthetic_air(o2_frac=q[k, 1]), q[k:k + 1, 0], batched=True, **dict(kw, seed=500 + k))
-        held.append(S.targets(res, q[k:k + 1, 0], W.N_GAS)[0])
+    res, _, _ = swarm_run(W.synthetic_air(), q[:, 0], o2_frac=q[:, 1], batched=True, **dict(kw, seed=500))
+    held = S.targets(res, q[:, 0], W.N_GAS)
     torch.cuda.synchronize()
     swarm_qps = len(q) / (time.perf_counter() - t0)
-    held = np.array(held)
     pred = sur.predict(q[:, 0], q[:, 1])
     table = Y.reshape(len(fr), len(EN), 6)
     lin = S.table_interp(EN, fr, table, q[:, 0], q[:, 1])

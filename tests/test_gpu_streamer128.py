@@ -10,7 +10,10 @@ Compared:
 - particles: float64 1e-12 per particle; float32 1e-5 (position per cell,
   velocity per |v| + 1e5 m/s) with decision flips (gross differences and
   particles on one side only) at most 1e-5 N + 2 and rounding amplification
-  near inelastic thresholds at most 1e-3 N (the single-step test's bounds);
+  near inelastic thresholds at most 1e-3 N (the single-step test's bounds;
+  measured up to 9.3e-4 N at step 100, where these particles end the step with
+  a median energy of 0.7 eV against 5 eV for all, 58 % of them products born
+  in the step with half of what the ionization left);
 - the deposit the step's own kernels made (pic_get_deposit) against the
   oracle's deposit of the GPU's particles after the step: bit for bit;
 - the ion grids' increments over the step against the oracle's (the same
@@ -58,6 +61,20 @@ def _grids(ctx, n, fresh=False):
     q = [torch.zeros(n, dtype=torch.int64, device="cuda") for _ in range(3)]
     (ctx.deposit if fresh else ctx.get_deposit)(*q)
     return [_np(a) for a in q]
+
+
+def _energy_split(gpu, ref, dx, tol):
+    """Median final kinetic energy (eV, oracle) of all common particles and of
+    those outside tol (position per cell, velocity per |v| + 1e5 m/s)."""
+    from tests.gpu_common import by_id
+    G, R = by_id(gpu), by_id(ref)
+    common, ig, ir = np.intersect1d(G["id"], R["id"], assume_unique=True, return_indices=True)
+    sp = np.sqrt(R["vx"][ir] ** 2 + R["vy"][ir] ** 2 + R["vz"][ir] ** 2)
+    err = np.max([np.abs(G[k][ig] - R[k][ir]) / dx for k in ("x", "y", "z")] +
+                 [np.abs(G[k][ig] - R[k][ir]) / (sp + 1e5) for k in ("vx", "vy", "vz")], axis=0)
+    e = 0.5 * O.M_ELEC * sp ** 2 / O.Q_E
+    out = err > tol
+    return float(np.median(e)), float(np.median(e[out])) if out.any() else 0.0
 
 
 def _phi(ctx, n):
@@ -121,6 +138,11 @@ def test_coupled_streamer_128_matches_oracle(prec):
         else:
             assert flips <= 1e-5 * N + 2, (done, flips, worst)
             assert bad - worst["gross"] <= 1e-3 * N, (done, bad, worst)
+            # the particles outside 1e-5 are the rounding amplification of an inelastic loss (eps - eps_th
+            # carries the float32 error of eps times eps / (eps - eps_th)): they end the step slow
+            e_med, e_bad = _energy_split(gpu, ref, g["dx"], tol)
+            print(f"step {done}: median final energy {e_med:.3g} eV, of the particles outside {tol:g} {e_bad:.3g} eV")
+            assert bad == 0 or e_bad < 0.5 * e_med, (done, e_bad, e_med)
         assert abs(st.n_events - ost.n_events) <= 1e-4 * ost.n_events + 10
 
         # the step's own deposit is the deposit of the particles it left, bit for bit

@@ -1,9 +1,14 @@
 """GPU swarms (Sec. 2.2.2) and multigrid Poisson (Sec. 2.5) against the CPU
 oracle and closed forms, through the C ABI.
 
-Swarm coefficients: |delta| <= 1 % or <= 3 sigma (combined batch-means
-errors), whichever is larger, per coefficient.  Poisson: relative residual
-1e-6 and agreement with the oracle's CG solution."""
+Swarm coefficients: every coefficient within 3 sigma of the oracle's (sigma
+the combined batch-means errors of both runs), and within 1 % where 3 sigma is
+below 1 %: the float32 swarms run at the size of the 120 Td workload (1e4
+electrons, 2000 steps of 1 ps) so that 3 sigma is below 1 % for the flux drift
+velocity, the mean energy, k_ion and alpha; where it is not (bulk drift,
+diffusion, attachment), 3 sigma governs.  Float64 swarms follow the
+oracle's trajectories exactly.  Poisson: relative residual 1e-6 and agreement
+with the oracle's CG solution."""
 import numpy as np
 import pytest
 
@@ -23,13 +28,30 @@ def built():
 
 
 def _agree(g, r, names=range(11)):
+    """Coefficients outside |delta| <= 3 sigma (combined), or outside 1 % where
+    3 sigma is below 1 %: (name, gpu, oracle, sigma) each."""
     bad = []
     for i in names:
         sig = np.hypot(g[11 + i], r[11 + i])
         d = abs(g[i] - r[i])
-        if not (d <= 0.01 * abs(r[i]) or d <= 3 * sig):
+        if d > 3 * sig or (3 * sig <= 0.01 * abs(r[i]) and d > 0.01 * abs(r[i])):
             bad.append((O.RES_NAMES[i], g[i], r[i], sig))
     return bad
+
+
+def _resolved_to_one_percent(g, r, names=(0, 6, 7, 9)):
+    """Coefficients whose combined 3 sigma is not below 1 %: at the workload's
+    size none of the flux drift velocity, the mean energy, the ionization rate
+    coefficient and alpha (measured 0.07-0.54 % at 120 and 400 Td); the bulk
+    drift (1.3-1.8 %), the diffusion coefficients and eta stay 3-sigma
+    governed."""
+    return [(O.RES_NAMES[i], 3 * np.hypot(g[11 + i], r[11 + i]) / abs(r[i])) for i in names
+            if not 3 * np.hypot(g[11 + i], r[11 + i]) < 0.01 * abs(r[i])]
+
+
+# the 120 Td workload's swarm size, with resampling bounds that keep the
+# strongly ionizing 400 Td swarm at a few times 1e4 electrons
+C1 = dict(n0=10_000, n_steps=2000, dt=1e-12, n_lo=5_000, n_hi=20_000)
 
 
 def test_swarm_fp64_matches_oracle():
@@ -46,16 +68,24 @@ def test_swarm_fp64_matches_oracle():
     assert not _agree(res[0], ores)
 
 
-def test_swarm_fp32_matches_oracle():
+def _fp32_swarms_match_oracle(batched, seed):
     from paper_2110_14494_gb300 import swarm_run
-    gas = W.synthetic_air()
-    seed = 2110144942
-    res, mom, cnt = swarm_run(gas, [120.0, 400.0], precision=32, n0=2000, n_steps=400, dt=1e-12, seed=seed,
-                              n_lo=1000, n_hi=4000, want_moments=True)
-    for s, EN in enumerate((120.0, 400.0)):
-        omom, ocnt, ores, _ = O.swarm(gas, EN, 2000, 400, 1e-12, seed + s, n_lo=1000, n_hi=4000)
-        bad = _agree(res[s], ores)
-        assert not bad, bad
+    from tests.gpu_common import oracle_swarms
+    ENs = (120.0, 400.0)
+    res, _, _ = swarm_run(W.synthetic_air(), list(ENs), precision=32, seed=seed, batched=batched, **C1)
+    ref = oracle_swarms([(EN, C1["n0"], C1["n_steps"], C1["dt"], seed + s, C1["n_lo"], C1["n_hi"])
+                         for s, EN in enumerate(ENs)])
+    for s, EN in enumerate(ENs):
+        bad = _agree(res[s], ref[s])
+        coarse = _resolved_to_one_percent(res[s], ref[s])
+        rel = {O.RES_NAMES[i]: round((res[s][i] - ref[s][i]) / ref[s][i], 5) for i in range(11) if ref[s][i]}
+        print(f"{'batched ' if batched else ''}float32 swarm at {EN} Td vs oracle: {rel}")
+        assert not bad, (EN, bad)
+        assert not coarse, (EN, coarse)
+
+
+def test_swarm_fp32_matches_oracle():
+    _fp32_swarms_match_oracle(False, 2110144942)
 
 
 def test_swarm_constant_nu_closed_form():
@@ -129,15 +159,17 @@ def test_poisson_plates_only():
     assert np.allclose(E[2].cpu().numpy(), -V0 / (64 * 2e-5), rtol=1e-5)
 
 
-def test_batched_swarms_fp64_match_oracle_per_swarm():
-    """All swarms in one launch per step (CUDA graph): each swarm's trajectory
-    is the oracle's for seed + s (same counts every step, same moments)."""
+@pytest.mark.parametrize("launch", [1, 2])
+def test_batched_swarms_fp64_match_oracle_per_swarm(launch):
+    """All swarms advanced together (1: the step replayed from a CUDA graph;
+    2: one persistent launch for every step): each swarm's trajectory is the
+    oracle's for seed + s (same counts every step, same moments)."""
     from paper_2110_14494_gb300 import swarm_run
     gas = W.synthetic_air()
     seed = 2110144950
     ENs = [60.0, 120.0, 400.0]
     res, mom, cnt = swarm_run(gas, ENs, precision=64, n0=1500, n_steps=300, dt=1e-12, seed=seed, n_lo=1000,
-                              n_hi=3000, want_moments=True, batched=True, block=128, blocks_per_sm=2)
+                              n_hi=3000, want_moments=True, batched=True, block=128, blocks_per_sm=2, use_graph=launch)
     for s, EN in enumerate(ENs):
         omom, ocnt, ores, _ = O.swarm(gas, EN, 1500, 300, 1e-12, seed + s, n_lo=1000, n_hi=3000)
         assert np.array_equal(cnt[s], ocnt), s
@@ -146,37 +178,60 @@ def test_batched_swarms_fp64_match_oracle_per_swarm():
         assert not _agree(res[s], ores), s
 
 
-def test_batched_swarms_graph_and_autotune():
+def test_batched_swarms_launch_modes_and_autotune():
+    """The autotuner's choice, and the three launch modes (kernels per step, the
+    step graph replayed, one persistent kernel) on the same swarms: the same
+    counts every step and the moments to float rounding."""
     from paper_2110_14494_gb300 import swarm_autotune, swarm_run
     gas = W.synthetic_air()
     ENs = list(W.swarm_en_grid(16, 10.0, 1000.0))
-    b, bps, ms = swarm_autotune(gas, ENs, precision=32, n0=2000, n_steps=40, dt=1e-12, seed=5, n_lo=1000,
-                                n_hi=8000)
-    assert b in (64, 128, 256) and bps >= 1 and ms > 0
+    b, bps, chunk, mode, ms = swarm_autotune(gas, ENs, precision=32, n0=2000, n_steps=40, dt=1e-12, seed=5,
+                                             n_lo=1000, n_hi=8000)
+    assert b in (64, 128, 256) and bps >= 1 and chunk in (256, 512, 1024, 2048) and mode in (1, 2) and ms > 0
     kw = dict(precision=32, n0=2000, n_steps=40, dt=1e-12, seed=5, n_lo=1000, n_hi=8000, want_moments=True,
-              batched=True, block=b, blocks_per_sm=bps)
-    r1, m1, c1 = swarm_run(gas, ENs, use_graph=True, **kw)
-    r2, m2, c2 = swarm_run(gas, ENs, use_graph=False, **kw)
-    assert np.array_equal(c1, c2)
-    # float32 warp partial sums depend on which electrons share a flush (set
-    # by the order warps take work), so the moments agree to float rounding
-    scale = np.abs(m1).max(axis=1, keepdims=True) + 1e-300
-    assert np.all(np.abs(m1 - m2) <= 1e-6 * scale)
+              batched=True, block=b, blocks_per_sm=bps, warp_chunk=chunk)
+    runs = [swarm_run(gas, ENs, use_graph=m, **kw) for m in (0, 1, 2)]
+    r1, m1, c1 = runs[1]
+    for r, m, c in (runs[0], runs[2]):
+        assert np.array_equal(c, c1)
+        # float32 warp partial sums depend on which electrons share a flush (set
+        # by the order warps take work), so the moments agree to float rounding
+        scale = np.abs(m1).max(axis=1, keepdims=True) + 1e-300
+        assert np.all(np.abs(m - m1) <= 1e-6 * scale)
     # resampling keeps every swarm inside its bounds (after the step that triggered it)
     assert c1.max() <= 2 * 8000 * 2 and c1[:, -1].min() > 0
 
 
-def test_batched_swarms_fp32_match_oracle():
+@pytest.mark.parametrize("batched", [False, True])
+def test_swarms_with_their_own_o2_fractions_match_oracle(batched):
+    """Per-swarm O2 fractions (each swarm its own rate table and nu_max): the
+    float64 trajectories are the oracle's run with that fraction's gas."""
     from paper_2110_14494_gb300 import swarm_run
+    seed = 2110144970
+    ENs = np.array([80.0, 150.0, 300.0, 150.0])
+    fr = np.array([0.1, 0.2, 0.3, 0.25])
+    res, mom, cnt = swarm_run(W.synthetic_air(), ENs, o2_frac=fr, precision=64, n0=1000, n_steps=200, dt=1e-12,
+                              seed=seed, n_lo=500, n_hi=2500, want_moments=True, batched=batched,
+                              block=128 if batched else 0, blocks_per_sm=2 if batched else 0)
+    for s in range(len(ENs)):
+        omom, ocnt, ores, _ = O.swarm(W.synthetic_air(o2_frac=fr[s]), ENs[s], 1000, 200, 1e-12, seed + s,
+                                      n_lo=500, n_hi=2500)
+        assert np.array_equal(cnt[s], ocnt), s
+        scale = np.abs(omom).max(axis=0) + 1e-300
+        assert np.all(np.abs(mom[s] - omom) <= 1e-9 * scale), s
+
+
+def test_o2_fractions_need_tagged_species():
+    from paper_2110_14494_gb300 import PicError, swarm_run
     gas = W.synthetic_air()
-    seed = 2110144960
-    ENs = [120.0, 400.0]
-    res, _, _ = swarm_run(gas, ENs, precision=32, n0=2000, n_steps=400, dt=1e-12, seed=seed, n_lo=1000, n_hi=4000,
-                          batched=True)
-    for s, EN in enumerate(ENs):
-        omom, ocnt, ores, _ = O.swarm(gas, EN, 2000, 400, 1e-12, seed + s, n_lo=1000, n_hi=4000)
-        bad = _agree(res[s], ores)
-        assert not bad, bad
+    del gas["species"]
+    with pytest.raises(PicError) as e:
+        swarm_run(gas, [100.0], o2_frac=[0.2], n0=100, n_steps=30, n_lo=10, n_hi=400)
+    assert e.value.code == -1
+
+
+def test_batched_swarms_fp32_match_oracle():
+    _fp32_swarms_match_oracle(True, 2110144960)
 
 
 def test_poisson_pair_precision_matches_oracle():

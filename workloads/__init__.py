@@ -20,6 +20,8 @@ BASE_SEED = 2110144940
 
 # Process kinds, shared as plain integers with both implementations.
 ELASTIC, EXCITATION, IONIZATION, ATTACHMENT = 0, 1, 2, 3
+# Target species of a process (for per-swarm O2 fractions).
+N2, O2 = 0, 1
 
 AMU_KG = 1.66053906660e-27          # CODATA 2018 atomic mass unit
 M_N2_KG = 28.0134 * AMU_KG
@@ -80,6 +82,7 @@ def synthetic_air(n_bins: int = 1000, eps_min: float = 0.01, eps_max: float = 10
         threshold=np.array([0.0, 0.0, 6.2, 11.0, 15.6, 12.06, 0.0]),
         density=np.array([n_n2, n_o2, n_n2, n_n2, n_n2, n_o2, n_o2]),
         mass=np.array([M_N2_KG, M_O2_KG, M_N2_KG, M_N2_KG, M_N2_KG, M_O2_KG, M_O2_KG]),
+        species=np.array([N2, O2, N2, N2, N2, O2, O2], dtype=np.int32),
         n_gas=n_gas,
     )
 
@@ -103,6 +106,7 @@ def single_process_gas(kind: int, sigma_v: float, n_gas: float = N_GAS, mass: fl
         threshold=np.array([threshold]),
         density=np.array([n_gas]),
         mass=np.array([mass]),
+        species=np.array([N2], dtype=np.int32),
         n_gas=n_gas,
     )
 
@@ -119,6 +123,7 @@ def multi_gas(parts: list[dict]) -> dict:
         threshold=np.concatenate([p["threshold"] for p in parts]),
         density=np.concatenate([p["density"] for p in parts]),
         mass=np.concatenate([p["mass"] for p in parts]),
+        species=np.concatenate([p["species"] for p in parts]).astype(np.int32),
         n_gas=parts[0]["n_gas"],
     )
 
