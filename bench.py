@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--swarm-bps", type=int, default=0, help="batched swarms: blocks per SM (0 = autotune)")
     ap.add_argument("--no-f64", action="store_true",
                     help="skip the float64 comparison (streamer: the float64 arm; batched swarms: the plain path)")
+    ap.add_argument("--mlp-steps", type=int, default=20000, help="surrogate: full-batch Adam steps")
+    ap.add_argument("--sort-interval", type=int, default=20, help="cell sort every this many steps (0: never)")
     ap.add_argument("--vcycle", default="2,2",
                     help="pre,post smoothing sweeps of the coupled solve's V-cycle preconditioner")
     ap.add_argument("--host-solve", action="store_true",
@@ -101,9 +103,10 @@ def workload(n_cells=128, n_initial=1_000_000):
     return wl
 
 
-def streamer_context(wl, precision=32, capacity=None, seed=2110144940, boundary=1, adaptive_dt=True, extra=None):
+def streamer_context(wl, precision=32, capacity=None, seed=2110144940, boundary=1, adaptive_dt=True, extra=None,
+                     sort_interval=20):
     """The coupled streamer context the benchmark times (weight update on
-    1.25x growth, cell sort every 20 steps, Poisson every step at rtol 1e-6,
+    1.25x growth, cell sort every 20 steps (by default), Poisson every step at rtol 1e-6,
     CFL 0.5 / dielectric relaxation / 20 % growth time-step control); the
     parity tests build theirs with this too."""
     import workloads as W
@@ -115,7 +118,7 @@ def streamer_context(wl, precision=32, capacity=None, seed=2110144940, boundary=
     cap = capacity or int(wl["particle_cap"] * 1.6)
     return PicContext(gas, g, precision=precision, capacity=cap, seed=seed, dt=wl["dt"], mask=mask,
                       n_ppc=wl["n_ppc"], w_min=wl["w_min"], growth_trigger=wl["growth_trigger"],
-                      particle_cap=wl["particle_cap"], sort_interval=20, coupled=True, v_lo=wl["v_bottom"],
+                      particle_cap=wl["particle_cap"], sort_interval=sort_interval, coupled=True, v_lo=wl["v_bottom"],
                       boundary=boundary, adaptive_dt=adaptive_dt, cfl=0.5, mobility=0.06, max_growth=1.2,
                       v_hi=wl["v_top"], v_mask=wl["v_top"], poisson_rtol=1e-6, poisson_max_cycles=200,
                       **(extra or {}))
@@ -495,11 +498,26 @@ def run_c1(args):
     print(json.dumps(out))
 
 
+def _oracle_swarm_job(job):
+    """One oracle process: a swarm of the batched workload (E/N, steps, seed):
+    (particle-updates, seconds)."""
+    EN, steps, seed = job
+    import oracle as O
+    import workloads as W
+    t0 = time.perf_counter()
+    mom, cnt, res, m = O.swarm(W.synthetic_air(), EN, 10000, steps, 1e-12, seed, n_lo=1000, n_hi=100_000)
+    return float(10000 + cnt[:-1].sum()), time.perf_counter() - t0
+
+
 def run_swarms(args):
-    """256 swarms, E/N log-spaced 10-1000 Td, 1e4 float32 electrons each, adaptive
-    resampling in [1e3, 1e6], dt = 1 ps: batched (one launch per step, CUDA graph,
-    autotuned launch shape) against the plain float64 path (swarms one after
-    another) on a subset."""
+    """The batched-swarm workload: 256 swarms, E/N log-spaced 10-1000 Td, 1e4
+    float32 electrons each, adaptive resampling in [1e3, 1e6], dt = 1 ps,
+    5000 steps, launch shape and mode from the autotuner.  Beside it: the same
+    256 swarms batched in float64 for a bounded number of steps (the precision
+    alone), the plain float64 path (swarms one after another) on 4 of them
+    (batching and precision together), and the oracle on one and on every host
+    core (one swarm per process, bounded steps)."""
+    import multiprocessing as mp
     import torch
     import __graft_entry__ as ge
     ge.build()
@@ -508,38 +526,72 @@ def run_swarms(args):
     gas = W.synthetic_air()
     ENs = W.swarm_en_grid(256, 10.0, 1000.0)
     steps = args.steps if args.steps != 1990 else 5000
+    kw = dict(n0=10000, dt=1e-12, seed=2110144943, n_lo=1000, n_hi=1_000_000)
     t0 = time.perf_counter()
     if args.swarm_block and args.swarm_bps:
-        b, bps, chunk, mode, ms_trial = args.swarm_block, args.swarm_bps, 1024, 2, None
+        b, bps, chunk, mode, ms_trial = args.swarm_block, args.swarm_bps, 1024, 1, None
     else:
-        b, bps, chunk, mode, ms_trial = swarm_autotune(gas, ENs, precision=32, n0=10000, n_steps=steps, dt=1e-12,
-                                                       seed=2110144943, n_lo=1000, n_hi=1_000_000)
+        b, bps, chunk, mode, ms_trial = swarm_autotune(gas, ENs, precision=32, n_steps=steps, **kw)
     t_tune = time.perf_counter() - t0
+    shape = dict(batched=True, block=b, blocks_per_sm=bps, warp_chunk=chunk, use_graph=mode)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    res, mom, cnt = swarm_run(gas, ENs, precision=32, n0=10000, n_steps=steps, dt=1e-12, seed=2110144943, n_lo=1000,
-                              n_hi=1_000_000, want_moments=True, batched=True, block=b, blocks_per_sm=bps,
-                              warp_chunk=chunk, use_graph=mode)
+    res, mom, cnt = swarm_run(gas, ENs, precision=32, n_steps=steps, want_moments=True, **shape, **kw)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
-    updates = float(cnt.sum())
-    # plain float64 path (one swarm after another) on 4 of the 256 E/N values, 500 steps
-    sub = ENs[::64]
-    t0 = time.perf_counter()
-    if args.no_f64:
-        c64, w64 = np.zeros(1), 1.0
-    else:
-        r64, _, c64 = swarm_run(gas, sub, precision=64, n0=10000, n_steps=500, dt=1e-12, seed=2110144943,
-                                n_lo=1000, n_hi=1_000_000, want_moments=True)
-    w64 = time.perf_counter() - t0
-    out = {"metric": "batched swarms particle-updates/s (256 E/N, float32, one launch per step)",
-           "value": updates / wall, "unit": UNIT, "n_gpus": 1, "steps": steps, "wall_s": wall,
+    updates = float(len(ENs) * kw["n0"] + cnt[:, :-1].sum())
+    f64 = seq = base = None
+    steps64 = min(steps, 100)
+    if not args.no_f64:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r64, _, c64 = swarm_run(gas, ENs, precision=64, n_steps=steps64, want_moments=True, **shape, **kw)
+        torch.cuda.synchronize()
+        w64 = time.perf_counter() - t0
+        r32s, _, c32s = swarm_run(gas, ENs, precision=32, n_steps=steps64, want_moments=True, **shape, **kw)
+        rel = {n: float(np.median(np.abs(r32s[:, i] - r64[:, i]) / np.maximum(np.abs(r64[:, i]), 1e-300)))
+               for n, i in (("W_flux", 0), ("mean_eps", 6), ("alpha", 9))}
+        f64 = {"value": float(len(ENs) * kw["n0"] + c64[:, :-1].sum()) / w64, "unit": UNIT, "swarms": len(ENs),
+               "steps": steps64, "wall_s": w64,
+               "median_relative_difference_fp32_vs_fp64": rel,
+               "note": "same seeds and launch shape; the two precisions take different collision decisions after "
+                       "rounding-level flips, so the differences mix precision with Monte Carlo noise"}
+        sub = ENs[::64]
+        t0 = time.perf_counter()
+        _, _, cs = swarm_run(gas, sub, precision=64, n_steps=steps64, want_moments=True, **kw)
+        ws = time.perf_counter() - t0
+        seq = {"value": float(len(sub) * kw["n0"] + cs[:, :-1].sum()) / ws, "unit": UNIT, "swarms": len(sub),
+               "steps": steps64, "wall_s": ws}
+    if not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        ctx = mp.get_context("spawn")
+        pick = ENs[::max(1, len(ENs) // cores)][:cores]
+        with ctx.Pool(1) as pool:
+            u1, t1 = pool.map(_oracle_swarm_job, [(float(pick[len(pick) // 2]), 100, 7)])[0]
+        with ctx.Pool(cores) as pool:
+            rs = pool.map(_oracle_swarm_job, [(float(e), 100, 7 + i) for i, e in enumerate(pick)])
+        base = {"value": sum(r[0] for r in rs) / max(r[1] for r in rs), "unit": UNIT, "cores": cores,
+                "kind": "oracle", "single_core": {"value": u1 / t1, "cores": 1, "seconds": round(t1, 2)},
+                "sample": f"the first 100 of the {steps} steps of {len(pick)} of the 256 swarms, one per process "
+                          "(E/N spread over 10-1000 Td; thinning above 1e5 electrons instead of 1e6 to bound the "
+                          "sample), and one of them alone for the single-core figure"}
+    hbm, peak_kind = peaks()
+    achieved = 72.0 * updates / wall / 1e9
+    out = {"metric": "batched swarms particle-updates/s (256 E/N, float32)",
+           "value": updates / wall, "unit": UNIT, "n_gpus": 1, "steps": steps, "wall_s": wall, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": "batched-swarms-256x1e4-fp32", "E_N_Td": [10.0, 1000.0], "electrons": 10000,
+                      "resampling": [1000, 1_000_000], "dt_ps": 1.0,
+                      "timing": "wall clock around the swarm_run call (host-synchronising): setup, every step "
+                                "and the moment read-back"},
            "tuning": {"block": b, "blocks_per_sm": bps, "warp_chunk": chunk,
                       "launch": {0: "kernels per step", 1: "step graph replayed", 2: "one persistent launch"}[mode],
                       "trial_ms_per_step": ms_trial, "tune_s": t_tune},
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                        "peak_source": peak_kind, "bytes_per_update": 72,
+                        "note": "whole run over wall time; the collision kernel is issue-bound like the PIC one"},
            "particles_per_step": {"mean": float(cnt.mean(axis=0).mean() * 256), "final": int(cnt[:, -1].sum())},
-           "plain_f64_sequential": {"value": float(c64.sum()) / w64, "unit": UNIT, "swarms": len(sub),
-                                    "steps": 500, "wall_s": w64},
+           "batched_f64": f64, "plain_f64_sequential": seq, "cpu_baseline": base,
            "results_sample": {f"{ENs[i]:.1f}Td": {"W_flux": res[i][0], "W_bulk": res[i][1], "alpha": res[i][9],
                                                   "eta": res[i][10], "mean_eps": res[i][6]}
                               for i in (0, 64, 128, 192, 255)}}
@@ -569,8 +621,8 @@ def run_mlp(args):
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
     sur = S.Surrogate(W.mlp_init(44), X, Y)
-    n_train = 20000
-    trace, t_train = sur.fit(n_train, lr=1e-3, chunk=2000)
+    n_train = args.mlp_steps
+    trace, t_train = sur.fit(n_train, lr=1e-3, chunk=min(2000, n_train))
     # held-out swarms at fresh random points (one batched call each)
     q = W.mlp_query_points(64, 45)
     torch.cuda.synchronize()
@@ -585,6 +637,9 @@ def run_mlp(args):
     def rms(a, b, cols):
         return {S.TARGET_NAMES[c]: float(np.sqrt(np.mean((a[:, c] - b[:, c]) ** 2))) for c in cols}
     hi = q[:, 0] > 200
+    # statistical scatter of the held-out values themselves: RMS of the batch-means error of each log target
+    err_cols = {0: (0, 11), 1: (2, 13), 2: (3, 14), 5: (6, 17)}
+    scatter = {S.TARGET_NAMES[c]: float(np.sqrt(np.mean((res[:, e] / res[:, v]) ** 2))) for c, (v, e) in err_cols.items()}
     # inference: 2^24 standardized points resident on the device
     n_q = 1 << 24
     qq = W.mlp_query_points(n_q, 46)
@@ -628,6 +683,7 @@ def run_mlp(args):
            "heldout": {"swarms": len(q), "swarm_queries_per_s": len(q) / t_held,
                        "rms_log_error_surrogate": rms(pred, held, [0, 1, 2, 5]),
                        "rms_log_error_table": rms(lin, held, [0, 1, 2, 5]),
+                       "heldout_scatter": scatter,
                        "rms_log_alpha_above_200Td": {"surrogate": float(np.sqrt(np.mean((pred[hi, 3] - held[hi, 3]) ** 2))),
                                                      "table": float(np.sqrt(np.mean((lin[hi, 3] - held[hi, 3]) ** 2)))}},
            "speedup_vs_swarm_per_query": n_q / (ms * 1e-3) / (len(q) / t_held)}
@@ -680,7 +736,7 @@ def main():
     if axi:
         photo.update(geometry=1, weight_interval=wl["weight_interval"])
     ctx = streamer_context(wl, args.precision, cap, 2110144940 + rank, boundary=args.boundary,
-                           adaptive_dt=not args.fixed_dt, extra=photo)
+                           adaptive_dt=not args.fixed_dt, extra=photo, sort_interval=args.sort_interval)
     if args.host_solve:
         ctx.set_poisson(1e-6, 200, device_loop=False)
     vpre, vpost = (int(v) for v in args.vcycle.split(","))

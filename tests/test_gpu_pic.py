@@ -356,3 +356,33 @@ def test_step_with_photoionization_matches_oracle(prec, steps):
         assert abs(st.n_photo - n_photo) <= max(2, 1e-3 * n_photo)
         nc, og, orf, bad, worst = compare_sets(gpu, ref, GRID["dx"], 1e-5, v_floor=1e5)
         assert worst["gross"] + og + orf <= 1e-4 * len(ref["id"]) + 4, (og, orf, worst)
+
+
+@pytest.mark.parametrize("sweeps", [(1, 1), (1, 2), (3, 3)])
+def test_vcycle_sweeps_keep_the_solve_tolerance(sweeps):
+    """pic_set_multigrid changes only the preconditioner: the coupled
+    float-pair solve still reaches its residual target and the oracle's
+    solution of the same (zero) charge."""
+    grid = W.grid_spec(32, 32, 48, 5e-5)
+    V0 = 2000.0
+    mask = W.needle_mask(grid, 0.8e-3, 0.15e-3)
+    ctx = _ctx(W.synthetic_air(), grid, 32, capacity=1024, seed=SEED, dt=1e-12, mask=mask, coupled=True,
+               v_lo=0.0, v_hi=V0, v_mask=V0, poisson_rtol=1e-8)
+    ctx.set_multigrid(*sweeps)
+    ref, _, _ = O.poisson(grid, np.zeros((48, 32, 32)), mask, V0, 0.0, V0, rtol=1e-12)
+    n = 32 * 32 * 48
+    for _ in range(3):
+        st = ctx.step(1, stats=True)
+        assert st.poisson_rel_res <= 1e-8, (sweeps, st.poisson_rel_res)
+        blob = ctx.save()
+        phi = np.frombuffer(blob, np.float64, count=n, offset=len(blob) - 8 * n).reshape(48, 32, 32)
+        assert np.linalg.norm(phi - ref) / np.linalg.norm(ref) < 1e-5
+
+
+def test_vcycle_sweeps_are_checked():
+    from paper_2110_14494_gb300 import PicError
+    ctx = _ctx(W.synthetic_air(), GRID, 32, capacity=1024, seed=SEED)
+    for bad in ((0, 2), (2, 5)):
+        with pytest.raises(PicError) as e:
+            ctx.set_multigrid(*bad)
+        assert e.value.code == -1
