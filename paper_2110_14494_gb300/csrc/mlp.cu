@@ -159,12 +159,20 @@ __global__ void __launch_bounds__(kHeadWarps * 32) k_head(const float* __restric
     float b2[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) b2[q] = th[OFF_B2 + lane + 32 * q];
+    // training batches are multiples of kHeadPts (train_size_ok): every point
+    // of the block exists; the next point's z2 row is loaded ahead
+    float zn[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) zn[q] = z2[(size_t)(blockIdx.x * kHeadPts + warp) * NH + lane + 32 * q];
     for (int pp = warp; pp < kHeadPts; pp += kHeadWarps) {
         const int p = blockIdx.x * kHeadPts + pp;
-        if (p >= n) break;
         float h2[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) h2[q] = tanh_fast(z2[(size_t)p * NH + lane + 32 * q] + b2[q]);
+        for (int q = 0; q < 4; ++q) h2[q] = tanh_fast(zn[q] + b2[q]);
+        if (pp + kHeadWarps < kHeadPts) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) zn[q] = z2[(size_t)(p + kHeadWarps) * NH + lane + 32 * q];
+        }
         float dy[NO];
         float lsum = 0.0f;
 #pragma unroll
@@ -216,15 +224,19 @@ __global__ void __launch_bounds__(kHeadWarps * 32) k_head(const float* __restric
 }
 
 // dz1 = dh1 (1 - h1^2); per-block partials of gW1[128][2] and gb1[128] over
-// kL1Pts points (thread = hidden unit).
+// kL1Pts points (thread = hidden unit).  Training batches are multiples of
+// kL1Pts (train_size_ok), so every block has all of its points; the loop is
+// unrolled so that the loads of several points are in flight together (the
+// sums still run over the points in order).
 constexpr int kL1Pts = 64, kL1Part = NH * NI + NH;
 __global__ void __launch_bounds__(NH) k_layer1_back(const float* __restrict__ dh1, const float* __restrict__ h1,
                                                     const float* __restrict__ x, int n, float* __restrict__ part) {
+    (void)n;
     const int u = threadIdx.x;
     float g0 = 0.0f, g1 = 0.0f, gb = 0.0f;
+#pragma unroll 16
     for (int pp = 0; pp < kL1Pts; ++pp) {
         const int p = blockIdx.x * kL1Pts + pp;
-        if (p >= n) break;
         const float h = h1[(size_t)p * NH + u];
         const float dz = dh1[(size_t)p * NH + u] * (1.0f - h * h);
         g0 = fmaf(dz, x[p * NI], g0);
