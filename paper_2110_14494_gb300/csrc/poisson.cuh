@@ -24,7 +24,7 @@ struct MG {
     uint8_t* m[kMaxLevels];
     double* norms = nullptr;  // CG scalars: ||b||^2, ||r||^2, rho, gamma, z.r, z.q, alpha, beta
     double *r64 = nullptr, *p64 = nullptr, *q64 = nullptr;  // CG vectors (float64)
-    int pre = 2, post = 2, coarse_sweeps = 8;
+    int pre = 2, post = 2, coarse_sweeps = 4;  // coarse: red-black sweeps on the coarsest level
     float omega = 1.0f;          // over-relaxation of the pre- and post-smoothing sweeps (1: Gauss-Seidel)
     // mixed solve: CG iterations run before the first convergence or
     // refinement test (0 to 2; at most max_cycles).  A coupled PIC context
