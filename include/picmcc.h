@@ -208,6 +208,11 @@ int pic_get_particles(pic_ctx *ctx, pic_particles_host *p, long long cap, long l
  * E_uniform without Ex). */
 int pic_set_field(pic_ctx *ctx, const float *Ex, const float *Ey, const float *Ez, const double E_uniform[3]);
 
+/* The same from float64 device arrays: a float64 context gathers from them
+ * unrounded, a float32 context from their rounding to float. */
+int pic_set_field_f64(pic_ctx *ctx, const double *Ex, const double *Ey, const double *Ez,
+                      const double E_uniform[3]);
+
 /* Advances all electrons n_steps times (Sec. 2.1): trilinear gather, Verlet
  * half-kick completing Eq. 2, collisional flight over dt with the
  * null-collision method, children finishing the step, reflection at the

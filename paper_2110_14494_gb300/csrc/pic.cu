@@ -217,8 +217,8 @@ __global__ void k_seed_maxwell(long long n, double sig, Keys K, Soa<T> p) {
     }
 }
 
-template <class T>
-__global__ void k_pack_field(const float* __restrict__ Ex, const float* __restrict__ Ey, const float* __restrict__ Ez,
+template <class TI, class T>
+__global__ void k_pack_field(const TI* __restrict__ Ex, const TI* __restrict__ Ey, const TI* __restrict__ Ez,
                              long long n, T* __restrict__ E4) {
     for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
         E4[4 * c] = (T)Ex[c];
@@ -1510,7 +1510,10 @@ extern "C" int pic_count(pic_ctx* c, long long* n) {
     return rc;
 }
 
-extern "C" int pic_set_field(pic_ctx* c, const float* Ex, const float* Ey, const float* Ez, const double E_uniform[3]) {
+// The field grids (float or double planes) packed into the context's [n][4]
+// layout in its own precision.
+template <class TI>
+static int set_field(pic_ctx* c, const TI* Ex, const TI* Ey, const TI* Ez, const double E_uniform[3]) {
     if (!c) return PIC_ERR_ARG;
     if (Ex == nullptr) {
         if (!E_uniform) return PIC_ERR_ARG;
@@ -1521,13 +1524,22 @@ extern "C" int pic_set_field(pic_ctx* c, const float* Ex, const float* Ey, const
         c->field_uniform = 0;
         const long long n = c->g.ncell();
         if (c->prec == 32)
-            k_pack_field<float><<<grid_n(n), 256, 0, c->s>>>(Ex, Ey, Ez, n, (float*)c->E4p(c->ph_cur));
+            k_pack_field<TI, float><<<grid_n(n), 256, 0, c->s>>>(Ex, Ey, Ez, n, (float*)c->E4p(c->ph_cur));
         else
-            k_pack_field<double><<<grid_n(n), 256, 0, c->s>>>(Ex, Ey, Ez, n, (double*)c->E4p(c->ph_cur));
+            k_pack_field<TI, double><<<grid_n(n), 256, 0, c->s>>>(Ex, Ey, Ez, n, (double*)c->E4p(c->ph_cur));
     }
     c->field_valid = 1;
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? PIC_OK : c->cuda_fail(e, "set field");
+}
+
+extern "C" int pic_set_field(pic_ctx* c, const float* Ex, const float* Ey, const float* Ez, const double E_uniform[3]) {
+    return set_field<float>(c, Ex, Ey, Ez, E_uniform);
+}
+
+extern "C" int pic_set_field_f64(pic_ctx* c, const double* Ex, const double* Ey, const double* Ez,
+                                 const double E_uniform[3]) {
+    return set_field<double>(c, Ex, Ey, Ez, E_uniform);
 }
 
 // Unpacks the packed field [n][4] (context precision) into float64 planes.

@@ -734,7 +734,7 @@ size_t MG::carve(void* base, int nx_, int ny_, int nz_, bool mixed_, bool pair_c
         loop = (MxLoop*)take(sizeof(MxLoop));
         const size_t b3 = (size_t)((nx_ + BX - 1) / BX) * ((ny_ + BY - 1) / BY) * ((nz_ + ZC - 1) / ZC);
         const size_t bf = (n0 + kFlatBlock * kFlatPer - 1) / (kFlatBlock * kFlatPer);
-        part = (double*)take(2 * 8 * (b3 > bf ? b3 : bf));
+        part = (double*)take(3 * 8 * (b3 > bf ? b3 : bf));  // up to three partial sums per block
         r64 = p64 = q64 = nullptr;
     } else {
         loop = nullptr;
@@ -952,18 +952,17 @@ void MG::iteration_mixed(cudaStream_t s, int it) {
     const int nx = lx[0], ny = ly[0], nz = lz[0], n = nx * ny * nz;
     const int cur = it & 1, first = it == 0 ? 1 : 0;
     vcycle(s);
-    launch_pdl(k_mx_dots, grid_mxf(n), dim3(kFlatBlock), 0, s, (const float*)e[0], (const float*)g[0],
-               (const float*)q32, n, first, part, ctr + 1, norms);
+    // w = A z goes to p32[cur] (the direction of two iterations ago, free
+    // here), where the second kernel replaces it by the new direction
     if (nx % 4 == 0)
-        launch_pdl(k_mx_dir_apply4, grid_mx3v(nx, ny, nz), kBlk, 0, s, (const float*)e[0],
-                   (const float*)p32[cur ^ 1], p32[cur], q32, (const uint8_t*)m[0], nx, ny, nz, first, part, ctr + 2,
-                   norms);
+        launch_pdl(k_mx_apply4, grid_mx3v(nx, ny, nz), kBlk, 0, s, (const float*)e[0], (const float*)g[0],
+                   (const float*)q32, p32[cur], (const uint8_t*)m[0], nx, ny, nz, first, part, ctr + 1, norms);
     else
-        launch_pdl(k_mx_dir_apply, grid_mx3(nx, ny, nz), kBlk, 0, s, (const float*)e[0], (const float*)p32[cur ^ 1],
-                   p32[cur], q32, (const uint8_t*)m[0], nx, ny, nz, first, part, ctr + 2, norms);
-    launch_pdl(k_mx_update, grid_mxf(n), dim3(kFlatBlock), 0, s, (const float*)p32[cur], (const float*)q32, d32,
-               g[0], n, first, part, ctr + 3, norms);
-    launches += 3;
+        launch_pdl(k_mx_apply, grid_mx3(nx, ny, nz), kBlk, 0, s, (const float*)e[0], (const float*)g[0],
+                   (const float*)q32, p32[cur], (const uint8_t*)m[0], nx, ny, nz, first, part, ctr + 1, norms);
+    launch_pdl(k_mx_step, grid_mxf(n), dim3(kFlatBlock), 0, s, (const float*)e[0], (const float*)p32[cur ^ 1],
+               p32[cur], q32, d32, g[0], n, first, part, ctr + 3, norms);
+    launches += 2;
 }
 
 void MG::extrapolate_pair(const float* ch, const float* cl, const float* ph, const float* pl, float* oh, float* ol,

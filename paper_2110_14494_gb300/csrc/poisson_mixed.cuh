@@ -298,22 +298,24 @@ __device__ __forceinline__ float4 fma4(float a, float4 x, float4 y) {
 __device__ __forceinline__ float4 ld4(const float* p, int v4) { return reinterpret_cast<const float4*>(p)[v4]; }
 __device__ __forceinline__ void st4(float* p, int v4, float4 v) { reinterpret_cast<float4*>(p)[v4] = v; }
 
-// t1 = z.r, t2 = z.q; the last block sets beta (flexible CG:
-// beta = -alpha (z.q) / rho_old) and rho = z.r.
-__global__ void __launch_bounds__(kFlatBlock) k_mx_dots(const float* __restrict__ z, const float* __restrict__ r,
-                                                        const float* __restrict__ q, int n, int first, double* part,
-                                                        unsigned* ctr, double* sc) {
-    pdl_wait();
-    float acc[2] = {0.0f, 0.0f};
-    FLAT4_LOOP(
-        const float4 zz = ld4(z, v4); acc[0] += dot4(zz, ld4(r, v4)); if (!first) acc[1] += dot4(zz, ld4(q, v4));,
-        acc[0] += z[c] * r[c]; if (!first) acc[1] += z[c] * q[c];)
-    double tot[2];
-    if (grid_sums<2>(acc, part, ctr, tot) && threadIdx.x == 0) {
-        const double rho_old = sc[S_RHO];
-        sc[S_BETA] = (first || rho_old == 0.0) ? 0.0 : -sc[S_ALPHA] * tot[1] / rho_old;
-        sc[S_RHO] = tot[0];
-    }
+// One flexible-CG iteration takes two kernels.  With z = M r, the new
+// direction p = z + beta p_prev and q = A p = A z + beta q_prev, so A z and
+// the three sums z.r, z.q_prev, z.(A z) can be formed in one stencil pass
+// before p exists: with A symmetric, p.q = z.Az + 2 beta z.q_prev + beta^2
+// p_prev.q_prev (p_prev.Az = q_prev.z), where p_prev.q_prev is the previous
+// iteration's gamma.  The second pass forms p and q and updates delta and r.
+
+// The scalars of the iteration from the three sums: beta = -alpha_prev
+// (z.q_prev) / rho_prev (flexible CG), rho = z.r, gamma = p.q, alpha = rho /
+// gamma.  First iteration of a pass: beta = 0, gamma = z.Az.
+__device__ __forceinline__ void cg_scalars(const double (&tot)[3], int first, double* sc) {
+    const double rho_old = sc[S_RHO];
+    const double beta = (first || rho_old == 0.0) ? 0.0 : -sc[S_ALPHA] * tot[1] / rho_old;
+    const double gam = first ? tot[2] : tot[2] + beta * (2.0 * tot[1] + beta * sc[S_GAM]);
+    sc[S_BETA] = beta;
+    sc[S_RHO] = tot[0];
+    sc[S_GAM] = gam;
+    sc[S_ALPHA] = gam > 0.0 ? tot[0] / gam : 0.0;
 }
 
 // Stencil kernels walk ZC planes per thread and load everything first: the
@@ -323,49 +325,46 @@ __global__ void __launch_bounds__(kFlatBlock) k_mx_dots(const float* __restrict_
 __device__ __forceinline__ float lane_xm(float v, int lane) { return __shfl_up_sync(kFull, v, 1); }
 __device__ __forceinline__ float lane_xp(float v, int lane) { return __shfl_down_sync(kFull, v, 1); }
 
-// p = z + beta p_prev (all cells, 0 on electrode cells), q = A p with the
-// neighbours' new directions formed on the fly, gamma = p.q; the last block
-// sets alpha = rho / gamma.
-__global__ void __launch_bounds__(BX * BY) k_mx_dir_apply(const float* __restrict__ z,
-                                                          const float* __restrict__ p_prev, float* __restrict__ p_cur,
-                                                          float* __restrict__ q, const uint8_t* __restrict__ mask,
-                                                          int nx, int ny, int nz, int first, double* part,
-                                                          unsigned* ctr, double* sc) {
+// w = A z (0 on electrode cells) with the sums z.r, z.q_prev, z.w, then the
+// iteration's scalars (last block).  q_prev is not read when first is set.
+__global__ void __launch_bounds__(BX * BY) k_mx_apply(const float* __restrict__ z, const float* __restrict__ r,
+                                                      const float* __restrict__ q_prev, float* __restrict__ w,
+                                                      const uint8_t* __restrict__ mask, int nx, int ny, int nz,
+                                                      int first, double* part, unsigned* ctr, double* sc) {
     pdl_wait();
-    const float beta = first ? 0.0f : (float)sc[S_BETA];
-    const bool use_prev = beta != 0.0f;
-    auto P = [&](int x) { return use_prev ? fmaf(beta, __ldg(p_prev + x), __ldg(z + x)) : __ldg(z + x); };
     const int lane = threadIdx.x;
     const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y, k0 = blockIdx.z * ZC;
     const bool in = i < nx && j < ny;
     const int pl = nx * ny;
     const int c0 = in ? lin(i, j, 0, nx, ny) : 0;
-    float col[ZC + 2], ym[ZC], yp[ZC], xe[ZC];
+    float col[ZC + 2], ym[ZC], yp[ZC], xe[ZC], rv[ZC], qv[ZC];
     uint8_t mk[ZC];
 #pragma unroll
     for (int d = 0; d < ZC + 2; ++d) {
         const int k = k0 - 1 + d;
-        col[d] = (in && k >= 0 && k < nz) ? P(c0 + k * pl) : 0.0f;
+        col[d] = (in && k >= 0 && k < nz) ? __ldg(z + c0 + k * pl) : 0.0f;
     }
 #pragma unroll
     for (int d = 0; d < ZC; ++d) {
         const int k = k0 + d;
         const bool ok = in && k < nz;
         const int c = c0 + (ok ? k : 0) * pl;
-        ym[d] = ok && j > 0 ? P(c - nx) : 0.0f;
-        yp[d] = ok && j < ny - 1 ? P(c + nx) : 0.0f;
+        ym[d] = ok && j > 0 ? __ldg(z + c - nx) : 0.0f;
+        yp[d] = ok && j < ny - 1 ? __ldg(z + c + nx) : 0.0f;
         // the warp's end lanes fetch their outer x neighbour
         xe[d] = 0.0f;
-        if (ok && lane == 0 && i > 0) xe[d] = P(c - 1);
-        if (ok && lane == BX - 1 && i < nx - 1) xe[d] = P(c + 1);
+        if (ok && lane == 0 && i > 0) xe[d] = __ldg(z + c - 1);
+        if (ok && lane == BX - 1 && i < nx - 1) xe[d] = __ldg(z + c + 1);
         mk[d] = ok ? mask[c] : 1;
+        rv[d] = ok ? __ldg(r + c) : 0.0f;
+        qv[d] = ok && !first ? __ldg(q_prev + c) : 0.0f;
     }
-    float acc[1] = {0.0f};
+    float acc[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int d = 0; d < ZC; ++d) {
         const int k = k0 + d;
-        const float pc = col[d + 1];
-        float xm = lane_xm(pc, lane), xp = lane_xp(pc, lane);
+        const float zc = col[d + 1];
+        float xm = lane_xm(zc, lane), xp = lane_xp(zc, lane);
         if (lane == 0) xm = xe[d];
         if (lane == BX - 1) xp = xe[d];
         if (!in || k >= nz) continue;
@@ -374,44 +373,31 @@ __global__ void __launch_bounds__(BX * BY) k_mx_dir_apply(const float* __restric
         const float zm = col[d], zp = col[d + 2];
         const float diag =
             6.0f - (float)((i == 0) + (i == nx - 1) + (j == 0) + (j == ny - 1)) + (float)((k == 0) + (k == nz - 1));
-        float qq = diag * pc - (((((xm + xp) + ym[d]) + yp[d]) + zm) + zp);
-        if (mk[d]) qq = 0.0f;
-        const int c = c0 + k * pl;
-        p_cur[c] = pc;
-        q[c] = qq;
-        acc[0] += pc * qq;
+        float ww = diag * zc - (((((xm + xp) + ym[d]) + yp[d]) + zm) + zp);
+        if (mk[d]) ww = 0.0f;
+        w[c0 + k * pl] = ww;
+        acc[0] += zc * rv[d];
+        acc[1] += zc * qv[d];
+        acc[2] += zc * ww;
     }
-    double tot[1];
-    if (grid_sums<1>(acc, part, ctr, tot) && threadIdx.x == 0 && threadIdx.y == 0) {
-        const double gam = tot[0];
-        sc[S_GAM] = gam;
-        sc[S_ALPHA] = gam > 0.0 ? sc[S_RHO] / gam : 0.0;
-    }
+    double tot[3];
+    if (grid_sums<3>(acc, part, ctr, tot) && threadIdx.x == 0 && threadIdx.y == 0) cg_scalars(tot, first, sc);
 }
 
-// The same as k_mx_dir_apply for nx % 4 == 0, with four consecutive x cells
-// per thread (16-byte loads and stores): lane l of a warp holds x = 4 (32 b
-// + l) .. + 3 of one row; the x neighbours across float4 boundaries come
-// from the adjacent lanes, and the warp's end lanes load them.  Each cell's
-// p and q are the scalar kernel's (same operations in the same order); the
-// partial sums of p.q group the cells differently.
+// The same for nx % 4 == 0, with four consecutive x cells per thread
+// (16-byte loads and stores): lane l of a warp holds x = 4 (32 b + l) .. + 3
+// of one row; the x neighbours across float4 boundaries come from the
+// adjacent lanes, and the warp's end lanes load them.  Each cell's w is the
+// scalar kernel's (same operations in the same order); the partial sums
+// group the cells differently.
 __device__ __forceinline__ float4 ld4g(const float* p, int c) { return __ldg(reinterpret_cast<const float4*>(p + c)); }
-__device__ __forceinline__ float4 pdir4(const float* z, const float* pp, float beta, bool use_prev, int c) {
-    const float4 zz = ld4g(z, c);
-    if (!use_prev) return zz;
-    const float4 q = ld4g(pp, c);
-    return make_float4(fmaf(beta, q.x, zz.x), fmaf(beta, q.y, zz.y), fmaf(beta, q.z, zz.z), fmaf(beta, q.w, zz.w));
-}
 __device__ __forceinline__ float f4c(const float4& v, int e) { return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w)); }
 
-__global__ void __launch_bounds__(BX * BY) k_mx_dir_apply4(const float* __restrict__ z,
-                                                           const float* __restrict__ p_prev,
-                                                           float* __restrict__ p_cur, float* __restrict__ q,
-                                                           const uint8_t* __restrict__ mask, int nx, int ny, int nz,
-                                                           int first, double* part, unsigned* ctr, double* sc) {
+__global__ void __launch_bounds__(BX * BY) k_mx_apply4(const float* __restrict__ z, const float* __restrict__ r,
+                                                       const float* __restrict__ q_prev, float* __restrict__ w,
+                                                       const uint8_t* __restrict__ mask, int nx, int ny, int nz,
+                                                       int first, double* part, unsigned* ctr, double* sc) {
     pdl_wait();
-    const float beta = first ? 0.0f : (float)sc[S_BETA];
-    const bool use_prev = beta != 0.0f;
     const int lane = threadIdx.x;
     const int i0 = 4 * (blockIdx.x * BX + threadIdx.x), j = blockIdx.y * BY + threadIdx.y, k0 = blockIdx.z * ZC;
     const bool in = i0 < nx && j < ny;
@@ -424,78 +410,85 @@ __global__ void __launch_bounds__(BX * BY) k_mx_dir_apply4(const float* __restri
 #pragma unroll
     for (int d = 0; d < ZC + 2; ++d) {
         const int k = k0 - 1 + d;
-        col[d] = (in && k >= 0 && k < nz) ? pdir4(z, p_prev, beta, use_prev, c0 + k * pl) : zero4;
+        col[d] = (in && k >= 0 && k < nz) ? ld4g(z, c0 + k * pl) : zero4;
     }
 #pragma unroll
     for (int d = 0; d < ZC; ++d) {
         const int k = k0 + d;
         const bool ok = in && k < nz;
         const int c = c0 + (ok ? k : 0) * pl;
-        ym[d] = ok && j > 0 ? pdir4(z, p_prev, beta, use_prev, c - nx) : zero4;
-        yp[d] = ok && j < ny - 1 ? pdir4(z, p_prev, beta, use_prev, c + nx) : zero4;
-        xl[d] = 0.0f;
-        xr[d] = 0.0f;
-        if (ok && lane == 0 && i0 > 0) {
-            const float a = __ldg(z + c - 1);
-            xl[d] = use_prev ? fmaf(beta, __ldg(p_prev + c - 1), a) : a;
-        }
-        if (ok && lane == BX - 1 && i0 + 4 < nx) {
-            const float a = __ldg(z + c + 4);
-            xr[d] = use_prev ? fmaf(beta, __ldg(p_prev + c + 4), a) : a;
-        }
+        ym[d] = ok && j > 0 ? ld4g(z, c - nx) : zero4;
+        yp[d] = ok && j < ny - 1 ? ld4g(z, c + nx) : zero4;
+        xl[d] = ok && lane == 0 && i0 > 0 ? __ldg(z + c - 1) : 0.0f;
+        xr[d] = ok && lane == BX - 1 && i0 + 4 < nx ? __ldg(z + c + 4) : 0.0f;
         mk[d] = ok ? *reinterpret_cast<const uchar4*>(mask + c) : make_uchar4(1, 1, 1, 1);
     }
-    float acc[1] = {0.0f};
+    float acc[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int d = 0; d < ZC; ++d) {
         const int k = k0 + d;
-        const float4 pc = col[d + 1];
-        float left = __shfl_up_sync(kFull, pc.w, 1), right = __shfl_down_sync(kFull, pc.x, 1);
+        const float4 zc = col[d + 1];
+        float left = __shfl_up_sync(kFull, zc.w, 1), right = __shfl_down_sync(kFull, zc.x, 1);
         if (lane == 0) left = xl[d];
         if (lane == BX - 1) right = xr[d];
         if (!in || k >= nz) continue;
         const float fz = (float)((k == 0) + (k == nz - 1));
         const float fy = (float)((j == 0) + (j == ny - 1));
         const unsigned char mm[4] = {mk[d].x, mk[d].y, mk[d].z, mk[d].w};
-        float qv[4];
+        float wv[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int i = i0 + e;
-            const float c = f4c(pc, e);
-            float xm = e == 0 ? left : f4c(pc, e - 1);
-            float xp = e == 3 ? right : f4c(pc, e + 1);
+            const float c = f4c(zc, e);
+            float xm = e == 0 ? left : f4c(zc, e - 1);
+            float xp = e == 3 ? right : f4c(zc, e + 1);
             if (i == 0) xm = 0.0f;
             if (i == nx - 1) xp = 0.0f;
             const float diag = 6.0f - ((float)((i == 0) + (i == nx - 1)) + fy) + fz;
-            float qq = diag * c - (((((xm + xp) + f4c(ym[d], e)) + f4c(yp[d], e)) + f4c(col[d], e)) + f4c(col[d + 2], e));
-            if (mm[e]) qq = 0.0f;
-            qv[e] = qq;
-            acc[0] += c * qq;
+            float ww = diag * c - (((((xm + xp) + f4c(ym[d], e)) + f4c(yp[d], e)) + f4c(col[d], e)) + f4c(col[d + 2], e));
+            if (mm[e]) ww = 0.0f;
+            wv[e] = ww;
+            acc[2] += c * ww;
         }
+        *reinterpret_cast<float4*>(w + c0 + k * pl) = make_float4(wv[0], wv[1], wv[2], wv[3]);
+    }
+    // z.r and z.q_prev after the stencil (fewer registers held across it)
+#pragma unroll
+    for (int d = 0; d < ZC; ++d) {
+        const int k = k0 + d;
+        if (!in || k >= nz) continue;
         const int c = c0 + k * pl;
-        *reinterpret_cast<float4*>(p_cur + c) = pc;
-        *reinterpret_cast<float4*>(q + c) = make_float4(qv[0], qv[1], qv[2], qv[3]);
+        const float4 zc = col[d + 1], rv = ld4g(r, c);
+        acc[0] += dot4(zc, rv);
+        if (!first) acc[1] += dot4(zc, ld4g(q_prev, c));
     }
-    double tot[1];
-    if (grid_sums<1>(acc, part, ctr, tot) && threadIdx.x == 0 && threadIdx.y == 0) {
-        const double gam = tot[0];
-        sc[S_GAM] = gam;
-        sc[S_ALPHA] = gam > 0.0 ? sc[S_RHO] / gam : 0.0;
-    }
+    double tot[3];
+    if (grid_sums<3>(acc, part, ctr, tot) && threadIdx.x == 0 && threadIdx.y == 0) cg_scalars(tot, first, sc);
 }
 
-// delta (+)= alpha p, r -= alpha q, ||r||^2 into sc[S_R2].
-__global__ void __launch_bounds__(kFlatBlock) k_mx_update(const float* __restrict__ p, const float* __restrict__ q,
-                                                          float* __restrict__ d, float* __restrict__ r, int n,
-                                                          int first, double* part, unsigned* ctr, double* sc) {
+// p = z + beta p_prev written over w (in p_w), q = w + beta q_prev (in place),
+// delta (+)= alpha p, r -= alpha q, ||r||^2 into sc[S_R2].  p_prev and q_prev
+// are not read when first is set (beta = 0).
+__global__ void __launch_bounds__(kFlatBlock) k_mx_step(const float* __restrict__ z,
+                                                        const float* __restrict__ p_prev, float* __restrict__ p_w,
+                                                        float* __restrict__ q, float* __restrict__ d,
+                                                        float* __restrict__ r, int n, int first, double* part,
+                                                        unsigned* ctr, double* sc) {
     pdl_wait();
     const float a = (float)sc[S_ALPHA];
+    const float b = first ? 0.0f : (float)sc[S_BETA];
+    const bool use_prev = b != 0.0f;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     float acc[1] = {0.0f};
     FLAT4_LOOP(
-        const float4 pp = ld4(p, v4); const float4 qq = ld4(q, v4); const float4 r0 = ld4(r, v4);
-        const float4 d0 = first ? make_float4(0.f, 0.f, 0.f, 0.f) : ld4(d, v4);
-        const float4 rr = fma4(-a, qq, r0); st4(r, v4, rr); st4(d, v4, fma4(a, pp, d0)); acc[0] += dot4(rr, rr);,
-        d[c] = first ? a * p[c] : fmaf(a, p[c], d[c]); const float rr = fmaf(-a, q[c], r[c]); r[c] = rr;
+        const float4 zz = ld4(z, v4); const float4 ww = ld4(p_w, v4); const float4 r0 = ld4(r, v4);
+        const float4 pp = use_prev ? fma4(b, ld4(p_prev, v4), zz) : zz;
+        const float4 qq = use_prev ? fma4(b, ld4(q, v4), ww) : ww;
+        const float4 d0 = first ? zero4 : ld4(d, v4);
+        const float4 rr = fma4(-a, qq, r0); st4(p_w, v4, pp); st4(q, v4, qq); st4(r, v4, rr);
+        st4(d, v4, fma4(a, pp, d0)); acc[0] += dot4(rr, rr);,
+        const float pp = use_prev ? fmaf(b, p_prev[c], z[c]) : z[c]; const float qq = use_prev ? fmaf(b, q[c], p_w[c]) : p_w[c];
+        p_w[c] = pp; q[c] = qq; d[c] = first ? a * pp : fmaf(a, pp, d[c]); const float rr = fmaf(-a, qq, r[c]); r[c] = rr;
         acc[0] += rr * rr;)
     double tot[1];
     if (grid_sums<1>(acc, part, ctr, tot) && threadIdx.x == 0) sc[S_R2] = tot[0];

@@ -102,7 +102,7 @@ class swarm_result(C.Structure):
 
 
 EXPORTS = ("pic_workspace_bytes", "pic_init", "pic_destroy", "pic_last_error", "pic_status_string",
-           "pic_seed_gaussian", "pic_set_particles", "pic_get_particles", "pic_set_field", "pic_step",
+           "pic_seed_gaussian", "pic_set_particles", "pic_get_particles", "pic_set_field", "pic_set_field_f64", "pic_step",
            "pic_deposit", "pic_weight_update", "pic_count", "pic_save", "pic_load", "pic_progress",
            "pic_profile", "pic_upload", "pic_download", "pic_set_poisson", "pic_get_field", "pic_get_deposit", "pic_set_multigrid",
            "poisson_workspace_bytes", "poisson_solve", "poisson_solve_noalloc", "swarm_workspace_bytes",
@@ -134,6 +134,7 @@ def lib():
     L.pic_set_particles.argtypes = [VP, C.c_longlong, P(pic_particles_host), C.c_int]
     L.pic_get_particles.argtypes = [VP, P(pic_particles_host), C.c_longlong, P(C.c_longlong)]
     L.pic_set_field.argtypes = [VP, VP, VP, VP, PD]
+    L.pic_set_field_f64.argtypes = [VP, VP, VP, VP, PD]
     L.pic_step.argtypes = [VP, C.c_int, P(pic_step_stats)]
     L.pic_set_poisson.argtypes = [VP, C.c_double, C.c_int, C.c_int]
     L.pic_set_multigrid.argtypes = [VP, C.c_int, C.c_int]
@@ -339,8 +340,20 @@ class PicContext:
         return out
 
     def set_field(self, Ex=None, Ey=None, Ez=None, uniform=None):
+        """Cell-centred field grids [nz][ny][nx] as contiguous CUDA tensors, all float32
+        (pic_set_field) or all float64 (pic_set_field_f64); or a uniform field."""
         u = (C.c_double * 3)(*(uniform if uniform is not None else (0.0, 0.0, 0.0)))
-        _check(lib().pic_set_field(self.h, _ptr(Ex), _ptr(Ey), _ptr(Ez), u), self.h, "pic_set_field")
+        if Ex is None:
+            _check(lib().pic_set_field(self.h, None, None, None, u), self.h, "pic_set_field")
+            return
+        import torch
+        n = self.grid["nx"] * self.grid["ny"] * self.grid["nz"]
+        for f in (Ex, Ey, Ez):
+            if (not isinstance(f, torch.Tensor) or not f.is_cuda or not f.is_contiguous() or f.numel() != n or
+                    f.dtype != Ex.dtype or f.dtype not in (torch.float32, torch.float64)):
+                raise TypeError("field grids: three contiguous CUDA tensors of %d float32 or float64 values" % n)
+        fn = "pic_set_field" if Ex.dtype == torch.float32 else "pic_set_field_f64"
+        _check(getattr(lib(), fn)(self.h, _ptr(Ex), _ptr(Ey), _ptr(Ez), u), self.h, fn)
 
     def step(self, n_steps=1, stats=False):
         st = pic_step_stats() if stats else None

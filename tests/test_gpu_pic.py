@@ -100,6 +100,59 @@ def test_step_fp64_matches_oracle(steps, boundary):
     assert int(qe.sum()) == int(rq_e.sum()) or abs(int(qe.sum()) - int(rq_e.sum())) < 64
 
 
+@pytest.mark.parametrize("steps", [1, 10])
+def test_step_fp64_field_matches_oracle(steps):
+    """pic_set_field_f64: a float64 context gathers from float64 grids
+    unrounded (a field with values no float32 can hold), against the oracle
+    stepping with the same float64 grids; a float32 context given the same
+    grids steps bit for bit as one given their float32 rounding."""
+    gas, F, mk, p0 = _setup(6000, 64, 5)
+    r = np.random.default_rng(17)
+    F64 = tuple(f.astype(np.float64) * (1.0 + 1e-9 * r.standard_normal(f.shape)) for f in F)
+    assert all(np.any(f != f.astype(np.float32)) for f in F64)
+    dt = 2e-12
+    ctx = _ctx(gas, GRID, 64, capacity=40000, seed=SEED, dt=dt, mask=mk)
+    ctx.set_field(*(torch.as_tensor(f).cuda() for f in F64))
+    got = tuple(f.cpu().numpy() for f in ctx.get_field())
+    assert all(np.array_equal(a, b) for a, b in zip(got, F64))
+    ctx.set_particles(p0)
+    ctx.step(steps)
+    gpu = ctx.get_particles()
+    m = O.Model(gas, dt, SEED, 64, GRID, F64, mask=mk)
+    P = O.Particles(40000, p0)
+    n = GRID["nx"] * GRID["ny"] * GRID["nz"]
+    rq_pos, rq_neg = np.zeros(n, np.int64), np.zeros(n, np.int64)
+    for s in range(1, steps + 1):
+        rc, _ = O.step(m, P, s, s == 1, np.zeros(n, np.int64), rq_pos, rq_neg)
+        assert rc == 0
+    nc, og, orf, bad, worst = compare_sets(gpu, P.view(), GRID["dx"], 1e-12, v_floor=1.0)
+    assert og == 0 and orf == 0 and bad == 0, (og, orf, worst)
+    # float32 contexts round the float64 grids to float
+    out = []
+    for fields in (F64, tuple(f.astype(np.float32) for f in F64)):
+        c32 = _ctx(gas, GRID, 32, capacity=40000, seed=SEED, dt=dt, mask=mk)
+        c32.set_field(*(torch.as_tensor(f).cuda() for f in fields))
+        c32.set_particles(p0)
+        c32.step(steps)
+        out.append(by_id(c32.get_particles()))
+    for k in out[0]:
+        assert np.array_equal(out[0][k], out[1][k]), k
+
+
+def test_set_field_checks_its_arrays():
+    from paper_2110_14494_gb300 import picmcc as P
+    ctx = _ctx(W.synthetic_air(), GRID, 32, capacity=1024, seed=SEED)
+    n = GRID["nx"] * GRID["ny"] * GRID["nz"]
+    good = [torch.zeros(n, device="cuda") for _ in range(3)]
+    for bad in ([good[0], good[1], good[2].double()], [good[0][:-1], good[1], good[2]],
+                [good[0].half(), good[1].half(), good[2].half()]):
+        with pytest.raises(TypeError):
+            ctx.set_field(*bad)
+    with pytest.raises(P.PicError) as e:
+        P._check(P.lib().pic_set_field_f64(ctx.h, P._ptr(good[0].double()), None, None, None), ctx.h, "f64")
+    assert e.value.code == -1
+
+
 def test_step_fp32_matches_oracle_single_step():
     gas, F, mk, p0 = _setup(100000, 32, 3)
     dt = 2e-12

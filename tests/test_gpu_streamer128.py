@@ -65,7 +65,8 @@ def _grids(ctx, n, fresh=False):
 
 def _energy_split(gpu, ref, dx, tol):
     """Median final kinetic energy (eV, oracle) of all common particles and of
-    those outside tol (position per cell, velocity per |v| + 1e5 m/s)."""
+    those outside tol but not gross (position per cell, velocity per |v| +
+    1e5 m/s; gross: beyond 1e-3, the decision flips counted separately)."""
     from tests.gpu_common import by_id
     G, R = by_id(gpu), by_id(ref)
     common, ig, ir = np.intersect1d(G["id"], R["id"], assume_unique=True, return_indices=True)
@@ -73,7 +74,7 @@ def _energy_split(gpu, ref, dx, tol):
     err = np.max([np.abs(G[k][ig] - R[k][ir]) / dx for k in ("x", "y", "z")] +
                  [np.abs(G[k][ig] - R[k][ir]) / (sp + 1e5) for k in ("vx", "vy", "vz")], axis=0)
     e = 0.5 * O.M_ELEC * sp ** 2 / O.Q_E
-    out = err > tol
+    out = (err > tol) & (err <= 1e-3)
     return float(np.median(e)), float(np.median(e[out])) if out.any() else 0.0
 
 
@@ -142,7 +143,7 @@ def test_coupled_streamer_128_matches_oracle(prec):
             # carries the float32 error of eps times eps / (eps - eps_th)): they end the step slow
             e_med, e_bad = _energy_split(gpu, ref, g["dx"], tol)
             print(f"step {done}: median final energy {e_med:.3g} eV, of the particles outside {tol:g} {e_bad:.3g} eV")
-            assert bad == 0 or e_bad < 0.5 * e_med, (done, e_bad, e_med)
+            assert bad - worst["gross"] == 0 or e_bad < 0.5 * e_med, (done, e_bad, e_med)
         assert abs(st.n_events - ost.n_events) <= 1e-4 * ost.n_events + 10
 
         # the step's own deposit is the deposit of the particles it left, bit for bit
