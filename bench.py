@@ -823,7 +823,13 @@ def main():
         print(json.dumps({"diag": "fp64 arm", **f64}), file=sys.stderr, flush=True)
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        base = cpu_baseline(wl)
+        if axi:
+            # the oracle's push on the Cartesian 128^3 streamer's seed (the same per-electron work: gather,
+            # flights, collisions, deposit); the (r, z) mesh changes only the grid arithmetic
+            base = cpu_baseline(workload(128, 1_000_000))
+            base["sample"] += "; Cartesian 128^3 streamer seed (the axisymmetric run has no Cartesian sample)"
+        else:
+            base = cpu_baseline(wl)
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
