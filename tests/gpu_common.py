@@ -26,6 +26,35 @@ def compare_sets(gpu: dict, ref: dict, dx: float, rtol: float, v_floor: float = 
     return len(common), len(g["id"]) - len(common), len(r["id"]) - len(common), int(bad.sum()), worst
 
 
+def rel_energy_error(gpu: dict, ref: dict, q: float) -> float:
+    """The q-quantile over the common particles of |eps_gpu - eps_ref| / eps_ref."""
+    g, r = by_id(gpu), by_id(ref)
+    _, ig, ir = np.intersect1d(g["id"], r["id"], assume_unique=True, return_indices=True)
+    eg = g["vx"][ig] ** 2 + g["vy"][ig] ** 2 + g["vz"][ig] ** 2
+    er = r["vx"][ir] ** 2 + r["vy"][ir] ** 2 + r["vz"][ir] ** 2
+    ok = er > 0
+    return float(np.quantile(np.abs(eg[ok] - er[ok]) / er[ok], q)) if ok.any() else 0.0
+
+
+def ill_conditioned(advance, before: dict, capacity: int, ref: dict, dx: float, tol: float, delta: float,
+                    seed: int):
+    """The oracle's own conditioning: the same starting state with every
+    energy moved by delta (relative, random sign) is advanced by
+    advance(particles) and compared with the unperturbed result ref.
+    Returns (flips: gross differences and particles on one side only, the
+    other particles outside tol).  Decisions taken within delta of their
+    thresholds flip, and near an inelastic threshold eps - eps_th amplifies
+    the error by eps / (eps - eps_th), whatever its source."""
+    import oracle as O
+    r = np.random.default_rng(seed)
+    s = np.sqrt(1.0 + delta * r.choice([-1.0, 1.0], size=len(before["vx"])))
+    pert = {k: (np.asarray(v) * s if k in ("vx", "vy", "vz") else np.array(v, copy=True)) for k, v in before.items()}
+    P = O.Particles(capacity, pert)
+    advance(P)
+    _, og, orf, bad, worst = compare_sets(P.view(), ref, dx, tol, v_floor=1e5)
+    return worst["gross"] + og + orf, bad - worst["gross"]
+
+
 def oracle_swarm_results(job):
     """The oracle's swarm coefficients for one (E/N, seed) job; a top-level
     function so that spawned worker processes can run several at once."""

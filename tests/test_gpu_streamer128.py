@@ -9,11 +9,15 @@ the same step (same step index, dt, half-kick length, field, electrode).
 Compared:
 - particles: float64 1e-12 per particle; float32 1e-5 (position per cell,
   velocity per |v| + 1e5 m/s) with decision flips (gross differences and
-  particles on one side only) at most 1e-5 N + 2 and rounding amplification
-  near inelastic thresholds at most 1e-3 N (the single-step test's bounds;
-  measured up to 9.3e-4 N at step 100, where these particles end the step with
-  a median energy of 0.7 eV against 5 eV for all, 58 % of them products born
-  in the step with half of what the ionization left);
+  particles on one side only) at most 1e-5 N + 2, and the other particles
+  outside 1e-5 (rounding amplification near inelastic thresholds: eps -
+  eps_th carries the error of eps times eps / (eps - eps_th)) at most twice
+  the step's own conditioning plus 10: the count the oracle leaves outside
+  1e-5 when it advances the same state with every energy moved by the
+  float32 path's measured error (the 90th percentile of |d eps| / eps over
+  the common particles, 1.4-1.9e-6); measured 843 and 987 particles against
+  1133 and 2375 at steps 11 and 100, ending the step with a median energy of
+  0.7-1.6 eV against 5 eV for all;
 - the deposit the step's own kernels made (pic_get_deposit) against the
   oracle's deposit of the GPU's particles after the step: bit for bit;
 - the ion grids' increments over the step against the oracle's (the same
@@ -32,7 +36,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from tests.gpu_common import compare_sets
+from tests.gpu_common import compare_sets, ill_conditioned, rel_energy_error
 
 pytestmark = pytest.mark.gpu
 
@@ -138,7 +142,18 @@ def test_coupled_streamer_128_matches_oracle(prec):
             assert og == 0 and orf == 0 and bad == 0, (done, og, orf, bad, worst)
         else:
             assert flips <= 1e-5 * N + 2, (done, flips, worst)
-            assert bad - worst["gross"] <= 1e-3 * N, (done, bad, worst)
+            # rounding amplification: bounded by the step's own conditioning under the float32 path's
+            # measured energy error (its 90th percentile over the common particles)
+            delta = rel_energy_error(gpu, ref, 0.9)
+
+            def advance(Pp):
+                rc, _ = O.step(m, Pp, done, done == 1, np.zeros(n, np.int64), qp0.copy(), qn0.copy())
+                assert rc == 0
+            c_flips, c_bad = ill_conditioned(advance, before, 3 * len(before["x"]) + 1024, ref, g["dx"], tol, delta,
+                                             1000 + done)
+            print(f"step {done}: energy error 90th percentile {delta:.3g}; under it the oracle has {c_flips} flips "
+                  f"and {c_bad} more outside {tol:g}; float32: {flips} flips, {bad - worst['gross']} more")
+            assert bad - worst["gross"] <= 2 * c_bad + 10, (done, bad, worst, c_bad, delta)
             # the particles outside 1e-5 are the rounding amplification of an inelastic loss (eps - eps_th
             # carries the float32 error of eps times eps / (eps - eps_th)): they end the step slow
             e_med, e_bad = _energy_split(gpu, ref, g["dx"], tol)
