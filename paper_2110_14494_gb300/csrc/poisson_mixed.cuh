@@ -17,7 +17,7 @@
 // and updates the CG scalars, so no separate scalar kernels are launched.
 
 constexpr int ZC = 4;            // z planes per thread in the stencil kernels
-constexpr int kFlatPer = 4;      // cells per thread in the flat kernels
+constexpr int kFlatPer = 2;      // float4 groups per thread in the flat kernels
 constexpr int kFlatBlock = 256;
 constexpr double kRefineDrop = 1e-4;
 
@@ -177,9 +177,10 @@ __device__ __forceinline__ void face_add(DFAcc& s, int& nmask, float2 nb, uint8_
 // electrode terms.  rho is h^2 rho / eps0 in float (RHO = float) or rho in
 // float64 (RHO = double, scaled by h2e here).  Sums ||b||^2 and ||r||^2 into
 // sc[S_B2], sc[S_R2].  Loads as in the other stencil kernels (column, y
-// neighbours, x from the adjacent lanes).
+// neighbours, x from the adjacent lanes).  Issue-bound (the pair
+// arithmetic): registers capped for eight blocks per SM.
 template <class RHO>
-__global__ void __launch_bounds__(BX * BY) k_mx_resid(const RHO* __restrict__ rho, double h2e,
+__global__ void __launch_bounds__(BX * BY, 8) k_mx_resid(const RHO* __restrict__ rho, double h2e,
                                                       const uint8_t* __restrict__ mask,
                                                       const float* __restrict__ phi_hi,
                                                       const float* __restrict__ phi_lo, int nx, int ny, int nz,
@@ -393,7 +394,8 @@ __global__ void __launch_bounds__(BX * BY) k_mx_apply(const float* __restrict__ 
 __device__ __forceinline__ float4 ld4g(const float* p, int c) { return __ldg(reinterpret_cast<const float4*>(p + c)); }
 __device__ __forceinline__ float f4c(const float4& v, int e) { return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w)); }
 
-__global__ void __launch_bounds__(BX * BY) k_mx_apply4(const float* __restrict__ z, const float* __restrict__ r,
+// Registers capped for six blocks per SM (latency-bound: more warps in flight).
+__global__ void __launch_bounds__(BX * BY, 6) k_mx_apply4(const float* __restrict__ z, const float* __restrict__ r,
                                                        const float* __restrict__ q_prev, float* __restrict__ w,
                                                        const uint8_t* __restrict__ mask, int nx, int ny, int nz,
                                                        int first, double* part, unsigned* ctr, double* sc) {
@@ -531,8 +533,8 @@ __global__ void __launch_bounds__(kFlatBlock) k_mx_extrapolate(const float* __re
 // out_hi set, also writes phi + delta there in the pair format.  delta may
 // be null, and is ignored when the device-driven loop state L (optional)
 // says no iteration ran since the last refinement.  E4 (if set) gets one
-// 16-byte store per cell.
-__global__ void __launch_bounds__(BX * BY) k_mx_grad(const float* __restrict__ hi, const float* __restrict__ lo,
+// 16-byte store per cell.  Registers capped for ten blocks per SM.
+__global__ void __launch_bounds__(BX * BY, 10) k_mx_grad(const float* __restrict__ hi, const float* __restrict__ lo,
                                                      const float* __restrict__ dl, float* __restrict__ out_hi,
                                                      float* __restrict__ out_lo, int nx, int ny, int nz, float inv2h,
                                                      MxBoundary bc, float* __restrict__ Ex, float* __restrict__ Ey,
