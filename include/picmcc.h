@@ -510,6 +510,24 @@ size_t mlp_workspace_bytes(int n_max);
 int mlp_forward(const float *params, const float *x, float *y, long long n, void *d_workspace,
                 size_t workspace_bytes, pic_stream_t stream);
 
+/* Folds the caller's standardizations into the parameters (Sec. 2.2.4 data:
+ * the network maps standardized inputs to standardized targets): out holds
+ * the parameters of the same network taking raw inputs x and giving raw
+ * targets, W1'[o][i] = W1[o][i] / x_scale[i], b1'[o] = b1[o] - sum_i W1[o][i]
+ * x_mean[i] / x_scale[i], W3'[o][j] = W3[o][j] y_scale[o], b3'[o] = b3[o]
+ * y_scale[o] + y_mean[o] (W2, b2 copied), in float64 arithmetic rounded to
+ * float once.  params, out: device float32 [MLP_NPARAMS], distinct; the
+ * means and scales: host arrays.  Errors: PIC_ERR_ARG (null or aliased
+ * pointers, a zero or non-finite scale, a non-finite mean). */
+int mlp_fold_standardization(const float *params, const double x_mean[2], const double x_scale[2],
+                             const double y_mean[6], const double y_scale[6], float *out, pic_stream_t stream);
+
+/* The network's raw inputs for transport-data queries: x[i] = (log10 EN_Td[i],
+ * f_o2[i]) as float32 (the logarithm of EN_Td rounded to float, in float32
+ * arithmetic).  EN_Td (Td), f_o2: device float64 [n]; x: device
+ * float32 [n][2].  Errors: PIC_ERR_ARG (n < 0, null pointers with n > 0). */
+int mlp_features(const double *EN_Td, const double *f_o2, float *x, long long n, pic_stream_t stream);
+
 /* The same with the kernel chosen: variant 0 = tcgen05 (as mlp_forward),
  * 1 = warp-level mma.sync (the pre-Blackwell tensor-core path, kept for
  * comparison).  If an internal wait on the tensor cores expires (it should

@@ -13,6 +13,7 @@
 // Parameters (float32, one vector): W1[128][2], b1[128], W2[128][128], b2[128],
 // W3[6][128], b3[6]; W[o][i] multiplies input i of unit o.
 #include <cuda_bf16.h>
+#include <math.h>
 #include <stdint.h>
 
 #include "common.cuh"
@@ -692,6 +693,40 @@ __global__ void __launch_bounds__(kTcThreads) k_infer_tc(const float* __restrict
     }
 }
 
+// ------------------------------------------------------------------ standardization
+// The caller's affine standardizations folded into the parameters (one
+// thread per parameter, float64 arithmetic rounded once): inputs x_std =
+// (x - xm) / xs enter layer 1, outputs y = y_std ys + ym leave layer 3.
+struct Affine {
+    double xm[NI], xs[NI], ym[NO], ys[NO];
+};
+__global__ void k_fold(const float* __restrict__ th, Affine a, float* __restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= NP) return;
+    double v = (double)th[k];
+    if (k < OFF_B1) {
+        v /= a.xs[k % NI];
+    } else if (k < OFF_W2) {
+        const int o = k - OFF_B1;
+        for (int i = 0; i < NI; ++i) v -= (double)th[OFF_W1 + o * NI + i] * a.xm[i] / a.xs[i];
+    } else if (k >= OFF_W3 && k < OFF_B3) {
+        v *= a.ys[(k - OFF_W3) / NH];
+    } else if (k >= OFF_B3) {
+        const int o = k - OFF_B3;
+        v = v * a.ys[o] + a.ym[o];
+    }
+    out[k] = (float)v;
+}
+
+// The network's inputs of transport-data queries: log10(E/N in Td) and the
+// O2 fraction, in float32 (the network's input precision; a float64
+// logarithm would run on this GPU's slow float64 units).
+__global__ void k_features(const double* __restrict__ en, const double* __restrict__ f, float* __restrict__ x,
+                           long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        reinterpret_cast<float2*>(x)[i] = make_float2(log10f((float)en[i]), (float)f[i]);
+}
+
 }  // namespace mlp
 
 // ------------------------------------------------------------------ C ABI
@@ -809,6 +844,34 @@ extern "C" int mlp_forward_variant(const float* params, const float* x, float* y
         if (blocks * kInfWarps > tiles) blocks = (tiles + kInfWarps - 1) / kInfWarps;
         k_infer<<<(unsigned)blocks, kInfWarps * 32, smem, s>>>(params, w.w2b, x, y, n);
     }
+    return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ERR_CUDA;
+}
+
+extern "C" int mlp_fold_standardization(const float* params, const double x_mean[2], const double x_scale[2],
+                                        const double y_mean[6], const double y_scale[6], float* out,
+                                        pic_stream_t stream) {
+    if (!params || !out || params == out || !x_mean || !x_scale || !y_mean || !y_scale) return PIC_ERR_ARG;
+    mlp::Affine a;
+    for (int i = 0; i < mlp::NI; ++i) {
+        if (!(x_scale[i] != 0.0) || !isfinite(x_scale[i]) || !isfinite(x_mean[i])) return PIC_ERR_ARG;
+        a.xm[i] = x_mean[i];
+        a.xs[i] = x_scale[i];
+    }
+    for (int o = 0; o < mlp::NO; ++o) {
+        if (!isfinite(y_scale[o]) || !isfinite(y_mean[o])) return PIC_ERR_ARG;
+        a.ym[o] = y_mean[o];
+        a.ys[o] = y_scale[o];
+    }
+    mlp::k_fold<<<(mlp::NP + 255) / 256, 256, 0, (cudaStream_t)stream>>>(params, a, out);
+    return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ERR_CUDA;
+}
+
+extern "C" int mlp_features(const double* EN_Td, const double* f_o2, float* x, long long n, pic_stream_t stream) {
+    if (n < 0 || (n > 0 && (!EN_Td || !f_o2 || !x))) return PIC_ERR_ARG;
+    if (n == 0) return PIC_OK;
+    long long g = (n + 255) / 256;
+    if (g > 65535) g = 65535;
+    mlp::k_features<<<(unsigned)g, 256, 0, (cudaStream_t)stream>>>(EN_Td, f_o2, x, n);
     return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ERR_CUDA;
 }
 

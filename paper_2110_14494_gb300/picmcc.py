@@ -107,6 +107,7 @@ EXPORTS = ("pic_workspace_bytes", "pic_init", "pic_destroy", "pic_last_error", "
            "pic_profile", "pic_upload", "pic_download", "pic_set_poisson", "pic_get_field", "pic_get_deposit", "pic_set_multigrid",
            "poisson_workspace_bytes", "poisson_solve", "poisson_solve_noalloc", "swarm_workspace_bytes",
            "swarm_run", "swarm_autotune", "mlp_workspace_bytes", "mlp_forward", "mlp_forward_variant", "mlp_loss_grad",
+           "mlp_fold_standardization", "mlp_features",
            "mlp_train", "poisson_axi_workspace_bytes", "poisson_axi_solve")
 
 _lib = None
@@ -168,6 +169,8 @@ def lib():
     L.mlp_workspace_bytes.argtypes = [C.c_int]
     L.mlp_workspace_bytes.restype = C.c_size_t
     L.mlp_forward.argtypes = [VP, VP, VP, C.c_longlong, VP, C.c_size_t, VP]
+    L.mlp_fold_standardization.argtypes = [VP, PD, PD, PD, PD, VP, VP]
+    L.mlp_features.argtypes = [VP, VP, VP, C.c_longlong, VP]
     L.mlp_forward_variant.argtypes = [VP, VP, VP, C.c_longlong, C.c_int, VP, C.c_size_t, VP]
     L.mlp_loss_grad.argtypes = [VP, VP, VP, C.c_int, VP, VP, VP, C.c_size_t, VP]
     L.mlp_train.argtypes = [VP, VP, VP, C.c_int, VP, VP, C.c_int, C.c_int, C.c_float, C.c_float, C.c_float,
@@ -538,6 +541,28 @@ def mlp_forward(params, x, y=None, stream=None, variant=0):
     _check(lib().mlp_forward_variant(_ptr(params), _ptr(x), _ptr(y), n, int(variant), C.c_void_p(ptr),
                                      lib().mlp_workspace_bytes(0), _stream(stream)), None, "mlp_forward")
     return y
+
+
+def mlp_fold_standardization(params, x_mean, x_scale, y_mean, y_scale, out=None, stream=None):
+    """Parameters of the network on raw inputs and targets (mlp_fold_standardization)."""
+    import torch
+    if out is None:
+        out = torch.empty_like(params)
+    arr = lambda v, m: (C.c_double * m)(*[float(a) for a in np.asarray(v, np.float64).ravel()[:m]])
+    _check(lib().mlp_fold_standardization(_ptr(params), arr(x_mean, MLP_NI), arr(x_scale, MLP_NI),
+                                          arr(y_mean, MLP_NO), arr(y_scale, MLP_NO), _ptr(out), _stream(stream)),
+           None, "mlp_fold_standardization")
+    return out
+
+
+def mlp_features(EN_Td, f_o2, x=None, stream=None):
+    """Network inputs (log10 E/N, O2 fraction) as float32 [n][2] from float64 CUDA tensors."""
+    import torch
+    n = int(EN_Td.shape[0])
+    if x is None:
+        x = torch.empty((n, MLP_NI), dtype=torch.float32, device=EN_Td.device)
+    _check(lib().mlp_features(_ptr(EN_Td), _ptr(f_o2), _ptr(x), n, _stream(stream)), None, "mlp_features")
+    return x
 
 
 def mlp_loss_grad(params, x, t, stream=None):

@@ -79,6 +79,7 @@ class Surrogate:
         self.m = torch.zeros_like(self.params)
         self.v = torch.zeros_like(self.params)
         self.step = 0
+        self._folded, self._folded_step = None, -1
         self.x = torch.as_tensor(self.sx.fwd(x).astype(np.float32)).cuda()
         self.y = torch.as_tensor(self.sy.fwd(y).astype(np.float32)).cuda()
 
@@ -102,11 +103,27 @@ class Surrogate:
         """Standardized outputs for standardized device inputs (no host copies)."""
         return P.mlp_forward(self.params, xs_dev)
 
+    def folded(self):
+        """Parameters that take raw inputs and give raw log targets
+        (mlp_fold_standardization), refolded after every fit."""
+        if self._folded is None or self._folded_step != self.step:
+            self._folded = P.mlp_fold_standardization(self.params, self.sx.mean, self.sx.std, self.sy.mean,
+                                                      self.sy.std)
+            self._folded_step = self.step
+        return self._folded
+
+    def predict_dev(self, EN_dev, f_dev):
+        """Log targets [n][6] on the device for float64 CUDA tensors of E/N (Td)
+        and O2 fraction: the feature kernel, then the network with the
+        standardizations folded in."""
+        return P.mlp_forward(self.folded(), P.mlp_features(EN_dev, f_dev))
+
     def predict(self, EN_Td, f_o2) -> np.ndarray:
-        """Log targets at raw inputs."""
+        """Log targets at raw inputs (host arrays in, host array out)."""
         import torch
-        xs = torch.as_tensor(self.sx.fwd(features(EN_Td, f_o2)).astype(np.float32)).cuda()
-        return self.sy.inv(self.predict_std(xs).cpu().numpy().astype(np.float64))
+        EN = torch.as_tensor(np.ascontiguousarray(EN_Td, np.float64)).cuda()
+        f = torch.as_tensor(np.ascontiguousarray(np.broadcast_to(np.asarray(f_o2, np.float64), EN.shape))).cuda()
+        return self.predict_dev(EN, f).cpu().numpy().astype(np.float64)
 
 
 def table_interp(EN_grid, f_grid, table: np.ndarray, EN_Td, f_o2) -> np.ndarray:

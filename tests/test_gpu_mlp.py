@@ -211,6 +211,47 @@ def test_inference_on_many_points_sampled(variant):
     assert np.isfinite(y).all()
 
 
+def test_folded_standardization_and_features():
+    """mlp_features and mlp_fold_standardization: the feature kernel gives
+    (log10 E/N, f) as float32; the folded parameters are the float64 fold
+    rounded once; the network with them on raw inputs gives the raw targets
+    of the network on standardized inputs, within the rounding model of the
+    forward pass (scaled by the target scales) plus the float32 rounding of
+    the standardized inputs."""
+    from paper_2110_14494_gb300 import mlp_features, mlp_fold_standardization, mlp_forward
+    th, _, _ = _problem(1, seed=6)
+    r = np.random.default_rng(9)
+    n = 5000
+    en = 10.0 * 100.0 ** r.random(n)
+    f = r.uniform(0.1, 0.3, n)
+    x = mlp_features(torch.as_tensor(en).cuda(), torch.as_tensor(f).cuda()).cpu().numpy().astype(np.float64)
+    ref_x = np.stack([np.log10(en), f], 1)
+    # float32 logarithm of E/N rounded to float: within 3 float32 spacings (rounding of E/N, log10f's own error)
+    assert np.all(np.abs(x - ref_x) <= 3 * np.spacing(np.abs(ref_x).astype(np.float32)).astype(np.float64))
+    xm, xs = np.array([2.0, 0.2]), np.array([0.57, 0.058])
+    ym, ys = r.normal(-40.0, 10.0, 6), r.uniform(0.5, 4.0, 6)
+    folded = mlp_fold_standardization(_dev(th), xm, xs, ym, ys).cpu().numpy().astype(np.float64)
+    ref = th.copy()
+    W1 = th[M.OFF["W1"]:M.OFF["b1"]].reshape(128, 2)
+    ref[M.OFF["W1"]:M.OFF["b1"]] = (W1 / xs).ravel()
+    b1 = th[M.OFF["b1"]:M.OFF["W2"]].copy()
+    for i in range(2):
+        b1 = b1 - W1[:, i] * xm[i] / xs[i]
+    ref[M.OFF["b1"]:M.OFF["W2"]] = b1
+    W3 = th[M.OFF["W3"]:M.OFF["b3"]].reshape(6, 128)
+    ref[M.OFF["W3"]:M.OFF["b3"]] = (W3 * ys[:, None]).ravel()
+    ref[M.OFF["b3"]:] = th[M.OFF["b3"]:] * ys + ym
+    # float64 fold rounded once to float32: within one float32 spacing of the float64 values
+    assert np.all(np.abs(folded - ref) <= np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64))
+    y = mlp_forward(_dev(folded), _dev(x), variant=0).cpu().numpy().astype(np.float64)
+    xstd = (x - xm) / xs
+    yo = M.forward(th, xstd) * ys + ym
+    # rounding model of the forward pass on the standardized inputs, scaled by the target scales, plus the
+    # float32 rounding of the folded layers (inputs up to |x / xs| ~ 6, outputs up to |ym| ~ 60)
+    bound = _fwd_bound(th, xstd, 0) * ys + 64 * 2.0 ** -24 * (np.abs(ym) + 10.0)
+    assert np.all(np.abs(y - yo) <= bound), float(np.max(np.abs(y - yo) / bound))
+
+
 def test_surrogate_gain_over_swarms():
     """The trained surrogate against the method without it.  Training table:
     batched swarms at 64 E/N values (20-800 Td) x 4 O2 fractions; held out: 12
