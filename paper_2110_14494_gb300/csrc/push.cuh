@@ -413,13 +413,20 @@ __device__ __forceinline__ int select_process(const PushArgs<T>& A, const Rates<
         const T tot = t0 + f * (t1 - t0);
         if (target >= tot) return -1;
     }
+    // the first k with target < sum_{i<=k} nu_i: every process is visited by
+    // every lane (the same sums in the same order), so the lanes of a warp
+    // stay together whichever process they pick
     T cum = (T)0;
-    for (int k = 0; k < A.n_proc; ++k) {
-        const T a = __ldg(r0 + k), b = __ldg(r1 + k);
-        cum += a + f * (b - a);
-        if (target < cum) return k;
+    int sel = -1;
+#pragma unroll
+    for (int k = 0; k < kTableStride - 1; ++k) {
+        if (k < A.n_proc) {
+            const T a = __ldg(r0 + k), b = __ldg(r1 + k);
+            cum += a + f * (b - a);
+            sel = (sel < 0 && target < cum) ? k : sel;
+        }
     }
-    return -1;
+    return sel;
 }
 
 // ------------------------------------------------------------------ flight
@@ -531,16 +538,12 @@ __device__ __forceinline__ int event(const PushArgs<T>& A, const Rates<T>& R, co
     T n[3];
     iso_dir(unif<T>(r.z), unif<T>(r.w), n);
     // energy after the collision: elastic recoil with cos(chi) = n_old . n_new,
-    // excitation loss, or half of what ionization leaves
-    T e2;
-    if (kind == PIC_PROC_ELASTIC) {
-        const T cchi = EvArith<T>::cosine(v[0] * n[0] + v[1] * n[1] + v[2] * n[2], v2);
-        e2 = dmax(e * ((T)1 - (T)2 * ps->mratio[p] * ((T)1 - cchi)), (T)0);
-    } else if (kind == PIC_PROC_EXCITATION) {
-        e2 = dmax(e - ps->thr[p], (T)0);
-    } else {
-        e2 = (T)0.5 * dmax(e - ps->thr[p], (T)0);
-    }
+    // excitation loss, or half of what ionization leaves (all three formed,
+    // one kept: no branch on the process kind)
+    const T cchi = EvArith<T>::cosine(v[0] * n[0] + v[1] * n[1] + v[2] * n[2], v2);
+    const T e_el = dmax(e * ((T)1 - (T)2 * ps->mratio[p] * ((T)1 - cchi)), (T)0);
+    const T e_in = dmax(e - ps->thr[p], (T)0);
+    const T e2 = kind == PIC_PROC_ELASTIC ? e_el : (kind == PIC_PROC_EXCITATION ? e_in : (T)0.5 * e_in);
     const T sp2 = Arith<T>::speed(e2);
     v[0] = sp2 * n[0]; v[1] = sp2 * n[1]; v[2] = sp2 * n[2];
     if (kind == PIC_PROC_IONIZATION) {
