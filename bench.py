@@ -38,13 +38,13 @@ WORKLOAD = "streamer-128^3-fp32"
 # DRAM bytes (read + write) per particle-update of the collision kernel in this workload's steady state, from
 # the ncu capture summarised in profiles/k_push_streamer128.md (39.6 MB per launch of ~7.9e5 updates); scaled to
 # the run's mean launch for roofline.traffic.  Only valid for the kernel build and workload it was taken on.
-PUSH_DRAM_BYTES_PER_UPDATE = 49.9
+PUSH_DRAM_BYTES_PER_UPDATE = 51.4
 # The collision kernels (parents and children) issue about this many warp
 # instructions per collision draw (a candidate event, or the last draw that
 # ends the step): ncu smsp__inst_executed.sum over three steady-state steps /
 # (updates x draws per update), from profiles/k_push_streamer128.md
 # (4.243e8 / (2.380e6 x 9.311)).
-PUSH_WARP_INST_PER_DRAW = 19.15
+PUSH_WARP_INST_PER_DRAW = 17.72
 ISSUE_SLOTS_PER_SM = 4   # warp schedulers per SM, one warp instruction each per clock
 
 
@@ -807,8 +807,9 @@ def main():
         n = ctx.count()
         capn = int(ctx.cfg.capacity)
         dt_ = torch.float32 if args.precision == 32 else torch.float64
-        host = [torch.empty(capn, dtype=dt_, pin_memory=True) for _ in range(10)] + \
-            [torch.empty(capn, dtype=torch.int64, pin_memory=True)]
+        # the ten real arrays as rows of one pinned block (one pitched copy each way), the ids apart
+        block = torch.empty((10, capn), dtype=dt_, pin_memory=True)
+        host = [block[i] for i in range(10)] + [torch.empty(capn, dtype=torch.int64, pin_memory=True)]
         ctx.download(host, capn)
         ee = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
         ue0 = ctx.progress()[0]

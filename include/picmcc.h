@@ -321,7 +321,10 @@ int pic_profile(pic_ctx *ctx, int enable, pic_profile_times *out);
  * keep them unchanged until the stream has passed the call.  pic_download
  * writes the current set (including any not-yet-compacted zero-weight slots,
  * which callers skip) and its size, and synchronises; PIC_ERR_CAPACITY (with
- * *n_out set, nothing copied) when the set is larger than cap. */
+ * *n_out set, nothing copied) when the set is larger than cap.  When
+ * arrays[0..9] lie at one constant pitch (one host block, rows at least n
+ * elements apart) they move in one pitched copy, else in ten; the ids
+ * always in one more. */
 int pic_upload(pic_ctx *ctx, long long n, const void *const *arrays, int accel_valid);
 int pic_download(pic_ctx *ctx, void *const *arrays, long long cap, long long *n_out);
 

@@ -2924,14 +2924,36 @@ extern "C" int pic_profile(pic_ctx* c, int enable, pic_profile_times* out) {
     return PIC_OK;
 }
 
+// Host arrays 0..9 laid out at one constant pitch of at least `row` bytes
+// (one host block): returns the pitch, else 0.
+static size_t host_pitch(const void* const* arrays, size_t row) {
+    const char* a0 = static_cast<const char*>(arrays[0]);
+    if (!a0 || !arrays[1]) return 0;
+    const ptrdiff_t d = static_cast<const char*>(arrays[1]) - a0;
+    if (d < (ptrdiff_t)row) return 0;
+    for (int f = 2; f < 10; ++f)
+        if (!arrays[f] || static_cast<const char*>(arrays[f]) - a0 != (ptrdiff_t)f * d) return 0;
+    return (size_t)d;
+}
+
 extern "C" int pic_upload(pic_ctx* c, long long n, const void* const* arrays, int accel_valid) {
     if (!c || n < 0 || (n > 0 && !arrays)) return PIC_ERR_ARG;
     if (n > c->cfg.capacity) return c->fail(PIC_ERR_CAPACITY, "more particles than capacity");
     c->cur = 0;
     const size_t R = real_size(c->prec), cap = (size_t)c->cfg.capacity;
     char* base = c->ws + c->L.buf[0];
-    for (int f = 0; f < 11 && n > 0; ++f) {
+    for (int f = 0; f < 11 && n > 0; ++f)
         if (!arrays[f]) return PIC_ERR_ARG;
+    // the ten real arrays in one pitched copy when the host keeps them in one block
+    const size_t hp = n > 0 ? host_pitch(arrays, (size_t)n * R) : 0;
+    if (hp) {
+        cudaError_t e = cudaMemcpy2DAsync(base, al256(cap * R), arrays[0], hp, (size_t)n * R, 10,
+                                          cudaMemcpyHostToDevice, c->s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(base + 10 * al256(cap * R), arrays[10], (size_t)n * 8, cudaMemcpyHostToDevice, c->s);
+        if (e != cudaSuccess) return c->cuda_fail(e, "upload");
+    }
+    for (int f = 0; f < 11 && n > 0 && !hp; ++f) {
         cudaError_t e = cudaMemcpyAsync(base + f * al256(cap * R), arrays[f], n * (f < 10 ? R : 8),
                                         cudaMemcpyHostToDevice, c->s);
         if (e != cudaSuccess) return c->cuda_fail(e, "upload");
@@ -2947,6 +2969,14 @@ extern "C" int pic_upload(pic_ctx* c, long long n, const void* const* arrays, in
 static cudaError_t download_async(pic_ctx* c, void* const* arrays, long long n) {
     const size_t R = real_size(c->prec), capd = (size_t)c->cfg.capacity;
     char* base = c->ws + c->L.buf[c->cur];
+    const size_t hp = n > 0 ? host_pitch(arrays, (size_t)n * R) : 0;
+    if (hp) {  // the ten real arrays in one pitched copy (one host block)
+        cudaError_t e = cudaMemcpy2DAsync(arrays[0], hp, base, al256(capd * R), (size_t)n * R, 10,
+                                          cudaMemcpyDeviceToHost, c->s);
+        if (e == cudaSuccess && arrays[10])
+            e = cudaMemcpyAsync(arrays[10], base + 10 * al256(capd * R), (size_t)n * 8, cudaMemcpyDeviceToHost, c->s);
+        return e;
+    }
     for (int f = 0; f < 11 && n > 0; ++f) {
         if (!arrays[f]) continue;
         cudaError_t e = cudaMemcpyAsync(arrays[f], base + f * al256(capd * R), n * (f < 10 ? R : 8),

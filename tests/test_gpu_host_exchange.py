@@ -40,24 +40,40 @@ def _native(p, prec, cap):
     return arrs
 
 
+def _native_block(p, prec, cap):
+    """The same 11 arrays with the ten real ones as rows of one host block
+    (one pitched copy each way)."""
+    dt = np.float32 if prec == 32 else np.float64
+    block = np.zeros((10, cap), dt)
+    arrs = [block[i] for i in range(10)] + [np.zeros(cap, np.int64)]
+    n = len(p["x"])
+    for a, k in zip(arrs, FIELDS):
+        a[:n] = p[k]
+    arrs[10][:n] = p["id"].astype(np.int64)
+    return arrs
+
+
 def _as_dict(arrs, n):
     d = {k: arrs[i][:n].astype(np.float64) for i, k in enumerate(FIELDS)}
     d["id"] = arrs[10][:n].astype(np.uint64)
     return d
 
 
-@pytest.mark.parametrize("prec", [32, 64])
-def test_upload_download_round_trip_is_exact(prec):
+@pytest.mark.parametrize("prec,block", [(32, False), (64, False), (32, True), (64, True)])
+def test_upload_download_round_trip_is_exact(prec, block):
+    """Separate host arrays (eleven copies each way) and the real arrays as
+    rows of one host block (a pitched copy), in and out in both layouts."""
     p0 = W.random_particles(5000, GRID, 17, vmax=2e6, w_range=(1.0, 9.0))
     cap = 8000
     ctx = _ctx(prec, cap)
-    up = _native(p0, prec, cap)
+    up = (_native_block if block else _native)(p0, prec, cap)
     ctx.upload(up, 5000, accel_valid=True)
-    back = [np.zeros_like(a) for a in up]
-    n = ctx.download(back, cap)
-    assert n == 5000
-    for a, b in zip(up, back):
-        assert np.array_equal(a[:n], b[:n])
+    for back in ([np.zeros_like(a) for a in up], _native_block({k: np.zeros(0) for k in FIELDS + ("id",)}, prec,
+                                                               cap)):
+        n = ctx.download(back, cap)
+        assert n == 5000
+        for a, b in zip(up, back):
+            assert np.array_equal(a[:n], b[:n])
     # the double-precision read-back sees the same particles
     g = by_id(ctx.get_particles())
     ref = by_id(_as_dict(up, n))
