@@ -471,7 +471,9 @@ struct TailSmem {
     float* e;
     float* g;
     uint8_t* m;
+    float* rdiag;  // [16]: inv_diag(d) for the integer diagonals d = 0..15
 };
+__host__ __device__ constexpr size_t tail_smem_bytes(int cells) { return (((size_t)cells * (2 * sizeof(float) + 1) + 15) & ~(size_t)15) + 16 * sizeof(float); }
 
 // Thread decomposition of a phase: thread owns (tx + a sx, ty + b sy, tz + c sz).
 struct Dec {
@@ -506,7 +508,8 @@ __device__ void tail_half(const TailLevels& T, const TailSmem& S, int l, int col
                     float diag;
                     const float s = nb_sum_e(e, i, j, k, nx, ny, nz, c, diag);
                     if (!m[c]) {
-                        const float v = (g[c] + s) * inv_diag(diag);
+                        // the diagonal is an integer (2..8): its reciprocal from the table (the same values)
+                        const float v = (g[c] + s) * S.rdiag[(int)diag];
                         e[c] = omega != 1.0f ? fmaf(omega, v - e[c], e[c]) : v;
                     }
                 }
@@ -593,6 +596,8 @@ __global__ void __launch_bounds__(1024) k_tail_vcycle(const TailLevels T) {
     S.e = reinterpret_cast<float*>(tail_raw);
     S.g = S.e + T.total;
     S.m = reinterpret_cast<uint8_t*>(S.g + T.total);
+    S.rdiag = reinterpret_cast<float*>(tail_raw + (tail_smem_bytes(T.total) - 16 * sizeof(float)));
+    if (threadIdx.x < 16) S.rdiag[threadIdx.x] = inv_diag((float)threadIdx.x);
     {
         // global loads in batches of kTailLoad per thread, issued before
         // their stores (the first level has at most kTailCells cells)
@@ -818,7 +823,7 @@ void MG::vcycle(cudaStream_t s) {
     T.coarse = coarse_sweeps;
     T.omega = omega;
     T.total = off;
-    const size_t smem = (size_t)off * (2 * sizeof(float) + 1);
+    const size_t smem = tail_smem_bytes(off);
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_tail_vcycle, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     launch_pdl(k_tail_vcycle, dim3(1), dim3(1024), smem, s, T);
     for (int l = t - 1; l >= 0; --l) {
