@@ -810,6 +810,7 @@ def main():
         # the ten real arrays as rows of one pinned block (one pitched copy each way), the ids apart
         block = torch.empty((10, capn), dtype=dt_, pin_memory=True)
         host = [block[i] for i in range(10)] + [torch.empty(capn, dtype=torch.int64, pin_memory=True)]
+        host = ctx.host_set(host, capn)  # checked once for the repeated exchanges
         ctx.download(host, capn)
         ee = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
         ue0 = ctx.progress()[0]

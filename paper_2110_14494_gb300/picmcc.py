@@ -195,6 +195,17 @@ def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
+class HostSet:
+    """Host arrays of pic_upload / pic_download checked once (see
+    _host_arrays): the pointers are kept with references to the arrays."""
+
+    def __init__(self, arrays, capacity: int, precision: int):
+        self.ptrs = _host_arrays(arrays, capacity, precision, "host set")
+        self.capacity = int(capacity)
+        self.precision = int(precision)
+        self._keep = list(arrays)
+
+
 def _stream(stream=None):
     import torch
     s = torch.cuda.current_stream() if stream is None else stream
@@ -408,13 +419,28 @@ class PicContext:
         _check(lib().pic_profile(self.h, int(enable), C.byref(t)), self.h, "pic_profile")
         return {f[0]: getattr(t, f[0]) for f in pic_profile_times._fields_}
 
+    def host_set(self, arrays, capacity):
+        """The 11 host arrays validated once (type, contiguity, at least
+        `capacity` entries) for repeated upload / download calls."""
+        return HostSet(arrays, capacity, self.cfg.precision)
+
     def upload(self, arrays, n, accel_valid=True):
-        """arrays: 11 host tensors/arrays (pinned for asynchronous copies) in native precision."""
-        ptrs = _host_arrays(arrays, n, self.cfg.precision, "pic_upload")
+        """arrays: 11 host tensors/arrays (pinned for asynchronous copies) in native precision, or a HostSet."""
+        if isinstance(arrays, HostSet):
+            if arrays.precision != self.cfg.precision or not 0 <= n <= arrays.capacity:
+                raise ValueError("pic_upload: host set of another precision or smaller than n")
+            ptrs = arrays.ptrs
+        else:
+            ptrs = _host_arrays(arrays, n, self.cfg.precision, "pic_upload")
         _check(lib().pic_upload(self.h, n, ptrs, int(accel_valid)), self.h, "pic_upload")
 
-    def download(self, arrays, cap) -> int:
-        ptrs = _host_arrays(arrays, cap, self.cfg.precision, "pic_download")
+    def download(self, arrays, cap=None) -> int:
+        if isinstance(arrays, HostSet):
+            if arrays.precision != self.cfg.precision:
+                raise ValueError("pic_download: host set of another precision")
+            ptrs, cap = arrays.ptrs, arrays.capacity if cap is None else min(cap, arrays.capacity)
+        else:
+            ptrs = _host_arrays(arrays, cap, self.cfg.precision, "pic_download")
         n = C.c_longlong()
         _check(lib().pic_download(self.h, ptrs, cap, C.byref(n)), self.h, "pic_download")
         return n.value

@@ -153,3 +153,16 @@ def test_noalloc_scratch_limit(L):
             pc = P.poisson_config(n, n, n, 1e-5, 0.0, 1.0, 1.0, prec)
             b = L.poisson_workspace_bytes(C.byref(pc))
             assert b > 0 and (b <= 32 << 20) == fits, (prec, n, b)
+
+
+def test_host_set_is_checked_once():
+    """HostSet validates the 11 host arrays once (type, contiguity, capacity)
+    for repeated pic_upload / pic_download calls."""
+    from paper_2110_14494_gb300 import picmcc as P
+    good = [np.zeros(100, np.float32) for _ in range(10)] + [np.zeros(100, np.int64)]
+    hs = P.HostSet(good, 100, 32)
+    assert hs.capacity == 100 and hs.precision == 32 and len(hs.ptrs) == 11
+    with pytest.raises(ValueError):
+        P.HostSet(good, 101, 32)   # arrays shorter than the capacity
+    with pytest.raises(ValueError):
+        P.HostSet(good, 100, 64)   # float32 arrays for a float64 set

@@ -74,6 +74,13 @@ def test_upload_download_round_trip_is_exact(prec, block):
         assert n == 5000
         for a, b in zip(up, back):
             assert np.array_equal(a[:n], b[:n])
+    # the same through host sets checked once
+    hs_up, back = ctx.host_set(up, cap), [np.zeros_like(a) for a in up]
+    hs_back = ctx.host_set(back, cap)
+    ctx.upload(hs_up, 5000, accel_valid=True)
+    assert ctx.download(hs_back) == 5000
+    for a, b in zip(up, back):
+        assert np.array_equal(a[:5000], b[:5000])
     # the double-precision read-back sees the same particles
     g = by_id(ctx.get_particles())
     ref = by_id(_as_dict(up, n))
