@@ -62,3 +62,32 @@ def test_fixed_to_rho():
     qn = np.array([0, 0, int(S) // 2], np.int64)
     rho = O.fixed_to_rho(dV, qe, qp, qn)
     assert np.allclose(rho, O.Q_E / dV * np.array([1.0, 0.0, -2.5]), rtol=1e-15)
+
+
+def test_binary32_corner_weights_against_float64():
+    """The error the single-precision path's binary32 deposit (Sec. 2.1.3)
+    makes against the float64 CIC, stated per particle: the cell coordinate
+    (x - ox) / dx of a grid of n cells is formed in binary32 with an absolute
+    error of at most ~1.5 n 2^-24, which each of a corner's three factors
+    carries, so every corner weight lies within 3 (1.5 n 2^-24 + 2^-23) of the
+    particle's weight (measured: at most 1.2e-5, median 2.3e-6 at n = 128);
+    the charge is conserved exactly in both (the eighth corner takes the
+    remainder) and totals agree for weights held in float32."""
+    n = 128
+    grid = W.grid_spec(n, n, n, 20e-6)
+    p0 = W.random_particles(400, grid, 5, w_range=(1.0, 500.0))
+    p = dict(p0)
+    for k in ("x", "y", "z", "w"):
+        p[k] = np.asarray(p0[k], np.float32).astype(np.float64)  # the state the float32 path holds
+    m32 = O.Model(W.zero_gas(), 1e-12, 1, 32, grid)
+    m64 = O.Model(W.zero_gas(), 1e-12, 1, 64, grid)
+    bound = 3 * (1.5 * n * 2.0 ** -24 + 2.0 ** -23)
+    worst = 0.0
+    for i in range(len(p["x"])):
+        pi = {k: np.asarray(v[i:i + 1]) for k, v in p.items()}
+        a = O.deposit(m32, O.Particles(1, pi))
+        b = O.deposit(m64, O.Particles(1, pi))
+        assert int(a.sum()) == int(b.sum())
+        worst = max(worst, float(np.abs(a - b).max()) / (pi["w"][0] * S))
+    assert worst <= bound, (worst, bound)
+    assert worst > 0.0   # the binary32 path is not the float64 one
