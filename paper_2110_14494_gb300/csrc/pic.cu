@@ -21,6 +21,10 @@
 
 namespace pic {
 
+// A coupled solve's CG iteration after the first two takes a V(1,1)-cycle
+// when the relative residual is already within this factor of the target.
+constexpr double kLightRatio = 3.0;
+
 // ================================================================== scan
 // Exclusive prefix sum of n uint32 values into out[0..n]; out[n] = total.
 constexpr int kScanTile = 2048;
@@ -1304,6 +1308,7 @@ extern "C" int pic_init(const pic_config* cfg, void* d_ws, size_t ws_bytes, cons
             c->mg.carve(c->ws + L.mg, cfg->nx, cfg->ny, cfg->nz, c->prec == 32, false);
             c->mg.persistent = true;
             c->mg.min_cycles = 2;
+            c->mg.light_ratio = kLightRatio;
         }
     }
     *out = c;

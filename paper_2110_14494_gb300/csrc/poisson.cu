@@ -781,10 +781,11 @@ cudaError_t MG::build_masks(const uint8_t* mask, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// One V(pre, post)-cycle on A e0 = g0; e0 is overwritten.  Levels above the
+// One V(pre, post)-cycle on A e0 = g0 (light: V(light_pre, light_post)); e0 is overwritten.  Levels above the
 // tail run as separate kernels; the tail runs as one block.
-void MG::vcycle(cudaStream_t s) {
+void MG::vcycle(cudaStream_t s, bool light) {
     const int t = tail_level();
+    const int pre = light ? light_pre : this->pre, post = light ? light_post : this->post;
     // per level: pre-smoothing (the first sweep from zero is one kernel), restriction, prolongation,
     // post-smoothing; then the tail
     launches += (long long)t * ((pre > 0 ? 2 * pre - 1 : 0) + 2 * post + 2) + 1;
@@ -840,7 +841,7 @@ void MG::vcycle(cudaStream_t s) {
 void MG::iteration(cudaStream_t s, double* phi, const uint8_t* mk, bool first) {
     const int nx = lx[0], ny = ly[0], nz = lz[0];
     const int n = nx * ny * nz;
-    vcycle(s);
+    vcycle(s, false);
     k_dot2<<<grid_red(n), kBlk, 0, s>>>(e[0], r64, q64, n, norms, first ? 0 : 1);
     k_beta<<<1, 1, 0, s>>>(norms, first ? 1 : 0);
     k_update_p<<<grid_flat(n), kBlk, 0, s>>>(p64, e[0], n, norms);
@@ -855,7 +856,7 @@ void MG::release() {
         if (g_iter[q]) { cudaGraphExecDestroy(g_iter[q]); g_iter[q] = nullptr; }
     for (int q = 0; q < 3; ++q)
         if (cap_body[q]) { cudaStreamDestroy(cap_body[q]); cap_body[q] = nullptr; }
-    for (int q = 0; q < 3; ++q)
+    for (int q = 0; q < 5; ++q)
         if (g_mx[q]) { cudaGraphExecDestroy(g_mx[q]); g_mx[q] = nullptr; }
     if (cap_stream) { cudaStreamDestroy(cap_stream); cap_stream = nullptr; }
 }
@@ -953,10 +954,10 @@ int MG::mixed_min_cycles(int max_cycles) const {
     return m < max_cycles ? m : max_cycles;
 }
 
-void MG::iteration_mixed(cudaStream_t s, int it) {
+void MG::iteration_mixed(cudaStream_t s, int it, bool light) {
     const int nx = lx[0], ny = ly[0], nz = lz[0], n = nx * ny * nz;
     const int cur = it & 1, first = it == 0 ? 1 : 0;
-    vcycle(s);
+    vcycle(s, light);
     // w = A z goes to p32[cur] (the direction of two iterations ago, free
     // here), where the second kernel replaces it by the new direction
     if (nx % 4 == 0)
@@ -1027,7 +1028,10 @@ int MG::solve_mixed(const void* rho, bool rho64, const uint8_t* mask, float* phi
             it = 0;
             continue;
         }
-        const int gi = it == 0 ? 0 : 1 + (it & 1);
+        // an iteration after the untested ones whose residual is already within light_ratio of the target
+        // takes the lighter V-cycle (flexible CG admits a preconditioner that changes between iterations)
+        const bool light = light_ratio > 0.0 && cyc >= min_c && it > 0 && rn / bn <= light_ratio * rtol;
+        const int gi = it == 0 ? 0 : (light ? 3 : 1) + (it & 1);
         if (persistent) {
             if (!g_mx[gi]) {
                 if (!cap_stream && cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking) != cudaSuccess)
@@ -1036,7 +1040,7 @@ int MG::solve_mixed(const void* rho, bool rho64, const uint8_t* mask, float* phi
                 const long long l0 = launches;
                 if (cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
                     return PIC_ERR_CUDA;
-                iteration_mixed(cap_stream, it);
+                iteration_mixed(cap_stream, it, light);
                 if (cudaStreamEndCapture(cap_stream, &gr) != cudaSuccess) return PIC_ERR_CUDA;
                 if (cudaGraphInstantiate(&g_mx[gi], gr, 0) != cudaSuccess) { cudaGraphDestroy(gr); return PIC_ERR_CUDA; }
                 cudaGraphDestroy(gr);
@@ -1046,7 +1050,7 @@ int MG::solve_mixed(const void* rho, bool rho64, const uint8_t* mask, float* phi
             if (cudaGraphLaunch(g_mx[gi], s) != cudaSuccess) return PIC_ERR_CUDA;
             launches += graph_kernels_mx[gi];
         } else {
-            iteration_mixed(s, it);
+            iteration_mixed(s, it, light);
         }
         ++it;
         ++cyc;
@@ -1134,33 +1138,33 @@ int MG::capture_solve_mixed(cudaStream_t cs, const float* rho, float* phi_hi, fl
     if (cudaStreamBeginCaptureToGraph(cap_body[0], body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
         cudaSuccess)
         return PIC_ERR_CUDA;
-    k_mx_decide<<<1, 1, 0, cap_body[0]>>>(norms, loop, rtol, max_cycles, h_loop, h_branch);
-    cudaGraph_t br[4] = {nullptr, nullptr, nullptr, nullptr};
-    const cudaError_t e_sw = add_conditional(cap_body[0], h_branch, cudaGraphCondTypeSwitch, 4, br);
+    k_mx_decide<<<1, 1, 0, cap_body[0]>>>(norms, loop, rtol, max_cycles, light_ratio, h_loop, h_branch);
+    cudaGraph_t br[kMxBranches] = {};
+    const cudaError_t e_sw = add_conditional(cap_body[0], h_branch, cudaGraphCondTypeSwitch, kMxBranches, br);
     if (end_body_capture(cap_body[0]) != cudaSuccess || e_sw != cudaSuccess) return PIC_ERR_CUDA;
-    // branches: iterations with index 0 (first), 2 (even) and 1 (odd), then the refinement
-    const int its[3] = {0, 2, 1};
-    int kb[4];
-    for (int b = 0; b < 4; ++b) {
+    // branches: iterations with index 0 (first), 2 (even) and 1 (odd), the refinement, then the light
+    // iterations (even, odd)
+    const int its[kMxBranches] = {0, 2, 1, -1, 2, 1};
+    MxBranchKernels kb;
+    for (int b = 0; b < kMxBranches; ++b) {
         if (cudaStreamBeginCaptureToGraph(cap_body[1], br[b], nullptr, nullptr, 0,
                                           cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             return PIC_ERR_CUDA;
         const long long l0 = launches;
-        if (b < 3) {
-            iteration_mixed(cap_body[1], its[b]);
-        } else {
+        if (b == 3) {
             k_mx_commit<<<gf, kFlatBlock, 0, cap_body[1]>>>(phi_hi, phi_lo, d32, n);
             ++launches;
             resid(cap_body[1]);
+        } else {
+            iteration_mixed(cap_body[1], its[b], b > 3);
         }
-        kb[b] = (int)(launches - l0);
+        kb.k[b] = (int)(launches - l0);
         if (end_body_capture(cap_body[1]) != cudaSuccess) return PIC_ERR_CUDA;
     }
     const float inv2h = (float)(1.0 / (2.0 * h));
     k_mx_grad<<<g3, kBlk, 0, cs>>>(phi_hi, phi_lo, d32, out_hi, out_lo, nx, ny, nz, inv2h, bc, nullptr, nullptr,
                                    nullptr, E4, loop);
-    k_mx_report<<<1, 1, 0, cs>>>(loop, cycles_dst, rel_dst, err_dst, err_bit, kernels_dst,
-                                 make_int4(kb[0], kb[1], kb[2], kb[3]));
+    k_mx_report<<<1, 1, 0, cs>>>(loop, cycles_dst, rel_dst, err_dst, err_bit, kernels_dst, kb);
     if (fixed_kernels) *fixed_kernels = 3 + (min_c > 0 ? 2 : 0);  // residual, gradient, report, prime, check
     return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ERR_CUDA;
 }

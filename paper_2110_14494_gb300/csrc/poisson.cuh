@@ -9,10 +9,16 @@ namespace pic {
 // memory): iteration index since the last refinement, cycles, decisions
 // taken, cycle-limit flag, branch counts, the residual norm at the last
 // refinement and the last relative residual.
+// Branches of the device-driven loop: iterations 0 (first), even, odd; the
+// refinement; light iterations (even, odd).
+constexpr int kMxBranches = 6;
 struct MxLoop {
     int it, cyc, trips, timeout;
-    int n_branch[4];
+    int n_branch[kMxBranches];
     double r_pass, rel;
+};
+struct MxBranchKernels {
+    int k[kMxBranches];  // kernels each branch runs
 };
 
 struct MG {
@@ -25,6 +31,11 @@ struct MG {
     double* norms = nullptr;  // CG scalars: ||b||^2, ||r||^2, rho, gamma, z.r, z.q, alpha, beta
     double *r64 = nullptr, *p64 = nullptr, *q64 = nullptr;  // CG vectors (float64)
     int pre = 2, post = 2, coarse_sweeps = 4;  // coarse: red-black sweeps on the coarsest level
+    // mixed solve: an iteration after the untested ones whose relative
+    // residual is already within light_ratio x rtol uses a V(light_pre,
+    // light_post)-cycle (0: never)
+    double light_ratio = 0.0;
+    int light_pre = 1, light_post = 1;
     float omega = 1.0f;          // over-relaxation of the pre- and post-smoothing sweeps (1: Gauss-Seidel)
     // mixed solve: CG iterations run before the first convergence or
     // refinement test (0 to 2; at most max_cycles).  A coupled PIC context
@@ -57,13 +68,13 @@ struct MG {
     float* phi_pair = nullptr;  // [2][n] pair copy for callers that hold phi in float64
     unsigned* ctr = nullptr;
     double* part = nullptr;
-    cudaGraphExec_t g_mx[3] = {nullptr, nullptr, nullptr};  // first, odd, even iterations
-    long long graph_kernels_mx[3] = {0, 0, 0};
+    cudaGraphExec_t g_mx[5] = {};  // first, even, odd iterations, light even, light odd
+    long long graph_kernels_mx[5] = {};
     MxLoop* loop = nullptr;
     // Creates the streams capture_solve_mixed records the loop bodies on
     // (call before the caller's capture begins).
     int prepare_capture();
-    void iteration_mixed(cudaStream_t s, int it);
+    void iteration_mixed(cudaStream_t s, int it, bool light = false);
     // Records the whole mixed solve on stream cs, which must be capturing a
     // graph: the residual, a device-side while loop (a decision kernel, then
     // a switch over the first / even / odd CG iteration and the refinement),
@@ -101,7 +112,7 @@ struct MG {
     static size_t bytes(int nx, int ny, int nz, bool mixed = false, bool pair_copy = false);
     size_t carve(void* base, int nx, int ny, int nz, bool mixed = false, bool pair_copy = false);
     cudaError_t build_masks(const uint8_t* mask, cudaStream_t s);
-    void vcycle(cudaStream_t s);
+    void vcycle(cudaStream_t s, bool light);
     int tail_level() const;
     // Returns PIC_OK, PIC_ERR_TIMEOUT or PIC_ERR_CUDA.  packed_prec selects the
     // element type (32: float, 64: double) of the optional packed field E4.

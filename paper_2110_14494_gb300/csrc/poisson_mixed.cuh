@@ -600,12 +600,13 @@ __global__ void __launch_bounds__(BX * BY, 10) k_mx_grad(const float* __restrict
 // every refinement is followed by an iteration or a stop, so the loop ends
 // within 2 max_cycles + 1 trips.
 __global__ void k_mx_decide(const double* __restrict__ sc, MxLoop* L, double rtol, int max_cycles,
-                            cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_branch) {
+                            double light_ratio, cudaGraphConditionalHandle h_loop,
+                            cudaGraphConditionalHandle h_branch) {
     const double bn = sc[S_B2] > 0.0 ? sqrt(sc[S_B2]) : 1.0;
     const double rn = sqrt(sc[S_R2]);
     if (L->it == 0) L->r_pass = rn;
     L->rel = rn / bn;
-    unsigned branch = 4;  // no branch
+    unsigned branch = kMxBranches;  // no branch
     bool stop = false;
     if (rn / bn <= rtol) {
         stop = true;
@@ -616,12 +617,13 @@ __global__ void k_mx_decide(const double* __restrict__ sc, MxLoop* L, double rto
         branch = 3;
         L->it = 0;
     } else {
-        branch = L->it == 0 ? 0u : 1u + (unsigned)(L->it & 1);
+        const bool light = light_ratio > 0.0 && L->it > 0 && rn / bn <= light_ratio * rtol;
+        branch = L->it == 0 ? 0u : (light ? 4u : 1u) + (unsigned)(L->it & 1);
         ++L->it;
         ++L->cyc;
     }
     ++L->trips;
-    if (branch < 4) ++L->n_branch[branch];
+    if (branch < (unsigned)kMxBranches) ++L->n_branch[branch];
     cudaGraphSetConditional(h_branch, branch);
     if (stop) cudaGraphSetConditional(h_loop, 0u);
 }
@@ -657,13 +659,13 @@ __global__ void k_mx_check(const double* __restrict__ sc, MxLoop* L, double rtol
 // Results of a device-driven solve: cycles, relative residual, the
 // cycle-limit flag, and the kernels its loop ran (kb: per branch).
 __global__ void k_mx_report(const MxLoop* __restrict__ L, int* cycles, double* rel, unsigned* err, unsigned bit,
-                            unsigned long long* kernels, int4 kb) {
+                            unsigned long long* kernels, MxBranchKernels kb) {
     *cycles = L->cyc;
     *rel = L->rel;
     if (L->timeout) *err |= bit;
-    *kernels += (unsigned long long)L->trips + (unsigned long long)L->n_branch[0] * kb.x +
-                (unsigned long long)L->n_branch[1] * kb.y + (unsigned long long)L->n_branch[2] * kb.z +
-                (unsigned long long)L->n_branch[3] * kb.w;
+    unsigned long long k = (unsigned long long)L->trips;
+    for (int b = 0; b < kMxBranches; ++b) k += (unsigned long long)L->n_branch[b] * kb.k[b];
+    *kernels += k;
 }
 
 // float64 <-> float pair, for callers that hold the potential in float64.
