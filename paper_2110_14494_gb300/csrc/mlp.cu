@@ -557,7 +557,7 @@ __global__ void __launch_bounds__(kTcThreads) k_infer_tc(const float* __restrict
     extern __shared__ __align__(1024) unsigned char tc_raw[];
     // align the operand tiles to 1024 bytes
     TcSmem& S = *reinterpret_cast<TcSmem*>(tc_raw + ((1024 - (smem_u32(tc_raw) & 1023)) & 1023));
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x, warp = tid >> 5;
     const int row = tid & (kTcRows - 1), half = tid >> 7;
     // operands and parameters
     for (int k = tid; k < NH * NH; k += kTcThreads) {
