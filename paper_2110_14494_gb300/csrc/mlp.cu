@@ -596,12 +596,22 @@ __global__ void __launch_bounds__(kTcThreads) k_infer_tc(const float* __restrict
     const uint32_t a_addr = smem_u32(S.a), w2_addr = smem_u32(S.w2), w3_addr = smem_u32(S.w3);
     uint32_t parity = 0;
     const long long n_tiles = (n + kTcRows - 1) / kTcRows;
+    // this thread's point of the next tile is loaded one tile ahead
+    float xn0 = 0.0f, xn1 = 0.0f;
+    {
+        const long long p0 = (long long)blockIdx.x * kTcRows + row;
+        if (p0 < n) { xn0 = x[p0 * NI]; xn1 = x[p0 * NI + 1]; }
+    }
     for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const long long p = tile * kTcRows + row;
         const bool valid = p < n;
+        const float x0 = xn0, x1 = xn1;
+        {
+            const long long pn = (tile + gridDim.x) * kTcRows + row;
+            if (pn < n) { xn0 = x[pn * NI]; xn1 = x[pn * NI + 1]; }
+        }
         // 1. layer 1 into the A operand (this thread: 64 units of its point)
         {
-            const float x0 = valid ? x[p * NI] : 0.0f, x1 = valid ? x[p * NI + 1] : 0.0f;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const int u0 = half * 64 + c * 8;
