@@ -401,8 +401,8 @@ int poisson_axi_solve(int nr, int nz, double dx, double v_lo, double v_hi, doubl
  * fits, 100^3 does not, at either precision); larger grids return
  * PIC_ERR_CAPACITY and touch nothing.  The first call on
  * a device looks up that array's device address (cudaGetSymbolAddress) with
- * the device current, so make the first call on each device outside any
- * stream capture.  Every call shares the one array: calls that can overlap
+ * the device current and keeps it for later calls on that device.  Every
+ * call shares the one array: calls that can overlap
  * on the GPU (other streams, other host threads) race and must be
  * serialised by the caller.  Nothing is allocated; arguments and results are
  * as for poisson_solve. */
