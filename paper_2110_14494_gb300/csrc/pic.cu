@@ -281,6 +281,17 @@ __global__ void k_end_step(DevState* st, long long* count_slot, long long cap) {
 // of the electron speeds (for the 90 % quantile of the CFL condition) and the
 // largest and total fixed-point electron deposit (for the dielectric
 // relaxation time and the growth limit).
+// Each thread takes kStatsUnroll elements per trip, one grid stride apart,
+// and issues all their loads before using any, so the grid keeps enough
+// loads in flight to stream both arrays at DRAM speed.
+constexpr int kStatsUnroll = 4;
+
+__device__ __forceinline__ int speed_bin(float vx, float vy, float vz) {
+    const float v2 = vx * vx + vy * vy + vz * vz;
+    const int b = v2 > 0.0f ? (int)floorf((0.5f * log2f(v2) - 10.0f) * kVBinsPerOctave) : 0;
+    return b < 0 ? 0 : (b >= kVBins ? kVBins - 1 : b);
+}
+
 template <class T>
 __global__ void k_step_stats(const Soa<T> p, const DevState* stc, const unsigned long long* __restrict__ qe,
                              long long ncell, int nr, DevState* st) {
@@ -289,36 +300,65 @@ __global__ void k_step_stats(const Soa<T> p, const DevState* stc, const unsigned
     __syncthreads();
     const long long n = (long long)stc->n_out;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        int b = -1;
-        if (p.r[PW][i] > (T)0) {
-            const float vx = (float)p.r[VX][i], vy = (float)p.r[VY][i], vz = (float)p.r[VZ][i];
-            const float v2 = vx * vx + vy * vy + vz * vz;
-            b = v2 > 0.0f ? (int)floorf((0.5f * log2f(v2) - 10.0f) * kVBinsPerOctave) : 0;
-            b = b < 0 ? 0 : (b >= kVBins ? kVBins - 1 : b);
+    for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kStatsUnroll * stride) {
+        T w[kStatsUnroll], vx[kStatsUnroll], vy[kStatsUnroll], vz[kStatsUnroll];
+#pragma unroll
+        for (int u = 0; u < kStatsUnroll; ++u) {
+            const long long i = i0 + u * stride;
+            w[u] = i < n ? p.r[PW][i] : (T)0;
+            vx[u] = i < n ? p.r[VX][i] : (T)0;
+            vy[u] = i < n ? p.r[VY][i] : (T)0;
+            vz[u] = i < n ? p.r[VZ][i] : (T)0;
         }
-        // lanes with the same bin add once (most electrons share a few bins)
-        const unsigned grp = __match_any_sync(__activemask(), b);
-        if (b >= 0 && __ffs(grp) - 1 == (int)(threadIdx.x & 31)) atomicAdd(&h[b], (unsigned)__popc(grp));
+#pragma unroll
+        for (int u = 0; u < kStatsUnroll; ++u) {
+            const int b = w[u] > (T)0 ? speed_bin((float)vx[u], (float)vy[u], (float)vz[u]) : -1;
+            // lanes with the same bin add once (most electrons share a few bins)
+            const unsigned grp = __match_any_sync(__activemask(), b);
+            if (b >= 0 && __ffs(grp) - 1 == (int)(threadIdx.x & 31)) atomicAdd(&h[b], (unsigned)__popc(grp));
+        }
     }
     long long mx = LLONG_MIN, sm = 0;
-    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += stride) {
-        const long long q = (long long)qe[c];
-        // axisymmetric (nr > 0): the maximum of q / (2i + 1), proportional to the density
-        const long long qd = nr > 0 ? q / (2 * (long long)(c % nr) + 1) : q;
-        mx = qd > mx ? qd : mx;
-        sm += q;
+    for (long long c0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; c0 < ncell; c0 += kStatsUnroll * stride) {
+        long long q[kStatsUnroll];
+#pragma unroll
+        for (int u = 0; u < kStatsUnroll; ++u) {
+            const long long c = c0 + u * stride;
+            q[u] = c < ncell ? (long long)qe[c] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kStatsUnroll; ++u) {
+            const long long c = c0 + u * stride;
+            if (c < ncell) {
+                // axisymmetric (nr > 0): the maximum of q / (2i + 1), proportional to the density
+                const long long qd = nr > 0 ? q[u] / (2 * (long long)(c % nr) + 1) : q[u];
+                mx = qd > mx ? qd : mx;
+                sm += q[u];
+            }
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         const long long om = __shfl_xor_sync(kFull, mx, o);
         mx = om > mx ? om : mx;
         sm += __shfl_xor_sync(kFull, sm, o);
     }
+    // one atomic per block and quantity (every block's warps would otherwise
+    // queue on the same two addresses)
+    __shared__ long long wmx[32], wsm[32];
+    const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
+        wmx[w] = mx;
+        wsm[w] = sm;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
+            mx = wmx[q] > mx ? wmx[q] : mx;
+            sm += wsm[q];
+        }
         atomicMax(&st->qe_max, mx);
         atomicAdd(&st->qe_sum, (unsigned long long)sm);
     }
-    __syncthreads();
     for (int b = threadIdx.x; b < kVBins; b += blockDim.x)
         if (h[b]) atomicAdd(&st->vhist[b], h[b]);
 }
