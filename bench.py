@@ -254,7 +254,7 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def issue_roofline(draws_per_update, updates_per_step, collide_ms_per_step, clk, sms=152):
+def issue_roofline(draws_per_update, updates_per_step, collide_ms_per_step, clk, sms):
     """The collision kernels' binding limit: warp-instruction issue.  The
     algorithmic work is one draw per candidate collision of the null-collision
     method (nu_max dt per electron-step, measured) plus the draw that ends the

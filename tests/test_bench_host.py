@@ -23,8 +23,9 @@ def test_clock_samples_median_max_and_reasons():
 
 def test_issue_roofline_arithmetic():
     """achieved = warp instructions per draw x draws per update x updates per
-    step / collision time per step; peak = 4 x 152 x the SM clock."""
-    r = bench.issue_roofline(10.0, 1.0e6, 0.25, {"sm_mhz": 2000.0})
+    step / collision time per step; peak = 4 warp schedulers x the SM count x
+    the SM clock."""
+    r = bench.issue_roofline(10.0, 1.0e6, 0.25, {"sm_mhz": 2000.0}, 152)
     assert abs(r["peak"] - 4 * 152 * 2.0) < 1e-9                   # Gwarp-inst/s
     assert abs(r["achieved"] - bench.PUSH_WARP_INST_PER_DRAW * 10.0 * 1.0e6 / 0.25e-3 / 1e9) < 1e-9
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
