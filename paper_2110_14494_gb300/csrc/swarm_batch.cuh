@@ -554,7 +554,11 @@ __device__ void batch_phase(const BatchArgs<T>& B, const ProcSmem<T>& ps, BatchS
         }
         int r = EV_CONTINUE;
         T sp = (T)0;
-        if (active) r = event<T, MODE_SWARM, FAST, false>(B.P, R, K, step, &ps, L, ls, sp);
+        if (active) {
+            // up to two candidate collisions per trip, as in the collision kernel
+            r = event<T, MODE_SWARM, FAST, false>(B.P, R, K, step, &ps, L, ls, sp);
+            if (r == EV_CONTINUE) r = event<T, MODE_SWARM, FAST, false>(B.P, R, K, step, &ps, L, ls, sp);
+        }
         const bool done = r == EV_DONE, ion = r == EV_IONIZED;
         if (r == EV_DONE || r == EV_ATTACHED) active = false;
         if (CHILD && ion) {
