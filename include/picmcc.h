@@ -305,6 +305,8 @@ typedef struct pic_profile_times {
      * host reads the step's counts; a step that then needs a weight update or
      * further product generations undoes that solve and solves again */
     long long n_speculative, n_undone;                 /* such solves, and those undone */
+    long long n_overlapped;                            /* pic_upload / pic_download calls that ran
+                                                          under such a solve (see pic_download) */
 } pic_profile_times;
 
 /* enable != 0 starts timing (cleared); out (optional) receives the
@@ -324,7 +326,13 @@ int pic_profile(pic_ctx *ctx, int enable, pic_profile_times *out);
  * *n_out set, nothing copied) when the set is larger than cap.  When
  * arrays[0..9] lie at one constant pitch (one host block, rows at least n
  * elements apart) they move in one pitched copy, else in ten; the ids
- * always in one more. */
+ * always in one more.  Right after a pic_step whose last step's field solve
+ * was enqueued speculatively (float32 Cartesian coupled contexts), with no
+ * other call on the context in between, both run their copies on a
+ * context-owned copy stream that waits only for that step's particles, so
+ * they overlap the solve still running: pic_download then returns once the
+ * particles are on the host, and pic_upload makes the context's stream wait
+ * for its copies.  Results are the same either way. */
 int pic_upload(pic_ctx *ctx, long long n, const void *const *arrays, int accel_valid);
 int pic_download(pic_ctx *ctx, void *const *arrays, long long cap, long long *n_out);
 

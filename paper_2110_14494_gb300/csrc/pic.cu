@@ -1070,6 +1070,14 @@ struct pic_ctx {
     // before the host looks at it.
     DevState* hs = nullptr;
     cudaEvent_t ev_state = nullptr;
+    // Host exchanges under the speculative solve: ev_parts is recorded once a
+    // speculative step's particles are final, before its solve is enqueued;
+    // parts_event says that no work touching the particle buffers has been
+    // enqueued since, so pic_download and pic_upload may copy on xs (waiting
+    // for ev_parts only) while the solve runs.
+    cudaStream_t xs = nullptr;
+    cudaEvent_t ev_parts = nullptr, ev_up = nullptr;
+    bool parts_event = false;
     bool spec_off = false;       // pinned memory or the event could not be had
     bool spec_now = false;       // the solve being enqueued is speculative
     int gate_spec = 0;           // the gate's settings in DevState (zero at init)
@@ -1131,6 +1139,9 @@ struct pic_ctx {
             if (fgraph[q]) cudaGraphExecDestroy(fgraph[q]);
         if (hs) cudaFreeHost(hs);
         if (ev_state) cudaEventDestroy(ev_state);
+        if (ev_parts) cudaEventDestroy(ev_parts);
+        if (ev_up) cudaEventDestroy(ev_up);
+        if (xs) cudaStreamDestroy(xs);
         if (fbody) cudaStreamDestroy(fbody);
         if (agraph) cudaGraphExecDestroy(agraph);
         if (fcap) cudaStreamDestroy(fcap);
@@ -1443,6 +1454,7 @@ template <class T> static void deposit_current(pic_ctx* c, unsigned long long* q
 
 extern "C" int pic_seed_gaussian(pic_ctx* c, double n0, double radius, const double center[3], double w0,
                                  long long* n_out) {
+    if (c) c->parts_event = false;  // work on the particle buffers may follow
     if (!c || !center || !(n0 >= 0) || !(radius > 0) || !(w0 > 0)) return PIC_ERR_ARG;
     if (c->g.axi && (center[0] != 0.0 || center[1] != 0.0))
         return c->fail(PIC_ERR_ARG, "axisymmetric seed: the centre must be on the axis");
@@ -1494,6 +1506,7 @@ template <class T> static int set_particles(pic_ctx* c, long long n, const pic_p
 }
 
 extern "C" int pic_set_particles(pic_ctx* c, long long n, const pic_particles_host* p, int accel_valid) {
+    if (c) c->parts_event = false;  // work on the particle buffers may follow
     if (!c || n < 0 || (n > 0 && (!p || !p->x || !p->y || !p->z || !p->w || !p->id))) return PIC_ERR_ARG;
     if (n > c->cfg.capacity) return c->fail(PIC_ERR_CAPACITY, "more particles than capacity");
     c->cur = 0;
@@ -1543,11 +1556,13 @@ template <class T> static int get_particles(pic_ctx* c, pic_particles_host* p, l
 }
 
 extern "C" int pic_get_particles(pic_ctx* c, pic_particles_host* p, long long cap, long long* n_out) {
+    if (c) c->parts_event = false;  // work on the particle buffers may follow
     if (!c) return PIC_ERR_ARG;
     return c->prec == 32 ? get_particles<float>(c, p, cap, n_out) : get_particles<double>(c, p, cap, n_out);
 }
 
 extern "C" int pic_count(pic_ctx* c, long long* n) {
+    if (c) c->parts_event = false;  // work on the particle buffers may follow
     if (!c || !n) return PIC_ERR_ARG;
     DevState h;
     int rc = read_state(c, &h);
@@ -1579,11 +1594,13 @@ static int set_field(pic_ctx* c, const TI* Ex, const TI* Ey, const TI* Ez, const
 }
 
 extern "C" int pic_set_field(pic_ctx* c, const float* Ex, const float* Ey, const float* Ez, const double E_uniform[3]) {
+    if (c) c->parts_event = false;  // work on the particle buffers may follow
     return set_field<float>(c, Ex, Ey, Ez, E_uniform);
 }
 
 extern "C" int pic_set_field_f64(pic_ctx* c, const double* Ex, const double* Ey, const double* Ez,
                                  const double E_uniform[3]) {
+    if (c) c->parts_event = false;  // work on the particle buffers may follow
     return set_field<double>(c, Ex, Ey, Ez, E_uniform);
 }
 
@@ -1599,6 +1616,7 @@ __global__ void k_unpack_field(const T* __restrict__ E4, long long n, double* __
 }
 
 extern "C" int pic_get_field(pic_ctx* c, double* Ex, double* Ey, double* Ez) {
+    if (c) c->parts_event = false;  // work on the particle buffers may follow
     if (!c) return PIC_ERR_ARG;
     if (!c->field_valid || c->field_uniform)
         return c->fail(PIC_ERR_STATE, "no field grid: set one, or step a coupled context (or call pic_step with 0 steps)");
@@ -1612,6 +1630,7 @@ extern "C" int pic_get_field(pic_ctx* c, double* Ex, double* Ey, double* Ez) {
 }
 
 extern "C" int pic_get_deposit(pic_ctx* c, int64_t* q_e, int64_t* q_pos, int64_t* q_neg) {
+    if (c) c->parts_event = false;  // work on the particle buffers may follow
     if (!c) return PIC_ERR_ARG;
     const size_t n = (size_t)c->g.ncell();
     cudaError_t e = cudaSuccess;
@@ -1846,6 +1865,7 @@ static int solve_field(pic_ctx* c) {
 }
 
 template <class T> static int sort_by_cell(pic_ctx* c) {
+    c->parts_event = false;
     const long long ncell = c->g.ncell();
     uint32_t* cnt = (uint32_t*)(c->ws + c->L.cnt);
     uint32_t* start = (uint32_t*)(c->ws + c->L.start);
@@ -1866,6 +1886,7 @@ template <class T> static int sort_by_cell(pic_ctx* c) {
 
 // Weight update (Sec. 2.1.2): sort by cell, per-cell merge and split, compaction.
 template <class T> static int weight_update(pic_ctx* c) {
+    c->parts_event = false;
     int rc = sort_by_cell<T>(c);
     if (rc) return rc;
     const long long ncell = c->g.ncell();
@@ -1911,6 +1932,7 @@ template <class T> static int weight_update(pic_ctx* c) {
 }
 
 extern "C" int pic_weight_update(pic_ctx* c) {
+    if (c) c->parts_event = false;  // work on the particle buffers may follow
     if (!c) return PIC_ERR_ARG;
     return c->prec == 32 ? weight_update<float>(c) : weight_update<double>(c);
 }
@@ -2018,6 +2040,10 @@ static bool can_speculate(pic_ctx* c) {
     if (!c->hs && cudaHostAlloc((void**)&c->hs, sizeof(DevState), cudaHostAllocDefault) != cudaSuccess) c->hs = nullptr;
     if (c->hs && !c->ev_state && cudaEventCreateWithFlags(&c->ev_state, cudaEventDisableTiming) != cudaSuccess)
         c->ev_state = nullptr;
+    if (!c->ev_parts && cudaEventCreateWithFlags(&c->ev_parts, cudaEventDisableTiming) != cudaSuccess) {
+        c->ev_parts = nullptr;  // host exchanges then wait for the solve
+        cudaGetLastError();
+    }
     if (!c->hs || !c->ev_state) {
         cudaGetLastError();
         c->spec_off = true;
@@ -2032,6 +2058,8 @@ template <class T> static int speculative_tail(pic_ctx* c, PushArgs<T>& A, bool 
     cudaError_t e = cudaMemcpyAsync(c->hs, c->st(), sizeof(DevState), cudaMemcpyDeviceToHost, c->s);
     if (e == cudaSuccess) e = cudaEventRecord(c->ev_state, c->s);
     if (e != cudaSuccess) return c->cuda_fail(e, "state read-back");
+    // the particles are final here unless the step is undone below
+    const bool parts = c->ev_parts && cudaEventRecord(c->ev_parts, c->s) == cudaSuccess;
     const int slots[4] = {c->ph_cur, c->ph_prev, c->ph_free, c->ph_out};
     const long long n_solves = c->n_solves;
     const bool on_device = c->last_on_device;
@@ -2058,6 +2086,7 @@ template <class T> static int speculative_tail(pic_ctx* c, PushArgs<T>& A, bool 
         c->n_next = n_next;
         if (c->cfg.adaptive_dt) next_dt(c, h);
         *solved = true;
+        c->parts_event = parts;
         return PIC_OK;
     }
     c->ph_cur = slots[0];
@@ -2080,6 +2109,7 @@ template <class T> static int speculative_tail(pic_ctx* c, PushArgs<T>& A, bool 
 
 template <class T> static int one_step(pic_ctx* c, bool stats, bool* solved) {
     *solved = false;
+    c->parts_event = false;
     c->step++;
     PushArgs<T> A = make_args<T>(c, MODE_PIC);
     cudaMemsetAsync(c->qe(), 0, (size_t)c->g.ncell() * 8, c->s);
@@ -2201,6 +2231,7 @@ extern "C" int pic_step(pic_ctx* c, int n_steps, pic_step_stats* stats) {
 }
 
 extern "C" int pic_deposit(pic_ctx* c, int64_t* q_e, int64_t* q_pos, int64_t* q_neg, double* rho) {
+    if (c) c->parts_event = false;  // work on the particle buffers may follow
     if (!c) return PIC_ERR_ARG;
     const size_t n = (size_t)c->g.ncell();
     cudaMemsetAsync(c->qe(), 0, n * 8, c->s);
@@ -2253,6 +2284,7 @@ struct BlobHead {
 static const uint64_t kMagic = 0x3230314D43435049ull;  // "IPCCM102"
 
 extern "C" int pic_save(pic_ctx* c, void* blob, size_t* bytes) {
+    if (c) c->parts_event = false;  // work on the particle buffers may follow
     if (!c || !bytes) return PIC_ERR_ARG;
     DevState h;
     int rc = read_state(c, &h);
@@ -2285,6 +2317,7 @@ extern "C" int pic_save(pic_ctx* c, void* blob, size_t* bytes) {
 }
 
 extern "C" int pic_load(pic_ctx* c, const void* blob, size_t bytes) {
+    if (c) c->parts_event = false;  // work on the particle buffers may follow
     if (!c || !blob || bytes < sizeof(BlobHead)) return PIC_ERR_ARG;
     BlobHead hd;
     memcpy(&hd, blob, sizeof hd);
@@ -2920,6 +2953,7 @@ extern "C" int pic_progress(pic_ctx* c, long long* updates, long long* parents, 
 }
 
 extern "C" int pic_set_poisson(pic_ctx* c, double rtol, int max_cycles, int device_loop) {
+    if (c) c->parts_event = false;  // work on the particle buffers may follow
     if (!c || !(rtol > 0.0) || max_cycles < 1) return PIC_ERR_ARG;
     // recorded graphs hold the old settings
     for (int q = 0; q < 4; ++q)
@@ -2938,6 +2972,7 @@ extern "C" int pic_set_poisson(pic_ctx* c, double rtol, int max_cycles, int devi
 }
 
 extern "C" int pic_set_multigrid(pic_ctx* c, int pre_sweeps, int post_sweeps) {
+    if (c) c->parts_event = false;  // work on the particle buffers may follow
     if (!c || pre_sweeps < 1 || pre_sweeps > 4 || post_sweeps < 1 || post_sweeps > 4) return PIC_ERR_ARG;
     if (c->g.axi) return c->fail(PIC_ERR_STATE, "the axisymmetric solve keeps its V(2,2)-cycle");
     // recorded graphs hold the old cycle
@@ -2953,6 +2988,7 @@ extern "C" int pic_set_multigrid(pic_ctx* c, int pre_sweeps, int post_sweeps) {
 }
 
 extern "C" int pic_profile(pic_ctx* c, int enable, pic_profile_times* out) {
+    if (c) c->parts_event = false;  // work on the particle buffers may follow
     if (!c) return PIC_ERR_ARG;
     DevState h;
     const int rc = read_state(c, &h);
@@ -2981,26 +3017,53 @@ static size_t host_pitch(const void* const* arrays, size_t row) {
     return (size_t)d;
 }
 
+// The copy stream of the host exchanges that overlap a speculative solve
+// (false: exchange on the context's stream).
+static bool exchange_stream(pic_ctx* c) {
+    if (!c->parts_event || !c->ev_parts) return false;
+    if (!c->xs && cudaStreamCreateWithFlags(&c->xs, cudaStreamNonBlocking) != cudaSuccess) c->xs = nullptr;
+    if (c->xs && !c->ev_up && cudaEventCreateWithFlags(&c->ev_up, cudaEventDisableTiming) != cudaSuccess)
+        c->ev_up = nullptr;
+    if (!c->xs || !c->ev_up) {
+        cudaGetLastError();
+        return false;
+    }
+    return cudaStreamWaitEvent(c->xs, c->ev_parts, 0) == cudaSuccess;
+}
+
 extern "C" int pic_upload(pic_ctx* c, long long n, const void* const* arrays, int accel_valid) {
     if (!c || n < 0 || (n > 0 && !arrays)) return PIC_ERR_ARG;
     if (n > c->cfg.capacity) return c->fail(PIC_ERR_CAPACITY, "more particles than capacity");
+    for (int f = 0; f < 11 && n > 0; ++f)
+        if (!arrays[f]) return PIC_ERR_ARG;
+    // Right after a speculative step nothing enqueued since its particles
+    // were final touches a particle buffer (only its field solve may still
+    // run), so the copies go on the exchange stream, behind those particles
+    // only, and the context's stream waits for them.
+    const bool ovl = exchange_stream(c);
+    c->parts_event = false;
+    if (ovl) c->pt.n_overlapped++;
+    cudaStream_t us = ovl ? c->xs : c->s;
     c->cur = 0;
     const size_t R = real_size(c->prec), cap = (size_t)c->cfg.capacity;
     char* base = c->ws + c->L.buf[0];
-    for (int f = 0; f < 11 && n > 0; ++f)
-        if (!arrays[f]) return PIC_ERR_ARG;
     // the ten real arrays in one pitched copy when the host keeps them in one block
     const size_t hp = n > 0 ? host_pitch(arrays, (size_t)n * R) : 0;
     if (hp) {
         cudaError_t e = cudaMemcpy2DAsync(base, al256(cap * R), arrays[0], hp, (size_t)n * R, 10,
-                                          cudaMemcpyHostToDevice, c->s);
+                                          cudaMemcpyHostToDevice, us);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(base + 10 * al256(cap * R), arrays[10], (size_t)n * 8, cudaMemcpyHostToDevice, c->s);
+            e = cudaMemcpyAsync(base + 10 * al256(cap * R), arrays[10], (size_t)n * 8, cudaMemcpyHostToDevice, us);
         if (e != cudaSuccess) return c->cuda_fail(e, "upload");
     }
     for (int f = 0; f < 11 && n > 0 && !hp; ++f) {
         cudaError_t e = cudaMemcpyAsync(base + f * al256(cap * R), arrays[f], n * (f < 10 ? R : 8),
-                                        cudaMemcpyHostToDevice, c->s);
+                                        cudaMemcpyHostToDevice, us);
+        if (e != cudaSuccess) return c->cuda_fail(e, "upload");
+    }
+    if (ovl) {
+        cudaError_t e = cudaEventRecord(c->ev_up, c->xs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->s, c->ev_up, 0);
         if (e != cudaSuccess) return c->cuda_fail(e, "upload");
     }
     k_set_count<<<1, 1, 0, c->s>>>(c->st(), (unsigned long long)n);
@@ -3010,22 +3073,22 @@ extern "C" int pic_upload(pic_ctx* c, long long n, const void* const* arrays, in
     return PIC_OK;
 }
 
-// Copies n particles of the current buffer to the host arrays (no wait).
-static cudaError_t download_async(pic_ctx* c, void* const* arrays, long long n) {
+// Copies n particles of the current buffer to the host arrays on stream ds (no wait).
+static cudaError_t download_async(pic_ctx* c, void* const* arrays, long long n, cudaStream_t ds) {
     const size_t R = real_size(c->prec), capd = (size_t)c->cfg.capacity;
     char* base = c->ws + c->L.buf[c->cur];
     const size_t hp = n > 0 ? host_pitch(arrays, (size_t)n * R) : 0;
     if (hp) {  // the ten real arrays in one pitched copy (one host block)
         cudaError_t e = cudaMemcpy2DAsync(arrays[0], hp, base, al256(capd * R), (size_t)n * R, 10,
-                                          cudaMemcpyDeviceToHost, c->s);
+                                          cudaMemcpyDeviceToHost, ds);
         if (e == cudaSuccess && arrays[10])
-            e = cudaMemcpyAsync(arrays[10], base + 10 * al256(capd * R), (size_t)n * 8, cudaMemcpyDeviceToHost, c->s);
+            e = cudaMemcpyAsync(arrays[10], base + 10 * al256(capd * R), (size_t)n * 8, cudaMemcpyDeviceToHost, ds);
         return e;
     }
     for (int f = 0; f < 11 && n > 0; ++f) {
         if (!arrays[f]) continue;
         cudaError_t e = cudaMemcpyAsync(arrays[f], base + f * al256(capd * R), n * (f < 10 ? R : 8),
-                                        cudaMemcpyDeviceToHost, c->s);
+                                        cudaMemcpyDeviceToHost, ds);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -3033,20 +3096,31 @@ static cudaError_t download_async(pic_ctx* c, void* const* arrays, long long n) 
 
 extern "C" int pic_download(pic_ctx* c, void* const* arrays, long long cap, long long* n_out) {
     if (!c || !arrays) return PIC_ERR_ARG;
+    long long n = c->n_host;
+    const bool fits = n <= cap;
+    // Right after a speculative step: its particles and count are final
+    // (the count was read back before the host let the solve stand), so the
+    // copy waits for them only and overlaps the solve.
+    if (fits && exchange_stream(c)) {
+        c->pt.n_overlapped++;
+        cudaError_t e = download_async(c, arrays, n, c->xs);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->xs);
+        if (e != cudaSuccess) return c->cuda_fail(e, "download");
+        if (n_out) *n_out = n;
+        return PIC_OK;
+    }
     // The host count is known after every call that changes it; the device
     // state and the particles are copied together and checked after one wait.
     DevState h;
-    long long n = c->n_host;
-    const bool fits = n <= cap;
     cudaError_t e = cudaMemcpyAsync(&h, c->st(), sizeof(DevState), cudaMemcpyDeviceToHost, c->s);
-    if (e == cudaSuccess && fits) e = download_async(c, arrays, n);
+    if (e == cudaSuccess && fits) e = download_async(c, arrays, n, c->s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
     if (e != cudaSuccess) return c->cuda_fail(e, "download");
     if ((long long)h.n_in != n) {  // not expected: copy again with the device count
         n = (long long)h.n_in;
         c->n_host = n;
         if (n <= cap) {
-            e = download_async(c, arrays, n);
+            e = download_async(c, arrays, n, c->s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
             if (e != cudaSuccess) return c->cuda_fail(e, "download");
         }

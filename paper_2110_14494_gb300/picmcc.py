@@ -77,7 +77,7 @@ class pic_step_stats(C.Structure):
 class pic_profile_times(C.Structure):
     _fields_ = [(k, C.c_double) for k in ("ms_push", "ms_children", "ms_field", "ms_reorder")] + \
                [(k, C.c_longlong) for k in ("n_push", "n_children", "n_field", "n_reorder", "n_launches",
-                                            "n_speculative", "n_undone")]
+                                            "n_speculative", "n_undone", "n_overlapped")]
 
 
 class poisson_config(C.Structure):

@@ -129,3 +129,62 @@ def test_download_into_too_small_arrays_is_reported():
     small = [np.zeros(1000, np.float32) for _ in FIELDS] + [np.zeros(1000, np.int64)]
     with pytest.raises(PicError):
         ctx.download(small, 1000)
+
+
+def _coupled_streamer():
+    """A small coupled float32 needle-plane streamer (speculative field
+    solves from the third step on, weight updates on growth)."""
+    from paper_2110_14494_gb300 import PicContext
+    grid = W.grid_spec(32, 32, 48, 2.5e-5)
+    mask = W.needle_mask(grid, 0.35e-3, 0.08e-3)
+    V0 = 4000.0
+    ctx = PicContext(W.synthetic_air(), grid, precision=32, capacity=400_000, seed=SEED, dt=2e-12, mask=mask,
+                     coupled=True, v_lo=0.0, v_hi=V0, v_mask=V0, poisson_rtol=1e-6, poisson_max_cycles=60,
+                     boundary=1, growth_trigger=1.5, particle_cap=150_000)
+    L = 32 * 2.5e-5
+    ctx.seed_gaussian(5e19, 6e-5, (0.5 * L, 0.5 * L, 0.45 * 48 * 2.5e-5), 2e3)
+    return ctx
+
+
+def test_exchanges_under_the_speculative_solve_match_ordered_ones():
+    """Steps through pinned host buffers (download, then upload, after every
+    step): right after a speculative step both copies overlap the solve on
+    the exchange stream; a context that makes one other call first (pic_count)
+    exchanges on its own stream behind the solve.  Bit-identical particle sets
+    every step, and the overlapped exchanges are counted."""
+    cap = 400_000
+    ctxs, hosts = [], []
+    for _ in range(2):
+        ctx = _coupled_streamer()
+        block = torch.empty((10, cap), dtype=torch.float32, pin_memory=True)
+        ids = torch.empty(cap, dtype=torch.int64, pin_memory=True)
+        hs = ctx.host_set([block[i] for i in range(10)] + [ids], cap)
+        ctx.profile(True)
+        ctxs.append(ctx)
+        hosts.append((hs, block, ids))
+    a, b = ctxs
+    (ha, ba, ia), (hb, bb, ib) = hosts
+
+    def sets(block, ids, n):  # the particle set by id (the output order of the collision kernel varies)
+        return by_id(_as_dict([block[i].numpy() for i in range(10)] + [ids.numpy()], n))
+
+    for step in range(12):
+        a.step(1)
+        b.step(1)
+        b.count()                 # any call in between: the exchanges then wait for the solve
+        na = a.download(ha)
+        nb = b.download(hb)
+        assert na == nb, step
+        sa, sb = sets(ba, ia, na), sets(bb, ib, nb)
+        for k in sa:
+            assert np.array_equal(sa[k], sb[k]), (step, k)
+        a.upload(ha, na, True)
+        b.upload(hb, nb, True)
+    pa, pb = a.profile(False), b.profile(False)
+    assert pa["n_speculative"] > 0 and pa["n_speculative"] == pb["n_speculative"]
+    # every exchange after a speculative step that stood overlapped its solve
+    assert pa["n_overlapped"] == 2 * (pa["n_speculative"] - pa["n_undone"]), pa
+    assert pb["n_overlapped"] == 0, pb
+    qa, qb = by_id(a.get_particles()), by_id(b.get_particles())
+    for k in qa:
+        assert np.array_equal(qa[k], qb[k]), k
