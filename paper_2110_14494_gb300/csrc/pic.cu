@@ -1008,10 +1008,13 @@ static Layout make_layout(const pic_config* c) {
     take(cap * 8); take(cap * 8); take(cap * 4); take(cap * 8); take(cap * 8); take(cap * 4);
     L.gas = take(((size_t)(c->gas.n_proc > 0 ? c->gas.n_proc : 1) + 1) * nb * 8 + 64 * 8);
     L.rho = take(ncell * 8);
-    L.phi = take(ncell * 8);
-    L.phi_prev = take(ncell * 8);
-    L.phi_x = take(ncell * 8);
-    L.phi_y = pair ? take(ncell * 8) : L.phi_x;
+    // a potential slot holds ncell doubles, or a float pair: hi, then lo at
+    // the next 256-byte boundary (the pair kernels use 16-byte accesses)
+    const size_t slot = 2 * al256(ncell * 4);
+    L.phi = take(slot);
+    L.phi_prev = take(slot);
+    L.phi_x = take(slot);
+    L.phi_y = pair ? take(slot) : L.phi_x;
     L.mg = take(c->geometry == 1 ? AxiMG::bytes(c->nx, c->nz) : MG::bytes(c->nx, c->ny, c->nz, c->precision == 32, false));
     {
         const size_t np = (size_t)photo_cap(c);
@@ -1195,7 +1198,7 @@ struct pic_ctx {
         ph_prev = ph_cur;
         ph_cur = o;
     }
-    float* ph_lo(int slot) { return ph_hi(slot) + g.ncell(); }
+    float* ph_lo(int slot) { return ph_hi(slot) + al256((size_t)g.ncell() * 4) / 4; }
     MergeScratch msc() {
         MergeScratch m;
         const size_t cap = (size_t)cfg.capacity;
@@ -2256,7 +2259,8 @@ static cudaError_t save_phi(pic_ctx* c, double* out) {
     const size_t n = (size_t)c->g.ncell();
     if (c->prec != 32 || c->g.axi) return cudaMemcpy(out, c->phi(), n * 8, cudaMemcpyDeviceToHost);
     std::vector<float> hl(2 * n);
-    cudaError_t e = cudaMemcpy(hl.data(), c->ph_hi(c->ph_cur), 2 * n * 4, cudaMemcpyDeviceToHost);
+    cudaError_t e = cudaMemcpy(hl.data(), c->ph_hi(c->ph_cur), n * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(hl.data() + n, c->ph_lo(c->ph_cur), n * 4, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return e;
     for (size_t i = 0; i < n; ++i) out[i] = (double)hl[i] + (double)hl[n + i];
     return cudaSuccess;
@@ -2270,7 +2274,9 @@ static cudaError_t load_phi(pic_ctx* c, const double* in) {
         hl[i] = (float)in[i];
         hl[n + i] = (float)(in[i] - (double)hl[i]);
     }
-    return cudaMemcpy(c->ph_hi(c->ph_cur), hl.data(), 2 * n * 4, cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemcpy(c->ph_hi(c->ph_cur), hl.data(), n * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->ph_lo(c->ph_cur), hl.data() + n, n * 4, cudaMemcpyHostToDevice);
+    return e;
 }
 
 struct BlobHead {

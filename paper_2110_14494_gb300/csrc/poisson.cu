@@ -599,34 +599,45 @@ __global__ void __launch_bounds__(1024) k_tail_vcycle(const TailLevels T) {
     S.rdiag = reinterpret_cast<float*>(tail_raw + (tail_smem_bytes(T.total) - 16 * sizeof(float)));
     if (threadIdx.x < 16) S.rdiag[threadIdx.x] = inv_diag((float)threadIdx.x);
     {
-        // global loads in batches of kTailLoad per thread, issued before
-        // their stores (the first level has at most kTailCells cells)
+        // every global load (the first level's g, the masks of all levels as
+        // one run of T.total bytes) issued before the first store: one round
+        // trip (the first level has at most kTailCells cells, the masks
+        // together fewer than 2 kTailCells)
         constexpr int kTailLoad = kTailCells / 1024;
         const int n0 = T.nx[T.first] * T.ny[T.first] * T.nz[T.first];
         float gv[kTailLoad];
+        uint8_t mv[2 * kTailLoad];
 #pragma unroll
         for (int u = 0; u < kTailLoad; ++u) {
             const int c = threadIdx.x + u * 1024;
             gv[u] = c < n0 ? T.g_first[c] : 0.0f;
         }
-        for (int l = T.first; l <= T.last; ++l) {
-            const int n = T.nx[l] * T.ny[l] * T.nz[l];
-            uint8_t mv[kTailLoad];
 #pragma unroll
-            for (int u = 0; u < kTailLoad; ++u) {
-                const int c = threadIdx.x + u * 1024;
-                mv[u] = c < n ? T.m[l][c] : 0;
+        for (int u = 0; u < 2 * kTailLoad; ++u) {
+            const int c = threadIdx.x + u * 1024;
+            mv[u] = 0;
+            if (c < T.total) {
+                int l = T.first;
+                while (l < T.last && c >= T.off[l + 1]) ++l;
+                mv[u] = T.m[l][c - T.off[l]];
             }
+        }
 #pragma unroll
-            for (int u = 0; u < kTailLoad; ++u) {
-                const int c = threadIdx.x + u * 1024;
-                if (c < n) S.m[T.off[l] + c] = mv[u];
-            }
+        for (int u = 0; u < 2 * kTailLoad; ++u) {
+            const int c = threadIdx.x + u * 1024;
+            if (c < T.total) S.m[c] = mv[u];
         }
 #pragma unroll
         for (int u = 0; u < kTailLoad; ++u) {
             const int c = threadIdx.x + u * 1024;
             if (c < n0) S.g[T.off[T.first] + c] = gv[u];
+        }
+        // a hierarchy of one level may have more cells than the batches cover
+        for (int c = threadIdx.x + kTailCells; c < n0; c += 1024) S.g[T.off[T.first] + c] = T.g_first[c];
+        for (int c = threadIdx.x + 2 * kTailCells; c < T.total; c += 1024) {
+            int l = T.first;
+            while (l < T.last && c >= T.off[l + 1]) ++l;
+            S.m[c] = T.m[l][c - T.off[l]];
         }
         for (int c = threadIdx.x; c < T.total; c += blockDim.x) S.e[c] = 0.0f;
     }
@@ -734,7 +745,8 @@ size_t MG::carve(void* base, int nx_, int ny_, int nz_, bool mixed_, bool pair_c
         p32[0] = (float*)take(n0 * 4);
         p32[1] = (float*)take(n0 * 4);
         q32 = (float*)take(n0 * 4);
-        phi_pair = pair_copy ? (float*)take(2 * n0 * 4) : nullptr;
+        // hi then lo, each 256-byte aligned (the pair kernels use 16-byte loads)
+        phi_pair = pair_copy ? (float*)take(2 * align256(n0 * 4)) : nullptr;
         ctr = (unsigned*)take(8 * sizeof(unsigned));
         loop = (MxLoop*)take(sizeof(MxLoop));
         const size_t b3 = (size_t)((nx_ + BX - 1) / BX) * ((ny_ + BY - 1) / BY) * ((nz_ + ZC - 1) / ZC);
@@ -1200,7 +1212,7 @@ int poisson_run(const poisson_config* pc, const double* rho, const uint8_t* mask
     if (mixed) {
         const int n = pc->nx * pc->ny * pc->nz;
         float* hi = mg.phi_pair;
-        float* lo = mg.phi_pair + n;
+        float* lo = mg.phi_pair + pic::align256((size_t)n * 4) / 4;
         pic::k_mx_split<<<(n + 255) / 256, 256, 0, s>>>(phi, hi, lo, n);
         rc = mg.solve_mixed(rho, true, mask, hi, lo, nullptr, nullptr, true, pc->dx, pc->v_lo, pc->v_hi, pc->v_mask, rtol,
                             max_cycles, nullptr, Ex, Ey, Ez, s, &cycles, &rel, hn);

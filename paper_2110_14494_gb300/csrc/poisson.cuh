@@ -65,7 +65,7 @@ struct MG {
     float* d32 = nullptr;
     float* p32[2] = {nullptr, nullptr};
     float* q32 = nullptr;
-    float* phi_pair = nullptr;  // [2][n] pair copy for callers that hold phi in float64
+    float* phi_pair = nullptr;  // pair copy for callers that hold phi in float64: hi at 0, lo 256-byte aligned after it
     unsigned* ctr = nullptr;
     double* part = nullptr;
     cudaGraphExec_t g_mx[5] = {};  // first, even, odd iterations, light even, light odd

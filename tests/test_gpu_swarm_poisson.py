@@ -146,6 +146,26 @@ def test_poisson_needle_matches_oracle_and_field():
     assert rel2 <= 1e-6 and cyc2 < 40, (cyc2, rel2)
 
 
+@pytest.mark.parametrize("prec", [64, 32])
+def test_poisson_single_level_grid_matches_oracle(prec):
+    """Odd sizes admit no coarser level: the whole grid (15,525 cells, more
+    than one batch of the tail's loads) is the single-block tail, whose
+    coarsest-level sweeps are the whole preconditioner."""
+    from paper_2110_14494_gb300 import poisson_solve
+    grid = W.grid_spec(25, 23, 27, 5e-5)
+    V0 = 1500.0
+    mask = W.needle_mask(grid, 0.5e-3, 0.12e-3)
+    rho = W.random_rho(grid, 13, 2e-2)
+    ref, rr, it = O.poisson(grid, rho, mask, V0, 0.0, V0, rtol=1e-12)
+    rt = torch.as_tensor(rho).cuda()
+    mt = torch.as_tensor(mask).cuda()
+    phi = torch.zeros_like(rt)
+    cyc, rel = poisson_solve(grid, rt, phi, mask=mt, v_lo=0.0, v_hi=V0, v_mask=V0, rtol=1e-8, max_cycles=1000,
+                             precision=prec)
+    assert rel <= 1e-8, (cyc, rel)
+    assert np.linalg.norm(phi.cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-6
+
+
 def test_poisson_plates_only():
     from paper_2110_14494_gb300 import poisson_solve
     grid = W.grid_spec(16, 16, 64, 2e-5)
