@@ -166,6 +166,30 @@ def test_poisson_single_level_grid_matches_oracle(prec):
     assert np.linalg.norm(phi.cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-6
 
 
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("shape", [(2, 2, 2), (3, 5, 7), (6, 6, 6), (9, 7, 8), (20, 12, 36), (33, 17, 10)])
+def test_poisson_shapes_match_oracle(shape, prec):
+    """Edge shapes of the hierarchy: a single 2^3 level (warp-level tail
+    only), odd sizes without a coarser level, x sizes that are not a multiple
+    of four (the scalar stencil kernels), a tail of several levels, and a
+    one-level coarsening; needle electrode where the grid holds one."""
+    from paper_2110_14494_gb300 import poisson_solve
+    nx, ny, nz = shape
+    h = 4e-5
+    grid = W.grid_spec(nx, ny, nz, h)
+    V0 = 800.0
+    mask = W.needle_mask(grid, 0.4 * nz * h, 1.5 * h) if min(shape) >= 6 else np.zeros((nz, ny, nx), np.uint8)
+    rho = W.random_rho(grid, 3 + nx, 1e-2)
+    ref, rr, it = O.poisson(grid, rho, mask, V0, 0.0, V0, rtol=1e-13)
+    rt = torch.as_tensor(rho).cuda()
+    mt = torch.as_tensor(mask).cuda()
+    phi = torch.zeros_like(rt)
+    cyc, rel = poisson_solve(grid, rt, phi, mask=mt, v_lo=0.0, v_hi=V0, v_mask=V0, rtol=1e-8, max_cycles=1000,
+                             precision=prec)
+    assert rel <= 1e-8, (cyc, rel)
+    assert np.linalg.norm(phi.cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-6
+
+
 def test_poisson_plates_only():
     from paper_2110_14494_gb300 import poisson_solve
     grid = W.grid_spec(16, 16, 64, 2e-5)
