@@ -103,6 +103,35 @@ def test_step_fp64_matches_oracle(steps, boundary):
     assert int(qe.sum()) == int(rq_e.sum()) or abs(int(qe.sum()) - int(rq_e.sum())) < 64
 
 
+@pytest.mark.parametrize("n", [0, 1, 33])
+def test_step_small_counts_match_oracle(n):
+    """Ragged and degenerate populations: no electron (the step launches
+    nothing that reads a particle, the counts stay zero), one electron (one
+    lane of one warp), and one warp plus one; float64, five steps, against
+    the oracle particle by particle."""
+    gas, F, mk, p0 = _setup(max(n, 1), 64, 7)
+    p0 = {k: v[:n] for k, v in p0.items()}
+    dt = 2e-12
+    ctx = _ctx(gas, GRID, 64, capacity=4096, seed=SEED, dt=dt, mask=mk)
+    ctx.set_field(*_field_dev(F))
+    ctx.set_particles(p0)
+    st = ctx.step(5, stats=True)
+    gpu = ctx.get_particles()
+    m = O.Model(gas, dt, SEED, 64, GRID, F, mask=mk)
+    P = O.Particles(4096, p0)
+    ncell = GRID["nx"] * GRID["ny"] * GRID["nz"]
+    rq_pos, rq_neg = np.zeros(ncell, np.int64), np.zeros(ncell, np.int64)
+    for s in range(1, 6):
+        rc, _ = O.step(m, P, s, s == 1, np.zeros(ncell, np.int64), rq_pos, rq_neg)
+        assert rc == 0
+    ref = P.view()
+    if n == 0:
+        assert len(gpu["x"]) == 0 and len(ref["x"]) == 0 and st.n_end == 0 and st.n_events == 0
+        return
+    nc, og, orf, bad, worst = compare_sets(gpu, ref, GRID["dx"], 1e-12, v_floor=1.0)
+    assert og == 0 and orf == 0 and bad == 0, (og, orf, worst)
+
+
 @pytest.mark.parametrize("steps", [1, 10])
 def test_step_fp64_field_matches_oracle(steps):
     """pic_set_field_f64: a float64 context gathers from float64 grids
