@@ -21,6 +21,16 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr int kVBinsPerOctave = 6;
 constexpr int kVBins = 20 * kVBinsPerOctave;  // 2^10 .. 2^30 m/s
 
+// Speed-histogram bin of a velocity (kVBinsPerOctave bins per octave from
+// 2^10 m/s, clamped to the histogram), every operation rounded on its own so
+// that kernels of units compiled with and without contraction bin alike.
+__device__ __forceinline__ int speed_bin(float vx, float vy, float vz) {
+    const float v2 = __fadd_rn(__fadd_rn(__fmul_rn(vx, vx), __fmul_rn(vy, vy)), __fmul_rn(vz, vz));
+    if (!(v2 > 0.0f)) return 0;
+    const int b = (int)floorf(__fmul_rn(__fsub_rn(__fmul_rn(0.5f, log2f(v2)), 10.0f), (float)kVBinsPerOctave));
+    return b < 0 ? 0 : (b >= kVBins ? kVBins - 1 : b);
+}
+
 // Error bits raised by kernels in DevState::err.
 enum : unsigned {
     kErrOutCapacity = 1u,    // output particle buffer full

@@ -277,47 +277,17 @@ __global__ void k_end_step(DevState* st, long long* count_slot, long long cap) {
     if (count_slot) *count_slot = (long long)st->n_in;
 }
 
-// End-of-step statistics for the time-step control (Sec. 2.1.4): a histogram
-// of the electron speeds (for the 90 % quantile of the CFL condition) and the
+// End-of-step statistics for the time-step control (Sec. 2.1.4): the
 // largest and total fixed-point electron deposit (for the dielectric
-// relaxation time and the growth limit).
-// Each thread takes kStatsUnroll elements per trip, one grid stride apart,
-// and issues all their loads before using any, so the grid keeps enough
-// loads in flight to stream both arrays at DRAM speed.
+// relaxation time and the growth limit).  The speed histogram for the 90 %
+// quantile of the CFL condition is formed by the kernels that store the
+// electrons (the collision kernels' output flush and the photoelectron
+// append).  Each thread takes kStatsUnroll cells per trip, one grid stride
+// apart, with all their loads issued before any use.
 constexpr int kStatsUnroll = 4;
 
-__device__ __forceinline__ int speed_bin(float vx, float vy, float vz) {
-    const float v2 = vx * vx + vy * vy + vz * vz;
-    const int b = v2 > 0.0f ? (int)floorf((0.5f * log2f(v2) - 10.0f) * kVBinsPerOctave) : 0;
-    return b < 0 ? 0 : (b >= kVBins ? kVBins - 1 : b);
-}
-
-template <class T>
-__global__ void k_step_stats(const Soa<T> p, const DevState* stc, const unsigned long long* __restrict__ qe,
-                             long long ncell, int nr, DevState* st) {
-    __shared__ unsigned int h[kVBins];
-    for (int b = threadIdx.x; b < kVBins; b += blockDim.x) h[b] = 0;
-    __syncthreads();
-    const long long n = (long long)stc->n_out;
+__global__ void k_step_stats(const unsigned long long* __restrict__ qe, long long ncell, int nr, DevState* st) {
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kStatsUnroll * stride) {
-        T w[kStatsUnroll], vx[kStatsUnroll], vy[kStatsUnroll], vz[kStatsUnroll];
-#pragma unroll
-        for (int u = 0; u < kStatsUnroll; ++u) {
-            const long long i = i0 + u * stride;
-            w[u] = i < n ? p.r[PW][i] : (T)0;
-            vx[u] = i < n ? p.r[VX][i] : (T)0;
-            vy[u] = i < n ? p.r[VY][i] : (T)0;
-            vz[u] = i < n ? p.r[VZ][i] : (T)0;
-        }
-#pragma unroll
-        for (int u = 0; u < kStatsUnroll; ++u) {
-            const int b = w[u] > (T)0 ? speed_bin((float)vx[u], (float)vy[u], (float)vz[u]) : -1;
-            // lanes with the same bin add once (most electrons share a few bins)
-            const unsigned grp = __match_any_sync(__activemask(), b);
-            if (b >= 0 && __ffs(grp) - 1 == (int)(threadIdx.x & 31)) atomicAdd(&h[b], (unsigned)__popc(grp));
-        }
-    }
     long long mx = LLONG_MIN, sm = 0;
     for (long long c0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; c0 < ncell; c0 += kStatsUnroll * stride) {
         long long q[kStatsUnroll];
@@ -359,8 +329,6 @@ __global__ void k_step_stats(const Soa<T> p, const DevState* stc, const unsigned
         atomicMax(&st->qe_max, mx);
         atomicAdd(&st->qe_sum, (unsigned long long)sm);
     }
-    for (int b = threadIdx.x; b < kVBins; b += blockDim.x)
-        if (h[b]) atomicAdd(&st->vhist[b], h[b]);
 }
 
 // Clears error bits (a speculative field solve that was undone).
@@ -1409,6 +1377,7 @@ template <class T> static PushArgs<T> make_args(pic_ctx* c, int mode) {
     for (int d = 0; d < 3; ++d) A.E0[d] = (T)c->E0[d];
     A.mask = c->mask;
     A.q_e = c->qe();
+    A.vhist = mode == MODE_PIC && c->cfg.adaptive_dt ? c->st()->vhist : nullptr;
     A.q_pos = c->qp();
     A.q_neg = c->qn();
     A.boundary = c->cfg.boundary;
@@ -1982,8 +1951,8 @@ template <class T> static int generation_tail(pic_ctx* c, PushArgs<T>& A, int mo
     }
     if (c->cfg.adaptive_dt && mode == MODE_PIC) {
         DevState* st = c->st();
-        cudaMemsetAsync(&st->qe_max, 0, sizeof(long long) + sizeof(unsigned long long) + sizeof(st->vhist), c->s);
-        k_step_stats<T><<<device_sms() * 4, 256, 0, c->s>>>(A.out, st, c->qe(), c->g.ncell(), c->g.axi ? c->g.nx : 0, st);
+        cudaMemsetAsync(&st->qe_max, 0, sizeof(long long) + sizeof(unsigned long long), c->s);
+        k_step_stats<<<device_sms() * 4, 256, 0, c->s>>>(c->qe(), c->g.ncell(), c->g.axi ? c->g.nx : 0, st);
         c->launches += 1;
     }
     return PIC_OK;
@@ -2116,6 +2085,8 @@ template <class T> static int one_step(pic_ctx* c, bool stats, bool* solved) {
     c->step++;
     PushArgs<T> A = make_args<T>(c, MODE_PIC);
     cudaMemsetAsync(c->qe(), 0, (size_t)c->g.ncell() * 8, c->s);
+    // the step's speed histogram accumulates over every kernel that stores its electrons
+    if (A.vhist) cudaMemsetAsync(A.vhist, 0, sizeof(c->st()->vhist), c->s);
     c->mark(0);
     c->launches += 3;
     // the gather and half-kick of Eq. 2 are done as the collision kernel loads each parent

@@ -52,6 +52,7 @@ template <class T> struct PushArgs {
     T E0[3];
     const uint8_t* mask;
     unsigned long long *q_e, *q_pos, *q_neg;
+    unsigned int* vhist;  // speed histogram of the stored electrons (adaptive time step), or null
     int boundary;
     int axi;                   // axisymmetric grid (see grid_pt)
     // photoionization (Sec. 2.4): emission probability per ionization, the
@@ -706,6 +707,7 @@ __global__ void __launch_bounds__(256) k_photo_append(const PushArgs<T> A) {
         }
         store(A.out, slot, x, v, a, w, A.ph_id[i]);
         if (A.q_e) deposit_at(A, x[0], x[1], x[2], w, A.q_e);
+        if (A.vhist && w > (T)0) atomicAdd(&A.vhist[0], 1u);  // at rest: the lowest speed bin
     }
 }
 
@@ -818,10 +820,12 @@ __device__ __forceinline__ void flush_out(const PushArgs<T>& A, Stage<T>* sg, in
         unsigned long long s0 = 0;
         if (lane == 0) s0 = atomicAdd(&A.st->n_out, (unsigned long long)__popc(m));
         s0 = __shfl_sync(kFull, s0, 0);
+        bool stored = false;
         if (live) {
             const unsigned long long slot = s0 + __popc(m & ((1u << lane) - 1u));
             if ((long long)slot < A.cap_out) {
                 store(A.out, slot, x, v, a, w, id);
+                stored = true;
                 if (MODE == MODE_PIC) {
                     if (A.q_e) deposit_at(A, x[0], x[1], x[2], w, A.q_e);
                 } else {
@@ -830,6 +834,13 @@ __device__ __forceinline__ void flush_out(const PushArgs<T>& A, Stage<T>* sg, in
             } else {
                 atomicOr(&A.st->err, kErrOutCapacity);
             }
+        }
+        if (MODE == MODE_PIC && A.vhist) {
+            // the speed histogram of the time-step control (Sec. 2.1.4) over the stored electrons; lanes
+            // with the same bin add once
+            const int b = stored && w > (T)0 ? speed_bin((float)v[0], (float)v[1], (float)v[2]) : -1;
+            const unsigned grp = __match_any_sync(kFull, b);
+            if (b >= 0 && __ffs(grp) - 1 == lane) atomicAdd(&A.vhist[b], (unsigned)__popc(grp));
         }
     }
     __syncwarp();
