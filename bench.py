@@ -36,15 +36,15 @@ BYTES_PER_UPDATE = 96          # float32 state x,v,a,w (40 B) + id (8 B), read a
 BYTES_PER_CHILD = 48           # an ionization product is born in registers: its state is written once
 WORKLOAD = "streamer-128^3-fp32"
 # DRAM bytes (read + write) per particle-update of the collision kernel in this workload's steady state, from
-# the ncu capture summarised in profiles/k_push_streamer128.md (46.6 MB per launch of ~9.2e5 updates); scaled to
+# the ncu capture summarised in profiles/k_push_streamer128.md (45.9 MB per launch of ~9.2e5 updates); scaled to
 # the run's mean launch for roofline.traffic.  Only valid for the kernel build and workload it was taken on.
-PUSH_DRAM_BYTES_PER_UPDATE = 50.8
+PUSH_DRAM_BYTES_PER_UPDATE = 50.0
 # The collision kernels (parents and children) issue about this many warp
 # instructions per collision draw (a candidate event, or the last draw that
 # ends the step): ncu smsp__inst_executed.sum over three steady-state steps /
 # (updates x draws per update), from profiles/k_push_streamer128.md
-# (5.061e8 / (2.752e6 x 11.076)).
-PUSH_WARP_INST_PER_DRAW = 16.61
+# (5.151e8 / (2.752e6 x 11.076)).
+PUSH_WARP_INST_PER_DRAW = 16.90
 ISSUE_SLOTS_PER_SM = 4   # warp schedulers per SM, one warp instruction each per clock
 
 
