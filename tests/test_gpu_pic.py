@@ -461,7 +461,7 @@ def test_step_with_photoionization_matches_oracle(prec, steps):
         print(f"photo fp32: energy error 90th percentile {delta:.3g}; under it the oracle has {c_flips} flips and "
               f"{c_bad} more outside 1e-5; float32: {worst['gross'] + og + orf} flips, {bad - worst['gross']} more "
               f"of {len(ref['id'])}")
-        # flips: the benchmark spec bound plus the decisions that the oracle's own conditioning puts within the
+        # flips: the stated 1e-5 N + 2 bound plus the decisions that the oracle's own conditioning puts within the
         # float32 error of their thresholds (photon emission and absorption add such decisions); the other
         # particles outside 1e-5 within twice the conditioning count
         assert worst["gross"] + og + orf <= 1e-5 * len(ref["id"]) + 2 + c_flips, (og, orf, worst, c_flips)
