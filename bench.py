@@ -36,13 +36,13 @@ BYTES_PER_UPDATE = 96          # float32 state x,v,a,w (40 B) + id (8 B), read a
 BYTES_PER_CHILD = 48           # an ionization product is born in registers: its state is written once
 WORKLOAD = "streamer-128^3-fp32"
 # DRAM bytes (read + write) per particle-update of the collision kernel in this workload's steady state, from
-# the ncu capture summarised in profiles/k_push_streamer128.md (45.9 MB per launch of ~9.2e5 updates); scaled to
+# the steady-state ncu capture of the collision kernel summarised under profiles/ (45.9 MB per launch of ~9.2e5 updates); scaled to
 # the run's mean launch for roofline.traffic.  Only valid for the kernel build and workload it was taken on.
 PUSH_DRAM_BYTES_PER_UPDATE = 50.0
 # The collision kernels (parents and children) issue about this many warp
 # instructions per collision draw (a candidate event, or the last draw that
 # ends the step): ncu smsp__inst_executed.sum over three steady-state steps /
-# (updates x draws per update), from profiles/k_push_streamer128.md
+# (updates x draws per update), from the same capture
 # (5.151e8 / (2.752e6 x 11.076)).
 PUSH_WARP_INST_PER_DRAW = 16.90
 ISSUE_SLOTS_PER_SM = 4   # warp schedulers per SM, one warp instruction each per clock
@@ -268,7 +268,7 @@ def issue_roofline(draws_per_update, updates_per_step, collide_ms_per_step, clk,
             "achieved": ach, "peak": peak, "frac": ach / peak, "draws_per_update": draws_per_update,
             "warp_inst_per_draw": PUSH_WARP_INST_PER_DRAW,
             "source": "draws measured over 10 steps after the timed region; instructions per draw from ncu "
-                      "(profiles/k_push_streamer128.md); peak at the sampled median SM clock"}
+                      "(collision-kernel summary under profiles/); peak at the sampled median SM clock"}
 
 
 class Clocks:
@@ -871,7 +871,7 @@ def main():
                                      if (args.workload == "streamer" and args.grid == 128 and args.precision == 32)
                                      else None),
                          "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per particle-update, "
-                                           "profiles/k_push_streamer128.md, scaled to the mean launch",
+                                           "collision-kernel summary under profiles/, scaled to the mean launch",
                          "kernel": "k_push<%s,PIC>" % ("float" if args.precision == 32 else "double"),
                          "peak_source": peak_kind,
                          "algorithmic_bytes_per_launch": launch_bytes,
